@@ -1,0 +1,636 @@
+/*
+ * ls_oracle.c -- the ORACLE for the dense Krylov solvers.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously-correct
+ * FP64 CPU statement of what the GPU library computes.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA library, and the
+ * library never calls it.
+ *
+ * Paper: Oancea, Andrei, Dragoescu, "Improving the performance of the linear
+ * systems solvers using CUDA" (arXiv:1511.07207).
+ *   - Krylov frame x(i) = x(i-1) + d(i), inner products / saxpy / matvec:
+ *     section "Serial iterative and direct methods", opening paragraphs.
+ *   - Conjugate gradient: same section, CG paragraph (prose only; the paper
+ *     points to Golub & Van Loan for the full statement, which is the
+ *     Hestenes-Stiefel form written out below).
+ *   - GMRES: same section, GMRES pseudocode (Arnoldi with Gram-Schmidt) and
+ *     the restart paragraph that follows it.  The paper stops before the
+ *     least-squares step; the Givens-rotation update used here is the
+ *     standard one from Saad's book, which the paper cites for GMRES.
+ *   - Gaussian elimination with partial pivoting: same section,
+ *     "Right-looking LU factorization", then forward/back substitution.
+ *   - Mixed precision (BF16 / FP8-e4m3 storage of A, FP32 inner CG, FP64
+ *     outer refinement) extends the paper's single/double precision axis
+ *     (section "Results").
+ *
+ * Parity status: every function here is pinned by tests/test_oracle_*.py
+ * against mathematics that does not depend on this file (numpy/LAPACK
+ * solves and least squares, Krylov optimality, Arnoldi relation,
+ * finite termination, nearest-value brute force for the roundings).
+ *
+ * Conventions: A is row-major with leading dimension lda >= n (element
+ * (i,j) at A[i*lda + j]).  Status codes: 0 converged, 1 not converged,
+ * 2 breakdown, -1 bad argument.
+ *
+ * Build: plain C99, -O2 -ffp-contract=off (no fused multiply-add, no
+ * reassociation), optional -fopenmp which only splits the rows of a
+ * matrix-vector product across threads (each row's sum keeps its order,
+ * so results do not depend on the thread count).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_NOT_CONVERGED 1
+#define OR_BREAKDOWN 2
+#define OR_ERR_ARG (-1)
+
+/* ------------------------------------------------------------------ */
+/* BLAS-1/2 in plain loops                                             */
+/* ------------------------------------------------------------------ */
+
+static double dot(int n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += x[i] * y[i];
+    return s;
+}
+
+static double nrm2(int n, const double *x) { return sqrt(dot(n, x, x)); }
+
+/* y = A x, row by row, each row summed left to right. */
+static void gemv(int nrows, int ncols, const double *A, long lda,
+                 const double *x, double *y, int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#else
+    (void)nthreads;
+#endif
+    for (int i = 0; i < nrows; i++) {
+        const double *a = A + (long)i * lda;
+        double s = 0.0;
+        for (int j = 0; j < ncols; j++) s += a[j] * x[j];
+        y[i] = s;
+    }
+}
+
+int or_gemv(int nrows, int ncols, const double *A, long lda, const double *x,
+            double *y, int nthreads) {
+    if (nrows < 0 || ncols < 0 || lda < ncols) return OR_ERR_ARG;
+    gemv(nrows, ncols, A, lda, x, y, nthreads);
+    return OR_OK;
+}
+
+/* r = b - A x */
+static void residual(int n, const double *A, long lda, const double *b,
+                     const double *x, double *r, int nthreads) {
+    gemv(n, n, A, lda, x, r, nthreads);
+    for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
+}
+
+int or_residual(int n, const double *A, long lda, const double *b,
+                const double *x, double *r, int nthreads) {
+    if (n < 0 || lda < n) return OR_ERR_ARG;
+    residual(n, A, lda, b, x, r, nthreads);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Conjugate gradient (Hestenes-Stiefel), FP64                         */
+/* ------------------------------------------------------------------ */
+/*
+ * Solves A x = b for SPD A.  Stops when the recursively updated residual
+ * satisfies ||r|| <= rtol ||b||; the true residual b - A x is then
+ * recomputed and, if it does not pass, the iteration restarts from it
+ * (r = b - A x, p = r).  iters counts the matrix-vector products inside the
+ * loop.  Optional histories (for tests on small n): R_hist and P_hist are
+ * column-major n x (max_iter+1) arrays receiving r_k and p_k, res_hist
+ * receives ||r_k|| for k = 0..iters.
+ */
+int or_cg(int n, const double *A, long lda, const double *b, double *x,
+          double rtol, int max_iter, int x0_given, int nthreads,
+          int *iters_out, double *rel_res_out,
+          double *res_hist, double *R_hist, double *P_hist) {
+    if (n < 0 || lda < n || max_iter < 0) return OR_ERR_ARG;
+    double *r = malloc(sizeof(double) * (n ? n : 1));
+    double *p = malloc(sizeof(double) * (n ? n : 1));
+    double *q = malloc(sizeof(double) * (n ? n : 1));
+    int status = OR_NOT_CONVERGED, k = 0;
+    double nb = nrm2(n, b), rho;
+
+    if (!x0_given) {
+        for (int i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
+    } else {
+        residual(n, A, lda, b, x, r, nthreads);
+    }
+    if (nb == 0.0) {                      /* b = 0: x = 0 solves exactly */
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        *iters_out = 0; *rel_res_out = 0.0;
+        free(r); free(p); free(q);
+        return OR_OK;
+    }
+    memcpy(p, r, sizeof(double) * n);
+    rho = dot(n, r, r);
+    if (res_hist) res_hist[0] = sqrt(rho);
+    if (R_hist) memcpy(R_hist, r, sizeof(double) * n);
+    if (P_hist) memcpy(P_hist, p, sizeof(double) * n);
+
+    int check = sqrt(rho) <= rtol * nb;
+    for (;;) {
+        if (check) {
+            /* recursive residual passed: confirm with the true residual */
+            residual(n, A, lda, b, x, q, nthreads);
+            double t = nrm2(n, q);
+            if (t <= rtol * nb) { status = OR_OK; break; }
+            memcpy(r, q, sizeof(double) * n);
+            memcpy(p, r, sizeof(double) * n);
+            rho = dot(n, r, r);
+            check = 0;
+        }
+        if (k >= max_iter) break;
+        gemv(n, n, A, lda, p, q, nthreads);          /* q = A p */
+        double pq = dot(n, p, q);
+        if (!(pq > 0.0)) { status = OR_BREAKDOWN; break; }  /* not SPD, or NaN */
+        double alpha = rho / pq;
+        for (int i = 0; i < n; i++) x[i] += alpha * p[i];
+        for (int i = 0; i < n; i++) r[i] -= alpha * q[i];
+        double rho_new = dot(n, r, r);
+        k++;
+        if (res_hist) res_hist[k] = sqrt(rho_new);
+        if (sqrt(rho_new) <= rtol * nb) {
+            check = 1;
+            rho = rho_new;
+            if (R_hist) memcpy(R_hist + (long)k * n, r, sizeof(double) * n);
+            continue;
+        }
+        double beta = rho_new / rho;
+        for (int i = 0; i < n; i++) p[i] = r[i] + beta * p[i];
+        rho = rho_new;
+        if (R_hist) memcpy(R_hist + (long)k * n, r, sizeof(double) * n);
+        if (P_hist) memcpy(P_hist + (long)k * n, p, sizeof(double) * n);
+    }
+    residual(n, A, lda, b, x, q, nthreads);
+    *rel_res_out = nrm2(n, q) / nb;
+    *iters_out = k;
+    free(r); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Restarted GMRES(m), FP64                                            */
+/* ------------------------------------------------------------------ */
+/*
+ * Each cycle: r = b - A x, beta = ||r||, v_1 = r / beta, g = beta e_1.
+ * Arnoldi step k: w = A v_k; modified Gram-Schmidt against v_1..v_k
+ * (h_jk = w . v_j, w -= h_jk v_j), with one more full pass when
+ * ||w|| < 0.7 ||A v_k|| (its coefficients are added to h); h_{k+1,k} = ||w||;
+ * v_{k+1} = w / h_{k+1,k}.  The previous Givens rotations are applied to
+ * column k, a new rotation (c, s) = (h_kk, h_{k+1,k}) / hypot(...) zeroes
+ * h_{k+1,k}, and g_{k+1} = -s g_k, g_k = c g_k, so |g_{k+1}| is the residual
+ * norm of the current cycle iterate.  The cycle ends when
+ * |g_{k+1}| <= rtol ||b||, when k = m, when the total step count reaches
+ * max_iter, or on a (lucky) breakdown h_{k+1,k} <= 1e-14 ||A v_k||.  Then
+ * R y = g is back-solved and x += V_k y.  The outer loop stops when the true
+ * residual passes.  iters counts Arnoldi steps over all cycles.
+ *
+ * Optional first-cycle outputs for tests: V1 (column-major n x (m+1)),
+ * H1 (column-major (m+1) x m, the unrotated Hessenberg matrix) and k1 (the
+ * number of Arnoldi steps of the first cycle).  est_out receives the last
+ * |g_{k+1}| / ||b||.
+ */
+int or_gmres(int n, const double *A, long lda, const double *b, double *x,
+             int m, double rtol, int max_iter, int x0_given, int nthreads,
+             int *iters_out, int *cycles_out, double *rel_res_out,
+             double *est_out, double *V1, double *H1, int *k1) {
+    if (n < 0 || lda < n || m < 1 || max_iter < 0) return OR_ERR_ARG;
+    long ln = n ? n : 1;
+    double *V = calloc((size_t)ln * (m + 1), sizeof(double));
+    double *H = calloc((size_t)(m + 1) * m, sizeof(double));  /* rotated, col-major */
+    double *Hraw = calloc((size_t)(m + 1) * m, sizeof(double));
+    double *cs = calloc(m, sizeof(double)), *sn = calloc(m, sizeof(double));
+    double *g = calloc(m + 1, sizeof(double)), *y = calloc(m, sizeof(double));
+    double *w = malloc(sizeof(double) * ln), *r = malloc(sizeof(double) * ln);
+    int status = OR_NOT_CONVERGED, total = 0, cycles = 0;
+    double nb = nrm2(n, b), est = 0.0;
+#define HR(i, j) H[(long)(j) * (m + 1) + (i)]
+#define HW(i, j) Hraw[(long)(j) * (m + 1) + (i)]
+
+    if (!x0_given) for (int i = 0; i < n; i++) x[i] = 0.0;
+    if (k1) *k1 = 0;
+    if (nb == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        *iters_out = 0; *cycles_out = 0; *rel_res_out = 0.0;
+        if (est_out) *est_out = 0.0;
+        status = OR_OK;
+        goto done;
+    }
+    for (;;) {
+        residual(n, A, lda, b, x, r, nthreads);
+        double beta = nrm2(n, r);
+        if (beta <= rtol * nb) { status = OR_OK; break; }
+        if (total >= max_iter) break;
+        cycles++;
+        for (int i = 0; i < n; i++) V[i] = r[i] / beta;
+        memset(g, 0, sizeof(double) * (m + 1));
+        memset(H, 0, sizeof(double) * (m + 1) * m);
+        memset(Hraw, 0, sizeof(double) * (m + 1) * m);
+        g[0] = beta;
+        int k = 0, stop = 0;
+        while (k < m && total < max_iter && !stop) {
+            double *vk = V + (long)k * n, *vn = V + (long)(k + 1) * n;
+            gemv(n, n, A, lda, vk, w, nthreads);
+            double wnorm0 = nrm2(n, w);
+            for (int j = 0; j <= k; j++) {                  /* MGS */
+                double h = dot(n, w, V + (long)j * n);
+                HR(j, k) = h;
+                for (int i = 0; i < n; i++) w[i] -= h * V[(long)j * n + i];
+            }
+            double wnorm = nrm2(n, w);
+            if (wnorm < 0.7 * wnorm0) {                     /* second pass */
+                for (int j = 0; j <= k; j++) {
+                    double h = dot(n, w, V + (long)j * n);
+                    HR(j, k) += h;
+                    for (int i = 0; i < n; i++) w[i] -= h * V[(long)j * n + i];
+                }
+                wnorm = nrm2(n, w);
+            }
+            HR(k + 1, k) = wnorm;
+            for (int j = 0; j <= k + 1; j++) HW(j, k) = HR(j, k);
+            int lucky = !(wnorm > 1e-14 * wnorm0);
+            if (!lucky) for (int i = 0; i < n; i++) vn[i] = w[i] / wnorm;
+            /* apply the earlier rotations to column k */
+            for (int j = 0; j < k; j++) {
+                double a = HR(j, k), c = HR(j + 1, k);
+                HR(j, k) = cs[j] * a + sn[j] * c;
+                HR(j + 1, k) = -sn[j] * a + cs[j] * c;
+            }
+            double den = hypot(HR(k, k), HR(k + 1, k));
+            if (den == 0.0) { status = OR_BREAKDOWN; stop = 2; break; }
+            cs[k] = HR(k, k) / den;
+            sn[k] = HR(k + 1, k) / den;
+            HR(k, k) = den;
+            HR(k + 1, k) = 0.0;
+            g[k + 1] = -sn[k] * g[k];
+            g[k] = cs[k] * g[k];
+            k++;
+            total++;
+            est = fabs(g[k]) / nb;
+            if (fabs(g[k]) <= rtol * nb || lucky) stop = 1;
+        }
+        if (cycles == 1) {
+            if (V1) memcpy(V1, V, sizeof(double) * n * (k + 1 <= m + 1 ? k + 1 : m + 1));
+            if (H1) memcpy(H1, Hraw, sizeof(double) * (m + 1) * m);
+            if (k1) *k1 = k;
+        }
+        if (stop == 2) break;
+        /* back-solve R y = g on the leading k x k block */
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int j = i + 1; j < k; j++) s -= HR(i, j) * y[j];
+            y[i] = s / HR(i, i);
+        }
+        for (int j = 0; j < k; j++)
+            for (int i = 0; i < n; i++) x[i] += V[(long)j * n + i] * y[j];
+    }
+    residual(n, A, lda, b, x, r, nthreads);
+    *rel_res_out = nrm2(n, r) / nb;
+    *iters_out = total;
+    *cycles_out = cycles;
+    if (est_out) *est_out = est;
+done:
+    free(V); free(H); free(Hraw); free(cs); free(sn); free(g); free(y);
+    free(w); free(r);
+#undef HR
+#undef HW
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gaussian elimination with partial pivoting (check solve, tiny n)    */
+/* ------------------------------------------------------------------ */
+/*
+ * Right-looking LU with partial pivoting: at step k pick the row v >= k
+ * with the largest |A(v,k)| (first one on ties), swap rows k and v (and the
+ * right-hand side), divide the sub-column by the pivot and subtract the
+ * rank-1 update from the trailing block.  Then L y = P b (unit lower,
+ * forward) and U x = y (back).  Returns OR_BREAKDOWN on a zero pivot.
+ */
+int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
+    if (n < 0 || lda < n) return OR_ERR_ARG;
+    double *W = malloc(sizeof(double) * (size_t)(n ? n : 1) * (n ? n : 1));
+    double *y = malloc(sizeof(double) * (n ? n : 1));
+    for (int i = 0; i < n; i++) {
+        memcpy(W + (long)i * n, A + (long)i * lda, sizeof(double) * n);
+        y[i] = b[i];
+    }
+    int status = OR_OK;
+    for (int k = 0; k < n; k++) {
+        int v = k;
+        double best = fabs(W[(long)k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double a = fabs(W[(long)i * n + k]);
+            if (a > best) { best = a; v = i; }
+        }
+        if (v != k) {
+            for (int j = 0; j < n; j++) {
+                double t = W[(long)k * n + j];
+                W[(long)k * n + j] = W[(long)v * n + j];
+                W[(long)v * n + j] = t;
+            }
+            double t = y[k]; y[k] = y[v]; y[v] = t;
+        }
+        double piv = W[(long)k * n + k];
+        if (piv == 0.0) { status = OR_BREAKDOWN; break; }
+        for (int i = k + 1; i < n; i++) {
+            double l = W[(long)i * n + k] / piv;
+            W[(long)i * n + k] = l;
+            for (int j = k + 1; j < n; j++) W[(long)i * n + j] -= l * W[(long)k * n + j];
+            y[i] -= l * y[k];                     /* forward substitution, fused */
+        }
+    }
+    if (status == OR_OK) {
+        for (int i = n - 1; i >= 0; i--) {        /* back substitution */
+            double s = y[i];
+            for (int j = i + 1; j < n; j++) s -= W[(long)i * n + j] * x[j];
+            x[i] = s / W[(long)i * n + i];
+        }
+    }
+    free(W); free(y);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Low-precision storage formats                                       */
+/* ------------------------------------------------------------------ */
+/*
+ * Both roundings are written from the format definitions: the value is
+ * scaled by its quantum (the spacing of the format at that magnitude),
+ * rounded to the nearest integer with ties to even (rint under the
+ * default rounding mode), and scaled back.
+ *
+ * BF16: 1 sign, 8 exponent (bias 127), 7 fraction bits; normal numbers
+ * carry 8 significant bits, so the quantum at |d| in [2^e, 2^(e+1)) is
+ * 2^(e-7); below 2^-126 the quantum is 2^-133.  Overflow goes to infinity.
+ */
+static double round_to_quantum(double d, double q) { return rint(d / q) * q; }
+
+double or_bf16_round(double d) {
+    if (isnan(d) || isinf(d) || d == 0.0) return d;
+    int e;
+    frexp(d, &e);                /* |d| in [2^(e-1), 2^e) */
+    int ex = e - 1;
+    double q = ex < -126 ? ldexp(1.0, -133) : ldexp(1.0, ex - 7);
+    double v = round_to_quantum(d, q);
+    const double maxv = ldexp(255.0, 120);           /* (2 - 2^-7) 2^127 */
+    if (fabs(v) > maxv) return copysign(INFINITY, d);
+    return v;
+}
+
+static uint16_t bf16_bits(double v) {
+    if (isnan(v)) return 0x7FC0;
+    float f = (float)v;                               /* exact: v is a BF16 value */
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (uint16_t)(u >> 16);
+}
+
+/*
+ * FP8 E4M3 (the "fn" variant: no infinities, one NaN pattern per sign):
+ * 1 sign, 4 exponent (bias 7), 3 fraction bits.  Normal numbers (>= 2^-6)
+ * carry 4 significant bits, quantum 2^(e-3); subnormals have quantum 2^-9.
+ * Largest finite value 448 = 1.75 * 2^8.  Saturating conversion: results
+ * beyond 448 in magnitude become +-448.
+ */
+double or_e4m3_round(double d) {
+    if (isnan(d)) return d;
+    if (isinf(d)) return copysign(448.0, d);
+    if (d == 0.0) return d;
+    int e;
+    frexp(d, &e);
+    int ex = e - 1;
+    double q = ex < -6 ? ldexp(1.0, -9) : ldexp(1.0, ex - 3);
+    double v = round_to_quantum(d, q);
+    if (fabs(v) > 448.0) v = copysign(448.0, d);
+    return v;
+}
+
+static uint8_t e4m3_bits(double v) {
+    if (isnan(v)) return 0x7F;
+    uint8_t s = signbit(v) ? 0x80 : 0x00;
+    double a = fabs(v);
+    if (a == 0.0) return s;
+    if (a < ldexp(1.0, -6)) return s | (uint8_t)(a / ldexp(1.0, -9));   /* subnormal */
+    int e;
+    double f = frexp(a, &e);                           /* a = f 2^e, f in [0.5,1) */
+    int ex = e - 1;                                    /* a = (2f) 2^ex */
+    int mant = (int)((2.0 * f - 1.0) * 8.0);
+    return s | (uint8_t)((ex + 7) << 3) | (uint8_t)mant;
+}
+
+double or_e4m3_decode(uint8_t c) {
+    int s = c >> 7, ex = (c >> 3) & 15, m = c & 7;
+    if (ex == 15 && m == 7) return NAN;
+    double v = ex == 0 ? ldexp((double)m, -9) : ldexp(1.0 + m / 8.0, ex - 7);
+    return s ? -v : v;
+}
+
+double or_bf16_decode(uint16_t c) {
+    uint32_t u = (uint32_t)c << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* Quantise a row-major n x n matrix to BF16 codes (row-major, ldq). */
+int or_quant_bf16(int nrows, int ncols, const double *A, long lda,
+                  uint16_t *Q, long ldq) {
+    if (nrows < 0 || ncols < 0 || lda < ncols || ldq < ncols) return OR_ERR_ARG;
+    for (int i = 0; i < nrows; i++)
+        for (int j = 0; j < ncols; j++)
+            Q[(long)i * ldq + j] = bf16_bits(or_bf16_round(A[(long)i * lda + j]));
+    return OR_OK;
+}
+
+/*
+ * Quantise to FP8-e4m3 with one FP32 scale per row:
+ * s_i = fp32(max_j |a_ij| / 448) (1 when that is zero), and
+ * q_ij = e4m3_sat(a_ij / s_i) with the division done in FP64.
+ * The stored matrix represents s_i * q_ij.
+ */
+int or_quant_fp8(int nrows, int ncols, const double *A, long lda,
+                 uint8_t *Q, long ldq, float *scale) {
+    if (nrows < 0 || ncols < 0 || lda < ncols || ldq < ncols) return OR_ERR_ARG;
+    for (int i = 0; i < nrows; i++) {
+        const double *a = A + (long)i * lda;
+        double mx = 0.0;
+        for (int j = 0; j < ncols; j++) if (fabs(a[j]) > mx) mx = fabs(a[j]);
+        float s = (float)(mx / 448.0);
+        if (!(s > 0.0f)) s = 1.0f;          /* all-zero row, or scale underflow */
+        scale[i] = s;
+        for (int j = 0; j < ncols; j++)
+            Q[(long)i * ldq + j] = e4m3_bits(or_e4m3_round(a[j] / (double)s));
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mixed precision: FP32 inner CG on the stored matrix, FP64 outer      */
+/* ------------------------------------------------------------------ */
+/*
+ * The stored matrix is given dequantised as FP32 values Af (row-major,
+ * ldf) -- exact for BF16 codes -- plus an optional FP32 row scale: the
+ * inner product is y_i = s_i * sum_j Af_ij p_j in FP32 arithmetic
+ * (s = NULL means s_i = 1).  For FP8 storage Af holds the decoded e4m3
+ * codes, exact in FP32.
+ */
+static void gemv_f32(int n, const float *Af, long ldf, const float *scale,
+                     const float *p, float *y, int nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#else
+    (void)nthreads;
+#endif
+    for (int i = 0; i < n; i++) {
+        const float *a = Af + (long)i * ldf;
+        float s = 0.0f;
+        for (int j = 0; j < n; j++) s += a[j] * p[j];
+        y[i] = scale ? scale[i] * s : s;
+    }
+}
+
+static float dot_f32(int n, const float *x, const float *y) {
+    float s = 0.0f;
+    for (int i = 0; i < n; i++) s += x[i] * y[i];
+    return s;
+}
+
+/*
+ * Inner solve: z ~ Ahat^{-1} rhs by CG in FP32 from z = 0, for at most
+ * `iters` iterations or until ||r|| <= inner_rtol ||rhs|| (inner_rtol <= 0
+ * disables the tolerance test).  A non-positive curvature stops the inner
+ * loop (z keeps its last value; if that is the first iteration z = rhs).
+ * Returns the number of iterations done.
+ */
+int or_cg_f32(int n, const float *Af, long ldf, const float *scale,
+              const float *rhs, float *z, int iters, float inner_rtol,
+              int nthreads) {
+    float *r = malloc(sizeof(float) * (n ? n : 1));
+    float *p = malloc(sizeof(float) * (n ? n : 1));
+    float *q = malloc(sizeof(float) * (n ? n : 1));
+    for (int i = 0; i < n; i++) { z[i] = 0.0f; r[i] = rhs[i]; p[i] = rhs[i]; }
+    float rho = dot_f32(n, r, r);
+    float stop = inner_rtol > 0.0f ? inner_rtol * inner_rtol * rho : -1.0f;
+    int k = 0;
+    for (; k < iters; k++) {
+        if (rho <= stop || rho == 0.0f) break;
+        gemv_f32(n, Af, ldf, scale, p, q, nthreads);
+        float pq = dot_f32(n, p, q);
+        if (!(pq > 0.0f)) {
+            if (k == 0) for (int i = 0; i < n; i++) z[i] = rhs[i];
+            break;
+        }
+        float alpha = rho / pq;
+        for (int i = 0; i < n; i++) z[i] += alpha * p[i];
+        for (int i = 0; i < n; i++) r[i] -= alpha * q[i];
+        float rho_new = dot_f32(n, r, r);
+        float beta = rho_new / rho;
+        for (int i = 0; i < n; i++) p[i] = r[i] + beta * p[i];
+        rho = rho_new;
+    }
+    free(r); free(p); free(q);
+    return k;
+}
+
+/*
+ * Outer FP64 loop driven by the FP64 residual.
+ *   mode 0 (flexible CG, Notay 2000): z_k = ||r|| * inner(r / ||r||);
+ *     p_k = z_k - sum_{j<k} (z_k . w_j / p_j . w_j) p_j with w_j = A p_j
+ *     (FP64), alpha = (p_k . r) / (p_k . w_k), x += alpha p_k,
+ *     r -= alpha w_k.  Every stored direction is kept (full
+ *     A-orthogonalisation).
+ *   mode 1 (classic refinement): r = b - A x (FP64), x += ||r|| inner(r/||r||).
+ * Stops when ||r|| <= rtol ||b||, confirmed on the true residual (the
+ * recursive FCG residual is replaced by the true one when it is not).
+ * outer_out counts outer steps, inner_out the inner CG iterations.
+ * P_out (optional, n x max_outer column-major) receives the FCG directions.
+ */
+int or_mixed_cg(int n, const double *A, long lda, const float *Af, long ldf,
+                const float *scale, const double *b, double *x, double rtol,
+                int max_outer, int inner_iters, double inner_rtol, int mode,
+                int nthreads, int *outer_out, int *inner_out,
+                double *rel_res_out, double *res_hist, double *P_out) {
+    if (n < 0 || lda < n || ldf < n || max_outer < 0) return OR_ERR_ARG;
+    long ln = n ? n : 1;
+    double *r = malloc(sizeof(double) * ln), *z = malloc(sizeof(double) * ln);
+    double *P = malloc(sizeof(double) * ln * (max_outer + 1));
+    double *W = malloc(sizeof(double) * ln * (max_outer + 1));
+    double *pw = malloc(sizeof(double) * (max_outer + 1));
+    float *rf = malloc(sizeof(float) * ln), *zf = malloc(sizeof(float) * ln);
+    int status = OR_NOT_CONVERGED, outer = 0, inner = 0, nstored = 0;
+    double nb = nrm2(n, b);
+    for (int i = 0; i < n; i++) x[i] = 0.0;
+    if (nb == 0.0) {
+        *outer_out = 0; *inner_out = 0; *rel_res_out = 0.0;
+        status = OR_OK;
+        goto done;
+    }
+    for (int i = 0; i < n; i++) r[i] = b[i];
+    int recursive = 0;          /* r is a recursively updated residual */
+    for (;;) {
+        double rn = nrm2(n, r);
+        if (res_hist) res_hist[outer] = rn / nb;
+        if (rn <= rtol * nb) {
+            if (!recursive) { status = OR_OK; break; }
+            residual(n, A, lda, b, x, r, nthreads);   /* confirm */
+            recursive = 0;
+            continue;
+        }
+        if (!(rn == rn)) { status = OR_BREAKDOWN; break; }
+        if (outer >= max_outer) break;
+        for (int i = 0; i < n; i++) rf[i] = (float)(r[i] / rn);
+        inner += or_cg_f32(n, Af, ldf, scale, rf, zf, inner_iters,
+                           (float)inner_rtol, nthreads);
+        for (int i = 0; i < n; i++) z[i] = rn * (double)zf[i];
+        outer++;
+        if (mode == 1) {
+            for (int i = 0; i < n; i++) x[i] += z[i];
+            residual(n, A, lda, b, x, r, nthreads);
+            continue;
+        }
+        double *p = P + (long)nstored * n, *w = W + (long)nstored * n;
+        memcpy(p, z, sizeof(double) * n);
+        for (int j = 0; j < nstored; j++) {
+            double c = dot(n, z, W + (long)j * n) / pw[j];
+            for (int i = 0; i < n; i++) p[i] -= c * P[(long)j * n + i];
+        }
+        gemv(n, n, A, lda, p, w, nthreads);
+        double d = dot(n, p, w);
+        if (!(d > 0.0)) { status = OR_BREAKDOWN; break; }
+        double alpha = dot(n, p, r) / d;
+        for (int i = 0; i < n; i++) x[i] += alpha * p[i];
+        for (int i = 0; i < n; i++) r[i] -= alpha * w[i];
+        pw[nstored++] = d;
+        recursive = 1;
+    }
+    residual(n, A, lda, b, x, r, nthreads);
+    *rel_res_out = nrm2(n, r) / nb;
+    *outer_out = outer;
+    *inner_out = inner;
+    if (P_out) memcpy(P_out, P, sizeof(double) * n * nstored);
+done:
+    free(r); free(z); free(P); free(W); free(pw); free(rf); free(zf);
+    return status;
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,64 @@
+"""The pins bite: plant a plausible mistake in a copy of the oracle source,
+build it, and check that at least one pin fails on it (CPU only).
+
+Each entry replaces one line of ls_oracle.c (a dropped term, a wrong sign, a
+wrong index, a transposed operand, a wrong rounding) and names the pin
+expected to catch it.
+"""
+import os
+
+import pytest
+
+import oracle as oracle_pkg
+import test_oracle_cg as tcg
+import test_oracle_ge_quant as tgq
+import test_oracle_gmres as tgm
+import test_oracle_mixed as tmx
+
+MUTATIONS = {
+    "cg_beta_sign": ("p[i] = r[i] + beta * p[i];", "p[i] = r[i] - beta * p[i];",
+                     lambda o: tcg.test_cg_krylov_optimality(o)),
+    "cg_alpha": ("double alpha = rho / pq;", "double alpha = rho / (pq * 1.0000001);",
+                 lambda o: tcg.test_cg_krylov_optimality(o)),
+    "gemv_transposed": ("for (int j = 0; j < ncols; j++) s += a[j] * x[j];",
+                        "for (int j = 0; j < ncols; j++) s += A[(long)j * lda + i] * x[j];",
+                        lambda o: tgm.test_gmres_matches_lapack(o, 64)),
+    "givens_g_sign": ("g[k + 1] = -sn[k] * g[k];", "g[k + 1] = sn[k] * g[k];",
+                      lambda o: tgm.test_gmres_minimal_residual(o)),
+    "givens_rot_sign": ("HR(j + 1, k) = -sn[j] * a + cs[j] * c;",
+                        "HR(j + 1, k) = sn[j] * a + cs[j] * c;",
+                        lambda o: tgm.test_gmres_minimal_residual(o)),
+    "mgs_drops_last": ("for (int j = 0; j <= k; j++) {                  /* MGS */",
+                       "for (int j = 0; j < k; j++) {                  /* MGS */",
+                       lambda o: tgm.test_arnoldi_relation_and_orthonormality(o, 12)),
+    "backsolve_index": ("for (int j = i + 1; j < k; j++) s -= HR(i, j) * y[j];",
+                        "for (int j = i + 1; j < k; j++) s -= HR(j, i) * y[j];",
+                        lambda o: tgm.test_gmres_minimal_residual(o)),
+    "ge_no_pivoting": ("if (a > best) { best = a; v = i; }", "if (0) { best = a; v = i; }",
+                       lambda o: tgq.test_ge_pivoting_and_singular(o)),
+    "round_truncates": ("static double round_to_quantum(double d, double q) { return rint(d / q) * q; }",
+                        "static double round_to_quantum(double d, double q) { return trunc(d / q) * q; }",
+                        lambda o: tgq.test_bf16_nearest_and_ties_to_even(o)),
+    "e4m3_bias": ("return s | (uint8_t)((ex + 7) << 3) | (uint8_t)mant;",
+                  "return s | (uint8_t)((ex + 6) << 3) | (uint8_t)mant;",
+                  lambda o: tgq.test_fp8_quant_row_scales(o)),
+    "fcg_no_orthogonalisation": ("double c = dot(n, z, W + (long)j * n) / pw[j];",
+                                 "double c = 0.0 * dot(n, z, W + (long)j * n) / pw[j];",
+                                 lambda o: tmx.test_fcg_ill_conditioned_bf16(o)),
+    "inner_beta_inverted": ("float beta = rho_new / rho;", "float beta = rho / rho_new;",
+                            lambda o: tmx.test_inner_cg_f32_solves_stored_matrix(o)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new, pin = MUTATIONS[name]
+    src = open(oracle_pkg.SOURCE).read()
+    assert src.count(old) >= 1, "mutation site not found: " + name
+    path = os.path.join(tmp_path, "mut.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new, 1))      # first occurrence (FP64 path)
+    lib = oracle_pkg.compile_source(path, os.path.join(tmp_path, "libmut.so"))
+    mutant = oracle_pkg.Oracle(lib)
+    with pytest.raises(AssertionError):
+        pin(mutant)
