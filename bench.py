@@ -1,0 +1,417 @@
+#!/usr/bin/env python3
+"""Benchmark of the dense Krylov hot path on GB300.
+
+One step = one full solve of each system of the n = 16384 FP64 workload to
+relative residual 1e-10 (x0 = 0): conjugate gradient on the SPD matrix
+A = G G^T / n + 1e-3 I (cond ~ 4e3) and GMRES(50) on A = 2 I + G / (2 sqrt n),
+x* ~ U[-1, 1], b = A x*.  Each A is 2 GiB of FP64, far larger than the L2
+cache, so no flush is needed between steps.
+
+  value        whole-job solves per second (device-resident inputs, CUDA events)
+  e2e          the same through the C ABI with pinned HOST buffers: the copy of
+               A and b to the device and of x back are inside the timed region
+  roofline     the dominant kernel (the FP64 matrix-vector product), timed with
+               CUDA events on its stream as back-to-back launches of the same
+               kernel and grid the solvers use
+  cpu_baseline the oracle (plain C, FP64) on this host's cores, on a bounded
+               sample of the same workload, scaled to solves per second
+
+--impl reference times the oracle itself as the reference arm.
+Multi-GPU: the path does not shard; every rank solves its own replica
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("time-to-1e-10 residual & GEMV HBM GB/s (mixed vs FP64); served solves/s, p99")
+N = 16384
+SIGMA = 1e-3
+RESTART = 50
+RTOL = 1e-10
+WORKLOAD = ("n=16384 dense FP64, x0=0, rtol 1e-10: CG on SPD GG^T/n+1e-3I (seed 0) and "
+            "GMRES(50) on 2I+G/(2sqrt n) (seed 1); x*~U[-1,1], b=Ax*")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 FMA pipe of GB300: 2 DFMA per clock per SM (measured 0.598 T DFMA/s at
+# 1.98 GHz on 152 SMs); one DFMA per 8-byte element of A.
+def dfma_peak_tflops(sm_mhz_max):
+    return 152 * 2 * 2 * sm_mhz_max * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=self.tmp,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(k)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# profile evidence for the roofline's traffic field
+# ---------------------------------------------------------------------------
+def gemv_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_gemv.cu", "ls_device.cuh", "ls_internal.h"):
+        with open(os.path.join(ROOT, "paper_1511_07207_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256_16") != gemv_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def make_inputs(device):
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    A_spd = inputs.spd_matrix(N, SIGMA, seed=0, device=device)
+    xs1 = torch.from_numpy(inputs.solution(N, seed=0)).to(device)
+    b_spd = A_spd @ xs1
+    A_ns = inputs.nonsym_matrix(N, seed=1, device=device)
+    xs2 = torch.from_numpy(inputs.solution(N, seed=1)).to(device)
+    b_ns = A_ns @ xs2
+    torch.cuda.synchronize(device)
+    return A_spd, b_spd, xs1, A_ns, b_ns, xs2
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(A_spd, b_spd, A_ns, b_ns, cg_iters, gm_iters, cg_sample=60):
+    """Time the oracle: `cg_sample` CG iterations and a GMRES(50) run of
+    `gm_iters` steps on this host's cores; return (solves/s extrapolated to
+    full solves of cg_iters and gm_iters steps, threads, seconds spent)."""
+    import oracle
+    nt = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.cg(A_spd, b_spd, rtol=0.0, max_iter=cg_sample, nthreads=nt)
+    t1 = time.perf_counter()
+    oracle.gmres(A_ns, b_ns, m=RESTART, rtol=0.0, max_iter=gm_iters, nthreads=nt)
+    t2 = time.perf_counter()
+    per_cg = (t1 - t0) / cg_sample
+    per_gm = (t2 - t1) / max(gm_iters, 1)
+    t_solves = per_cg * cg_iters + per_gm * gm_iters
+    return 2.0 / t_solves, nt, t2 - t0, per_cg, per_gm
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1511_07207_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    B.load()
+    ctx = B.ls_create(local, stream)
+
+    A_spd, b_spd, xs1, A_ns, b_ns, xs2 = make_inputs(dev)
+    x1 = torch.zeros(N, dtype=torch.float64, device=dev)
+    x2 = torch.zeros(N, dtype=torch.float64, device=dev)
+    o_cg = B.make_opts(rtol=RTOL)
+    o_gm = B.make_opts(rtol=RTOL, restart=RESTART)
+
+    def step():
+        st1, i1 = B.ls_cg_solve(ctx, A_spd, b_spd, x1, o_cg)
+        st2, i2 = B.ls_gmres_solve(ctx, A_ns, b_ns, x2, o_gm)
+        assert st1 == B.LS_OK and st2 == B.LS_OK, (B.ls_strerror(st1), B.ls_strerror(st2))
+        return i1, i2
+
+    for _ in range(args.warmup):
+        i1, i2 = step()
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    infos = []
+    for _ in range(args.steps):
+        i1, i2 = step()
+        launches += i1["launches"] + i2["launches"]
+        infos.append((i1, i2))
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * 2 * args.steps / (ms_max / 1e3)
+
+    # accuracy of the timed results (checked, not assumed)
+    err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
+    err_gm = float(torch.linalg.norm(x2 - xs2) / torch.linalg.norm(xs2))
+
+    # dominant kernel: the FP64 GEMV, same kernel/grid as inside the solves
+    p = torch.from_numpy(np.random.default_rng(0).standard_normal(N)).to(dev)
+    y = torch.empty(N, dtype=torch.float64, device=dev)
+    st, gemv_ms = B.ls_gemv_timed(ctx, B.LS_F64, A_spd, p, y, 30)
+    assert st == B.LS_OK
+    peaks, peak_src = load_peaks()
+    gemv_bytes = 8.0 * N * N + 16.0 * N
+    gemv_gbs = gemv_bytes / (gemv_ms * 1e-3) / 1e9
+    gemv_tflops = 2.0 * N * N / (gemv_ms * 1e-3) / 1e12
+    sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = dfma_peak_tflops(sm_max)
+    traffic = profiled_traffic("gemv_f64_n16384.md")
+    roofline = {"bound": "alu", "achieved": round(gemv_tflops, 4), "peak": round(alu_peak, 4),
+                "unit": "TFLOP/s", "frac": round(gemv_tflops / alu_peak, 4),
+                "traffic": traffic,
+                "kernel": "gemv_kernel<F64,TMA> (K1)",
+                "note": ("FP64 FMA pipe bound: peak = 152 SMs x 2 DFMA/clk x 2 flop x SM max clock; "
+                         "HBM view: %.1f GB/s = %.3f of %s %.1f GB/s" %
+                         (gemv_gbs, gemv_gbs / peaks["hbm_gbs"], peak_src, peaks["hbm_gbs"]))}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA1 = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+        hA1.copy_(A_spd)
+        hA2 = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+        hA2.copy_(A_ns)
+        hb1 = b_spd.cpu().pin_memory()
+        hb2 = b_ns.cpu().pin_memory()
+        hx1 = torch.zeros(N, dtype=torch.float64).pin_memory()
+        hx2 = torch.zeros(N, dtype=torch.float64).pin_memory()
+
+        def step_e2e():
+            s1, _ = B.ls_cg_solve(ctx, hA1, hb1, hx1, o_cg)
+            s2, _ = B.ls_gmres_solve(ctx, hA2, hb2, hx2, o_gm)
+            assert s1 == B.LS_OK and s2 == B.LS_OK
+
+        step_e2e()
+        barrier()
+        t0 = time.perf_counter()
+        k_e2e = max(1, min(args.steps, 3))
+        for _ in range(k_e2e):
+            step_e2e()
+        barrier()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(world * 2 * k_e2e / float(tt.item()), 4), "unit": "solves/s",
+               "h2d_bytes_per_step": int(2 * (8 * N * N + 8 * N)),
+               "d2h_bytes_per_step": int(2 * 8 * N)}
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        hA1 = A_spd.cpu().numpy()
+        hA2 = A_ns.cpu().numpy()
+        v, nt, secs, per_cg, per_gm = oracle_sample(
+            hA1, b_spd.cpu().numpy(), hA2, b_ns.cpu().numpy(),
+            infos[-1][0]["iters"], infos[-1][1]["iters"], cg_sample=args.cpu_cg_sample)
+        cpu = {"value": round(v, 6), "unit": "solves/s", "cores": nt, "kind": "oracle",
+               "sample": ("%d oracle CG iterations + a full oracle GMRES(50) solve (%d steps) on "
+                          "the same n=16384 matrices, %.1f s; CG scaled to the GPU's %d "
+                          "iterations" % (args.cpu_cg_sample, infos[-1][1]["iters"], secs,
+                                          infos[-1][0]["iters"])),
+               "ms_per_cg_iter": round(per_cg * 1e3, 3), "ms_per_gmres_step": round(per_gm * 1e3, 3)}
+
+    if rank == 0:
+        i1, i2 = infos[-1]
+        out = {
+            "metric": METRIC, "value": round(value, 4), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "restart": RESTART, "rtol": RTOL,
+                       "l2": "inputs larger than L2 (each A is 2 GiB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "time_to_1e-10_ms": {"cg": round(i1["time_ms"], 3), "gmres": round(i2["time_ms"], 3)},
+            "iters": {"cg": i1["iters"], "gmres": i2["iters"]},
+            "true_rel_res": {"cg": i1["true_rel_res"], "gmres": i2["true_rel_res"]},
+            "rel_err_vs_xstar": {"cg": err_cg, "gmres": err_gm},
+            "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
+                         "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
+                         "peak_source": peak_src},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    B.ls_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """Reference arm: the oracle on this host's cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    import oracle
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
+    if dev is not None:
+        A_spd, b_spd, _, A_ns, b_ns, _ = make_inputs(dev)
+        A1, b1 = A_spd.cpu().numpy(), b_spd.cpu().numpy()
+        A2, b2 = A_ns.cpu().numpy(), b_ns.cpu().numpy()
+        del A_spd, A_ns
+    else:
+        from paper_1511_07207_gb300 import inputs
+        A1 = inputs.spd_matrix(N, SIGMA, seed=0)
+        b1 = A1 @ inputs.solution(N, seed=0)
+        A2 = inputs.nonsym_matrix(N, seed=1)
+        b2 = A2 @ inputs.solution(N, seed=1)
+    nt = os.cpu_count() or 1
+    # the oracle's own iteration counts, once (GMRES in full; CG from a full solve)
+    full_gm = oracle.gmres(A2, b2, m=RESTART, rtol=RTOL, nthreads=nt)
+    cg_iters = args.ref_cg_iters
+    if cg_iters <= 0:
+        cg_iters = oracle.cg(A1, b1, rtol=RTOL, nthreads=nt)["iters"]
+    gm_iters = full_gm["iters"]
+    vals = []
+    secs = 0.0
+    for i in range(args.warmup + args.steps):
+        v, _, s, _, _ = oracle_sample(A1, b1, A2, b2, cg_iters, gm_iters, cg_sample=args.cpu_cg_sample)
+        if i >= args.warmup:
+            vals.append(v)
+            secs += s
+    value = args.steps / sum(1.0 / v for v in vals)    # harmonic mean of solves/s
+    sample = ("per step: %d oracle CG iterations (scaled to the oracle's %d) + a full oracle "
+              "GMRES(50) solve (%d steps), n=16384 FP64, %d threads" %
+              (args.cpu_cg_sample, cg_iters, gm_iters, nt))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": N, "restart": RESTART, "rtol": RTOL},
+           "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": nt,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-cg-sample", type=int, default=60)
+    ap.add_argument("--ref-cg-iters", type=int, default=0,
+                    help="reference arm: CG iteration count to scale to (0 = run the oracle once)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

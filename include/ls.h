@@ -1,0 +1,256 @@
+/*
+ * ls.h -- C ABI of the GB300-native dense Krylov solver library.
+ *
+ * The library solves dense linear systems A x = b on one GPU, the problem
+ * statement of Oancea, Andrei and Dragoescu, "Improving the performance of
+ * the linear systems solvers using CUDA" (arXiv:1511.07207), section
+ * "Serial iterative and direct methods ...": Krylov methods whose iterate
+ * update x(i) = x(i-1) + d(i) needs only inner products, saxpy operations and
+ * one dense matrix-vector product per step.  The methods are the conjugate
+ * gradient (CG paragraph of that section) and restarted GMRES(m) (its GMRES
+ * pseudocode and restart paragraph).  The host flow of the paper's section
+ * "Parallel implementation ... using CUDA" (allocate, copy in, run kernels,
+ * copy out) is kept, but every iteration runs on the device: no host
+ * synchronisation per iteration.
+ *
+ * Conventions, for every entry point:
+ *   - Matrices are dense and row-major: element (i, j) of A is A[i*lda + j],
+ *     lda >= n.  Blocks of right-hand sides B and solutions X are n x nrhs,
+ *     column-major (column j starts at B + j*ldb), ldb >= n.
+ *   - Pointers may be host or device memory; the library tells them apart
+ *     with cudaPointerGetAttributes.  Host inputs are copied to the device
+ *     inside the call, host outputs copied back before it returns.  Device
+ *     inputs are read in place (A is never modified).
+ *   - The caller owns every buffer it passes.  Solve calls are synchronous:
+ *     they return after the result is in x (or X) and in the info struct.
+ *   - Every function returns an int status: 0 = LS_OK, > 0 = a numerical
+ *     outcome (the result and info are still filled in), < 0 = an error
+ *     (outputs untouched unless stated).  No function aborts, exits or
+ *     throws.
+ *   - One context per host thread; a context is not thread-safe, except for
+ *     the server calls, which are.
+ */
+#ifndef LS_H
+#define LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LS_OK               0   /* converged: ||b - A x|| <= rtol ||b|| (true residual) */
+#define LS_NOT_CONVERGED    1   /* iteration limit reached; x is the last iterate        */
+#define LS_BREAKDOWN        2   /* p.Ap <= 0 in CG (A not SPD), or a zero Givens pivot   */
+#define LS_ERR_ARG         -1   /* invalid argument (size, stride, null pointer, opts)  */
+#define LS_ERR_NOMEM       -2   /* device allocation failed or workspace too small      */
+#define LS_ERR_CUDA        -3   /* a CUDA runtime call failed                           */
+#define LS_ERR_TIMEOUT     -4   /* a bounded on-device wait ran out                     */
+#define LS_ERR_BUSY        -5   /* server: no capacity / queue full                      */
+#define LS_ERR_NAN         -6   /* a NaN or Inf appeared in b or in the iteration        */
+#define LS_ERR_UNSUPPORTED -7   /* the combination of options is not supported           */
+
+/* ---- methods and precisions ------------------------------------------- */
+#define LS_METHOD_CG     0
+#define LS_METHOD_GMRES  1
+
+#define LS_F64      0   /* plain FP64 solve                                            */
+#define LS_BF16_IR  1   /* A stored in BF16, FP32 inner CG, FP64 outer refinement        */
+#define LS_FP8_IR   2   /* A stored in FP8-e4m3 with one FP32 scale per row, as above    */
+#define LS_F32_IR   3   /* A stored in FP32, as above                                    */
+
+#define LS_REFINE_FCG 0 /* outer loop = flexible CG preconditioned by the inner solve    */
+#define LS_REFINE_IR  1 /* outer loop = classic refinement x += inner(b - A x)           */
+
+/* ---- options and results ---------------------------------------------- */
+typedef struct {
+    double rtol;        /* stop when ||b - A x||_2 <= rtol ||b||_2 (default 1e-10)      */
+    int max_iter;       /* matrix-vector products of the method (default 10 n + 10);
+                           for LS_*_IR: outer iterations (default 60)                   */
+    int restart;        /* GMRES restart length m, 1..LS_MAX_RESTART (default 30)       */
+    int precision;      /* LS_F64 (default), LS_BF16_IR, LS_FP8_IR, LS_F32_IR (CG only) */
+    int refine;         /* LS_REFINE_FCG (default) or LS_REFINE_IR                      */
+    int inner_iters;    /* inner FP32 CG iterations per outer step (default 25)         */
+    double inner_rtol;  /* inner relative tolerance, 0 = run inner_iters (default 0)    */
+    int x0_given;       /* 1: x holds the initial guess; 0: start from x = 0 (default)  */
+    int reorth;         /* GMRES: 0 = one Gram-Schmidt pass with a second pass when the
+                           norm drops below 0.7x (default), 1 = always two passes       */
+} ls_opts;
+
+#define LS_MAX_RESTART 128
+
+typedef struct {
+    int status;          /* same as the return value                                     */
+    int iters;           /* matrix-vector products of the method (inner ones for LS_*_IR)*/
+    int outer_iters;     /* LS_*_IR outer steps; GMRES restart cycles                    */
+    double rel_res;      /* last recursive (or Givens-estimated) relative residual       */
+    double true_rel_res; /* ||b - A x|| / ||b|| recomputed in FP64 at exit               */
+    double time_ms;      /* device time of the solve (CUDA events on the context stream) */
+    double bytes_moved;  /* algorithmic bytes of A streamed (sum over all products)      */
+    long long launches;  /* kernels executed on the device for this call                 */
+} ls_info;
+
+/* Fill *o with the defaults listed above.  Returns LS_OK, or LS_ERR_ARG for NULL. */
+int ls_opts_default(ls_opts *o);
+
+/* ---- context ------------------------------------------------------------ */
+typedef struct ls_ctx ls_ctx;
+
+/*
+ * Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream may be a
+ * PyTorch stream handle.  Returns LS_ERR_CUDA if the device is unusable,
+ * LS_ERR_UNSUPPORTED if it is not an sm_103 GPU.
+ */
+int ls_create(ls_ctx **ctx, int device, void *cuda_stream);
+
+/* Release the context and everything it allocated.  NULL is accepted. */
+int ls_destroy(ls_ctx *ctx);
+
+/*
+ * Device workspace, in bytes, that a solve of size n (nrhs right-hand sides)
+ * with `method` and options `o` (NULL = defaults) needs.  It excludes A
+ * itself when A is a device pointer and includes a staging copy of A
+ * otherwise (`a_on_device` = 0).
+ */
+int ls_workspace_size(ls_ctx *ctx, int method, int n, int nrhs, const ls_opts *o,
+                      int a_on_device, size_t *bytes);
+
+/*
+ * Hand the context a caller-allocated device buffer (e.g. from PyTorch's
+ * caching allocator) of `bytes` bytes, 256-byte aligned.  The library then
+ * allocates nothing for solves that fit in it and returns LS_ERR_NOMEM for
+ * those that do not.  dev_ptr = NULL returns to library-managed memory.
+ */
+int ls_set_workspace(ls_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* ---- single-system solvers ----------------------------------------------- */
+/*
+ * Conjugate gradient (paper: CG paragraph; Hestenes-Stiefel form) for SPD A.
+ * n >= 0, lda >= n; A row-major n x n (FP64); b and x vectors of n FP64.
+ * With opts->precision = LS_BF16_IR / LS_FP8_IR / LS_F32_IR, A is quantised
+ * on the device (BF16 round-to-nearest-even from FP64; FP8-e4m3 with
+ * s_i = fp32(max_j |a_ij| / 448), q_ij = e4m3_rn_satfinite(a_ij / s_i)),
+ * an FP32 CG on the stored matrix is the inner solver, and the outer loop
+ * (opts->refine) runs in FP64 on the FP64 A.  x receives the solution on
+ * status >= 0.
+ */
+int ls_cg_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
+                double *x, const ls_opts *opts, ls_info *info);
+
+/*
+ * Restarted GMRES(m), m = opts->restart (paper: GMRES pseudocode, Arnoldi
+ * with classical Gram-Schmidt, and the restart paragraph), for general
+ * nonsingular A.  The Hessenberg least-squares problem is updated with
+ * Givens rotations, so the residual norm of every iterate is known without
+ * forming it; each restart recomputes the true FP64 residual.  Arguments as
+ * for ls_cg_solve; opts->precision must be LS_F64.
+ */
+int ls_gmres_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
+                   double *x, const ls_opts *opts, ls_info *info);
+
+/* ---- batched solver -------------------------------------------------------- */
+typedef struct {
+    int method;          /* LS_METHOD_CG (SPD A) or LS_METHOD_GMRES                     */
+    int n;               /* 1 .. LS_BATCH_MAX_N                                          */
+    int nrhs;            /* 1 .. LS_BATCH_MAX_RHS                                        */
+    const double *A;     /* row-major n x n, leading dimension lda (host or device)      */
+    int64_t lda;
+    const double *B;     /* n x nrhs column-major, leading dimension ldb                 */
+    int64_t ldb;
+    double *X;           /* n x nrhs column-major, leading dimension ldx (output)        */
+    int64_t ldx;
+    ls_opts opts;        /* rtol, max_iter, restart used per system; precision ignored  */
+} ls_system;
+
+#define LS_BATCH_MAX_N   4096
+#define LS_BATCH_MAX_RHS 32
+
+/*
+ * Solve `count` independent systems in one persistent device launch.  Every
+ * right-hand side column is solved on its own (column-independent CG or
+ * GMRES(m) sharing each matrix product A*P across the columns of a system),
+ * with FP32 products on the tensor cores inside an FP64 refinement loop on
+ * the FP64 residual B - A X.  infos[i] receives the outcome of system i
+ * (worst column).  Returns the worst status over the systems.
+ */
+int ls_batch_solve(ls_ctx *ctx, int count, const ls_system *sys, ls_info *infos);
+
+/* ---- server (continuous batching) ----------------------------------------- */
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory the server may hold for requests      */
+    int max_slots;             /* requests resident on the device at once             */
+    int step_iters;            /* iterations each resident request advances per step  */
+    int queue_capacity;        /* pending requests before submit returns LS_ERR_BUSY  */
+} ls_server_cfg;
+
+typedef struct ls_server ls_server;
+
+/*
+ * Start a server on the context's device with its own scheduler thread.
+ * Requests are admitted when their device bytes fit in the budget and a slot
+ * is free; every scheduler step advances all resident requests on the
+ * device; finished requests retire and free their memory.
+ */
+int ls_server_start(ls_ctx *ctx, const ls_server_cfg *cfg, ls_server **srv);
+
+/*
+ * Queue one system.  A, B are deep-copied before the call returns (the
+ * caller may free them); X must stay valid until ls_server_poll reports the
+ * ticket done.  Thread-safe.  LS_ERR_BUSY when the queue is full,
+ * LS_ERR_NOMEM when the request alone exceeds the budget.
+ */
+int ls_server_submit(ls_server *srv, const ls_system *req, uint64_t *ticket);
+
+/*
+ * Non-blocking: *done = 1 once X has been written and *info filled in.
+ * Thread-safe.  LS_ERR_ARG for an unknown ticket.  A finished ticket can be
+ * polled once more and is then forgotten.
+ */
+int ls_server_poll(ls_server *srv, uint64_t ticket, int *done, ls_info *info);
+
+/* Stop the scheduler: resident requests finish or are cancelled
+ * (status LS_NOT_CONVERGED), pending ones are cancelled.  Never hangs. */
+int ls_server_stop(ls_server *srv);
+
+/* ---- kernel-level entry points (used by the tests and the benchmark) ------ */
+/*
+ * y = A x for a row-major rows x cols matrix stored as `dtype`
+ * (LS_F64: double A, double x and y; LS_BF16_IR: uint16 BF16 codes;
+ * LS_FP8_IR: uint8 e4m3 codes with FP32 row scales `scale`, y_i = s_i (Q x)_i;
+ * LS_F32_IR: float A).  For the low-precision formats x and y are FP32.
+ * All pointers are device pointers.
+ */
+int ls_gemv(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int64_t lda,
+            const float *scale, const void *x, void *y);
+
+/*
+ * Quantise a row-major FP64 matrix on the device: LS_BF16_IR -> uint16 codes,
+ * LS_FP8_IR -> uint8 codes plus FP32 row scales, LS_F32_IR -> float.
+ * Roundings as described for ls_cg_solve.  Device pointers.
+ */
+int ls_quantize(ls_ctx *ctx, int dtype, int rows, int cols, const double *A, int64_t lda,
+                void *Q, int64_t ldq, float *scale);
+
+/*
+ * Benchmark helper: launch the y = A x kernel of ls_gemv `reps` times back to
+ * back on the context stream (same kernel, grid and tiles as inside the
+ * solvers) and return in *ms_per_launch the mean device time of one launch,
+ * measured with CUDA events recorded on that stream.
+ */
+int ls_gemv_timed(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int64_t lda,
+                  const float *scale, const void *x, void *y, int reps, double *ms_per_launch);
+
+/* Kernels the context has executed on the device since it was created. */
+long long ls_kernel_launches(ls_ctx *ctx);
+
+/* Static description of a status code. */
+const char *ls_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LS_H */

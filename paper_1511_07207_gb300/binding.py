@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in ``include/ls.h`` (ctypes).
+
+The functions keep the C names and only marshal arguments: numpy arrays
+(host memory) and torch tensors (host or CUDA memory) are turned into
+pointers, sizes and leading dimensions; every step of a solve runs in the
+CUDA library.  There is no CPU fallback: if the library cannot be loaded the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN = 0, 1, 2
+LS_ERR_ARG, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT = -1, -2, -3, -4
+LS_ERR_BUSY, LS_ERR_NAN, LS_ERR_UNSUPPORTED = -5, -6, -7
+LS_METHOD_CG, LS_METHOD_GMRES = 0, 1
+LS_F64, LS_BF16_IR, LS_FP8_IR, LS_F32_IR = 0, 1, 2, 3
+LS_REFINE_FCG, LS_REFINE_IR = 0, 1
+LS_MAX_RESTART = 128
+LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 4096, 32
+
+# every symbol declared in include/ls.h
+ABI_FUNCTIONS = (
+    "ls_opts_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_set_workspace",
+    "ls_cg_solve", "ls_gmres_solve", "ls_batch_solve", "ls_server_start", "ls_server_submit",
+    "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_quantize",
+    "ls_kernel_launches", "ls_strerror",
+)
+
+
+class ls_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
+                ("precision", ctypes.c_int), ("refine", ctypes.c_int),
+                ("inner_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int)]
+
+
+class ls_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer_iters", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("time_ms", ctypes.c_double), ("bytes_moved", ctypes.c_double),
+                ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ls_system(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("n", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64), ("opts", ls_opts)]
+
+
+class ls_server_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
+                ("step_iters", ctypes.c_int), ("queue_capacity", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the CUDA library (building it first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is missing; run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.ls_opts_default.argtypes = [ctypes.POINTER(ls_opts)]
+        lib.ls_create.argtypes = [ctypes.POINTER(P), I, P]
+        lib.ls_destroy.argtypes = [P]
+        lib.ls_workspace_size.argtypes = [P, I, I, I, ctypes.POINTER(ls_opts), I,
+                                          ctypes.POINTER(ctypes.c_size_t)]
+        lib.ls_set_workspace.argtypes = [P, P, ctypes.c_size_t]
+        for fn in (lib.ls_cg_solve, lib.ls_gmres_solve):
+            fn.argtypes = [P, I, P, I64, P, P, ctypes.POINTER(ls_opts), ctypes.POINTER(ls_info)]
+        lib.ls_batch_solve.argtypes = [P, I, ctypes.POINTER(ls_system), ctypes.POINTER(ls_info)]
+        lib.ls_server_start.argtypes = [P, ctypes.POINTER(ls_server_cfg), ctypes.POINTER(P)]
+        lib.ls_server_submit.argtypes = [P, ctypes.POINTER(ls_system),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        lib.ls_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(I),
+                                       ctypes.POINTER(ls_info)]
+        lib.ls_server_stop.argtypes = [P]
+        lib.ls_gemv.argtypes = [P, I, I, I, P, I64, P, P, P]
+        lib.ls_gemv_timed.argtypes = [P, I, I, I, P, I64, P, P, P, I,
+                                      ctypes.POINTER(ctypes.c_double)]
+        lib.ls_quantize.argtypes = [P, I, I, I, P, I64, P, I64, P]
+        lib.ls_kernel_launches.argtypes = [P]
+        lib.ls_kernel_launches.restype = ctypes.c_longlong
+        lib.ls_strerror.argtypes = [I]
+        lib.ls_strerror.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _itemsize(a):
+    return a.element_size() if _is_torch(a) else a.itemsize
+
+
+def lead_dim(a) -> int:
+    """Leading dimension (elements) of a row-major 2-D array; rows must be unit-stride."""
+    if _is_torch(a):
+        assert a.dim() == 2 and a.stride(1) == 1, "row-major with unit column stride required"
+        return a.stride(0)
+    assert a.ndim == 2 and a.strides[1] == a.itemsize, "row-major with unit column stride required"
+    return a.strides[0] // a.itemsize
+
+
+def col_lead_dim(a) -> int:
+    """Leading dimension of a column-major n x k block (column j at a + j*ld)."""
+    if _is_torch(a):
+        if a.dim() == 1:
+            return a.shape[0]
+        assert a.stride(0) == 1
+        return a.stride(1)
+    if a.ndim == 1:
+        return a.shape[0]
+    assert a.strides[0] == a.itemsize
+    return a.strides[1] // a.itemsize
+
+
+def make_opts(**kw) -> ls_opts:
+    o = ls_opts()
+    load().ls_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(o, k):
+            raise TypeError("unknown option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def _check_f64(*arrs):
+    for a in arrs:
+        if a is None:
+            continue
+        dt = str(a.dtype)
+        assert dt in ("float64", "torch.float64"), "FP64 arrays required, got %s" % dt
+
+
+# ---------------------------------------------------------------------------
+# ABI functions (same names as include/ls.h)
+# ---------------------------------------------------------------------------
+
+def ls_create(device: int = 0, stream=None):
+    """Returns an opaque context handle.  `stream` is a cudaStream_t (int), a
+    torch.cuda.Stream, or None for the default stream."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = ctypes.c_void_p()
+    st = load().ls_create(ctypes.byref(h), device, stream)
+    if st != LS_OK:
+        raise RuntimeError("ls_create failed: %s" % ls_strerror(st))
+    return h
+
+
+def ls_destroy(ctx):
+    return load().ls_destroy(ctx)
+
+
+def ls_strerror(status: int) -> str:
+    return load().ls_strerror(status).decode()
+
+
+def ls_kernel_launches(ctx) -> int:
+    return load().ls_kernel_launches(ctx)
+
+
+def ls_workspace_size(ctx, method, n, nrhs=1, opts=None, a_on_device=True) -> int:
+    b = ctypes.c_size_t(0)
+    st = load().ls_workspace_size(ctx, method, n, nrhs, ctypes.byref(opts) if opts else None,
+                                  int(a_on_device), ctypes.byref(b))
+    if st != LS_OK:
+        raise RuntimeError(ls_strerror(st))
+    return b.value
+
+
+def ls_set_workspace(ctx, buf=None, nbytes=0):
+    return load().ls_set_workspace(ctx, ptr(buf), nbytes)
+
+
+def _solve(fn, ctx, A, b, x, opts):
+    _check_f64(A, b, x)
+    n = A.shape[0]
+    assert A.shape[1] == n
+    info = ls_info()
+    o = opts if opts is not None else make_opts()
+    st = fn(ctx, n, ptr(A), lead_dim(A), ptr(b), ptr(x), ctypes.byref(o), ctypes.byref(info))
+    return st, info.as_dict()
+
+
+def ls_cg_solve(ctx, A, b, x, opts=None):
+    """CG on A x = b; A (n x n row-major), b, x FP64 (host or device).  x is
+    written in place.  Returns (status, info dict)."""
+    return _solve(load().ls_cg_solve, ctx, A, b, x, opts)
+
+
+def ls_gmres_solve(ctx, A, b, x, opts=None):
+    """Restarted GMRES(m) on A x = b; see ls_cg_solve."""
+    return _solve(load().ls_gmres_solve, ctx, A, b, x, opts)
+
+
+def ls_gemv(ctx, dtype, A, x, y, scale=None):
+    """y = A x on the device (see ls.h for the per-format types)."""
+    rows, cols = A.shape
+    return load().ls_gemv(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x), ptr(y))
+
+
+def ls_gemv_timed(ctx, dtype, A, x, y, reps, scale=None):
+    """Mean device ms of one y = A x launch over `reps` back-to-back launches."""
+    rows, cols = A.shape
+    ms = ctypes.c_double(0)
+    st = load().ls_gemv_timed(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x),
+                              ptr(y), reps, ctypes.byref(ms))
+    return st, ms.value
+
+
+def ls_quantize(ctx, dtype, A, Q, scale=None):
+    """Quantise FP64 A (device) into Q (device) [and FP32 row scales]."""
+    rows, cols = A.shape
+    return load().ls_quantize(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(Q), lead_dim(Q),
+                              ptr(scale))
+
+
+def make_system(method, A, B, X, opts=None) -> ls_system:
+    s = ls_system()
+    s.method = method
+    s.n = A.shape[0]
+    s.nrhs = 1 if B.ndim == 1 else B.shape[1]
+    s.A, s.lda = ptr(A), lead_dim(A)
+    s.B, s.ldb = ptr(B), col_lead_dim(B)
+    s.X, s.ldx = ptr(X), col_lead_dim(X)
+    s.opts = opts if opts is not None else make_opts()
+    return s
+
+
+def ls_batch_solve(ctx, systems):
+    """systems: list of ls_system.  Returns (status, [info dict])."""
+    arr = (ls_system * len(systems))(*systems)
+    infos = (ls_info * len(systems))()
+    st = load().ls_batch_solve(ctx, len(systems), arr, infos)
+    return st, [i.as_dict() for i in infos]
+
+
+def ls_server_start(ctx, hbm_budget_bytes, max_slots=64, step_iters=8, queue_capacity=1 << 16):
+    cfg = ls_server_cfg(hbm_budget_bytes, max_slots, step_iters, queue_capacity)
+    h = ctypes.c_void_p()
+    st = load().ls_server_start(ctx, ctypes.byref(cfg), ctypes.byref(h))
+    if st != LS_OK:
+        raise RuntimeError("ls_server_start failed: %s" % ls_strerror(st))
+    return h
+
+
+def ls_server_submit(srv, system: ls_system):
+    t = ctypes.c_uint64(0)
+    st = load().ls_server_submit(srv, ctypes.byref(system), ctypes.byref(t))
+    return st, t.value
+
+
+def ls_server_poll(srv, ticket):
+    done = ctypes.c_int(0)
+    info = ls_info()
+    st = load().ls_server_poll(srv, ticket, ctypes.byref(done), ctypes.byref(info))
+    return st, bool(done.value), info.as_dict()
+
+
+def ls_server_stop(srv):
+    return load().ls_server_stop(srv)

@@ -1,0 +1,578 @@
+// k_gemv.cu -- the dense matrix-vector product y = A x (K1 FP64, K2 BF16 /
+// FP8 / FP32 storage) and the quantisation of A (stage A).
+//
+// The matrix-vector product is the Theta(n^2) operation that every Krylov
+// step needs once (paper, section "Serial iterative and direct methods",
+// Krylov paragraph: "inner products, saxpy and matrix-vector products");
+// it moves all of A, so it is bound by HBM bandwidth (or, for FP64 on
+// GB300, by the FP64 FMA pipe: one FMA per 8 bytes of A).
+//
+// Design (GB300):
+//  * persistent grid of 2 CTAs per SM; the (row-tile, column-tile) sequence
+//    of A is cut into equal contiguous pieces, one per CTA, so every SM gets
+//    the same number of bytes whatever n is;
+//  * one producer warp streams TR x TC tiles of A with 2-D TMA bulk copies
+//    (cp.async.bulk.tensor) into a GEMV_STAGES-deep shared-memory ring with
+//    mbarrier completion; four consumer warps read the tiles with 128-bit
+//    (64-bit for FP8) shared loads, keep RW row accumulators per lane and
+//    the x chunk in registers, and reduce with warp shuffles;
+//  * a row tile cut between CTAs leaves partial sums in scratch; the last
+//    CTA to finish (atomic ticket) adds them in CTA order, applies the
+//    epilogue to those rows and reduces the fused dot product in a fixed
+//    order, so results are deterministic for a given n;
+//  * fused epilogues: y = s, y = s with z.y, y = b - s with y.y, y = s with
+//    y.y; the last CTA runs the solver's scalar update (alpha = rho / p.q,
+//    residual norm, ...) so no extra launch is needed.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "ls_device.cuh"
+#include "ls_internal.h"
+
+namespace lsi {
+
+template <int DT>
+struct Cfg;
+template <>
+struct Cfg<DT_F64> {
+    using T = double;   // stored element
+    using V = double;   // vector element / accumulator
+    static constexpr int VEC = 2, WC = 4, WR = 1, RW = 8;
+};
+template <>
+struct Cfg<DT_BF16> {
+    using T = uint16_t;
+    using V = float;
+    static constexpr int VEC = 8, WC = 1, WR = 4, RW = 8;
+};
+template <>
+struct Cfg<DT_FP8> {
+    using T = uint8_t;
+    using V = float;
+    static constexpr int VEC = 8, WC = 1, WR = 4, RW = 16;
+};
+template <>
+struct Cfg<DT_F32> {
+    using T = float;
+    using V = float;
+    static constexpr int VEC = 4, WC = 2, WR = 2, RW = 8;
+};
+
+template <int DT>
+struct Geo {
+    using C = Cfg<DT>;
+    static constexpr int TC = C::WC * 32 * C::VEC;
+    static constexpr int TR = C::WR * C::RW;
+    static constexpr int TILE_ELEMS = TC * TR;
+    static constexpr int TILE_BYTES = TILE_ELEMS * (int)sizeof(typename C::T);
+    static_assert(TC <= 256 && TR <= 256, "TMA box dimension");
+    static_assert(TR <= GEMV_MAX_TR, "scratch");
+    static_assert(C::WC * C::WR == GEMV_CONSUMER_WARPS, "warp grid");
+};
+
+int gemv_tile_rows(int dtype) {
+    switch (dtype) {
+        case DT_F64: return Geo<DT_F64>::TR;
+        case DT_BF16: return Geo<DT_BF16>::TR;
+        case DT_FP8: return Geo<DT_FP8>::TR;
+        default: return Geo<DT_F32>::TR;
+    }
+}
+
+// ---- x chunk loads --------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ void load_x(const typename Cfg<DT>::V *x, int c0, int cols,
+                                       typename Cfg<DT>::V (&p)[Cfg<DT>::VEC]) {
+    constexpr int VEC = Cfg<DT>::VEC;
+    if (c0 + VEC <= cols && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
+        if constexpr (DT == DT_F64) {
+            double2 v = __ldg(reinterpret_cast<const double2 *>(x + c0));
+            p[0] = v.x;
+            p[1] = v.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; k += 4) {
+                float4 v = __ldg(reinterpret_cast<const float4 *>(x + c0 + k));
+                p[k] = v.x;
+                p[k + 1] = v.y;
+                p[k + 2] = v.z;
+                p[k + 3] = v.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; k++) p[k] = (c0 + k < cols) ? x[c0 + k] : 0;
+    }
+}
+
+// acc += a[0:VEC] . p[0:VEC]; `a` points at VEC consecutive stored elements in
+// shared memory (aligned to the vector width).
+template <int DT>
+__device__ __forceinline__ void dot_tile(const typename Cfg<DT>::T *a,
+                                         const typename Cfg<DT>::V (&p)[Cfg<DT>::VEC],
+                                         typename Cfg<DT>::V &acc) {
+    if constexpr (DT == DT_F64) {
+        double2 v = *reinterpret_cast<const double2 *>(a);
+        acc = fma(v.x, p[0], acc);
+        acc = fma(v.y, p[1], acc);
+    } else if constexpr (DT == DT_BF16) {
+        uint4 v = *reinterpret_cast<const uint4 *>(a);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            acc = fmaf(__uint_as_float(w[k] << 16), p[2 * k], acc);
+            acc = fmaf(__uint_as_float(w[k] & 0xffff0000u), p[2 * k + 1], acc);
+        }
+    } else if constexpr (DT == DT_FP8) {
+        uint2 v = *reinterpret_cast<const uint2 *>(a);
+        const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            __half2_raw h0 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu),
+                                                        __NV_E4M3);
+            __half2_raw h1 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16),
+                                                        __NV_E4M3);
+            float2 f0 = __half22float2(*reinterpret_cast<__half2 *>(&h0));
+            float2 f1 = __half22float2(*reinterpret_cast<__half2 *>(&h1));
+            acc = fmaf(f0.x, p[4 * k + 0], acc);
+            acc = fmaf(f0.y, p[4 * k + 1], acc);
+            acc = fmaf(f1.x, p[4 * k + 2], acc);
+            acc = fmaf(f1.y, p[4 * k + 3], acc);
+        }
+    } else {
+        float4 v = *reinterpret_cast<const float4 *>(a);
+        acc = fmaf(v.x, p[0], acc);
+        acc = fmaf(v.y, p[1], acc);
+        acc = fmaf(v.z, p[2], acc);
+        acc = fmaf(v.w, p[3], acc);
+    }
+}
+
+// plain global loads (fallback when A cannot be described by a TMA map)
+template <int DT>
+__device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, long long lda, int row,
+                                           int c0, int cols,
+                                           const typename Cfg<DT>::V (&p)[Cfg<DT>::VEC],
+                                           typename Cfg<DT>::V &acc) {
+    using T = typename Cfg<DT>::T;
+    const T *a = A + (long long)row * lda;
+#pragma unroll
+    for (int k = 0; k < Cfg<DT>::VEC; k++) {
+        int c = c0 + k;
+        if (c < cols) {
+            T e = a[c];
+            if constexpr (DT == DT_F64) {
+                acc = fma(e, p[k], acc);
+            } else if constexpr (DT == DT_BF16) {
+                acc = fmaf(__uint_as_float((uint32_t)e << 16), p[k], acc);
+            } else if constexpr (DT == DT_FP8) {
+                __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)e, __NV_E4M3);
+                acc = fmaf(__half2float(*reinterpret_cast<__half *>(&h)), p[k], acc);
+            } else {
+                acc = fmaf(e, p[k], acc);
+            }
+        }
+    }
+}
+
+// ---- epilogue for one finished row ---------------------------------------------------
+template <int DT>
+__device__ __forceinline__ double epilogue(const GemvArgs &a, const MatDesc &M, int row,
+                                           typename Cfg<DT>::V s) {
+    using V = typename Cfg<DT>::V;
+    if constexpr (DT == DT_FP8) s *= M.scale[row];
+    V *y = static_cast<V *>(a.y);
+    switch (a.epi) {
+        case EPI_STORE:
+            y[row] = s;
+            return 0.0;
+        case EPI_DOT:
+            y[row] = s;
+            return (double)(static_cast<const V *>(a.z)[row] * s);
+        case EPI_RESID: {
+            V r = (V)(a.b[row] - (double)s);
+            y[row] = r;
+            return (double)r * (double)r;
+        }
+        default:  // EPI_NRM
+            y[row] = s;
+            return (double)s * (double)s;
+    }
+}
+
+__device__ __forceinline__ void run_finaliser(const GemvArgs &a, double dot) {
+    State *st = a.st;
+    if (a.dot_out) *a.dot_out = dot;
+    switch (a.fin) {
+        case FIN_CG_ALPHA:
+            st->pq = dot;
+            if (!(dot > 0.0)) {
+                st->status = LS_BREAKDOWN;
+                st->alpha = 0.0;
+            } else {
+                st->alpha = st->rho / dot;
+            }
+            break;
+        case FIN_TRUE_RES:
+            st->true_rnorm = sqrt(dot);
+            break;
+        case FIN_WNORM0:
+            st->wnorm0 = dot;
+            break;
+        case FIN_INNER_ALPHA:
+            st->in_pq = dot;
+            if (!(dot > 0.0)) {
+                st->in_stop = 2;    // breakdown of the inner solve: keep the iterate
+                st->in_alpha = 0.0;
+            } else {
+                st->in_alpha = st->in_rho / dot;
+            }
+            break;
+        case FIN_FCG_D:
+            st->pq = dot;
+            break;
+        default:
+            st->dot = dot;
+            break;
+    }
+}
+
+// Consumer-warp-only named barrier (ids 1..; 0 is __syncthreads).
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(GEMV_CONSUMER_WARPS * 32) : "memory");
+}
+
+// ---- the kernel ----------------------------------------------------------------------------
+template <int DT, bool TMA>
+__global__ void __launch_bounds__(GEMV_THREADS, 2)
+    gemv_kernel(const MatDesc *__restrict__ dA, GemvArgs args) {
+    using C = Cfg<DT>;
+    using G = Geo<DT>;
+    using T = typename C::T;
+    using V = typename C::V;
+    constexpr int TC = G::TC, TR = G::TR, VEC = C::VEC, RW = C::RW, WC = C::WC;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)GEMV_STAGES * G::TILE_BYTES);
+    uint64_t *empty = full + GEMV_STAGES;
+    __shared__ V red[WC][TR];
+    __shared__ double dred[GEMV_THREADS / 32];
+    __shared__ int abort_s, last_s;
+
+    const MatDesc &M = *dA;
+    const int rows = M.rows, cols = M.cols;
+    if (args.kptr) {   // walk the Krylov basis: x = column k, y = column k + 1
+        const long long k = *args.kptr;
+        args.x = static_cast<const V *>(args.x) + k * args.kstride;
+        args.y = static_cast<V *>(args.y) + (k + 1) * args.kstride;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int RT = (rows + TR - 1) / TR, CT = (cols + TC - 1) / TC;
+    const long long T_all = (long long)RT * CT;
+    const int G_ = gridDim.x, cta = blockIdx.x;
+    const long long t0 = T_all * cta / G_, t1 = T_all * (cta + 1) / G_;
+    const int ntiles = (int)(t1 - t0);
+    count_launch(args.st);
+
+    if (threadIdx.x == 0) {
+        abort_s = 0;
+        if (TMA) {
+            for (int s = 0; s < GEMV_STAGES; s++) {
+                mbar_init(&full[s], 1);
+                mbar_init(&empty[s], GEMV_CONSUMER_WARPS);
+            }
+            fence_mbar_init();
+        }
+    }
+    __syncthreads();
+
+    double mydot = 0.0;
+    if (warp == GEMV_CONSUMER_WARPS) {
+        // ---------------- producer warp ----------------
+        if (TMA && lane == 0 && ntiles > 0) {
+            tmap_acquire(&M.tmap);
+            int issued = 0;
+            for (int i = 0; i < ntiles; i++) {
+                const int s = i % GEMV_STAGES;
+                if (i >= GEMV_STAGES) {
+                    if (!mbar_wait(&empty[s], ((i / GEMV_STAGES) - 1) & 1)) {
+                        set_err(args.st, ERRB_TIMEOUT);
+                        abort_s = 1;
+                        break;
+                    }
+                }
+                if (*(volatile int *)&abort_s) break;
+                const long long t = t0 + i;
+                const int rt = (int)(t / CT), ct = (int)(t % CT);
+                mbar_arrive_expect_tx(&full[s], G::TILE_BYTES);
+                tma_load_2d(ring + (size_t)s * G::TILE_ELEMS, &M.tmap, ct * TC, rt * TR, &full[s]);
+                issued = i + 1;
+            }
+            // never leave with copies in flight: wait for the last stages
+            for (int i = issued > GEMV_STAGES ? issued - GEMV_STAGES : 0; i < issued; i++) {
+                if (!mbar_wait(&full[i % GEMV_STAGES], (i / GEMV_STAGES) & 1)) {
+                    set_err(args.st, ERRB_TIMEOUT);
+                }
+            }
+        }
+    } else {
+        // ---------------- consumer warps ----------------
+        const int wr = warp / WC, wc = warp % WC;
+        const int lane_col = wc * 32 * VEC + lane * VEC;   // column offset inside a tile
+        V acc[RW];
+#pragma unroll
+        for (int r = 0; r < RW; r++) acc[r] = 0;
+        const T *Ag = static_cast<const T *>(M.ptr);
+        const V *x = static_cast<const V *>(args.x);
+
+        for (int i = 0; i < ntiles; i++) {
+            const long long t = t0 + i;
+            const int rt = (int)(t / CT), ct = (int)(t % CT);
+            V p[VEC];
+            load_x<DT>(x, ct * TC + lane_col, cols, p);
+            if (TMA) {
+                // On a timeout the warp stops waiting and computing but keeps
+                // walking the tile sequence, so it still meets the other
+                // consumer warps at every named barrier below.
+                const int s = i % GEMV_STAGES;
+                if (!*(volatile int *)&abort_s && !mbar_wait(&full[s], (i / GEMV_STAGES) & 1)) {
+                    set_err(args.st, ERRB_TIMEOUT);
+                    abort_s = 1;
+                }
+                if (!*(volatile int *)&abort_s) {
+                    const T *tile = ring + (size_t)s * G::TILE_ELEMS;
+#pragma unroll
+                    for (int r = 0; r < RW; r++)
+                        dot_tile<DT>(tile + (wr * RW + r) * TC + lane_col, p, acc[r]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < RW; r++) {
+                    const int row = rt * TR + wr * RW + r;
+                    if (row < rows) dot_global<DT>(Ag, M.lda, row, ct * TC + lane_col, cols, p, acc[r]);
+                }
+            }
+            if (ct == CT - 1 || i == ntiles - 1) {
+                // this CTA's share of row tile rt is done: reduce it
+#pragma unroll
+                for (int r = 0; r < RW; r++) {
+                    V v = warp_sum(acc[r]);
+                    if (lane == 0) red[wc][wr * RW + r] = v;
+                    acc[r] = 0;
+                }
+                consumers_sync();
+                const long long rt_first = (long long)rt * CT;
+                const bool complete = (t0 <= rt_first) && (rt_first + CT <= t1);
+                const int slot = (rt == (int)(t0 / CT)) ? 0 : 1;
+                for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
+                    V s = 0;
+#pragma unroll
+                    for (int c = 0; c < WC; c++) s += red[c][tr];
+                    const int row = rt * TR + tr;
+                    if (complete) {
+                        if (row < rows) mydot += epilogue<DT>(args, M, row, s);
+                    } else {
+                        args.scr->fix[((size_t)cta * 2 + slot) * TR + tr] = (double)s;
+                    }
+                }
+                consumers_sync();
+            }
+        }
+    }
+
+    // ---- per-CTA dot, then the last CTA finishes split rows and the reduction ----
+    double cd = block_sum(mydot, dred);
+    if (threadIdx.x == 0) {
+        args.scr->cta_dot[cta] = cd;
+        __threadfence();
+        unsigned tk = atomicAdd(&args.scr->ticket, 1u);
+        last_s = (tk == (unsigned)G_ - 1);
+    }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+
+    // split row tiles: one per distinct CTA boundary b_c falling inside a row tile
+    double fixdot = 0.0;
+    auto start = [&](int c) -> long long { return T_all * c / G_; };
+    for (int c = 1 + warp; c < G_; c += GEMV_THREADS / 32) {
+        const long long bc = start(c), bprev = start(c - 1);
+        if (bc <= bprev || bc >= T_all || bc % CT == 0) continue;
+        const int rt = (int)(bc / CT);
+        const long long rfirst = (long long)rt * CT, rend = rfirst + CT;
+        if (bprev > rfirst) continue;   // an earlier boundary already covers this row tile
+        for (int tr = lane; tr < TR; tr += 32) {
+            double s = 0.0;
+            for (int cc = c - 1; cc < G_; cc++) {
+                const long long a0 = start(cc), a1 = start(cc + 1);
+                if (a0 >= rend) break;
+                if (a1 <= a0) continue;          // empty CTA range
+                const int slot = (rt == (int)(a0 / CT)) ? 0 : 1;
+                s += __ldcg(&args.scr->fix[((size_t)cc * 2 + slot) * TR + tr]);
+            }
+            const int row = rt * TR + tr;
+            if (row < rows) fixdot += epilogue<DT>(args, M, row, (V)s);
+        }
+    }
+    double fd = block_sum(fixdot, dred);
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int c = 0; c < G_; c++) tot += __ldcg(&args.scr->cta_dot[c]);
+        tot += fd;
+        run_finaliser(args, tot);
+        atomicExch(&args.scr->ticket, 0u);
+    }
+}
+
+// ---- host side -------------------------------------------------------------------------
+template <int DT>
+static size_t gemv_smem() {
+    return (size_t)GEMV_STAGES * Geo<DT>::TILE_BYTES + 2 * GEMV_STAGES * sizeof(uint64_t);
+}
+
+template <int DT, bool TMA>
+static void *gemv_func() {
+    return reinterpret_cast<void *>(&gemv_kernel<DT, TMA>);
+}
+
+GemvLaunch gemv_plan(int dtype, bool use_tma, int epi, int num_sms) {
+    (void)epi;
+    GemvLaunch L{};
+    L.block = GEMV_THREADS;
+    L.grid = 2 * num_sms;
+    switch (dtype) {
+        case DT_F64:
+            L.func = use_tma ? gemv_func<DT_F64, true>() : gemv_func<DT_F64, false>();
+            L.smem = gemv_smem<DT_F64>();
+            break;
+        case DT_BF16:
+            L.func = use_tma ? gemv_func<DT_BF16, true>() : gemv_func<DT_BF16, false>();
+            L.smem = gemv_smem<DT_BF16>();
+            break;
+        case DT_FP8:
+            L.func = use_tma ? gemv_func<DT_FP8, true>() : gemv_func<DT_FP8, false>();
+            L.smem = gemv_smem<DT_FP8>();
+            break;
+        default:
+            L.func = use_tma ? gemv_func<DT_F32, true>() : gemv_func<DT_F32, false>();
+            L.smem = gemv_smem<DT_F32>();
+            break;
+    }
+    if (!use_tma) L.smem = 2 * GEMV_STAGES * sizeof(uint64_t);
+    static bool attr_done[4][2] = {};
+    if (!attr_done[dtype & 3][use_tma]) {
+        cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        attr_done[dtype & 3][use_tma] = true;
+    }
+    if (L.grid > MAX_GRID) L.grid = MAX_GRID;
+    return L;
+}
+
+cudaError_t gemv_launch(const GemvLaunch &L, const MatDesc *dA, const GemvArgs &a,
+                        cudaStream_t s) {
+    GemvArgs aa = a;
+    void *params[] = {(void *)&dA, (void *)&aa};
+    return cudaLaunchKernel(L.func, dim3(L.grid), dim3(L.block), params, L.smem, s);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_tensor_map(MatDesc *h, int dtype, const void *ptr, int rows, int cols, long long lda) {
+    h->ptr = ptr;
+    h->lda = lda;
+    h->rows = rows;
+    h->cols = cols;
+    h->dtype = dtype;
+    h->use_tma = 0;
+    const int esz = dtype == DT_F64 ? 8 : dtype == DT_BF16 ? 2 : dtype == DT_FP8 ? 1 : 4;
+    const int tc = dtype == DT_F64 ? Geo<DT_F64>::TC : dtype == DT_BF16 ? Geo<DT_BF16>::TC
+                   : dtype == DT_FP8 ? Geo<DT_FP8>::TC : Geo<DT_F32>::TC;
+    const int tr = gemv_tile_rows(dtype);
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || rows <= 0 || cols <= 0) return false;
+    if (((uintptr_t)ptr & 15) != 0 || ((lda * esz) & 15) != 0) return false;
+    if ((unsigned long long)lda * esz >= (1ull << 40)) return false;
+    CUtensorMapDataType dt = dtype == DT_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                             : dtype == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                             : dtype == DT_FP8  ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)lda * esz};
+    cuuint32_t box[2] = {(cuuint32_t)tc, (cuuint32_t)tr};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(&h->tmap, dt, 2, const_cast<void *>(ptr), gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+    h->use_tma = 1;
+    return true;
+}
+
+// ---- quantisation of A (stage A, done once per solve) ------------------------------------
+// BF16: round-to-nearest-even directly from FP64.  FP32: the same to FP32.
+// FP8-e4m3: s_i = fp32(max_j |a_ij| / 448) (1 when that is 0), then
+// q_ij = e4m3 round-to-nearest-even, saturating, of a_ij / s_i (FP64 division).
+__global__ void quantize_kernel(int dtype, int rows, int cols, const double *__restrict__ A,
+                                long long lda, void *Q, long long ldq, float *scale) {
+    __shared__ double red[32];
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double *a = A + (long long)row * lda;
+        if (dtype == DT_FP8) {
+            double mx = 0.0;
+            for (int j = threadIdx.x; j < cols; j += blockDim.x) mx = fmax(mx, fabs(a[j]));
+            // block max (fixed order)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+            __syncthreads();
+            mx = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) mx = fmax(mx, red[w]);
+            float s = __double2float_rn(mx / 448.0);
+            if (!(s > 0.0f)) s = 1.0f;
+            if (threadIdx.x == 0) scale[row] = s;
+            const double sd = (double)s;
+            uint8_t *q = static_cast<uint8_t *>(Q) + (long long)row * ldq;
+            for (int j = threadIdx.x; j < cols; j += blockDim.x)
+                q[j] = (uint8_t)__nv_cvt_double_to_fp8(a[j] / sd, __NV_SATFINITE, __NV_E4M3);
+        } else if (dtype == DT_BF16) {
+            __nv_bfloat16 *q = static_cast<__nv_bfloat16 *>(Q) + (long long)row * ldq;
+            for (int j = threadIdx.x; j < cols; j += blockDim.x) q[j] = __double2bfloat16(a[j]);
+        } else {
+            float *q = static_cast<float *>(Q) + (long long)row * ldq;
+            for (int j = threadIdx.x; j < cols; j += blockDim.x) q[j] = __double2float_rn(a[j]);
+        }
+    }
+}
+
+cudaError_t quantize_launch(int dtype, int rows, int cols, const double *A, long long lda,
+                            void *Q, long long ldq, float *scale, int num_sms, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    int grid = rows < 8 * num_sms ? rows : 8 * num_sms;
+    quantize_kernel<<<grid, 256, 0, s>>>(dtype, rows, cols, A, lda, Q, ldq, scale);
+    return cudaGetLastError();
+}
+
+}  // namespace lsi

@@ -1,0 +1,703 @@
+// ls_api.cu -- the C ABI (include/ls.h): contexts, workspace, staging of host
+// or device buffers, and the device-resident solve drivers.
+//
+// The paper's host flow (section "Parallel implementation ... using CUDA":
+// allocate, copy in, choose the grid, run the kernel, copy out) becomes: copy
+// or borrow the inputs once, upload a small state block, launch ONE CUDA
+// graph whose while-nodes run the whole iteration on the device (the kernels
+// set the loop conditions), and read back the solution and the state.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ls_api_internal.h"
+
+using namespace lsi;
+
+// ============================================================================
+// small utilities
+// ============================================================================
+namespace lsi {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int is_device_ptr(const void *p) {
+    if (!p) return 0;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int map_cuda(cudaError_t e) { return e == cudaSuccess ? LS_OK : (e == cudaErrorMemoryAllocation ? LS_ERR_NOMEM : LS_ERR_CUDA); }
+
+// ---- workspace ----------------------------------------------------------------
+int ws_reserve(ls_ctx *c, size_t bytes) {
+    if (bytes <= c->ws_bytes) return LS_OK;
+    if (c->ws_user) return LS_ERR_NOMEM;
+    if (c->ws) cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    c->graph_cg.reset();
+    c->graph_gm.reset();
+    c->graph_mx.reset();
+    cudaError_t e = cudaMalloc(&c->ws, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LS_ERR_NOMEM;
+    }
+    c->ws_bytes = bytes;
+    return LS_OK;
+}
+
+// Carves consecutive 256-byte aligned regions out of a base pointer.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
+    template <class T>
+    T *take(size_t count) {
+        off = align_up(off, 256);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// ---- graphs ---------------------------------------------------------------------
+void GraphCache::reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    memset(key, 0, sizeof(key));
+}
+
+bool GraphCache::matches(const long long *k) const {
+    return exec && memcmp(key, k, sizeof(key)) == 0;
+}
+
+// Adds nodes one after another to a graph.
+struct Chain {
+    cudaGraph_t g;
+    cudaGraphNode_t last = nullptr;
+    cudaError_t err = cudaSuccess;
+    explicit Chain(cudaGraph_t gr) : g(gr) {}
+
+    void kernel(void *func, int grid, int block, size_t smem, void **args, bool coop) {
+        if (err != cudaSuccess) return;
+        cudaKernelNodeParams p{};
+        p.func = func;
+        p.gridDim = dim3(grid);
+        p.blockDim = dim3(block);
+        p.sharedMemBytes = (unsigned)smem;
+        p.kernelParams = args;
+        cudaGraphNode_t node;
+        err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &p);
+        if (err != cudaSuccess) return;
+        if (coop) {
+            cudaLaunchAttributeValue v{};
+            v.cooperative = 1;
+            err = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v);
+        }
+        last = node;
+    }
+    // Appends a while-node on handle h; returns its body graph.
+    cudaGraph_t loop(cudaGraphConditionalHandle h) {
+        if (err != cudaSuccess) return nullptr;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        err = cudaGraphAddNode(&node, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np);
+        if (err != cudaSuccess) return nullptr;
+        last = node;
+        return np.conditional.phGraph_out[0];
+    }
+};
+
+void gemv_node(Chain &ch, const GemvLaunch &L, const MatDesc *dA, const GemvArgs &a) {
+    // kernelParams must point at storage that outlives the call only until the
+    // node is added (the values are copied), so locals are fine.
+    const MatDesc *pA = dA;
+    GemvArgs aa = a;
+    void *args[] = {(void *)&pA, (void *)&aa};
+    ch.kernel(L.func, L.grid, L.block, L.smem, args, false);
+}
+
+int finish_graph(ls_ctx *c, GraphCache &gc, cudaGraph_t g, const long long *key) {
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    gc.reset();
+    gc.graph = g;
+    gc.exec = ex;
+    memcpy(gc.key, key, sizeof(gc.key));
+    (void)c;
+    return LS_OK;
+}
+
+// ---- state upload / download -------------------------------------------------------
+void state_init(State *h, int max_iter) {
+    memset(h, 0, sizeof(State));
+    h->max_iter = max_iter;
+}
+
+int upload_state(ls_ctx *c) {
+    return map_cuda(cudaMemcpyAsync(c->st, c->h_st, sizeof(State), cudaMemcpyHostToDevice, c->stream));
+}
+
+int upload_desc(ls_ctx *c, int which) {
+    return map_cuda(cudaMemcpyAsync(c->dA + which, c->h_desc + which, sizeof(MatDesc),
+                                    cudaMemcpyHostToDevice, c->stream));
+}
+
+int read_state(ls_ctx *c) {
+    cudaError_t e = cudaMemcpyAsync(c->h_st, c->st, sizeof(State), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return map_cuda(e);
+}
+
+int status_from_state(const State &s) {
+    if (s.err & ERRB_TIMEOUT) return LS_ERR_TIMEOUT;
+    if (s.err & ERRB_NAN) return LS_ERR_NAN;
+    if (s.status == LS_OK || s.status == LS_NOT_CONVERGED || s.status == LS_BREAKDOWN) return s.status;
+    return LS_NOT_CONVERGED;
+}
+
+// Input staging: copy a vector (host or device) into a device buffer.
+int copy_in(ls_ctx *c, double *dst, const double *src, size_t count) {
+    if (count == 0) return LS_OK;
+    return map_cuda(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->stream));
+}
+
+// A row-major n x n FP64 matrix: borrow it if it lives on the device,
+// otherwise copy it into `stage` with a 16-byte multiple leading dimension.
+int stage_matrix(ls_ctx *c, int n, const double *A, long long lda, double *stage,
+                 long long lda_stage, const double **outA, long long *outlda) {
+    if (is_device_ptr(A)) {
+        *outA = A;
+        *outlda = lda;
+        return LS_OK;
+    }
+    cudaError_t e = cudaMemcpy2DAsync(stage, lda_stage * sizeof(double), A, lda * sizeof(double),
+                                      n * sizeof(double), n, cudaMemcpyHostToDevice, c->stream);
+    *outA = stage;
+    *outlda = lda_stage;
+    return map_cuda(e);
+}
+
+}  // namespace lsi
+
+// ============================================================================
+// ABI: options, context, workspace
+// ============================================================================
+extern "C" int ls_opts_default(ls_opts *o) {
+    if (!o) return LS_ERR_ARG;
+    o->rtol = 1e-10;
+    o->max_iter = 0;          // 0 = method default
+    o->restart = 30;
+    o->precision = LS_F64;
+    o->refine = LS_REFINE_FCG;
+    o->inner_iters = 25;
+    o->inner_rtol = 0.0;
+    o->x0_given = 0;
+    o->reorth = 0;
+    return LS_OK;
+}
+
+extern "C" const char *ls_strerror(int s) {
+    switch (s) {
+        case LS_OK: return "converged";
+        case LS_NOT_CONVERGED: return "iteration limit reached before the tolerance";
+        case LS_BREAKDOWN: return "breakdown (non-positive curvature or zero rotation pivot)";
+        case LS_ERR_ARG: return "invalid argument";
+        case LS_ERR_NOMEM: return "out of device memory / workspace too small";
+        case LS_ERR_CUDA: return "CUDA runtime error";
+        case LS_ERR_TIMEOUT: return "an on-device wait timed out";
+        case LS_ERR_BUSY: return "server queue full or no capacity";
+        case LS_ERR_NAN: return "NaN or Inf in the input or the iteration";
+        case LS_ERR_UNSUPPORTED: return "unsupported option combination or device";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int ls_create(ls_ctx **out, int device, void *stream) {
+    if (!out) return LS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return LS_ERR_CUDA;
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, device) != cudaSuccess) return LS_ERR_CUDA;
+    if (!(pr.major == 10 && pr.minor == 3)) return LS_ERR_UNSUPPORTED;
+    ls_ctx *c = new (std::nothrow) ls_ctx();
+    if (!c) return LS_ERR_NOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->num_sms = pr.multiProcessorCount;
+    c->K = krylov_kernels(c->num_sms);
+    // fixed device block: state, small GMRES state, GEMV scratch, barrier, descriptors, partials
+    Carver cv(nullptr);
+    cv.take<State>(1);
+    cv.take<GmresSmall>(1);
+    cv.take<GemvScratch>(1);
+    cv.take<GridBar>(1);
+    cv.take<MatDesc>(2);
+    cv.take<double>((size_t)PART_SLOTS * MAX_GRID);
+    size_t fixed = align_up(cv.off, 256);
+    if (cudaMalloc(&c->fixed, fixed) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LS_ERR_NOMEM;
+    }
+    Carver cf(c->fixed);
+    c->st = cf.take<State>(1);
+    c->gm = cf.take<GmresSmall>(1);
+    c->scr = cf.take<GemvScratch>(1);
+    c->bar = cf.take<GridBar>(1);
+    c->dA = cf.take<MatDesc>(2);
+    c->part = cf.take<double>((size_t)PART_SLOTS * MAX_GRID);
+    cudaError_t e = cudaMemsetAsync(c->fixed, 0, fixed, c->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_st, sizeof(State));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_desc, 2 * sizeof(MatDesc));
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ls_destroy(c);
+        return LS_ERR_CUDA;
+    }
+    *out = c;
+    return LS_OK;
+}
+
+extern "C" int ls_destroy(ls_ctx *c) {
+    if (!c) return LS_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    c->graph_cg.reset();
+    c->graph_gm.reset();
+    c->graph_mx.reset();
+    extra_destroy(c);
+    if (c->ws && !c->ws_user) cudaFree(c->ws);
+    if (c->fixed) cudaFree(c->fixed);
+    if (c->h_st) cudaFreeHost(c->h_st);
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return LS_OK;
+}
+
+extern "C" int ls_set_workspace(ls_ctx *c, void *ptr, size_t bytes) {
+    if (!c) return LS_ERR_ARG;
+    if (ptr && ((uintptr_t)ptr & 255)) return LS_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->ws && !c->ws_user) cudaFree(c->ws);
+    c->graph_cg.reset();
+    c->graph_gm.reset();
+    c->graph_mx.reset();
+    c->ws = static_cast<char *>(ptr);
+    c->ws_bytes = ptr ? bytes : 0;
+    c->ws_user = ptr != nullptr;
+    return LS_OK;
+}
+
+extern "C" long long ls_kernel_launches(ls_ctx *c) { return c ? c->launches_total : 0; }
+
+// ============================================================================
+// FP64 CG / GMRES
+// ============================================================================
+namespace lsi {
+
+struct F64Layout {
+    double *x, *b, *r, *p, *q, *V, *Astage;
+    long long npad, ldv, lda_stage;
+    size_t bytes;
+};
+
+F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA) {
+    F64Layout L{};
+    L.npad = (long long)align_up((size_t)std::max(n, 1), 64);
+    L.ldv = L.npad;
+    L.lda_stage = (long long)align_up((size_t)std::max(n, 1), 2);
+    Carver cv(base);
+    L.x = cv.take<double>(L.npad);
+    L.b = cv.take<double>(L.npad);
+    L.r = cv.take<double>(L.npad);
+    L.p = cv.take<double>(L.npad);
+    L.q = cv.take<double>(L.npad);
+    L.V = gmres ? cv.take<double>((size_t)L.ldv * (m + 1)) : nullptr;
+    L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
+    L.bytes = align_up(cv.off, 256);
+    return L;
+}
+
+int check_common(ls_ctx *c, int n, const double *A, long long lda, const double *b, double *x,
+                 const ls_opts *o) {
+    if (!c || n < 0 || lda < n || (n > 0 && (!A || !b || !x)) || !o) return LS_ERR_ARG;
+    if (!(o->rtol >= 0.0) || o->max_iter < 0) return LS_ERR_ARG;
+    return LS_OK;
+}
+
+void fill_info(ls_info *info, const State &s, int status, float ms, double bytes, long long launches) {
+    if (!info) return;
+    info->status = status;
+    info->iters = s.iter;
+    info->outer_iters = s.cycles;
+    info->rel_res = s.bnorm > 0 ? s.rnorm / s.bnorm : 0.0;
+    info->true_rel_res = s.bnorm > 0 ? s.true_rnorm / s.bnorm : 0.0;
+    info->time_ms = ms;
+    info->bytes_moved = bytes;
+    info->launches = launches;
+}
+
+Vecs make_vecs(ls_ctx *c, const F64Layout &L, int n, double rtol) {
+    Vecs v{};
+    v.n = n;
+    v.x = L.x;
+    v.b = L.b;
+    v.r = L.r;
+    v.p = L.p;
+    v.q = L.q;
+    v.V = L.V;
+    v.ldv = L.ldv;
+    v.part = c->part;
+    v.bar = c->bar;
+    v.st = c->st;
+    v.gm = c->gm;
+    v.rtol = rtol;
+    return v;
+}
+
+}  // namespace lsi
+
+// Builds: [resid GEMV if x0] cg_init, while(outer){ while(inner){GEMV, update}, resid GEMV, check }
+static int build_cg_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
+                          const long long *key) {
+    cudaGraph_t g;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LS_ERR_CUDA;
+    cudaGraphConditionalHandle ho, hi;
+    if (cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    Chain top(g);
+    const MatDesc *dA = c->dA;
+    if (x0_given) {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.r; a.b = v.b; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_RESID; a.fin = FIN_TRUE_RES;
+        gemv_node(top, L, dA, a);
+    }
+    {
+        Vecs vv = v;
+        int x0 = x0_given;
+        void *args[] = {&vv, &x0, &ho, &hi};
+        top.kernel(c->K.cg_init, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    cudaGraph_t body_o = top.loop(ho);
+    if (top.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
+    Chain outer(body_o);
+    cudaGraph_t body_i = outer.loop(hi);
+    if (outer.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
+    Chain inner(body_i);
+    {
+        GemvArgs a{};
+        a.x = v.p; a.y = v.q; a.z = v.p; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_DOT; a.fin = FIN_CG_ALPHA;
+        gemv_node(inner, L, dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &hi};
+        inner.kernel(c->K.cg_update, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.q; a.b = v.b; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_RESID; a.fin = FIN_TRUE_RES;
+        gemv_node(outer, L, dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &ho, &hi};
+        outer.kernel(c->K.cg_check, c->K.coop_grid, c->K.block, 0, args, false);
+    }
+    if (inner.err != cudaSuccess || outer.err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    return finish_graph(c, c->graph_cg, g, key);
+}
+
+// Builds: gm_init, while(outer){ resid GEMV, gm_start, while(inner){GEMV, arnoldi}, gm_finish }
+static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
+                             const long long *key) {
+    cudaGraph_t g;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LS_ERR_CUDA;
+    cudaGraphConditionalHandle ho, hi;
+    if (cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    const MatDesc *dA = c->dA;
+    Chain top(g);
+    {
+        Vecs vv = v;
+        int x0 = x0_given;
+        void *args[] = {&vv, &x0, &ho};
+        top.kernel(c->K.gm_init, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    cudaGraph_t body_o = top.loop(ho);
+    if (top.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
+    Chain outer(body_o);
+    {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.q; a.b = v.b; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_RESID; a.fin = FIN_TRUE_RES;
+        gemv_node(outer, L, dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &ho, &hi};
+        outer.kernel(c->K.gm_start, c->K.coop_grid, c->K.block, 0, args, false);
+    }
+    cudaGraph_t body_i = outer.loop(hi);
+    if (outer.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
+    Chain inner(body_i);
+    {
+        GemvArgs a{};
+        a.x = v.V; a.y = v.V; a.kptr = &v.st->k; a.kstride = v.ldv; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_NRM; a.fin = FIN_WNORM0;
+        gemv_node(inner, L, dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &hi};
+        inner.kernel(c->K.gm_arnoldi, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    {
+        Vecs vv = v;
+        void *args[] = {&vv};
+        outer.kernel(c->K.gm_finish, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    if (inner.err != cudaSuccess || outer.err != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    return finish_graph(c, c->graph_gm, g, key);
+}
+
+static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda, const double *b,
+                      double *x, const ls_opts *opts, ls_info *info) {
+    ls_opts o;
+    if (opts) o = *opts;
+    else ls_opts_default(&o);
+    int rc = check_common(c, n, A, lda, b, x, &o);
+    if (rc) return rc;
+    if (method == LS_METHOD_GMRES && (o.restart < 1 || o.restart > LS_MAX_RESTART)) return LS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+    if (n == 0) {
+        State s{};
+        fill_info(info, s, LS_OK, 0.f, 0.0, 0);
+        return LS_OK;
+    }
+    const int m = o.restart;
+    const int max_iter = o.max_iter > 0 ? o.max_iter : 10 * n + 10;
+    const bool a_dev = is_device_ptr(A);
+    F64Layout L = f64_layout(nullptr, n, m, method == LS_METHOD_GMRES, !a_dev);
+    rc = ws_reserve(c, L.bytes);
+    if (rc) return rc;
+    L = f64_layout(c->ws, n, m, method == LS_METHOD_GMRES, !a_dev);
+
+    // stage inputs
+    const double *Ad;
+    long long ldad;
+    rc = stage_matrix(c, n, A, lda, L.Astage, L.lda_stage, &Ad, &ldad);
+    if (!rc) rc = copy_in(c, L.b, b, n);
+    if (!rc && o.x0_given) rc = copy_in(c, L.x, x, n);
+    if (rc) return rc;
+    MatDesc *hd = &c->h_desc[0];
+    memset(hd, 0, sizeof(MatDesc));
+    make_tensor_map(hd, DT_F64, Ad, n, n, ldad);
+    rc = upload_desc(c, 0);
+    State *hs = c->h_st;
+    state_init(hs, max_iter);
+    hs->m = m;
+    hs->reorth = o.reorth;
+    if (!rc) rc = upload_state(c);
+    if (rc) return rc;
+
+    Vecs v = make_vecs(c, L, n, o.rtol);
+    GemvLaunch GL = gemv_plan(DT_F64, hd->use_tma != 0, EPI_DOT, c->num_sms);
+    long long key[8] = {method, n, (long long)(uintptr_t)c->ws, L.ldv, o.x0_given, hd->use_tma,
+                        (long long)(uintptr_t)c->stream, 0};
+    GraphCache &gc = method == LS_METHOD_CG ? c->graph_cg : c->graph_gm;
+    if (!gc.matches(key)) {
+        rc = method == LS_METHOD_CG ? build_cg_graph(c, v, GL, o.x0_given, key)
+                                    : build_gmres_graph(c, v, GL, o.x0_given, key);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaEventRecord(c->ev0, c->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gc.exec, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    rc = read_state(c);
+    if (rc) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    const State &s = *hs;
+    int status = status_from_state(s);
+    // x back to the caller (host or device)
+    if (status >= 0) {
+        e = cudaMemcpyAsync(x, L.x, n * sizeof(double), cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    // matrix passes: method products + true-residual checks (+ the x0 residual)
+    double passes;
+    State sc = s;
+    if (method == LS_METHOD_CG) {
+        passes = s.iter + s.cycles + (o.x0_given ? 1 : 0);
+    } else {
+        passes = s.total + s.cycles + 1;
+        sc.iter = s.total;
+    }
+    c->launches_total += (long long)s.launches;
+    fill_info(info, sc, status, ms, passes * (double)n * n * 8.0, (long long)s.launches);
+    return status;
+}
+
+extern "C" int ls_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b,
+                           double *x, const ls_opts *opts, ls_info *info) {
+    if (opts && opts->precision != LS_F64) return mixed_cg_solve(c, n, A, lda, b, x, opts, info);
+    return krylov_f64(c, LS_METHOD_CG, n, A, lda, b, x, opts, info);
+}
+
+extern "C" int ls_gmres_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b,
+                              double *x, const ls_opts *opts, ls_info *info) {
+    if (opts && opts->precision != LS_F64) return LS_ERR_UNSUPPORTED;
+    return krylov_f64(c, LS_METHOD_GMRES, n, A, lda, b, x, opts, info);
+}
+
+extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const ls_opts *opts,
+                                 int a_on_device, size_t *bytes) {
+    if (!c || !bytes || n < 0 || nrhs < 1) return LS_ERR_ARG;
+    ls_opts o;
+    if (opts) o = *opts;
+    else ls_opts_default(&o);
+    if (o.precision != LS_F64 && method == LS_METHOD_CG) {
+        *bytes = mixed_workspace_bytes(n, &o, a_on_device != 0);
+        return LS_OK;
+    }
+    *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device).bytes;
+    return LS_OK;
+}
+
+// ============================================================================
+// kernel-level entry points
+// ============================================================================
+extern "C" int ls_gemv(ls_ctx *c, int dtype, int rows, int cols, const void *A, int64_t lda,
+                       const float *scale, const void *x, void *y) {
+    if (!c || rows < 0 || cols < 0 || lda < cols || dtype < 0 || dtype > 3) return LS_ERR_ARG;
+    if (rows == 0) return LS_OK;
+    if (!A || !x || !y || (dtype == DT_FP8 && !scale)) return LS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+    MatDesc *hd = &c->h_desc[1];
+    memset(hd, 0, sizeof(MatDesc));
+    make_tensor_map(hd, dtype, A, rows, cols, lda);
+    hd->scale = scale;
+    int rc = upload_desc(c, 1);
+    if (rc) return rc;
+    state_init(c->h_st, 0);
+    rc = upload_state(c);
+    if (rc) return rc;
+    GemvLaunch L = gemv_plan(dtype, hd->use_tma != 0, EPI_STORE, c->num_sms);
+    GemvArgs a{};
+    a.x = x;
+    a.y = y;
+    a.st = c->st;
+    a.scr = c->scr;
+    a.epi = EPI_STORE;
+    a.fin = FIN_STORE;
+    cudaError_t e = gemv_launch(L, c->dA + 1, a, c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    rc = read_state(c);
+    if (rc) return rc;
+    c->launches_total += (long long)c->h_st->launches;
+    if (c->h_st->err & ERRB_TIMEOUT) return LS_ERR_TIMEOUT;
+    return LS_OK;
+}
+
+extern "C" int ls_gemv_timed(ls_ctx *c, int dtype, int rows, int cols, const void *A, int64_t lda,
+                             const float *scale, const void *x, void *y, int reps,
+                             double *ms_per_launch) {
+    if (!c || rows <= 0 || cols <= 0 || lda < cols || dtype < 0 || dtype > 3 || reps < 1 ||
+        !ms_per_launch)
+        return LS_ERR_ARG;
+    if (!A || !x || !y || (dtype == DT_FP8 && !scale)) return LS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+    MatDesc *hd = &c->h_desc[1];
+    memset(hd, 0, sizeof(MatDesc));
+    make_tensor_map(hd, dtype, A, rows, cols, lda);
+    hd->scale = scale;
+    int rc = upload_desc(c, 1);
+    if (rc) return rc;
+    state_init(c->h_st, 0);
+    rc = upload_state(c);
+    if (rc) return rc;
+    GemvLaunch L = gemv_plan(dtype, hd->use_tma != 0, EPI_STORE, c->num_sms);
+    GemvArgs a{};
+    a.x = x;
+    a.y = y;
+    a.st = c->st;
+    a.scr = c->scr;
+    a.epi = EPI_STORE;
+    a.fin = FIN_STORE;
+    cudaError_t e = gemv_launch(L, c->dA + 1, a, c->stream);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev0, c->stream);
+    for (int i = 0; i < reps && e == cudaSuccess; i++) e = gemv_launch(L, c->dA + 1, a, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    rc = read_state(c);
+    if (rc) return rc;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    *ms_per_launch = ms / reps;
+    c->launches_total += (long long)c->h_st->launches;
+    if (c->h_st->err & ERRB_TIMEOUT) return LS_ERR_TIMEOUT;
+    return LS_OK;
+}
+
+extern "C" int ls_quantize(ls_ctx *c, int dtype, int rows, int cols, const double *A, int64_t lda,
+                           void *Q, int64_t ldq, float *scale) {
+    if (!c || rows < 0 || cols < 0 || lda < cols || ldq < cols) return LS_ERR_ARG;
+    if (dtype != DT_BF16 && dtype != DT_FP8 && dtype != DT_F32) return LS_ERR_ARG;
+    if (rows == 0) return LS_OK;
+    if (!A || !Q || (dtype == DT_FP8 && !scale)) return LS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+    cudaError_t e = quantize_launch(dtype, rows, cols, A, lda, Q, ldq, scale, c->num_sms, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) c->launches_total += 1;
+    return map_cuda(e);
+}

@@ -1,0 +1,166 @@
+// ls_internal.h -- structures shared by the host drivers and the kernels.
+#pragma once
+
+#include <cuda.h>            // CUtensorMap (type only; the driver is reached by entry point)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ls.h"
+
+namespace lsi {
+
+// storage formats of A
+enum DType : int { DT_F64 = 0, DT_BF16 = 1, DT_FP8 = 2, DT_F32 = 3 };
+
+// ---- GEMV geometry ----------------------------------------------------------
+// A tile of TR rows x TC columns is one TMA box.  Consumer warps form a
+// WR x WC grid over the tile: each lane holds VEC consecutive columns and
+// RW rows (TR = WR * RW, TC = WC * 32 * VEC).
+constexpr int GEMV_CONSUMER_WARPS = 4;
+constexpr int GEMV_THREADS = (GEMV_CONSUMER_WARPS + 1) * 32;
+constexpr int GEMV_STAGES = 6;
+constexpr int GEMV_MAX_TR = 64;
+constexpr int MAX_GRID = 2048;     // upper bound on CTAs of any persistent launch
+
+// ---- device-resident matrix descriptor ---------------------------------------
+struct alignas(128) MatDesc {
+    CUtensorMap tmap;        // 2-D tiled TMA map of A (valid when use_tma)
+    const void *ptr;         // A (row-major)
+    const float *scale;      // FP8 row scales (else nullptr)
+    long long lda;           // elements
+    int rows, cols;
+    int dtype;
+    int use_tma;
+    int pad_[8];
+};
+
+// error bits
+enum : int { ERRB_TIMEOUT = 1, ERRB_NAN = 2 };
+
+// stop reasons / status written by the kernels (same values as LS_*)
+// State lives in device memory; one per context.
+struct State {
+    // CG / common
+    double rho;          // r.r
+    double alpha, beta;
+    double pq;           // p.Ap
+    double bnorm;        // ||b||
+    double tol_abs;      // rtol * ||b||
+    double rnorm;        // recursive residual norm
+    double true_rnorm;   // ||b - A x|| at the last check
+    double dot;          // scratch result of FIN_STORE
+    // GMRES
+    double est;          // |g_{k+1}|
+    double wnorm0;       // ||A v_k||^2 before orthogonalisation
+    // mixed precision (inner FP32 loop, outer FP64 loop)
+    double in_rho, in_alpha, in_pq, in_rho0;
+    double prn;          // p.r partial total (FCG)
+    double outer_rn;     // ||r|| at the start of the outer step
+    int iter;            // method matvecs (inner ones for the mixed path)
+    int max_iter;
+    int status;          // 0 running/converged, LS_NOT_CONVERGED, LS_BREAKDOWN
+    int err;             // ERRB_* bits
+    int conv;            // recursive residual passed the test
+    int k;               // GMRES: Arnoldi steps in the current cycle
+    int m;               // GMRES restart length
+    int reorth;          // GMRES: 1 = always two passes
+    int total;           // GMRES: Arnoldi steps over all cycles
+    int cycles;          // GMRES cycles / mixed outer steps
+    int in_iter, in_max; // inner loop counters
+    int outer, max_outer;
+    int nstored;         // FCG directions stored
+    int in_stop;
+    float in_tol2;       // inner (rtol^2 * rho0), <0 = fixed count
+    int launches_lo;     // kernels executed (low word; counted by block 0)
+    unsigned long long launches;
+};
+
+// GMRES small dense state (device)
+struct GmresSmall {
+    double H[(LS_MAX_RESTART + 1) * LS_MAX_RESTART];  // rotated Hessenberg, column-major
+    double cs[LS_MAX_RESTART], sn[LS_MAX_RESTART];
+    double g[LS_MAX_RESTART + 1];
+    double y[LS_MAX_RESTART];
+    double h[LS_MAX_RESTART + 1];                     // current column (projection)
+};
+
+// ---- per-launch scratch of the persistent GEMV --------------------------------
+struct GemvScratch {
+    unsigned ticket;                                 // last-CTA detection (self-resetting)
+    unsigned pad_[31];
+    double cta_dot[MAX_GRID];                        // per-CTA dot contributions
+    double fix[MAX_GRID * 2 * GEMV_MAX_TR];          // partial row sums of split row tiles
+};
+
+// epilogues: what is done with a finished row sum s_i
+enum : int {
+    EPI_STORE = 0,      // y_i = s_i
+    EPI_DOT = 1,        // y_i = s_i; dot += z_i y_i
+    EPI_RESID = 2,      // y_i = b_i - s_i; dot += y_i^2
+    EPI_NRM = 3,        // y_i = s_i; dot += y_i^2
+};
+// finalisers run by the last CTA on the reduced dot
+enum : int {
+    FIN_STORE = 0,      // st->dot = dot (and *dot_out if given)
+    FIN_CG_ALPHA = 1,   // pq = dot; alpha = rho / pq; breakdown if !(pq > 0)
+    FIN_TRUE_RES = 2,   // true_rnorm = sqrt(dot)
+    FIN_WNORM0 = 3,     // wnorm0 = dot
+    FIN_INNER_ALPHA = 4,// in_pq = dot; in_alpha = in_rho / in_pq (inner stop on breakdown)
+    FIN_FCG_D = 5,      // pq = dot (p.Ap of the outer direction)
+};
+
+struct GemvArgs {
+    const void *x;       // input vector (double for F64, float otherwise)
+    void *y;             // output vector (same type as x)
+    const int *kptr;     // if set: x += (*kptr) * kstride, y += (*kptr + 1) * kstride
+    long long kstride;   // (elements) -- lets one graph node walk the Krylov basis
+    const double *b;     // EPI_RESID
+    const void *z;       // EPI_DOT
+    double *dot_out;     // optional copy of the final dot
+    State *st;
+    GemvScratch *scr;
+    int epi, fin;
+};
+
+// ---- launchers (k_gemv.cu) -------------------------------------------------------
+struct GemvLaunch {
+    void *func;          // kernel entry
+    int grid, block;
+    size_t smem;
+};
+// Choose the kernel for a matrix (TMA or plain-load variant) and epilogue.
+GemvLaunch gemv_plan(int dtype, bool use_tma, int epi, int num_sms);
+cudaError_t gemv_launch(const GemvLaunch &L, const MatDesc *dA, const GemvArgs &a,
+                        cudaStream_t s);
+// Fill the TMA map of a matrix descriptor (host side); returns false when the
+// layout cannot be streamed by TMA (alignment), in which case use_tma = 0.
+bool make_tensor_map(MatDesc *h, int dtype, const void *ptr, int rows, int cols, long long lda);
+int gemv_tile_rows(int dtype);
+cudaError_t quantize_launch(int dtype, int rows, int cols, const double *A, long long lda,
+                            void *Q, long long ldq, float *scale, int num_sms, cudaStream_t s);
+
+// ---- FP64 solver vectors (workspace) ---------------------------------------------
+struct GridBar;
+struct Vecs {
+    int n;
+    double *x, *b, *r, *p, *q;
+    double *V;           // GMRES basis, column-major, column stride ldv
+    long long ldv;
+    double *part;        // cooperative partial sums, [slot][block]
+    GridBar *bar;
+    State *st;
+    GmresSmall *gm;
+    double rtol;
+};
+constexpr int PART_SLOTS = LS_MAX_RESTART + 4;
+
+// ---- Krylov launchers (k_krylov.cu) -----------------------------------------------
+struct KrylovKernels {
+    void *cg_init, *cg_update, *cg_check;
+    void *gm_init, *gm_start, *gm_arnoldi, *gm_finish;
+    int coop_grid;       // blocks of the cooperative vector kernels
+    int block;           // threads per block
+};
+KrylovKernels krylov_kernels(int num_sms);
+
+}  // namespace lsi

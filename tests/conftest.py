@@ -17,3 +17,26 @@ def pytest_configure(config):
 def oracle():
     import oracle as o
     return o.default()
+
+
+@pytest.fixture(scope="session")
+def lslib():
+    from paper_1511_07207_gb300 import binding
+    return binding.load()
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="session")
+def ctx(gpu, lslib):
+    import torch
+    from paper_1511_07207_gb300 import binding
+    h = binding.ls_create(0, torch.cuda.current_stream(gpu))
+    yield h
+    binding.ls_destroy(h)
