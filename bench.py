@@ -393,6 +393,45 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_kernel(args):
+    """Kernel-only mode (used for ncu captures on small cases): time the
+    y = A x kernel on a random n x n matrix of the given storage format."""
+    import numpy as np
+    import torch
+    from paper_1511_07207_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    ctx = B.ls_create(0, torch.cuda.current_stream(dev))
+    n = args.n
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    A64 = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
+    dt = {"f64": B.LS_F64, "bf16": B.LS_BF16_IR, "fp8": B.LS_FP8_IR, "f32": B.LS_F32_IR}[args.dtype]
+    scale = None
+    if dt == B.LS_F64:
+        A = A64
+        x = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        esz = 8
+    else:
+        tdt = {B.LS_BF16_IR: torch.int16, B.LS_FP8_IR: torch.uint8, B.LS_F32_IR: torch.float32}[dt]
+        A = torch.empty((n, n), dtype=tdt, device=dev)
+        scale = torch.empty(n, dtype=torch.float32, device=dev) if dt == B.LS_FP8_IR else None
+        assert B.ls_quantize(ctx, dt, A64, A, scale) == B.LS_OK
+        del A64
+        x = torch.randn(n, dtype=torch.float32, device=dev, generator=g)
+        y = torch.empty(n, dtype=torch.float32, device=dev)
+        esz = {B.LS_BF16_IR: 2, B.LS_FP8_IR: 1, B.LS_F32_IR: 4}[dt]
+    st, ms = B.ls_gemv_timed(ctx, dt, A, x, y, args.reps)
+    assert st == B.LS_OK
+    byts = esz * n * n + (8 if dt == B.LS_F64 else 4) * 2 * n + (4 * n if scale is not None else 0)
+    peaks, src = load_peaks()
+    print(json.dumps({"kernel": "gemv", "dtype": args.dtype, "n": n, "reps": args.reps,
+                      "ms": round(ms, 5), "GB/s": round(byts / ms / 1e6, 1),
+                      "hbm_frac": round(byts / ms / 1e6 / peaks["hbm_gbs"], 4),
+                      "peak_source": src}))
+    B.ls_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,12 +441,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-cg-sample", type=int, default=60)
+    ap.add_argument("--kernel", choices=["gemv"], default=None,
+                    help="kernel-only timing (small cases for ncu captures)")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--dtype", choices=["f64", "bf16", "fp8", "f32"], default="f64")
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--ref-cg-iters", type=int, default=0,
                     help="reference arm: CG iteration count to scale to (0 = run the oracle once)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if args.kernel == "gemv":
+        run_kernel(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)
