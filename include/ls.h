@@ -243,6 +243,36 @@ int ls_quantize(ls_ctx *ctx, int dtype, int rows, int cols, const double *A, int
 int ls_gemv_timed(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int64_t lda,
                   const float *scale, const void *x, void *y, int reps, double *ms_per_launch);
 
+/*
+ * y = A x without any device allocation and without a context.  The paper has
+ * no counterpart: this is a library service for callers that cannot allocate
+ * device memory -- a process whose device memory is already fully reserved by
+ * a framework's caching allocator or a memory pool (a direct cudaMalloc would
+ * fail or fragment the pool), or a latency-bound loop that must not pay for
+ * cudaMalloc / cudaFree, which can synchronise the whole device.  (ls_gemv
+ * needs a context, and ls_create allocates the context's device block.)
+ *
+ * Arguments are those of ls_gemv, plus the cudaStream_t to run on (NULL = the
+ * legacy default stream); the current device is used.  The call returns after
+ * y is written.  Every piece of scratch the kernel needs (matrix descriptor,
+ * state block, completion ticket, per-CTA and per-row-tile partial sums)
+ * lives in one static device array of LS_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading this library holds until the process exits; it has room for the
+ * partial sums of LS_NOALLOC_MAX_CTAS CTAs (the kernel runs 2 CTAs per SM), so
+ * on a device with more than LS_NOALLOC_MAX_CTAS / 2 SMs the call returns
+ * LS_ERR_UNSUPPORTED.  The array is shared by every call on a device and keeps
+ * the last call's contents (each call clears what must start at zero), so
+ * calls whose work overlaps on the GPU -- from several host threads, or on
+ * several streams -- race and must be serialised by the caller.  The first
+ * call on each device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * LS_ERR_ARG for bad sizes or pointers; LS_ERR_CUDA if a CUDA call fails.
+ */
+#define LS_NOALLOC_MAX_CTAS 512
+#define LS_NOALLOC_SCRATCH_BYTES (576 * 1024)
+int ls_gemv_noalloc(int dtype, int rows, int cols, const void *A, int64_t lda,
+                    const float *scale, const void *x, void *y, void *cuda_stream);
+
 /* Kernels the context has executed on the device since it was created. */
 long long ls_kernel_launches(ls_ctx *ctx);
 

@@ -27,8 +27,8 @@ LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 4096, 32
 ABI_FUNCTIONS = (
     "ls_opts_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_set_workspace",
     "ls_cg_solve", "ls_gmres_solve", "ls_batch_solve", "ls_server_start", "ls_server_submit",
-    "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_quantize",
-    "ls_kernel_launches", "ls_strerror",
+    "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
+    "ls_quantize", "ls_kernel_launches", "ls_strerror",
 )
 
 
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.ls_gemv.argtypes = [P, I, I, I, P, I64, P, P, P]
         lib.ls_gemv_timed.argtypes = [P, I, I, I, P, I64, P, P, P, I,
                                       ctypes.POINTER(ctypes.c_double)]
+        lib.ls_gemv_noalloc.argtypes = [I, I, I, P, I64, P, P, P, P]
         lib.ls_quantize.argtypes = [P, I, I, I, P, I64, P, I64, P]
         lib.ls_kernel_launches.argtypes = [P]
         lib.ls_kernel_launches.restype = ctypes.c_longlong
@@ -247,6 +248,17 @@ def ls_gemv_timed(ctx, dtype, A, x, y, reps, scale=None):
     st = load().ls_gemv_timed(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x),
                               ptr(y), reps, ctypes.byref(ms))
     return st, ms.value
+
+
+def ls_gemv_noalloc(dtype, A, x, y, scale=None, stream=None):
+    """y = A x with no device allocation and no context (see ls.h): for callers
+    that cannot allocate device memory.  Runs on `stream` (a cudaStream_t int,
+    a torch.cuda.Stream, or None) on the current device."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rows, cols = A.shape
+    return load().ls_gemv_noalloc(dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x),
+                                  ptr(y), stream)
 
 
 def ls_quantize(ctx, dtype, A, Q, scale=None):
