@@ -421,7 +421,7 @@ def run_kernel(args):
         x = torch.randn(n, dtype=torch.float32, device=dev, generator=g)
         y = torch.empty(n, dtype=torch.float32, device=dev)
         esz = {B.LS_BF16_IR: 2, B.LS_FP8_IR: 1, B.LS_F32_IR: 4}[dt]
-    st, ms = B.ls_gemv_timed(ctx, dt, A, x, y, args.reps)
+    st, ms = B.ls_gemv_timed(ctx, dt, A, x, y, args.reps, scale=scale)
     assert st == B.LS_OK
     byts = esz * n * n + (8 if dt == B.LS_F64 else 4) * 2 * n + (4 * n if scale is not None else 0)
     peaks, src = load_peaks()

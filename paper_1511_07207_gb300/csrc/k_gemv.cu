@@ -106,23 +106,23 @@ __device__ __forceinline__ void load_x(const typename Cfg<DT>::V *x, int c0, int
     }
 }
 
-// acc += a[0:VEC] . p[0:VEC]; `a` points at VEC consecutive stored elements in
-// shared memory (aligned to the vector width).
+// acc0 + acc1 += a[0:VEC] . p[0:VEC] (two independent FMA chains); `a` points
+// at VEC consecutive stored elements in shared memory, aligned to the vector.
 template <int DT>
 __device__ __forceinline__ void dot_tile(const typename Cfg<DT>::T *a,
                                          const typename Cfg<DT>::V (&p)[Cfg<DT>::VEC],
-                                         typename Cfg<DT>::V &acc) {
+                                         typename Cfg<DT>::V &acc0, typename Cfg<DT>::V &acc1) {
     if constexpr (DT == DT_F64) {
         double2 v = *reinterpret_cast<const double2 *>(a);
-        acc = fma(v.x, p[0], acc);
-        acc = fma(v.y, p[1], acc);
+        acc0 = fma(v.x, p[0], acc0);
+        acc1 = fma(v.y, p[1], acc1);
     } else if constexpr (DT == DT_BF16) {
         uint4 v = *reinterpret_cast<const uint4 *>(a);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            acc = fmaf(__uint_as_float(w[k] << 16), p[2 * k], acc);
-            acc = fmaf(__uint_as_float(w[k] & 0xffff0000u), p[2 * k + 1], acc);
+            acc0 = fmaf(__uint_as_float(w[k] << 16), p[2 * k], acc0);
+            acc1 = fmaf(__uint_as_float(w[k] & 0xffff0000u), p[2 * k + 1], acc1);
         }
     } else if constexpr (DT == DT_FP8) {
         uint2 v = *reinterpret_cast<const uint2 *>(a);
@@ -135,26 +135,53 @@ __device__ __forceinline__ void dot_tile(const typename Cfg<DT>::T *a,
                                                         __NV_E4M3);
             float2 f0 = __half22float2(*reinterpret_cast<__half2 *>(&h0));
             float2 f1 = __half22float2(*reinterpret_cast<__half2 *>(&h1));
-            acc = fmaf(f0.x, p[4 * k + 0], acc);
-            acc = fmaf(f0.y, p[4 * k + 1], acc);
-            acc = fmaf(f1.x, p[4 * k + 2], acc);
-            acc = fmaf(f1.y, p[4 * k + 3], acc);
+            acc0 = fmaf(f0.x, p[4 * k + 0], acc0);
+            acc1 = fmaf(f0.y, p[4 * k + 1], acc1);
+            acc0 = fmaf(f1.x, p[4 * k + 2], acc0);
+            acc1 = fmaf(f1.y, p[4 * k + 3], acc1);
         }
     } else {
         float4 v = *reinterpret_cast<const float4 *>(a);
-        acc = fmaf(v.x, p[0], acc);
-        acc = fmaf(v.y, p[1], acc);
-        acc = fmaf(v.z, p[2], acc);
-        acc = fmaf(v.w, p[3], acc);
+        acc0 = fmaf(v.x, p[0], acc0);
+        acc1 = fmaf(v.y, p[1], acc1);
+        acc0 = fmaf(v.z, p[2], acc0);
+        acc1 = fmaf(v.w, p[3], acc1);
     }
 }
+
+// Butterfly transpose-reduction of RW per-lane row accumulators over the warp:
+// each round a lane keeps half of its rows and adds the partner's copy of
+// them, so RW - 1 + (5 - log2 RW) additions replace RW full reductions.
+// Afterwards lane l holds the warp total of row (l >> (5 - log2 RW)).
+template <int N, int OFF, class V, int RW>
+__device__ __forceinline__ void butterfly(V (&acc)[RW], int lane) {
+    if constexpr (OFF >= 1) {
+        if constexpr (N > 1) {
+            constexpr int H = N / 2;
+            const bool upper = (lane & OFF) != 0;
+#pragma unroll
+            for (int i = 0; i < H; i++) {
+                const V send = upper ? acc[i] : acc[i + H];
+                const V keep = upper ? acc[i + H] : acc[i];
+                acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+            }
+            butterfly<H, OFF / 2>(acc, lane);
+        } else {
+            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], OFF);
+            butterfly<1, OFF / 2>(acc, lane);
+        }
+    }
+}
+
+template <int RW>
+__host__ __device__ constexpr int log2i() { return RW <= 1 ? 0 : 1 + log2i<RW / 2>(); }
 
 // plain global loads (fallback when A cannot be described by a TMA map)
 template <int DT>
 __device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, long long lda, int row,
                                            int c0, int cols,
                                            const typename Cfg<DT>::V (&p)[Cfg<DT>::VEC],
-                                           typename Cfg<DT>::V &acc) {
+                                           typename Cfg<DT>::V &acc, typename Cfg<DT>::V &acc1) {
     using T = typename Cfg<DT>::T;
     const T *a = A + (long long)row * lda;
 #pragma unroll
@@ -163,7 +190,8 @@ __device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, long lo
         if (c < cols) {
             T e = a[c];
             if constexpr (DT == DT_F64) {
-                acc = fma(e, p[k], acc);
+                if (k & 1) acc1 = fma(e, p[k], acc1);
+                else acc = fma(e, p[k], acc);
             } else if constexpr (DT == DT_BF16) {
                 acc = fmaf(__uint_as_float((uint32_t)e << 16), p[k], acc);
             } else if constexpr (DT == DT_FP8) {
@@ -244,6 +272,13 @@ __device__ __forceinline__ void consumers_sync() {
 }
 
 // ---- the kernel ----------------------------------------------------------------------------
+// Tile t of the (row tile, column tile) sequence belongs to CTA c with
+// start(c) <= t < start(c + 1), start(c) = floor(T c / G).
+__device__ __forceinline__ long long tile_start(long long T, int c, int G) { return T * c / G; }
+__device__ __forceinline__ int tile_owner(long long t, long long T, int G) {
+    return (int)(((long long)G * (t + 1) + T - 1) / T) - 1;
+}
+
 template <int DT, bool TMA>
 __global__ void __launch_bounds__(GEMV_THREADS, 2)
     gemv_kernel(const MatDesc *__restrict__ dA, GemvArgs args) {
@@ -252,6 +287,8 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
     using T = typename C::T;
     using V = typename C::V;
     constexpr int TC = G::TC, TR = G::TR, VEC = C::VEC, RW = C::RW, WC = C::WC;
+    constexpr int LGR = log2i<RW>();
+    static_assert((1 << LGR) == RW && RW <= 32, "RW must be a power of two");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
@@ -259,25 +296,37 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
     uint64_t *empty = full + GEMV_STAGES;
     __shared__ V red[WC][TR];
     __shared__ double dred[GEMV_THREADS / 32];
-    __shared__ int abort_s, last_s;
+    __shared__ int abort_s, last_s, fin_s, ca_s, cb_s;
+    __shared__ double tdot[TR];
 
     const MatDesc &M = *dA;
     const int rows = M.rows, cols = M.cols;
-    if (args.kptr) {   // walk the Krylov basis: x = column k, y = column k + 1
+    if (args.kptr) {   // walk a stored basis: x = column k, y = column k + kyoff
         const long long k = *args.kptr;
         args.x = static_cast<const V *>(args.x) + k * args.kstride;
-        args.y = static_cast<V *>(args.y) + (k + 1) * args.kstride;
+        args.y = static_cast<V *>(args.y) + (k + args.kyoff) * args.kstride;
     }
+    if (args.z_is_x) args.z = args.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int RT = (rows + TR - 1) / TR, CT = (cols + TC - 1) / TC;
     const long long T_all = (long long)RT * CT;
     const int G_ = gridDim.x, cta = blockIdx.x;
-    const long long t0 = T_all * cta / G_, t1 = T_all * (cta + 1) / G_;
+    const long long t0 = tile_start(T_all, cta, G_), t1 = tile_start(T_all, cta + 1, G_);
     const int ntiles = (int)(t1 - t0);
     count_launch(args.st);
 
     if (threadIdx.x == 0) {
         abort_s = 0;
+        // The dot contribution of a row tile shared between CTAs goes to the
+        // slot of the CTA holding its first tile, so that the final sum does
+        // not depend on which CTA finished the tile.  A CTA that is not the
+        // first holder of a shared tile clears its own slot.
+        bool holds_shared_first = false;
+        if (ntiles > 0) {
+            const long long rl = (t1 - 1) / CT;                 // last row tile of this CTA
+            holds_shared_first = (t0 <= rl * CT) && (t1 < (rl + 1) * CT);
+        }
+        if (!holds_shared_first) args.scr->fixdot[cta] = 0.0;
         if (TMA) {
             for (int s = 0; s < GEMV_STAGES; s++) {
                 mbar_init(&full[s], 1);
@@ -294,6 +343,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
         if (TMA && lane == 0 && ntiles > 0) {
             tmap_acquire(&M.tmap);
             int issued = 0;
+            int rt = (int)(t0 / CT), ct = (int)(t0 % CT);
             for (int i = 0; i < ntiles; i++) {
                 const int s = i % GEMV_STAGES;
                 if (i >= GEMV_STAGES) {
@@ -304,11 +354,10 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
                     }
                 }
                 if (*(volatile int *)&abort_s) break;
-                const long long t = t0 + i;
-                const int rt = (int)(t / CT), ct = (int)(t % CT);
                 mbar_arrive_expect_tx(&full[s], G::TILE_BYTES);
                 tma_load_2d(ring + (size_t)s * G::TILE_ELEMS, &M.tmap, ct * TC, rt * TR, &full[s]);
                 issued = i + 1;
+                if (++ct == CT) { ct = 0; ++rt; }
             }
             // never leave with copies in flight: wait for the last stages
             for (int i = issued > GEMV_STAGES ? issued - GEMV_STAGES : 0; i < issued; i++) {
@@ -321,15 +370,15 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
         // ---------------- consumer warps ----------------
         const int wr = warp / WC, wc = warp % WC;
         const int lane_col = wc * 32 * VEC + lane * VEC;   // column offset inside a tile
-        V acc[RW];
+        V acc[RW], acc1[RW];
 #pragma unroll
-        for (int r = 0; r < RW; r++) acc[r] = 0;
+        for (int r = 0; r < RW; r++) acc[r] = acc1[r] = 0;
         const T *Ag = static_cast<const T *>(M.ptr);
         const V *x = static_cast<const V *>(args.x);
+        int rt = ntiles > 0 ? (int)(t0 / CT) : 0, ct = ntiles > 0 ? (int)(t0 % CT) : 0;
+        const int first_rt = rt;
 
         for (int i = 0; i < ntiles; i++) {
-            const long long t = t0 + i;
-            const int rt = (int)(t / CT), ct = (int)(t % CT);
             V p[VEC];
             load_x<DT>(x, ct * TC + lane_col, cols, p);
             if (TMA) {
@@ -345,7 +394,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
                     const T *tile = ring + (size_t)s * G::TILE_ELEMS;
 #pragma unroll
                     for (int r = 0; r < RW; r++)
-                        dot_tile<DT>(tile + (wr * RW + r) * TC + lane_col, p, acc[r]);
+                        dot_tile<DT>(tile + (wr * RW + r) * TC + lane_col, p, acc[r], acc1[r]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
@@ -353,38 +402,86 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
 #pragma unroll
                 for (int r = 0; r < RW; r++) {
                     const int row = rt * TR + wr * RW + r;
-                    if (row < rows) dot_global<DT>(Ag, M.lda, row, ct * TC + lane_col, cols, p, acc[r]);
+                    if (row < rows)
+                        dot_global<DT>(Ag, M.lda, row, ct * TC + lane_col, cols, p, acc[r], acc1[r]);
                 }
             }
             if (ct == CT - 1 || i == ntiles - 1) {
-                // this CTA's share of row tile rt is done: reduce it
+                // this CTA's share of row tile rt is done: reduce it over the warp
 #pragma unroll
                 for (int r = 0; r < RW; r++) {
-                    V v = warp_sum(acc[r]);
-                    if (lane == 0) red[wc][wr * RW + r] = v;
-                    acc[r] = 0;
+                    acc[r] += acc1[r];
+                    acc1[r] = 0;
                 }
-                consumers_sync();
-                const long long rt_first = (long long)rt * CT;
-                const bool complete = (t0 <= rt_first) && (rt_first + CT <= t1);
-                const int slot = (rt == (int)(t0 / CT)) ? 0 : 1;
-                for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
-                    V s = 0;
+                butterfly<RW, 16>(acc, lane);
+                if ((lane & ((32 >> LGR) - 1)) == 0) red[wc][wr * RW + (lane >> (5 - LGR))] = acc[0];
 #pragma unroll
-                    for (int c = 0; c < WC; c++) s += red[c][tr];
-                    const int row = rt * TR + tr;
-                    if (complete) {
+                for (int r = 0; r < RW; r++) acc[r] = 0;
+                consumers_sync();
+                const long long rfirst = (long long)rt * CT;
+                const bool complete = (t0 <= rfirst) && (rfirst + CT <= t1);
+                if (complete) {
+                    for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
+                        V s = 0;
+#pragma unroll
+                        for (int c = 0; c < WC; c++) s += red[c][tr];
+                        const int row = rt * TR + tr;
                         if (row < rows) mydot += epilogue<DT>(args, M, row, s);
-                    } else {
+                    }
+                } else {
+                    // A row tile shared with neighbouring CTAs: publish the
+                    // partial sums; the last of the sharing CTAs to arrive adds
+                    // them in CTA order and finishes those rows.
+                    const int slot = (rt == first_rt) ? 0 : 1;
+                    for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
+                        V s = 0;
+#pragma unroll
+                        for (int c = 0; c < WC; c++) s += red[c][tr];
                         args.scr->fix[((size_t)cta * 2 + slot) * TR + tr] = (double)s;
+                        __threadfence();
+                    }
+                    consumers_sync();
+                    if (threadIdx.x == 0) {
+                        const int ca = tile_owner(rfirst, T_all, G_);
+                        const int cb = tile_owner(rfirst + CT - 1, T_all, G_);
+                        int ncov = 0;
+                        for (int c = ca; c <= cb; c++)
+                            ncov += tile_start(T_all, c, G_) < tile_start(T_all, c + 1, G_);
+                        const unsigned prev = atomicAdd(&args.scr->bticket[ca], 1u);
+                        fin_s = (prev == (unsigned)ncov - 1);
+                        if (fin_s) atomicExch(&args.scr->bticket[ca], 0u);
+                        ca_s = ca;
+                        cb_s = cb;
+                    }
+                    consumers_sync();
+                    if (fin_s) {
+                        __threadfence();
+                        for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
+                            double s = 0.0;
+                            for (int c = ca_s; c <= cb_s; c++) {
+                                const long long a0 = tile_start(T_all, c, G_);
+                                if (tile_start(T_all, c + 1, G_) <= a0) continue;   // empty CTA
+                                const int sl = (rt == (int)(a0 / CT)) ? 0 : 1;
+                                s += __ldcg(&args.scr->fix[((size_t)c * 2 + sl) * TR + tr]);
+                            }
+                            const int row = rt * TR + tr;
+                            tdot[tr] = row < rows ? epilogue<DT>(args, M, row, (V)s) : 0.0;
+                        }
+                        consumers_sync();
+                        if (threadIdx.x == 0) {
+                            double d = 0.0;
+                            for (int tr = 0; tr < TR; tr++) d += tdot[tr];
+                            args.scr->fixdot[ca_s] = d;
+                        }
                     }
                 }
                 consumers_sync();
             }
+            if (++ct == CT) { ct = 0; ++rt; }
         }
     }
 
-    // ---- per-CTA dot, then the last CTA finishes split rows and the reduction ----
+    // ---- per-CTA dot; the last CTA reduces them (all threads, fixed order) ----
     double cd = block_sum(mydot, dred);
     if (threadIdx.x == 0) {
         args.scr->cta_dot[cta] = cd;
@@ -395,34 +492,11 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
     __syncthreads();
     if (!last_s) return;
     __threadfence();
-
-    // split row tiles: one per distinct CTA boundary b_c falling inside a row tile
-    double fixdot = 0.0;
-    auto start = [&](int c) -> long long { return T_all * c / G_; };
-    for (int c = 1 + warp; c < G_; c += GEMV_THREADS / 32) {
-        const long long bc = start(c), bprev = start(c - 1);
-        if (bc <= bprev || bc >= T_all || bc % CT == 0) continue;
-        const int rt = (int)(bc / CT);
-        const long long rfirst = (long long)rt * CT, rend = rfirst + CT;
-        if (bprev > rfirst) continue;   // an earlier boundary already covers this row tile
-        for (int tr = lane; tr < TR; tr += 32) {
-            double s = 0.0;
-            for (int cc = c - 1; cc < G_; cc++) {
-                const long long a0 = start(cc), a1 = start(cc + 1);
-                if (a0 >= rend) break;
-                if (a1 <= a0) continue;          // empty CTA range
-                const int slot = (rt == (int)(a0 / CT)) ? 0 : 1;
-                s += __ldcg(&args.scr->fix[((size_t)cc * 2 + slot) * TR + tr]);
-            }
-            const int row = rt * TR + tr;
-            if (row < rows) fixdot += epilogue<DT>(args, M, row, (V)s);
-        }
-    }
-    double fd = block_sum(fixdot, dred);
+    double part = 0.0;
+    for (int c = threadIdx.x; c < G_; c += GEMV_THREADS)
+        part += __ldcg(&args.scr->cta_dot[c]) + __ldcg(&args.scr->fixdot[c]);
+    const double tot = block_sum(part, dred);
     if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int c = 0; c < G_; c++) tot += __ldcg(&args.scr->cta_dot[c]);
-        tot += fd;
         run_finaliser(args, tot);
         atomicExch(&args.scr->ticket, 0u);
     }

@@ -88,8 +88,10 @@ struct GmresSmall {
 struct GemvScratch {
     unsigned ticket;                                 // last-CTA detection (self-resetting)
     unsigned pad_[31];
+    unsigned bticket[MAX_GRID];                      // per shared row tile (self-resetting)
     double cta_dot[MAX_GRID];                        // per-CTA dot contributions
-    double fix[MAX_GRID * 2 * GEMV_MAX_TR];          // partial row sums of split row tiles
+    double fixdot[MAX_GRID];                         // dot of shared row tiles, by first CTA
+    double fix[MAX_GRID * 2 * GEMV_MAX_TR];          // partial row sums of shared row tiles
 };
 
 // epilogues: what is done with a finished row sum s_i
@@ -112,8 +114,10 @@ enum : int {
 struct GemvArgs {
     const void *x;       // input vector (double for F64, float otherwise)
     void *y;             // output vector (same type as x)
-    const int *kptr;     // if set: x += (*kptr) * kstride, y += (*kptr + 1) * kstride
-    long long kstride;   // (elements) -- lets one graph node walk the Krylov basis
+    const int *kptr;     // if set: x += (*kptr) * kstride, y += (*kptr + kyoff) * kstride
+    long long kstride;   // (elements) -- lets one graph node walk a stored basis
+    int kyoff;           // GMRES: 1 (w = A v_k goes to column k+1); FCG: 0
+    int z_is_x;          // EPI_DOT with z = x (after the k offset)
     const double *b;     // EPI_RESID
     const void *z;       // EPI_DOT
     double *dot_out;     // optional copy of the final dot
@@ -153,6 +157,27 @@ struct Vecs {
     double rtol;
 };
 constexpr int PART_SLOTS = LS_MAX_RESTART + 4;
+
+// ---- mixed-precision vectors (workspace) -------------------------------------------
+struct MixVecs {
+    int n;
+    int mode;            // LS_REFINE_FCG or LS_REFINE_IR
+    double *x, *b, *r, *q;
+    double *P, *W;       // FCG directions and A * directions, column stride ldp
+    long long ldp;
+    double *dvals;       // p_j . A p_j
+    float *rf, *zf, *pf, *qf;
+    double *part;
+    GridBar *bar;
+    State *st;
+    double rtol;
+};
+
+struct MixedKernels {
+    void *mx_init, *in_init, *in_update, *fcg_project, *fcg_update, *mx_check, *ir_start,
+        *ir_update;
+};
+MixedKernels mixed_kernels();
 
 // ---- Krylov launchers (k_krylov.cu) -----------------------------------------------
 struct KrylovKernels {
