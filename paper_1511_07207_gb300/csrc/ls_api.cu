@@ -58,20 +58,6 @@ int ws_reserve(ls_ctx *c, size_t bytes) {
     return LS_OK;
 }
 
-// Carves consecutive 256-byte aligned regions out of a base pointer.
-struct Carver {
-    char *base;
-    size_t off = 0;
-    explicit Carver(void *b) : base(static_cast<char *>(b)) {}
-    template <class T>
-    T *take(size_t count) {
-        off = align_up(off, 256);
-        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
-        off += count * sizeof(T);
-        return p;
-    }
-};
-
 // ---- graphs ---------------------------------------------------------------------
 void GraphCache::reset() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -83,56 +69,6 @@ void GraphCache::reset() {
 
 bool GraphCache::matches(const long long *k) const {
     return exec && memcmp(key, k, sizeof(key)) == 0;
-}
-
-// Adds nodes one after another to a graph.
-struct Chain {
-    cudaGraph_t g;
-    cudaGraphNode_t last = nullptr;
-    cudaError_t err = cudaSuccess;
-    explicit Chain(cudaGraph_t gr) : g(gr) {}
-
-    void kernel(void *func, int grid, int block, size_t smem, void **args, bool coop) {
-        if (err != cudaSuccess) return;
-        cudaKernelNodeParams p{};
-        p.func = func;
-        p.gridDim = dim3(grid);
-        p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)smem;
-        p.kernelParams = args;
-        cudaGraphNode_t node;
-        err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &p);
-        if (err != cudaSuccess) return;
-        if (coop) {
-            cudaLaunchAttributeValue v{};
-            v.cooperative = 1;
-            err = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &v);
-        }
-        last = node;
-    }
-    // Appends a while-node on handle h; returns its body graph.
-    cudaGraph_t loop(cudaGraphConditionalHandle h) {
-        if (err != cudaSuccess) return nullptr;
-        cudaGraphNodeParams np{};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        cudaGraphNode_t node;
-        err = cudaGraphAddNode(&node, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np);
-        if (err != cudaSuccess) return nullptr;
-        last = node;
-        return np.conditional.phGraph_out[0];
-    }
-};
-
-void gemv_node(Chain &ch, const GemvLaunch &L, const MatDesc *dA, const GemvArgs &a) {
-    // kernelParams must point at storage that outlives the call only until the
-    // node is added (the values are copied), so locals are fine.
-    const MatDesc *pA = dA;
-    GemvArgs aa = a;
-    void *args[] = {(void *)&pA, (void *)&aa};
-    ch.kernel(L.func, L.grid, L.block, L.smem, args, false);
 }
 
 int finish_graph(ls_ctx *c, GraphCache &gc, cudaGraph_t g, const long long *key) {
@@ -488,7 +424,8 @@ static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int 
     Chain inner(body_i);
     {
         GemvArgs a{};
-        a.x = v.V; a.y = v.V; a.kptr = &v.st->k; a.kstride = v.ldv; a.st = v.st; a.scr = c->scr;
+        a.x = v.V; a.y = v.V; a.kptr = &v.st->k; a.kstride = v.ldv; a.kyoff = 1;
+        a.st = v.st; a.scr = c->scr;
         a.epi = EPI_NRM; a.fin = FIN_WNORM0;
         gemv_node(inner, L, dA, a);
         Vecs vv = v;
