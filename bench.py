@@ -115,10 +115,15 @@ class ClockSampler:
 # profile evidence for the roofline's traffic field
 # ---------------------------------------------------------------------------
 def gemv_source_hash():
+    """Hash of the GEMV kernel source: k_gemv.cu, the device helpers and the
+    GEMV_* constants of ls_internal.h."""
     h = hashlib.sha256()
-    for f in ("k_gemv.cu", "ls_device.cuh", "ls_internal.h"):
-        with open(os.path.join(ROOT, "paper_1511_07207_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1511_07207_gb300", "csrc")
+    for f in ("k_gemv.cu", "ls_device.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "ls_internal.h")) as fh:
+        h.update("".join(l for l in fh if "GEMV_" in l).encode())
     return h.hexdigest()[:16]
 
 
@@ -299,6 +304,11 @@ def run_native(args):
                "h2d_bytes_per_step": int(2 * (8 * N * N + 8 * N)),
                "d2h_bytes_per_step": int(2 * 8 * N)}
 
+    # mixed vs FP64: n = 32768 SPD system (cond ~ 4e3), time to 1e-10 and GEMV GB/s
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed_compare(B, ctx, dev, stream, args)
+
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -332,6 +342,7 @@ def run_native(args):
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
                          "peak_source": peak_src},
             "roofline": roofline,
+            "mixed_vs_fp64": mixed,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -341,6 +352,61 @@ def run_native(args):
     B.ls_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_mixed_compare(B, ctx, dev, stream, args, n=32768):
+    """Plain FP64 CG vs BF16 / FP8 storage + FP64 flexible CG on one SPD
+    system A = G G^T / n + 1e-3 I (n = 32768, A is 8 GiB in FP64), and the
+    matrix-vector product of each storage format on that A."""
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    A = inputs.spd_matrix(n, SIGMA, seed=2, device=dev)
+    xs = torch.from_numpy(inputs.solution(n, seed=2)).to(dev)
+    b = A @ xs
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    out = {"n": n, "workload": "SPD GG^T/n+1e-3I (seed 2), x*~U[-1,1], b=Ax*, x0=0, rtol 1e-10",
+           "inner_iters": 25}
+    runs = {"fp64": B.make_opts(rtol=RTOL),
+            "bf16_fcg": B.make_opts(rtol=RTOL, precision=B.LS_BF16_IR),
+            "fp8_fcg": B.make_opts(rtol=RTOL, precision=B.LS_FP8_IR, max_iter=60)}
+    reps = max(1, min(args.steps, 3))
+    for name, o in runs.items():
+        st, info = B.ls_cg_solve(ctx, A, b, x, o)            # warm-up (graph build)
+        t = []
+        for _ in range(reps):
+            x.zero_()
+            st, info = B.ls_cg_solve(ctx, A, b, x, o)
+            t.append(info["time_ms"])
+        err = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+        out[name] = {"status": B.ls_strerror(st), "time_to_tol_ms": round(min(t), 3),
+                     "iters": info["iters"], "outer_iters": info["outer_iters"],
+                     "true_rel_res": info["true_rel_res"], "rel_err_vs_xstar": err,
+                     "A_bytes_streamed": info["bytes_moved"]}
+    if out["fp64"]["status"] == "converged" and out["bf16_fcg"]["status"] == "converged":
+        out["speedup_bf16_vs_fp64"] = round(out["fp64"]["time_to_tol_ms"] /
+                                            out["bf16_fcg"]["time_to_tol_ms"], 3)
+    # GEMV per storage format on this A
+    peaks, src = load_peaks()
+    gb = {}
+    xv = torch.randn(n, dtype=torch.float64, device=dev)
+    yv = torch.empty(n, dtype=torch.float64, device=dev)
+    st, ms = B.ls_gemv_timed(ctx, B.LS_F64, A, xv, yv, 10)
+    gb["f64"] = round((8.0 * n * n + 16.0 * n) / ms / 1e6, 1)
+    xf = xv.float()
+    yf = torch.empty(n, dtype=torch.float32, device=dev)
+    for name, dt, tdt, esz in (("bf16", B.LS_BF16_IR, torch.int16, 2),
+                               ("fp8", B.LS_FP8_IR, torch.uint8, 1)):
+        Q = torch.empty((n, n), dtype=tdt, device=dev)
+        sc = torch.empty(n, dtype=torch.float32, device=dev) if dt == B.LS_FP8_IR else None
+        B.ls_quantize(ctx, dt, A, Q, sc)
+        st, ms = B.ls_gemv_timed(ctx, dt, Q, xf, yf, 20, scale=sc)
+        gb[name] = round((esz * n * n + 8.0 * n + (4.0 * n if sc is not None else 0)) / ms / 1e6, 1)
+        del Q
+    out["gemv_GBs"] = gb
+    out["gemv_hbm_frac"] = {k: round(v / peaks["hbm_gbs"], 4) for k, v in gb.items()}
+    del A
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -440,7 +506,9 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-cg-sample", type=int, default=60)
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
+    ap.add_argument("--cpu-cg-sample", type=int, default=600)
     ap.add_argument("--kernel", choices=["gemv"], default=None,
                     help="kernel-only timing (small cases for ncu captures)")
     ap.add_argument("--n", type=int, default=8192)
