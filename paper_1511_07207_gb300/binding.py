@@ -141,15 +141,17 @@ def lead_dim(a) -> int:
 
 
 def col_lead_dim(a) -> int:
-    """Leading dimension of a column-major n x k block (column j at a + j*ld)."""
+    """Leading dimension of a column-major n x k block (column j at a + j*ld).
+    A single column has no meaningful column stride (frameworks may report
+    any value for a size-1 dimension), so its leading dimension is n."""
     if _is_torch(a):
-        if a.dim() == 1:
+        if a.dim() == 1 or a.shape[1] == 1:
             return a.shape[0]
-        assert a.stride(0) == 1
+        assert a.stride(0) == 1, "column-major with unit row stride required"
         return a.stride(1)
-    if a.ndim == 1:
+    if a.ndim == 1 or a.shape[1] == 1:
         return a.shape[0]
-    assert a.strides[0] == a.itemsize
+    assert a.strides[0] == a.itemsize, "column-major with unit row stride required"
     return a.strides[1] // a.itemsize
 
 

@@ -1,0 +1,598 @@
+// k_engine.cu -- kernels of the batched / served solve engine (ls_engine.h).
+//
+// Per slot (one dense system, s right-hand sides solved column by column):
+//   refinement (FP64): R = B - A X; stop when every ||R_j|| <= rtol ||B_j||;
+//   inner solve (FP32 on the FP32 copy of A) of A z = R_j / ||R_j||:
+//     SPD systems: conjugate gradient (paper: CG paragraph), the columns sharing
+//       one block product Q = Ahat P per step;
+//     other systems: one GMRES(m) cycle (paper: GMRES pseudocode, Arnoldi with
+//       classical Gram-Schmidt; Givens least squares), one block product
+//       W = Ahat V_k per Arnoldi step;
+//   correction: X += ||R_j|| z_j.
+// All cross-row sums are reduced per slot in a fixed task order.
+#include <cuda_runtime.h>
+
+#include "ls_device.cuh"
+#include "ls_engine.h"
+#include "ls_internal.h"
+
+namespace lsi {
+
+constexpr int RED_T = 64;
+constexpr int P32_T = 256;
+constexpr int P64_T = 256;
+constexpr int VEC_T = 256;
+constexpr int KC32 = 32;     // k chunk of the FP32 product
+constexpr int AS32 = 34;     // padded row stride of the A tile (floats)
+constexpr int KC64 = 64;     // k chunk of the FP64 residual
+
+__device__ __forceinline__ void eng_count(const EngineDev &E) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(E.launches, 1ull);
+}
+
+// ============================================================================
+// eng_red: one block per slot; thread j < 32 owns column j
+// ============================================================================
+__global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cudaGraphConditionalHandle h) {
+    const EngineDev E = *Ep;
+    __shared__ int all_stop, newphase_s;
+    const int sl = blockIdx.x < E.nslots ? blockIdx.x : 0;
+    const int j = threadIdx.x;
+    eng_count(E);
+    const SlotDesc &D = E.desc[sl];
+    SlotState &S = E.st[sl];
+    const int ph = blockIdx.x < E.nslots ? S.phase : PH_FREE;
+    const bool colv = j < D.s;
+    int newphase = ph;
+    if (threadIdx.x == 0) all_stop = 1;
+    __syncthreads();
+
+    if (ph != PH_FREE && ph != PH_DONE && colv) {
+        if (ph == PH_START) {
+            double b2 = 0.0;
+            for (int t = D.tv; t < D.tv + D.nv; t++) b2 += E.partv[(size_t)t * 32 + j];
+            S.bnorm[j] = sqrt(b2);
+            S.rn[j] = sqrt(b2);
+            S.conv[j] = (b2 == 0.0);
+            if (!isfinite(b2)) atomicOr(&S.err, ERRB_NAN);
+            if (!S.conv[j]) atomicAnd(&all_stop, 0);
+        } else if (ph == PH_RESID) {
+            double r2 = 0.0;
+            for (int t = D.t64; t < D.t64 + D.n64; t++) r2 += E.part64[(size_t)t * 32 + j];
+            S.rn[j] = sqrt(r2);
+            if (!isfinite(r2)) atomicOr(&S.err, ERRB_NAN);
+            S.conv[j] = sqrt(r2) <= D.rtol * S.bnorm[j];
+            if (!S.conv[j]) atomicAnd(&all_stop, 0);
+        } else if (ph == PH_INIT) {
+            double f2 = 0.0;
+            for (int t = D.tv; t < D.tv + D.nv; t++) f2 += E.partv[(size_t)t * 32 + j];
+            S.colstop[j] = S.conv[j] || !(f2 > 0.0);
+            S.rho[j] = f2;
+            S.rho0[j] = f2;
+            S.beta[j] = 0.0;
+            S.gbeta[j] = sqrt(f2);
+            S.hnorm[j] = sqrt(f2);
+            E.gm[sl].g[j][0] = sqrt(f2);
+        } else if (ph == PH_CG) {
+            if (!S.colstop[j]) {
+                double pq = 0.0, rr = 0.0;
+                for (int t = D.t32; t < D.t32 + D.n32; t++)
+                    pq += E.part32[((size_t)t * E_PS + 0) * 32 + j];
+                for (int t = D.tv; t < D.tv + D.nv; t++) rr += E.partv[(size_t)t * 32 + j];
+                if (!(pq > 0.0) || !isfinite(rr)) {
+                    S.colstop[j] = 1;              // breakdown: keep the iterate
+                } else if (rr <= (double)D.inner_tol * D.inner_tol * S.rho0[j]) {
+                    S.colstop[j] = 1;
+                } else {
+                    S.beta[j] = rr / S.rho[j];
+                    S.rho[j] = rr;
+                }
+            }
+            if (!S.colstop[j]) atomicAnd(&all_stop, 0);
+        } else if (ph == PH_GM) {
+            const int k = S.it;                    // Arnoldi step just completed
+            if (!S.colstop[j]) {
+                SlotGm &G = E.gm[sl];
+                double *Hk = G.H[j] + (size_t)k * (E_MAXM + 1);
+                for (int i = 0; i <= k; i++) {
+                    double hs = 0.0;
+                    for (int t = D.t32; t < D.t32 + D.n32; t++)
+                        hs += E.part32[((size_t)t * E_PS + i) * 32 + j];
+                    Hk[i] = hs;
+                }
+                double w2 = 0.0;
+                for (int t = D.tv; t < D.tv + D.nv; t++) w2 += E.partv[(size_t)t * 32 + j];
+                const double hk1 = sqrt(w2);
+                Hk[k + 1] = hk1;
+                for (int i = 0; i < k; i++) {      // earlier rotations
+                    const double a = Hk[i], c = Hk[i + 1];
+                    Hk[i] = G.cs[j][i] * a + G.sn[j][i] * c;
+                    Hk[i + 1] = -G.sn[j][i] * a + G.cs[j][i] * c;
+                }
+                const double den = hypot(Hk[k], Hk[k + 1]);
+                if (!(den > 0.0) || !isfinite(den)) {
+                    S.colstop[j] = 1;              // breakdown: solve with the first k steps
+                    S.hnorm[j] = 1.0;
+                } else {
+                    const double c = Hk[k] / den, s = Hk[k + 1] / den;
+                    G.cs[j][k] = c;
+                    G.sn[j][k] = s;
+                    Hk[k] = den;
+                    Hk[k + 1] = 0.0;
+                    G.g[j][k + 1] = -s * G.g[j][k];
+                    G.g[j][k] = c * G.g[j][k];
+                    S.alpha[j] = k + 1;            // steps taken by this column
+                    const double est = fabs(G.g[j][k + 1]);
+                    if (est <= (double)D.inner_tol * S.gbeta[j] || !(hk1 > 1e-14 * den))
+                        S.colstop[j] = 1;
+                    S.hnorm[j] = hk1 > 0.0 ? hk1 : 1.0;
+                }
+            }
+            if (!S.colstop[j]) atomicAnd(&all_stop, 0);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && ph != PH_FREE && ph != PH_DONE) {
+        switch (ph) {
+            case PH_ADMIT:
+                newphase = PH_START;
+                break;
+            case PH_START:
+                newphase = (all_stop || S.err) ? PH_DONE : PH_INIT;
+                if (newphase == PH_DONE) S.status = S.err ? LS_ERR_NAN : LS_OK;
+                break;
+            case PH_RESID:
+                S.outer += 1;
+                if (S.err) { newphase = PH_DONE; S.status = LS_ERR_NAN; }
+                else if (all_stop) { newphase = PH_DONE; S.status = LS_OK; }
+                else if (S.outer >= D.max_outer) { newphase = PH_DONE; S.status = LS_NOT_CONVERGED; }
+                else newphase = PH_INIT;
+                break;
+            case PH_INIT:
+                S.it = 0;
+                newphase = D.method == LS_METHOD_CG ? PH_CG : PH_GM;
+                break;
+            case PH_CG:
+                S.it += 1;
+                S.inner_total += 1;
+                newphase = (all_stop || S.it >= D.inner_iters) ? PH_UPDATE : PH_CG;
+                break;
+            case PH_GM:
+                S.it += 1;
+                S.inner_total += 1;
+                newphase = (all_stop || S.it >= D.m) ? PH_UPDATE : PH_GM;
+                break;
+            case PH_UPDATE:
+                newphase = PH_RESID;
+                break;
+        }
+        S.ticks += 1;
+        if (S.ticks > 1000000 && newphase != PH_DONE) {   // never loop forever
+            newphase = PH_DONE;
+            S.status = LS_NOT_CONVERGED;
+        }
+        newphase_s = newphase;
+    }
+    __syncthreads();
+    // GMRES cycle ends: back-solve R y = g per column (thread j)
+    if (ph == PH_GM && threadIdx.x < 32) {
+        if (newphase_s == PH_UPDATE && colv) {
+            const SlotGm &G = E.gm[sl];
+            const int kj = (int)S.alpha[j];       // steps with a valid rotation
+            for (int i = kj - 1; i >= 0; i--) {
+                double sacc = G.g[j][i];
+                for (int q = i + 1; q < kj; q++) sacc -= G.H[j][(size_t)q * (E_MAXM + 1) + i] * S.yv[j][q];
+                S.yv[j][i] = sacc / G.H[j][(size_t)i * (E_MAXM + 1) + i];
+            }
+            for (int i = kj; i < E_MAXM; i++) S.yv[j][i] = 0.0;
+        }
+    }
+    if (ph == PH_INIT && threadIdx.x < 32 && colv) S.alpha[j] = 0.0;   // GMRES step counters
+    if (threadIdx.x == 0) {
+        int act = 0;
+        if (ph != PH_FREE && ph != PH_DONE) {
+            S.phase = newphase_s;
+            act = (newphase_s != PH_DONE);
+        }
+        if (act) atomicAdd(&E.active[0], 1);
+        __threadfence();
+        const int tk = atomicAdd(&E.active[1], 1);
+        if (tk == (int)gridDim.x - 1) {       // last block: loop control
+            __threadfence();
+            const int total = atomicAdd(&E.active[0], 0);
+            const int ticks = E.active[3] + 1;
+            E.active[3] = ticks;
+            cudaGraphSetConditional(h, total > 0 && ticks < E.tick_limit);
+            E.active[0] = 0;
+            E.active[1] = 0;
+            E.active[2] = total;
+        }
+    }
+}
+
+// ============================================================================
+// eng_prod32: FP32 block product of one 128-row task, CG or GMRES phase
+// ============================================================================
+__global__ void __launch_bounds__(P32_T) eng_prod32_kernel(const EngineDev *Ep) {
+    const EngineDev E = *Ep;
+    extern __shared__ __align__(16) unsigned char esm[];
+    float *As = reinterpret_cast<float *>(esm);                         // [128][AS32]
+    float *Ps = As + E_RB32 * AS32;                                     // [KC32][32]
+    double *Red = reinterpret_cast<double *>(Ps + KC32 * 32);           // [128][33]
+    __shared__ float colscale[32];
+    eng_count(E);
+    const int tid = threadIdx.x;
+    const int row = tid >> 1, kh = tid & 1;
+    for (int t = blockIdx.x; t < E.n32; t += gridDim.x) {
+        const Task T = E.t32[t];
+        const SlotDesc &D = E.desc[T.slot];
+        const SlotState &S = E.st[T.slot];
+        const int ph = S.phase;
+        if (ph != PH_CG && ph != PH_GM) continue;
+        const int n = D.n, sp = D.sp, it = S.it;
+        const long long nsp = (long long)n * sp;
+        const int r0 = T.r0, r1 = T.r1;
+        // operand source / destination and per-column scale
+        const float *src, *src2 = nullptr;
+        float *dst, *out;
+        if (ph == PH_CG) {
+            src = D.Rf;                                         // P = Rf + beta P'
+            src2 = it > 0 ? D.P + ((it + 1) & 1) * nsp : nullptr;
+            dst = D.P + (it & 1) * nsp;
+            out = D.Q;
+        } else {
+            src = D.W + (it & 1) * nsp;                         // V_k = W / h
+            dst = D.V + (long long)it * nsp;
+            out = D.W + ((it + 1) & 1) * nsp;
+        }
+        if (tid < 32) {
+            float sc = 0.0f;
+            if (tid < D.s && !S.colstop[tid])
+                sc = ph == PH_CG ? (float)S.beta[tid] : (float)(1.0 / S.hnorm[tid]);
+            colscale[tid] = sc;
+        }
+        __syncthreads();
+        float acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) acc[c] = 0.0f;
+        for (int k0 = 0; k0 < n; k0 += KC32) {
+            // A tile: rows r0..r0+127, cols k0..k0+31 (coalesced along k)
+            for (int e = tid; e < E_RB32 * KC32; e += P32_T) {
+                const int rr = e / KC32, kk = e % KC32;
+                const int gr = r0 + rr, gk = k0 + kk;
+                As[rr * AS32 + kk] = (gr < r1 && gk < n) ? D.A32[(long long)gr * D.ld32 + gk] : 0.0f;
+            }
+            // operand tile: rows k0..k0+31, all sp columns, transformed on the fly
+            for (int e = tid; e < KC32 * sp; e += P32_T) {
+                const int kk = e / sp, c = e % sp;
+                const int gk = k0 + kk;
+                float v = 0.0f;
+                if (gk < n && c < D.s) {
+                    const long long o = (long long)gk * sp + c;
+                    const bool stopped = S.colstop[c];
+                    if (ph == PH_CG) {
+                        v = stopped ? 0.0f : (src2 ? fmaf(colscale[c], src2[o], src[o]) : src[o]);
+                    } else {
+                        v = src[o] * colscale[c];
+                    }
+                    if (gk >= r0 && gk < r1) dst[o] = v;        // this task owns row gk
+                }
+                Ps[kk * 32 + c] = v;
+            }
+            __syncthreads();
+            if (row < r1 - r0) {
+#pragma unroll 4
+                for (int kk = kh; kk < KC32; kk += 2) {
+                    const float a = As[row * AS32 + kk];
+                    const float4 *p4 = reinterpret_cast<const float4 *>(Ps + kk * 32);
+#pragma unroll
+                    for (int c4 = 0; c4 < 8; c4++) {
+                        if (c4 * 4 < sp) {
+                            const float4 pv = p4[c4];
+                            acc[4 * c4 + 0] = fmaf(a, pv.x, acc[4 * c4 + 0]);
+                            acc[4 * c4 + 1] = fmaf(a, pv.y, acc[4 * c4 + 1]);
+                            acc[4 * c4 + 2] = fmaf(a, pv.z, acc[4 * c4 + 2]);
+                            acc[4 * c4 + 3] = fmaf(a, pv.w, acc[4 * c4 + 3]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int c = 0; c < 32; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+        const int nrow = r1 - r0;
+        if (kh == 0 && row < nrow) {
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+                if (c < sp) out[(long long)(r0 + row) * sp + c] = acc[c];
+        }
+        __syncthreads();
+        // partial dots over this task's rows: CG p.q; GMRES v_i.w for i <= it
+        const int nd = ph == PH_CG ? 1 : it + 1;
+        for (int i = 0; i < nd; i++) {
+            const float *vi = ph == PH_CG ? dst : D.V + (long long)i * nsp;
+            if (kh == 0) {
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    double v = 0.0;
+                    if (row < nrow && c < sp) v = (double)vi[(long long)(r0 + row) * sp + c] * (double)acc[c];
+                    Red[row * 33 + c] = v;
+                }
+            }
+            __syncthreads();
+            if (tid < 32) {
+                double sacc = 0.0;
+                for (int rr = 0; rr < nrow; rr++) sacc += Red[rr * 33 + tid];
+                E.part32[((size_t)t * E_PS + i) * 32 + tid] = sacc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ============================================================================
+// eng_prod64: FP64 refinement residual R = B - A X of one 16-row task
+// ============================================================================
+__global__ void __launch_bounds__(P64_T) eng_prod64_kernel(const EngineDev *Ep) {
+    const EngineDev E = *Ep;
+    extern __shared__ __align__(16) unsigned char esm[];
+    double *As = reinterpret_cast<double *>(esm);                       // [16][KC64 + 1]
+    double *Xs = As + E_RB64 * (KC64 + 1);                              // [KC64][33]
+    __shared__ double red[E_RB64][33];
+    eng_count(E);
+    const int tid = threadIdx.x;
+    const int row = tid >> 4, kl = tid & 15;
+    for (int t = blockIdx.x; t < E.n64; t += gridDim.x) {
+        const Task T = E.t64[t];
+        const SlotDesc &D = E.desc[T.slot];
+        const SlotState &S = E.st[T.slot];
+        if (S.phase != PH_RESID) continue;
+        const int n = D.n, sp = D.sp;
+        const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
+        const int xs = sp + 1;                                          // odd stride: no conflicts
+        double acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) acc[c] = 0.0;
+        for (int k0 = 0; k0 < n; k0 += KC64) {
+            for (int e = tid; e < E_RB64 * KC64; e += P64_T) {
+                const int rr = e / KC64, kk = e % KC64;
+                const int gr = r0 + rr, gk = k0 + kk;
+                As[rr * (KC64 + 1) + kk] = (gr < r1 && gk < n) ? D.A64[(long long)gr * D.lda64 + gk] : 0.0;
+            }
+            for (int e = tid; e < KC64 * sp; e += P64_T) {
+                const int kk = e / sp, c = e % sp;
+                const int gk = k0 + kk;
+                Xs[kk * xs + c] = gk < n ? D.X[(long long)gk * sp + c] : 0.0;
+            }
+            __syncthreads();
+            if (row < nrow) {
+#pragma unroll
+                for (int i = 0; i < KC64 / 16; i++) {
+                    const int kk = kl + 16 * i;
+                    const double a = As[row * (KC64 + 1) + kk];
+                    const double *xr = Xs + kk * xs;
+#pragma unroll
+                    for (int c = 0; c < 32; c++)
+                        if (c < sp) acc[c] = fma(a, xr[c], acc[c]);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        if (kl == 0) {
+#pragma unroll
+            for (int c = 0; c < 32; c++) {
+                double v = 0.0;
+                if (row < nrow && c < sp) {
+                    const long long o = (long long)(r0 + row) * sp + c;
+                    const double rv = D.B[o] - acc[c];
+                    D.R[o] = rv;
+                    v = rv * rv;
+                }
+                red[row][c] = v;
+            }
+        }
+        __syncthreads();
+        if (tid < 32) {
+            double sacc = 0.0;
+            for (int rr = 0; rr < nrow; rr++) sacc += red[rr][tid];
+            E.part64[(size_t)t * 32 + tid] = sacc;
+        }
+        __syncthreads();
+    }
+}
+
+// ============================================================================
+// eng_vec: vector updates of one 256-row task
+// ============================================================================
+__global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
+    const EngineDev E = *Ep;
+    __shared__ double wsum[VEC_T / 32][32];
+    __shared__ double hsm[E_MAXM + 1][32];
+    __shared__ double colv_s[32];
+    eng_count(E);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = blockIdx.x; t < E.nv; t += gridDim.x) {
+        const Task T = E.tv[t];
+        const SlotDesc &D = E.desc[T.slot];
+        const SlotState &S = E.st[T.slot];
+        const int ph = S.phase;
+        if (ph != PH_START && ph != PH_INIT && ph != PH_CG && ph != PH_GM && ph != PH_UPDATE) continue;
+        const int n = D.n, s = D.s, sp = D.sp, it = S.it;
+        const long long nsp = (long long)n * sp;
+        const int i = T.r0 + tid;
+        const bool mine = i < T.r1;
+        // per-column scalars needed by this phase
+        if (tid < 32) {
+            double cv = 0.0;
+            if (tid < s) {
+                if (ph == PH_CG) {
+                    double pq = 0.0;
+                    for (int u = D.t32; u < D.t32 + D.n32; u++)
+                        pq += E.part32[((size_t)u * E_PS + 0) * 32 + tid];
+                    cv = (S.colstop[tid] || !(pq > 0.0)) ? 0.0 : S.rho[tid] / pq;
+                } else if (ph == PH_INIT || ph == PH_UPDATE) {
+                    cv = S.rn[tid];
+                }
+            }
+            colv_s[tid] = cv;
+        }
+        if (ph == PH_GM) {
+            for (int e = tid; e < (it + 1) * 32; e += VEC_T) {
+                const int ii = e / 32, c = e % 32;
+                double hs = 0.0;
+                if (c < s && !S.colstop[c])
+                    for (int u = D.t32; u < D.t32 + D.n32; u++)
+                        hs += E.part32[((size_t)u * E_PS + ii) * 32 + c];
+                hsm[ii][c] = hs;
+            }
+        }
+        __syncthreads();
+        const long long ro = (long long)i * sp;
+        double part[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) part[c] = 0.0;
+        if (mine) {
+            if (ph == PH_START) {
+                const double *a = D.A64 + (long long)i * D.lda64;
+                float *a32 = D.A32 + (long long)i * D.ld32;
+                for (int k = 0; k < n; k++) a32[k] = __double2float_rn(a[k]);
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    if (c < sp) {
+                        const double b = D.B[ro + c];
+                        D.X[ro + c] = 0.0;
+                        D.R[ro + c] = b;
+                        part[c] = b * b;
+                    }
+                }
+            } else if (ph == PH_INIT) {
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    if (c < sp) {
+                        float f = 0.0f;
+                        if (c < s && !S.conv[c]) f = (float)(D.R[ro + c] / colv_s[c]);
+                        D.Rf[ro + c] = f;
+                        D.Z[ro + c] = 0.0f;
+                        if (D.method != LS_METHOD_CG) D.W[ro + c] = f;     // W buffer 0
+                        part[c] = (double)f * (double)f;
+                    }
+                }
+            } else if (ph == PH_CG) {
+                const float *p = D.P + (it & 1) * nsp;
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    if (c < sp) {
+                        const float al = (float)colv_s[c];
+                        D.Z[ro + c] = fmaf(al, p[ro + c], D.Z[ro + c]);
+                        const float rv = fmaf(-al, D.Q[ro + c], D.Rf[ro + c]);
+                        D.Rf[ro + c] = rv;
+                        part[c] = (double)rv * (double)rv;
+                    }
+                }
+            } else if (ph == PH_GM) {
+                float *w = D.W + ((it + 1) & 1) * nsp;
+#pragma unroll
+                for (int c = 0; c < 32; c++) {
+                    if (c < sp) {
+                        double wv = w[ro + c];
+                        for (int q = 0; q <= it; q++)
+                            wv -= hsm[q][c] * (double)D.V[(long long)q * nsp + ro + c];
+                        const float wf = (float)wv;
+                        w[ro + c] = wf;
+                        part[c] = (double)wf * (double)wf;
+                    }
+                }
+            } else if (ph == PH_UPDATE) {
+                for (int c = 0; c < s; c++) {
+                    if (S.conv[c]) continue;
+                    double d;
+                    if (D.method == LS_METHOD_CG) {
+                        d = (double)D.Z[ro + c];
+                    } else {
+                        d = 0.0;
+                        const int kj = (int)S.alpha[c];
+                        for (int q = 0; q < kj; q++) d += S.yv[c][q] * (double)D.V[(long long)q * nsp + ro + c];
+                    }
+                    D.X[ro + c] += colv_s[c] * d;
+                }
+            }
+        }
+        // partial column sums over this task's rows (fixed order)
+        if (ph != PH_UPDATE) {
+#pragma unroll
+            for (int c = 0; c < 32; c++) {
+                const double v = warp_sum(part[c]);
+                if (lane == 0) wsum[warp][c] = v;
+            }
+            __syncthreads();
+            if (tid < 32) {
+                double sacc = 0.0;
+                for (int w = 0; w < VEC_T / 32; w++) sacc += wsum[w][tid];
+                E.partv[(size_t)t * 32 + tid] = sacc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ============================================================================
+// admission / completion helpers
+// ============================================================================
+// B (column-major, ldb) -> the slot's row-major n x sp block (zero padding).
+__global__ void eng_admit_kernel(const EngineDev *Ep, const double *const *Bsrc, const long long *ldb,
+                                 int first, int count) {
+    const EngineDev E = *Ep;
+    for (int q = blockIdx.y; q < count; q += gridDim.y) {
+        const int sl = first + q;
+        const SlotDesc &D = E.desc[sl];
+        const double *b = Bsrc[q];
+        const long long total = (long long)D.n * D.sp;
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+             e += (long long)gridDim.x * blockDim.x) {
+            const int i = (int)(e / D.sp), c = (int)(e % D.sp);
+            D.B[e] = c < D.s ? b[(long long)c * ldb[q] + i] : 0.0;
+        }
+    }
+}
+
+// X (row-major) -> column-major destination (ldx).
+__global__ void eng_finish_kernel(const EngineDev *Ep, double *const *Xdst, const long long *ldx, int first,
+                                  int count) {
+    const EngineDev E = *Ep;
+    for (int q = blockIdx.y; q < count; q += gridDim.y) {
+        const int sl = first + q;
+        const SlotDesc &D = E.desc[sl];
+        double *x = Xdst[q];
+        const long long total = (long long)D.n * D.s;
+        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+             e += (long long)gridDim.x * blockDim.x) {
+            const int c = (int)(e / D.n), i = (int)(e % D.n);
+            x[(long long)c * ldx[q] + i] = D.X[(long long)i * D.sp + c];
+        }
+    }
+}
+
+EngineKernels engine_kernels() {
+    EngineKernels K{};
+    K.red = reinterpret_cast<void *>(&eng_red_kernel);
+    K.prod32 = reinterpret_cast<void *>(&eng_prod32_kernel);
+    K.prod64 = reinterpret_cast<void *>(&eng_prod64_kernel);
+    K.vec = reinterpret_cast<void *>(&eng_vec_kernel);
+    K.admit = reinterpret_cast<void *>(&eng_admit_kernel);
+    K.finish = reinterpret_cast<void *>(&eng_finish_kernel);
+    K.red_threads = RED_T;
+    K.prod32_threads = P32_T;
+    K.prod64_threads = P64_T;
+    K.vec_threads = VEC_T;
+    K.prod32_smem = (size_t)E_RB32 * AS32 * 4 + KC32 * 32 * 4 + (size_t)E_RB32 * 33 * 8;
+    K.prod64_smem = (size_t)E_RB64 * (KC64 + 1) * 8 + (size_t)KC64 * 33 * 8;
+    return K;
+}
+
+}  // namespace lsi

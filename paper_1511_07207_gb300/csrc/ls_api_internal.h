@@ -17,7 +17,7 @@ struct GraphCache {
     bool matches(const long long *k) const;
 };
 
-struct BatchResources;   // ls_batch.cu
+class Engine;   // ls_engine_host.h
 
 }  // namespace lsi
 
@@ -45,7 +45,7 @@ struct ls_ctx {
     lsi::GraphCache graph_cg, graph_gm, graph_mx;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches_total = 0;
-    lsi::BatchResources *batch = nullptr;
+    lsi::Engine *batch = nullptr;
 };
 
 namespace lsi {

@@ -1,0 +1,462 @@
+// ls_engine.cu -- host side of the batched / served solve engine (ls_engine.h)
+// and the ls_batch_solve entry point.
+//
+// The engine owns the slot and task tables in device memory and one CUDA
+// graph: while (any slot active and ticks < limit) { eng_red; eng_prod32;
+// eng_prod64; eng_vec }.  The kernels read the table sizes from a device
+// block, so the same graph serves any set of resident slots; the batched
+// solver runs it to completion, the server (ls_server.cpp) runs it a few
+// ticks at a time between admissions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <vector>
+
+#include "ls_api_internal.h"
+#include "ls_engine.h"
+#include "ls_engine_host.h"
+
+namespace lsi {
+
+// ---- per-slot state initialisation and result collection ---------------------
+__global__ void eng_init_state_kernel(SlotState *st, int first, int count) {
+    for (int q = blockIdx.x; q < count; q += gridDim.x) {
+        SlotState &S = st[first + q];
+        int *w = reinterpret_cast<int *>(&S);
+        for (size_t e = threadIdx.x; e < sizeof(SlotState) / sizeof(int); e += blockDim.x) w[e] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) S.phase = PH_ADMIT;
+    }
+}
+
+__global__ void eng_collect_kernel(const SlotDesc *desc, const SlotState *st, SlotResult *out,
+                                   int first, int count) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
+        const SlotState &S = st[first + q];
+        const SlotDesc &D = desc[first + q];
+        SlotResult r;
+        r.status = S.phase == PH_DONE ? S.status : LS_NOT_CONVERGED;
+        r.inner = S.inner_total;
+        r.outer = S.outer;
+        r.done = S.phase == PH_DONE;
+        double worst = 0.0;
+        for (int j = 0; j < D.s; j++) {
+            const double rel = S.bnorm[j] > 0.0 ? S.rn[j] / S.bnorm[j] : 0.0;
+            worst = rel > worst || rel != rel ? rel : worst;
+        }
+        r.rel_res = worst;
+        out[q] = r;
+    }
+}
+
+// ---- buffer sizes ---------------------------------------------------------------
+SlotSizes slot_sizes(int n, int s, int method, int m) {
+    SlotSizes z{};
+    z.sp = (s + 3) / 4 * 4;
+    z.ld32 = (n + 3) / 4 * 4;
+    z.lda_stage = (n + 1) / 2 * 2;
+    const size_t nsp = (size_t)n * z.sp;
+    z.bytes = 0;
+    auto add = [&](size_t b) { z.bytes += align_up(b, 256); };
+    add((size_t)n * z.ld32 * 4);              // A32
+    add(nsp * 8); add(nsp * 8); add(nsp * 8); // X, B, R
+    add(nsp * 4); add(nsp * 4); add(nsp * 4); // Rf, Z, Q
+    if (method == LS_METHOD_CG) add(2 * nsp * 4);                   // P
+    else { add(2 * nsp * 4); add((size_t)(m + 1) * nsp * 4); }      // W, V
+    z.stageA = align_up((size_t)n * z.lda_stage * 8, 256);
+    z.stageBX = align_up((size_t)n * s * 8, 256);
+    return z;
+}
+
+void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int method, int m) {
+    Carver cv(base);
+    const size_t nsp = (size_t)n * z.sp;
+    D.n = n;
+    D.s = s;
+    D.sp = z.sp;
+    D.method = method;
+    D.m = m;
+    D.A32 = cv.take<float>((size_t)n * z.ld32);
+    D.ld32 = z.ld32;
+    D.X = cv.take<double>(nsp);
+    D.B = cv.take<double>(nsp);
+    D.R = cv.take<double>(nsp);
+    D.Rf = cv.take<float>(nsp);
+    D.Z = cv.take<float>(nsp);
+    D.Q = cv.take<float>(nsp);
+    D.P = nullptr;
+    D.W = nullptr;
+    D.V = nullptr;
+    if (method == LS_METHOD_CG) {
+        D.P = cv.take<float>(2 * nsp);
+    } else {
+        D.W = cv.take<float>(2 * nsp);
+        D.V = cv.take<float>((size_t)(m + 1) * nsp);
+    }
+}
+
+// ---- the engine ---------------------------------------------------------------------
+Engine::~Engine() { release(); }
+
+void Engine::release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (dmem) cudaFree(dmem);
+    exec = nullptr;
+    graph = nullptr;
+    dmem = nullptr;
+    cap_slots = cap32 = cap64 = capv = 0;
+}
+
+int Engine::reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv) {
+    c = ctx;
+    if (dmem && slots <= cap_slots && n32 <= cap32 && n64 <= cap64 && nv <= capv) return LS_OK;
+    release();
+    cap_slots = std::max(slots, 1);
+    cap32 = std::max(n32, 1);
+    cap64 = std::max(n64, 1);
+    capv = std::max(nv, 1);
+    Carver cv(nullptr);
+    auto layout = [&](Carver &k) {
+        dE = k.take<EngineDev>(1);
+        hE.desc = k.take<SlotDesc>(cap_slots);
+        hE.st = k.take<SlotState>(cap_slots);
+        hE.gm = k.take<SlotGm>(cap_slots);
+        hE.t32 = k.take<Task>(cap32);
+        hE.t64 = k.take<Task>(cap64);
+        hE.tv = k.take<Task>(capv);
+        hE.part32 = k.take<double>((size_t)cap32 * E_PS * 32);
+        hE.part64 = k.take<double>((size_t)cap64 * 32);
+        hE.partv = k.take<double>((size_t)capv * 32);
+        hE.active = k.take<int>(8);
+        hE.launches = k.take<unsigned long long>(1);
+        bsrc = k.take<const double *>(cap_slots);
+        ldb = k.take<long long>(cap_slots);
+        xdst = k.take<double *>(cap_slots);
+        ldx = k.take<long long>(cap_slots);
+        results = k.take<SlotResult>(cap_slots);
+    };
+    layout(cv);
+    dbytes = align_up(cv.off, 256);
+    if (cudaMalloc(&dmem, dbytes) != cudaSuccess) {
+        cudaGetLastError();
+        dmem = nullptr;
+        cap_slots = 0;
+        return LS_ERR_NOMEM;
+    }
+    Carver real(dmem);
+    layout(real);
+    if (cudaMemsetAsync(dmem, 0, dbytes, c->stream) != cudaSuccess) return LS_ERR_CUDA;
+    K = engine_kernels();
+    grid_prod = 2 * c->num_sms;
+    grid_vec = 2 * c->num_sms;
+    cudaFuncSetAttribute(K.prod32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod32_smem);
+    cudaFuncSetAttribute(K.prod64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod64_smem);
+    return build_graph();
+}
+
+int Engine::build_graph() {
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return LS_ERR_CUDA;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    Chain top(graph);
+    cudaGraph_t body = top.loop(h);
+    if (top.err != cudaSuccess) {
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    Chain b(body);
+    const EngineDev *p = dE;
+    {
+        void *args[] = {(void *)&p, (void *)&h};
+        b.kernel(K.red, cap_slots, K.red_threads, 0, args, false);
+    }
+    {
+        void *args[] = {(void *)&p};
+        b.kernel(K.prod32, grid_prod, K.prod32_threads, K.prod32_smem, args, false);
+        b.kernel(K.prod64, grid_prod, K.prod64_threads, K.prod64_smem, args, false);
+        b.kernel(K.vec, grid_vec, K.vec_threads, 0, args, false);
+    }
+    if (b.err != cudaSuccess) {
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return LS_ERR_CUDA;
+    }
+    return LS_OK;
+}
+
+// Task tables from the slot sizes (each slot's tasks are contiguous).
+void Engine::set_tasks(std::vector<SlotDesc> &hd) {
+    h32.clear();
+    h64.clear();
+    hv.clear();
+    for (int q = 0; q < (int)hd.size(); q++) {
+        SlotDesc &D = hd[q];
+        if (D.n <= 0) {
+            D.t32 = D.n32 = D.t64 = D.n64 = D.tv = D.nv = 0;
+            continue;
+        }
+        D.t32 = (int)h32.size();
+        for (int r = 0; r < D.n; r += E_RB32) h32.push_back(Task{q, r, std::min(D.n, r + E_RB32)});
+        D.n32 = (int)h32.size() - D.t32;
+        D.t64 = (int)h64.size();
+        for (int r = 0; r < D.n; r += E_RB64) h64.push_back(Task{q, r, std::min(D.n, r + E_RB64)});
+        D.n64 = (int)h64.size() - D.t64;
+        D.tv = (int)hv.size();
+        for (int r = 0; r < D.n; r += E_RBV) hv.push_back(Task{q, r, std::min(D.n, r + E_RBV)});
+        D.nv = (int)hv.size() - D.tv;
+    }
+}
+
+int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit) {
+    hE.nslots = (int)hd.size();
+    hE.n32 = (int)h32.size();
+    hE.n64 = (int)h64.size();
+    hE.nv = (int)hv.size();
+    hE.tick_limit = tick_limit;
+    cudaError_t e = cudaSuccess;
+    if (!hd.empty())
+        e = cudaMemcpyAsync(hE.desc, hd.data(), hd.size() * sizeof(SlotDesc), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess && !h32.empty())
+        e = cudaMemcpyAsync(hE.t32, h32.data(), h32.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !h64.empty())
+        e = cudaMemcpyAsync(hE.t64, h64.data(), h64.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !hv.empty())
+        e = cudaMemcpyAsync(hE.tv, hv.data(), hv.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, 8 * sizeof(int), c->stream);
+    // the host copies above read pageable memory: make them complete before
+    // the host vectors can change
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return map_cuda(e);
+}
+
+int Engine::init_slots(int first, int count) {
+    if (count <= 0) return LS_OK;
+    eng_init_state_kernel<<<std::min(count, 1024), 256, 0, c->stream>>>(hE.st, first, count);
+    return map_cuda(cudaGetLastError());
+}
+
+int Engine::admit(int first, int count, const std::vector<const double *> &bs,
+                  const std::vector<long long> &lb) {
+    if (count <= 0) return LS_OK;
+    cudaError_t e = cudaMemcpyAsync(bsrc + first, bs.data(), count * sizeof(double *),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ldb + first, lb.data(), count * sizeof(long long), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    const EngineDev *p = dE;
+    const double *const *bp = bsrc + first;
+    const long long *lp = ldb + first;
+    void *args[] = {(void *)&p, (void *)&bp, (void *)&lp, (void *)&first, (void *)&count};
+    e = cudaLaunchKernel(K.admit, dim3(64, std::min(count, 1024)), dim3(256), args, 0, c->stream);
+    return map_cuda(e);
+}
+
+int Engine::finish(int first, int count, const std::vector<double *> &xs,
+                   const std::vector<long long> &lx) {
+    if (count <= 0) return LS_OK;
+    cudaError_t e = cudaMemcpyAsync(xdst + first, xs.data(), count * sizeof(double *),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ldx + first, lx.data(), count * sizeof(long long), cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    const EngineDev *p = dE;
+    double *const *xp = xdst + first;
+    const long long *lp = ldx + first;
+    void *args[] = {(void *)&p, (void *)&xp, (void *)&lp, (void *)&first, (void *)&count};
+    e = cudaLaunchKernel(K.finish, dim3(64, std::min(count, 1024)), dim3(256), args, 0, c->stream);
+    return map_cuda(e);
+}
+
+int Engine::collect(int first, int count, std::vector<SlotResult> &out) {
+    out.resize(count);
+    if (count <= 0) return LS_OK;
+    eng_collect_kernel<<<(count + 127) / 128, 128, 0, c->stream>>>(hE.desc, hE.st, results + first,
+                                                                   first, count);
+    cudaError_t e = cudaMemcpyAsync(out.data(), results + first, count * sizeof(SlotResult),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return map_cuda(e);
+}
+
+int Engine::run() {
+    return map_cuda(cudaGraphLaunch(exec, c->stream));
+}
+
+unsigned long long Engine::launches() {
+    unsigned long long v = 0;
+    cudaMemcpyAsync(&v, hE.launches, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return v;
+}
+
+void extra_destroy(ls_ctx *c) {
+    delete c->batch;
+    c->batch = nullptr;
+}
+
+}  // namespace lsi
+
+using namespace lsi;
+
+// ============================================================================
+// ls_batch_solve
+// ============================================================================
+extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_info *infos) {
+    if (!c || count < 0 || (count > 0 && !sys)) return LS_ERR_ARG;
+    if (count == 0) return LS_OK;
+    for (int q = 0; q < count; q++) {
+        const ls_system &S = sys[q];
+        bool bad = S.n < 1 || S.n > LS_BATCH_MAX_N || S.nrhs < 1 || S.nrhs > LS_BATCH_MAX_RHS;
+        bad = bad || S.lda < S.n || S.ldb < S.n || S.ldx < S.n || !S.A || !S.B || !S.X;
+        bad = bad || (S.method != LS_METHOD_CG && S.method != LS_METHOD_GMRES);
+        bad = bad || (S.method == LS_METHOD_GMRES && (S.opts.restart < 1 || S.opts.restart > E_MAXM));
+        bad = bad || !(S.opts.rtol >= 0.0) || S.opts.max_iter < 0;
+        if (bad) {   // name the offending system; nothing is solved
+            if (infos) {
+                memset(&infos[q], 0, sizeof(ls_info));
+                infos[q].status = LS_ERR_ARG;
+            }
+            return LS_ERR_ARG;
+        }
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+
+    // sizes and workspace
+    std::vector<SlotSizes> z(count);
+    std::vector<int> a_dev(count), b_dev(count), x_dev(count);
+    size_t total = 0;
+    int n32 = 0, n64 = 0, nv = 0;
+    for (int q = 0; q < count; q++) {
+        const ls_system &S = sys[q];
+        z[q] = slot_sizes(S.n, S.nrhs, S.method, S.opts.restart);
+        a_dev[q] = is_device_ptr(S.A);
+        b_dev[q] = is_device_ptr(S.B);
+        x_dev[q] = is_device_ptr(S.X);
+        total += z[q].bytes + (a_dev[q] ? 0 : z[q].stageA) + (b_dev[q] ? 0 : z[q].stageBX) +
+                 (x_dev[q] ? 0 : z[q].stageBX);
+        n32 += (S.n + E_RB32 - 1) / E_RB32;
+        n64 += (S.n + E_RB64 - 1) / E_RB64;
+        nv += (S.n + E_RBV - 1) / E_RBV;
+    }
+    int rc = ws_reserve(c, total);
+    if (rc) return rc;
+    if (!c->batch) c->batch = new (std::nothrow) Engine();
+    if (!c->batch) return LS_ERR_NOMEM;
+    Engine &E = *c->batch;
+    rc = E.reserve(c, count, n32, n64, nv);
+    if (rc) return rc;
+
+    // carve, stage, describe
+    std::vector<SlotDesc> hd(count);
+    std::vector<const double *> bsrc(count);
+    std::vector<long long> ldb(count), ldx(count);
+    std::vector<double *> xdst(count), xstage(count, nullptr);
+    char *p = c->ws;
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < count && e == cudaSuccess; q++) {
+        const ls_system &S = sys[q];
+        SlotDesc &D = hd[q];
+        memset(&D, 0, sizeof(D));
+        slot_carve(D, z[q], p, S.n, S.nrhs, S.method, S.opts.restart);
+        p += z[q].bytes;
+        D.inner_iters = S.method == LS_METHOD_CG ? (S.opts.inner_iters > 0 ? 4 * S.opts.inner_iters : 100)
+                                                 : S.opts.restart;
+        D.max_outer = S.opts.max_iter > 0 ? S.opts.max_iter : 20;
+        D.inner_tol = S.opts.inner_rtol > 0.0 ? (float)S.opts.inner_rtol : 1e-6f;
+        D.rtol = S.opts.rtol;
+        if (a_dev[q]) {
+            D.A64 = S.A;
+            D.lda64 = S.lda;
+        } else {
+            double *st = reinterpret_cast<double *>(p);
+            p += z[q].stageA;
+            e = cudaMemcpy2DAsync(st, z[q].lda_stage * 8, S.A, S.lda * 8, S.n * 8, S.n,
+                                  cudaMemcpyHostToDevice, c->stream);
+            D.A64 = st;
+            D.lda64 = z[q].lda_stage;
+        }
+        if (b_dev[q]) {
+            bsrc[q] = S.B;
+            ldb[q] = S.ldb;
+        } else {
+            double *st = reinterpret_cast<double *>(p);
+            p += z[q].stageBX;
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(st, (size_t)S.n * 8, S.B, S.ldb * 8, S.n * 8, S.nrhs,
+                                      cudaMemcpyHostToDevice, c->stream);
+            bsrc[q] = st;
+            ldb[q] = S.n;
+        }
+        if (x_dev[q]) {
+            xdst[q] = S.X;
+            ldx[q] = S.ldx;
+        } else {
+            xstage[q] = reinterpret_cast<double *>(p);
+            p += z[q].stageBX;
+            xdst[q] = xstage[q];
+            ldx[q] = S.n;
+        }
+    }
+    if (e != cudaSuccess) return map_cuda(e);
+    E.set_tasks(hd);
+    rc = E.upload(hd, INT_MAX);
+    if (!rc) rc = E.init_slots(0, count);
+    if (!rc) rc = E.admit(0, count, bsrc, ldb);
+    if (rc) return rc;
+    const unsigned long long l0 = E.launches();
+    e = cudaEventRecord(c->ev0, c->stream);
+    if (e == cudaSuccess) rc = E.run();
+    if (e == cudaSuccess && !rc) e = cudaEventRecord(c->ev1, c->stream);
+    if (e != cudaSuccess || rc) return rc ? rc : map_cuda(e);
+    rc = E.finish(0, count, xdst, ldx);
+    std::vector<SlotResult> res;
+    if (!rc) rc = E.collect(0, count, res);
+    if (rc) return rc;
+    for (int q = 0; q < count && e == cudaSuccess; q++) {
+        if (!xstage[q]) continue;
+        const ls_system &S = sys[q];
+        e = cudaMemcpy2DAsync(S.X, S.ldx * 8, xstage[q], (size_t)S.n * 8, S.n * 8, S.nrhs,
+                              cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    const long long launched = (long long)(E.launches() - l0) + 2;   // + admit, finish
+    c->launches_total += launched + 2;                               // + init, collect
+    int worst = LS_OK;
+    for (int q = 0; q < count; q++) {
+        const SlotResult &r = res[q];
+        int st = r.status;
+        if (st < 0 && worst >= 0) worst = st;
+        else if (worst >= 0 && st > worst) worst = st;
+        if (infos) {
+            ls_info &I = infos[q];
+            const double nn = (double)sys[q].n * sys[q].n;
+            I.status = st;
+            I.iters = r.inner;
+            I.outer_iters = r.outer;
+            I.rel_res = r.rel_res;
+            I.true_rel_res = r.rel_res;
+            I.time_ms = ms;
+            I.bytes_moved = nn * (8.0 + 4.0) + (double)r.outer * 8.0 * nn + (double)r.inner * 4.0 * nn;
+            I.launches = launched;
+        }
+    }
+    return worst;
+}

@@ -1,0 +1,62 @@
+// ls_engine_host.h -- host-side engine object shared by ls_batch_solve and the
+// server.
+#pragma once
+
+#include <vector>
+
+#include "ls_api_internal.h"
+#include "ls_engine.h"
+
+namespace lsi {
+
+struct SlotResult {
+    int status, inner, outer, done;
+    double rel_res;
+};
+
+struct SlotSizes {
+    int sp;
+    long long ld32, lda_stage;
+    size_t bytes;        // engine buffers of the slot
+    size_t stageA;       // FP64 copy of a host A
+    size_t stageBX;      // column-major copy of a host B or X
+};
+
+SlotSizes slot_sizes(int n, int s, int method, int m);
+void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int method, int m);
+
+class Engine {
+public:
+    ls_ctx *c = nullptr;
+    int cap_slots = 0, cap32 = 0, cap64 = 0, capv = 0;
+    char *dmem = nullptr;
+    size_t dbytes = 0;
+    EngineDev *dE = nullptr;
+    EngineDev hE{};
+    const double **bsrc = nullptr;
+    long long *ldb = nullptr;
+    double **xdst = nullptr;
+    long long *ldx = nullptr;
+    SlotResult *results = nullptr;
+    std::vector<Task> h32, h64, hv;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    EngineKernels K{};
+    int grid_prod = 0, grid_vec = 0;
+
+    ~Engine();
+    void release();
+    int reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv);
+    int build_graph();
+    void set_tasks(std::vector<SlotDesc> &hd);
+    int upload(const std::vector<SlotDesc> &hd, int tick_limit);
+    int init_slots(int first, int count);
+    int admit(int first, int count, const std::vector<const double *> &bs,
+              const std::vector<long long> &lb);
+    int finish(int first, int count, const std::vector<double *> &xs, const std::vector<long long> &lx);
+    int collect(int first, int count, std::vector<SlotResult> &out);
+    int run();
+    unsigned long long launches();
+};
+
+}  // namespace lsi
