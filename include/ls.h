@@ -165,7 +165,7 @@ typedef struct {
     ls_opts opts;        /* rtol, max_iter, restart used per system; precision ignored  */
 } ls_system;
 
-#define LS_BATCH_MAX_N   4096
+#define LS_BATCH_MAX_N   8192
 #define LS_BATCH_MAX_RHS 32
 
 /*
@@ -197,17 +197,22 @@ typedef struct ls_server ls_server;
 int ls_server_start(ls_ctx *ctx, const ls_server_cfg *cfg, ls_server **srv);
 
 /*
- * Queue one system.  A, B are deep-copied before the call returns (the
- * caller may free them); X must stay valid until ls_server_poll reports the
- * ticket done.  Thread-safe.  LS_ERR_BUSY when the queue is full,
- * LS_ERR_NOMEM when the request alone exceeds the budget.
+ * Queue one system (n <= LS_BATCH_MAX_N, nrhs <= LS_BATCH_MAX_RHS).  B is
+ * copied before the call returns.  A in host memory is copied too; A in
+ * device memory is read in place, so that a set of matrices kept resident on
+ * the device can be served without copies -- it must stay valid and unchanged
+ * until the ticket is done.  X (host or device) must stay valid until
+ * ls_server_poll reports the ticket done.  Thread-safe.  LS_ERR_BUSY when the
+ * queue is full or the server is stopping, LS_ERR_NOMEM when the request
+ * alone exceeds the budget.
  */
 int ls_server_submit(ls_server *srv, const ls_system *req, uint64_t *ticket);
 
 /*
- * Non-blocking: *done = 1 once X has been written and *info filled in.
- * Thread-safe.  LS_ERR_ARG for an unknown ticket.  A finished ticket can be
- * polled once more and is then forgotten.
+ * Non-blocking: *done = 1 once X has been written and *info filled in
+ * (info->time_ms is the latency from submit to completion).  Thread-safe.
+ * The call that reports done = 1 also forgets the ticket: a later poll of it,
+ * like a poll of a ticket never issued, returns LS_ERR_ARG.
  */
 int ls_server_poll(ls_server *srv, uint64_t ticket, int *done, ls_info *info);
 

@@ -21,7 +21,7 @@ LS_METHOD_CG, LS_METHOD_GMRES = 0, 1
 LS_F64, LS_BF16_IR, LS_FP8_IR, LS_F32_IR = 0, 1, 2, 3
 LS_REFINE_FCG, LS_REFINE_IR = 0, 1
 LS_MAX_RESTART = 128
-LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 4096, 32
+LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 8192, 32
 
 # every symbol declared in include/ls.h
 ABI_FUNCTIONS = (

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(P32_T) eng_prod32_kernel(const EngineDev *Ep) 
     const int row = tid >> 1, kh = tid & 1;
     for (int t = blockIdx.x; t < E.n32; t += gridDim.x) {
         const Task T = E.t32[t];
+        if (T.slot < 0) continue;                                       // unused entry
         const SlotDesc &D = E.desc[T.slot];
         const SlotState &S = E.st[T.slot];
         const int ph = S.phase;
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(P64_T) eng_prod64_kernel(const EngineDev *Ep) 
     const int row = tid >> 4, kl = tid & 15;
     for (int t = blockIdx.x; t < E.n64; t += gridDim.x) {
         const Task T = E.t64[t];
+        if (T.slot < 0) continue;                                       // unused entry
         const SlotDesc &D = E.desc[T.slot];
         const SlotState &S = E.st[T.slot];
         if (S.phase != PH_RESID) continue;
@@ -419,6 +421,7 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = blockIdx.x; t < E.nv; t += gridDim.x) {
         const Task T = E.tv[t];
+        if (T.slot < 0) continue;                                       // unused entry
         const SlotDesc &D = E.desc[T.slot];
         const SlotState &S = E.st[T.slot];
         const int ph = S.phase;

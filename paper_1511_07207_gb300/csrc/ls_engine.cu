@@ -193,36 +193,53 @@ int Engine::build_graph() {
     return LS_OK;
 }
 
-// Task tables from the slot sizes (each slot's tasks are contiguous).
-void Engine::set_tasks(std::vector<SlotDesc> &hd) {
+// Task tables from the slot sizes.  Packed: each slot's tasks follow the
+// previous slot's (the batched solver, whose slot set never changes).  With
+// fixed regions of max_n rows per slot, a slot's task indices -- and so the
+// partial sums it left in the previous tick -- never move when other slots
+// are admitted or retired (the server); unused entries have slot = -1.
+void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     h32.clear();
     h64.clear();
     hv.clear();
+    const int per32 = (fixed_max_n + E_RB32 - 1) / E_RB32, per64 = (fixed_max_n + E_RB64 - 1) / E_RB64,
+              perv = (fixed_max_n + E_RBV - 1) / E_RBV;
+    auto fill = [](std::vector<Task> &tab, int q, int n, int rb, int per, int fixed, int &t0, int &cnt) {
+        if (fixed) {
+            t0 = q * per;
+            tab.resize((size_t)(q + 1) * per, Task{-1, 0, 0});
+        } else {
+            t0 = (int)tab.size();
+        }
+        cnt = 0;
+        for (int r = 0; r < n; r += rb, cnt++) {
+            const Task t{q, r, std::min(n, r + rb)};
+            if (fixed) tab[t0 + cnt] = t;
+            else tab.push_back(t);
+        }
+    };
     for (int q = 0; q < (int)hd.size(); q++) {
         SlotDesc &D = hd[q];
-        if (D.n <= 0) {
-            D.t32 = D.n32 = D.t64 = D.n64 = D.tv = D.nv = 0;
-            continue;
-        }
-        D.t32 = (int)h32.size();
-        for (int r = 0; r < D.n; r += E_RB32) h32.push_back(Task{q, r, std::min(D.n, r + E_RB32)});
-        D.n32 = (int)h32.size() - D.t32;
-        D.t64 = (int)h64.size();
-        for (int r = 0; r < D.n; r += E_RB64) h64.push_back(Task{q, r, std::min(D.n, r + E_RB64)});
-        D.n64 = (int)h64.size() - D.t64;
-        D.tv = (int)hv.size();
-        for (int r = 0; r < D.n; r += E_RBV) hv.push_back(Task{q, r, std::min(D.n, r + E_RBV)});
-        D.nv = (int)hv.size() - D.tv;
+        const int n = D.n > 0 ? D.n : 0;
+        fill(h32, q, n, E_RB32, per32, fixed_max_n, D.t32, D.n32);
+        fill(h64, q, n, E_RB64, per64, fixed_max_n, D.t64, D.n64);
+        fill(hv, q, n, E_RBV, perv, fixed_max_n, D.tv, D.nv);
     }
 }
 
-int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit) {
+int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables) {
     hE.nslots = (int)hd.size();
     hE.n32 = (int)h32.size();
     hE.n64 = (int)h64.size();
     hE.nv = (int)hv.size();
     hE.tick_limit = tick_limit;
     cudaError_t e = cudaSuccess;
+    if (!tables) {   // same slot set: only the loop counters are reset
+        e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, 8 * sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        return map_cuda(e);
+    }
     if (!hd.empty())
         e = cudaMemcpyAsync(hE.desc, hd.data(), hd.size() * sizeof(SlotDesc), cudaMemcpyHostToDevice,
                             c->stream);
@@ -413,8 +430,8 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
         }
     }
     if (e != cudaSuccess) return map_cuda(e);
-    E.set_tasks(hd);
-    rc = E.upload(hd, INT_MAX);
+    E.set_tasks(hd, 0);
+    rc = E.upload(hd, INT_MAX, true);
     if (!rc) rc = E.init_slots(0, count);
     if (!rc) rc = E.admit(0, count, bsrc, ldb);
     if (rc) return rc;

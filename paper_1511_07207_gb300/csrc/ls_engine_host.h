@@ -48,8 +48,8 @@ public:
     void release();
     int reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv);
     int build_graph();
-    void set_tasks(std::vector<SlotDesc> &hd);
-    int upload(const std::vector<SlotDesc> &hd, int tick_limit);
+    void set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n);
+    int upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables);
     int init_slots(int first, int count);
     int admit(int first, int count, const std::vector<const double *> &bs,
               const std::vector<long long> &lb);
