@@ -308,6 +308,8 @@ def run_native(args):
     mixed = None
     if not args.no_mixed:
         mixed = run_mixed_compare(B, ctx, dev, stream, args)
+    batch = run_batch_compare(B, ctx, dev, args) if not args.no_batch else None
+    serve = run_serve(B, ctx, dev, args) if not args.no_serve else None
 
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -343,6 +345,8 @@ def run_native(args):
                          "peak_source": peak_src},
             "roofline": roofline,
             "mixed_vs_fp64": mixed,
+            "batch_512": batch,
+            "serve": serve,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
@@ -405,6 +409,135 @@ def run_mixed_compare(B, ctx, dev, stream, args, n=32768):
     out["gemv_GBs"] = gb
     out["gemv_hbm_frac"] = {k: round(v / peaks["hbm_gbs"], 4) for k, v in gb.items()}
     del A
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch_compare(B, ctx, dev, args, count=512):
+    """512 independent systems, n log-uniform in [64, 2048], half SPD (CG),
+    half nonsymmetric (GMRES(30)), 1..32 right-hand sides, FP64 refinement
+    to 1e-10 around FP32 inner solves, in one ls_batch_solve call."""
+    import numpy as np
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    specs = inputs.batch_specs(count, seed=0)
+    systems, keep = [], []
+    for sp in specs:
+        A = sp.matrix(device=dev)
+        Xs = torch.from_numpy(sp.solution()).to(dev)
+        Bm = (A @ Xs).T.contiguous().T                      # column-major n x s
+        X = torch.zeros_like(Bm).T.contiguous().T
+        method = B.LS_METHOD_CG if sp.kind == "spd" else B.LS_METHOD_GMRES
+        systems.append(B.make_system(method, A, Bm, X, B.make_opts(rtol=RTOL, restart=30)))
+        keep.append((A, Bm, X, Xs))
+    torch.cuda.synchronize(dev)
+    st, infos = B.ls_batch_solve(ctx, systems)               # warm-up (engine + graph set-up)
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        for (_, _, X, _) in keep:
+            X.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st, infos = B.ls_batch_solve(ctx, systems)
+        times.append((time.perf_counter() - t0, infos[0]["time_ms"]))
+    wall, dev_ms = min(times)
+    ok = sum(i["status"] == B.LS_OK for i in infos)
+    cols = sum(sp.nrhs for sp in specs)
+    worst_res = max(i["true_rel_res"] for i in infos)
+    err = max(float(torch.linalg.norm(X - Xs) / torch.linalg.norm(Xs)) for (_, _, X, Xs) in keep)
+    bytes_moved = sum(i["bytes_moved"] for i in infos)
+    out = {"systems": count, "rhs_columns": cols, "n_range": [64, 2048],
+           "status_ok": ok, "batch_ms_device": round(dev_ms, 3), "batch_ms_wall": round(wall * 1e3, 3),
+           "systems_per_s": round(count / (dev_ms * 1e-3), 2),
+           "rhs_solves_per_s": round(cols / (dev_ms * 1e-3), 1),
+           "A_bytes_streamed_GB": round(bytes_moved / 1e9, 3),
+           "A_stream_GBs": round(bytes_moved / (dev_ms * 1e-3) / 1e9, 1),
+           "max_true_rel_res": worst_res, "max_rel_err_vs_xstar": err,
+           "inner_iters_max": max(i["iters"] for i in infos),
+           "outer_iters_max": max(i["outer_iters"] for i in infos),
+           "gpu_launches": infos[0]["launches"]}
+    del keep, systems
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(B, ctx, dev, args):
+    """Poisson arrivals at 2000 requests/s; each request draws a matrix from a
+    resident pool (64 SPD + 64 nonsymmetric, n log-uniform in [128, 8192]),
+    asks for 1e-6 or 1e-10, with 1..8 right-hand sides; 120 GB HBM budget."""
+    import threading
+    import numpy as np
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    reqs, pool = inputs.serve_requests(rate=2000.0, duration=args.serve_seconds, seed=0)
+    mats = [p.matrix(device=dev) for p in pool]
+    key = {p.seed: i for i, p in enumerate(pool)}
+    # right-hand sides B = A X* per request, prepared before the clock starts
+    prepared = []
+    for rq in reqs:
+        A = mats[key[rq.spec.seed]]
+        xs = torch.from_numpy(inputs.solution(rq.spec.n, seed=rq.spec.seed + 7, nrhs=rq.spec.nrhs)).to(dev)
+        Bh = np.asfortranarray((A @ xs).cpu().numpy())
+        Xh = np.zeros((rq.spec.n, rq.spec.nrhs), order="F")
+        method = B.LS_METHOD_CG if rq.spec.kind == "spd" else B.LS_METHOD_GMRES
+        o = B.make_opts(rtol=rq.spec.rtol, restart=30)
+        prepared.append((rq.t_arrival, B.make_system(method, A, Bh, Xh, o), Bh, Xh))
+    torch.cuda.synchronize(dev)
+    srv = B.ls_server_start(ctx, hbm_budget_bytes=120 * (1 << 30), max_slots=args.serve_slots,
+                            step_iters=args.serve_step)
+    import collections
+    tickets = [None] * len(prepared)
+    lat = [None] * len(prepared)
+    fresh = collections.deque()
+    done_evt = threading.Event()
+    t_start = time.perf_counter()
+
+    def poller():
+        pending = set()
+        while not done_evt.is_set() or pending or fresh:
+            while fresh:
+                pending.add(fresh.popleft())
+            for i in list(pending):
+                st, done, info = B.ls_server_poll(srv, tickets[i])
+                if done:
+                    lat[i] = info
+                    pending.discard(i)
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    busy = 0
+    for i, (ta, sysd, _, _) in enumerate(prepared):
+        now = time.perf_counter() - t_start
+        if ta > now:
+            time.sleep(ta - now)
+        while True:
+            st, t = B.ls_server_submit(srv, sysd)
+            if st != B.LS_ERR_BUSY:
+                break
+            busy += 1
+            time.sleep(0.001)
+        tickets[i] = t
+        fresh.append(i)
+    done_evt.set()
+    th.join(timeout=600)
+    t_end = time.perf_counter()
+    B.ls_server_stop(srv)
+    infos = [x for x in lat if x is not None]
+    ms = np.array([x["time_ms"] for x in infos])
+    ok = sum(x["status"] == B.LS_OK for x in infos)
+    out = {"arrival_rate_per_s": 2000, "duration_s": args.serve_seconds, "requests": len(prepared),
+           "completed": len(infos), "status_ok": ok,
+           "solves_per_s": round(len(infos) / (t_end - t_start), 1),
+           "latency_ms": {"p50": round(float(np.percentile(ms, 50)), 3),
+                          "p90": round(float(np.percentile(ms, 90)), 3),
+                          "p99": round(float(np.percentile(ms, 99)), 3),
+                          "max": round(float(ms.max()), 3)} if len(ms) else None,
+           "max_slots": args.serve_slots, "step_ticks": args.serve_step, "hbm_budget_GB": 120,
+           "queue_full_retries": busy,
+           "max_rel_res": max((x["true_rel_res"] for x in infos), default=None),
+           "pool": "64 SPD + 64 nonsymmetric matrices, n log-uniform in [128, 8192], resident on the device"}
+    del mats, prepared
     torch.cuda.empty_cache()
     return out
 
@@ -506,6 +639,12 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-system batched solve")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served workload")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson arrival window (60 s in the full workload)")
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-step", type=int, default=4)
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
     ap.add_argument("--cpu-cg-sample", type=int, default=600)

@@ -22,19 +22,26 @@ constexpr int RED_T = 64;
 constexpr int P32_T = 256;
 constexpr int P64_T = 256;
 constexpr int VEC_T = 256;
-constexpr int KC32 = 32;     // k chunk of the FP32 product
-constexpr int AS32 = 34;     // padded row stride of the A tile (floats)
 constexpr int KC64 = 64;     // k chunk of the FP64 residual
 
 __device__ __forceinline__ void eng_count(const EngineDev &E) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(E.launches, 1ull);
 }
 
+// Tasks are claimed one at a time from a per-tick counter, so CTAs that draw
+// large tasks do not hold up the tick while others sit idle.
+__device__ __forceinline__ int claim(int *counter, int *slot_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) *slot_s = atomicAdd(counter, 1);
+    __syncthreads();
+    return *slot_s;
+}
+
 // ============================================================================
 // eng_red: one block per slot; thread j < 32 owns column j
 // ============================================================================
 __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cudaGraphConditionalHandle h) {
-    const EngineDev E = *Ep;
+    const EngineDev &E = *Ep;
     __shared__ int all_stop, newphase_s;
     const int sl = blockIdx.x < E.nslots ? blockIdx.x : 0;
     const int j = threadIdx.x;
@@ -202,133 +209,233 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
             const int total = atomicAdd(&E.active[0], 0);
             const int ticks = E.active[3] + 1;
             E.active[3] = ticks;
-            cudaGraphSetConditional(h, total > 0 && ticks < E.tick_limit);
+            const int go = total > 0 && ticks < E.tick_limit;
+            if (E.host_loop) E.active[4] = go;
+            else cudaGraphSetConditional(h, go);
             E.active[0] = 0;
             E.active[1] = 0;
             E.active[2] = total;
+            E.active[5] = 0;   // task claim counters of prod32 / prod64 / vec
+            E.active[6] = 0;
+            E.active[7] = 0;
         }
     }
 }
 
 // ============================================================================
-// eng_prod32: FP32 block product of one 128-row task, CG or GMRES phase
+// eng_prod32: FP32 block product Y = Ahat P of one task (256 rows, all sp
+// columns), register-blocked: each thread owns an (sp/4)-row x 4-column tile
+// of Y.  The A chunk (32 columns of the task's rows) sits transposed in
+// shared memory; the next chunk is prefetched into registers meanwhile.
 // ============================================================================
-__global__ void __launch_bounds__(P32_T) eng_prod32_kernel(const EngineDev *Ep) {
-    const EngineDev E = *Ep;
+template <int SP>
+__device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, int t, float *As,
+                                            float *Ps, double *Red, float *colscale, int *colstop) {
+    constexpr int RB = E_RB32, KC = E_KC32;
+    constexpr int RPT = SP / 4;                 // rows per thread
+    constexpr int NCG = SP / 4;                 // column groups of 4
+    constexpr int RBP = RB + 4;                 // padded row stride of the transposed tile
+    constexpr int AV = RB * KC / 4 / P32_T;     // float4 loads of A per thread per chunk (8)
+    constexpr int PV = (KC * SP + P32_T - 1) / P32_T;
+    static_assert((RB / RPT) * NCG == P32_T, "thread grid");
+    const SlotDesc &D = E.desc[T.slot];
+    const SlotState &S = E.st[T.slot];
+    const int ph = S.phase;
+    const int n = D.n, s = D.s, it = S.it;
+    const long long nsp = (long long)n * SP;
+    const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
+    const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
+    const float *src, *src2 = nullptr;
+    float *dst, *out;
+    if (ph == PH_CG) {
+        src = D.Rf;                                             // P = Rf + beta P'
+        src2 = it > 0 ? D.P + ((it + 1) & 1) * nsp : nullptr;
+        dst = D.P + (it & 1) * nsp;
+        out = D.Q;
+    } else {
+        src = D.W + (it & 1) * nsp;                             // V_k = W / h
+        dst = D.V + (long long)it * nsp;
+        out = D.W + ((it + 1) & 1) * nsp;
+    }
+    if (tid < 32) {
+        float sc = 0.0f;
+        const int stp = tid < s ? S.colstop[tid] : 1;
+        if (!stp) sc = ph == PH_CG ? (float)S.beta[tid] : (float)(1.0 / S.hnorm[tid]);
+        colscale[tid] = sc;
+        colstop[tid] = stp;
+    }
+    __syncthreads();
+    const float *A = D.A32;
+    const long long lda = D.ld32;
+    float4 areg[AV];
+    float preg[PV];
+    // lane l of warp w loads rows 32*(w % 8) + l ... : all lanes of a warp hold
+    // the same k-quad, so the transposed stores hit 32 different banks
+    auto a_index = [&](int v, int &rr, int &q) {
+        const int e = tid + v * P32_T;                          // 0 .. RB*KC/4 - 1
+        rr = (e & 31) + 32 * ((e >> 5) % (RB / 32));
+        q = (e >> 5) / (RB / 32);
+    };
+    auto prefetch = [&](int k0) {
+#pragma unroll
+        for (int v = 0; v < AV; v++) {
+            int rr, q;
+            a_index(v, rr, q);
+            const int gr = r0 + rr, gk = k0 + 4 * q;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < r1) {
+                const float *ap = A + (long long)gr * lda + gk;
+                if (gk + 3 < n) x = *reinterpret_cast<const float4 *>(ap);
+                else {
+                    if (gk < n) x.x = ap[0];
+                    if (gk + 1 < n) x.y = ap[1];
+                    if (gk + 2 < n) x.z = ap[2];
+                }
+            }
+            areg[v] = x;
+        }
+#pragma unroll
+        for (int v = 0; v < PV; v++) {
+            const int e = tid + v * P32_T;
+            float val = 0.0f;
+            if (e < KC * SP) {
+                const int kk = e / SP, c = e % SP, gk = k0 + kk;
+                if (gk < n && c < s) {
+                    const long long o = (long long)gk * SP + c;
+                    if (ph == PH_CG)
+                        val = colstop[c] ? 0.0f : (src2 ? fmaf(colscale[c], src2[o], src[o]) : src[o]);
+                    else
+                        val = src[o] * colscale[c];
+                    if (gk >= r0 && gk < r1) dst[o] = val;      // this task owns row gk
+                }
+            }
+            preg[v] = val;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int v = 0; v < AV; v++) {
+            int rr, q;
+            a_index(v, rr, q);
+            As[(4 * q + 0) * RBP + rr] = areg[v].x;
+            As[(4 * q + 1) * RBP + rr] = areg[v].y;
+            As[(4 * q + 2) * RBP + rr] = areg[v].z;
+            As[(4 * q + 3) * RBP + rr] = areg[v].w;
+        }
+#pragma unroll
+        for (int v = 0; v < PV; v++) {
+            const int e = tid + v * P32_T;
+            if (e < KC * SP) Ps[e] = preg[v];
+        }
+    };
+    float acc[RPT][4];
+#pragma unroll
+    for (int r = 0; r < RPT; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0.0f;
+    prefetch(0);
+    for (int k0 = 0; k0 < n; k0 += KC) {
+        store();
+        __syncthreads();
+        if (k0 + KC < n) prefetch(k0 + KC);                      // overlaps with the math below
+#pragma unroll 8
+        for (int kk = 0; kk < KC; kk++) {
+            float av[RPT];
+            const float *ar = As + kk * RBP + rg * RPT;
+            if constexpr (RPT == 1) {
+                av[0] = ar[0];
+            } else if constexpr (RPT == 2) {
+                const float2 a2 = *reinterpret_cast<const float2 *>(ar);
+                av[0] = a2.x;
+                av[1] = a2.y;
+            } else {
+#pragma unroll
+                for (int r4 = 0; r4 < RPT; r4 += 4) {
+                    const float4 a4 = *reinterpret_cast<const float4 *>(ar + r4);
+                    av[r4] = a4.x;
+                    av[r4 + 1] = a4.y;
+                    av[r4 + 2] = a4.z;
+                    av[r4 + 3] = a4.w;
+                }
+            }
+            const float4 pv = *reinterpret_cast<const float4 *>(Ps + kk * SP + cg * 4);
+            const float pc[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av[r], pc[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    // Y rows of this task
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+        const int row = rg * RPT + r;
+        if (row < nrow)
+            *reinterpret_cast<float4 *>(out + (long long)(r0 + row) * SP + cg * 4) =
+                make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    }
+    // partial dots over this task's rows: CG p.q; GMRES v_i.w for i <= it
+    const int nd = ph == PH_CG ? 1 : it + 1;
+    constexpr int NRG = RB / RPT;               // row groups
+    constexpr int NG = P32_T / SP;              // second-level groups per column
+    for (int i = 0; i < nd; i++) {
+        const float *vi = ph == PH_CG ? dst : D.V + (long long)i * nsp;
+        double pc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            const int row = rg * RPT + r;
+            if (row < nrow) {
+                const float4 v = *reinterpret_cast<const float4 *>(vi + (long long)(r0 + row) * SP + cg * 4);
+                pc[0] += (double)v.x * acc[r][0];
+                pc[1] += (double)v.y * acc[r][1];
+                pc[2] += (double)v.z * acc[r][2];
+                pc[3] += (double)v.w * acc[r][3];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) Red[rg * SP + cg * 4 + c] = pc[c];
+        __syncthreads();
+        {   // thread (group g, column c) sums row groups g, g + NG, ... (fixed order)
+            const int c = tid % SP, g = tid / SP;
+            double sacc = 0.0;
+            for (int q = g; q < NRG; q += NG) sacc += Red[q * SP + c];
+            __syncthreads();
+            Red[g * SP + c] = sacc;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            double sacc = 0.0;
+            if (tid < SP)
+                for (int g = 0; g < NG; g++) sacc += Red[g * SP + tid];
+            E.part32[((size_t)t * E_PS + i) * 32 + tid] = sacc;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(P32_T, 2) eng_prod32_kernel(const EngineDev *Ep) {
+    const EngineDev &E = *Ep;
     extern __shared__ __align__(16) unsigned char esm[];
-    float *As = reinterpret_cast<float *>(esm);                         // [128][AS32]
-    float *Ps = As + E_RB32 * AS32;                                     // [KC32][32]
-    double *Red = reinterpret_cast<double *>(Ps + KC32 * 32);           // [128][33]
+    float *As = reinterpret_cast<float *>(esm);                         // [KC][RB + 4]
+    float *Ps = As + E_KC32 * (E_RB32 + 4);                             // [KC][SP]
+    double *Red = reinterpret_cast<double *>(Ps + E_KC32 * 32);         // [row groups][SP]
     __shared__ float colscale[32];
+    __shared__ int colstop[32];
+    __shared__ int claim_s;
     eng_count(E);
-    const int tid = threadIdx.x;
-    const int row = tid >> 1, kh = tid & 1;
-    for (int t = blockIdx.x; t < E.n32; t += gridDim.x) {
+    for (int t = claim(E.active + 5, &claim_s); t < E.n32; t = claim(E.active + 5, &claim_s)) {
         const Task T = E.t32[t];
         if (T.slot < 0) continue;                                       // unused entry
-        const SlotDesc &D = E.desc[T.slot];
-        const SlotState &S = E.st[T.slot];
-        const int ph = S.phase;
+        const int ph = E.st[T.slot].phase;
         if (ph != PH_CG && ph != PH_GM) continue;
-        const int n = D.n, sp = D.sp, it = S.it;
-        const long long nsp = (long long)n * sp;
-        const int r0 = T.r0, r1 = T.r1;
-        // operand source / destination and per-column scale
-        const float *src, *src2 = nullptr;
-        float *dst, *out;
-        if (ph == PH_CG) {
-            src = D.Rf;                                         // P = Rf + beta P'
-            src2 = it > 0 ? D.P + ((it + 1) & 1) * nsp : nullptr;
-            dst = D.P + (it & 1) * nsp;
-            out = D.Q;
-        } else {
-            src = D.W + (it & 1) * nsp;                         // V_k = W / h
-            dst = D.V + (long long)it * nsp;
-            out = D.W + ((it + 1) & 1) * nsp;
-        }
-        if (tid < 32) {
-            float sc = 0.0f;
-            if (tid < D.s && !S.colstop[tid])
-                sc = ph == PH_CG ? (float)S.beta[tid] : (float)(1.0 / S.hnorm[tid]);
-            colscale[tid] = sc;
+        switch (E.desc[T.slot].sp) {
+            case 4: prod32_task<4>(E, T, t, As, Ps, Red, colscale, colstop); break;
+            case 8: prod32_task<8>(E, T, t, As, Ps, Red, colscale, colstop); break;
+            case 16: prod32_task<16>(E, T, t, As, Ps, Red, colscale, colstop); break;
+            default: prod32_task<32>(E, T, t, As, Ps, Red, colscale, colstop); break;
         }
         __syncthreads();
-        float acc[32];
-#pragma unroll
-        for (int c = 0; c < 32; c++) acc[c] = 0.0f;
-        for (int k0 = 0; k0 < n; k0 += KC32) {
-            // A tile: rows r0..r0+127, cols k0..k0+31 (coalesced along k)
-            for (int e = tid; e < E_RB32 * KC32; e += P32_T) {
-                const int rr = e / KC32, kk = e % KC32;
-                const int gr = r0 + rr, gk = k0 + kk;
-                As[rr * AS32 + kk] = (gr < r1 && gk < n) ? D.A32[(long long)gr * D.ld32 + gk] : 0.0f;
-            }
-            // operand tile: rows k0..k0+31, all sp columns, transformed on the fly
-            for (int e = tid; e < KC32 * sp; e += P32_T) {
-                const int kk = e / sp, c = e % sp;
-                const int gk = k0 + kk;
-                float v = 0.0f;
-                if (gk < n && c < D.s) {
-                    const long long o = (long long)gk * sp + c;
-                    const bool stopped = S.colstop[c];
-                    if (ph == PH_CG) {
-                        v = stopped ? 0.0f : (src2 ? fmaf(colscale[c], src2[o], src[o]) : src[o]);
-                    } else {
-                        v = src[o] * colscale[c];
-                    }
-                    if (gk >= r0 && gk < r1) dst[o] = v;        // this task owns row gk
-                }
-                Ps[kk * 32 + c] = v;
-            }
-            __syncthreads();
-            if (row < r1 - r0) {
-#pragma unroll 4
-                for (int kk = kh; kk < KC32; kk += 2) {
-                    const float a = As[row * AS32 + kk];
-                    const float4 *p4 = reinterpret_cast<const float4 *>(Ps + kk * 32);
-#pragma unroll
-                    for (int c4 = 0; c4 < 8; c4++) {
-                        if (c4 * 4 < sp) {
-                            const float4 pv = p4[c4];
-                            acc[4 * c4 + 0] = fmaf(a, pv.x, acc[4 * c4 + 0]);
-                            acc[4 * c4 + 1] = fmaf(a, pv.y, acc[4 * c4 + 1]);
-                            acc[4 * c4 + 2] = fmaf(a, pv.z, acc[4 * c4 + 2]);
-                            acc[4 * c4 + 3] = fmaf(a, pv.w, acc[4 * c4 + 3]);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int c = 0; c < 32; c++) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
-        const int nrow = r1 - r0;
-        if (kh == 0 && row < nrow) {
-#pragma unroll
-            for (int c = 0; c < 32; c++)
-                if (c < sp) out[(long long)(r0 + row) * sp + c] = acc[c];
-        }
-        __syncthreads();
-        // partial dots over this task's rows: CG p.q; GMRES v_i.w for i <= it
-        const int nd = ph == PH_CG ? 1 : it + 1;
-        for (int i = 0; i < nd; i++) {
-            const float *vi = ph == PH_CG ? dst : D.V + (long long)i * nsp;
-            if (kh == 0) {
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    double v = 0.0;
-                    if (row < nrow && c < sp) v = (double)vi[(long long)(r0 + row) * sp + c] * (double)acc[c];
-                    Red[row * 33 + c] = v;
-                }
-            }
-            __syncthreads();
-            if (tid < 32) {
-                double sacc = 0.0;
-                for (int rr = 0; rr < nrow; rr++) sacc += Red[rr * 33 + tid];
-                E.part32[((size_t)t * E_PS + i) * 32 + tid] = sacc;
-            }
-            __syncthreads();
-        }
     }
 }
 
@@ -336,15 +443,16 @@ __global__ void __launch_bounds__(P32_T) eng_prod32_kernel(const EngineDev *Ep) 
 // eng_prod64: FP64 refinement residual R = B - A X of one 16-row task
 // ============================================================================
 __global__ void __launch_bounds__(P64_T) eng_prod64_kernel(const EngineDev *Ep) {
-    const EngineDev E = *Ep;
+    const EngineDev &E = *Ep;
     extern __shared__ __align__(16) unsigned char esm[];
     double *As = reinterpret_cast<double *>(esm);                       // [16][KC64 + 1]
     double *Xs = As + E_RB64 * (KC64 + 1);                              // [KC64][33]
     __shared__ double red[E_RB64][33];
+    __shared__ int claim_s;
     eng_count(E);
     const int tid = threadIdx.x;
     const int row = tid >> 4, kl = tid & 15;
-    for (int t = blockIdx.x; t < E.n64; t += gridDim.x) {
+    for (int t = claim(E.active + 6, &claim_s); t < E.n64; t = claim(E.active + 6, &claim_s)) {
         const Task T = E.t64[t];
         if (T.slot < 0) continue;                                       // unused entry
         const SlotDesc &D = E.desc[T.slot];
@@ -413,13 +521,14 @@ __global__ void __launch_bounds__(P64_T) eng_prod64_kernel(const EngineDev *Ep) 
 // eng_vec: vector updates of one 256-row task
 // ============================================================================
 __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
-    const EngineDev E = *Ep;
+    const EngineDev &E = *Ep;
     __shared__ double wsum[VEC_T / 32][32];
     __shared__ double hsm[E_MAXM + 1][32];
     __shared__ double colv_s[32];
+    __shared__ int claim_s;
     eng_count(E);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int t = blockIdx.x; t < E.nv; t += gridDim.x) {
+    for (int t = claim(E.active + 7, &claim_s); t < E.nv; t = claim(E.active + 7, &claim_s)) {
         const Task T = E.tv[t];
         if (T.slot < 0) continue;                                       // unused entry
         const SlotDesc &D = E.desc[T.slot];
@@ -456,15 +565,19 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
             }
         }
         __syncthreads();
+        if (ph == PH_START) {   // FP32 copy of this task's rows of A, a warp per row
+            for (int r = T.r0 + warp; r < T.r1; r += VEC_T / 32) {
+                const double *a = D.A64 + (long long)r * D.lda64;
+                float *a32 = D.A32 + (long long)r * D.ld32;
+                for (int k = lane; k < n; k += 32) a32[k] = __double2float_rn(a[k]);
+            }
+        }
         const long long ro = (long long)i * sp;
         double part[32];
 #pragma unroll
         for (int c = 0; c < 32; c++) part[c] = 0.0;
         if (mine) {
             if (ph == PH_START) {
-                const double *a = D.A64 + (long long)i * D.lda64;
-                float *a32 = D.A32 + (long long)i * D.ld32;
-                for (int k = 0; k < n; k++) a32[k] = __double2float_rn(a[k]);
 #pragma unroll
                 for (int c = 0; c < 32; c++) {
                     if (c < sp) {
@@ -550,7 +663,7 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
 // B (column-major, ldb) -> the slot's row-major n x sp block (zero padding).
 __global__ void eng_admit_kernel(const EngineDev *Ep, const double *const *Bsrc, const long long *ldb,
                                  int first, int count) {
-    const EngineDev E = *Ep;
+    const EngineDev &E = *Ep;
     for (int q = blockIdx.y; q < count; q += gridDim.y) {
         const int sl = first + q;
         const SlotDesc &D = E.desc[sl];
@@ -567,7 +680,7 @@ __global__ void eng_admit_kernel(const EngineDev *Ep, const double *const *Bsrc,
 // X (row-major) -> column-major destination (ldx).
 __global__ void eng_finish_kernel(const EngineDev *Ep, double *const *Xdst, const long long *ldx, int first,
                                   int count) {
-    const EngineDev E = *Ep;
+    const EngineDev &E = *Ep;
     for (int q = blockIdx.y; q < count; q += gridDim.y) {
         const int sl = first + q;
         const SlotDesc &D = E.desc[sl];
@@ -593,7 +706,8 @@ EngineKernels engine_kernels() {
     K.prod32_threads = P32_T;
     K.prod64_threads = P64_T;
     K.vec_threads = VEC_T;
-    K.prod32_smem = (size_t)E_RB32 * AS32 * 4 + KC32 * 32 * 4 + (size_t)E_RB32 * 33 * 8;
+    // transposed A chunk (+ padding), operand chunk, reduction scratch (P32_T x 4 doubles)
+    K.prod32_smem = (size_t)E_KC32 * (E_RB32 + 4) * 4 + E_KC32 * 32 * 4 + (size_t)E_RB32 * 32 / 4 * 8;
     K.prod64_smem = (size_t)E_RB64 * (KC64 + 1) * 8 + (size_t)KC64 * 33 * 8;
     return K;
 }

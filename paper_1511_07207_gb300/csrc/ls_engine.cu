@@ -11,6 +11,8 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -54,7 +56,7 @@ __global__ void eng_collect_kernel(const SlotDesc *desc, const SlotState *st, Sl
 // ---- buffer sizes ---------------------------------------------------------------
 SlotSizes slot_sizes(int n, int s, int method, int m) {
     SlotSizes z{};
-    z.sp = (s + 3) / 4 * 4;
+    z.sp = s <= 4 ? 4 : s <= 8 ? 8 : s <= 16 ? 16 : 32;   // the product kernel's widths
     z.ld32 = (n + 3) / 4 * 4;
     z.lda_stage = (n + 1) / 2 * 2;
     const size_t nsp = (size_t)n * z.sp;
@@ -218,10 +220,18 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
             else tab.push_back(t);
         }
     };
-    for (int q = 0; q < (int)hd.size(); q++) {
+    // packed tables list the costliest slots first (tasks are claimed in
+    // table order, so the long ones start early and the short ones fill in)
+    std::vector<int> order(hd.size());
+    for (int q = 0; q < (int)hd.size(); q++) order[q] = q;
+    if (!fixed_max_n)
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (double)hd[a].n * hd[a].n * hd[a].sp > (double)hd[b].n * hd[b].n * hd[b].sp;
+        });
+    for (int q : order) {
         SlotDesc &D = hd[q];
         const int n = D.n > 0 ? D.n : 0;
-        fill(h32, q, n, E_RB32, per32, fixed_max_n, D.t32, D.n32);
+        fill(h32, q, n, rb32(D.sp > 0 ? D.sp : 32), per32, fixed_max_n, D.t32, D.n32);
         fill(h64, q, n, E_RB64, per64, fixed_max_n, D.t64, D.n64);
         fill(hv, q, n, E_RBV, perv, fixed_max_n, D.tv, D.nv);
     }
@@ -310,8 +320,56 @@ int Engine::collect(int first, int count, std::vector<SlotResult> &out) {
     return map_cuda(e);
 }
 
+// LS_ENGINE_HOSTLOOP=1 runs the same kernels from a host loop instead of the
+// graph's while-node (the loop condition is read back every tick), which lets
+// profilers see each kernel; LS_ENGINE_HOSTLOOP=2 also times every kernel with
+// CUDA events and prints the totals to stderr.
 int Engine::run() {
-    return map_cuda(cudaGraphLaunch(exec, c->stream));
+    const char *env = getenv("LS_ENGINE_HOSTLOOP");
+    const int mode = env ? atoi(env) : 0;
+    if (mode <= 0) return map_cuda(cudaGraphLaunch(exec, c->stream));
+    hE.host_loop = 1;
+    cudaError_t e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
+    cudaGraphConditionalHandle none = 0;
+    const EngineDev *p = dE;
+    void *args_red[] = {(void *)&p, (void *)&none};
+    void *args[] = {(void *)&p};
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; i++) cudaEventCreate(&ev[i]);
+    double tot[4] = {0, 0, 0, 0};
+    long long ticks = 0;
+    int go = 1;
+    while (e == cudaSuccess && go) {
+        if (mode == 2) cudaEventRecord(ev[0], c->stream);
+        e = cudaLaunchKernel(K.red, dim3(cap_slots), dim3(K.red_threads), args_red, 0, c->stream);
+        if (mode == 2) cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(K.prod32, dim3(grid_prod), dim3(K.prod32_threads), args, K.prod32_smem, c->stream);
+        if (mode == 2) cudaEventRecord(ev[2], c->stream);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(K.prod64, dim3(grid_prod), dim3(K.prod64_threads), args, K.prod64_smem, c->stream);
+        if (mode == 2) cudaEventRecord(ev[3], c->stream);
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(K.vec, dim3(grid_vec), dim3(K.vec_threads), args, 0, c->stream);
+        if (mode == 2) cudaEventRecord(ev[4], c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&go, hE.active + 4, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (mode == 2 && e == cudaSuccess)
+            for (int i = 0; i < 4; i++) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+                tot[i] += ms;
+            }
+        ticks++;
+    }
+    for (int i = 0; i < 5; i++) cudaEventDestroy(ev[i]);
+    if (mode == 2)
+        fprintf(stderr, "engine ticks %lld  red %.3f ms  prod32 %.3f ms  prod64 %.3f ms  vec %.3f ms\n",
+                ticks, tot[0], tot[1], tot[2], tot[3]);
+    hE.host_loop = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
+    return map_cuda(e);
 }
 
 unsigned long long Engine::launches() {
@@ -366,7 +424,7 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
         x_dev[q] = is_device_ptr(S.X);
         total += z[q].bytes + (a_dev[q] ? 0 : z[q].stageA) + (b_dev[q] ? 0 : z[q].stageBX) +
                  (x_dev[q] ? 0 : z[q].stageBX);
-        n32 += (S.n + E_RB32 - 1) / E_RB32;
+        n32 += (S.n + rb32(z[q].sp) - 1) / rb32(z[q].sp);
         n64 += (S.n + E_RB64 - 1) / E_RB64;
         nv += (S.n + E_RBV - 1) / E_RBV;
     }

@@ -25,7 +25,8 @@ namespace lsi {
 
 constexpr int E_MAXS = LS_BATCH_MAX_RHS;   // right-hand sides per slot (32)
 constexpr int E_MAXM = 32;                 // GMRES restart length in the engine
-constexpr int E_RB32 = 128;                // rows per FP32 product task
+constexpr int E_RB32 = 256;                // rows per FP32 product task (any width)
+constexpr int E_KC32 = 32;                 // k per chunk of the FP32 product
 constexpr int E_RB64 = 16;                 // rows per FP64 residual task
 constexpr int E_RBV = 256;                 // rows per vector task
 constexpr int E_PS = E_MAXM + 2;           // partial-dot slots per FP32 product task
@@ -43,9 +44,13 @@ enum : int {
     PH_ADMIT = 8,     // just admitted: eng_red turns it into START (nothing to reduce yet)
 };
 
+// rows of one FP32 product task for a padded width sp (4, 8, 16 or 32):
+// tasks hold the same number of rows, i.e. the same bytes of A, for any sp
+__host__ __device__ constexpr int rb32(int) { return E_RB32; }
+
 struct SlotDesc {                // written at admission
     int n, s;                    // size and right-hand sides (s <= 32)
-    int sp;                      // row stride of the n x sp row-major blocks (multiple of 4)
+    int sp;                      // row stride of the n x sp row-major blocks: 4, 8, 16 or 32
     int method;                  // LS_METHOD_CG / LS_METHOD_GMRES
     int m;                       // GMRES restart (<= E_MAXM)
     int inner_iters;             // inner iterations per refinement step
@@ -107,6 +112,7 @@ struct EngineDev {               // pointers handed to every engine kernel
     double *partv;               // [taskv][32]
     int *active;                 // [0] count, [1] ticket, [2] last count, [3] ticks run
     int tick_limit;              // ticks per graph launch (loop control)
+    int host_loop;               // 1: no graph; eng_red writes the loop condition to active[4]
     unsigned long long *launches;
 };
 
