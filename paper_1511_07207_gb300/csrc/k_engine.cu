@@ -22,7 +22,6 @@ constexpr int RED_T = 64;
 constexpr int P32_T = 256;
 constexpr int P64_T = 256;
 constexpr int VEC_T = 256;
-constexpr int KC64 = 64;     // k chunk of the FP64 residual
 
 __device__ __forceinline__ void eng_count(const EngineDev &E) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(E.launches, 1ull);
@@ -440,89 +439,131 @@ __global__ void __launch_bounds__(P32_T, 2) eng_prod32_kernel(const EngineDev *E
 }
 
 // ============================================================================
-// eng_prod64: FP64 refinement residual R = B - A X of one 16-row task
+// eng_prod64: FP64 refinement residual R = B - A X of one 16-row task.
+// Thread (row, kl) handles every 16th k of its row for all right-hand sides;
+// the A and X chunks of the next 128 k are prefetched into registers.
 // ============================================================================
+constexpr int KC64 = 128;
+
+template <int SP>
+__device__ __forceinline__ void prod64_task(const EngineDev &E, const Task &T, int t, double *As,
+                                            double *Xs, double (*red)[33]) {
+    constexpr int XS = SP + 1;                  // odd stride: conflict-free column reads
+    constexpr int AV = E_RB64 * KC64 / P64_T;   // A doubles per thread per chunk (8)
+    constexpr int XV = KC64 * SP / P64_T;       // X doubles per thread per chunk
+    const SlotDesc &D = E.desc[T.slot];
+    const int n = D.n, s = D.s;
+    const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
+    const int tid = threadIdx.x, row = tid >> 4, kl = tid & 15;
+    const double *A = D.A64;
+    const long long lda = D.lda64;
+    const double *X = D.X;
+    double areg[AV], xreg[XV > 0 ? XV : 1];
+    auto prefetch = [&](int k0) {
+#pragma unroll
+        for (int v = 0; v < AV; v++) {
+            const int e = tid + v * P64_T;
+            const int rr = e / KC64, kk = e % KC64;
+            const int gr = r0 + rr, gk = k0 + kk;
+            areg[v] = (gr < r1 && gk < n) ? A[(long long)gr * lda + gk] : 0.0;
+        }
+#pragma unroll
+        for (int v = 0; v < XV; v++) {
+            const int e = tid + v * P64_T;
+            const int kk = e / SP, c = e % SP;
+            const int gk = k0 + kk;
+            xreg[v] = gk < n ? X[(long long)gk * SP + c] : 0.0;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int v = 0; v < AV; v++) {
+            const int e = tid + v * P64_T;
+            As[(e / KC64) * (KC64 + 1) + e % KC64] = areg[v];
+        }
+#pragma unroll
+        for (int v = 0; v < XV; v++) {
+            const int e = tid + v * P64_T;
+            Xs[(e / SP) * XS + e % SP] = xreg[v];
+        }
+    };
+    double acc[SP];
+#pragma unroll
+    for (int c = 0; c < SP; c++) acc[c] = 0.0;
+    prefetch(0);
+    for (int k0 = 0; k0 < n; k0 += KC64) {
+        store();
+        __syncthreads();
+        if (k0 + KC64 < n) prefetch(k0 + KC64);
+        if (row < nrow) {
+#pragma unroll 4
+            for (int i = 0; i < KC64 / 16; i++) {
+                const int kk = kl + 16 * i;
+                const double a = As[row * (KC64 + 1) + kk];
+                const double *xr = Xs + kk * XS;
+#pragma unroll
+                for (int c = 0; c < SP; c++)
+                    if (c < s) acc[c] = fma(a, xr[c], acc[c]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < SP; c++) {
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    }
+    if (kl == 0) {
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+            double v = 0.0;
+            if (c < SP && row < nrow) {
+                const long long o = (long long)(r0 + row) * SP + c;
+                const double rv = c < s ? D.B[o] - acc[c] : 0.0;
+                D.R[o] = rv;
+                v = rv * rv;
+            }
+            red[row][c] = v;
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {
+        double sacc = 0.0;
+        for (int rr = 0; rr < nrow; rr++) sacc += red[rr][tid];
+        E.part64[(size_t)t * 32 + tid] = sacc;
+    }
+}
+
 __global__ void __launch_bounds__(P64_T) eng_prod64_kernel(const EngineDev *Ep) {
     const EngineDev &E = *Ep;
     extern __shared__ __align__(16) unsigned char esm[];
     double *As = reinterpret_cast<double *>(esm);                       // [16][KC64 + 1]
-    double *Xs = As + E_RB64 * (KC64 + 1);                              // [KC64][33]
+    double *Xs = As + E_RB64 * (KC64 + 1);                              // [KC64][SP + 1]
     __shared__ double red[E_RB64][33];
     __shared__ int claim_s;
     eng_count(E);
-    const int tid = threadIdx.x;
-    const int row = tid >> 4, kl = tid & 15;
     for (int t = claim(E.active + 6, &claim_s); t < E.n64; t = claim(E.active + 6, &claim_s)) {
         const Task T = E.t64[t];
         if (T.slot < 0) continue;                                       // unused entry
-        const SlotDesc &D = E.desc[T.slot];
-        const SlotState &S = E.st[T.slot];
-        if (S.phase != PH_RESID) continue;
-        const int n = D.n, sp = D.sp;
-        const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
-        const int xs = sp + 1;                                          // odd stride: no conflicts
-        double acc[32];
-#pragma unroll
-        for (int c = 0; c < 32; c++) acc[c] = 0.0;
-        for (int k0 = 0; k0 < n; k0 += KC64) {
-            for (int e = tid; e < E_RB64 * KC64; e += P64_T) {
-                const int rr = e / KC64, kk = e % KC64;
-                const int gr = r0 + rr, gk = k0 + kk;
-                As[rr * (KC64 + 1) + kk] = (gr < r1 && gk < n) ? D.A64[(long long)gr * D.lda64 + gk] : 0.0;
-            }
-            for (int e = tid; e < KC64 * sp; e += P64_T) {
-                const int kk = e / sp, c = e % sp;
-                const int gk = k0 + kk;
-                Xs[kk * xs + c] = gk < n ? D.X[(long long)gk * sp + c] : 0.0;
-            }
-            __syncthreads();
-            if (row < nrow) {
-#pragma unroll
-                for (int i = 0; i < KC64 / 16; i++) {
-                    const int kk = kl + 16 * i;
-                    const double a = As[row * (KC64 + 1) + kk];
-                    const double *xr = Xs + kk * xs;
-#pragma unroll
-                    for (int c = 0; c < 32; c++)
-                        if (c < sp) acc[c] = fma(a, xr[c], acc[c]);
-                }
-            }
-            __syncthreads();
+        if (E.st[T.slot].phase != PH_RESID) continue;
+        switch (E.desc[T.slot].sp) {
+            case 4: prod64_task<4>(E, T, t, As, Xs, red); break;
+            case 8: prod64_task<8>(E, T, t, As, Xs, red); break;
+            case 16: prod64_task<16>(E, T, t, As, Xs, red); break;
+            default: prod64_task<32>(E, T, t, As, Xs, red); break;
         }
-#pragma unroll
-        for (int c = 0; c < 32; c++) {
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-        }
-        if (kl == 0) {
-#pragma unroll
-            for (int c = 0; c < 32; c++) {
-                double v = 0.0;
-                if (row < nrow && c < sp) {
-                    const long long o = (long long)(r0 + row) * sp + c;
-                    const double rv = D.B[o] - acc[c];
-                    D.R[o] = rv;
-                    v = rv * rv;
-                }
-                red[row][c] = v;
-            }
-        }
-        __syncthreads();
-        if (tid < 32) {
-            double sacc = 0.0;
-            for (int rr = 0; rr < nrow; rr++) sacc += red[rr][tid];
-            E.part64[(size_t)t * 32 + tid] = sacc;
-        }
-        __syncthreads();
     }
 }
 
 // ============================================================================
-// eng_vec: vector updates of one 256-row task
+// eng_vec: vector updates of one 256-row task.  The task's n x sp block is
+// walked as a flat array: thread t always sees column t % sp (sp divides the
+// block size), so loads are coalesced and each thread's partial sum belongs
+// to one column.
 // ============================================================================
 __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
     const EngineDev &E = *Ep;
-    __shared__ double wsum[VEC_T / 32][32];
+    __shared__ double psum[VEC_T];
     __shared__ double hsm[E_MAXM + 1][32];
     __shared__ double colv_s[32];
     __shared__ int claim_s;
@@ -537,8 +578,6 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
         if (ph != PH_START && ph != PH_INIT && ph != PH_CG && ph != PH_GM && ph != PH_UPDATE) continue;
         const int n = D.n, s = D.s, sp = D.sp, it = S.it;
         const long long nsp = (long long)n * sp;
-        const int i = T.r0 + tid;
-        const bool mine = i < T.r1;
         // per-column scalars needed by this phase
         if (tid < 32) {
             double cv = 0.0;
@@ -549,7 +588,7 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                         pq += E.part32[((size_t)u * E_PS + 0) * 32 + tid];
                     cv = (S.colstop[tid] || !(pq > 0.0)) ? 0.0 : S.rho[tid] / pq;
                 } else if (ph == PH_INIT || ph == PH_UPDATE) {
-                    cv = S.rn[tid];
+                    cv = (ph == PH_UPDATE && S.conv[tid]) ? 0.0 : S.rn[tid];
                 }
             }
             colv_s[tid] = cv;
@@ -564,7 +603,6 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                 hsm[ii][c] = hs;
             }
         }
-        __syncthreads();
         if (ph == PH_START) {   // FP32 copy of this task's rows of A, a warp per row
             for (int r = T.r0 + warp; r < T.r1; r += VEC_T / 32) {
                 const double *a = D.A64 + (long long)r * D.lda64;
@@ -572,84 +610,70 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                 for (int k = lane; k < n; k += 32) a32[k] = __double2float_rn(a[k]);
             }
         }
-        const long long ro = (long long)i * sp;
-        double part[32];
-#pragma unroll
-        for (int c = 0; c < 32; c++) part[c] = 0.0;
-        if (mine) {
-            if (ph == PH_START) {
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    if (c < sp) {
-                        const double b = D.B[ro + c];
-                        D.X[ro + c] = 0.0;
-                        D.R[ro + c] = b;
-                        part[c] = b * b;
-                    }
-                }
-            } else if (ph == PH_INIT) {
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    if (c < sp) {
-                        float f = 0.0f;
-                        if (c < s && !S.conv[c]) f = (float)(D.R[ro + c] / colv_s[c]);
-                        D.Rf[ro + c] = f;
-                        D.Z[ro + c] = 0.0f;
-                        if (D.method != LS_METHOD_CG) D.W[ro + c] = f;     // W buffer 0
-                        part[c] = (double)f * (double)f;
-                    }
-                }
-            } else if (ph == PH_CG) {
-                const float *p = D.P + (it & 1) * nsp;
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    if (c < sp) {
-                        const float al = (float)colv_s[c];
-                        D.Z[ro + c] = fmaf(al, p[ro + c], D.Z[ro + c]);
-                        const float rv = fmaf(-al, D.Q[ro + c], D.Rf[ro + c]);
-                        D.Rf[ro + c] = rv;
-                        part[c] = (double)rv * (double)rv;
-                    }
-                }
-            } else if (ph == PH_GM) {
-                float *w = D.W + ((it + 1) & 1) * nsp;
-#pragma unroll
-                for (int c = 0; c < 32; c++) {
-                    if (c < sp) {
-                        double wv = w[ro + c];
-                        for (int q = 0; q <= it; q++)
-                            wv -= hsm[q][c] * (double)D.V[(long long)q * nsp + ro + c];
-                        const float wf = (float)wv;
-                        w[ro + c] = wf;
-                        part[c] = (double)wf * (double)wf;
-                    }
-                }
-            } else if (ph == PH_UPDATE) {
-                for (int c = 0; c < s; c++) {
-                    if (S.conv[c]) continue;
+        __syncthreads();
+        const long long e0 = (long long)T.r0 * sp, e1 = (long long)T.r1 * sp;
+        const int c = tid % sp;                                        // fixed for this thread
+        const bool live = c < s;
+        double part = 0.0;
+        if (ph == PH_START) {
+            for (long long e = e0 + tid; e < e1; e += VEC_T) {
+                const double b = D.B[e];
+                D.X[e] = 0.0;
+                D.R[e] = b;
+                part += b * b;
+            }
+        } else if (ph == PH_INIT) {
+            const bool on = live && !S.conv[c];
+            const double rn = colv_s[c];
+            for (long long e = e0 + tid; e < e1; e += VEC_T) {
+                const float f = on ? (float)(D.R[e] / rn) : 0.0f;
+                D.Rf[e] = f;
+                D.Z[e] = 0.0f;
+                if (D.method != LS_METHOD_CG) D.W[e] = f;               // W buffer 0
+                part += (double)f * (double)f;
+            }
+        } else if (ph == PH_CG) {
+            const float al = (float)colv_s[c];
+            const float *p = D.P + (it & 1) * nsp;
+            for (long long e = e0 + tid; e < e1; e += VEC_T) {
+                D.Z[e] = fmaf(al, p[e], D.Z[e]);
+                const float rv = fmaf(-al, D.Q[e], D.Rf[e]);
+                D.Rf[e] = rv;
+                part += (double)rv * (double)rv;
+            }
+        } else if (ph == PH_GM) {
+            float *w = D.W + ((it + 1) & 1) * nsp;
+            for (long long e = e0 + tid; e < e1; e += VEC_T) {
+                double wv = w[e];
+                for (int q = 0; q <= it; q++) wv -= hsm[q][c] * (double)D.V[(long long)q * nsp + e];
+                const float wf = (float)wv;
+                w[e] = wf;
+                part += (double)wf * (double)wf;
+            }
+        } else if (ph == PH_UPDATE) {
+            const double rn = colv_s[c];
+            if (live && rn != 0.0) {
+                const int kj = D.method == LS_METHOD_CG ? 0 : (int)S.alpha[c];
+                for (long long e = e0 + tid; e < e1; e += VEC_T) {
                     double d;
                     if (D.method == LS_METHOD_CG) {
-                        d = (double)D.Z[ro + c];
+                        d = (double)D.Z[e];
                     } else {
                         d = 0.0;
-                        const int kj = (int)S.alpha[c];
-                        for (int q = 0; q < kj; q++) d += S.yv[c][q] * (double)D.V[(long long)q * nsp + ro + c];
+                        for (int q = 0; q < kj; q++) d += S.yv[c][q] * (double)D.V[(long long)q * nsp + e];
                     }
-                    D.X[ro + c] += colv_s[c] * d;
+                    D.X[e] += rn * d;
                 }
             }
         }
         // partial column sums over this task's rows (fixed order)
         if (ph != PH_UPDATE) {
-#pragma unroll
-            for (int c = 0; c < 32; c++) {
-                const double v = warp_sum(part[c]);
-                if (lane == 0) wsum[warp][c] = v;
-            }
+            psum[tid] = part;
             __syncthreads();
             if (tid < 32) {
                 double sacc = 0.0;
-                for (int w = 0; w < VEC_T / 32; w++) sacc += wsum[w][tid];
+                if (tid < sp)
+                    for (int q = tid; q < VEC_T; q += sp) sacc += psum[q];
                 E.partv[(size_t)t * 32 + tid] = sacc;
             }
         }
