@@ -1,7 +1,8 @@
 // k_engine.cu -- kernels of the batched / served solve engine (ls_engine.h).
 //
 // Per slot (one dense system, s right-hand sides solved column by column):
-//   refinement (FP64): R = B - A X; stop when every ||R_j|| <= rtol ||B_j||;
+//   refinement (FP64 accuracy): R = B - A X; stop when every
+//     ||R_j|| <= rtol ||B_j||;
 //   inner solve (FP32 on the FP32 copy of A) of A z = R_j / ||R_j||:
 //     SPD systems: conjugate gradient (paper: CG paragraph), the columns sharing
 //       one block product Q = Ahat P per step;
@@ -19,8 +20,7 @@
 namespace lsi {
 
 constexpr int RED_T = 64;
-constexpr int P32_T = 256;
-constexpr int P64_T = 256;
+constexpr int P32_T = 256;            // threads of eng_prod (both task kinds)
 constexpr int VEC_T = 256;
 
 __device__ __forceinline__ void eng_count(const EngineDev &E) {
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
         } else if (ph == PH_CG) {
             if (!S.colstop[j]) {
                 double pq = 0.0, rr = 0.0;
-                for (int t = D.t32; t < D.t32 + D.n32; t++)
-                    pq += E.part32[((size_t)t * E_PS + 0) * 32 + j];
+                for (int b = D.b32; b < D.b32 + D.nb32; b++)
+                    pq += E.part32[((size_t)b * E_PS + 0) * 32 + j];
                 for (int t = D.tv; t < D.tv + D.nv; t++) rr += E.partv[(size_t)t * 32 + j];
                 if (!(pq > 0.0) || !isfinite(rr)) {
                     S.colstop[j] = 1;              // breakdown: keep the iterate
@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
                 double *Hk = G.H[j] + (size_t)k * (E_MAXM + 1);
                 for (int i = 0; i <= k; i++) {
                     double hs = 0.0;
-                    for (int t = D.t32; t < D.t32 + D.n32; t++)
-                        hs += E.part32[((size_t)t * E_PS + i) * 32 + j];
+                    for (int b = D.b32; b < D.b32 + D.nb32; b++)
+                        hs += E.part32[((size_t)b * E_PS + i) * 32 + j];
                     Hk[i] = hs;
                 }
                 double w2 = 0.0;
@@ -214,22 +214,25 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
             E.active[0] = 0;
             E.active[1] = 0;
             E.active[2] = total;
-            E.active[5] = 0;   // task claim counters of prod32 / prod64 / vec
-            E.active[6] = 0;
+            E.active[5] = 0;   // task claim counters of prod / vec
             E.active[7] = 0;
         }
     }
 }
 
 // ============================================================================
-// eng_prod32: FP32 block product Y = Ahat P of one task (256 rows, all sp
-// columns), register-blocked: each thread owns an (sp/4)-row x 4-column tile
-// of Y.  The A chunk (32 columns of the task's rows) sits transposed in
-// shared memory; the next chunk is prefetched into registers meanwhile.
+// eng_prod, FP32 block product task: Y = Ahat P for 256 rows and the task's
+// K chunk of up to 512 columns of A, all sp columns, register-blocked: each
+// thread owns an (sp/4)-row x 4-column tile of Y.  The A chunk (32 columns of
+// the task's rows) sits transposed in shared memory; the next chunk is
+// prefetched into registers meanwhile.  When a row block has several K
+// chunks, each task stores its partial product and the last one to finish
+// sums them in chunk order (so the result does not depend on which task came
+// last) and runs the epilogue: Y rows and partial dots.
 // ============================================================================
 template <int SP>
-__device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, int t, float *As,
-                                            float *Ps, double *Red, float *colscale, int *colstop) {
+__device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, float *As, float *Ps,
+                                            double *Red, float *colscale, int *colstop, int *flag_s) {
     constexpr int RB = E_RB32, KC = E_KC32;
     constexpr int RPT = SP / 4;                 // rows per thread
     constexpr int NCG = SP / 4;                 // column groups of 4
@@ -237,6 +240,7 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, i
     constexpr int AV = RB * KC / 4 / P32_T;     // float4 loads of A per thread per chunk (8)
     constexpr int PV = (KC * SP + P32_T - 1) / P32_T;
     static_assert((RB / RPT) * NCG == P32_T, "thread grid");
+    static_assert(E_KS32 % KC == 0 && E_KS32 % RB == 0, "K chunks hold whole row blocks");
     const SlotDesc &D = E.desc[T.slot];
     const SlotState &S = E.st[T.slot];
     const int ph = S.phase;
@@ -332,11 +336,11 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, i
     for (int r = 0; r < RPT; r++)
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[r][c] = 0.0f;
-    prefetch(0);
-    for (int k0 = 0; k0 < n; k0 += KC) {
+    prefetch(T.k0);
+    for (int k0 = T.k0; k0 < T.k1; k0 += KC) {
         store();
         __syncthreads();
-        if (k0 + KC < n) prefetch(k0 + KC);                      // overlaps with the math below
+        if (k0 + KC < T.k1) prefetch(k0 + KC);                  // overlaps with the math below
 #pragma unroll 8
         for (int kk = 0; kk < KC; kk++) {
             float av[RPT];
@@ -366,7 +370,46 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, i
         }
         __syncthreads();
     }
-    // Y rows of this task
+    const int kc32 = (n + E_KS32 - 1) / E_KS32;
+    if (kc32 > 1) {
+        // publish this chunk's partial product; the last task of the row block
+        // adds all chunks in chunk order
+        float *yk = D.Yk + (long long)T.kc * nsp;
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            const int row = rg * RPT + r;
+            if (row < nrow)
+                __stcg(reinterpret_cast<float4 *>(yk + (long long)(r0 + row) * SP + cg * 4),
+                       make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
+        }
+        __threadfence();
+        __syncthreads();
+        const int rbl = r0 / E_RB32;
+        if (tid == 0) *flag_s = atomicAdd(D.ticket + rbl, 1) == kc32 - 1;
+        __syncthreads();
+        if (!*flag_s) return;
+        __threadfence();
+        if (tid == 0) D.ticket[rbl] = 0;                        // ready for the next tick
+#pragma unroll
+        for (int r = 0; r < RPT; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[r][c] = 0.0f;
+        for (int q = 0; q < kc32; q++) {
+            const float *yq = D.Yk + (long long)q * nsp;
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                const int row = rg * RPT + r;
+                if (row < nrow) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(yq + (long long)(r0 + row) * SP + cg * 4));
+                    acc[r][0] += v.x;
+                    acc[r][1] += v.y;
+                    acc[r][2] += v.z;
+                    acc[r][3] += v.w;
+                }
+            }
+        }
+    }
+    // Y rows of this row block
 #pragma unroll
     for (int r = 0; r < RPT; r++) {
         const int row = rg * RPT + r;
@@ -374,7 +417,8 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, i
             *reinterpret_cast<float4 *>(out + (long long)(r0 + row) * SP + cg * 4) =
                 make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
     }
-    // partial dots over this task's rows: CG p.q; GMRES v_i.w for i <= it
+    // partial dots over this row block: CG p.q; GMRES v_i.w for i <= it
+    // (the new direction's rows may come from another task: read through L2)
     const int nd = ph == PH_CG ? 1 : it + 1;
     constexpr int NRG = RB / RPT;               // row groups
     constexpr int NG = P32_T / SP;              // second-level groups per column
@@ -385,7 +429,7 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, i
         for (int r = 0; r < RPT; r++) {
             const int row = rg * RPT + r;
             if (row < nrow) {
-                const float4 v = *reinterpret_cast<const float4 *>(vi + (long long)(r0 + row) * SP + cg * 4);
+                const float4 v = __ldcg(reinterpret_cast<const float4 *>(vi + (long long)(r0 + row) * SP + cg * 4));
                 pc[0] += (double)v.x * acc[r][0];
                 pc[1] += (double)v.y * acc[r][1];
                 pc[2] += (double)v.z * acc[r][2];
@@ -407,151 +451,209 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, i
             double sacc = 0.0;
             if (tid < SP)
                 for (int g = 0; g < NG; g++) sacc += Red[g * SP + tid];
-            E.part32[((size_t)t * E_PS + i) * 32 + tid] = sacc;
-        }
-        __syncthreads();
-    }
-}
-
-__global__ void __launch_bounds__(P32_T, 2) eng_prod32_kernel(const EngineDev *Ep) {
-    const EngineDev &E = *Ep;
-    extern __shared__ __align__(16) unsigned char esm[];
-    float *As = reinterpret_cast<float *>(esm);                         // [KC][RB + 4]
-    float *Ps = As + E_KC32 * (E_RB32 + 4);                             // [KC][SP]
-    double *Red = reinterpret_cast<double *>(Ps + E_KC32 * 32);         // [row groups][SP]
-    __shared__ float colscale[32];
-    __shared__ int colstop[32];
-    __shared__ int claim_s;
-    eng_count(E);
-    for (int t = claim(E.active + 5, &claim_s); t < E.n32; t = claim(E.active + 5, &claim_s)) {
-        const Task T = E.t32[t];
-        if (T.slot < 0) continue;                                       // unused entry
-        const int ph = E.st[T.slot].phase;
-        if (ph != PH_CG && ph != PH_GM) continue;
-        switch (E.desc[T.slot].sp) {
-            case 4: prod32_task<4>(E, T, t, As, Ps, Red, colscale, colstop); break;
-            case 8: prod32_task<8>(E, T, t, As, Ps, Red, colscale, colstop); break;
-            case 16: prod32_task<16>(E, T, t, As, Ps, Red, colscale, colstop); break;
-            default: prod32_task<32>(E, T, t, As, Ps, Red, colscale, colstop); break;
+            E.part32[((size_t)T.rb * E_PS + i) * 32 + tid] = sacc;
         }
         __syncthreads();
     }
 }
 
 // ============================================================================
-// eng_prod64: FP64 refinement residual R = B - A X of one 16-row task.
-// Thread (row, kl) handles every 16th k of its row for all right-hand sides;
-// the A and X chunks of the next 128 k are prefetched into registers.
+// eng_prod, refinement residual task: R = B - A X for 8 rows, to about FP64
+// accuracy on the FP32 pipe.  A = A32 + A32lo and X = Xh + Xl are fp32 pairs;
+// each term a x = ah xh + ah xl + al xh (+ al xl, below 2^-48 |a x|, dropped)
+// is accumulated in a (hi, lo) pair: ah xh = p + e exactly (product error by
+// FMA), hi += p exactly with the rounding error moved to lo (two-sum, Knuth),
+// lo also takes e and the cross terms.  Warp w owns row w, lane l the k = l
+// (mod 32) part of it; the pairs are reduced across the warp in the same
+// arithmetic and the total is formed in FP64.
 // ============================================================================
-constexpr int KC64 = 128;
+struct DS {
+    float h, l;
+};
+
+// (hi, lo) + (hi, lo): the high parts by two-sum, all errors into lo.
+__device__ __forceinline__ DS ds_add(DS a, DS b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bv = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
+    return DS{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+
+__device__ __forceinline__ DS ds_shfl_xor(DS v, int o) {
+    return DS{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+
+// Butterfly transpose-reduction over the warp: each round a lane keeps half of
+// its columns and adds the partner's copy of them; afterwards lane l holds the
+// warp total of column l >> (5 - log2 N0).
+template <int N, int OFF, int N0>
+__device__ __forceinline__ void ds_butterfly(DS (&acc)[N0], int lane) {
+    if constexpr (OFF >= 1) {
+        if constexpr (N > 1) {
+            constexpr int H = N / 2;
+            const bool upper = (lane & OFF) != 0;
+#pragma unroll
+            for (int i = 0; i < H; i++) {
+                const DS send = upper ? acc[i] : acc[i + H];
+                const DS keep = upper ? acc[i + H] : acc[i];
+                acc[i] = ds_add(keep, ds_shfl_xor(send, OFF));
+            }
+            ds_butterfly<H, OFF / 2>(acc, lane);
+        } else {
+            acc[0] = ds_add(acc[0], ds_shfl_xor(acc[0], OFF));
+            ds_butterfly<1, OFF / 2>(acc, lane);
+        }
+    }
+}
+
+template <int N>
+__host__ __device__ constexpr int ilog2() { return N <= 1 ? 0 : 1 + ilog2<N / 2>(); }
 
 template <int SP>
-__device__ __forceinline__ void prod64_task(const EngineDev &E, const Task &T, int t, double *As,
-                                            double *Xs, double (*red)[33]) {
+__device__ __forceinline__ void res_task(const EngineDev &E, const Task &T, int t, float *sm,
+                                         double (*red)[33]) {
+    constexpr int KC = 1024 / SP;               // k per chunk: 32 terms per thread per chunk
+    constexpr int AP = KC + 1;                  // padded row stride of the A chunk
     constexpr int XS = SP + 1;                  // odd stride: conflict-free column reads
-    constexpr int AV = E_RB64 * KC64 / P64_T;   // A doubles per thread per chunk (8)
-    constexpr int XV = KC64 * SP / P64_T;       // X doubles per thread per chunk
+    constexpr int AV = E_RB64 * KC / P32_T;     // A floats (each of hi / lo) per thread per chunk
+    constexpr int XV = KC * SP / P32_T;         // X floats (each of hi / lo) per thread per chunk
+    static_assert(E_RB64 * 32 == P32_T, "a warp per row");
+    float *Ah = sm, *Al = Ah + E_RB64 * AP, *Xh = Al + E_RB64 * AP, *Xl = Xh + KC * XS;
     const SlotDesc &D = E.desc[T.slot];
     const int n = D.n, s = D.s;
     const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
-    const int tid = threadIdx.x, row = tid >> 4, kl = tid & 15;
-    const double *A = D.A64;
-    const long long lda = D.lda64;
-    const double *X = D.X;
-    double areg[AV], xreg[XV > 0 ? XV : 1];
+    const int tid = threadIdx.x, row = tid >> 5, lane = tid & 31;
+    const float *A = D.A32, *Alo = D.A32lo, *XH = D.Xh, *XL = D.Xl;
+    const long long lda = D.ld32;
+    float ahr[AV], alr[AV], xhr[XV], xlr[XV];
     auto prefetch = [&](int k0) {
 #pragma unroll
         for (int v = 0; v < AV; v++) {
-            const int e = tid + v * P64_T;
-            const int rr = e / KC64, kk = e % KC64;
+            const int e = tid + v * P32_T;
+            const int rr = e / KC, kk = e % KC;
             const int gr = r0 + rr, gk = k0 + kk;
-            areg[v] = (gr < r1 && gk < n) ? A[(long long)gr * lda + gk] : 0.0;
+            const bool in = gr < r1 && gk < n;
+            const long long o = (long long)gr * lda + gk;
+            ahr[v] = in ? A[o] : 0.0f;
+            alr[v] = in ? Alo[o] : 0.0f;
         }
 #pragma unroll
         for (int v = 0; v < XV; v++) {
-            const int e = tid + v * P64_T;
-            const int kk = e / SP, c = e % SP;
-            const int gk = k0 + kk;
-            xreg[v] = gk < n ? X[(long long)gk * SP + c] : 0.0;
+            const int e = tid + v * P32_T;             // the chunk is contiguous: rows k0.. of n x SP
+            const bool in = k0 + e / SP < n;
+            const long long o = (long long)k0 * SP + e;
+            xhr[v] = in ? XH[o] : 0.0f;
+            xlr[v] = in ? XL[o] : 0.0f;
         }
     };
     auto store = [&]() {
 #pragma unroll
         for (int v = 0; v < AV; v++) {
-            const int e = tid + v * P64_T;
-            As[(e / KC64) * (KC64 + 1) + e % KC64] = areg[v];
+            const int e = tid + v * P32_T;
+            Ah[(e / KC) * AP + e % KC] = ahr[v];
+            Al[(e / KC) * AP + e % KC] = alr[v];
         }
 #pragma unroll
         for (int v = 0; v < XV; v++) {
-            const int e = tid + v * P64_T;
-            Xs[(e / SP) * XS + e % SP] = xreg[v];
+            const int e = tid + v * P32_T;
+            Xh[(e / SP) * XS + e % SP] = xhr[v];
+            Xl[(e / SP) * XS + e % SP] = xlr[v];
         }
     };
-    double acc[SP];
+    DS acc[SP];
 #pragma unroll
-    for (int c = 0; c < SP; c++) acc[c] = 0.0;
+    for (int c = 0; c < SP; c++) acc[c] = DS{0.0f, 0.0f};
     prefetch(0);
-    for (int k0 = 0; k0 < n; k0 += KC64) {
+    for (int k0 = 0; k0 < n; k0 += KC) {
         store();
         __syncthreads();
-        if (k0 + KC64 < n) prefetch(k0 + KC64);
+        if (k0 + KC < n) prefetch(k0 + KC);
         if (row < nrow) {
-#pragma unroll 4
-            for (int i = 0; i < KC64 / 16; i++) {
-                const int kk = kl + 16 * i;
-                const double a = As[row * (KC64 + 1) + kk];
-                const double *xr = Xs + kk * XS;
 #pragma unroll
-                for (int c = 0; c < SP; c++)
-                    if (c < s) acc[c] = fma(a, xr[c], acc[c]);
+            for (int i = 0; i < KC / 32; i++) {
+                const int kk = lane + 32 * i;
+                const float ah = Ah[row * AP + kk], al = Al[row * AP + kk];
+                const float *xh = Xh + kk * XS, *xl = Xl + kk * XS;
+#pragma unroll
+                for (int c = 0; c < SP; c++) {
+                    if (c < s) {
+                        const float xhc = xh[c];
+                        const float p = __fmul_rn(ah, xhc);
+                        const float pe = fmaf(ah, xhc, -p);             // ah xh - p, exact
+                        const float tc = fmaf(al, xhc, fmaf(ah, xl[c], pe));
+                        const float sh = __fadd_rn(acc[c].h, p);
+                        const float bv = __fsub_rn(sh, acc[c].h);
+                        const float er = __fadd_rn(__fsub_rn(acc[c].h, __fsub_rn(sh, bv)), __fsub_rn(p, bv));
+                        acc[c].h = sh;
+                        acc[c].l = __fadd_rn(acc[c].l, __fadd_rn(tc, er));
+                    }
+                }
             }
         }
         __syncthreads();
     }
-#pragma unroll
-    for (int c = 0; c < SP; c++) {
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-    }
-    if (kl == 0) {
-#pragma unroll
-        for (int c = 0; c < 32; c++) {
-            double v = 0.0;
-            if (c < SP && row < nrow) {
-                const long long o = (long long)(r0 + row) * SP + c;
-                const double rv = c < s ? D.B[o] - acc[c] : 0.0;
-                D.R[o] = rv;
-                v = rv * rv;
-            }
-            red[row][c] = v;
+    ds_butterfly<SP, 16>(acc, lane);
+    constexpr int LG = ilog2<SP>();
+    if ((lane & ((32 >> LG) - 1)) == 0) {
+        const int c = lane >> (5 - LG);
+        double v = 0.0;
+        if (row < nrow) {
+            const long long o = (long long)(r0 + row) * SP + c;
+            const double rv = c < s ? D.B[o] - ((double)acc[0].h + (double)acc[0].l) : 0.0;
+            D.R[o] = rv;
+            v = rv * rv;
         }
+        red[row][c] = v;
     }
     __syncthreads();
     if (tid < 32) {
         double sacc = 0.0;
-        for (int rr = 0; rr < nrow; rr++) sacc += red[rr][tid];
+        if (tid < SP)
+            for (int rr = 0; rr < nrow; rr++) sacc += red[rr][tid];
         E.part64[(size_t)t * 32 + tid] = sacc;
     }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(P64_T) eng_prod64_kernel(const EngineDev *Ep) {
+// One queue per tick: the refinement-residual tasks first, then the FP32
+// product tasks; tasks of slots in other phases are skipped.
+__global__ void __launch_bounds__(P32_T, 2) eng_prod_kernel(const EngineDev *Ep) {
     const EngineDev &E = *Ep;
     extern __shared__ __align__(16) unsigned char esm[];
-    double *As = reinterpret_cast<double *>(esm);                       // [16][KC64 + 1]
-    double *Xs = As + E_RB64 * (KC64 + 1);                              // [KC64][SP + 1]
-    __shared__ double red[E_RB64][33];
-    __shared__ int claim_s;
+    float *As = reinterpret_cast<float *>(esm);                         // [KC][RB + 4]
+    float *Ps = As + E_KC32 * (E_RB32 + 4);                             // [KC][SP]
+    double *Red = reinterpret_cast<double *>(Ps + E_KC32 * 32);         // [row groups][SP]
+    __shared__ double red64[E_RB64][33];
+    __shared__ float colscale[32];
+    __shared__ int colstop[32];
+    __shared__ int claim_s, flag_s;
     eng_count(E);
-    for (int t = claim(E.active + 6, &claim_s); t < E.n64; t = claim(E.active + 6, &claim_s)) {
-        const Task T = E.t64[t];
-        if (T.slot < 0) continue;                                       // unused entry
-        if (E.st[T.slot].phase != PH_RESID) continue;
-        switch (E.desc[T.slot].sp) {
-            case 4: prod64_task<4>(E, T, t, As, Xs, red); break;
-            case 8: prod64_task<8>(E, T, t, As, Xs, red); break;
-            case 16: prod64_task<16>(E, T, t, As, Xs, red); break;
-            default: prod64_task<32>(E, T, t, As, Xs, red); break;
+    const int total = E.n64 + E.n32;
+    for (int u = claim(E.active + 5, &claim_s); u < total; u = claim(E.active + 5, &claim_s)) {
+        if (u < E.n64) {
+            const Task T = E.t64[u];
+            if (T.slot < 0) continue;                                   // unused entry
+            if (E.st[T.slot].phase != PH_RESID) continue;
+            float *sm = reinterpret_cast<float *>(esm);
+            switch (E.desc[T.slot].sp) {
+                case 4: res_task<4>(E, T, u, sm, red64); break;
+                case 8: res_task<8>(E, T, u, sm, red64); break;
+                case 16: res_task<16>(E, T, u, sm, red64); break;
+                default: res_task<32>(E, T, u, sm, red64); break;
+            }
+        } else {
+            const Task T = E.t32[u - E.n64];
+            if (T.slot < 0) continue;
+            const int ph = E.st[T.slot].phase;
+            if (ph != PH_CG && ph != PH_GM) continue;
+            switch (E.desc[T.slot].sp) {
+                case 4: prod32_task<4>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
+                case 8: prod32_task<8>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
+                case 16: prod32_task<16>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
+                default: prod32_task<32>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -584,7 +686,7 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
             if (tid < s) {
                 if (ph == PH_CG) {
                     double pq = 0.0;
-                    for (int u = D.t32; u < D.t32 + D.n32; u++)
+                    for (int u = D.b32; u < D.b32 + D.nb32; u++)
                         pq += E.part32[((size_t)u * E_PS + 0) * 32 + tid];
                     cv = (S.colstop[tid] || !(pq > 0.0)) ? 0.0 : S.rho[tid] / pq;
                 } else if (ph == PH_INIT || ph == PH_UPDATE) {
@@ -598,17 +700,25 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                 const int ii = e / 32, c = e % 32;
                 double hs = 0.0;
                 if (c < s && !S.colstop[c])
-                    for (int u = D.t32; u < D.t32 + D.n32; u++)
+                    for (int u = D.b32; u < D.b32 + D.nb32; u++)
                         hs += E.part32[((size_t)u * E_PS + ii) * 32 + c];
                 hsm[ii][c] = hs;
             }
         }
-        if (ph == PH_START) {   // FP32 copy of this task's rows of A, a warp per row
+        if (ph == PH_START) {   // A = A32 + A32lo for this task's rows, a warp per row
             for (int r = T.r0 + warp; r < T.r1; r += VEC_T / 32) {
                 const double *a = D.A64 + (long long)r * D.lda64;
                 float *a32 = D.A32 + (long long)r * D.ld32;
-                for (int k = lane; k < n; k += 32) a32[k] = __double2float_rn(a[k]);
+                float *alo = D.A32lo + (long long)r * D.ld32;
+                for (int k = lane; k < n; k += 32) {
+                    const double v = a[k];
+                    const float hi = __double2float_rn(v);
+                    a32[k] = hi;
+                    alo[k] = __double2float_rn(v - (double)hi);
+                }
             }
+            if (T.r0 == 0)      // split-K tickets of the FP32 product start at zero
+                for (int b = tid; b < D.nb32; b += VEC_T) D.ticket[b] = 0;
         }
         __syncthreads();
         const long long e0 = (long long)T.r0 * sp, e1 = (long long)T.r1 * sp;
@@ -619,6 +729,8 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
             for (long long e = e0 + tid; e < e1; e += VEC_T) {
                 const double b = D.B[e];
                 D.X[e] = 0.0;
+                D.Xh[e] = 0.0f;
+                D.Xl[e] = 0.0f;
                 D.R[e] = b;
                 part += b * b;
             }
@@ -662,7 +774,11 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                         d = 0.0;
                         for (int q = 0; q < kj; q++) d += S.yv[c][q] * (double)D.V[(long long)q * nsp + e];
                     }
-                    D.X[e] += rn * d;
+                    const double xn = D.X[e] + rn * d;
+                    const float xh = __double2float_rn(xn);
+                    D.X[e] = xn;
+                    D.Xh[e] = xh;
+                    D.Xl[e] = __double2float_rn(xn - (double)xh);
                 }
             }
         }
@@ -721,18 +837,16 @@ __global__ void eng_finish_kernel(const EngineDev *Ep, double *const *Xdst, cons
 EngineKernels engine_kernels() {
     EngineKernels K{};
     K.red = reinterpret_cast<void *>(&eng_red_kernel);
-    K.prod32 = reinterpret_cast<void *>(&eng_prod32_kernel);
-    K.prod64 = reinterpret_cast<void *>(&eng_prod64_kernel);
+    K.prod = reinterpret_cast<void *>(&eng_prod_kernel);
     K.vec = reinterpret_cast<void *>(&eng_vec_kernel);
     K.admit = reinterpret_cast<void *>(&eng_admit_kernel);
     K.finish = reinterpret_cast<void *>(&eng_finish_kernel);
     K.red_threads = RED_T;
-    K.prod32_threads = P32_T;
-    K.prod64_threads = P64_T;
+    K.prod_threads = P32_T;
     K.vec_threads = VEC_T;
-    // transposed A chunk (+ padding), operand chunk, reduction scratch (P32_T x 4 doubles)
-    K.prod32_smem = (size_t)E_KC32 * (E_RB32 + 4) * 4 + E_KC32 * 32 * 4 + (size_t)E_RB32 * 32 / 4 * 8;
-    K.prod64_smem = (size_t)E_RB64 * (KC64 + 1) * 8 + (size_t)KC64 * 33 * 8;
+    // FP32 product: transposed A chunk (+ padding), operand chunk, reduction
+    // scratch (P32_T x 4 doubles); the residual tasks reuse the same bytes
+    K.prod_smem = (size_t)E_KC32 * (E_RB32 + 4) * 4 + E_KC32 * 32 * 4 + (size_t)E_RB32 * 32 / 4 * 8;
     return K;
 }
 

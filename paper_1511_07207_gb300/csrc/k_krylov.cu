@@ -47,10 +47,6 @@ __device__ __forceinline__ void publish(double *part, int slot, double v) {
     if (threadIdx.x == 0) part[(size_t)slot * gridDim.x + blockIdx.x] = v;
 }
 
-__device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, unsigned v) {
-    cudaGraphSetConditional(h, v);
-}
-
 // ============================================================================
 // CG
 // ============================================================================
@@ -111,8 +107,8 @@ __global__ void __launch_bounds__(KB) cg_init_kernel(Vecs v, int x0_given,
                 st->status = LS_NOT_CONVERGED;
                 go = 0;
             }
-            set_cond(h_outer, go);
-            set_cond(h_inner, go);
+            set_cond(v.st, h_outer, go);
+            set_cond(v.st, h_inner, go);
         }
     }
 }
@@ -124,7 +120,7 @@ __global__ void __launch_bounds__(KB) cg_update_kernel(Vecs v, cudaGraphConditio
     const double alpha = st->alpha, rho = st->rho, tol = st->tol_abs;
     const int status = st->status, err = st->err;
     if (status == LS_BREAKDOWN || err) {   // the GEMV found p.Ap <= 0 (or a wait failed)
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h_inner, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
         return;
     }
     long long lo, hi;
@@ -139,7 +135,7 @@ __global__ void __launch_bounds__(KB) cg_update_kernel(Vecs v, cudaGraphConditio
     rr = block_sum(rr, red);
     publish(v.part, 0, rr);
     if (!grid_sync(v.bar, st)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h_inner, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
         return;
     }
     __shared__ double rho_new_s;
@@ -163,7 +159,7 @@ __global__ void __launch_bounds__(KB) cg_update_kernel(Vecs v, cudaGraphConditio
         st->iter += 1;
         st->conv = conv;
         if (!finite) set_err(st, ERRB_NAN);
-        if (!finite || conv || st->iter >= st->max_iter) set_cond(h_inner, 0);
+        if (!finite || conv || st->iter >= st->max_iter) set_cond(v.st, h_inner, 0);
     }
 }
 
@@ -198,8 +194,8 @@ __global__ void __launch_bounds__(KB) cg_check_kernel(Vecs v, cudaGraphCondition
             st->rnorm = t;
             st->conv = 0;
         }
-        set_cond(h_outer, decision == 3);
-        set_cond(h_inner, decision == 3);
+        set_cond(v.st, h_outer, decision == 3);
+        set_cond(v.st, h_inner, decision == 3);
     }
 }
 
@@ -245,7 +241,7 @@ __global__ void __launch_bounds__(KB) gm_init_kernel(Vecs v, int x0_given,
                 st->true_rnorm = 0.0;
                 go = 0;
             }
-            set_cond(h_outer, go);
+            set_cond(v.st, h_outer, go);
         }
     }
 }
@@ -281,8 +277,8 @@ __global__ void __launch_bounds__(KB) gm_start_kernel(Vecs v, cudaGraphCondition
             st->est = beta;
             st->cycles += 1;
         }
-        set_cond(h_outer, go == 1);
-        set_cond(h_inner, go == 1);
+        set_cond(v.st, h_outer, go == 1);
+        set_cond(v.st, h_inner, go == 1);
     }
 }
 
@@ -345,7 +341,7 @@ __global__ void __launch_bounds__(KB) gm_arnoldi_kernel(Vecs v, cudaGraphConditi
         if (pass == 0 && !always2 && !(wn2 < 0.49 * wnorm0)) break;
     }
     if (st->err) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(h_inner, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
         return;
     }
     const double wn = sqrt(wn2);
@@ -383,7 +379,7 @@ __global__ void __launch_bounds__(KB) gm_arnoldi_kernel(Vecs v, cudaGraphConditi
             if (st->est <= st->tol_abs || lucky || k + 1 >= st->m || st->total >= st->max_iter)
                 stop = true;
         }
-        if (stop) set_cond(h_inner, 0);
+        if (stop) set_cond(v.st, h_inner, 0);
     }
 }
 

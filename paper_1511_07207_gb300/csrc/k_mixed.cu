@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(MB) mx_init_kernel(MixVecs v, int x0_given,
             st->status = LS_NOT_CONVERGED;
             go = 0;
         }
-        cudaGraphSetConditional(h_super, go);
-        cudaGraphSetConditional(h_outer, go);
+        set_cond(v.st, h_super, go);
+        set_cond(v.st, h_outer, go);
     }
 }
 
@@ -123,7 +123,7 @@ __device__ __forceinline__ void inner_setup(const MixVecs &v, double rn, double 
             st->in_iter = 0;
             st->in_stop = 0;
             st->in_tol2 = st->in_tol2 > 0.0f ? st->in_tol2 : -1.0f;
-            cudaGraphSetConditional(h_inner, st->in_max > 0 && rho > 0.0);
+            set_cond(v.st, h_inner, st->in_max > 0 && rho > 0.0);
         }
     }
 }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(MB) in_update_kernel(MixVecs v, cudaGraphCondi
     if (st->in_stop == 2) {   // p.Ahat p <= 0: keep the iterate (the rhs itself on step 0)
         if (st->in_iter == 0)
             for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) v.zf[i] = v.pf[i];
-        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_inner, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
         return;
     }
     const float alpha = (float)st->in_alpha;
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(MB) in_update_kernel(MixVecs v, cudaGraphCondi
     const double t = block_sum((double)acc, red);
     publish_m(v.part, 0, t);
     if (!grid_sync(v.bar, st)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_inner, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
         return;
     }
     const double rho_new = all_reduce_slot(v.part, 0);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(MB) in_update_kernel(MixVecs v, cudaGraphCondi
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->in_rho = rho_new;
         st->in_iter = it + 1;
-        if (stop) cudaGraphSetConditional(h_inner, 0);
+        if (stop) set_cond(v.st, h_inner, 0);
     }
 }
 
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(MB) fcg_update_kernel(MixVecs v, cudaGraphCond
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->status = LS_BREAKDOWN;
             if (!isfinite(pr) || !(d == d)) set_err(st, ERRB_NAN);
-            cudaGraphSetConditional(h_outer, 0);
+            set_cond(v.st, h_outer, 0);
         }
         return;
     }
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(MB) fcg_update_kernel(MixVecs v, cudaGraphCond
     rr = block_sum(rr, red);
     publish_m(v.part, 0, rr);
     if (!grid_sync(v.bar, st)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_outer, 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_outer, 0);
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(MB) fcg_update_kernel(MixVecs v, cudaGraphCond
             if (!finite) set_err(st, ERRB_NAN);
             if (!finite || rn <= st->tol_abs || st->outer >= st->max_outer ||
                 st->nstored >= st->m)
-                cudaGraphSetConditional(h_outer, 0);
+                set_cond(v.st, h_outer, 0);
         }
     }
 }
@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(MB) mx_check_kernel(MixVecs v, cudaGraphCondit
             if (st->nstored >= st->m) st->nstored = 0;
         }
         st->cycles += 1;
-        cudaGraphSetConditional(h_super, decision == 3);
-        cudaGraphSetConditional(h_outer, decision == 3);
+        set_cond(v.st, h_super, decision == 3);
+        set_cond(v.st, h_outer, decision == 3);
     }
 }
 
@@ -324,8 +324,8 @@ __global__ void __launch_bounds__(MB) ir_start_kernel(MixVecs v, cudaGraphCondit
             if (go == -2) st->status = LS_NOT_CONVERGED;
             st->rnorm = t;
             st->in_stop = 3;      // no step this time: ir_update must not apply z again
-            cudaGraphSetConditional(h_outer, 0);
-            cudaGraphSetConditional(h_inner, 0);
+            set_cond(v.st, h_outer, 0);
+            set_cond(v.st, h_inner, 0);
         }
         return;
     }

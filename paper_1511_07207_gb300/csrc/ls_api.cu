@@ -64,33 +64,86 @@ void GraphCache::reset() {
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
+    prog.reset();
     memset(key, 0, sizeof(key));
 }
 
 bool GraphCache::matches(const long long *k) const {
-    return exec && memcmp(key, k, sizeof(key)) == 0;
+    return (exec || prog) && memcmp(key, k, sizeof(key)) == 0;
 }
 
-int finish_graph(ls_ctx *c, GraphCache &gc, cudaGraph_t g, const long long *key) {
+int hostloop_mode() {
+    static const int mode = [] {
+        const char *e = getenv("LS_HOSTLOOP");
+        if (!e) e = getenv("LS_ENGINE_HOSTLOOP");
+        return e ? atoi(e) : 0;
+    }();
+    return mode > 0;
+}
+
+int finish_graph(ls_ctx *c, GraphCache &gc, Root &r, const long long *key) {
+    (void)c;
+    if (r.prog) {
+        gc.reset();
+        gc.prog = r.prog;
+        memcpy(gc.key, key, sizeof(gc.key));
+        return LS_OK;
+    }
     cudaGraphExec_t ex = nullptr;
-    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&ex, r.g, 0);
     if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+        r.discard();
         return LS_ERR_CUDA;
     }
     gc.reset();
-    gc.graph = g;
+    gc.graph = r.g;
     gc.exec = ex;
+    r.g = nullptr;
     memcpy(gc.key, key, sizeof(gc.key));
-    (void)c;
     return LS_OK;
+}
+
+// Host-loop execution of a recorded program: kernels in order, each while-loop
+// re-entered while the device-side condition it reads back is set.
+static cudaError_t run_prog(ls_ctx *c, const Prog &p) {
+    constexpr long long LOOP_LIMIT = 100000000;   // far above any iteration limit
+    for (const ProgOp &op : p.ops) {
+        cudaError_t e = cudaSuccess;
+        if (op.handle >= 0) {
+            for (long long it = 0; it < LOOP_LIMIT; it++) {
+                unsigned go = 0;
+                e = cudaMemcpyAsync(&go, &c->st->cond[op.handle], sizeof(unsigned),
+                                    cudaMemcpyDeviceToHost, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                if (e != cudaSuccess || !go) break;
+                e = run_prog(c, *op.body);
+                if (e != cudaSuccess) break;
+            }
+        } else {
+            std::vector<void *> args(op.offs.size());
+            for (size_t i = 0; i < op.offs.size(); i++)
+                args[i] = const_cast<char *>(op.args.data()) + op.offs[i];
+            e = op.coop ? cudaLaunchCooperativeKernel(op.func, dim3(op.grid), dim3(op.block),
+                                                      args.data(), op.smem, c->stream)
+                        : cudaLaunchKernel(op.func, dim3(op.grid), dim3(op.block), args.data(),
+                                           op.smem, c->stream);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int launch_cached(ls_ctx *c, GraphCache &gc) {
+    if (gc.prog) return map_cuda(run_prog(c, *gc.prog));
+    return map_cuda(cudaGraphLaunch(gc.exec, c->stream));
 }
 
 // ---- state upload / download -------------------------------------------------------
 void state_init(State *h, int max_iter) {
     memset(h, 0, sizeof(State));
     h->max_iter = max_iter;
+    h->hostloop = hostloop_mode();
+    for (int i = 0; i < LS_COND_SLOTS; i++) h->cond[i] = 1;
 }
 
 int upload_state(ls_ctx *c) {
@@ -332,16 +385,14 @@ Vecs make_vecs(ls_ctx *c, const F64Layout &L, int n, double rtol) {
 // Builds: [resid GEMV if x0] cg_init, while(outer){ while(inner){GEMV, update}, resid GEMV, check }
 static int build_cg_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
                           const long long *key) {
-    cudaGraph_t g;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LS_ERR_CUDA;
+    Root R;
+    if (!R.create()) return LS_ERR_CUDA;
     cudaGraphConditionalHandle ho, hi;
-    if (cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
-        cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+    if (!R.handle(&ho) || !R.handle(&hi)) {
+        R.discard();
         return LS_ERR_CUDA;
     }
-    Chain top(g);
+    Chain top = R.chain();
     const MatDesc *dA = c->dA;
     if (x0_given) {
         GemvArgs a{};
@@ -355,12 +406,8 @@ static int build_cg_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_
         void *args[] = {&vv, &x0, &ho, &hi};
         top.kernel(c->K.cg_init, c->K.coop_grid, c->K.block, 0, args, true);
     }
-    cudaGraph_t body_o = top.loop(ho);
-    if (top.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
-    Chain outer(body_o);
-    cudaGraph_t body_i = outer.loop(hi);
-    if (outer.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
-    Chain inner(body_i);
+    Chain outer = top.loop(ho);
+    Chain inner = outer.loop(hi);
     {
         GemvArgs a{};
         a.x = v.p; a.y = v.q; a.z = v.p; a.st = v.st; a.scr = c->scr;
@@ -379,37 +426,32 @@ static int build_cg_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_
         void *args[] = {&vv, &ho, &hi};
         outer.kernel(c->K.cg_check, c->K.coop_grid, c->K.block, 0, args, false);
     }
-    if (inner.err != cudaSuccess || outer.err != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+    if (top.err != cudaSuccess || inner.err != cudaSuccess || outer.err != cudaSuccess) {
+        R.discard();
         return LS_ERR_CUDA;
     }
-    return finish_graph(c, c->graph_cg, g, key);
+    return finish_graph(c, c->graph_cg, R, key);
 }
 
 // Builds: gm_init, while(outer){ resid GEMV, gm_start, while(inner){GEMV, arnoldi}, gm_finish }
 static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
                              const long long *key) {
-    cudaGraph_t g;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LS_ERR_CUDA;
+    Root R;
+    if (!R.create()) return LS_ERR_CUDA;
     cudaGraphConditionalHandle ho, hi;
-    if (cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
-        cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+    if (!R.handle(&ho) || !R.handle(&hi)) {
+        R.discard();
         return LS_ERR_CUDA;
     }
     const MatDesc *dA = c->dA;
-    Chain top(g);
+    Chain top = R.chain();
     {
         Vecs vv = v;
         int x0 = x0_given;
         void *args[] = {&vv, &x0, &ho};
         top.kernel(c->K.gm_init, c->K.coop_grid, c->K.block, 0, args, true);
     }
-    cudaGraph_t body_o = top.loop(ho);
-    if (top.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
-    Chain outer(body_o);
+    Chain outer = top.loop(ho);
     {
         GemvArgs a{};
         a.x = v.x; a.y = v.q; a.b = v.b; a.st = v.st; a.scr = c->scr;
@@ -419,9 +461,7 @@ static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int 
         void *args[] = {&vv, &ho, &hi};
         outer.kernel(c->K.gm_start, c->K.coop_grid, c->K.block, 0, args, false);
     }
-    cudaGraph_t body_i = outer.loop(hi);
-    if (outer.err != cudaSuccess) { cudaGraphDestroy(g); cudaGetLastError(); return LS_ERR_CUDA; }
-    Chain inner(body_i);
+    Chain inner = outer.loop(hi);
     {
         GemvArgs a{};
         a.x = v.V; a.y = v.V; a.kptr = &v.st->k; a.kstride = v.ldv; a.kyoff = 1;
@@ -437,12 +477,11 @@ static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int 
         void *args[] = {&vv};
         outer.kernel(c->K.gm_finish, c->K.coop_grid, c->K.block, 0, args, true);
     }
-    if (inner.err != cudaSuccess || outer.err != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+    if (top.err != cudaSuccess || inner.err != cudaSuccess || outer.err != cudaSuccess) {
+        R.discard();
         return LS_ERR_CUDA;
     }
-    return finish_graph(c, c->graph_gm, g, key);
+    return finish_graph(c, c->graph_gm, R, key);
 }
 
 static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda, const double *b,
@@ -496,8 +535,10 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
         if (rc) return rc;
     }
     cudaError_t e = cudaEventRecord(c->ev0, c->stream);
-    if (e == cudaSuccess) e = cudaGraphLaunch(gc.exec, c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    rc = launch_cached(c, gc);
+    if (rc) return rc;
+    e = cudaEventRecord(c->ev1, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
     rc = read_state(c);
     if (rc) return rc;

@@ -4,14 +4,21 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+#include <memory>
+#include <vector>
+
 #include "ls_device.cuh"
 #include "ls_internal.h"
 
 namespace lsi {
 
+struct Prog;
+
 struct GraphCache {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::shared_ptr<Prog> prog;        // host-loop mode
     long long key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     void reset();
     bool matches(const long long *k) const;
@@ -65,23 +72,64 @@ struct Carver {
     }
 };
 
-// Adds nodes one after another to a graph.
+// A solver loop recorded for the host instead of a graph (host-loop mode): the
+// same kernels with the same arguments, and while-loops whose condition the
+// kernels write to State::cond[handle] and the host reads back before every
+// pass.  Profilers see each kernel of such a run; graph mode hides the kernels
+// inside conditional bodies from them.
+struct ProgOp {
+    void *func = nullptr;
+    int grid = 0, block = 0;
+    size_t smem = 0;
+    bool coop = false;
+    std::vector<char> args;            // parameter bytes at their offsets
+    std::vector<size_t> offs;          // parameter offsets
+    int handle = -1;                   // >= 0: a while-loop on State::cond[handle]
+    std::shared_ptr<struct Prog> body;
+};
+struct Prog {
+    std::vector<ProgOp> ops;
+};
+
+// True when LS_HOSTLOOP (or LS_ENGINE_HOSTLOOP) is set to a positive value.
+int hostloop_mode();
+
+// Adds nodes one after another to a graph, or ops to a host program.
 struct Chain {
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
+    Prog *p = nullptr;
     cudaGraphNode_t last = nullptr;
     cudaError_t err = cudaSuccess;
     explicit Chain(cudaGraph_t gr) : g(gr) {}
+    explicit Chain(Prog *pr) : p(pr) {}
+    Chain() : err(cudaErrorUnknown) {}
 
     void kernel(void *func, int grid, int block, size_t smem, void **args, bool coop) {
         if (err != cudaSuccess) return;
-        cudaKernelNodeParams p{};
-        p.func = func;
-        p.gridDim = dim3(grid);
-        p.blockDim = dim3(block);
-        p.sharedMemBytes = (unsigned)smem;
-        p.kernelParams = args;
+        if (p) {
+            ProgOp op;
+            op.func = func; op.grid = grid; op.block = block; op.smem = smem; op.coop = coop;
+            for (size_t i = 0;; i++) {
+                size_t off = 0, size = 0;
+                if (cudaFuncGetParamInfo(func, i, &off, &size) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;
+                }
+                if (op.args.size() < off + size) op.args.resize(off + size);
+                memcpy(op.args.data() + off, args[i], size);
+                op.offs.push_back(off);
+            }
+            p->ops.push_back(std::move(op));
+            return;
+        }
+        cudaKernelNodeParams kp{};
+        kp.func = func;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = args;
         cudaGraphNode_t node;
-        err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &p);
+        err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &kp);
         if (err != cudaSuccess) return;
         if (coop) {
             cudaLaunchAttributeValue v{};
@@ -90,9 +138,17 @@ struct Chain {
         }
         last = node;
     }
-    // Appends a while-node on handle h; returns its body graph.
-    cudaGraph_t loop(cudaGraphConditionalHandle h) {
-        if (err != cudaSuccess) return nullptr;
+    // Appends a while-loop on handle h; returns the chain of its body.
+    Chain loop(cudaGraphConditionalHandle h) {
+        if (err != cudaSuccess) return Chain();
+        if (p) {
+            ProgOp op;
+            op.handle = (int)h;
+            op.body = std::make_shared<Prog>();
+            Prog *b = op.body.get();
+            p->ops.push_back(std::move(op));
+            return Chain(b);
+        }
         cudaGraphNodeParams np{};
         np.type = cudaGraphNodeTypeConditional;
         np.conditional.handle = h;
@@ -100,9 +156,41 @@ struct Chain {
         np.conditional.size = 1;
         cudaGraphNode_t node;
         err = cudaGraphAddNode(&node, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np);
-        if (err != cudaSuccess) return nullptr;
+        if (err != cudaSuccess) return Chain();
         last = node;
-        return np.conditional.phGraph_out[0];
+        return Chain(np.conditional.phGraph_out[0]);
+    }
+};
+
+// The root of a solver loop: a graph, or a host program in host-loop mode.
+struct Root {
+    cudaGraph_t g = nullptr;
+    std::shared_ptr<Prog> prog;
+    int handles = 0;
+    // Creates the root; returns false on a CUDA error.
+    bool create() {
+        if (hostloop_mode()) {
+            prog = std::make_shared<Prog>();
+            return true;
+        }
+        return cudaGraphCreate(&g, 0) == cudaSuccess;
+    }
+    // A loop condition: a graph handle (default 1 at every launch), or an
+    // index into State::cond (set to 1 by state_init).
+    bool handle(cudaGraphConditionalHandle *h) {
+        if (prog) {
+            if (handles >= LS_COND_SLOTS) return false;
+            *h = (cudaGraphConditionalHandle)handles++;
+            return true;
+        }
+        return cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    }
+    Chain chain() { return prog ? Chain(prog.get()) : Chain(g); }
+    void discard() {
+        if (g) cudaGraphDestroy(g);
+        g = nullptr;
+        prog.reset();
+        cudaGetLastError();
     }
 };
 
@@ -115,7 +203,9 @@ inline void gemv_node(Chain &ch, const GemvLaunch &L, const MatDesc *dA, const G
     ch.kernel(L.func, L.grid, L.block, L.smem, args, false);
 }
 
-int finish_graph(ls_ctx *c, GraphCache &gc, cudaGraph_t g, const long long *key);
+int finish_graph(ls_ctx *c, GraphCache &gc, Root &r, const long long *key);
+// Runs a cached solver loop on the context's stream (graph launch or host loop).
+int launch_cached(ls_ctx *c, GraphCache &gc);
 
 int is_device_ptr(const void *p);
 int map_cuda(cudaError_t e);

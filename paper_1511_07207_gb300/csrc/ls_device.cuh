@@ -23,6 +23,15 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Sets a solver loop condition: through the graph handle, or into
+// State::cond[h] when the loop runs from the host.
+__device__ __forceinline__ void set_cond(State *st, cudaGraphConditionalHandle h, unsigned v) {
+    if (*(volatile int *)&st->hostloop)
+        ((volatile unsigned *)st->cond)[h & (LS_COND_SLOTS - 1)] = v;
+    else
+        cudaGraphSetConditional(h, v);
+}
+
 // ---- mbarrier ------------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)

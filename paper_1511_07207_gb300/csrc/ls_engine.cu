@@ -2,8 +2,8 @@
 // and the ls_batch_solve entry point.
 //
 // The engine owns the slot and task tables in device memory and one CUDA
-// graph: while (any slot active and ticks < limit) { eng_red; eng_prod32;
-// eng_prod64; eng_vec }.  The kernels read the table sizes from a device
+// graph: while (any slot active and ticks < limit) { eng_red; eng_prod;
+// eng_vec }.  The kernels read the table sizes from a device
 // block, so the same graph serves any set of resident slots; the batched
 // solver runs it to completion, the server (ls_server.cpp) runs it a few
 // ticks at a time between admissions.
@@ -62,9 +62,14 @@ SlotSizes slot_sizes(int n, int s, int method, int m) {
     const size_t nsp = (size_t)n * z.sp;
     z.bytes = 0;
     auto add = [&](size_t b) { z.bytes += align_up(b, 256); };
+    const SlotTasks tk = slot_tasks(n);
     add((size_t)n * z.ld32 * 4);              // A32
+    add((size_t)n * z.ld32 * 4);              // A32lo
     add(nsp * 8); add(nsp * 8); add(nsp * 8); // X, B, R
+    add(nsp * 4); add(nsp * 4);               // Xh, Xl
     add(nsp * 4); add(nsp * 4); add(nsp * 4); // Rf, Z, Q
+    if (tk.kc32 > 1) add((size_t)tk.kc32 * nsp * 4);                // Yk
+    add((size_t)(tk.rb32 > 0 ? tk.rb32 : 1) * sizeof(int));         // ticket
     if (method == LS_METHOD_CG) add(2 * nsp * 4);                   // P
     else { add(2 * nsp * 4); add((size_t)(m + 1) * nsp * 4); }      // W, V
     z.stageA = align_up((size_t)n * z.lda_stage * 8, 256);
@@ -80,14 +85,20 @@ void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int m
     D.sp = z.sp;
     D.method = method;
     D.m = m;
+    const SlotTasks tk = slot_tasks(n);
     D.A32 = cv.take<float>((size_t)n * z.ld32);
+    D.A32lo = cv.take<float>((size_t)n * z.ld32);
     D.ld32 = z.ld32;
     D.X = cv.take<double>(nsp);
     D.B = cv.take<double>(nsp);
     D.R = cv.take<double>(nsp);
+    D.Xh = cv.take<float>(nsp);
+    D.Xl = cv.take<float>(nsp);
     D.Rf = cv.take<float>(nsp);
     D.Z = cv.take<float>(nsp);
     D.Q = cv.take<float>(nsp);
+    D.Yk = tk.kc32 > 1 ? cv.take<float>((size_t)tk.kc32 * nsp) : nullptr;
+    D.ticket = cv.take<int>(tk.rb32 > 0 ? tk.rb32 : 1);
     D.P = nullptr;
     D.W = nullptr;
     D.V = nullptr;
@@ -109,15 +120,17 @@ void Engine::release() {
     exec = nullptr;
     graph = nullptr;
     dmem = nullptr;
-    cap_slots = cap32 = cap64 = capv = 0;
+    cap_slots = cap32 = capb = cap64 = capv = 0;
 }
 
-int Engine::reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv) {
+int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
     c = ctx;
-    if (dmem && slots <= cap_slots && n32 <= cap32 && n64 <= cap64 && nv <= capv) return LS_OK;
+    if (dmem && slots <= cap_slots && n32 <= cap32 && nrb <= capb && n64 <= cap64 && nv <= capv)
+        return LS_OK;
     release();
     cap_slots = std::max(slots, 1);
     cap32 = std::max(n32, 1);
+    capb = std::max(nrb, 1);
     cap64 = std::max(n64, 1);
     capv = std::max(nv, 1);
     Carver cv(nullptr);
@@ -129,7 +142,7 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv) {
         hE.t32 = k.take<Task>(cap32);
         hE.t64 = k.take<Task>(cap64);
         hE.tv = k.take<Task>(capv);
-        hE.part32 = k.take<double>((size_t)cap32 * E_PS * 32);
+        hE.part32 = k.take<double>((size_t)capb * E_PS * 32);
         hE.part64 = k.take<double>((size_t)cap64 * 32);
         hE.partv = k.take<double>((size_t)capv * 32);
         hE.active = k.take<int>(8);
@@ -154,8 +167,7 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv) {
     K = engine_kernels();
     grid_prod = 2 * c->num_sms;
     grid_vec = 2 * c->num_sms;
-    cudaFuncSetAttribute(K.prod32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod32_smem);
-    cudaFuncSetAttribute(K.prod64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod64_smem);
+    cudaFuncSetAttribute(K.prod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod_smem);
     return build_graph();
 }
 
@@ -167,12 +179,11 @@ int Engine::build_graph() {
         return LS_ERR_CUDA;
     }
     Chain top(graph);
-    cudaGraph_t body = top.loop(h);
+    Chain b = top.loop(h);
     if (top.err != cudaSuccess) {
         cudaGetLastError();
         return LS_ERR_CUDA;
     }
-    Chain b(body);
     const EngineDev *p = dE;
     {
         void *args[] = {(void *)&p, (void *)&h};
@@ -180,8 +191,7 @@ int Engine::build_graph() {
     }
     {
         void *args[] = {(void *)&p};
-        b.kernel(K.prod32, grid_prod, K.prod32_threads, K.prod32_smem, args, false);
-        b.kernel(K.prod64, grid_prod, K.prod64_threads, K.prod64_smem, args, false);
+        b.kernel(K.prod, grid_prod, K.prod_threads, K.prod_smem, args, false);
         b.kernel(K.vec, grid_vec, K.vec_threads, 0, args, false);
     }
     if (b.err != cudaSuccess) {
@@ -197,28 +207,27 @@ int Engine::build_graph() {
 
 // Task tables from the slot sizes.  Packed: each slot's tasks follow the
 // previous slot's (the batched solver, whose slot set never changes).  With
-// fixed regions of max_n rows per slot, a slot's task indices -- and so the
-// partial sums it left in the previous tick -- never move when other slots
-// are admitted or retired (the server); unused entries have slot = -1.
+// fixed regions sized for max_n rows per slot, a slot's task indices -- and so
+// the partial sums it left in the previous tick -- never move when other
+// slots are admitted or retired (the server); unused entries have slot = -1.
 void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     h32.clear();
     h64.clear();
     hv.clear();
-    const int per32 = (fixed_max_n + E_RB32 - 1) / E_RB32, per64 = (fixed_max_n + E_RB64 - 1) / E_RB64,
-              perv = (fixed_max_n + E_RBV - 1) / E_RBV;
-    auto fill = [](std::vector<Task> &tab, int q, int n, int rb, int per, int fixed, int &t0, int &cnt) {
-        if (fixed) {
-            t0 = q * per;
-            tab.resize((size_t)(q + 1) * per, Task{-1, 0, 0});
+    nb32 = 0;
+    const SlotTasks per = slot_tasks(fixed_max_n);
+    const Task none{-1, 0, 0, 0, 0, 0, 0, 0};
+    auto region = [&](std::vector<Task> &tab, int q, int per_slot, int &t0) {
+        if (fixed_max_n) {
+            t0 = q * per_slot;
+            tab.resize((size_t)(q + 1) * per_slot, none);
         } else {
             t0 = (int)tab.size();
         }
-        cnt = 0;
-        for (int r = 0; r < n; r += rb, cnt++) {
-            const Task t{q, r, std::min(n, r + rb)};
-            if (fixed) tab[t0 + cnt] = t;
-            else tab.push_back(t);
-        }
+    };
+    auto put = [&](std::vector<Task> &tab, int idx, const Task &t) {
+        if (fixed_max_n) tab[idx] = t;
+        else tab.push_back(t);
     };
     // packed tables list the costliest slots first (tasks are claimed in
     // table order, so the long ones start early and the short ones fill in)
@@ -231,10 +240,30 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     for (int q : order) {
         SlotDesc &D = hd[q];
         const int n = D.n > 0 ? D.n : 0;
-        fill(h32, q, n, rb32(D.sp > 0 ? D.sp : 32), per32, fixed_max_n, D.t32, D.n32);
-        fill(h64, q, n, E_RB64, per64, fixed_max_n, D.t64, D.n64);
-        fill(hv, q, n, E_RBV, perv, fixed_max_n, D.tv, D.nv);
+        const SlotTasks tk = slot_tasks(n);
+        // FP32 product: row block x K chunk; row blocks own the partial dots
+        region(h32, q, per.t32, D.t32);
+        D.b32 = fixed_max_n ? q * per.rb32 : nb32;
+        D.nb32 = tk.rb32;
+        D.n32 = 0;
+        for (int b = 0; b < tk.rb32; b++)
+            for (int kc = 0; kc < tk.kc32; kc++) {
+                const Task t{q, b * E_RB32, std::min(n, (b + 1) * E_RB32), kc * E_KS32,
+                             std::min(n, (kc + 1) * E_KS32), kc, D.b32 + b, 0};
+                put(h32, D.t32 + D.n32, t);
+                D.n32++;
+            }
+        if (!fixed_max_n) nb32 += tk.rb32;
+        region(h64, q, per.t64, D.t64);
+        D.n64 = 0;
+        for (int r = 0; r < n; r += E_RB64, D.n64++)
+            put(h64, D.t64 + D.n64, Task{q, r, std::min(n, r + E_RB64), 0, 0, 0, 0, 0});
+        region(hv, q, per.tv, D.tv);
+        D.nv = 0;
+        for (int r = 0; r < n; r += E_RBV, D.nv++)
+            put(hv, D.tv + D.nv, Task{q, r, std::min(n, r + E_RBV), 0, 0, 0, 0, 0});
     }
+    if (fixed_max_n) nb32 = (int)hd.size() * per.rb32;
 }
 
 int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables) {
@@ -320,12 +349,13 @@ int Engine::collect(int first, int count, std::vector<SlotResult> &out) {
     return map_cuda(e);
 }
 
-// LS_ENGINE_HOSTLOOP=1 runs the same kernels from a host loop instead of the
-// graph's while-node (the loop condition is read back every tick), which lets
-// profilers see each kernel; LS_ENGINE_HOSTLOOP=2 also times every kernel with
-// CUDA events and prints the totals to stderr.
+// LS_HOSTLOOP=1 (or LS_ENGINE_HOSTLOOP=1) runs the same kernels from a host
+// loop instead of the graph's while-node (the loop condition is read back every
+// tick), which lets profilers see each kernel; the value 2 also times every
+// kernel with CUDA events and prints the totals to stderr.
 int Engine::run() {
-    const char *env = getenv("LS_ENGINE_HOSTLOOP");
+    const char *env = getenv("LS_HOSTLOOP");
+    if (!env) env = getenv("LS_ENGINE_HOSTLOOP");
     const int mode = env ? atoi(env) : 0;
     if (mode <= 0) return map_cuda(cudaGraphLaunch(exec, c->stream));
     hE.host_loop = 1;
@@ -334,9 +364,9 @@ int Engine::run() {
     const EngineDev *p = dE;
     void *args_red[] = {(void *)&p, (void *)&none};
     void *args[] = {(void *)&p};
-    cudaEvent_t ev[5];
-    for (int i = 0; i < 5; i++) cudaEventCreate(&ev[i]);
-    double tot[4] = {0, 0, 0, 0};
+    cudaEvent_t ev[4];
+    for (int i = 0; i < 4; i++) cudaEventCreate(&ev[i]);
+    double tot[3] = {0, 0, 0};
     long long ticks = 0;
     int go = 1;
     while (e == cudaSuccess && go) {
@@ -344,29 +374,26 @@ int Engine::run() {
         e = cudaLaunchKernel(K.red, dim3(cap_slots), dim3(K.red_threads), args_red, 0, c->stream);
         if (mode == 2) cudaEventRecord(ev[1], c->stream);
         if (e == cudaSuccess)
-            e = cudaLaunchKernel(K.prod32, dim3(grid_prod), dim3(K.prod32_threads), args, K.prod32_smem, c->stream);
+            e = cudaLaunchKernel(K.prod, dim3(grid_prod), dim3(K.prod_threads), args, K.prod_smem, c->stream);
         if (mode == 2) cudaEventRecord(ev[2], c->stream);
         if (e == cudaSuccess)
-            e = cudaLaunchKernel(K.prod64, dim3(grid_prod), dim3(K.prod64_threads), args, K.prod64_smem, c->stream);
-        if (mode == 2) cudaEventRecord(ev[3], c->stream);
-        if (e == cudaSuccess)
             e = cudaLaunchKernel(K.vec, dim3(grid_vec), dim3(K.vec_threads), args, 0, c->stream);
-        if (mode == 2) cudaEventRecord(ev[4], c->stream);
+        if (mode == 2) cudaEventRecord(ev[3], c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&go, hE.active + 4, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (mode == 2 && e == cudaSuccess)
-            for (int i = 0; i < 4; i++) {
+            for (int i = 0; i < 3; i++) {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
                 tot[i] += ms;
             }
         ticks++;
     }
-    for (int i = 0; i < 5; i++) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 4; i++) cudaEventDestroy(ev[i]);
     if (mode == 2)
-        fprintf(stderr, "engine ticks %lld  red %.3f ms  prod32 %.3f ms  prod64 %.3f ms  vec %.3f ms\n",
-                ticks, tot[0], tot[1], tot[2], tot[3]);
+        fprintf(stderr, "engine ticks %lld  red %.3f ms  prod %.3f ms  vec %.3f ms\n", ticks, tot[0],
+                tot[1], tot[2]);
     hE.host_loop = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
     return map_cuda(e);
@@ -415,7 +442,7 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
     std::vector<SlotSizes> z(count);
     std::vector<int> a_dev(count), b_dev(count), x_dev(count);
     size_t total = 0;
-    int n32 = 0, n64 = 0, nv = 0;
+    int n32 = 0, nb32 = 0, n64 = 0, nv = 0;
     for (int q = 0; q < count; q++) {
         const ls_system &S = sys[q];
         z[q] = slot_sizes(S.n, S.nrhs, S.method, S.opts.restart);
@@ -424,16 +451,18 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
         x_dev[q] = is_device_ptr(S.X);
         total += z[q].bytes + (a_dev[q] ? 0 : z[q].stageA) + (b_dev[q] ? 0 : z[q].stageBX) +
                  (x_dev[q] ? 0 : z[q].stageBX);
-        n32 += (S.n + rb32(z[q].sp) - 1) / rb32(z[q].sp);
-        n64 += (S.n + E_RB64 - 1) / E_RB64;
-        nv += (S.n + E_RBV - 1) / E_RBV;
+        const SlotTasks tk = slot_tasks(S.n);
+        n32 += tk.t32;
+        nb32 += tk.rb32;
+        n64 += tk.t64;
+        nv += tk.tv;
     }
     int rc = ws_reserve(c, total);
     if (rc) return rc;
     if (!c->batch) c->batch = new (std::nothrow) Engine();
     if (!c->batch) return LS_ERR_NOMEM;
     Engine &E = *c->batch;
-    rc = E.reserve(c, count, n32, n64, nv);
+    rc = E.reserve(c, count, n32, nb32, n64, nv);
     if (rc) return rc;
 
     // carve, stage, describe

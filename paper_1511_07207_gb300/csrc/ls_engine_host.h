@@ -28,7 +28,8 @@ void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int m
 class Engine {
 public:
     ls_ctx *c = nullptr;
-    int cap_slots = 0, cap32 = 0, cap64 = 0, capv = 0;
+    int cap_slots = 0, cap32 = 0, capb = 0, cap64 = 0, capv = 0;
+    int nb32 = 0;                        // FP32 row blocks in the current tables
     char *dmem = nullptr;
     size_t dbytes = 0;
     EngineDev *dE = nullptr;
@@ -46,7 +47,7 @@ public:
 
     ~Engine();
     void release();
-    int reserve(ls_ctx *ctx, int slots, int n32, int n64, int nv);
+    int reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv);
     int build_graph();
     void set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n);
     int upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables);

@@ -39,6 +39,8 @@ enum : int { ERRB_TIMEOUT = 1, ERRB_NAN = 2 };
 
 // stop reasons / status written by the kernels (same values as LS_*)
 // State lives in device memory; one per context.
+constexpr int LS_COND_SLOTS = 4;
+
 struct State {
     // CG / common
     double rho;          // r.r
@@ -72,6 +74,8 @@ struct State {
     int in_stop;
     float in_tol2;       // inner (rtol^2 * rho0), <0 = fixed count
     int launches_lo;     // kernels executed (low word; counted by block 0)
+    int hostloop;        // 1: loop conditions go to cond[] instead of graph handles
+    unsigned cond[LS_COND_SLOTS];
     unsigned long long launches;
 };
 

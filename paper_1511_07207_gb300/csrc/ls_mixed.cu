@@ -65,23 +65,19 @@ static int build_mixed_graph(ls_ctx *c, const MixVecs &v, const GemvLaunch &L64,
                              const GemvLaunch &Llo, int x0_given, const long long *key) {
     const MixedKernels K = mixed_kernels();
     const int G = c->K.coop_grid, B = c->K.block;
-    cudaGraph_t g;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return LS_ERR_CUDA;
+    Root R;
+    if (!R.create()) return LS_ERR_CUDA;
     // Every handle must belong to a conditional node of the graph: the
     // refinement loop has no super loop, so it passes its outer handle twice.
     cudaGraphConditionalHandle hs, ho, hi;
-    if (cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
-        cudaGraphConditionalHandleCreate(&hi, g, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
-        (v.mode == LS_REFINE_FCG &&
-         cudaGraphConditionalHandleCreate(&hs, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+    if (!R.handle(&ho) || !R.handle(&hi) || (v.mode == LS_REFINE_FCG && !R.handle(&hs))) {
+        R.discard();
         return LS_ERR_CUDA;
     }
     if (v.mode != LS_REFINE_FCG) hs = ho;
     const MatDesc *d64 = c->dA, *dlo = c->dA + 1;
     MixVecs vv = v;
-    Chain top(g);
+    Chain top = R.chain();
     if (x0_given) {
         GemvArgs a{};
         a.x = v.x; a.y = v.r; a.b = v.b; a.st = v.st; a.scr = c->scr;
@@ -94,8 +90,7 @@ static int build_mixed_graph(ls_ctx *c, const MixVecs &v, const GemvLaunch &L64,
         top.kernel(K.mx_init, G, B, 0, args, true);
     }
     // inner FP32 CG body (shared by both outer loops)
-    auto inner_body = [&](cudaGraph_t body) {
-        Chain in(body);
+    auto inner_body = [&](Chain &in) {
         GemvArgs a{};
         a.x = v.pf; a.y = v.qf; a.z = v.pf; a.st = v.st; a.scr = c->scr;
         a.epi = EPI_DOT; a.fin = FIN_INNER_ALPHA;
@@ -106,16 +101,14 @@ static int build_mixed_graph(ls_ctx *c, const MixVecs &v, const GemvLaunch &L64,
     };
     cudaError_t err = cudaSuccess;
     if (v.mode == LS_REFINE_FCG) {
-        cudaGraph_t bs = top.loop(hs);
-        Chain sup(bs);
-        cudaGraph_t bo = sup.loop(ho);
-        Chain out(bo);
+        Chain sup = top.loop(hs);
+        Chain out = sup.loop(ho);
         {
             void *args[] = {&vv, &hi};
             out.kernel(K.in_init, G, B, 0, args, true);
         }
-        cudaGraph_t bi = out.loop(hi);
-        if (bi) err = inner_body(bi);
+        Chain in = out.loop(hi);
+        err = inner_body(in);
         {
             void *args[] = {&vv};
             out.kernel(K.fcg_project, G, B, 0, args, true);
@@ -137,8 +130,7 @@ static int build_mixed_graph(ls_ctx *c, const MixVecs &v, const GemvLaunch &L64,
         }
         if (top.err || sup.err || out.err || err) err = cudaErrorUnknown;
     } else {
-        cudaGraph_t bo = top.loop(ho);
-        Chain out(bo);
+        Chain out = top.loop(ho);
         {
             GemvArgs a{};
             a.x = v.x; a.y = v.r; a.b = v.b; a.st = v.st; a.scr = c->scr;
@@ -147,8 +139,8 @@ static int build_mixed_graph(ls_ctx *c, const MixVecs &v, const GemvLaunch &L64,
             void *args[] = {&vv, &ho, &hi};
             out.kernel(K.ir_start, G, B, 0, args, true);
         }
-        cudaGraph_t bi = out.loop(hi);
-        if (bi) err = inner_body(bi);
+        Chain in = out.loop(hi);
+        err = inner_body(in);
         {
             void *args[] = {&vv};
             out.kernel(K.ir_update, G, B, 0, args, false);
@@ -156,11 +148,10 @@ static int build_mixed_graph(ls_ctx *c, const MixVecs &v, const GemvLaunch &L64,
         if (top.err || out.err || err) err = cudaErrorUnknown;
     }
     if (err != cudaSuccess) {
-        cudaGraphDestroy(g);
-        cudaGetLastError();
+        R.discard();
         return LS_ERR_CUDA;
     }
-    return finish_graph(c, c->graph_mx, g, key);
+    return finish_graph(c, c->graph_mx, R, key);
 }
 
 int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b, double *x,
@@ -234,8 +225,9 @@ int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double 
         rc = build_mixed_graph(c, v, L64, Llo, o.x0_given, key);
         if (rc) return rc;
     }
-    e = cudaGraphLaunch(c->graph_mx.exec, c->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, c->stream);
+    rc = launch_cached(c, c->graph_mx);
+    if (rc) return rc;
+    e = cudaEventRecord(c->ev1, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
     rc = read_state(c);
     if (rc) return rc;

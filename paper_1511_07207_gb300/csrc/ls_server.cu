@@ -337,9 +337,8 @@ extern "C" int ls_server_start(ls_ctx *c, const ls_server_cfg *cfg, ls_server **
     }
     int rc = s->pool.init(cfg->hbm_budget_bytes);
     const int cap = cfg->max_slots;
-    const int per32 = (SERVER_MAX_N + E_RB32 - 1) / E_RB32, per64 = (SERVER_MAX_N + E_RB64 - 1) / E_RB64,
-              perv = (SERVER_MAX_N + E_RBV - 1) / E_RBV;
-    if (!rc) rc = s->eng.reserve(&s->shadow, cap, cap * per32, cap * per64, cap * perv);
+    const SlotTasks per = slot_tasks(SERVER_MAX_N);
+    if (!rc) rc = s->eng.reserve(&s->shadow, cap, cap * per.t32, cap * per.rb32, cap * per.t64, cap * per.tv);
     if (rc) {
         s->eng.release();
         s->pool.release();
