@@ -41,8 +41,8 @@ __device__ __forceinline__ int claim(int *counter, int *slot_s) {
 // ============================================================================
 __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cudaGraphConditionalHandle h) {
     const EngineDev &E = *Ep;
-    __shared__ int all_stop, newphase_s;
-    const int sl = blockIdx.x < E.nslots ? blockIdx.x : 0;
+    __shared__ int all_stop, newphase_s, cnt_s, first_s, base_s, cntv_s, basev_s;
+    const int sl = blockIdx.x < E.nslots ? E.order[blockIdx.x] : 0;
     const int j = threadIdx.x;
     eng_count(E);
     const SlotDesc &D = E.desc[sl];
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
             if (!S.conv[j]) atomicAnd(&all_stop, 0);
         } else if (ph == PH_RESID) {
             double r2 = 0.0;
-            for (int t = D.t64; t < D.t64 + D.n64; t++) r2 += E.part64[(size_t)t * 32 + j];
+            for (int b = D.b32; b < D.b32 + D.nb32; b++) r2 += E.part64[(size_t)b * 32 + j];
             S.rn[j] = sqrt(r2);
             if (!isfinite(r2)) atomicOr(&S.err, ERRB_NAN);
             S.conv[j] = sqrt(r2) <= D.rtol * S.bnorm[j];
@@ -194,202 +194,236 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
         }
     }
     if (ph == PH_INIT && threadIdx.x < 32 && colv) S.alpha[j] = 0.0;   // GMRES step counters
+    // this tick's runnable tasks of the slot go to the work lists of the
+    // tick's parity (eng_prod and eng_vec claim from those lists only)
+    const int par = E.active[A_TICKS] & 1;
+    if (threadIdx.x == 0) {
+        const int np = (ph != PH_FREE && ph != PH_DONE) ? newphase_s : PH_FREE;
+        int cnt = 0, first = 0, cntv = 0;
+        if (np == PH_RESID) {
+            cnt = D.n64;
+            first = D.t64;
+        } else if (np == PH_CG || np == PH_GM || np == PH_START) {   // START: A32 / A32lo split
+            cnt = D.n32;
+            first = E.n64 + D.t32;
+        }
+        if (np == PH_START || np == PH_INIT || np == PH_CG || np == PH_GM || np == PH_UPDATE) cntv = D.nv;
+        cnt_s = cnt;
+        first_s = first;
+        cntv_s = cntv;
+        base_s = cnt ? atomicAdd(&E.active[A_LEN_PROD + par], cnt) : 0;
+        basev_s = cntv ? atomicAdd(&E.active[A_LEN_VEC + par], cntv) : 0;
+    }
+    __syncthreads();
+    {
+        int *wp = E.work[par];
+        for (int i = threadIdx.x; i < cnt_s; i += RED_T) wp[base_s + i] = first_s + i;
+        for (int i = threadIdx.x; i < cntv_s; i += RED_T) wp[E.wvec + basev_s + i] = D.tv + i;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int act = 0;
         if (ph != PH_FREE && ph != PH_DONE) {
             S.phase = newphase_s;
             act = (newphase_s != PH_DONE);
         }
-        if (act) atomicAdd(&E.active[0], 1);
+        if (act) atomicAdd(&E.active[A_COUNT], 1);
         __threadfence();
-        const int tk = atomicAdd(&E.active[1], 1);
+        const int tk = atomicAdd(&E.active[A_TICKET], 1);
         if (tk == (int)gridDim.x - 1) {       // last block: loop control
             __threadfence();
-            const int total = atomicAdd(&E.active[0], 0);
-            const int ticks = E.active[3] + 1;
-            E.active[3] = ticks;
+            const int total = atomicAdd(&E.active[A_COUNT], 0);
+            const int ticks = E.active[A_TICKS] + 1;
+            E.active[A_TICKS] = ticks;
             const int go = total > 0 && ticks < E.tick_limit;
-            if (E.host_loop) E.active[4] = go;
+            if (E.host_loop) E.active[A_GO] = go;
             else cudaGraphSetConditional(h, go);
-            E.active[0] = 0;
-            E.active[1] = 0;
-            E.active[2] = total;
-            E.active[5] = 0;   // task claim counters of prod / vec
-            E.active[7] = 0;
+            E.active[A_COUNT] = 0;
+            E.active[A_TICKET] = 0;
+            E.active[A_LAST] = total;
+            E.active[A_CLAIM_PROD] = 0;    // task claim counters of eng_prod / eng_vec
+            E.active[A_CLAIM_VEC] = 0;
+            E.active[A_LEN_PROD + (par ^ 1)] = 0;   // lists of the next tick
+            E.active[A_LEN_VEC + (par ^ 1)] = 0;
         }
     }
 }
 
 // ============================================================================
-// eng_prod, FP32 block product task: Y = Ahat P for 256 rows and the task's
-// K chunk of up to 512 columns of A, all sp columns, register-blocked: each
-// thread owns an (sp/4)-row x 4-column tile of Y.  The A chunk (32 columns of
-// the task's rows) sits transposed in shared memory; the next chunk is
-// prefetched into registers meanwhile.  When a row block has several K
-// chunks, each task stores its partial product and the last one to finish
-// sums them in chunk order (so the result does not depend on which task came
-// last) and runs the epilogue: Y rows and partial dots.
+// eng_prod: one CTA per SM, warp-specialised.  The producer warp claims the
+// tick's runnable tasks and streams, for every 32-column chunk of an FP32
+// product task, the 256 x 32 tile of A32 (2-D TMA, 128-byte swizzle) and the
+// operand inputs (1-D bulk copies of the rows k0 .. k0+31 of the n x sp
+// blocks) into a ring of shared-memory stages, across task boundaries; the
+// eight consumer warps multiply.  Refinement-residual tasks stream the same
+// way (A32 and A32lo tiles, Xh and Xl rows); A-split tasks pass through the
+// ring as one header-only stage each and are run by the consumers with
+// ordinary loads.
 // ============================================================================
+constexpr int PC_W = P32_T / 32;                     // consumer warps
+constexpr int PROD_T = P32_T + 32;                   // + the producer warp
+constexpr int PSTAGES = 4;                           // ring stages
+constexpr int TILE_B = E_RB32 * E_KC32 * 4;          // 32 KB A tile
+constexpr int OPR_B = E_KC32 * 32 * 4;               // one raw operand chunk (widest slot)
+static_assert(E_KC32 * 4 == 128, "a tile row is one 128-byte swizzle row");
+
+struct StageHdr {
+    int kind, u, k0, flags;
+    int slot, sp, pad_[2];
+    float colscale[32];
+    int colstop[32];
+};
+enum : int { SK_STOP = 0, SK_PROD = 1, SK_GENERIC = 2, SK_RES = 3 };
+enum : int { SF_FIRST = 1, SF_LAST = 2, SF_SRC2 = 4 };
+
+constexpr size_t align_c(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr size_t OFF_TILE = 0;                                         // 1024-aligned tiles
+constexpr size_t OFF_OPR = OFF_TILE + (size_t)PSTAGES * TILE_B;        // [stage][2][OPR_B]
+constexpr size_t OFF_HDR = OFF_OPR + (size_t)PSTAGES * 2 * OPR_B;
+constexpr size_t OFF_BAR = align_c(OFF_HDR + PSTAGES * sizeof(StageHdr), 16);
+constexpr size_t OFF_PS = align_c(OFF_BAR + 2 * PSTAGES * sizeof(uint64_t), 16);   // [2][OPR_B]
+constexpr size_t OFF_RED = OFF_PS + 2 * OPR_B;                         // 1024 doubles
+constexpr size_t PROD_SMEM = OFF_RED + 1024 * sizeof(double) + 1024;  // + alignment slack
+
+struct ProdSmem {
+    unsigned char *base;
+    __device__ float *tile(int st) const { return reinterpret_cast<float *>(base + OFF_TILE + (size_t)st * TILE_B); }
+    __device__ float *opr(int st, int w) const {
+        return reinterpret_cast<float *>(base + OFF_OPR + ((size_t)st * 2 + w) * OPR_B);
+    }
+    __device__ StageHdr *hdr(int st) const { return reinterpret_cast<StageHdr *>(base + OFF_HDR) + st; }
+    __device__ uint64_t *full(int st) const { return reinterpret_cast<uint64_t *>(base + OFF_BAR) + st; }
+    __device__ uint64_t *empty(int st) const {
+        return reinterpret_cast<uint64_t *>(base + OFF_BAR) + PSTAGES + st;
+    }
+    __device__ float *ps(int b) const { return reinterpret_cast<float *>(base + OFF_PS + (size_t)b * OPR_B); }
+    __device__ double *red() const { return reinterpret_cast<double *>(base + OFF_RED); }
+};
+
+__device__ __forceinline__ void release_stage(const ProdSmem &M, int st) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(M.empty(st));
+}
+
+// ----------------------------------------------------------------------------
+// consumers: one FP32 product task, Y = Ahat P for 256 rows x ks32(SP)
+// columns of A, all SP columns.  Each thread owns RPT rows (rg + NRG r) x 4
+// columns (cg); per 4 k it reads each row's 4 A values with one 16-byte load
+// from the swizzled tile and 4 operand quads, then does 16 RPT multiply-adds
+// in increasing k.  The first stage was waited for by the caller.  When the
+// row block has several K chunks, each task stores its partial product and
+// the last one to finish sums them in chunk order and runs the epilogue: Y
+// rows and the partial dots.  Returns false on a timeout (all consumers
+// together).
+// ----------------------------------------------------------------------------
 template <int SP>
-__device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, float *As, float *Ps,
-                                            double *Red, float *colscale, int *colstop, int *flag_s) {
-    constexpr int RB = E_RB32, KC = E_KC32;
+__device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *flag_s) {
+    constexpr int KC = E_KC32;
     constexpr int RPT = SP / 4;                 // rows per thread
     constexpr int NCG = SP / 4;                 // column groups of 4
-    constexpr int RBP = RB + 4;                 // padded row stride of the transposed tile
-    constexpr int AV = RB * KC / 4 / P32_T;     // float4 loads of A per thread per chunk (8)
-    constexpr int PV = (KC * SP + P32_T - 1) / P32_T;
-    static_assert((RB / RPT) * NCG == P32_T, "thread grid");
-    static_assert(E_KS32 % KC == 0 && E_KS32 % RB == 0, "K chunks hold whole row blocks");
+    constexpr int NRG = E_RB32 / RPT;           // row groups
+    static_assert(NRG * NCG == P32_T, "thread grid");
+    static_assert(NRG % 8 == 0, "a thread's rows share one swizzle phase");
+    static_assert(ks32(SP) % KC == 0, "K chunks hold whole shared-memory chunks");
+    const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
+    const StageHdr &H0 = *M.hdr(seq % PSTAGES);
+    const int u = H0.u;
+    const Task T = E.t32[u - E.n64];
     const SlotDesc &D = E.desc[T.slot];
     const SlotState &S = E.st[T.slot];
     const int ph = S.phase;
     const int n = D.n, s = D.s, it = S.it;
     const long long nsp = (long long)n * SP;
     const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
-    const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
-    const float *src, *src2 = nullptr;
     float *dst, *out;
     if (ph == PH_CG) {
-        src = D.Rf;                                             // P = Rf + beta P'
-        src2 = it > 0 ? D.P + ((it + 1) & 1) * nsp : nullptr;
         dst = D.P + (it & 1) * nsp;
         out = D.Q;
     } else {
-        src = D.W + (it & 1) * nsp;                             // V_k = W / h
         dst = D.V + (long long)it * nsp;
         out = D.W + ((it + 1) & 1) * nsp;
     }
-    if (tid < 32) {
-        float sc = 0.0f;
-        const int stp = tid < s ? S.colstop[tid] : 1;
-        if (!stp) sc = ph == PH_CG ? (float)S.beta[tid] : (float)(1.0 / S.hnorm[tid]);
-        colscale[tid] = sc;
-        colstop[tid] = stp;
-    }
-    __syncthreads();
-    const float *A = D.A32;
-    const long long lda = D.ld32;
-    float4 areg[AV];
-    float preg[PV];
-    // lane l of warp w loads rows 32*(w % 8) + l ... : all lanes of a warp hold
-    // the same k-quad, so the transposed stores hit 32 different banks
-    auto a_index = [&](int v, int &rr, int &q) {
-        const int e = tid + v * P32_T;                          // 0 .. RB*KC/4 - 1
-        rr = (e & 31) + 32 * ((e >> 5) % (RB / 32));
-        q = (e >> 5) / (RB / 32);
-    };
-    auto prefetch = [&](int k0) {
-#pragma unroll
-        for (int v = 0; v < AV; v++) {
-            int rr, q;
-            a_index(v, rr, q);
-            const int gr = r0 + rr, gk = k0 + 4 * q;
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gr < r1) {
-                const float *ap = A + (long long)gr * lda + gk;
-                if (gk + 3 < n) x = *reinterpret_cast<const float4 *>(ap);
-                else {
-                    if (gk < n) x.x = ap[0];
-                    if (gk + 1 < n) x.y = ap[1];
-                    if (gk + 2 < n) x.z = ap[2];
-                }
-            }
-            areg[v] = x;
-        }
-#pragma unroll
-        for (int v = 0; v < PV; v++) {
-            const int e = tid + v * P32_T;
-            float val = 0.0f;
-            if (e < KC * SP) {
-                const int kk = e / SP, c = e % SP, gk = k0 + kk;
-                if (gk < n && c < s) {
-                    const long long o = (long long)gk * SP + c;
-                    if (ph == PH_CG)
-                        val = colstop[c] ? 0.0f : (src2 ? fmaf(colscale[c], src2[o], src[o]) : src[o]);
-                    else
-                        val = src[o] * colscale[c];
-                    if (gk >= r0 && gk < r1) dst[o] = val;      // this task owns row gk
-                }
-            }
-            preg[v] = val;
-        }
-    };
-    auto store = [&]() {
-#pragma unroll
-        for (int v = 0; v < AV; v++) {
-            int rr, q;
-            a_index(v, rr, q);
-            As[(4 * q + 0) * RBP + rr] = areg[v].x;
-            As[(4 * q + 1) * RBP + rr] = areg[v].y;
-            As[(4 * q + 2) * RBP + rr] = areg[v].z;
-            As[(4 * q + 3) * RBP + rr] = areg[v].w;
-        }
-#pragma unroll
-        for (int v = 0; v < PV; v++) {
-            const int e = tid + v * P32_T;
-            if (e < KC * SP) Ps[e] = preg[v];
-        }
-    };
     float acc[RPT][4];
 #pragma unroll
     for (int r = 0; r < RPT; r++)
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[r][c] = 0.0f;
-    prefetch(T.k0);
-    for (int k0 = T.k0; k0 < T.k1; k0 += KC) {
-        store();
-        __syncthreads();
-        if (k0 + KC < T.k1) prefetch(k0 + KC);                  // overlaps with the math below
-#pragma unroll 8
-        for (int kk = 0; kk < KC; kk++) {
-            float av[RPT];
-            const float *ar = As + kk * RBP + rg * RPT;
-            if constexpr (RPT == 1) {
-                av[0] = ar[0];
-            } else if constexpr (RPT == 2) {
-                const float2 a2 = *reinterpret_cast<const float2 *>(ar);
-                av[0] = a2.x;
-                av[1] = a2.y;
-            } else {
+    const int nch = (T.k1 - T.k0 + KC - 1) / KC;
+    for (int ch = 0; ch < nch; ch++) {
+        const int st = seq % PSTAGES;
+        const bool ok = ch == 0 || mbar_wait(M.full(st), (seq / PSTAGES) & 1);
+        float *Ps = M.ps(ch & 1);
+        if (ok) {   // the operand chunk: P = Rf + beta P' (CG) or V_k = W / h (GMRES)
+            const StageHdr &H = *M.hdr(st);
+            const float *o1 = M.opr(st, 0), *o2 = M.opr(st, 1);
+            const bool two = (H.flags & SF_SRC2) != 0;
+            const int k0 = H.k0;
+            for (int e = tid; e < KC * SP; e += P32_T) {
+                const int kk = e / SP, c = e % SP, gk = k0 + kk;
+                float val = 0.0f;
+                if (gk < n && c < s) {
+                    if (ph == PH_CG)
+                        val = H.colstop[c] ? 0.0f : (two ? fmaf(H.colscale[c], o2[e], o1[e]) : o1[e]);
+                    else
+                        val = o1[e] * H.colscale[c];
+                    if (gk >= r0 && gk < r1) dst[(long long)gk * SP + c] = val;   // owned rows
+                }
+                Ps[e] = val;
+            }
+        }
+        if (named_bar_or(1, P32_T, !ok)) return false;
+        // rows rg + NRG r share the swizzle phase rg & 7 (NRG is a multiple
+        // of 8): one chunk offset per k quad, fixed offsets between the rows
+        const float *At = M.tile(st) + rg * KC;
+        const int sw = rg & 7;
 #pragma unroll
-                for (int r4 = 0; r4 < RPT; r4 += 4) {
-                    const float4 a4 = *reinterpret_cast<const float4 *>(ar + r4);
-                    av[r4] = a4.x;
-                    av[r4 + 1] = a4.y;
-                    av[r4 + 2] = a4.z;
-                    av[r4 + 3] = a4.w;
+        for (int kq = 0; kq < KC / 4; kq++) {
+            const float *Aq = At + ((kq ^ sw) << 2);
+            float4 a[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; r++) a[r] = *reinterpret_cast<const float4 *>(Aq + r * NRG * KC);
+            float4 p[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) p[j] = *reinterpret_cast<const float4 *>(Ps + (4 * kq + j) * SP + cg * 4);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float pc[4] = {p[j].x, p[j].y, p[j].z, p[j].w};
+#pragma unroll
+                for (int r = 0; r < RPT; r++) {
+                    const float av = j == 0 ? a[r].x : j == 1 ? a[r].y : j == 2 ? a[r].z : a[r].w;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av, pc[c], acc[r][c]);
                 }
             }
-            const float4 pv = *reinterpret_cast<const float4 *>(Ps + kk * SP + cg * 4);
-            const float pc[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-            for (int r = 0; r < RPT; r++)
-#pragma unroll
-                for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av[r], pc[c], acc[r][c]);
         }
-        __syncthreads();
+        release_stage(M, st);
+        seq++;
     }
-    const int kc32 = (n + E_KS32 - 1) / E_KS32;
+    const int kc32 = (n + ks32(SP) - 1) / ks32(SP);
     if (kc32 > 1) {
         // publish this chunk's partial product; the last task of the row block
         // adds all chunks in chunk order
         float *yk = D.Yk + (long long)T.kc * nsp;
 #pragma unroll
         for (int r = 0; r < RPT; r++) {
-            const int row = rg * RPT + r;
+            const int row = rg + NRG * r;
             if (row < nrow)
                 __stcg(reinterpret_cast<float4 *>(yk + (long long)(r0 + row) * SP + cg * 4),
                        make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]));
         }
-        __threadfence();
-        __syncthreads();
+        named_bar(1, P32_T);
         const int rbl = r0 / E_RB32;
-        if (tid == 0) *flag_s = atomicAdd(D.ticket + rbl, 1) == kc32 - 1;
-        __syncthreads();
-        if (!*flag_s) return;
-        __threadfence();
-        if (tid == 0) D.ticket[rbl] = 0;                        // ready for the next tick
+        if (tid == 0) {     // one fence for the CTA's stores (ordered by the barrier)
+            __threadfence();
+            const int last = atomicAdd(D.ticket + rbl, 1) == kc32 - 1;
+            if (last) {
+                __threadfence();
+                D.ticket[rbl] = 0;                              // ready for the next tick
+            }
+            *flag_s = last;
+        }
+        named_bar(1, P32_T);
+        if (!*flag_s) return true;
 #pragma unroll
         for (int r = 0; r < RPT; r++)
 #pragma unroll
@@ -398,7 +432,7 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, f
             const float *yq = D.Yk + (long long)q * nsp;
 #pragma unroll
             for (int r = 0; r < RPT; r++) {
-                const int row = rg * RPT + r;
+                const int row = rg + NRG * r;
                 if (row < nrow) {
                     const float4 v = __ldcg(reinterpret_cast<const float4 *>(yq + (long long)(r0 + row) * SP + cg * 4));
                     acc[r][0] += v.x;
@@ -412,22 +446,24 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, f
     // Y rows of this row block
 #pragma unroll
     for (int r = 0; r < RPT; r++) {
-        const int row = rg * RPT + r;
+        const int row = rg + NRG * r;
         if (row < nrow)
             *reinterpret_cast<float4 *>(out + (long long)(r0 + row) * SP + cg * 4) =
                 make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
     }
     // partial dots over this row block: CG p.q; GMRES v_i.w for i <= it
-    // (the new direction's rows may come from another task: read through L2)
+    // (the new direction's rows may come from another task: read through L2).
+    // Per dot: a shuffle tree over the warp's row groups, then the 8 warps'
+    // sums in warp order; the two halves of Red alternate between dots.
+    double *Red = M.red();
     const int nd = ph == PH_CG ? 1 : it + 1;
-    constexpr int NRG = RB / RPT;               // row groups
-    constexpr int NG = P32_T / SP;              // second-level groups per column
+    const int lane = tid & 31, warp = tid >> 5;
     for (int i = 0; i < nd; i++) {
         const float *vi = ph == PH_CG ? dst : D.V + (long long)i * nsp;
         double pc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
         for (int r = 0; r < RPT; r++) {
-            const int row = rg * RPT + r;
+            const int row = rg + NRG * r;
             if (row < nrow) {
                 const float4 v = __ldcg(reinterpret_cast<const float4 *>(vi + (long long)(r0 + row) * SP + cg * 4));
                 pc[0] += (double)v.x * acc[r][0];
@@ -437,223 +473,403 @@ __device__ __forceinline__ void prod32_task(const EngineDev &E, const Task &T, f
             }
         }
 #pragma unroll
-        for (int c = 0; c < 4; c++) Red[rg * SP + cg * 4 + c] = pc[c];
-        __syncthreads();
-        {   // thread (group g, column c) sums row groups g, g + NG, ... (fixed order)
-            const int c = tid % SP, g = tid / SP;
-            double sacc = 0.0;
-            for (int q = g; q < NRG; q += NG) sacc += Red[q * SP + c];
-            __syncthreads();
-            Red[g * SP + c] = sacc;
-        }
-        __syncthreads();
+        for (int o = NCG; o < 32; o <<= 1)
+#pragma unroll
+            for (int c = 0; c < 4; c++) pc[c] += __shfl_xor_sync(0xffffffffu, pc[c], o);
+        double *Rb = Red + (i & 1) * (PC_W * 32);
+        if (lane < NCG)
+#pragma unroll
+            for (int c = 0; c < 4; c++) Rb[warp * 32 + lane * 4 + c] = pc[c];
+        named_bar(1, P32_T);
         if (tid < 32) {
             double sacc = 0.0;
             if (tid < SP)
-                for (int g = 0; g < NG; g++) sacc += Red[g * SP + tid];
+                for (int w = 0; w < PC_W; w++) sacc += Rb[w * 32 + tid];
             E.part32[((size_t)T.rb * E_PS + i) * 32 + tid] = sacc;
         }
-        __syncthreads();
     }
+    named_bar(1, P32_T);        // Red free for the next task
+    return true;
 }
 
-// ============================================================================
-// eng_prod, refinement residual task: R = B - A X for 8 rows, to about FP64
-// accuracy on the FP32 pipe.  A = A32 + A32lo and X = Xh + Xl are fp32 pairs;
-// each term a x = ah xh + ah xl + al xh (+ al xl, below 2^-48 |a x|, dropped)
-// is accumulated in a (hi, lo) pair: ah xh = p + e exactly (product error by
+// ----------------------------------------------------------------------------
+// consumers: one refinement-residual task, R = B - A X for 256 rows and the
+// task's ks64(SP) columns of A, to about FP64 accuracy on the FP32 pipe.
+// A = A32 + A32lo and X = Xh + Xl are fp32 pairs; each 32-column chunk comes
+// as two stages (A32 tile + Xh rows, then A32lo tile + Xl rows).  Each term
+// a x = ah xh + ah xl + al xh (+ al xl, below 2^-48 |a x|, dropped) is
+// accumulated in a (hi, lo) pair: ah xh = p + e exactly (product error by
 // FMA), hi += p exactly with the rounding error moved to lo (two-sum, Knuth),
-// lo also takes e and the cross terms.  Warp w owns row w, lane l the k = l
-// (mod 32) part of it; the pairs are reduced across the warp in the same
-// arithmetic and the total is formed in FP64.
-// ============================================================================
-struct DS {
-    float h, l;
-};
-
-// (hi, lo) + (hi, lo): the high parts by two-sum, all errors into lo.
-__device__ __forceinline__ DS ds_add(DS a, DS b) {
-    const float s = __fadd_rn(a.h, b.h);
-    const float bv = __fsub_rn(s, a.h);
-    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
-    return DS{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
-}
-
-__device__ __forceinline__ DS ds_shfl_xor(DS v, int o) {
-    return DS{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
-}
-
-// Butterfly transpose-reduction over the warp: each round a lane keeps half of
-// its columns and adds the partner's copy of them; afterwards lane l holds the
-// warp total of column l >> (5 - log2 N0).
-template <int N, int OFF, int N0>
-__device__ __forceinline__ void ds_butterfly(DS (&acc)[N0], int lane) {
-    if constexpr (OFF >= 1) {
-        if constexpr (N > 1) {
-            constexpr int H = N / 2;
-            const bool upper = (lane & OFF) != 0;
-#pragma unroll
-            for (int i = 0; i < H; i++) {
-                const DS send = upper ? acc[i] : acc[i + H];
-                const DS keep = upper ? acc[i + H] : acc[i];
-                acc[i] = ds_add(keep, ds_shfl_xor(send, OFF));
-            }
-            ds_butterfly<H, OFF / 2>(acc, lane);
-        } else {
-            acc[0] = ds_add(acc[0], ds_shfl_xor(acc[0], OFF));
-            ds_butterfly<1, OFF / 2>(acc, lane);
-        }
-    }
-}
-
-template <int N>
-__host__ __device__ constexpr int ilog2() { return N <= 1 ? 0 : 1 + ilog2<N / 2>(); }
-
+// lo also takes e and the cross terms.  Thread tile: RPT rows x 4 columns as
+// in the FP32 product.  The (hi, lo) totals are formed in FP64; split-K
+// partials are added in chunk order by the last task of the row block, which
+// also stores R and the partial ||R_j||^2 of its rows.
+// ----------------------------------------------------------------------------
 template <int SP>
-__device__ __forceinline__ void res_task(const EngineDev &E, const Task &T, int t, float *sm,
-                                         double (*red)[33]) {
-    constexpr int KC = 1024 / SP;               // k per chunk: 32 terms per thread per chunk
-    constexpr int AP = KC + 1;                  // padded row stride of the A chunk
-    constexpr int XS = SP + 1;                  // odd stride: conflict-free column reads
-    constexpr int AV = E_RB64 * KC / P32_T;     // A floats (each of hi / lo) per thread per chunk
-    constexpr int XV = KC * SP / P32_T;         // X floats (each of hi / lo) per thread per chunk
-    static_assert(E_RB64 * 32 == P32_T, "a warp per row");
-    float *Ah = sm, *Al = Ah + E_RB64 * AP, *Xh = Al + E_RB64 * AP, *Xl = Xh + KC * XS;
+__device__ bool res_task(const EngineDev &E, const ProdSmem &M, int &seq, int *flag_s) {
+    constexpr int KC = E_KC32;
+    constexpr int RPT = SP / 4, NCG = SP / 4, NRG = E_RB32 / RPT;
+    static_assert(NRG * NCG == P32_T && NRG % 8 == 0, "thread grid");
+    static_assert(ks64(SP) % KC == 0, "K chunks hold whole shared-memory chunks");
+    const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
+    const int u = M.hdr(seq % PSTAGES)->u;
+    const Task T = E.t64[u];
     const SlotDesc &D = E.desc[T.slot];
     const int n = D.n, s = D.s;
-    const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
-    const int tid = threadIdx.x, row = tid >> 5, lane = tid & 31;
-    const float *A = D.A32, *Alo = D.A32lo, *XH = D.Xh, *XL = D.Xl;
-    const long long lda = D.ld32;
-    float ahr[AV], alr[AV], xhr[XV], xlr[XV];
-    auto prefetch = [&](int k0) {
+    const long long nsp = (long long)n * SP;
+    const int r0 = T.r0, nrow = T.r1 - T.r0;
+    float hi[RPT][4], lo[RPT][4];
 #pragma unroll
-        for (int v = 0; v < AV; v++) {
-            const int e = tid + v * P32_T;
-            const int rr = e / KC, kk = e % KC;
-            const int gr = r0 + rr, gk = k0 + kk;
-            const bool in = gr < r1 && gk < n;
-            const long long o = (long long)gr * lda + gk;
-            ahr[v] = in ? A[o] : 0.0f;
-            alr[v] = in ? Alo[o] : 0.0f;
+    for (int r = 0; r < RPT; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) hi[r][c] = lo[r][c] = 0.0f;
+    const int sw = rg & 7;
+    const int nch = (T.k1 - T.k0 + KC - 1) / KC;
+    for (int ch = 0; ch < nch; ch++) {
+        const int sa = seq % PSTAGES, sb = (seq + 1) % PSTAGES;
+        bool ok = ch == 0 || mbar_wait(M.full(sa), (seq / PSTAGES) & 1);
+        ok = ok && mbar_wait(M.full(sb), ((seq + 1) / PSTAGES) & 1);
+        if (named_bar_or(1, P32_T, !ok)) return false;
+        const int rows = min(KC, n - M.hdr(sa)->k0);         // operand rows present
+        const float *Ah = M.tile(sa) + rg * KC, *Al = M.tile(sb) + rg * KC;
+        const float *Xh = M.opr(sa, 0) + cg * 4, *Xl = M.opr(sb, 0) + cg * 4;
+#pragma unroll 4
+        for (int kk = 0; kk < KC; kk++) {
+            const int off = (((kk >> 2) ^ sw) << 2) + (kk & 3);
+            float ah[RPT], al[RPT];
+#pragma unroll
+            for (int r = 0; r < RPT; r++) {
+                ah[r] = Ah[off + r * NRG * KC];
+                al[r] = Al[off + r * NRG * KC];
+            }
+            float4 xh4 = make_float4(0.f, 0.f, 0.f, 0.f), xl4 = xh4;
+            if (kk < rows) {                                    // beyond n the rows were not copied
+                xh4 = *reinterpret_cast<const float4 *>(Xh + kk * SP);
+                xl4 = *reinterpret_cast<const float4 *>(Xl + kk * SP);
+            }
+            const float xh[4] = {xh4.x, xh4.y, xh4.z, xh4.w}, xl[4] = {xl4.x, xl4.y, xl4.z, xl4.w};
+#pragma unroll
+            for (int r = 0; r < RPT; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    const float p = __fmul_rn(ah[r], xh[c]);
+                    const float pe = fmaf(ah[r], xh[c], -p);            // ah xh - p, exact
+                    const float tc = fmaf(al[r], xh[c], fmaf(ah[r], xl[c], pe));
+                    const float sh = __fadd_rn(hi[r][c], p);
+                    const float bv = __fsub_rn(sh, hi[r][c]);
+                    const float er = __fadd_rn(__fsub_rn(hi[r][c], __fsub_rn(sh, bv)), __fsub_rn(p, bv));
+                    hi[r][c] = sh;
+                    lo[r][c] = __fadd_rn(lo[r][c], __fadd_rn(tc, er));
+                }
         }
+        release_stage(M, sa);
+        release_stage(M, sb);
+        seq += 2;
+    }
+    double v[RPT][4];
 #pragma unroll
-        for (int v = 0; v < XV; v++) {
-            const int e = tid + v * P32_T;             // the chunk is contiguous: rows k0.. of n x SP
-            const bool in = k0 + e / SP < n;
-            const long long o = (long long)k0 * SP + e;
-            xhr[v] = in ? XH[o] : 0.0f;
-            xlr[v] = in ? XL[o] : 0.0f;
+    for (int r = 0; r < RPT; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) v[r][c] = (double)hi[r][c] + (double)lo[r][c];
+    const int kc64 = (n + ks64(SP) - 1) / ks64(SP);
+    if (kc64 > 1) {
+        double *rk = D.Rk + (long long)T.kc * nsp;
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            const int row = rg + NRG * r;
+            if (row < nrow) {
+                double *q = rk + (long long)(r0 + row) * SP + cg * 4;
+                __stcg(reinterpret_cast<double2 *>(q), make_double2(v[r][0], v[r][1]));
+                __stcg(reinterpret_cast<double2 *>(q + 2), make_double2(v[r][2], v[r][3]));
+            }
         }
-    };
-    auto store = [&]() {
-#pragma unroll
-        for (int v = 0; v < AV; v++) {
-            const int e = tid + v * P32_T;
-            Ah[(e / KC) * AP + e % KC] = ahr[v];
-            Al[(e / KC) * AP + e % KC] = alr[v];
+        named_bar(1, P32_T);
+        const int rbl = r0 / E_RB32;
+        if (tid == 0) {     // one fence for the CTA's stores (ordered by the barrier)
+            __threadfence();
+            const int last = atomicAdd(D.ticket + rbl, 1) == kc64 - 1;
+            if (last) {
+                __threadfence();
+                D.ticket[rbl] = 0;                              // ready for the next tick
+            }
+            *flag_s = last;
         }
+        named_bar(1, P32_T);
+        if (!*flag_s) return true;
 #pragma unroll
-        for (int v = 0; v < XV; v++) {
-            const int e = tid + v * P32_T;
-            Xh[(e / SP) * XS + e % SP] = xhr[v];
-            Xl[(e / SP) * XS + e % SP] = xlr[v];
-        }
-    };
-    DS acc[SP];
+        for (int r = 0; r < RPT; r++)
 #pragma unroll
-    for (int c = 0; c < SP; c++) acc[c] = DS{0.0f, 0.0f};
-    prefetch(0);
-    for (int k0 = 0; k0 < n; k0 += KC) {
-        store();
-        __syncthreads();
-        if (k0 + KC < n) prefetch(k0 + KC);
-        if (row < nrow) {
+            for (int c = 0; c < 4; c++) v[r][c] = 0.0;
+        for (int q = 0; q < kc64; q++) {
+            const double *rq = D.Rk + (long long)q * nsp;
 #pragma unroll
-            for (int i = 0; i < KC / 32; i++) {
-                const int kk = lane + 32 * i;
-                const float ah = Ah[row * AP + kk], al = Al[row * AP + kk];
-                const float *xh = Xh + kk * XS, *xl = Xl + kk * XS;
-#pragma unroll
-                for (int c = 0; c < SP; c++) {
-                    if (c < s) {
-                        const float xhc = xh[c];
-                        const float p = __fmul_rn(ah, xhc);
-                        const float pe = fmaf(ah, xhc, -p);             // ah xh - p, exact
-                        const float tc = fmaf(al, xhc, fmaf(ah, xl[c], pe));
-                        const float sh = __fadd_rn(acc[c].h, p);
-                        const float bv = __fsub_rn(sh, acc[c].h);
-                        const float er = __fadd_rn(__fsub_rn(acc[c].h, __fsub_rn(sh, bv)), __fsub_rn(p, bv));
-                        acc[c].h = sh;
-                        acc[c].l = __fadd_rn(acc[c].l, __fadd_rn(tc, er));
-                    }
+            for (int r = 0; r < RPT; r++) {
+                const int row = rg + NRG * r;
+                if (row < nrow) {
+                    const double *pq = rq + (long long)(r0 + row) * SP + cg * 4;
+                    const double2 a = __ldcg(reinterpret_cast<const double2 *>(pq));
+                    const double2 b = __ldcg(reinterpret_cast<const double2 *>(pq + 2));
+                    v[r][0] += a.x;
+                    v[r][1] += a.y;
+                    v[r][2] += b.x;
+                    v[r][3] += b.y;
                 }
             }
         }
-        __syncthreads();
     }
-    ds_butterfly<SP, 16>(acc, lane);
-    constexpr int LG = ilog2<SP>();
-    if ((lane & ((32 >> LG) - 1)) == 0) {
-        const int c = lane >> (5 - LG);
-        double v = 0.0;
+    // R = B - A X for the row block, partial ||R_j||^2 (shuffle tree over the
+    // warp's row groups, then the 8 warps in order)
+    double pc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int r = 0; r < RPT; r++) {
+        const int row = rg + NRG * r;
         if (row < nrow) {
-            const long long o = (long long)(r0 + row) * SP + c;
-            const double rv = c < s ? D.B[o] - ((double)acc[0].h + (double)acc[0].l) : 0.0;
-            D.R[o] = rv;
-            v = rv * rv;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const long long o = (long long)(r0 + row) * SP + cg * 4 + c;
+                const double rv = cg * 4 + c < s ? D.B[o] - v[r][c] : 0.0;
+                D.R[o] = rv;
+                pc[c] += rv * rv;
+            }
         }
-        red[row][c] = v;
     }
-    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = NCG; o < 32; o <<= 1)
+#pragma unroll
+        for (int c = 0; c < 4; c++) pc[c] += __shfl_xor_sync(0xffffffffu, pc[c], o);
+    double *Rb = M.red();
+    if (lane < NCG)
+#pragma unroll
+        for (int c = 0; c < 4; c++) Rb[warp * 32 + lane * 4 + c] = pc[c];
+    named_bar(1, P32_T);
     if (tid < 32) {
         double sacc = 0.0;
         if (tid < SP)
-            for (int rr = 0; rr < nrow; rr++) sacc += red[rr][tid];
-        E.part64[(size_t)t * 32 + tid] = sacc;
+            for (int w = 0; w < PC_W; w++) sacc += Rb[w * 32 + tid];
+        E.part64[(size_t)T.rb * 32 + tid] = sacc;
     }
-    __syncthreads();
+    named_bar(1, P32_T);        // Red free for the next task
+    return true;
 }
 
-// One queue per tick: the refinement-residual tasks first, then the FP32
-// product tasks; tasks of slots in other phases are skipped.
-__global__ void __launch_bounds__(P32_T, 2) eng_prod_kernel(const EngineDev *Ep) {
-    const EngineDev &E = *Ep;
-    extern __shared__ __align__(16) unsigned char esm[];
-    float *As = reinterpret_cast<float *>(esm);                         // [KC][RB + 4]
-    float *Ps = As + E_KC32 * (E_RB32 + 4);                             // [KC][SP]
-    double *Red = reinterpret_cast<double *>(Ps + E_KC32 * 32);         // [row groups][SP]
-    __shared__ double red64[E_RB64][33];
-    __shared__ float colscale[32];
-    __shared__ int colstop[32];
-    __shared__ int claim_s, flag_s;
-    eng_count(E);
-    const int total = E.n64 + E.n32;
-    for (int u = claim(E.active + 5, &claim_s); u < total; u = claim(E.active + 5, &claim_s)) {
-        if (u < E.n64) {
-            const Task T = E.t64[u];
-            if (T.slot < 0) continue;                                   // unused entry
-            if (E.st[T.slot].phase != PH_RESID) continue;
-            float *sm = reinterpret_cast<float *>(esm);
-            switch (E.desc[T.slot].sp) {
-                case 4: res_task<4>(E, T, u, sm, red64); break;
-                case 8: res_task<8>(E, T, u, sm, red64); break;
-                case 16: res_task<16>(E, T, u, sm, red64); break;
-                default: res_task<32>(E, T, u, sm, red64); break;
-            }
-        } else {
-            const Task T = E.t32[u - E.n64];
-            if (T.slot < 0) continue;
-            const int ph = E.st[T.slot].phase;
-            if (ph != PH_CG && ph != PH_GM) continue;
-            switch (E.desc[T.slot].sp) {
-                case 4: prod32_task<4>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
-                case 8: prod32_task<8>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
-                case 16: prod32_task<16>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
-                default: prod32_task<32>(E, T, As, Ps, Red, colscale, colstop, &flag_s); break;
+// At admission (START), the FP32 product tasks' tiles of A are split instead:
+// A = A32 + A32lo, rows [r0, r1) x columns [k0, k1), a warp per row.
+__device__ __forceinline__ void convert_task(const SlotDesc &D, const Task &T) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = T.r0 + warp; r < T.r1; r += P32_T / 32) {
+        const double *a = D.A64 + (long long)r * D.lda64;
+        float *a32 = D.A32 + (long long)r * D.ld32;
+        float *alo = D.A32lo + (long long)r * D.ld32;
+        for (int kb = T.k0 + lane; kb < T.k1; kb += 4 * 32) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = kb + 32 * u < T.k1 ? a[kb + 32 * u] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (kb + 32 * u < T.k1) {
+                    const float hi = __double2float_rn(v[u]);
+                    a32[kb + 32 * u] = hi;
+                    alo[kb + 32 * u] = __double2float_rn(v[u] - (double)hi);
+                }
             }
         }
-        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// producer: fills one stage (header by all 32 lanes, copies by lane 0).
+// ----------------------------------------------------------------------------
+// Lane 0 waits until the consumers have released the stage of sequence
+// number seq's previous use; the outcome is the same in every lane.
+__device__ __forceinline__ bool wait_empty(const ProdSmem &M, int seq) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0 && seq >= PSTAGES)
+        ok = mbar_wait(M.empty(seq % PSTAGES), ((seq / PSTAGES) - 1) & 1);
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep) {
+    const EngineDev &E = *Ep;
+    extern __shared__ __align__(16) unsigned char esm[];
+    ProdSmem M;
+    M.base = esm + ((1024 - (smem_u32(esm) & 1023)) & 1023);             // 1024-aligned tiles
+    __shared__ int flag_s;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    eng_count(E);
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < PSTAGES; st++) {
+            mbar_init(M.full(st), 32);
+            mbar_init(M.empty(st), PC_W);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int par = (E.active[A_TICKS] - 1) & 1;               // list set of this tick
+    if (warp == PC_W) {
+        // ---------------- producer warp ----------------
+        const int total = E.active[A_LEN_PROD + par];
+        const int *wp = E.work[par];
+        int seq = 0;
+        bool fail = false;
+        auto push_marker = [&](int kind, int u) -> bool {
+            if (!wait_empty(M, seq)) return false;
+            StageHdr *H = M.hdr(seq % PSTAGES);
+            if (lane == 0) {
+                H->kind = kind;
+                H->u = u;
+                H->flags = 0;
+            }
+            mbar_arrive(M.full(seq % PSTAGES));
+            seq++;
+            return true;
+        };
+        for (;;) {
+            int w = 0;
+            if (lane == 0) w = atomicAdd(E.active + A_CLAIM_PROD, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (w >= total) break;
+            const int u = wp[w];
+            const Task T = u < E.n64 ? E.t64[u] : E.t32[u - E.n64];
+            if (T.slot < 0) continue;                                   // unused entry
+            const int ph = E.st[T.slot].phase;
+            if (u >= E.n64 && ph == PH_START) {                         // A split: run by the consumers
+                if (!push_marker(SK_GENERIC, u)) { fail = true; break; }
+                continue;
+            }
+            if (u < E.n64) {                                            // refinement residual
+                if (ph != PH_RESID) continue;
+                const SlotDesc &D = E.desc[T.slot];
+                const int n = D.n, sp = D.sp;
+                const void *mh = E.tmaps + (size_t)T.slot * 256, *ml = E.tmaps + (size_t)T.slot * 256 + 128;
+                if (lane == 0) {
+                    tmap_acquire(mh);
+                    tmap_acquire(ml);
+                }
+                for (int k0 = T.k0; k0 < T.k1 && !fail; k0 += E_KC32) {
+                    const unsigned ob = (unsigned)(min(E_KC32, n - k0) * sp * 4);
+                    for (int half = 0; half < 2; half++) {              // A32 + Xh, then A32lo + Xl
+                        if (!wait_empty(M, seq)) { fail = true; break; }
+                        const int st = seq % PSTAGES;
+                        if (lane == 0) {
+                            StageHdr *H = M.hdr(st);
+                            H->kind = SK_RES;
+                            H->u = u;
+                            H->k0 = k0;
+                            H->flags = 0;
+                            H->slot = T.slot;
+                            H->sp = sp;
+                            mbar_arrive_expect_tx(M.full(st), TILE_B + ob);
+                            tma_load_2d(M.tile(st), half ? ml : mh, k0, T.r0, M.full(st));
+                            bulk_load_1d(M.opr(st, 0), (half ? D.Xl : D.Xh) + (long long)k0 * sp, ob, M.full(st));
+                        } else {
+                            mbar_arrive(M.full(st));
+                        }
+                        seq++;
+                    }
+                }
+                if (fail) break;
+                continue;
+            }
+            if (ph != PH_CG && ph != PH_GM) continue;
+            const SlotDesc &D = E.desc[T.slot];
+            const SlotState &S = E.st[T.slot];
+            const int n = D.n, sp = D.sp, it = S.it;
+            const long long nsp = (long long)n * sp;
+            const float *src, *src2 = nullptr;
+            if (ph == PH_CG) {
+                src = D.Rf;                                             // P = Rf + beta P'
+                src2 = it > 0 ? D.P + ((it + 1) & 1) * nsp : nullptr;
+            } else {
+                src = D.W + (it & 1) * nsp;                             // V_k = W / h
+            }
+            const int stp = lane < D.s ? S.colstop[lane] : 1;
+            float sc = 0.0f;
+            if (!stp) sc = ph == PH_CG ? (float)S.beta[lane] : (float)(1.0 / S.hnorm[lane]);
+            const void *tmap = E.tmaps + (size_t)T.slot * 256;
+            if (lane == 0) tmap_acquire(tmap);
+            for (int k0 = T.k0; k0 < T.k1; k0 += E_KC32) {
+                if (!wait_empty(M, seq)) { fail = true; break; }
+                const int st = seq % PSTAGES;
+                StageHdr *H = M.hdr(st);
+                H->colscale[lane] = sc;
+                H->colstop[lane] = stp;
+                const int rows = min(E_KC32, n - k0);
+                const unsigned ob = (unsigned)(rows * sp * 4);
+                if (lane == 0) {
+                    H->kind = SK_PROD;
+                    H->u = u;
+                    H->k0 = k0;
+                    H->flags = (k0 == T.k0 ? SF_FIRST : 0) | (k0 + E_KC32 >= T.k1 ? SF_LAST : 0) |
+                               (src2 ? SF_SRC2 : 0);
+                    H->slot = T.slot;
+                    H->sp = sp;
+                    mbar_arrive_expect_tx(M.full(st), TILE_B + ob + (src2 ? ob : 0));
+                    tma_load_2d(M.tile(st), tmap, k0, T.r0, M.full(st));
+                    bulk_load_1d(M.opr(st, 0), src + (long long)k0 * sp, ob, M.full(st));
+                    if (src2) bulk_load_1d(M.opr(st, 1), src2 + (long long)k0 * sp, ob, M.full(st));
+                } else {
+                    mbar_arrive(M.full(st));
+                }
+                seq++;
+            }
+            if (fail) break;
+        }
+        if (!fail && !push_marker(SK_STOP, 0)) fail = true;
+        if (fail && lane == 0) atomicExch(E.active + A_ERR, 1);     // the consumers time out too
+        // never leave with copies in flight
+        if (lane == 0)
+            for (int i = seq > PSTAGES ? seq - PSTAGES : 0; i < seq; i++)
+                if (!mbar_wait(M.full(i % PSTAGES), (i / PSTAGES) & 1)) atomicExch(E.active + A_ERR, 1);
+        __syncwarp();
+    } else {
+        // ---------------- consumer warps ----------------
+        int seq = 0;
+        for (;;) {
+            const int st = seq % PSTAGES;
+            const bool ok = mbar_wait(M.full(st), (seq / PSTAGES) & 1);
+            if (named_bar_or(1, P32_T, !ok)) {
+                if (threadIdx.x == 0) atomicExch(E.active + A_ERR, 1);
+                break;
+            }
+            const StageHdr &H = *M.hdr(st);
+            const int kind = H.kind;
+            if (kind == SK_STOP) break;
+            if (kind == SK_GENERIC) {
+                const int u = H.u;
+                named_bar(1, P32_T);                                    // header read by all
+                release_stage(M, st);
+                seq++;
+                const Task T = E.t32[u - E.n64];
+                convert_task(E.desc[T.slot], T);
+                continue;
+            }
+            if (kind == SK_RES) {
+                bool good;
+                switch (H.sp) {
+                    case 4: good = res_task<4>(E, M, seq, &flag_s); break;
+                    case 8: good = res_task<8>(E, M, seq, &flag_s); break;
+                    case 16: good = res_task<16>(E, M, seq, &flag_s); break;
+                    default: good = res_task<32>(E, M, seq, &flag_s); break;
+                }
+                if (!good) {
+                    if (threadIdx.x == 0) atomicExch(E.active + A_ERR, 1);
+                    break;
+                }
+                continue;
+            }
+            bool good;
+            switch (H.sp) {
+                case 4: good = prod_task<4>(E, M, seq, &flag_s); break;
+                case 8: good = prod_task<8>(E, M, seq, &flag_s); break;
+                case 16: good = prod_task<16>(E, M, seq, &flag_s); break;
+                default: good = prod_task<32>(E, M, seq, &flag_s); break;
+            }
+            if (!good) {
+                if (threadIdx.x == 0) atomicExch(E.active + A_ERR, 1);
+                break;
+            }
+        }
     }
 }
 
@@ -670,8 +886,13 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
     __shared__ double colv_s[32];
     __shared__ int claim_s;
     eng_count(E);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int t = claim(E.active + 7, &claim_s); t < E.nv; t = claim(E.active + 7, &claim_s)) {
+    const int tid = threadIdx.x;
+    const int par = (E.active[A_TICKS] - 1) & 1;               // list set of this tick
+    const int total = E.active[A_LEN_VEC + par];
+    const int *wv = E.work[par] + E.wvec;
+    for (int w = claim(E.active + A_CLAIM_VEC, &claim_s); w < total;
+         w = claim(E.active + A_CLAIM_VEC, &claim_s)) {
+        const int t = wv[w];
         const Task T = E.tv[t];
         if (T.slot < 0) continue;                                       // unused entry
         const SlotDesc &D = E.desc[T.slot];
@@ -705,80 +926,149 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                 hsm[ii][c] = hs;
             }
         }
-        if (ph == PH_START) {   // A = A32 + A32lo for this task's rows, a warp per row
-            for (int r = T.r0 + warp; r < T.r1; r += VEC_T / 32) {
-                const double *a = D.A64 + (long long)r * D.lda64;
-                float *a32 = D.A32 + (long long)r * D.ld32;
-                float *alo = D.A32lo + (long long)r * D.ld32;
-                for (int k = lane; k < n; k += 32) {
-                    const double v = a[k];
-                    const float hi = __double2float_rn(v);
-                    a32[k] = hi;
-                    alo[k] = __double2float_rn(v - (double)hi);
-                }
-            }
-            if (T.r0 == 0)      // split-K tickets of the FP32 product start at zero
-                for (int b = tid; b < D.nb32; b += VEC_T) D.ticket[b] = 0;
-        }
+        if (ph == PH_START && T.r0 == 0)   // split-K tickets of the FP32 product start at zero
+            for (int b = tid; b < D.nb32; b += VEC_T) D.ticket[b] = 0;
         __syncthreads();
+        // The task's rows form one contiguous stretch of the n x sp block;
+        // thread t always sees column t % sp (sp divides VEC_T).  Elements are
+        // handled VU at a time, all loads first, so they are in flight
+        // together (the stores may alias the loads as far as the compiler
+        // knows, so it would not batch them itself).
+        constexpr int VU = 4;
         const long long e0 = (long long)T.r0 * sp, e1 = (long long)T.r1 * sp;
         const int c = tid % sp;                                        // fixed for this thread
         const bool live = c < s;
         double part = 0.0;
         if (ph == PH_START) {
-            for (long long e = e0 + tid; e < e1; e += VEC_T) {
-                const double b = D.B[e];
-                D.X[e] = 0.0;
-                D.Xh[e] = 0.0f;
-                D.Xl[e] = 0.0f;
-                D.R[e] = b;
-                part += b * b;
+            for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
+                double b[VU];
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    b[u] = e < e1 ? D.B[e] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    if (e < e1) {
+                        D.X[e] = 0.0;
+                        D.Xh[e] = 0.0f;
+                        D.Xl[e] = 0.0f;
+                        D.R[e] = b[u];
+                        part += b[u] * b[u];
+                    }
+                }
             }
         } else if (ph == PH_INIT) {
             const bool on = live && !S.conv[c];
             const double rn = colv_s[c];
-            for (long long e = e0 + tid; e < e1; e += VEC_T) {
-                const float f = on ? (float)(D.R[e] / rn) : 0.0f;
-                D.Rf[e] = f;
-                D.Z[e] = 0.0f;
-                if (D.method != LS_METHOD_CG) D.W[e] = f;               // W buffer 0
-                part += (double)f * (double)f;
+            const bool gm = D.method != LS_METHOD_CG;
+            for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
+                double r[VU];
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    r[u] = e < e1 ? D.R[e] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    if (e < e1) {
+                        const float f = on ? (float)(r[u] / rn) : 0.0f;
+                        D.Rf[e] = f;
+                        D.Z[e] = 0.0f;
+                        if (gm) D.W[e] = f;                             // W buffer 0
+                        part += (double)f * (double)f;
+                    }
+                }
             }
         } else if (ph == PH_CG) {
             const float al = (float)colv_s[c];
             const float *p = D.P + (it & 1) * nsp;
-            for (long long e = e0 + tid; e < e1; e += VEC_T) {
-                D.Z[e] = fmaf(al, p[e], D.Z[e]);
-                const float rv = fmaf(-al, D.Q[e], D.Rf[e]);
-                D.Rf[e] = rv;
-                part += (double)rv * (double)rv;
+            for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
+                float z[VU], pv[VU], q[VU], r[VU];
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    const bool in = e < e1;
+                    z[u] = in ? D.Z[e] : 0.0f;
+                    pv[u] = in ? __ldcg(p + e) : 0.0f;                 // written by other CTAs
+                    q[u] = in ? __ldcg(D.Q + e) : 0.0f;
+                    r[u] = in ? D.Rf[e] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    if (e < e1) {
+                        D.Z[e] = fmaf(al, pv[u], z[u]);
+                        const float rv = fmaf(-al, q[u], r[u]);
+                        D.Rf[e] = rv;
+                        part += (double)rv * (double)rv;
+                    }
+                }
             }
         } else if (ph == PH_GM) {
             float *w = D.W + ((it + 1) & 1) * nsp;
-            for (long long e = e0 + tid; e < e1; e += VEC_T) {
-                double wv = w[e];
-                for (int q = 0; q <= it; q++) wv -= hsm[q][c] * (double)D.V[(long long)q * nsp + e];
-                const float wf = (float)wv;
-                w[e] = wf;
-                part += (double)wf * (double)wf;
+            for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
+                double wv[VU];
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    wv[u] = e < e1 ? (double)__ldcg(w + e) : 0.0;
+                }
+                for (int q = 0; q <= it; q++) {
+                    const float *vq = D.V + (long long)q * nsp;
+                    const double hq = hsm[q][c];
+#pragma unroll
+                    for (int u = 0; u < VU; u++) {
+                        const long long e = eb + (long long)u * VEC_T;
+                        if (e < e1) wv[u] -= hq * (double)__ldcg(vq + e);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < VU; u++) {
+                    const long long e = eb + (long long)u * VEC_T;
+                    if (e < e1) {
+                        const float wf = (float)wv[u];
+                        w[e] = wf;
+                        part += (double)wf * (double)wf;
+                    }
+                }
             }
         } else if (ph == PH_UPDATE) {
             const double rn = colv_s[c];
             if (live && rn != 0.0) {
-                const int kj = D.method == LS_METHOD_CG ? 0 : (int)S.alpha[c];
-                for (long long e = e0 + tid; e < e1; e += VEC_T) {
-                    double d;
-                    if (D.method == LS_METHOD_CG) {
-                        d = (double)D.Z[e];
-                    } else {
-                        d = 0.0;
-                        for (int q = 0; q < kj; q++) d += S.yv[c][q] * (double)D.V[(long long)q * nsp + e];
+                const bool cgm = D.method == LS_METHOD_CG;
+                const int kj = cgm ? 0 : (int)S.alpha[c];
+                for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
+                    double d[VU], x[VU];
+#pragma unroll
+                    for (int u = 0; u < VU; u++) {
+                        const long long e = eb + (long long)u * VEC_T;
+                        const bool in = e < e1;
+                        x[u] = in ? D.X[e] : 0.0;
+                        d[u] = (in && cgm) ? (double)D.Z[e] : 0.0;
                     }
-                    const double xn = D.X[e] + rn * d;
-                    const float xh = __double2float_rn(xn);
-                    D.X[e] = xn;
-                    D.Xh[e] = xh;
-                    D.Xl[e] = __double2float_rn(xn - (double)xh);
+                    for (int q = 0; q < kj; q++) {
+                        const float *vq = D.V + (long long)q * nsp;
+                        const double yq = S.yv[c][q];
+#pragma unroll
+                        for (int u = 0; u < VU; u++) {
+                            const long long e = eb + (long long)u * VEC_T;
+                            if (e < e1) d[u] += yq * (double)vq[e];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < VU; u++) {
+                        const long long e = eb + (long long)u * VEC_T;
+                        if (e < e1) {
+                            const double xn = x[u] + rn * d[u];
+                            const float xh = __double2float_rn(xn);
+                            D.X[e] = xn;
+                            D.Xh[e] = xh;
+                            D.Xl[e] = __double2float_rn(xn - (double)xh);
+                        }
+                    }
                 }
             }
         }
@@ -842,11 +1132,9 @@ EngineKernels engine_kernels() {
     K.admit = reinterpret_cast<void *>(&eng_admit_kernel);
     K.finish = reinterpret_cast<void *>(&eng_finish_kernel);
     K.red_threads = RED_T;
-    K.prod_threads = P32_T;
+    K.prod_threads = PROD_T;
     K.vec_threads = VEC_T;
-    // FP32 product: transposed A chunk (+ padding), operand chunk, reduction
-    // scratch (P32_T x 4 doubles); the residual tasks reuse the same bytes
-    K.prod_smem = (size_t)E_KC32 * (E_RB32 + 4) * 4 + E_KC32 * 32 * 4 + (size_t)E_RB32 * 32 / 4 * 8;
+    K.prod_smem = PROD_SMEM;
     return K;
 }
 

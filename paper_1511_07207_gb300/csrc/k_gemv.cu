@@ -604,6 +604,22 @@ bool make_tensor_map(MatDesc *h, int dtype, const void *ptr, int rows, int cols,
     return true;
 }
 
+bool encode_f32_tile_map_sw128(void *map, const float *ptr, int rows, int cols, long long ld,
+                               int box_cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || rows <= 0 || cols <= 0 || box_cols * 4 > 128) return false;
+    if (((uintptr_t)ptr & 15) != 0 || ((ld * 4) & 15) != 0 || ((uintptr_t)map & 63) != 0) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<float *>(ptr), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ---- quantisation of A (stage A, done once per solve) ------------------------------------
 // BF16: round-to-nearest-even directly from FP64.  FP32: the same to FP32.
 // FP8-e4m3: s_i = fp32(max_j |a_ij| / 448) (1 when that is 0), then

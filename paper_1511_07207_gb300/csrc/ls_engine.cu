@@ -62,13 +62,14 @@ SlotSizes slot_sizes(int n, int s, int method, int m) {
     const size_t nsp = (size_t)n * z.sp;
     z.bytes = 0;
     auto add = [&](size_t b) { z.bytes += align_up(b, 256); };
-    const SlotTasks tk = slot_tasks(n);
+    const SlotTasks tk = slot_tasks(n, z.sp);
     add((size_t)n * z.ld32 * 4);              // A32
     add((size_t)n * z.ld32 * 4);              // A32lo
     add(nsp * 8); add(nsp * 8); add(nsp * 8); // X, B, R
     add(nsp * 4); add(nsp * 4);               // Xh, Xl
     add(nsp * 4); add(nsp * 4); add(nsp * 4); // Rf, Z, Q
     if (tk.kc32 > 1) add((size_t)tk.kc32 * nsp * 4);                // Yk
+    if (tk.kc64 > 1) add((size_t)tk.kc64 * nsp * 8);                // Rk
     add((size_t)(tk.rb32 > 0 ? tk.rb32 : 1) * sizeof(int));         // ticket
     if (method == LS_METHOD_CG) add(2 * nsp * 4);                   // P
     else { add(2 * nsp * 4); add((size_t)(m + 1) * nsp * 4); }      // W, V
@@ -85,7 +86,7 @@ void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int m
     D.sp = z.sp;
     D.method = method;
     D.m = m;
-    const SlotTasks tk = slot_tasks(n);
+    const SlotTasks tk = slot_tasks(n, z.sp);
     D.A32 = cv.take<float>((size_t)n * z.ld32);
     D.A32lo = cv.take<float>((size_t)n * z.ld32);
     D.ld32 = z.ld32;
@@ -98,6 +99,7 @@ void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int m
     D.Z = cv.take<float>(nsp);
     D.Q = cv.take<float>(nsp);
     D.Yk = tk.kc32 > 1 ? cv.take<float>((size_t)tk.kc32 * nsp) : nullptr;
+    D.Rk = tk.kc64 > 1 ? cv.take<double>((size_t)tk.kc64 * nsp) : nullptr;
     D.ticket = cv.take<int>(tk.rb32 > 0 ? tk.rb32 : 1);
     D.P = nullptr;
     D.W = nullptr;
@@ -143,9 +145,14 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
         hE.t64 = k.take<Task>(cap64);
         hE.tv = k.take<Task>(capv);
         hE.part32 = k.take<double>((size_t)capb * E_PS * 32);
-        hE.part64 = k.take<double>((size_t)cap64 * 32);
+        hE.part64 = k.take<double>((size_t)capb * 32);
         hE.partv = k.take<double>((size_t)capv * 32);
-        hE.active = k.take<int>(8);
+        hE.order = k.take<int>(cap_slots);
+        hE.tmaps = k.take<unsigned char>((size_t)cap_slots * 256);
+        hE.work[0] = k.take<int>((size_t)cap64 + cap32 + capv);
+        hE.work[1] = k.take<int>((size_t)cap64 + cap32 + capv);
+        hE.wvec = cap64 + cap32;
+        hE.active = k.take<int>(A_SIZE);
         hE.launches = k.take<unsigned long long>(1);
         bsrc = k.take<const double *>(cap_slots);
         ldb = k.take<long long>(cap_slots);
@@ -165,7 +172,7 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
     layout(real);
     if (cudaMemsetAsync(dmem, 0, dbytes, c->stream) != cudaSuccess) return LS_ERR_CUDA;
     K = engine_kernels();
-    grid_prod = 2 * c->num_sms;
+    grid_prod = c->num_sms;                 // one warp-specialised CTA per SM
     grid_vec = 2 * c->num_sms;
     cudaFuncSetAttribute(K.prod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod_smem);
     return build_graph();
@@ -215,7 +222,7 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     h64.clear();
     hv.clear();
     nb32 = 0;
-    const SlotTasks per = slot_tasks(fixed_max_n);
+    const SlotTasks per = slot_tasks(fixed_max_n, 32);   // the widest slot has the most tasks
     const Task none{-1, 0, 0, 0, 0, 0, 0, 0};
     auto region = [&](std::vector<Task> &tab, int q, int per_slot, int &t0) {
         if (fixed_max_n) {
@@ -231,7 +238,8 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     };
     // packed tables list the costliest slots first (tasks are claimed in
     // table order, so the long ones start early and the short ones fill in)
-    std::vector<int> order(hd.size());
+    std::vector<int> &order = h_order;
+    order.resize(hd.size());
     for (int q = 0; q < (int)hd.size(); q++) order[q] = q;
     if (!fixed_max_n)
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -240,7 +248,8 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     for (int q : order) {
         SlotDesc &D = hd[q];
         const int n = D.n > 0 ? D.n : 0;
-        const SlotTasks tk = slot_tasks(n);
+        const SlotTasks tk = slot_tasks(n, D.sp);
+        const int ks = ks32(D.sp);
         // FP32 product: row block x K chunk; row blocks own the partial dots
         region(h32, q, per.t32, D.t32);
         D.b32 = fixed_max_n ? q * per.rb32 : nb32;
@@ -248,20 +257,28 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
         D.n32 = 0;
         for (int b = 0; b < tk.rb32; b++)
             for (int kc = 0; kc < tk.kc32; kc++) {
-                const Task t{q, b * E_RB32, std::min(n, (b + 1) * E_RB32), kc * E_KS32,
-                             std::min(n, (kc + 1) * E_KS32), kc, D.b32 + b, 0};
+                const Task t{q, b * E_RB32, std::min(n, (b + 1) * E_RB32), kc * ks,
+                             std::min(n, (kc + 1) * ks), kc, D.b32 + b, 0};
                 put(h32, D.t32 + D.n32, t);
                 D.n32++;
             }
         if (!fixed_max_n) nb32 += tk.rb32;
+        // refinement residual: row block x K chunk (the same row blocks)
         region(h64, q, per.t64, D.t64);
         D.n64 = 0;
-        for (int r = 0; r < n; r += E_RB64, D.n64++)
-            put(h64, D.t64 + D.n64, Task{q, r, std::min(n, r + E_RB64), 0, 0, 0, 0, 0});
+        const int k64 = ks64(D.sp);
+        for (int b = 0; b < tk.rb32; b++)
+            for (int kc = 0; kc < tk.kc64; kc++) {
+                const Task t{q, b * E_RB32, std::min(n, (b + 1) * E_RB32), kc * k64,
+                             std::min(n, (kc + 1) * k64), kc, D.b32 + b, 0};
+                put(h64, D.t64 + D.n64, t);
+                D.n64++;
+            }
         region(hv, q, per.tv, D.tv);
         D.nv = 0;
-        for (int r = 0; r < n; r += E_RBV, D.nv++)
-            put(hv, D.tv + D.nv, Task{q, r, std::min(n, r + E_RBV), 0, 0, 0, 0, 0});
+        const int rv = rbv(D.sp);
+        for (int r = 0; r < n; r += rv, D.nv++)
+            put(hv, D.tv + D.nv, Task{q, r, std::min(n, r + rv), 0, 0, 0, 0, 0});
     }
     if (fixed_max_n) nb32 = (int)hd.size() * per.rb32;
 }
@@ -275,7 +292,7 @@ int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables)
     cudaError_t e = cudaSuccess;
     if (!tables) {   // same slot set: only the loop counters are reset
         e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, 8 * sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, A_SIZE * sizeof(int), c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         return map_cuda(e);
     }
@@ -288,8 +305,25 @@ int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables)
         e = cudaMemcpyAsync(hE.t64, h64.data(), h64.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !hv.empty())
         e = cudaMemcpyAsync(hE.tv, hv.data(), hv.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !h_order.empty())
+        e = cudaMemcpyAsync(hE.order, h_order.data(), h_order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream);
+    // TMA maps of every resident slot's A32 and A32lo (read by eng_prod's
+    // producer warp)
+    h_tmaps.assign(hd.size() * 256 + 64, 0);
+    unsigned char *maps = h_tmaps.data() + ((64 - ((uintptr_t)h_tmaps.data() & 63)) & 63);
+    for (size_t q = 0; q < hd.size() && e == cudaSuccess; q++) {
+        const SlotDesc &D = hd[q];
+        if (D.n <= 0 || !D.A32) continue;
+        if (!encode_f32_tile_map_sw128(maps + q * 256, D.A32, D.n, D.n, D.ld32, E_KC32, E_RB32) ||
+            !encode_f32_tile_map_sw128(maps + q * 256 + 128, D.A32lo, D.n, D.n, D.ld32, E_KC32, E_RB32))
+            return LS_ERR_CUDA;
+    }
+    if (e == cudaSuccess && !hd.empty())
+        e = cudaMemcpyAsync(const_cast<unsigned char *>(hE.tmaps), maps, hd.size() * 256, cudaMemcpyHostToDevice,
+                            c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, 8 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, A_SIZE * sizeof(int), c->stream);
     // the host copies above read pageable memory: make them complete before
     // the host vectors can change
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -343,9 +377,13 @@ int Engine::collect(int first, int count, std::vector<SlotResult> &out) {
     if (count <= 0) return LS_OK;
     eng_collect_kernel<<<(count + 127) / 128, 128, 0, c->stream>>>(hE.desc, hE.st, results + first,
                                                                    first, count);
+    int err = 0;
     cudaError_t e = cudaMemcpyAsync(out.data(), results + first, count * sizeof(SlotResult),
                                     cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&err, hE.active + A_ERR, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && err) return LS_ERR_TIMEOUT;
     return map_cuda(e);
 }
 
@@ -451,7 +489,7 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
         x_dev[q] = is_device_ptr(S.X);
         total += z[q].bytes + (a_dev[q] ? 0 : z[q].stageA) + (b_dev[q] ? 0 : z[q].stageBX) +
                  (x_dev[q] ? 0 : z[q].stageBX);
-        const SlotTasks tk = slot_tasks(S.n);
+        const SlotTasks tk = slot_tasks(S.n, z[q].sp);
         n32 += tk.t32;
         nb32 += tk.rb32;
         n64 += tk.t64;

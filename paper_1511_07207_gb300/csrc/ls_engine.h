@@ -31,14 +31,13 @@ constexpr int E_MAXM = 32;                 // GMRES restart length in the engine
 constexpr int E_RB32 = 256;                // rows per FP32 product task (any width)
 constexpr int E_KS32 = 512;                // columns of A per FP32 product task (split K)
 constexpr int E_KC32 = 32;                 // k per shared-memory chunk of the FP32 product
-constexpr int E_RB64 = 8;                  // rows per refinement-residual task
-constexpr int E_RBV = 256;                 // rows per vector task
+constexpr int E_VEL = 8192;                // elements of the n x sp block per vector task
 constexpr int E_PS = E_MAXM + 2;           // partial-dot slots per FP32 row block
 
 // slot phases: what eng_prod / eng_vec do in the current tick
 enum : int {
     PH_FREE = 0,
-    PH_START = 1,     // vec: X = 0, R = B, partial ||B||^2
+    PH_START = 1,     // prod: A = A32 + A32lo; vec: X = 0, R = B, partial ||B||^2
     PH_RESID = 2,     // prod (FP64): R = B - A X, partial ||R||^2
     PH_INIT = 3,      // vec: Rf = R / ||R||, Z = 0 (GMRES: W0 = Rf), partial ||Rf||^2
     PH_CG = 4,        // prod: P = Rf + beta P', Q = Ahat P, partial P.Q; vec: Z, Rf, ||Rf||^2
@@ -48,23 +47,35 @@ enum : int {
     PH_ADMIT = 8,     // just admitted: eng_red turns it into START (nothing to reduce yet)
 };
 
-// Work decomposition of one slot of size n (the same for any s, so a slot's
-// reduction order never depends on its neighbours).
+// Columns of A per FP32 product task for a padded width sp.
+__host__ __device__ constexpr int ks32(int) { return E_KS32; }
+// Columns of A per refinement-residual task (256 rows): the double-single
+// arithmetic costs 12 FP32 operations per term, so about the same time per
+// task for every width.
+__host__ __device__ constexpr int ks64(int sp) { return 4096 / (sp > 0 ? sp : 32); }
+
+// Rows per vector task: the same number of elements for any width.
+__host__ __device__ constexpr int rbv(int sp) { return E_VEL / (sp > 0 ? sp : 32); }
+
+// Work decomposition of one slot of size n and padded width sp (it depends on
+// nothing else, so a slot's reduction order never depends on its neighbours).
 struct SlotTasks {
     int rb32;        // FP32 row blocks (E_RB32 rows each)
-    int kc32;        // K chunks per row block (E_KS32 columns of A each)
+    int kc32;        // K chunks per row block (ks32(sp) columns of A each)
     int t32;         // FP32 product tasks = rb32 * kc32
-    int t64;         // residual tasks (E_RB64 rows each)
-    int tv;          // vector tasks (E_RBV rows each)
+    int kc64;        // K chunks per row block of the residual (ks64(sp) columns each)
+    int t64;         // residual tasks = rb32 * kc64
+    int tv;          // vector tasks (rbv(sp) rows each)
 };
-__host__ __device__ inline SlotTasks slot_tasks(int n) {
+__host__ __device__ inline SlotTasks slot_tasks(int n, int sp) {
     SlotTasks t;
     n = n > 0 ? n : 0;
     t.rb32 = (n + E_RB32 - 1) / E_RB32;
-    t.kc32 = n > 0 ? (n + E_KS32 - 1) / E_KS32 : 0;
+    t.kc32 = n > 0 ? (n + ks32(sp) - 1) / ks32(sp) : 0;
     t.t32 = t.rb32 * t.kc32;
-    t.t64 = (n + E_RB64 - 1) / E_RB64;
-    t.tv = (n + E_RBV - 1) / E_RBV;
+    t.kc64 = n > 0 ? (n + ks64(sp) - 1) / ks64(sp) : 0;
+    t.t64 = t.rb32 * t.kc64;
+    t.tv = (n + rbv(sp) - 1) / rbv(sp);
     return t;
 }
 
@@ -85,13 +96,14 @@ struct SlotDesc {                // written at admission
     double *X, *B, *R;           // n x sp row-major FP64
     float *Xh, *Xl;              // X = Xh + Xl (fp32 pair), refreshed with X
     float *Yk;                   // split-K partial products: kc32 x n x sp (kc32 > 1)
+    double *Rk;                  // split-K partial residual products: kc64 x n x sp (kc64 > 1)
     int *ticket;                 // per FP32 row block: K-chunk tasks finished this tick
     float *Rf, *Z, *Q;           // n x sp row-major FP32
     float *P;                    // CG: two n x sp buffers (current / previous direction)
     float *W;                    // GMRES: two n x sp buffers (unnormalised new vector)
     float *V;                    // GMRES: (m + 1) normalised n x sp blocks
     int t32, n32;                // FP32 product tasks [t32, t32 + n32)
-    int b32, nb32;               // FP32 row blocks (partial-dot rows) [b32, b32 + nb32)
+    int b32, nb32;               // row blocks (partial-dot / residual-norm rows) [b32, b32 + nb32)
     int t64, n64;                // residual tasks
     int tv, nv;                  // vector tasks
 };
@@ -137,12 +149,33 @@ struct EngineDev {               // pointers handed to every engine kernel
     Task *t32, *t64, *tv;        // task tables
     int n32, n64, nv;            // table sizes
     double *part32;              // [row block][E_PS][32]
-    double *part64;              // [task64][32]
+    double *part64;              // [row block][32]
     double *partv;               // [taskv][32]
-    int *active;                 // [0] count, [1] ticket, [2] last count, [3] ticks run
+    int *order;                  // eng_red block b handles slot order[b] (costliest first)
+    const unsigned char *tmaps;  // per slot: 2 x 128-byte TMA maps, A32 and A32lo (256 x 32 tiles,
+                                 // 128-byte swizzle)
+    int *work[2];                // per tick parity: runnable eng_prod tasks, then room for
+                                 // the runnable eng_vec tasks at work[p] + wvec
+    int wvec;                    // offset of the vector-task list in work[p]
+    int *active;                 // engine counters, see the A_* indices
     int tick_limit;              // ticks per graph launch (loop control)
     int host_loop;               // 1: no graph; eng_red writes the loop condition to active[4]
     unsigned long long *launches;
+};
+
+// indices into EngineDev::active
+enum : int {
+    A_COUNT = 0,      // slots still active after this tick's eng_red
+    A_TICKET = 1,     // eng_red blocks finished
+    A_LAST = 2,       // active slots seen by the last loop test
+    A_TICKS = 3,      // ticks run by this launch
+    A_GO = 4,         // host-loop mode: the loop condition
+    A_CLAIM_PROD = 5, // eng_prod task claims this tick
+    A_CLAIM_VEC = 6,  // eng_vec task claims this tick
+    A_ERR = 7,        // a bounded wait in eng_prod gave up (the launch's results are void)
+    A_LEN_PROD = 8,   // [8 + parity]: runnable eng_prod tasks listed by eng_red
+    A_LEN_VEC = 10,   // [10 + parity]: runnable eng_vec tasks
+    A_SIZE = 16
 };
 
 struct EngineKernels {

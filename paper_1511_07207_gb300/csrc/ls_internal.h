@@ -143,6 +143,10 @@ cudaError_t gemv_launch(const GemvLaunch &L, const MatDesc *dA, const GemvArgs &
 // Fill the TMA map of a matrix descriptor (host side); returns false when the
 // layout cannot be streamed by TMA (alignment), in which case use_tma = 0.
 bool make_tensor_map(MatDesc *h, int dtype, const void *ptr, int rows, int cols, long long lda);
+// FP32 row-major rows x cols (leading dimension ld) read in box_rows x box_cols
+// tiles with the 128-byte swizzle; `map` is 128 bytes, 64-byte aligned.
+bool encode_f32_tile_map_sw128(void *map, const float *ptr, int rows, int cols, long long ld,
+                               int box_cols, int box_rows);
 int gemv_tile_rows(int dtype);
 cudaError_t quantize_launch(int dtype, int rows, int cols, const double *A, long long lda,
                             void *Q, long long ldq, float *scale, int num_sms, cudaStream_t s);

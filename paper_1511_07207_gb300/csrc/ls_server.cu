@@ -337,7 +337,7 @@ extern "C" int ls_server_start(ls_ctx *c, const ls_server_cfg *cfg, ls_server **
     }
     int rc = s->pool.init(cfg->hbm_budget_bytes);
     const int cap = cfg->max_slots;
-    const SlotTasks per = slot_tasks(SERVER_MAX_N);
+    const SlotTasks per = slot_tasks(SERVER_MAX_N, 32);   // the widest slot has the most tasks
     if (!rc) rc = s->eng.reserve(&s->shadow, cap, cap * per.t32, cap * per.rb32, cap * per.t64, cap * per.tv);
     if (rc) {
         s->eng.release();
