@@ -354,43 +354,54 @@ __device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *
         const bool ok = ch == 0 || mbar_wait(M.full(st), (seq / PSTAGES) & 1);
         float *Ps = M.ps(ch & 1);
         if (ok) {   // the operand chunk: P = Rf + beta P' (CG) or V_k = W / h (GMRES)
+            // thread tid always builds column tid % SP (SP divides the block)
             const StageHdr &H = *M.hdr(st);
             const float *o1 = M.opr(st, 0), *o2 = M.opr(st, 1);
             const bool two = (H.flags & SF_SRC2) != 0;
-            const int k0 = H.k0;
-            for (int e = tid; e < KC * SP; e += P32_T) {
-                const int kk = e / SP, c = e % SP, gk = k0 + kk;
-                float val = 0.0f;
-                if (gk < n && c < s) {
-                    if (ph == PH_CG)
-                        val = H.colstop[c] ? 0.0f : (two ? fmaf(H.colscale[c], o2[e], o1[e]) : o1[e]);
-                    else
-                        val = o1[e] * H.colscale[c];
-                    if (gk >= r0 && gk < r1) dst[(long long)gk * SP + c] = val;   // owned rows
+            const int k0 = H.k0, c = tid % SP;
+            const bool live = c < s && !(ph == PH_CG && H.colstop[c]);
+            const float cs = H.colscale[c];
+            const bool own = k0 < r1 && k0 + KC > r0;           // the chunk holds rows of this block
+#pragma unroll
+            for (int j = 0; j < (KC * SP + P32_T - 1) / P32_T; j++) {
+                const int e = tid + j * P32_T;
+                if (KC * SP % P32_T == 0 || e < KC * SP) {
+                    const int gk = k0 + e / SP;
+                    float val = 0.0f;
+                    if (live && gk < n) {
+                        if (ph == PH_CG) val = two ? fmaf(cs, o2[e], o1[e]) : o1[e];
+                        else val = o1[e] * cs;
+                        if (own && gk >= r0 && gk < r1) dst[(long long)gk * SP + c] = val;   // owned rows
+                    }
+                    Ps[e] = val;
                 }
-                Ps[e] = val;
             }
         }
         if (named_bar_or(1, P32_T, !ok)) return false;
         // rows rg + NRG r share the swizzle phase rg & 7 (NRG is a multiple
-        // of 8): one chunk offset per k quad, fixed offsets between the rows
+        // of 8): one chunk offset per k quad, fixed offsets between the rows.
+        // The next quad's operands are loaded before this quad's FMAs.
         const float *At = M.tile(st) + rg * KC;
         const int sw = rg & 7;
+        float4 a[2][RPT], p[2][4];
+        auto load_q = [&](int kq, int b) {
+            const float *Aq = At + ((kq ^ sw) << 2);
+#pragma unroll
+            for (int r = 0; r < RPT; r++) a[b][r] = *reinterpret_cast<const float4 *>(Aq + r * NRG * KC);
+#pragma unroll
+            for (int j = 0; j < 4; j++) p[b][j] = *reinterpret_cast<const float4 *>(Ps + (4 * kq + j) * SP + cg * 4);
+        };
+        load_q(0, 0);
 #pragma unroll
         for (int kq = 0; kq < KC / 4; kq++) {
-            const float *Aq = At + ((kq ^ sw) << 2);
-            float4 a[RPT];
-#pragma unroll
-            for (int r = 0; r < RPT; r++) a[r] = *reinterpret_cast<const float4 *>(Aq + r * NRG * KC);
-            float4 p[4];
-#pragma unroll
-            for (int j = 0; j < 4; j++) p[j] = *reinterpret_cast<const float4 *>(Ps + (4 * kq + j) * SP + cg * 4);
+            const int b = kq & 1;
+            if (kq + 1 < KC / 4) load_q(kq + 1, b ^ 1);
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const float pc[4] = {p[j].x, p[j].y, p[j].z, p[j].w};
+                const float pc[4] = {p[b][j].x, p[b][j].y, p[b][j].z, p[b][j].w};
 #pragma unroll
                 for (int r = 0; r < RPT; r++) {
-                    const float av = j == 0 ? a[r].x : j == 1 ? a[r].y : j == 2 ? a[r].z : a[r].w;
+                    const float av = j == 0 ? a[b][r].x : j == 1 ? a[b][r].y : j == 2 ? a[b][r].z : a[b][r].w;
 #pragma unroll
                     for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av, pc[c], acc[r][c]);
                 }
@@ -413,13 +424,9 @@ __device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *
         }
         named_bar(1, P32_T);
         const int rbl = r0 / E_RB32;
-        if (tid == 0) {     // one fence for the CTA's stores (ordered by the barrier)
-            __threadfence();
-            const int last = atomicAdd(D.ticket + rbl, 1) == kc32 - 1;
-            if (last) {
-                __threadfence();
-                D.ticket[rbl] = 0;                              // ready for the next tick
-            }
+        if (tid == 0) {     // the CTA's stores are ordered before this by the barrier
+            const int last = atom_add_acq_rel(D.ticket + rbl, 1) == kc32 - 1;
+            if (last) D.ticket[rbl] = 0;                        // ready for the next tick
             *flag_s = last;
         }
         named_bar(1, P32_T);
@@ -585,13 +592,9 @@ __device__ bool res_task(const EngineDev &E, const ProdSmem &M, int &seq, int *f
         }
         named_bar(1, P32_T);
         const int rbl = r0 / E_RB32;
-        if (tid == 0) {     // one fence for the CTA's stores (ordered by the barrier)
-            __threadfence();
-            const int last = atomicAdd(D.ticket + rbl, 1) == kc64 - 1;
-            if (last) {
-                __threadfence();
-                D.ticket[rbl] = 0;                              // ready for the next tick
-            }
+        if (tid == 0) {     // the CTA's stores are ordered before this by the barrier
+            const int last = atom_add_acq_rel(D.ticket + rbl, 1) == kc64 - 1;
+            if (last) D.ticket[rbl] = 0;                        // ready for the next tick
             *flag_s = last;
         }
         named_bar(1, P32_T);
