@@ -10,9 +10,10 @@ cache, so no flush is needed between steps.
   value        whole-job solves per second (device-resident inputs, CUDA events)
   e2e          the same through the C ABI with pinned HOST buffers: the copy of
                A and b to the device and of x back are inside the timed region
-  roofline     the dominant kernel (the FP64 matrix-vector product), timed with
-               CUDA events on its stream as back-to-back launches of the same
-               kernel and grid the solvers use
+  roofline     the dominant kernel (the FP64 matrix-vector product, formed on the
+               FP32 pipe from the FP32 pair hi + lo of A), timed with CUDA
+               events on its stream as back-to-back launches of the same
+               kernel and grid the solvers use; HBM-bound
   cpu_baseline the oracle (plain C, FP64) on this host's cores, on a bounded
                sample of the same workload, scaled to solves per second
 
@@ -252,25 +253,36 @@ def run_native(args):
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
     err_gm = float(torch.linalg.norm(x2 - xs2) / torch.linalg.norm(xs2))
 
-    # dominant kernel: the FP64 GEMV, same kernel/grid as inside the solves
+    # dominant kernel: the FP64 GEMV through the FP32 pair (the solvers'
+    # default), same kernel/grid as inside the solves
     p = torch.from_numpy(np.random.default_rng(0).standard_normal(N)).to(dev)
     y = torch.empty(N, dtype=torch.float64, device=dev)
-    st, gemv_ms = B.ls_gemv_timed(ctx, B.LS_F64, A_spd, p, y, 30)
+    pair = torch.empty((2 * N, N), dtype=torch.float32, device=dev)
+    assert B.ls_split_f64(ctx, A_spd, pair) == B.LS_OK
+    st, gemv_ms = B.ls_gemv_timed(ctx, B.LS_F64_PAIR, pair[:N], p, y, 30)
+    assert st == B.LS_OK
+    del pair
+    st, native_ms = B.ls_gemv_timed(ctx, B.LS_F64, A_spd, p, y, 30)
     assert st == B.LS_OK
     peaks, peak_src = load_peaks()
     gemv_bytes = 8.0 * N * N + 16.0 * N
     gemv_gbs = gemv_bytes / (gemv_ms * 1e-3) / 1e9
-    gemv_tflops = 2.0 * N * N / (gemv_ms * 1e-3) / 1e12
+    native_gbs = gemv_bytes / (native_ms * 1e-3) / 1e9
+    native_tflops = 2.0 * N * N / (native_ms * 1e-3) / 1e12
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = dfma_peak_tflops(sm_max)
-    traffic = profiled_traffic("gemv_f64_n16384.md")
-    roofline = {"bound": "alu", "achieved": round(gemv_tflops, 4), "peak": round(alu_peak, 4),
-                "unit": "TFLOP/s", "frac": round(gemv_tflops / alu_peak, 4),
+    traffic = profiled_traffic("gemv_pair_n16384.md")
+    roofline = {"bound": "hbm", "achieved": round(gemv_gbs, 1), "peak": round(peaks["hbm_gbs"], 1),
+                "unit": "GB/s", "frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
                 "traffic": traffic,
-                "kernel": "gemv_kernel<F64,TMA> (K1)",
-                "note": ("FP64 FMA pipe bound: peak = 152 SMs x 2 DFMA/clk x 2 flop x SM max clock; "
-                         "HBM view: %.1f GB/s = %.3f of %s %.1f GB/s" %
-                         (gemv_gbs, gemv_gbs / peaks["hbm_gbs"], peak_src, peaks["hbm_gbs"]))}
+                "kernel": "gemv_kernel<DS,TMA> (K1: FP64 A as the FP32 pair hi + lo, double-single FMA)",
+                "note": ("algorithmic bytes 8n^2 + 16n per launch (hi and lo are 4 + 4 bytes per element); "
+                         "peak = %s copy bandwidth" % peak_src)}
+    gemv_native = {"ms": round(native_ms, 4), "GB/s": round(native_gbs, 1),
+                   "hbm_frac": round(native_gbs / peaks["hbm_gbs"], 4),
+                   "dfma_frac": round(native_tflops / alu_peak, 4),
+                   "note": "native FP64 FMA (f64_matvec = 1): bound by the FP64 pipe, "
+                           "peak = 152 SMs x 2 DFMA/clk x 2 flop x SM max clock"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -340,6 +352,7 @@ def run_native(args):
             "iters": {"cg": i1["iters"], "gmres": i2["iters"]},
             "true_rel_res": {"cg": i1["true_rel_res"], "gmres": i2["true_rel_res"]},
             "rel_err_vs_xstar": {"cg": err_cg, "gmres": err_gm},
+            "gemv_f64_native": gemv_native,
             "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
                          "peak_source": peak_src},
@@ -604,9 +617,18 @@ def run_kernel(args):
     g = torch.Generator(device=dev)
     g.manual_seed(0)
     A64 = torch.randn((n, n), dtype=torch.float64, device=dev, generator=g)
-    dt = {"f64": B.LS_F64, "bf16": B.LS_BF16_IR, "fp8": B.LS_FP8_IR, "f32": B.LS_F32_IR}[args.dtype]
+    dt = {"f64": B.LS_F64, "pair": B.LS_F64_PAIR, "bf16": B.LS_BF16_IR, "fp8": B.LS_FP8_IR,
+          "f32": B.LS_F32_IR}[args.dtype]
     scale = None
-    if dt == B.LS_F64:
+    if dt == B.LS_F64_PAIR:
+        A = torch.empty((2 * n, (n + 3) // 4 * 4), dtype=torch.float32, device=dev)
+        assert B.ls_split_f64(ctx, A64, A[:, :n]) == B.LS_OK
+        del A64
+        A = A[:n, :n]
+        x = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+        y = torch.empty(n, dtype=torch.float64, device=dev)
+        esz = 8
+    elif dt == B.LS_F64:
         A = A64
         x = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
         y = torch.empty(n, dtype=torch.float64, device=dev)
@@ -622,7 +644,7 @@ def run_kernel(args):
         esz = {B.LS_BF16_IR: 2, B.LS_FP8_IR: 1, B.LS_F32_IR: 4}[dt]
     st, ms = B.ls_gemv_timed(ctx, dt, A, x, y, args.reps, scale=scale)
     assert st == B.LS_OK
-    byts = esz * n * n + (8 if dt == B.LS_F64 else 4) * 2 * n + (4 * n if scale is not None else 0)
+    byts = esz * n * n + (8 if dt in (B.LS_F64, B.LS_F64_PAIR) else 4) * 2 * n + (4 * n if scale is not None else 0)
     peaks, src = load_peaks()
     print(json.dumps({"kernel": "gemv", "dtype": args.dtype, "n": n, "reps": args.reps,
                       "ms": round(ms, 5), "GB/s": round(byts / ms / 1e6, 1),
@@ -651,7 +673,7 @@ def main():
     ap.add_argument("--kernel", choices=["gemv"], default=None,
                     help="kernel-only timing (small cases for ncu captures)")
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--dtype", choices=["f64", "bf16", "fp8", "f32"], default="f64")
+    ap.add_argument("--dtype", choices=["f64", "pair", "bf16", "fp8", "f32"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--ref-cg-iters", type=int, default=0,
                     help="reference arm: CG iteration count to scale to (0 = run the oracle once)")

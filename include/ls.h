@@ -57,6 +57,9 @@ extern "C" {
 #define LS_METHOD_GMRES  1
 
 #define LS_F64      0   /* plain FP64 solve                                            */
+#define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
+                           made by ls_split_f64 (hi rows, then lo rows), FP64 x and y,
+                           products in double-single arithmetic                         */
 #define LS_BF16_IR  1   /* A stored in BF16, FP32 inner CG, FP64 outer refinement        */
 #define LS_FP8_IR   2   /* A stored in FP8-e4m3 with one FP32 scale per row, as above    */
 #define LS_F32_IR   3   /* A stored in FP32, as above                                    */
@@ -77,6 +80,12 @@ typedef struct {
     int x0_given;       /* 1: x holds the initial guess; 0: start from x = 0 (default)  */
     int reorth;         /* GMRES: 0 = one Gram-Schmidt pass with a second pass when the
                            norm drops below 0.7x (default), 1 = always two passes       */
+    int f64_matvec;     /* LS_F64 solves: 0 = split A once into the FP32 pair
+                           hi = fp32(A), lo = fp32(A - hi) (about 48 bits) and form
+                           every A v in double-single arithmetic on the FP32 pipe
+                           (default: GB300 runs FP32 at 64x its FP64 FMA rate, so the
+                           product becomes HBM-bound; extra workspace 8 n^2 bytes);
+                           1 = native FP64 FMA                                          */
 } ls_opts;
 
 #define LS_MAX_RESTART 128
@@ -225,11 +234,21 @@ int ls_server_stop(ls_server *srv);
  * y = A x for a row-major rows x cols matrix stored as `dtype`
  * (LS_F64: double A, double x and y; LS_BF16_IR: uint16 BF16 codes;
  * LS_FP8_IR: uint8 e4m3 codes with FP32 row scales `scale`, y_i = s_i (Q x)_i;
- * LS_F32_IR: float A).  For the low-precision formats x and y are FP32.
+ * LS_F32_IR: float A; LS_F64_PAIR: the FP32 pair of ls_split_f64 with lda = its
+ * ldp, double x and y).  For the low-precision formats x and y are FP32.
  * All pointers are device pointers.
  */
 int ls_gemv(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int64_t lda,
             const float *scale, const void *x, void *y);
+
+/*
+ * Split a row-major FP64 matrix (device) into the FP32 pair used by the FP64
+ * solvers' products: pair[i * ldp + j] = hi_ij = fp32(a_ij) (round to nearest
+ * even), pair[(rows + i) * ldp + j] = lo_ij = fp32(a_ij - hi_ij); hi + lo equals
+ * a_ij to within 2^-48 |a_ij|.  ldp >= cols and a multiple of 4 (16-byte rows);
+ * `pair` holds 2 rows ldp floats.  Device pointers; LS_ERR_ARG on bad sizes.
+ */
+int ls_split_f64(ls_ctx *ctx, int rows, int cols, const double *A, int64_t lda, float *pair, int64_t ldp);
 
 /*
  * Quantise a row-major FP64 matrix on the device: LS_BF16_IR -> uint16 codes,

@@ -19,6 +19,7 @@ LS_ERR_ARG, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT = -1, -2, -3, -4
 LS_ERR_BUSY, LS_ERR_NAN, LS_ERR_UNSUPPORTED = -5, -6, -7
 LS_METHOD_CG, LS_METHOD_GMRES = 0, 1
 LS_F64, LS_BF16_IR, LS_FP8_IR, LS_F32_IR = 0, 1, 2, 3
+LS_F64_PAIR = 4
 LS_REFINE_FCG, LS_REFINE_IR = 0, 1
 LS_MAX_RESTART = 128
 LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 8192, 32
@@ -28,7 +29,7 @@ ABI_FUNCTIONS = (
     "ls_opts_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_set_workspace",
     "ls_cg_solve", "ls_gmres_solve", "ls_batch_solve", "ls_server_start", "ls_server_submit",
     "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
-    "ls_quantize", "ls_kernel_launches", "ls_strerror",
+    "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror",
 )
 
 
@@ -36,7 +37,7 @@ class ls_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("restart", ctypes.c_int),
                 ("precision", ctypes.c_int), ("refine", ctypes.c_int),
                 ("inner_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
-                ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int)]
+                ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int), ("f64_matvec", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):
@@ -102,6 +103,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_double)]
         lib.ls_gemv_noalloc.argtypes = [I, I, I, P, I64, P, P, P, P]
         lib.ls_quantize.argtypes = [P, I, I, I, P, I64, P, I64, P]
+        lib.ls_split_f64.argtypes = [P, I, I, P, I64, P, I64]
         lib.ls_kernel_launches.argtypes = [P]
         lib.ls_kernel_launches.restype = ctypes.c_longlong
         lib.ls_strerror.argtypes = [I]
@@ -268,6 +270,13 @@ def ls_quantize(ctx, dtype, A, Q, scale=None):
     rows, cols = A.shape
     return load().ls_quantize(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(Q), lead_dim(Q),
                               ptr(scale))
+
+
+def ls_split_f64(ctx, A, pair):
+    """Split FP64 A (device, rows x cols) into the FP32 pair `pair` (device,
+    2 rows x ldp floats: hi rows, then lo rows)."""
+    rows, cols = A.shape
+    return load().ls_split_f64(ctx, rows, cols, ptr(A), lead_dim(A), ptr(pair), lead_dim(pair))
 
 
 def make_system(method, A, B, X, opts=None) -> ls_system:

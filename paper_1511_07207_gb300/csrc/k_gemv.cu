@@ -12,7 +12,7 @@
 //    of A is cut into equal contiguous pieces, one per CTA, so every SM gets
 //    the same number of bytes whatever n is;
 //  * one producer warp streams TR x TC tiles of A with 2-D TMA bulk copies
-//    (cp.async.bulk.tensor) into a GEMV_STAGES-deep shared-memory ring with
+//    (cp.async.bulk.tensor) into a 6-deep (3 for FP32 pairs) shared-memory ring with
 //    mbarrier completion; four consumer warps read the tiles with 128-bit
 //    (64-bit for FP8) shared loads, keep RW row accumulators per lane and
 //    the x chunk in registers, and reduce with warp shuffles;
@@ -32,31 +32,84 @@
 
 namespace lsi {
 
+// Double-single accumulator (hi, lo): hi + lo carries about 48 bits.
+struct DSV {
+    float h, l;
+};
+// (hi, lo) + (hi, lo): the high parts by two-sum (Knuth), every rounding
+// error into lo.  The intrinsics keep the compiler from contracting or
+// reassociating the error-free steps.
+__device__ __forceinline__ DSV operator+(DSV a, DSV b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bv = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
+    return DSV{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ DSV &operator+=(DSV &a, DSV b) { return a = a + b; }
+__device__ __forceinline__ double to_double(DSV v) { return (double)v.h + (double)v.l; }
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ float to_double(float v) { return v; }
+__device__ __forceinline__ float shfl_xor_v(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor_v(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ DSV shfl_xor_v(DSV v, int o) {
+    return DSV{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+// acc += a x for a = ah + al, x = xh + xl: ah xh = p + e exactly (FMA gives
+// the product error), the cross terms ah xl + al xh and e go to lo with the
+// two-sum error of hi + p (al xl, below 2^-48 |a x|, is dropped).
+__device__ __forceinline__ void ds_fma(float ah, float al, DSV x, DSV &acc) {
+    const float p = __fmul_rn(ah, x.h);
+    const float pe = fmaf(ah, x.h, -p);
+    const float t = fmaf(al, x.h, fmaf(ah, x.l, pe));
+    const float sh = __fadd_rn(acc.h, p);
+    const float bv = __fsub_rn(sh, acc.h);
+    const float er = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(sh, bv)), __fsub_rn(p, bv));
+    acc.h = sh;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(t, er));
+}
+
 template <int DT>
 struct Cfg;
+// T: stored element; V: accumulator; X: vector element read; Y: result stored
 template <>
 struct Cfg<DT_F64> {
-    using T = double;   // stored element
-    using V = double;   // vector element / accumulator
-    static constexpr int VEC = 2, WC = 4, WR = 1, RW = 8;
+    using T = double;
+    using V = double;
+    using X = double;
+    using Y = double;
+    static constexpr int VEC = 2, WC = 4, WR = 1, RW = 8, PARTS = 1;
+};
+template <>
+struct Cfg<DT_DS> {
+    using T = float;    // hi and lo tiles of the same shape, one after the other
+    using V = DSV;
+    using X = double;
+    using Y = double;
+    static constexpr int VEC = 2, WC = 4, WR = 1, RW = 8, PARTS = 2;
 };
 template <>
 struct Cfg<DT_BF16> {
     using T = uint16_t;
     using V = float;
-    static constexpr int VEC = 8, WC = 1, WR = 4, RW = 8;
+    using X = float;
+    using Y = float;
+    static constexpr int VEC = 8, WC = 1, WR = 4, RW = 8, PARTS = 1;
 };
 template <>
 struct Cfg<DT_FP8> {
     using T = uint8_t;
     using V = float;
-    static constexpr int VEC = 8, WC = 1, WR = 4, RW = 16;
+    using X = float;
+    using Y = float;
+    static constexpr int VEC = 8, WC = 1, WR = 4, RW = 16, PARTS = 1;
 };
 template <>
 struct Cfg<DT_F32> {
     using T = float;
     using V = float;
-    static constexpr int VEC = 4, WC = 2, WR = 2, RW = 8;
+    using X = float;
+    using Y = float;
+    static constexpr int VEC = 4, WC = 2, WR = 2, RW = 8, PARTS = 1;
 };
 
 template <int DT>
@@ -71,9 +124,15 @@ struct Geo {
     static_assert(C::WC * C::WR == GEMV_CONSUMER_WARPS, "warp grid");
 };
 
+// Ring depth: the FP32-pair tiles are twice as large, so fewer stages keep
+// two CTAs per SM.
+template <int DT>
+__host__ __device__ constexpr int stages() { return Cfg<DT>::PARTS > 1 ? 3 : GEMV_STAGES; }
+
 int gemv_tile_rows(int dtype) {
     switch (dtype) {
         case DT_F64: return Geo<DT_F64>::TR;
+        case DT_DS: return Geo<DT_DS>::TR;
         case DT_BF16: return Geo<DT_BF16>::TR;
         case DT_FP8: return Geo<DT_FP8>::TR;
         default: return Geo<DT_F32>::TR;
@@ -82,10 +141,25 @@ int gemv_tile_rows(int dtype) {
 
 // ---- x chunk loads --------------------------------------------------------------
 template <int DT>
-__device__ __forceinline__ void load_x(const typename Cfg<DT>::V *x, int c0, int cols,
+__device__ __forceinline__ void load_x(const typename Cfg<DT>::X *x, int c0, int cols,
                                        typename Cfg<DT>::V (&p)[Cfg<DT>::VEC]) {
     constexpr int VEC = Cfg<DT>::VEC;
-    if (c0 + VEC <= cols && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
+    if constexpr (DT == DT_DS) {        // FP64 x split into (hi, lo) floats
+        double v[VEC];
+        if (c0 + VEC <= cols && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
+            const double2 w = __ldg(reinterpret_cast<const double2 *>(x + c0));
+            v[0] = w.x;
+            v[1] = w.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; k++) v[k] = (c0 + k < cols) ? x[c0 + k] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const float h = __double2float_rn(v[k]);
+            p[k] = DSV{h, __double2float_rn(v[k] - (double)h)};
+        }
+    } else if (c0 + VEC <= cols && ((reinterpret_cast<uintptr_t>(x) & 15) == 0)) {
         if constexpr (DT == DT_F64) {
             double2 v = __ldg(reinterpret_cast<const double2 *>(x + c0));
             p[0] = v.x;
@@ -116,6 +190,11 @@ __device__ __forceinline__ void dot_tile(const typename Cfg<DT>::T *a,
         double2 v = *reinterpret_cast<const double2 *>(a);
         acc0 = fma(v.x, p[0], acc0);
         acc1 = fma(v.y, p[1], acc1);
+    } else if constexpr (DT == DT_DS) {    // the lo tile follows the hi tile
+        const float2 h = *reinterpret_cast<const float2 *>(a);
+        const float2 l = *reinterpret_cast<const float2 *>(a + Geo<DT>::TILE_ELEMS);
+        ds_fma(h.x, l.x, p[0], acc0);
+        ds_fma(h.y, l.y, p[1], acc1);
     } else if constexpr (DT == DT_BF16) {
         uint4 v = *reinterpret_cast<const uint4 *>(a);
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -163,11 +242,11 @@ __device__ __forceinline__ void butterfly(V (&acc)[RW], int lane) {
             for (int i = 0; i < H; i++) {
                 const V send = upper ? acc[i] : acc[i + H];
                 const V keep = upper ? acc[i + H] : acc[i];
-                acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+                acc[i] = keep + shfl_xor_v(send, OFF);
             }
             butterfly<H, OFF / 2>(acc, lane);
         } else {
-            acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], OFF);
+            acc[0] += shfl_xor_v(acc[0], OFF);
             butterfly<1, OFF / 2>(acc, lane);
         }
     }
@@ -178,12 +257,19 @@ __host__ __device__ constexpr int log2i() { return RW <= 1 ? 0 : 1 + log2i<RW / 
 
 // plain global loads (fallback when A cannot be described by a TMA map)
 template <int DT>
-__device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, long long lda, int row,
-                                           int c0, int cols,
+__device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, const typename Cfg<DT>::T *Alo,
+                                           long long lda, int row, int c0, int cols,
                                            const typename Cfg<DT>::V (&p)[Cfg<DT>::VEC],
                                            typename Cfg<DT>::V &acc, typename Cfg<DT>::V &acc1) {
     using T = typename Cfg<DT>::T;
     const T *a = A + (long long)row * lda;
+    if constexpr (DT == DT_DS) {
+        const T *al = Alo + (long long)row * lda;
+#pragma unroll
+        for (int k = 0; k < Cfg<DT>::VEC; k++)
+            if (c0 + k < cols) ds_fma(a[c0 + k], al[c0 + k], p[k], (k & 1) ? acc1 : acc);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < Cfg<DT>::VEC; k++) {
         int c = c0 + k;
@@ -197,7 +283,7 @@ __device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, long lo
             } else if constexpr (DT == DT_FP8) {
                 __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)e, __NV_E4M3);
                 acc = fmaf(__half2float(*reinterpret_cast<__half *>(&h)), p[k], acc);
-            } else {
+            } else if constexpr (DT == DT_F32) {
                 acc = fmaf(e, p[k], acc);
             }
         }
@@ -207,8 +293,8 @@ __device__ __forceinline__ void dot_global(const typename Cfg<DT>::T *A, long lo
 // ---- epilogue for one finished row ---------------------------------------------------
 template <int DT>
 __device__ __forceinline__ double epilogue(const GemvArgs &a, const MatDesc &M, int row,
-                                           typename Cfg<DT>::V s) {
-    using V = typename Cfg<DT>::V;
+                                           typename Cfg<DT>::Y s) {
+    using V = typename Cfg<DT>::Y;
     if constexpr (DT == DT_FP8) s *= M.scale[row];
     V *y = static_cast<V *>(a.y);
     switch (a.epi) {
@@ -286,14 +372,18 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
     using G = Geo<DT>;
     using T = typename C::T;
     using V = typename C::V;
+    using X = typename C::X;
+    using Y = typename C::Y;
     constexpr int TC = G::TC, TR = G::TR, VEC = C::VEC, RW = C::RW, WC = C::WC;
+    constexpr int STAGE_ELEMS = G::TILE_ELEMS * C::PARTS;
+    constexpr int NST = stages<DT>();
     constexpr int LGR = log2i<RW>();
     static_assert((1 << LGR) == RW && RW <= 32, "RW must be a power of two");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)GEMV_STAGES * G::TILE_BYTES);
-    uint64_t *empty = full + GEMV_STAGES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)NST * G::TILE_BYTES * C::PARTS);
+    uint64_t *empty = full + NST;
     __shared__ V red[WC][TR];
     __shared__ double dred[GEMV_THREADS / 32];
     __shared__ int abort_s, last_s, fin_s, ca_s, cb_s;
@@ -303,8 +393,8 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
     const int rows = M.rows, cols = M.cols;
     if (args.kptr) {   // walk a stored basis: x = column k, y = column k + kyoff
         const long long k = *args.kptr;
-        args.x = static_cast<const V *>(args.x) + k * args.kstride;
-        args.y = static_cast<V *>(args.y) + (k + args.kyoff) * args.kstride;
+        args.x = static_cast<const X *>(args.x) + k * args.kstride;
+        args.y = static_cast<Y *>(args.y) + (k + args.kyoff) * args.kstride;
     }
     if (args.z_is_x) args.z = args.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -328,7 +418,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
         }
         if (!holds_shared_first) args.scr->fixdot[cta] = 0.0;
         if (TMA) {
-            for (int s = 0; s < GEMV_STAGES; s++) {
+            for (int s = 0; s < NST; s++) {
                 mbar_init(&full[s], 1);
                 mbar_init(&empty[s], GEMV_CONSUMER_WARPS);
             }
@@ -342,26 +432,30 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
         // ---------------- producer warp ----------------
         if (TMA && lane == 0 && ntiles > 0) {
             tmap_acquire(&M.tmap);
+            if (C::PARTS > 1) tmap_acquire(&M.tmap_lo);
             int issued = 0;
             int rt = (int)(t0 / CT), ct = (int)(t0 % CT);
             for (int i = 0; i < ntiles; i++) {
-                const int s = i % GEMV_STAGES;
-                if (i >= GEMV_STAGES) {
-                    if (!mbar_wait(&empty[s], ((i / GEMV_STAGES) - 1) & 1)) {
+                const int s = i % NST;
+                if (i >= NST) {
+                    if (!mbar_wait(&empty[s], ((i / NST) - 1) & 1)) {
                         set_err(args.st, ERRB_TIMEOUT);
                         abort_s = 1;
                         break;
                     }
                 }
                 if (*(volatile int *)&abort_s) break;
-                mbar_arrive_expect_tx(&full[s], G::TILE_BYTES);
-                tma_load_2d(ring + (size_t)s * G::TILE_ELEMS, &M.tmap, ct * TC, rt * TR, &full[s]);
+                mbar_arrive_expect_tx(&full[s], G::TILE_BYTES * C::PARTS);
+                tma_load_2d(ring + (size_t)s * STAGE_ELEMS, &M.tmap, ct * TC, rt * TR, &full[s]);
+                if (C::PARTS > 1)
+                    tma_load_2d(ring + (size_t)s * STAGE_ELEMS + G::TILE_ELEMS, &M.tmap_lo, ct * TC, rt * TR,
+                                &full[s]);
                 issued = i + 1;
                 if (++ct == CT) { ct = 0; ++rt; }
             }
             // never leave with copies in flight: wait for the last stages
-            for (int i = issued > GEMV_STAGES ? issued - GEMV_STAGES : 0; i < issued; i++) {
-                if (!mbar_wait(&full[i % GEMV_STAGES], (i / GEMV_STAGES) & 1)) {
+            for (int i = issued > NST ? issued - NST : 0; i < issued; i++) {
+                if (!mbar_wait(&full[i % NST], (i / NST) & 1)) {
                     set_err(args.st, ERRB_TIMEOUT);
                 }
             }
@@ -372,9 +466,10 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
         const int lane_col = wc * 32 * VEC + lane * VEC;   // column offset inside a tile
         V acc[RW], acc1[RW];
 #pragma unroll
-        for (int r = 0; r < RW; r++) acc[r] = acc1[r] = 0;
+        for (int r = 0; r < RW; r++) acc[r] = acc1[r] = V{};
         const T *Ag = static_cast<const T *>(M.ptr);
-        const V *x = static_cast<const V *>(args.x);
+        const T *Agl = static_cast<const T *>(M.ptr_lo);
+        const X *x = static_cast<const X *>(args.x);
         int rt = ntiles > 0 ? (int)(t0 / CT) : 0, ct = ntiles > 0 ? (int)(t0 % CT) : 0;
         const int first_rt = rt;
 
@@ -385,13 +480,13 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
                 // On a timeout the warp stops waiting and computing but keeps
                 // walking the tile sequence, so it still meets the other
                 // consumer warps at every named barrier below.
-                const int s = i % GEMV_STAGES;
-                if (!*(volatile int *)&abort_s && !mbar_wait(&full[s], (i / GEMV_STAGES) & 1)) {
+                const int s = i % NST;
+                if (!*(volatile int *)&abort_s && !mbar_wait(&full[s], (i / NST) & 1)) {
                     set_err(args.st, ERRB_TIMEOUT);
                     abort_s = 1;
                 }
                 if (!*(volatile int *)&abort_s) {
-                    const T *tile = ring + (size_t)s * G::TILE_ELEMS;
+                    const T *tile = ring + (size_t)s * STAGE_ELEMS;
 #pragma unroll
                     for (int r = 0; r < RW; r++)
                         dot_tile<DT>(tile + (wr * RW + r) * TC + lane_col, p, acc[r], acc1[r]);
@@ -403,7 +498,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
                 for (int r = 0; r < RW; r++) {
                     const int row = rt * TR + wr * RW + r;
                     if (row < rows)
-                        dot_global<DT>(Ag, M.lda, row, ct * TC + lane_col, cols, p, acc[r], acc1[r]);
+                        dot_global<DT>(Ag, Agl, M.lda, row, ct * TC + lane_col, cols, p, acc[r], acc1[r]);
                 }
             }
             if (ct == CT - 1 || i == ntiles - 1) {
@@ -411,22 +506,22 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
 #pragma unroll
                 for (int r = 0; r < RW; r++) {
                     acc[r] += acc1[r];
-                    acc1[r] = 0;
+                    acc1[r] = V{};
                 }
                 butterfly<RW, 16>(acc, lane);
                 if ((lane & ((32 >> LGR) - 1)) == 0) red[wc][wr * RW + (lane >> (5 - LGR))] = acc[0];
 #pragma unroll
-                for (int r = 0; r < RW; r++) acc[r] = 0;
+                for (int r = 0; r < RW; r++) acc[r] = V{};
                 consumers_sync();
                 const long long rfirst = (long long)rt * CT;
                 const bool complete = (t0 <= rfirst) && (rfirst + CT <= t1);
                 if (complete) {
                     for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
-                        V s = 0;
+                        V s{};
 #pragma unroll
                         for (int c = 0; c < WC; c++) s += red[c][tr];
                         const int row = rt * TR + tr;
-                        if (row < rows) mydot += epilogue<DT>(args, M, row, s);
+                        if (row < rows) mydot += epilogue<DT>(args, M, row, (Y)to_double(s));
                     }
                 } else {
                     // A row tile shared with neighbouring CTAs: publish the
@@ -434,10 +529,10 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
                     // them in CTA order and finishes those rows.
                     const int slot = (rt == first_rt) ? 0 : 1;
                     for (int tr = threadIdx.x; tr < TR; tr += GEMV_CONSUMER_WARPS * 32) {
-                        V s = 0;
+                        V s{};
 #pragma unroll
                         for (int c = 0; c < WC; c++) s += red[c][tr];
-                        args.scr->fix[((size_t)cta * 2 + slot) * TR + tr] = (double)s;
+                        args.scr->fix[((size_t)cta * 2 + slot) * TR + tr] = (double)to_double(s);
                         __threadfence();
                     }
                     consumers_sync();
@@ -465,7 +560,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
                                 s += __ldcg(&args.scr->fix[((size_t)c * 2 + sl) * TR + tr]);
                             }
                             const int row = rt * TR + tr;
-                            tdot[tr] = row < rows ? epilogue<DT>(args, M, row, (V)s) : 0.0;
+                            tdot[tr] = row < rows ? epilogue<DT>(args, M, row, (Y)s) : 0.0;
                         }
                         consumers_sync();
                         if (threadIdx.x == 0) {
@@ -505,7 +600,7 @@ __global__ void __launch_bounds__(GEMV_THREADS, 2)
 // ---- host side -------------------------------------------------------------------------
 template <int DT>
 static size_t gemv_smem() {
-    return (size_t)GEMV_STAGES * Geo<DT>::TILE_BYTES + 2 * GEMV_STAGES * sizeof(uint64_t);
+    return (size_t)stages<DT>() * Geo<DT>::TILE_BYTES * Cfg<DT>::PARTS + 2 * stages<DT>() * sizeof(uint64_t);
 }
 
 template <int DT, bool TMA>
@@ -523,6 +618,10 @@ GemvLaunch gemv_plan(int dtype, bool use_tma, int epi, int num_sms) {
             L.func = use_tma ? gemv_func<DT_F64, true>() : gemv_func<DT_F64, false>();
             L.smem = gemv_smem<DT_F64>();
             break;
+        case DT_DS:
+            L.func = use_tma ? gemv_func<DT_DS, true>() : gemv_func<DT_DS, false>();
+            L.smem = gemv_smem<DT_DS>();
+            break;
         case DT_BF16:
             L.func = use_tma ? gemv_func<DT_BF16, true>() : gemv_func<DT_BF16, false>();
             L.smem = gemv_smem<DT_BF16>();
@@ -536,11 +635,12 @@ GemvLaunch gemv_plan(int dtype, bool use_tma, int epi, int num_sms) {
             L.smem = gemv_smem<DT_F32>();
             break;
     }
-    if (!use_tma) L.smem = 2 * GEMV_STAGES * sizeof(uint64_t);
-    static bool attr_done[4][2] = {};
-    if (!attr_done[dtype & 3][use_tma]) {
+    if (!use_tma) L.smem = 2 * GEMV_STAGES * sizeof(uint64_t);   // barriers only (no ring)
+    static bool attr_done[5][2] = {};
+    const int di = dtype >= 0 && dtype < 5 ? dtype : 3;
+    if (!attr_done[di][use_tma]) {
         cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-        attr_done[dtype & 3][use_tma] = true;
+        attr_done[di][use_tma] = true;
     }
     if (L.grid > MAX_GRID) L.grid = MAX_GRID;
     return L;
@@ -602,6 +702,55 @@ bool make_tensor_map(MatDesc *h, int dtype, const void *ptr, int rows, int cols,
     if (r != CUDA_SUCCESS) return false;
     h->use_tma = 1;
     return true;
+}
+
+bool make_tensor_map_ds(MatDesc *h, const float *hi, const float *lo, int rows, int cols, long long ld) {
+    h->ptr = hi;
+    h->ptr_lo = lo;
+    h->lda = ld;
+    h->rows = rows;
+    h->cols = cols;
+    h->dtype = DT_DS;
+    h->use_tma = 0;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || rows <= 0 || cols <= 0) return false;
+    if (((uintptr_t)hi & 15) != 0 || ((uintptr_t)lo & 15) != 0 || ((ld * 4) & 15) != 0) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)Geo<DT_DS>::TC, (cuuint32_t)Geo<DT_DS>::TR};
+    cuuint32_t estr[2] = {1, 1};
+    for (int part = 0; part < 2; part++) {
+        CUresult r = fn(part ? &h->tmap_lo : &h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<float *>(part ? lo : hi), gdim, gstride, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    h->use_tma = 1;
+    return true;
+}
+
+// hi = fp32(A), lo = fp32(A - hi): one pass over A, done once per solve.
+__global__ void split_f64_kernel(int rows, int cols, const double *__restrict__ A, long long lda,
+                                 float *__restrict__ hi, float *__restrict__ lo, long long ld) {
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double *a = A + (long long)row * lda;
+        float *h = hi + (long long)row * ld, *l = lo + (long long)row * ld;
+        for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+            const double v = a[j];
+            const float vh = __double2float_rn(v);
+            h[j] = vh;
+            l[j] = __double2float_rn(v - (double)vh);
+        }
+    }
+}
+
+cudaError_t split_f64_launch(int rows, int cols, const double *A, long long lda, float *hi, float *lo,
+                             long long ld, int num_sms, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int grid = rows < 8 * num_sms ? rows : 8 * num_sms;
+    split_f64_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, hi, lo, ld);
+    return cudaGetLastError();
 }
 
 bool encode_f32_tile_map_sw128(void *map, const float *ptr, int rows, int cols, long long ld,

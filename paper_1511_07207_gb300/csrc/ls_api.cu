@@ -206,6 +206,7 @@ extern "C" int ls_opts_default(ls_opts *o) {
     o->inner_rtol = 0.0;
     o->x0_given = 0;
     o->reorth = 0;
+    o->f64_matvec = 0;
     return LS_OK;
 }
 
@@ -322,11 +323,12 @@ namespace lsi {
 
 struct F64Layout {
     double *x, *b, *r, *p, *q, *V, *Astage;
-    long long npad, ldv, lda_stage;
+    float *Ahi, *Alo;    // the FP32 pair of A (double-single products)
+    long long npad, ldv, lda_stage, ld32;
     size_t bytes;
 };
 
-F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA) {
+F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA, bool split) {
     F64Layout L{};
     L.npad = (long long)align_up((size_t)std::max(n, 1), 64);
     L.ldv = L.npad;
@@ -339,6 +341,9 @@ F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA) {
     L.q = cv.take<double>(L.npad);
     L.V = gmres ? cv.take<double>((size_t)L.ldv * (m + 1)) : nullptr;
     L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
+    L.ld32 = (long long)align_up((size_t)std::max(n, 1), 4);
+    L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
+    L.Alo = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
     L.bytes = align_up(cv.off, 256);
     return L;
 }
@@ -501,10 +506,11 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     const int m = o.restart;
     const int max_iter = o.max_iter > 0 ? o.max_iter : 10 * n + 10;
     const bool a_dev = is_device_ptr(A);
-    F64Layout L = f64_layout(nullptr, n, m, method == LS_METHOD_GMRES, !a_dev);
+    const bool split = o.f64_matvec == 0;
+    F64Layout L = f64_layout(nullptr, n, m, method == LS_METHOD_GMRES, !a_dev, split);
     rc = ws_reserve(c, L.bytes);
     if (rc) return rc;
-    L = f64_layout(c->ws, n, m, method == LS_METHOD_GMRES, !a_dev);
+    L = f64_layout(c->ws, n, m, method == LS_METHOD_GMRES, !a_dev, split);
 
     // stage inputs
     const double *Ad;
@@ -515,7 +521,8 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     if (rc) return rc;
     MatDesc *hd = &c->h_desc[0];
     memset(hd, 0, sizeof(MatDesc));
-    make_tensor_map(hd, DT_F64, Ad, n, n, ldad);
+    if (split) make_tensor_map_ds(hd, L.Ahi, L.Alo, n, n, L.ld32);
+    else make_tensor_map(hd, DT_F64, Ad, n, n, ldad);
     rc = upload_desc(c, 0);
     State *hs = c->h_st;
     state_init(hs, max_iter);
@@ -525,9 +532,10 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     if (rc) return rc;
 
     Vecs v = make_vecs(c, L, n, o.rtol);
-    GemvLaunch GL = gemv_plan(DT_F64, hd->use_tma != 0, EPI_DOT, c->num_sms);
+    const int dt = split ? DT_DS : DT_F64;
+    GemvLaunch GL = gemv_plan(dt, hd->use_tma != 0, EPI_DOT, c->num_sms);
     long long key[8] = {method, n, (long long)(uintptr_t)c->ws, L.ldv, o.x0_given, hd->use_tma,
-                        (long long)(uintptr_t)c->stream, 0};
+                        (long long)(uintptr_t)c->stream, dt};
     GraphCache &gc = method == LS_METHOD_CG ? c->graph_cg : c->graph_gm;
     if (!gc.matches(key)) {
         rc = method == LS_METHOD_CG ? build_cg_graph(c, v, GL, o.x0_given, key)
@@ -535,6 +543,8 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
         if (rc) return rc;
     }
     cudaError_t e = cudaEventRecord(c->ev0, c->stream);
+    // the FP32 pair of A: one pass over A, timed as part of the solve
+    if (e == cudaSuccess && split) e = split_f64_launch(n, n, Ad, ldad, L.Ahi, L.Alo, L.ld32, c->num_sms, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
     rc = launch_cached(c, gc);
     if (rc) return rc;
@@ -588,22 +598,46 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
         *bytes = mixed_workspace_bytes(n, &o, a_on_device != 0);
         return LS_OK;
     }
-    *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device).bytes;
+    *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device, o.f64_matvec == 0).bytes;
     return LS_OK;
 }
 
 // ============================================================================
 // kernel-level entry points
 // ============================================================================
+// The matrix descriptor of a kernel-level call (LS_F64_PAIR: hi rows, then lo rows).
+static void kernel_desc(MatDesc *hd, int dtype, const void *A, int rows, int cols, long long lda) {
+    memset(hd, 0, sizeof(MatDesc));
+    if (dtype == DT_DS) {
+        const float *hi = static_cast<const float *>(A);
+        make_tensor_map_ds(hd, hi, hi + (long long)rows * lda, rows, cols, lda);
+    } else {
+        make_tensor_map(hd, dtype, A, rows, cols, lda);
+    }
+}
+
+extern "C" int ls_split_f64(ls_ctx *c, int rows, int cols, const double *A, int64_t lda, float *pair,
+                            int64_t ldp) {
+    if (!c || rows < 0 || cols < 0 || lda < cols || ldp < cols || (ldp & 3)) return LS_ERR_ARG;
+    if (rows == 0 || cols == 0) return LS_OK;
+    if (!A || !pair) return LS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+    cudaError_t e = split_f64_launch(rows, cols, A, lda, pair, pair + (long long)rows * ldp, ldp, c->num_sms,
+                                     c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) c->launches_total += 1;
+    return map_cuda(e);
+}
+
 extern "C" int ls_gemv(ls_ctx *c, int dtype, int rows, int cols, const void *A, int64_t lda,
                        const float *scale, const void *x, void *y) {
-    if (!c || rows < 0 || cols < 0 || lda < cols || dtype < 0 || dtype > 3) return LS_ERR_ARG;
+    if (!c || rows < 0 || cols < 0 || lda < cols || dtype < 0 || dtype > 4) return LS_ERR_ARG;
+    if (dtype == DT_DS && (lda & 3)) return LS_ERR_ARG;
     if (rows == 0) return LS_OK;
     if (!A || !x || !y || (dtype == DT_FP8 && !scale)) return LS_ERR_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
     MatDesc *hd = &c->h_desc[1];
-    memset(hd, 0, sizeof(MatDesc));
-    make_tensor_map(hd, dtype, A, rows, cols, lda);
+    kernel_desc(hd, dtype, A, rows, cols, lda);
     hd->scale = scale;
     int rc = upload_desc(c, 1);
     if (rc) return rc;
@@ -630,14 +664,13 @@ extern "C" int ls_gemv(ls_ctx *c, int dtype, int rows, int cols, const void *A, 
 extern "C" int ls_gemv_timed(ls_ctx *c, int dtype, int rows, int cols, const void *A, int64_t lda,
                              const float *scale, const void *x, void *y, int reps,
                              double *ms_per_launch) {
-    if (!c || rows <= 0 || cols <= 0 || lda < cols || dtype < 0 || dtype > 3 || reps < 1 ||
-        !ms_per_launch)
+    if (!c || rows <= 0 || cols <= 0 || lda < cols || dtype < 0 || dtype > 4 || reps < 1 ||
+        !ms_per_launch || (dtype == DT_DS && (lda & 3)))
         return LS_ERR_ARG;
     if (!A || !x || !y || (dtype == DT_FP8 && !scale)) return LS_ERR_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
     MatDesc *hd = &c->h_desc[1];
-    memset(hd, 0, sizeof(MatDesc));
-    make_tensor_map(hd, dtype, A, rows, cols, lda);
+    kernel_desc(hd, dtype, A, rows, cols, lda);
     hd->scale = scale;
     int rc = upload_desc(c, 1);
     if (rc) return rc;

@@ -10,7 +10,10 @@
 namespace lsi {
 
 // storage formats of A
-enum DType : int { DT_F64 = 0, DT_BF16 = 1, DT_FP8 = 2, DT_F32 = 3 };
+// DT_DS: an FP64 matrix split once into an FP32 pair A = hi + lo (hi = fp32(A),
+// lo = fp32(A - hi), about 48 significant bits), multiplied in double-single
+// arithmetic on the FP32 pipe; vectors and results stay FP64.
+enum DType : int { DT_F64 = 0, DT_BF16 = 1, DT_FP8 = 2, DT_F32 = 3, DT_DS = 4 };
 
 // ---- GEMV geometry ----------------------------------------------------------
 // A tile of TR rows x TC columns is one TMA box.  Consumer warps form a
@@ -25,7 +28,9 @@ constexpr int MAX_GRID = 2048;     // upper bound on CTAs of any persistent laun
 // ---- device-resident matrix descriptor ---------------------------------------
 struct alignas(128) MatDesc {
     CUtensorMap tmap;        // 2-D tiled TMA map of A (valid when use_tma)
-    const void *ptr;         // A (row-major)
+    CUtensorMap tmap_lo;     // DT_DS: the same for the low part
+    const void *ptr;         // A (row-major); DT_DS: the high part
+    const void *ptr_lo;      // DT_DS: the low part (same layout)
     const float *scale;      // FP8 row scales (else nullptr)
     long long lda;           // elements
     int rows, cols;
@@ -143,6 +148,11 @@ cudaError_t gemv_launch(const GemvLaunch &L, const MatDesc *dA, const GemvArgs &
 // Fill the TMA map of a matrix descriptor (host side); returns false when the
 // layout cannot be streamed by TMA (alignment), in which case use_tma = 0.
 bool make_tensor_map(MatDesc *h, int dtype, const void *ptr, int rows, int cols, long long lda);
+// DT_DS descriptor of the FP32 pair (hi, lo), both row-major with leading dimension ld.
+bool make_tensor_map_ds(MatDesc *h, const float *hi, const float *lo, int rows, int cols, long long ld);
+// hi = fp32(A), lo = fp32(A - hi), row-major with leading dimension ld (a multiple of 4).
+cudaError_t split_f64_launch(int rows, int cols, const double *A, long long lda, float *hi, float *lo,
+                             long long ld, int num_sms, cudaStream_t s);
 // FP32 row-major rows x cols (leading dimension ld) read in box_rows x box_cols
 // tiles with the 128-byte swizzle; `map` is 128 bytes, 64-byte aligned.
 bool encode_f32_tile_map_sw128(void *map, const float *ptr, int rows, int cols, long long ld,

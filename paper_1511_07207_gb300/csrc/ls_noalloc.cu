@@ -24,10 +24,10 @@ using namespace lsi;
 
 namespace {
 
-// The static array is laid out as [MatDesc | State | GemvScratch head + the
+// The static array is laid out as [MatDesc (512 B slot) | State | GemvScratch head + the
 // partial sums of at most NOALLOC_MAX_CTAS CTAs].
 constexpr size_t OFF_DESC = 0;
-constexpr size_t OFF_STATE = 256;
+constexpr size_t OFF_STATE = 512;
 constexpr size_t OFF_SCRATCH = OFF_STATE + ((sizeof(State) + 255) / 256) * 256;
 constexpr size_t SCRATCH_HEAD = offsetof(GemvScratch, fix);
 constexpr size_t NOALLOC_BYTES =

@@ -56,6 +56,23 @@ def test_cg_matches_oracle(ctx, gpu, oracle, n, sigma):
     assert info["launches"] >= 2 * info["iters"]
 
 
+@pytest.mark.parametrize("n", [257, 1000])
+def test_cg_native_fp64_matvec(ctx, gpu, oracle, n):
+    """f64_matvec = 1 (FP64 FMA products) meets the same bar as the default
+    double-single products, and the two agree within kappa * rtol."""
+    A = inputs.spd_matrix(n, 0.05, seed=n + 5)
+    xs = inputs.solution(n, seed=n + 5)
+    b = A @ xs
+    st1, i1, x1 = _solve(ctx, gpu, A, b, rtol=1e-10, f64_matvec=1)
+    st0, i0, x0 = _solve(ctx, gpu, A, b, rtol=1e-10, f64_matvec=0)
+    assert st0 == st1 == B.LS_OK
+    for x in (x0, x1):
+        assert np.linalg.norm(oracle.residual(A, b, x)) <= 1e-10 * np.linalg.norm(b)
+    kap = _kappa(A)
+    assert np.linalg.norm(x0 - x1) <= 4 * kap * 1e-10 * np.linalg.norm(xs)
+    assert abs(i0["iters"] - i1["iters"]) <= 2
+
+
 def test_cg_config_small_exact(ctx, gpu, oracle):
     """The n = 512, seed 0 SPD system (cond ~ 40): GPU and oracle agree."""
     n = 512

@@ -2,7 +2,11 @@
 the quantisation of A, against the oracle, through the C ABI.
 
 FP64: |y_gpu - y_oracle| <= 2 gamma_n |A| |x| elementwise (Higham's bound for
-two summation orders, u = 2^-53).  Low precision: the stored codes must equal
+two summation orders, u = 2^-53).  FP64 through the FP32 pair (the solvers'
+default): the split must equal fp32 rounding bit for bit, and the
+double-single product stays within cols 2^-45 |A| |x| of the oracle (each
+term carries errors of order 2^-48 |a x|, the low accumulator adds at most
+one 2^-24 rounding of an O(2^-24) quantity per term).  Low precision: the stored codes must equal
 the oracle's bit for bit; the product is compared with the FP64 product of the
 oracle-decoded matrix within 2 gamma_n(FP32) |A| |x|.  Sizes span several
 tiles with ragged row and column tails, padded leading dimensions, and odd
@@ -42,6 +46,31 @@ def test_gemv_f64(ctx, gpu, oracle, rows, cols, pad):
     ref = oracle.gemv(np.ascontiguousarray(A), x)
     bound = 2 * gamma(cols, 2.0 ** -53) * (np.abs(A) @ np.abs(x))
     assert np.all(np.abs(y - ref) <= bound + 1e-300)
+
+
+@pytest.mark.parametrize("rows,cols,pad", [(1, 1, 0), (31, 33, 3), (255, 256, 0), (513, 1000, 8),
+                                          (2049, 2047, 1), (300, 4100, 4), (4096, 4096, 0)])
+def test_gemv_f64_pair(ctx, gpu, oracle, rows, cols, pad):
+    rng = np.random.default_rng(rows * 11 + cols)
+    full, A = _strided(rng, rows, cols, pad)
+    x = rng.standard_normal(cols)
+    Ad = torch.from_numpy(full).to(gpu)[:, :cols]
+    ldp = (cols + 3) // 4 * 4
+    pair = torch.full((2 * rows, ldp), np.nan, dtype=torch.float32, device=gpu)
+    assert B.ls_split_f64(ctx, Ad, pair[:, :cols]) == B.LS_OK
+    hi = pair[:rows, :cols].cpu().numpy()
+    lo = pair[rows:, :cols].cpu().numpy()
+    assert np.array_equal(hi, A.astype(np.float32))
+    assert np.array_equal(lo, (A - hi.astype(np.float64)).astype(np.float32))
+    xd = torch.from_numpy(x).to(gpu)
+    yd = torch.full((rows,), np.nan, dtype=torch.float64, device=gpu)
+    assert B.ls_gemv(ctx, B.LS_F64_PAIR, pair[:rows, :cols], xd, yd) == B.LS_OK
+    y = yd.cpu().numpy()
+    ref = oracle.gemv(np.ascontiguousarray(A), x)
+    bound = cols * 2.0 ** -45 * (np.abs(A) @ np.abs(x))
+    assert np.all(np.abs(y - ref) <= bound + 1e-300)
+    # and far closer than an FP32 product would be
+    assert np.max(np.abs(y - ref) / (np.abs(A) @ np.abs(x))) < 1e-12
 
 
 def test_gemv_deterministic(ctx, gpu):

@@ -46,6 +46,19 @@ def test_gmres_matches_oracle(ctx, gpu, oracle, n, m):
     assert abs(info["iters"] - ref["iters"]) <= 1
 
 
+@pytest.mark.parametrize("f64_matvec", [0, 1])
+def test_gmres_both_matvec_modes(ctx, gpu, oracle, f64_matvec):
+    n = 700
+    A = inputs.nonsym_matrix(n, seed=77)
+    xs = inputs.solution(n, seed=77)
+    b = A @ xs
+    st, info, x = _solve(ctx, gpu, A, b, restart=30, rtol=1e-10, f64_matvec=f64_matvec)
+    ref = oracle.gmres(A, b, m=30, rtol=1e-10)
+    assert st == B.LS_OK
+    assert np.linalg.norm(oracle.residual(A, b, x)) <= 1e-10 * np.linalg.norm(b)
+    assert abs(info["iters"] - ref["iters"]) <= 1
+
+
 @pytest.mark.parametrize("m,reorth", [(5, 0), (12, 1), (30, 0)])
 def test_gmres_restarts(ctx, gpu, oracle, m, reorth):
     n = 300
