@@ -79,13 +79,15 @@ struct Cfg<DT_F64> {
     using Y = double;
     static constexpr int VEC = 2, WC = 4, WR = 1, RW = 8, PARTS = 1;
 };
+// 16 rows per warp: each lane's split x values (FP64-pipe conversions) serve
+// twice as many products as with 8
 template <>
 struct Cfg<DT_DS> {
     using T = float;    // hi and lo tiles of the same shape, one after the other
     using V = DSV;
     using X = double;
     using Y = double;
-    static constexpr int VEC = 2, WC = 4, WR = 1, RW = 8, PARTS = 2;
+    static constexpr int VEC = 2, WC = 4, WR = 1, RW = 16, PARTS = 2;
 };
 template <>
 struct Cfg<DT_BF16> {
