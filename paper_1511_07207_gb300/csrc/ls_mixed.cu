@@ -14,15 +14,16 @@ namespace lsi {
 struct MixLayout {
     double *x, *b, *r, *q, *P, *W, *dvals, *Astage;
     float *rf, *zf, *pf, *qf, *scale;
+    float *Ahi, *Alo;       // FP32 pair of A for the outer FP64 products (f64_matvec = 0)
     void *Q;
-    long long npad, ldp, ldq, lda_stage;
+    long long npad, ldp, ldq, lda_stage, ld32;
     int m;
     size_t bytes;
 };
 
 static int elt_size(int dtype) { return dtype == DT_BF16 ? 2 : dtype == DT_FP8 ? 1 : 4; }
 
-static MixLayout mix_layout(void *base, int n, int dtype, int m, bool fcg, bool stageA) {
+static MixLayout mix_layout(void *base, int n, int dtype, int m, bool fcg, bool stageA, bool split) {
     MixLayout L{};
     L.npad = (long long)align_up((size_t)std::max(n, 1), 64);
     L.ldp = L.npad;
@@ -44,6 +45,9 @@ static MixLayout mix_layout(void *base, int n, int dtype, int m, bool fcg, bool 
     L.scale = cv.take<float>(L.npad);
     L.Q = cv.take<unsigned char>((size_t)n * L.ldq * elt_size(dtype));
     L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
+    L.ld32 = (long long)align_up((size_t)std::max(n, 1), 4);
+    L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
+    L.Alo = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
     L.bytes = align_up(cv.off, 256);
     return L;
 }
@@ -57,7 +61,7 @@ static int outer_limit(const ls_opts &o) { return o.max_iter > 0 ? o.max_iter : 
 size_t mixed_workspace_bytes(int n, const ls_opts *o, bool a_on_device) {
     const int max_outer = outer_limit(*o);
     const int m = std::min(max_outer, LS_MAX_RESTART);
-    return mix_layout(nullptr, n, storage_dtype(o->precision), m, o->refine == LS_REFINE_FCG,
+    return mix_layout(nullptr, n, storage_dtype(o->precision), m, o->refine == LS_REFINE_FCG, o->f64_matvec == 0,
                       !a_on_device).bytes;
 }
 
@@ -175,10 +179,11 @@ int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double 
     const int m = std::min(max_outer, LS_MAX_RESTART);
     const bool fcg = o.refine == LS_REFINE_FCG;
     const bool a_dev = is_device_ptr(A);
-    MixLayout L = mix_layout(nullptr, n, dtype, m, fcg, !a_dev);
+    const bool split = o.f64_matvec == 0;
+    MixLayout L = mix_layout(nullptr, n, dtype, m, fcg, !a_dev, split);
     int rc = ws_reserve(c, L.bytes);
     if (rc) return rc;
-    L = mix_layout(c->ws, n, dtype, m, fcg, !a_dev);
+    L = mix_layout(c->ws, n, dtype, m, fcg, !a_dev, split);
 
     const double *Ad;
     long long ldad;
@@ -190,12 +195,15 @@ int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double 
     cudaError_t e = cudaEventRecord(c->ev0, c->stream);
     if (e == cudaSuccess)   // stage A: quantise once per solve
         e = quantize_launch(dtype, n, n, Ad, ldad, L.Q, L.ldq, L.scale, c->num_sms, c->stream);
+    if (e == cudaSuccess && split)   // and the FP32 pair for the outer FP64 products
+        e = split_f64_launch(n, n, Ad, ldad, L.Ahi, L.Alo, L.ld32, c->num_sms, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
 
     MatDesc *h64 = &c->h_desc[0], *hlo = &c->h_desc[1];
     memset(h64, 0, sizeof(MatDesc));
     memset(hlo, 0, sizeof(MatDesc));
-    make_tensor_map(h64, DT_F64, Ad, n, n, ldad);
+    if (split) make_tensor_map_ds(h64, L.Ahi, L.Alo, n, n, L.ld32);
+    else make_tensor_map(h64, DT_F64, Ad, n, n, ldad);
     make_tensor_map(hlo, dtype, L.Q, n, n, L.ldq);
     hlo->scale = dtype == DT_FP8 ? L.scale : nullptr;
     rc = upload_desc(c, 0);
@@ -206,7 +214,7 @@ int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double 
     hs->m = m;
     hs->in_max = o.inner_iters;
     hs->in_tol2 = o.inner_rtol > 0.0 ? (float)(o.inner_rtol * o.inner_rtol) : -1.0f;
-    hs->launches = 1;   // the quantisation kernel
+    hs->launches = split ? 2 : 1;   // the quantisation (and split) kernels
     if (!rc) rc = upload_state(c);
     if (rc) return rc;
 
@@ -217,9 +225,9 @@ int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double 
     v.dvals = L.dvals;
     v.rf = L.rf; v.zf = L.zf; v.pf = L.pf; v.qf = L.qf;
     v.part = c->part; v.bar = c->bar; v.st = c->st; v.rtol = o.rtol;
-    GemvLaunch L64 = gemv_plan(DT_F64, h64->use_tma != 0, EPI_DOT, c->num_sms);
+    GemvLaunch L64 = gemv_plan(split ? DT_DS : DT_F64, h64->use_tma != 0, EPI_DOT, c->num_sms);
     GemvLaunch Llo = gemv_plan(dtype, hlo->use_tma != 0, EPI_DOT, c->num_sms);
-    long long key[8] = {100 + o.refine, n, (long long)(uintptr_t)c->ws, dtype, o.x0_given,
+    long long key[8] = {100 + o.refine, n, (long long)(uintptr_t)c->ws, dtype * 2 + (split ? 1 : 0), o.x0_given,
                         h64->use_tma * 2 + hlo->use_tma, (long long)(uintptr_t)c->stream, m};
     if (!c->graph_mx.matches(key)) {
         rc = build_mixed_graph(c, v, L64, Llo, o.x0_given, key);
