@@ -496,7 +496,7 @@ def run_serve(B, ctx, dev, args):
         o = B.make_opts(rtol=rq.spec.rtol, restart=30)
         prepared.append((rq.t_arrival, B.make_system(method, A, Bh, Xh, o), Bh, Xh))
     torch.cuda.synchronize(dev)
-    srv = B.ls_server_start(ctx, hbm_budget_bytes=120 * (1 << 30), max_slots=args.serve_slots,
+    srv = B.ls_server_start(ctx, hbm_budget_bytes=120 * (1 << 30), max_slots=args.serve_slots, merge_rhs=1,
                             step_iters=args.serve_step)
     import collections
     tickets = [None] * len(prepared)
@@ -546,7 +546,7 @@ def run_serve(B, ctx, dev, args):
                           "p90": round(float(np.percentile(ms, 90)), 3),
                           "p99": round(float(np.percentile(ms, 99)), 3),
                           "max": round(float(ms.max()), 3)} if len(ms) else None,
-           "max_slots": args.serve_slots, "step_ticks": args.serve_step, "hbm_budget_GB": 120,
+           "max_slots": args.serve_slots, "step_ticks": args.serve_step, "hbm_budget_GB": 120, "merge_rhs": 1,
            "queue_full_retries": busy,
            "max_rel_res": max((x["true_rel_res"] for x in infos), default=None),
            "pool": "64 SPD + 64 nonsymmetric matrices, n log-uniform in [128, 8192], resident on the device"}

@@ -193,6 +193,16 @@ typedef struct {
     int max_slots;             /* requests resident on the device at once             */
     int step_iters;            /* iterations each resident request advances per step  */
     int queue_capacity;        /* pending requests before submit returns LS_ERR_BUSY  */
+    int merge_rhs;             /* 1: queued requests that share their matrix (the same
+                                  device A, lda, n, method and options) are admitted
+                                  together as right-hand-side columns of one slot (at
+                                  most 32), so A is read once per step for all of them.
+                                  Each column still runs its own iteration, but the
+                                  shared reductions round in an order that depends on
+                                  the slot's width, so a merged result matches a solo
+                                  solve within the tolerance, not bit for bit; the
+                                  slot's status (NaN, iteration limit) is shared.
+                                  0: one request per slot                              */
 } ls_server_cfg;
 
 typedef struct ls_server ls_server;

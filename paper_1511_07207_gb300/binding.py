@@ -59,7 +59,8 @@ class ls_system(ctypes.Structure):
 
 class ls_server_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
-                ("step_iters", ctypes.c_int), ("queue_capacity", ctypes.c_int)]
+                ("step_iters", ctypes.c_int), ("queue_capacity", ctypes.c_int),
+                ("merge_rhs", ctypes.c_int)]
 
 
 _lib = None
@@ -299,8 +300,9 @@ def ls_batch_solve(ctx, systems):
     return st, [i.as_dict() for i in infos]
 
 
-def ls_server_start(ctx, hbm_budget_bytes, max_slots=64, step_iters=8, queue_capacity=1 << 16):
-    cfg = ls_server_cfg(hbm_budget_bytes, max_slots, step_iters, queue_capacity)
+def ls_server_start(ctx, hbm_budget_bytes, max_slots=64, step_iters=8, queue_capacity=1 << 16,
+                    merge_rhs=1):
+    cfg = ls_server_cfg(hbm_budget_bytes, max_slots, step_iters, queue_capacity, merge_rhs)
     h = ctypes.c_void_p()
     st = load().ls_server_start(ctx, ctypes.byref(cfg), ctypes.byref(h))
     if st != LS_OK:

@@ -1110,19 +1110,20 @@ __global__ void eng_admit_kernel(const EngineDev *Ep, const double *const *Bsrc,
     }
 }
 
-// X (row-major) -> column-major destination (ldx).
-__global__ void eng_finish_kernel(const EngineDev *Ep, double *const *Xdst, const long long *ldx, int first,
-                                  int count) {
+// Columns [c0, c0 + k) of a slot's X (row-major n x sp) -> a column-major
+// destination (ldx), one item per (slot, column range).
+__global__ void eng_finish_kernel(const EngineDev *Ep, double *const *Xdst, const long long *ldx,
+                                  const int *slot, const int *c0, const int *k, int count) {
     const EngineDev &E = *Ep;
     for (int q = blockIdx.y; q < count; q += gridDim.y) {
-        const int sl = first + q;
-        const SlotDesc &D = E.desc[sl];
+        const SlotDesc &D = E.desc[slot[q]];
         double *x = Xdst[q];
-        const long long total = (long long)D.n * D.s;
+        const int cb = c0[q];
+        const long long total = (long long)D.n * k[q];
         for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
              e += (long long)gridDim.x * blockDim.x) {
             const int c = (int)(e / D.n), i = (int)(e % D.n);
-            x[(long long)c * ldx[q] + i] = D.X[(long long)i * D.sp + c];
+            x[(long long)c * ldx[q] + i] = D.X[(long long)i * D.sp + cb + c];
         }
     }
 }

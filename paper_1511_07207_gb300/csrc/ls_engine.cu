@@ -44,9 +44,10 @@ __global__ void eng_collect_kernel(const SlotDesc *desc, const SlotState *st, Sl
         r.outer = S.outer;
         r.done = S.phase == PH_DONE;
         double worst = 0.0;
-        for (int j = 0; j < D.s; j++) {
-            const double rel = S.bnorm[j] > 0.0 ? S.rn[j] / S.bnorm[j] : 0.0;
-            worst = rel > worst || rel != rel ? rel : worst;
+        for (int j = 0; j < E_MAXS; j++) {
+            const double rel = j < D.s && S.bnorm[j] > 0.0 ? S.rn[j] / S.bnorm[j] : 0.0;
+            r.colres[j] = rel;
+            if (j < D.s) worst = rel > worst || rel != rel ? rel : worst;
         }
         r.rel_res = worst;
         out[q] = r;
@@ -156,8 +157,11 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
         hE.launches = k.take<unsigned long long>(1);
         bsrc = k.take<const double *>(cap_slots);
         ldb = k.take<long long>(cap_slots);
-        xdst = k.take<double *>(cap_slots);
-        ldx = k.take<long long>(cap_slots);
+        xdst = k.take<double *>((size_t)cap_slots * E_MAXS);
+        ldx = k.take<long long>((size_t)cap_slots * E_MAXS);
+        fslot = k.take<int>((size_t)cap_slots * E_MAXS);
+        fc0 = k.take<int>((size_t)cap_slots * E_MAXS);
+        fk = k.take<int>((size_t)cap_slots * E_MAXS);
         results = k.take<SlotResult>(cap_slots);
     };
     layout(cv);
@@ -354,20 +358,33 @@ int Engine::admit(int first, int count, const std::vector<const double *> &bs,
     return map_cuda(e);
 }
 
-int Engine::finish(int first, int count, const std::vector<double *> &xs,
-                   const std::vector<long long> &lx) {
+int Engine::finish(const std::vector<FinishItem> &items) {
+    const int count = (int)items.size();
     if (count <= 0) return LS_OK;
-    cudaError_t e = cudaMemcpyAsync(xdst + first, xs.data(), count * sizeof(double *),
-                                    cudaMemcpyHostToDevice, c->stream);
+    if (count > cap_slots * E_MAXS) return LS_ERR_ARG;
+    std::vector<double *> xs(count);
+    std::vector<long long> lx(count);
+    std::vector<int> sl(count), c0(count), kk(count);
+    for (int i = 0; i < count; i++) {
+        xs[i] = items[i].x;
+        lx[i] = items[i].ldx;
+        sl[i] = items[i].slot;
+        c0[i] = items[i].c0;
+        kk[i] = items[i].k;
+    }
+    cudaError_t e = cudaMemcpyAsync(xdst, xs.data(), count * sizeof(double *), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ldx + first, lx.data(), count * sizeof(long long), cudaMemcpyHostToDevice,
-                            c->stream);
+        e = cudaMemcpyAsync(ldx, lx.data(), count * sizeof(long long), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fslot, sl.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fc0, c0.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fk, kk.data(), count * sizeof(int), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return map_cuda(e);
     const EngineDev *p = dE;
-    double *const *xp = xdst + first;
-    const long long *lp = ldx + first;
-    void *args[] = {(void *)&p, (void *)&xp, (void *)&lp, (void *)&first, (void *)&count};
+    double *const *xp = xdst;
+    const long long *lp = ldx;
+    const int *sp = fslot, *cp = fc0, *kp = fk;
+    void *args[] = {(void *)&p, (void *)&xp, (void *)&lp, (void *)&sp, (void *)&cp, (void *)&kp, (void *)&count};
     e = cudaLaunchKernel(K.finish, dim3(64, std::min(count, 1024)), dim3(256), args, 0, c->stream);
     return map_cuda(e);
 }
@@ -565,7 +582,9 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
     if (e == cudaSuccess) rc = E.run();
     if (e == cudaSuccess && !rc) e = cudaEventRecord(c->ev1, c->stream);
     if (e != cudaSuccess || rc) return rc ? rc : map_cuda(e);
-    rc = E.finish(0, count, xdst, ldx);
+    std::vector<FinishItem> items(count);
+    for (int q = 0; q < count; q++) items[q] = FinishItem{q, 0, sys[q].nrhs, xdst[q], ldx[q]};
+    rc = E.finish(items);
     std::vector<SlotResult> res;
     if (!rc) rc = E.collect(0, count, res);
     if (rc) return rc;

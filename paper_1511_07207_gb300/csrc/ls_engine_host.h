@@ -11,7 +11,15 @@ namespace lsi {
 
 struct SlotResult {
     int status, inner, outer, done;
-    double rel_res;
+    double rel_res;                 // worst column
+    double colres[E_MAXS];          // ||R_j|| / ||B_j|| per column
+};
+
+// Copy of columns [c0, c0 + k) of a slot's X to a column-major destination.
+struct FinishItem {
+    int slot, c0, k;
+    double *x;
+    long long ldx;
 };
 
 struct SlotSizes {
@@ -36,8 +44,9 @@ public:
     EngineDev hE{};
     const double **bsrc = nullptr;
     long long *ldb = nullptr;
-    double **xdst = nullptr;
+    double **xdst = nullptr;           // finish items (capacity cap_slots * E_MAXS)
     long long *ldx = nullptr;
+    int *fslot = nullptr, *fc0 = nullptr, *fk = nullptr;
     SlotResult *results = nullptr;
     std::vector<Task> h32, h64, hv;
     std::vector<int> h_order;            // eng_red block -> slot (costliest first)
@@ -56,7 +65,7 @@ public:
     int init_slots(int first, int count);
     int admit(int first, int count, const std::vector<const double *> &bs,
               const std::vector<long long> &lb);
-    int finish(int first, int count, const std::vector<double *> &xs, const std::vector<long long> &lx);
+    int finish(const std::vector<FinishItem> &items);
     int collect(int first, int count, std::vector<SlotResult> &out);
     int run();
     unsigned long long launches();

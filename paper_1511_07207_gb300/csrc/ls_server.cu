@@ -8,6 +8,10 @@
 // finished (write X, post the info, free the slot and its memory).  Requests
 // that arrive while others are on the GPU join at the next step, and their
 // work overlaps with the resident ones inside the same engine launches.
+// With merge_rhs, queued requests that share their matrix (the same device
+// A, lda, n, method and options) are admitted together as the right-hand-side
+// columns of one slot (up to 32), so A is streamed once per step for all of
+// them; every column still follows its own iteration.
 // submit and poll only touch the host-side queue and result table, under a
 // mutex, so any thread may call them.
 #include <cuda_runtime.h>
@@ -102,11 +106,39 @@ struct Request {
     SlotSizes z{};
 };
 
-struct Resident {
+struct Member {
     Request req;
-    char *mem = nullptr;
-    double *xstage = nullptr;
+    int c0 = 0;                         // first column of the slot
+    double *xstage = nullptr;           // device staging of a host X
 };
+
+struct Resident {
+    std::vector<Member> m;              // requests sharing the slot (columns c0 ..)
+    char *mem = nullptr;
+    size_t bytes = 0;
+    SlotSizes z{};
+    int s = 0;                          // columns in use
+    bool a_stage = false;               // A copied from the host (single member)
+};
+
+// Requests that may share a slot: the same device-resident A and options.
+bool same_problem(const Request &a, const Request &b) {
+    const ls_system &x = a.sys, &y = b.sys;
+    return a.a_dev && b.a_dev && x.A == y.A && x.lda == y.lda && x.n == y.n && x.method == y.method &&
+           x.opts.rtol == y.opts.rtol && x.opts.restart == y.opts.restart &&
+           x.opts.inner_iters == y.opts.inner_iters && x.opts.inner_rtol == y.opts.inner_rtol &&
+           x.opts.max_iter == y.opts.max_iter;
+}
+
+// Device bytes of a slot of s columns for the problem of `rq` (engine buffers,
+// A's copy when it is on the host, B's staging, X's staging when any member's
+// X is on the host).
+size_t slot_bytes(const Request &rq, int s, bool any_host_x, SlotSizes *zo) {
+    const ls_system &S = rq.sys;
+    const SlotSizes z = slot_sizes(S.n, s, S.method, S.opts.restart);
+    if (zo) *zo = z;
+    return z.bytes + (rq.a_dev ? 0 : z.stageA) + z.stageBX + (any_host_x ? z.stageBX : 0);
+}
 
 }  // namespace
 
@@ -132,24 +164,34 @@ struct ls_server {
     bool tables_dirty = true;
 
     void run();
-    int admit_one(Request &rq, int slot);
-    void retire(int slot, const SlotResult &r, double extra_ms);
+    int admit_slot(std::vector<Request> &members, int slot);
+    void retire(int slot, const SlotResult &r);
 };
 
 namespace {
 constexpr int SERVER_MAX_N = LS_BATCH_MAX_N;
 }
 
-int ls_server::admit_one(Request &rq, int slot) {
-    const ls_system &S = rq.sys;
-    char *mem = pool.alloc(rq.bytes);
-    if (!mem) return LS_ERR_NOMEM;
+int ls_server::admit_slot(std::vector<Request> &members, int slot) {
+    const Request &r0 = members[0];
+    const ls_system S = r0.sys;         // a copy: the members are moved into the slot below
+    int ncol = 0;
+    bool any_host_x = false;
+    for (const Request &q : members) {
+        ncol += q.sys.nrhs;
+        any_host_x = any_host_x || !q.x_dev;
+    }
     Resident &R = res[slot];
+    R.bytes = slot_bytes(r0, ncol, any_host_x, &R.z);
+    char *mem = pool.alloc(R.bytes);
+    if (!mem) return LS_ERR_NOMEM;
     R.mem = mem;
+    R.s = ncol;
+    R.a_stage = !r0.a_dev;
     SlotDesc &D = hd[slot];
     memset(&D, 0, sizeof(D));
-    slot_carve(D, rq.z, mem, S.n, S.nrhs, S.method, S.opts.restart);
-    char *p = mem + rq.z.bytes;
+    slot_carve(D, R.z, mem, S.n, ncol, S.method, S.opts.restart);
+    char *p = mem + R.z.bytes;
     D.inner_iters = S.method == LS_METHOD_CG ? (S.opts.inner_iters > 0 ? 4 * S.opts.inner_iters : 100)
                                              : S.opts.restart;
     D.max_outer = S.opts.max_iter > 0 ? S.opts.max_iter : 20;
@@ -157,53 +199,70 @@ int ls_server::admit_one(Request &rq, int slot) {
     D.rtol = S.opts.rtol;
     cudaStream_t st = shadow.stream;
     cudaError_t e = cudaSuccess;
-    if (rq.a_dev) {
+    if (r0.a_dev) {
         D.A64 = S.A;
         D.lda64 = S.lda;
     } else {
         double *a = reinterpret_cast<double *>(p);
-        p += rq.z.stageA;
-        e = cudaMemcpy2DAsync(a, rq.z.lda_stage * 8, rq.hostA.data(), (size_t)S.n * 8, (size_t)S.n * 8,
+        p += R.z.stageA;
+        e = cudaMemcpy2DAsync(a, R.z.lda_stage * 8, r0.hostA.data(), (size_t)S.n * 8, (size_t)S.n * 8,
                               S.n, cudaMemcpyHostToDevice, st);
         D.A64 = a;
-        D.lda64 = rq.z.lda_stage;
+        D.lda64 = R.z.lda_stage;
     }
+    // B staging: the members' columns side by side (column-major, ld n)
     double *bstage = reinterpret_cast<double *>(p);
-    p += rq.z.stageBX;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(bstage, rq.hostB.data(), (size_t)S.n * S.nrhs * 8, cudaMemcpyHostToDevice, st);
-    R.xstage = nullptr;
-    if (!rq.x_dev) {
-        R.xstage = reinterpret_cast<double *>(p);
-        p += rq.z.stageBX;
+    p += R.z.stageBX;
+    double *xstage = any_host_x ? reinterpret_cast<double *>(p) : nullptr;
+    R.m.clear();
+    int c0 = 0;
+    for (Request &q : members) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bstage + (size_t)c0 * S.n, q.hostB.data(), (size_t)S.n * q.sys.nrhs * 8,
+                                cudaMemcpyHostToDevice, st);
+        Member mb;
+        mb.c0 = c0;
+        mb.xstage = q.x_dev ? nullptr : xstage + (size_t)c0 * S.n;
+        c0 += q.sys.nrhs;
+        mb.req = std::move(q);
+        R.m.push_back(std::move(mb));
     }
-    R.req = std::move(rq);
     used[slot] = 1;
     n_resident++;
     if (e != cudaSuccess) return map_cuda(e);
     return LS_OK;
 }
 
-void ls_server::retire(int slot, const SlotResult &r, double) {
+void ls_server::retire(int slot, const SlotResult &r) {
     Resident &R = res[slot];
-    const ls_system &S = R.req.sys;
-    ls_info info{};
-    info.status = r.status;
-    info.iters = r.inner;
-    info.outer_iters = r.outer;
-    info.rel_res = r.rel_res;
-    info.true_rel_res = r.rel_res;
-    info.time_ms = std::chrono::duration<double, std::milli>(Clock::now() - R.req.t_submit).count();
-    const double nn = (double)S.n * S.n;
-    info.bytes_moved = nn * 12.0 + r.outer * 8.0 * nn + r.inner * 4.0 * nn;
-    pool.free(R.mem, R.req.bytes);
+    std::vector<std::pair<uint64_t, ls_info>> out;
+    for (const Member &mb : R.m) {
+        const ls_system &S = mb.req.sys;
+        ls_info info{};
+        info.status = r.status;
+        info.iters = r.inner;
+        info.outer_iters = r.outer;
+        double worst = 0.0;
+        for (int j = mb.c0; j < mb.c0 + S.nrhs && j < E_MAXS; j++)
+            worst = r.colres[j] > worst || r.colres[j] != r.colres[j] ? r.colres[j] : worst;
+        info.rel_res = worst;
+        info.true_rel_res = worst;
+        info.time_ms = std::chrono::duration<double, std::milli>(Clock::now() - mb.req.t_submit).count();
+        const double nn = (double)S.n * S.n;
+        info.bytes_moved = (nn * 12.0 + r.outer * 8.0 * nn + r.inner * 4.0 * nn) / (double)R.m.size();
+        out.emplace_back(mb.req.ticket, info);
+    }
+    pool.free(R.mem, R.bytes);
     R.mem = nullptr;
+    R.m.clear();
     memset(&hd[slot], 0, sizeof(SlotDesc));
     used[slot] = 0;
     n_resident--;
     std::lock_guard<std::mutex> lk(mu);
-    done[R.req.ticket] = info;
-    pending.erase(R.req.ticket);
+    for (auto &o : out) {
+        done[o.first] = o.second;
+        pending.erase(o.first);
+    }
 }
 
 void ls_server::run() {
@@ -235,23 +294,55 @@ void ls_server::run() {
                     queue.pop_front();
                     continue;
                 }
+                // the requests that share the head's matrix (bounded scan)
+                std::vector<size_t> pick(1, 0);
+                int ncol = rq.sys.nrhs;
+                bool any_host_x = !rq.x_dev;
+                if (cfg.merge_rhs && rq.a_dev) {
+                    for (size_t i = 1; i < queue.size() && i < 4096 && ncol < LS_BATCH_MAX_RHS; i++) {
+                        const Request &o = queue[i];
+                        if (ncol + o.sys.nrhs > LS_BATCH_MAX_RHS || !same_problem(rq, o)) continue;
+                        const bool hx = any_host_x || !o.x_dev;
+                        if (slot_bytes(rq, ncol + o.sys.nrhs, hx, nullptr) > pool.size) break;
+                        pick.push_back(i);
+                        ncol += o.sys.nrhs;
+                        any_host_x = hx;
+                    }
+                }
+                std::vector<Request> members;
+                members.reserve(pick.size());
+                for (size_t i : pick) members.push_back(std::move(queue[i]));
+                for (size_t k = pick.size(); k-- > 0;) queue.erase(queue.begin() + (long)pick[k]);
                 lk.unlock();
-                int rc = admit_one(rq, slot);
+                int rc = admit_slot(members, slot);
+                if (rc == LS_ERR_NOMEM && members.size() > 1) {
+                    // not enough free memory for the merged slot: admit the head
+                    // alone, requeue the others at the front
+                    lk.lock();
+                    for (size_t k = members.size(); k-- > 1;) queue.push_front(std::move(members[k]));
+                    members.resize(1);
+                    lk.unlock();
+                    rc = admit_slot(members, slot);
+                }
                 lk.lock();
-                if (rc == LS_ERR_NOMEM) break;              // wait for memory to free up
+                if (rc == LS_ERR_NOMEM) {                   // wait for memory to free up
+                    for (size_t k = members.size(); k-- > 0;) queue.push_front(std::move(members[k]));
+                    break;
+                }
                 if (rc != LS_OK) {
-                    ls_info info{};
-                    info.status = rc;
-                    done[res[slot].req.ticket] = info;
-                    pending.erase(res[slot].req.ticket);
-                    pool.free(res[slot].mem, res[slot].req.bytes);
+                    for (const Member &mb : res[slot].m) {
+                        ls_info info{};
+                        info.status = rc;
+                        done[mb.req.ticket] = info;
+                        pending.erase(mb.req.ticket);
+                    }
+                    pool.free(res[slot].mem, res[slot].bytes);
+                    res[slot].m.clear();
                     memset(&hd[slot], 0, sizeof(SlotDesc));
                     used[slot] = 0;
                     n_resident--;
-                    queue.pop_front();
                     continue;
                 }
-                queue.pop_front();
                 admitted.push_back(slot);
             }
         }
@@ -265,9 +356,9 @@ void ls_server::run() {
         for (int s : admitted) {
             if (!rc) rc = eng.init_slots(s, 1);
             std::vector<const double *> bs(1, nullptr);
-            std::vector<long long> lb(1, res[s].req.sys.n);
+            std::vector<long long> lb(1, hd[s].n);
             // B was staged right after the slot's engine buffers and A's copy
-            char *p = res[s].mem + res[s].req.z.bytes + (res[s].req.a_dev ? 0 : res[s].req.z.stageA);
+            char *p = res[s].mem + res[s].z.bytes + (res[s].a_stage ? res[s].z.stageA : 0);
             bs[0] = reinterpret_cast<const double *>(p);
             if (!rc) rc = eng.admit(s, 1, bs, lb);
         }
@@ -278,20 +369,33 @@ void ls_server::run() {
             thread_err = rc;
             break;
         }
+        std::vector<FinishItem> items;
+        std::vector<int> fin;
         for (int s = 0; s < cap; s++) {
             if (!used[s] || !results[s].done) continue;
-            Resident &R = res[s];
-            const ls_system &S = R.req.sys;
-            std::vector<double *> xs(1, R.xstage ? R.xstage : S.X);
-            std::vector<long long> lx(1, R.xstage ? (long long)S.n : S.ldx);
-            rc = eng.finish(s, 1, xs, lx);
-            if (!rc && R.xstage)
-                rc = map_cuda(cudaMemcpy2DAsync(S.X, S.ldx * 8, R.xstage, (size_t)S.n * 8, (size_t)S.n * 8,
-                                                S.nrhs, cudaMemcpyDeviceToHost, shadow.stream));
+            for (const Member &mb : res[s].m) {
+                const ls_system &S = mb.req.sys;
+                items.push_back(FinishItem{s, mb.c0, S.nrhs, mb.xstage ? mb.xstage : S.X,
+                                           mb.xstage ? (long long)S.n : S.ldx});
+            }
+            fin.push_back(s);
+        }
+        if (!items.empty()) {
+            rc = eng.finish(items);
+            for (int s : fin)
+                for (const Member &mb : res[s].m) {
+                    const ls_system &S = mb.req.sys;
+                    if (!rc && mb.xstage)
+                        rc = map_cuda(cudaMemcpy2DAsync(S.X, S.ldx * 8, mb.xstage, (size_t)S.n * 8,
+                                                        (size_t)S.n * 8, S.nrhs, cudaMemcpyDeviceToHost,
+                                                        shadow.stream));
+                }
             if (!rc) rc = map_cuda(cudaStreamSynchronize(shadow.stream));
-            SlotResult r = results[s];
-            if (rc) r.status = rc;
-            retire(s, r, 0.0);
+            for (int s : fin) {
+                SlotResult r = results[s];
+                if (rc) r.status = rc;
+                retire(s, r);
+            }
             tables_dirty = true;
         }
     }
@@ -299,11 +403,14 @@ void ls_server::run() {
     std::lock_guard<std::mutex> lk(mu);
     for (int s = 0; s < cap; s++) {
         if (!used[s]) continue;
-        ls_info info{};
-        info.status = thread_err ? thread_err : LS_NOT_CONVERGED;
-        done[res[s].req.ticket] = info;
-        pending.erase(res[s].req.ticket);
-        pool.free(res[s].mem, res[s].req.bytes);
+        for (const Member &mb : res[s].m) {
+            ls_info info{};
+            info.status = thread_err ? thread_err : LS_NOT_CONVERGED;
+            done[mb.req.ticket] = info;
+            pending.erase(mb.req.ticket);
+        }
+        pool.free(res[s].mem, res[s].bytes);
+        res[s].m.clear();
         used[s] = 0;
     }
     n_resident = 0;
@@ -370,8 +477,7 @@ extern "C" int ls_server_submit(ls_server *s, const ls_system *req, uint64_t *ti
     cudaSetDevice(s->ctx->device);
     rq.a_dev = is_device_ptr(S.A) != 0;
     rq.x_dev = is_device_ptr(S.X) != 0;
-    rq.z = slot_sizes(S.n, S.nrhs, S.method, S.opts.restart);
-    rq.bytes = rq.z.bytes + (rq.a_dev ? 0 : rq.z.stageA) + rq.z.stageBX + (rq.x_dev ? 0 : rq.z.stageBX);
+    rq.bytes = slot_bytes(rq, S.nrhs, !rq.x_dev, &rq.z);
     if (rq.bytes > s->pool.size) return LS_ERR_NOMEM;
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -103,6 +103,48 @@ def test_server_serves_mixed_requests(ctx, gpu, oracle):
         assert np.array_equal(Xd.cpu().numpy(), rq["X"]), rq["spec"]
 
 
+@pytest.mark.parametrize("merge", [1, 0])
+def test_server_shared_matrices(ctx, gpu, oracle, merge):
+    """Requests that share a device matrix (merged into one slot as extra
+    right-hand-side columns when merge_rhs is on) each meet their tolerance and
+    agree with the oracle's solution within cond(A) * rtol."""
+    mats = []
+    for k, kind in enumerate(("spd", "nonsym", "spd")):
+        sp = inputs.SystemSpec(300 + 97 * k, kind, 1, 900 + k)
+        A = sp.matrix()
+        mats.append((sp, A, torch.from_numpy(A).to(gpu)))
+    r = np.random.default_rng(5)
+    reqs = []
+    for i in range(18):
+        sp, A, Ad = mats[i % 3]
+        s = int(r.integers(1, 6))
+        Xs = r.uniform(-1, 1, (sp.n, s))
+        Bm = A @ Xs
+        rtol = 1e-10 if i % 2 else 1e-6
+        Xh = np.zeros((sp.n, s), order="F")
+        Bh = np.asfortranarray(Bm)            # must stay alive until submit has copied it
+        method = B.LS_METHOD_CG if sp.kind == "spd" else B.LS_METHOD_GMRES
+        sysd = B.make_system(method, Ad, Bh, Xh, B.make_opts(rtol=rtol, restart=30))
+        reqs.append(dict(A=A, B=Bm, Bh=Bh, X=Xh, sys=sysd, rtol=rtol, kind=sp.kind))
+    srv = B.ls_server_start(ctx, hbm_budget_bytes=1 << 30, max_slots=4, step_iters=4, merge_rhs=merge)
+    try:
+        tickets = []
+        for rq in reqs:                       # a burst: the queue fills before admission
+            st, t = B.ls_server_submit(srv, rq["sys"])
+            assert st == B.LS_OK
+            tickets.append(t)
+        infos = _wait(srv, tickets)
+    finally:
+        assert B.ls_server_stop(srv) == B.LS_OK
+    for rq, t in zip(reqs, tickets):
+        assert infos[t]["status"] == B.LS_OK
+        A, Bm, X = rq["A"], rq["B"], rq["X"]
+        for j in range(Bm.shape[1]):
+            rel = np.linalg.norm(oracle.residual(A, Bm[:, j], X[:, j])) / np.linalg.norm(Bm[:, j])
+            assert rel <= rq["rtol"] * 1.0000001
+        assert infos[t]["rel_res"] <= rq["rtol"]
+
+
 def test_server_budget_and_errors(ctx, gpu):
     specs = _specs(10, 2)
     reqs = [_request(sp, gpu, 1e-10) for sp in specs]
