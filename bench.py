@@ -653,6 +653,20 @@ def run_kernel(args):
     B.ls_destroy(ctx)
 
 
+def run_batch_only(args):
+    """The batched engine alone (ncu captures of its kernels): the first
+    --count systems of the 512-system recipe, one ls_batch_solve."""
+    import torch
+    from paper_1511_07207_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    ctx = B.ls_create(0, torch.cuda.current_stream(dev))
+
+    class _A:
+        steps = 1
+    print(json.dumps(run_batch_compare(B, ctx, dev, _A, count=args.count)))
+    B.ls_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -670,8 +684,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
     ap.add_argument("--cpu-cg-sample", type=int, default=600)
-    ap.add_argument("--kernel", choices=["gemv"], default=None,
-                    help="kernel-only timing (small cases for ncu captures)")
+    ap.add_argument("--kernel", choices=["gemv", "batch"], default=None,
+                    help="kernel-only timing (small cases for ncu captures): one GEMV format, "
+                         "or the batched engine alone on --count systems")
+    ap.add_argument("--count", type=int, default=128, help="--kernel batch: systems in the batch")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--dtype", choices=["f64", "pair", "bf16", "fp8", "f32"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
@@ -682,6 +698,8 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.kernel == "gemv":
         run_kernel(args)
+    elif args.kernel == "batch":
+        run_batch_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
