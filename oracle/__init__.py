@@ -75,6 +75,7 @@ class Oracle:
         lib.or_residual.argtypes = [i, P, l, P, P, P, i]
         lib.or_cg.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P, P, P]
         lib.or_gmres.argtypes = [i, P, l, P, P, i, d, i, i, i, P, P, P, P, P, P, P]
+        lib.or_bicgstab.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P, P, P, P]
         lib.or_ge_solve.argtypes = [i, P, l, P, P]
         for name in ("or_bf16_round", "or_e4m3_round"):
             getattr(lib, name).argtypes = [d]
@@ -128,6 +129,25 @@ class Oracle:
         if history:
             k = it.value
             out.update(res_hist=rh[: k + 1], R=R[: k + 1], P=P[: k + 1])
+        return out
+
+    def bicgstab(self, A, b, rtol=1e-10, max_iter=None, x0=None, nthreads=1, trace=False):
+        """BiCGSTAB.  Returns dict(x, status, iters, rel_res[, shs, rt, alphas])."""
+        A = _mat(A)
+        n = A.shape[0]
+        b = _vec(b, n)
+        max_iter = 10 * n + 10 if max_iter is None else max_iter
+        x = np.zeros(n) if x0 is None else _vec(x0, n).copy()
+        it, rr, steps = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_int(0)
+        shs = np.zeros(max_iter + 1) if trace else None
+        rt = np.zeros(max_iter + 1) if trace else None
+        al = np.zeros(max_iter + 1) if trace else None
+        st = self.lib.or_bicgstab(n, _p(A), n, _p(b), _p(x), rtol, max_iter, int(x0 is not None),
+                                  nthreads, ctypes.byref(it), ctypes.byref(rr), _p(shs), _p(rt),
+                                  _p(al), ctypes.byref(steps))
+        out = dict(x=x, status=st, iters=it.value, rel_res=rr.value)
+        if trace:
+            out.update(shs=shs[: steps.value], rt=rt[: steps.value], alphas=al[: steps.value])
         return out
 
     def gmres(self, A, b, m=30, rtol=1e-10, max_iter=None, x0=None, nthreads=1,

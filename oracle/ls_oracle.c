@@ -18,6 +18,8 @@
  *     the restart paragraph that follows it.  The paper stops before the
  *     least-squares step; the Givens-rotation update used here is the
  *     standard one from Saad's book, which the paper cites for GMRES.
+ *   - BiCGSTAB: same section, BiCGSTAB listing, with the steps the listing
+ *     leaves out written in (see or_bicgstab).
  *   - Gaussian elimination with partial pivoting: same section,
  *     "Right-looking LU factorization", then forward/back substitution.
  *   - Mixed precision (BF16 / FP8-e4m3 storage of A, FP32 inner CG, FP64
@@ -178,6 +180,124 @@ int or_cg(int n, const double *A, long lda, const double *b, double *x,
     *rel_res_out = nrm2(n, q) / nb;
     *iters_out = k;
     free(r); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* BiCGSTAB, FP64                                                      */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper's BiCGSTAB (van der Vorst's stabilised BiCG), in the order of its
+ * listing: rho_0 = 1, rho_1 = r^.r with the shadow residual r^ = r(0),
+ * alpha = omega = 1, p = v = 0; per step beta = (rho_k / rho_{k-1})
+ * (alpha / omega), p = r + beta (p - omega v), v = A p, alpha = rho_k /
+ * (r^.v), s = r - alpha v, t = A s, omega, x += alpha p + omega s.  The
+ * listing prints omega as a product and leaves out three steps, written in
+ * here: omega = (t.s) / (t.t); r = s - omega t; rho_{k+1} = r^.r; and the
+ * stop test ||r|| <= rtol ||b||, confirmed on the true residual b - A x (when
+ * it fails, the iteration restarts from it with r^ = r).  When ||s|| already
+ * passes the test the step ends with x += alpha p (no second product).
+ * Breakdown (status 2): rho = 0, r^.v = 0, or t.t = 0 / omega = 0 with s != 0.
+ * iters counts the matrix-vector products inside the loop (two per full
+ * step).  Optional traces for tests, one entry per step (length max_iter):
+ * shs[k] = (r^.s) / (|r^| |s|) and rt[k] = (r_new.t) / (|r_new| |t|); both
+ * are zero in exact arithmetic (alpha makes s orthogonal to r^, omega
+ * minimises ||s - omega t||, so r_new is orthogonal to t); alphas[k] = alpha of
+ * the step (equal to BiCG's in exact arithmetic).  steps_out receives the
+ * number of traced steps.
+ */
+int or_bicgstab(int n, const double *A, long lda, const double *b, double *x,
+                double rtol, int max_iter, int x0_given, int nthreads,
+                int *iters_out, double *rel_res_out, double *shs, double *rt, double *alphas,
+                int *steps_out) {
+    if (n < 0 || lda < n || max_iter < 0) return OR_ERR_ARG;
+    const size_t sz = sizeof(double) * (n ? n : 1);
+    double *r = malloc(sz), *rh = malloc(sz), *p = malloc(sz), *v = malloc(sz);
+    double *s = malloc(sz), *t = malloc(sz), *q = malloc(sz);
+    int status = OR_NOT_CONVERGED, k = 0, steps = 0;
+    const double nb = nrm2(n, b), tol = rtol * nrm2(n, b);
+    double rho_prev, rho, alpha, omega;
+
+    if (!x0_given) {
+        for (int i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
+    } else {
+        residual(n, A, lda, b, x, r, nthreads);
+    }
+    if (nb == 0.0) {                      /* b = 0: x = 0 solves exactly */
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        *iters_out = 0; *rel_res_out = 0.0;
+        if (steps_out) *steps_out = 0;
+        free(r); free(rh); free(p); free(v); free(s); free(t); free(q);
+        return OR_OK;
+    }
+    int check = nrm2(n, r) <= tol, fresh = 1;
+    for (;;) {
+        if (fresh) {                      /* (re)start: r^ = r, rho_0 = 1, p = v = 0 */
+            memcpy(rh, r, sizeof(double) * n);
+            for (int i = 0; i < n; i++) { p[i] = 0.0; v[i] = 0.0; }
+            rho_prev = 1.0;
+            rho = dot(n, rh, r);
+            alpha = 1.0;
+            omega = 1.0;
+            fresh = 0;
+        }
+        if (check) {
+            residual(n, A, lda, b, x, q, nthreads);
+            if (nrm2(n, q) <= tol) { status = OR_OK; break; }
+            memcpy(r, q, sizeof(double) * n);
+            check = 0;
+            fresh = 1;
+            continue;
+        }
+        if (k >= max_iter) break;
+        if (rho == 0.0 || !isfinite(rho)) { status = OR_BREAKDOWN; break; }
+        const double beta = (rho / rho_prev) * (alpha / omega);
+        for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        gemv(n, n, A, lda, p, v, nthreads);          /* v = A p */
+        k++;
+        const double rv = dot(n, rh, v);
+        if (rv == 0.0 || !isfinite(rv)) { status = OR_BREAKDOWN; break; }
+        alpha = rho / rv;
+        if (alphas) alphas[steps] = alpha;
+        for (int i = 0; i < n; i++) s[i] = r[i] - alpha * v[i];
+        const double ns = nrm2(n, s);
+        if (shs) shs[steps] = dot(n, rh, s) / (nrm2(n, rh) * (ns > 0.0 ? ns : 1.0));
+        if (ns <= tol) {                  /* s passes: x += alpha p ends the step */
+            for (int i = 0; i < n; i++) x[i] += alpha * p[i];
+            memcpy(r, s, sizeof(double) * n);
+            if (rt) rt[steps] = 0.0;
+            steps++;
+            check = 1;
+            continue;
+        }
+        if (k >= max_iter) {
+            for (int i = 0; i < n; i++) x[i] += alpha * p[i];
+            memcpy(r, s, sizeof(double) * n);
+            steps++;
+            break;
+        }
+        gemv(n, n, A, lda, s, t, nthreads);          /* t = A s */
+        k++;
+        const double tt = dot(n, t, t);
+        if (tt == 0.0 || !isfinite(tt)) { status = OR_BREAKDOWN; break; }
+        omega = dot(n, t, s) / tt;
+        for (int i = 0; i < n; i++) x[i] += alpha * p[i] + omega * s[i];
+        for (int i = 0; i < n; i++) r[i] = s[i] - omega * t[i];
+        if (rt) {
+            const double nr = nrm2(n, r), nt = sqrt(tt);
+            rt[steps] = dot(n, r, t) / ((nr > 0.0 ? nr : 1.0) * nt);
+        }
+        steps++;
+        rho_prev = rho;
+        rho = dot(n, rh, r);
+        if (omega == 0.0) { status = OR_BREAKDOWN; break; }
+        check = nrm2(n, r) <= tol;
+    }
+    residual(n, A, lda, b, x, q, nthreads);
+    *rel_res_out = nrm2(n, q) / nb;
+    *iters_out = k;
+    if (steps_out) *steps_out = steps;
+    free(r); free(rh); free(p); free(v); free(s); free(t); free(q);
     return status;
 }
 

@@ -10,6 +10,7 @@ import os
 import pytest
 
 import oracle as oracle_pkg
+import test_oracle_bicgstab as tbs
 import test_oracle_cg as tcg
 import test_oracle_ge_quant as tgq
 import test_oracle_gmres as tgm
@@ -47,6 +48,16 @@ MUTATIONS = {
                                  lambda o: tmx.test_fcg_ill_conditioned_bf16(o)),
     "inner_beta_inverted": ("float beta = rho_new / rho;", "float beta = rho / rho_new;",
                             lambda o: tmx.test_inner_cg_f32_solves_stored_matrix(o)),
+    "bicgstab_omega_sign": ("for (int i = 0; i < n; i++) r[i] = s[i] - omega * t[i];",
+                            "for (int i = 0; i < n; i++) r[i] = s[i] + omega * t[i];",
+                            lambda o: tbs.test_bicgstab_step_orthogonality(o)),
+    "bicgstab_alpha_not_shadow": ("const double rv = dot(n, rh, v);", "const double rv = dot(n, r, v);",
+                                  lambda o: tbs.test_bicgstab_step_orthogonality(o)),
+    "bicgstab_p_drops_v": ("p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];",
+                           lambda o: tbs.test_bicgstab_alphas_equal_bicg(o)),
+    "bicgstab_beta_inverted": ("const double beta = (rho / rho_prev) * (alpha / omega);",
+                               "const double beta = (rho / rho_prev) * (omega / alpha);",
+                               lambda o: tbs.test_bicgstab_alphas_equal_bicg(o)),
 }
 
 
