@@ -55,6 +55,7 @@ extern "C" {
 /* ---- methods and precisions ------------------------------------------- */
 #define LS_METHOD_CG     0
 #define LS_METHOD_GMRES  1
+#define LS_METHOD_BICGSTAB 2   /* ls_bicgstab_solve only (not in the batched engine) */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -159,6 +160,22 @@ int ls_cg_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *
  */
 int ls_gmres_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
                    double *x, const ls_opts *opts, ls_info *info);
+
+/*
+ * BiCGSTAB (paper: BiCGSTAB listing, van der Vorst's stabilised BiCG) for
+ * general nonsingular A: two matrix-vector products, four inner products and
+ * six vector updates per step, shadow residual r^ = r(0).  The steps the
+ * listing leaves out are: omega = (t.s) / (t.t), r = s - omega t,
+ * rho_{k+1} = r^.r, and the stop test ||r|| <= rtol ||b|| (confirmed on the
+ * true residual; when it fails the iteration restarts from it with r^ = r).
+ * When ||s|| already passes, x += alpha p ends the step.  info->iters counts
+ * matrix-vector products (two per full step).  Breakdown (r^.v = 0,
+ * rho = 0, t.t = 0 or omega = 0 before convergence) returns LS_BREAKDOWN with
+ * the last iterate in x.  Arguments as for ls_cg_solve; opts->precision must
+ * be LS_F64 (else LS_ERR_UNSUPPORTED).
+ */
+int ls_bicgstab_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
+                      double *x, const ls_opts *opts, ls_info *info);
 
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {

@@ -348,6 +348,15 @@ __device__ __forceinline__ void run_finaliser(const GemvArgs &a, double dot) {
         case FIN_FCG_D:
             st->pq = dot;
             break;
+        case FIN_BS_ALPHA:
+            st->pq = dot;
+            if (dot == 0.0 || !isfinite(dot)) {
+                st->status = LS_BREAKDOWN;
+                st->alpha = 0.0;
+            } else {
+                st->alpha = st->rho / dot;
+            }
+            break;
         default:
             st->dot = dot;
             break;

@@ -9,6 +9,18 @@
 //                alpha itself is produced by the GEMV's last CTA (p.q);
 //     cg_check   after the loop: accept on the true residual b - A x, or
 //                restart from it (residual replacement) while iterations remain.
+//   BiCGSTAB (paper, BiCGSTAB listing; the steps it leaves out -- omega =
+//   t.s / t.t, r = s - omega t, the next rho = r^.r and the stop test -- are
+//   written in):
+//     bs_init    x = 0 (or keep x0), r = b (or b - A x0), r^ = r, p = r, v = 0,
+//                rho = r^.r, ||b||, the tolerance, the loop conditions;
+//     bs_s       s = r - alpha v (alpha from the first GEMV's last CTA: rho /
+//                r^.v), ||s||; when ||s|| passes, x += alpha p ends the step;
+//     bs_update  omega = t.s / t.t (t.s from the second GEMV), x += alpha p +
+//                omega s, r = s - omega t, rho' = r^.r, stop test,
+//                beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v);
+//     bs_check   after the loop: accept on the true residual, or restart from
+//                it with r^ = r while iterations remain.
 //   GMRES(m) (paper, GMRES pseudocode and the restart paragraph; the
 //   least-squares update by Givens rotations follows Saad's book):
 //     gm_init    x = 0 (or keep x0), ||b|| and the tolerance;
@@ -416,11 +428,277 @@ __global__ void __launch_bounds__(KB) gm_finish_kernel(Vecs v) {
     }
 }
 
+// ============================================================================
+// BiCGSTAB
+// ============================================================================
+__global__ void __launch_bounds__(KB) bs_init_kernel(Vecs v, int x0_given,
+                                                     cudaGraphConditionalHandle h_outer,
+                                                     cudaGraphConditionalHandle h_inner) {
+    __shared__ double red[KB / 32];
+    State *st = v.st;
+    count_launch(st);
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    double bb = 0.0, rr = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double bi = v.b[i];
+        double ri;
+        if (!x0_given) {
+            v.x[i] = 0.0;
+            ri = bi;
+            v.r[i] = ri;
+        } else {
+            ri = v.r[i];           // b - A x0, written by the residual GEMV
+        }
+        v.rh[i] = ri;
+        v.p[i] = ri;
+        v.vv[i] = 0.0;
+        bb += bi * bi;
+        rr += ri * ri;
+    }
+    bb = block_sum(bb, red);
+    rr = block_sum(rr, red);
+    publish(v.part, 0, bb);
+    publish(v.part, 1, rr);
+    if (!grid_sync(v.bar, st)) return;
+    __shared__ double b2_s;
+    if (threadIdx.x < 32) {
+        const double t = reduce_slot(v.part, 0, gridDim.x);
+        if (threadIdx.x == 0) b2_s = t;
+    }
+    __syncthreads();
+    if (b2_s == 0.0 && x0_given)   // b = 0: x = 0 solves exactly, whatever x0 was
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) v.x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const double b2 = b2_s;
+        const double r2 = reduce_slot(v.part, 1, gridDim.x);
+        if (threadIdx.x == 0) {
+            const double bn = sqrt(b2);
+            st->bnorm = bn;
+            st->tol_abs = v.rtol * bn;
+            st->rho = r2;              // r^ = r
+            st->alpha = 1.0;
+            st->omega = 1.0;
+            st->skip = 0;
+            st->rnorm = sqrt(r2);
+            st->true_rnorm = sqrt(r2);
+            int go = 1;
+            if (!isfinite(b2) || !isfinite(r2)) {
+                set_err(st, ERRB_NAN);
+                go = 0;
+            } else if (bn == 0.0 || sqrt(r2) <= st->tol_abs) {
+                st->status = LS_OK;
+                go = 0;
+            } else if (st->max_iter <= 0) {
+                st->status = LS_NOT_CONVERGED;
+                go = 0;
+            }
+            set_cond(v.st, h_outer, go);
+            set_cond(v.st, h_inner, go);
+        }
+    }
+}
+
+// s = r - alpha v, ||s||^2; when ||s|| passes the test (or the next product
+// would exceed the limit) x += alpha p, r = s and the step ends here.
+__global__ void __launch_bounds__(KB) bs_s_kernel(Vecs v, cudaGraphConditionalHandle h_inner) {
+    __shared__ double red[KB / 32];
+    State *st = v.st;
+    count_launch(st);
+    if (st->status == LS_BREAKDOWN || st->err) {   // r^.v = 0 (or a wait failed)
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->skip = 1;
+            set_cond(v.st, h_inner, 0);
+        }
+        return;
+    }
+    const double alpha = st->alpha, tol = st->tol_abs;
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    double ss = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double si = v.r[i] - alpha * v.vv[i];
+        v.s[i] = si;
+        ss += si * si;
+    }
+    ss = block_sum(ss, red);
+    publish(v.part, 0, ss);
+    if (!grid_sync(v.bar, st)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->skip = 1;
+            set_cond(v.st, h_inner, 0);
+        }
+        return;
+    }
+    __shared__ double ss_s;
+    if (threadIdx.x < 32) {
+        const double t = reduce_slot(v.part, 0, gridDim.x);
+        if (threadIdx.x == 0) ss_s = t;
+    }
+    __syncthreads();
+    const double s2 = ss_s;
+    const bool finite = isfinite(s2);
+    const bool pass = finite && sqrt(s2) <= tol;
+    const bool last = st->iter + 1 >= st->max_iter;   // no room for the second product
+    if (finite && (pass || last)) {
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            v.x[i] += alpha * v.p[i];
+            v.r[i] = v.s[i];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->iter += 1;                 // v = A p
+        if (!finite) set_err(st, ERRB_NAN);
+        const int stop = !finite || pass || last;
+        st->skip = stop;
+        if (pass) {
+            st->conv = 1;
+            st->rnorm = sqrt(s2);
+        }
+        if (stop) set_cond(v.st, h_inner, 0);
+    }
+}
+
+// omega = t.s / t.t, x += alpha p + omega s, r = s - omega t, rho' = r^.r,
+// stop test, beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
+__global__ void __launch_bounds__(KB) bs_update_kernel(Vecs v, cudaGraphConditionalHandle h_inner) {
+    __shared__ double red[KB / 32];
+    State *st = v.st;
+    count_launch(st);
+    if (st->skip) return;
+    const double alpha = st->alpha, rho = st->rho, tol = st->tol_abs, ts = st->dot;
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    double tt = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double ti = v.t[i];
+        tt += ti * ti;
+    }
+    tt = block_sum(tt, red);
+    publish(v.part, 0, tt);
+    if (!grid_sync(v.bar, st)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
+        return;
+    }
+    __shared__ double tt_s;
+    if (threadIdx.x < 32) {
+        const double t = reduce_slot(v.part, 0, gridDim.x);
+        if (threadIdx.x == 0) tt_s = t;
+    }
+    __syncthreads();
+    const double t2 = tt_s;
+    if (t2 == 0.0 || !isfinite(t2) || !isfinite(ts)) {   // t = A s = 0 with s != 0, or NaN
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->iter += 1;
+            if (!isfinite(t2) || !isfinite(ts)) set_err(st, ERRB_NAN);
+            else st->status = LS_BREAKDOWN;
+            set_cond(v.st, h_inner, 0);
+        }
+        return;
+    }
+    const double omega = ts / t2;
+    double rr = 0.0, rhr = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double si = v.s[i];
+        v.x[i] += alpha * v.p[i] + omega * si;
+        const double ri = si - omega * v.t[i];
+        v.r[i] = ri;
+        rr += ri * ri;
+        rhr += v.rh[i] * ri;
+    }
+    rr = block_sum(rr, red);
+    rhr = block_sum(rhr, red);
+    publish(v.part, 1, rr);
+    publish(v.part, 2, rhr);
+    if (!grid_sync(v.bar, st)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(v.st, h_inner, 0);
+        return;
+    }
+    __shared__ double rr_s, rhr_s;
+    if (threadIdx.x < 32) {
+        const double a = reduce_slot(v.part, 1, gridDim.x);
+        const double b = reduce_slot(v.part, 2, gridDim.x);
+        if (threadIdx.x == 0) {
+            rr_s = a;
+            rhr_s = b;
+        }
+    }
+    __syncthreads();
+    const double r2 = rr_s, rho_new = rhr_s;
+    const bool finite = isfinite(r2) && isfinite(rho_new);
+    const bool conv = finite && sqrt(r2) <= tol;
+    const bool broke = omega == 0.0 || rho_new == 0.0;
+    const int iter_new = st->iter + 1;                 // t = A s
+    const bool go = finite && !conv && !broke && iter_new < st->max_iter;
+    if (go) {
+        const double beta = (rho_new / rho) * (alpha / omega);
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+            v.p[i] = v.r[i] + beta * (v.p[i] - omega * v.vv[i]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->omega = omega;
+        st->beta = (rho_new / rho) * (alpha / omega);
+        st->rho = rho_new;
+        st->rnorm = sqrt(r2);
+        st->iter = iter_new;
+        st->conv = conv;
+        if (!finite) set_err(st, ERRB_NAN);
+        else if (broke && !conv) st->status = LS_BREAKDOWN;
+        if (!go) set_cond(v.st, h_inner, 0);
+    }
+}
+
+// After the loop the GEMV has put q = b - A x and ||q|| (true_rnorm) in place:
+// accept, stop, or restart from q with a new shadow residual r^ = q.
+__global__ void __launch_bounds__(KB) bs_check_kernel(Vecs v, cudaGraphConditionalHandle h_outer,
+                                                      cudaGraphConditionalHandle h_inner) {
+    State *st = v.st;
+    count_launch(st);
+    const double t = st->true_rnorm;
+    int decision;   // 0 accept, 1 limit, 2 breakdown/error, 3 restart
+    if (st->err || !isfinite(t)) decision = 2;
+    else if (t <= st->tol_abs) decision = 0;
+    else if (st->status == LS_BREAKDOWN) decision = 2;
+    else if (st->iter >= st->max_iter) decision = 1;
+    else decision = 3;
+    if (decision == 3) {
+        long long lo, hi;
+        block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const double qi = v.q[i];
+            v.r[i] = qi;
+            v.rh[i] = qi;
+            v.p[i] = qi;
+            v.vv[i] = 0.0;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (decision == 0) st->status = LS_OK;
+        if (decision == 1) st->status = LS_NOT_CONVERGED;
+        if (decision == 2 && !isfinite(t)) set_err(st, ERRB_NAN);
+        st->cycles += 1;   // true-residual checks
+        if (decision == 3) {
+            st->rho = t * t;
+            st->rnorm = t;
+            st->alpha = 1.0;
+            st->omega = 1.0;
+            st->conv = 0;
+            st->skip = 0;
+        }
+        set_cond(v.st, h_outer, decision == 3);
+        set_cond(v.st, h_inner, decision == 3);
+    }
+}
+
 KrylovKernels krylov_kernels(int num_sms) {
     KrylovKernels K{};
     K.cg_init = reinterpret_cast<void *>(&cg_init_kernel);
     K.cg_update = reinterpret_cast<void *>(&cg_update_kernel);
     K.cg_check = reinterpret_cast<void *>(&cg_check_kernel);
+    K.bs_init = reinterpret_cast<void *>(&bs_init_kernel);
+    K.bs_s = reinterpret_cast<void *>(&bs_s_kernel);
+    K.bs_update = reinterpret_cast<void *>(&bs_update_kernel);
+    K.bs_check = reinterpret_cast<void *>(&bs_check_kernel);
     K.gm_init = reinterpret_cast<void *>(&gm_init_kernel);
     K.gm_start = reinterpret_cast<void *>(&gm_start_kernel);
     K.gm_arnoldi = reinterpret_cast<void *>(&gm_arnoldi_kernel);

@@ -49,6 +49,7 @@ int ws_reserve(ls_ctx *c, size_t bytes) {
     c->graph_cg.reset();
     c->graph_gm.reset();
     c->graph_mx.reset();
+    c->graph_bs.reset();
     cudaError_t e = cudaMalloc(&c->ws, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -288,6 +289,7 @@ extern "C" int ls_destroy(ls_ctx *c) {
     c->graph_cg.reset();
     c->graph_gm.reset();
     c->graph_mx.reset();
+    c->graph_bs.reset();
     extra_destroy(c);
     if (c->ws && !c->ws_user) cudaFree(c->ws);
     if (c->fixed) cudaFree(c->fixed);
@@ -308,6 +310,7 @@ extern "C" int ls_set_workspace(ls_ctx *c, void *ptr, size_t bytes) {
     c->graph_cg.reset();
     c->graph_gm.reset();
     c->graph_mx.reset();
+    c->graph_bs.reset();
     c->ws = static_cast<char *>(ptr);
     c->ws_bytes = ptr ? bytes : 0;
     c->ws_user = ptr != nullptr;
@@ -323,6 +326,7 @@ namespace lsi {
 
 struct F64Layout {
     double *x, *b, *r, *p, *q, *V, *Astage;
+    double *rh, *vv, *s, *t;   // BiCGSTAB
     float *Ahi, *Alo;    // the FP32 pair of A (double-single products)
     long long npad, ldv, lda_stage, ld32;
     size_t bytes;
@@ -340,6 +344,10 @@ F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA, bool spl
     L.p = cv.take<double>(L.npad);
     L.q = cv.take<double>(L.npad);
     L.V = gmres ? cv.take<double>((size_t)L.ldv * (m + 1)) : nullptr;
+    L.rh = cv.take<double>(L.npad);
+    L.vv = cv.take<double>(L.npad);
+    L.s = cv.take<double>(L.npad);
+    L.t = cv.take<double>(L.npad);
     L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
     L.ld32 = (long long)align_up((size_t)std::max(n, 1), 4);
     L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
@@ -377,6 +385,10 @@ Vecs make_vecs(ls_ctx *c, const F64Layout &L, int n, double rtol) {
     v.q = L.q;
     v.V = L.V;
     v.ldv = L.ldv;
+    v.rh = L.rh;
+    v.vv = L.vv;
+    v.s = L.s;
+    v.t = L.t;
     v.part = c->part;
     v.bar = c->bar;
     v.st = c->st;
@@ -436,6 +448,64 @@ static int build_cg_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_
         return LS_ERR_CUDA;
     }
     return finish_graph(c, c->graph_cg, R, key);
+}
+
+// Builds: [resid GEMV if x0] bs_init, while(outer){ while(inner){GEMV v = A p (r^.v -> alpha),
+// bs_s, GEMV t = A s (t.s), bs_update}, resid GEMV, bs_check }
+static int build_bicgstab_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
+                                const long long *key) {
+    Root R;
+    if (!R.create()) return LS_ERR_CUDA;
+    cudaGraphConditionalHandle ho, hi;
+    if (!R.handle(&ho) || !R.handle(&hi)) {
+        R.discard();
+        return LS_ERR_CUDA;
+    }
+    Chain top = R.chain();
+    const MatDesc *dA = c->dA;
+    if (x0_given) {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.r; a.b = v.b; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_RESID; a.fin = FIN_TRUE_RES;
+        gemv_node(top, L, dA, a);
+    }
+    {
+        Vecs vv = v;
+        int x0 = x0_given;
+        void *args[] = {&vv, &x0, &ho, &hi};
+        top.kernel(c->K.bs_init, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    Chain outer = top.loop(ho);
+    Chain inner = outer.loop(hi);
+    {
+        GemvArgs a{};
+        a.x = v.p; a.y = v.vv; a.z = v.rh; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_DOT; a.fin = FIN_BS_ALPHA;
+        gemv_node(inner, L, dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &hi};
+        inner.kernel(c->K.bs_s, c->K.coop_grid, c->K.block, 0, args, true);
+        GemvArgs a2{};
+        a2.x = v.s; a2.y = v.t; a2.z = v.s; a2.st = v.st; a2.scr = c->scr;
+        a2.epi = EPI_DOT; a2.fin = FIN_STORE;          // st->dot = t.s
+        gemv_node(inner, L, dA, a2);
+        void *args2[] = {&vv, &hi};
+        inner.kernel(c->K.bs_update, c->K.coop_grid, c->K.block, 0, args2, true);
+    }
+    {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.q; a.b = v.b; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_RESID; a.fin = FIN_TRUE_RES;
+        gemv_node(outer, L, dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &ho, &hi};
+        outer.kernel(c->K.bs_check, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    if (top.err != cudaSuccess || inner.err != cudaSuccess || outer.err != cudaSuccess) {
+        R.discard();
+        return LS_ERR_CUDA;
+    }
+    return finish_graph(c, c->graph_bs, R, key);
 }
 
 // Builds: gm_init, while(outer){ resid GEMV, gm_start, while(inner){GEMV, arnoldi}, gm_finish }
@@ -536,10 +606,12 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     GemvLaunch GL = gemv_plan(dt, hd->use_tma != 0, EPI_DOT, c->num_sms);
     long long key[8] = {method, n, (long long)(uintptr_t)c->ws, L.ldv, o.x0_given, hd->use_tma,
                         (long long)(uintptr_t)c->stream, dt};
-    GraphCache &gc = method == LS_METHOD_CG ? c->graph_cg : c->graph_gm;
+    GraphCache &gc = method == LS_METHOD_CG ? c->graph_cg : method == LS_METHOD_BICGSTAB ? c->graph_bs
+                                                                                        : c->graph_gm;
     if (!gc.matches(key)) {
-        rc = method == LS_METHOD_CG ? build_cg_graph(c, v, GL, o.x0_given, key)
-                                    : build_gmres_graph(c, v, GL, o.x0_given, key);
+        rc = method == LS_METHOD_CG         ? build_cg_graph(c, v, GL, o.x0_given, key)
+             : method == LS_METHOD_BICGSTAB ? build_bicgstab_graph(c, v, GL, o.x0_given, key)
+                                            : build_gmres_graph(c, v, GL, o.x0_given, key);
         if (rc) return rc;
     }
     cudaError_t e = cudaEventRecord(c->ev0, c->stream);
@@ -565,7 +637,7 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     // matrix passes: method products + true-residual checks (+ the x0 residual)
     double passes;
     State sc = s;
-    if (method == LS_METHOD_CG) {
+    if (method == LS_METHOD_CG || method == LS_METHOD_BICGSTAB) {
         passes = s.iter + s.cycles + (o.x0_given ? 1 : 0);
     } else {
         passes = s.total + s.cycles + 1;
@@ -586,6 +658,12 @@ extern "C" int ls_gmres_solve(ls_ctx *c, int n, const double *A, int64_t lda, co
                               double *x, const ls_opts *opts, ls_info *info) {
     if (opts && opts->precision != LS_F64) return LS_ERR_UNSUPPORTED;
     return krylov_f64(c, LS_METHOD_GMRES, n, A, lda, b, x, opts, info);
+}
+
+extern "C" int ls_bicgstab_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b,
+                                 double *x, const ls_opts *opts, ls_info *info) {
+    if (opts && opts->precision != LS_F64) return LS_ERR_UNSUPPORTED;
+    return krylov_f64(c, LS_METHOD_BICGSTAB, n, A, lda, b, x, opts, info);
 }
 
 extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const ls_opts *opts,

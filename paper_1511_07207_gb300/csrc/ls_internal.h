@@ -50,6 +50,7 @@ struct State {
     // CG / common
     double rho;          // r.r
     double alpha, beta;
+    double omega;        // BiCGSTAB stabilisation step
     double pq;           // p.Ap
     double bnorm;        // ||b||
     double tol_abs;      // rtol * ||b||
@@ -77,6 +78,7 @@ struct State {
     int outer, max_outer;
     int nstored;         // FCG directions stored
     int in_stop;
+    int skip;            // BiCGSTAB: the rest of the step is skipped (s passed, or stop)
     float in_tol2;       // inner (rtol^2 * rho0), <0 = fixed count
     int launches_lo;     // kernels executed (low word; counted by block 0)
     int hostloop;        // 1: loop conditions go to cond[] instead of graph handles
@@ -118,6 +120,7 @@ enum : int {
     FIN_WNORM0 = 3,     // wnorm0 = dot
     FIN_INNER_ALPHA = 4,// in_pq = dot; in_alpha = in_rho / in_pq (inner stop on breakdown)
     FIN_FCG_D = 5,      // pq = dot (p.Ap of the outer direction)
+    FIN_BS_ALPHA = 6,   // BiCGSTAB: pq = r^.v; alpha = rho / pq; breakdown if pq = 0
 };
 
 struct GemvArgs {
@@ -166,6 +169,7 @@ struct GridBar;
 struct Vecs {
     int n;
     double *x, *b, *r, *p, *q;
+    double *rh, *vv, *s, *t;   // BiCGSTAB: shadow residual r^, v = A p, s, t = A s
     double *V;           // GMRES basis, column-major, column stride ldv
     long long ldv;
     double *part;        // cooperative partial sums, [slot][block]
@@ -200,6 +204,7 @@ MixedKernels mixed_kernels();
 // ---- Krylov launchers (k_krylov.cu) -----------------------------------------------
 struct KrylovKernels {
     void *cg_init, *cg_update, *cg_check;
+    void *bs_init, *bs_s, *bs_update, *bs_check;
     void *gm_init, *gm_start, *gm_arnoldi, *gm_finish;
     int coop_grid;       // blocks of the cooperative vector kernels
     int block;           // threads per block
