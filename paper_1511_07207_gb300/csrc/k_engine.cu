@@ -41,7 +41,7 @@ __device__ __forceinline__ int claim(int *counter, int *slot_s) {
 // ============================================================================
 __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cudaGraphConditionalHandle h) {
     const EngineDev &E = *Ep;
-    __shared__ int all_stop, newphase_s, cnt_s, first_s, base_s, cntv_s, basev_s;
+    __shared__ int all_stop, newphase_s, cnt_s, first_s, base_s, cntv_s, basev_s, res_s;
     const int sl = blockIdx.x < E.nslots ? E.order[blockIdx.x] : 0;
     const int j = threadIdx.x;
     eng_count(E);
@@ -199,10 +199,11 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
     const int par = E.active[A_TICKS] & 1;
     if (threadIdx.x == 0) {
         const int np = (ph != PH_FREE && ph != PH_DONE) ? newphase_s : PH_FREE;
-        int cnt = 0, first = 0, cntv = 0;
-        if (np == PH_RESID) {
+        int cnt = 0, first = 0, cntv = 0, res = 0;
+        if (np == PH_RESID) {          // the longest tasks: listed apart, claimed first
             cnt = D.n64;
             first = D.t64;
+            res = 1;
         } else if (np == PH_CG || np == PH_GM || np == PH_START) {   // START: A32 / A32lo split
             cnt = D.n32;
             first = E.n64 + D.t32;
@@ -211,14 +212,16 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
         cnt_s = cnt;
         first_s = first;
         cntv_s = cntv;
-        base_s = cnt ? atomicAdd(&E.active[A_LEN_PROD + par], cnt) : 0;
+        res_s = res;
+        base_s = cnt ? atomicAdd(&E.active[(res ? A_LEN_RES : A_LEN_PROD) + par], cnt) : 0;
         basev_s = cntv ? atomicAdd(&E.active[A_LEN_VEC + par], cntv) : 0;
     }
     __syncthreads();
     {
-        int *wp = E.work[par];
+        int *wp = E.work[par] + (res_s ? E.wres : 0);
         for (int i = threadIdx.x; i < cnt_s; i += RED_T) wp[base_s + i] = first_s + i;
-        for (int i = threadIdx.x; i < cntv_s; i += RED_T) wp[E.wvec + basev_s + i] = D.tv + i;
+        int *wv = E.work[par] + E.wvec;
+        for (int i = threadIdx.x; i < cntv_s; i += RED_T) wv[basev_s + i] = D.tv + i;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
             E.active[A_CLAIM_PROD] = 0;    // task claim counters of eng_prod / eng_vec
             E.active[A_CLAIM_VEC] = 0;
             E.active[A_LEN_PROD + (par ^ 1)] = 0;   // lists of the next tick
+            E.active[A_LEN_RES + (par ^ 1)] = 0;
             E.active[A_LEN_VEC + (par ^ 1)] = 0;
         }
     }
@@ -711,8 +715,9 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
     const int par = (E.active[A_TICKS] - 1) & 1;               // list set of this tick
     if (warp == PC_W) {
         // ---------------- producer warp ----------------
-        const int total = E.active[A_LEN_PROD + par];
-        const int *wp = E.work[par];
+        const int nres = E.active[A_LEN_RES + par];
+        const int total = nres + E.active[A_LEN_PROD + par];
+        const int *wp = E.work[par], *wr = E.work[par] + E.wres;
         int seq = 0;
         bool fail = false;
         auto push_marker = [&](int kind, int u) -> bool {
@@ -732,7 +737,7 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
             if (lane == 0) w = atomicAdd(E.active + A_CLAIM_PROD, 1);
             w = __shfl_sync(0xffffffffu, w, 0);
             if (w >= total) break;
-            const int u = wp[w];
+            const int u = w < nres ? wr[w] : wp[w - nres];
             const Task T = u < E.n64 ? E.t64[u] : E.t32[u - E.n64];
             if (T.slot < 0) continue;                                   // unused entry
             const int ph = E.st[T.slot].phase;

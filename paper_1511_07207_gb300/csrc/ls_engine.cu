@@ -152,7 +152,8 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
         hE.tmaps = k.take<unsigned char>((size_t)cap_slots * 256);
         hE.work[0] = k.take<int>((size_t)cap64 + cap32 + capv);
         hE.work[1] = k.take<int>((size_t)cap64 + cap32 + capv);
-        hE.wvec = cap64 + cap32;
+        hE.wres = cap32;
+        hE.wvec = cap32 + cap64;
         hE.active = k.take<int>(A_SIZE);
         hE.launches = k.take<unsigned long long>(1);
         bsrc = k.take<const double *>(cap_slots);

@@ -154,9 +154,10 @@ struct EngineDev {               // pointers handed to every engine kernel
     int *order;                  // eng_red block b handles slot order[b] (costliest first)
     const unsigned char *tmaps;  // per slot: 2 x 128-byte TMA maps, A32 and A32lo (256 x 32 tiles,
                                  // 128-byte swizzle)
-    int *work[2];                // per tick parity: runnable eng_prod tasks, then room for
-                                 // the runnable eng_vec tasks at work[p] + wvec
-    int wvec;                    // offset of the vector-task list in work[p]
+    int *work[2];                // per tick parity: runnable FP32 product tasks, then the
+                                 // residual tasks at work[p] + wres, the vector tasks at
+                                 // work[p] + wvec
+    int wres, wvec;              // offsets of the residual and vector lists in work[p]
     int *active;                 // engine counters, see the A_* indices
     int tick_limit;              // ticks per graph launch (loop control)
     int host_loop;               // 1: no graph; eng_red writes the loop condition to active[4]
@@ -175,6 +176,7 @@ enum : int {
     A_ERR = 7,        // a bounded wait in eng_prod gave up (the launch's results are void)
     A_LEN_PROD = 8,   // [8 + parity]: runnable eng_prod tasks listed by eng_red
     A_LEN_VEC = 10,   // [10 + parity]: runnable eng_vec tasks
+    A_LEN_RES = 12,   // [12 + parity]: runnable refinement-residual tasks (claimed first)
     A_SIZE = 16
 };
 
