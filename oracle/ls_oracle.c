@@ -18,6 +18,8 @@
  *     the restart paragraph that follows it.  The paper stops before the
  *     least-squares step; the Givens-rotation update used here is the
  *     standard one from Saad's book, which the paper cites for GMRES.
+ *   - Jacobi: same section, first paragraph (the stationary methods, which
+ *     the paper takes from the textbooks): x(k+1) = x(k) + D^-1 (b - A x(k)).
  *   - BiCGSTAB: same section, BiCGSTAB listing, with the steps the listing
  *     leaves out written in (see or_bicgstab).
  *   - Gaussian elimination with partial pivoting: same section,
@@ -180,6 +182,51 @@ int or_cg(int n, const double *A, long lda, const double *b, double *x,
     *rel_res_out = nrm2(n, q) / nb;
     *iters_out = k;
     free(r); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Jacobi, FP64                                                        */
+/* ------------------------------------------------------------------ */
+/*
+ * The stationary Jacobi iteration x(k+1) = x(k) + D^-1 (b - A x(k)), D the
+ * diagonal of A.  Every product gives the residual of the current iterate;
+ * the iteration stops when ||b - A x(k)|| <= rtol ||b|| and returns that
+ * x(k).  iters counts the products (the last one only tested x(k)).  A zero
+ * diagonal entry is a breakdown (status 2).  res_hist (optional, length
+ * max_iter + 1) receives ||b - A x(k)|| for k = 0 .. iters - 1.
+ */
+int or_jacobi(int n, const double *A, long lda, const double *b, double *x,
+              double rtol, int max_iter, int x0_given, int nthreads,
+              int *iters_out, double *rel_res_out, double *res_hist) {
+    if (n < 0 || lda < n || max_iter < 0) return OR_ERR_ARG;
+    const size_t sz = sizeof(double) * (n ? n : 1);
+    double *r = malloc(sz);
+    int status = OR_NOT_CONVERGED, k = 0;
+    const double nb = nrm2(n, b), tol = rtol * nrm2(n, b);
+    if (!x0_given)
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+    for (int i = 0; i < n; i++)
+        if (A[(long)i * lda + i] == 0.0) { status = OR_BREAKDOWN; goto done; }
+    if (nb == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        status = OR_OK;
+        goto done;
+    }
+    while (k < max_iter) {
+        residual(n, A, lda, b, x, r, nthreads);          /* r = b - A x(k) */
+        const double nr = nrm2(n, r);
+        if (res_hist) res_hist[k] = nr;
+        k++;
+        if (!isfinite(nr)) break;
+        if (nr <= tol) { status = OR_OK; break; }
+        for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i];
+    }
+done:
+    residual(n, A, lda, b, x, r, nthreads);
+    *rel_res_out = nb > 0.0 ? nrm2(n, r) / nb : 0.0;
+    *iters_out = k;
+    free(r);
     return status;
 }
 

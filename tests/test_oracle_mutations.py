@@ -14,6 +14,7 @@ import test_oracle_bicgstab as tbs
 import test_oracle_cg as tcg
 import test_oracle_ge_quant as tgq
 import test_oracle_gmres as tgm
+import test_oracle_jacobi as tja
 import test_oracle_mixed as tmx
 
 MUTATIONS = {
@@ -58,6 +59,17 @@ MUTATIONS = {
     "bicgstab_beta_inverted": ("const double beta = (rho / rho_prev) * (alpha / omega);",
                                "const double beta = (rho / rho_prev) * (omega / alpha);",
                                lambda o: tbs.test_bicgstab_alphas_equal_bicg(o)),
+    "jacobi_divides_by_row_sum": ("for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i];",
+                                  "for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i + 1];",
+                                  lambda o: tja.test_jacobi_diagonal_one_update(o)),
+    "jacobi_update_sign": ("for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i];",
+                           "for (int i = 0; i < n; i++) x[i] -= r[i] / A[(long)i * lda + i];",
+                           lambda o: tja.test_jacobi_matches_lapack(o, 40)),
+    "jacobi_gauss_seidel_sweep": ("for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i];",
+                                  "for (int i = 0; i < n; i++) { x[i] += r[i] / A[(long)i * lda + i];"
+                                  " for (int q = i + 1; q < n; q++) r[q] -= A[(long)q * lda + i] * r[i]"
+                                  " / A[(long)i * lda + i]; }",
+                                  lambda o: tja.test_jacobi_rate_is_spectral_radius(o)),
 }
 
 
