@@ -191,8 +191,9 @@ int or_cg(int n, const double *A, long lda, const double *b, double *x,
 /*
  * The stationary Jacobi iteration x(k+1) = x(k) + D^-1 (b - A x(k)), D the
  * diagonal of A.  Every product gives the residual of the current iterate;
- * the iteration stops when ||b - A x(k)|| <= rtol ||b|| and returns that
- * x(k).  iters counts the products (the last one only tested x(k)).  A zero
+ * the iteration stops when ||b - A x(k)|| <= rtol ||b||, or after max_iter
+ * products, and returns the last iterate it measured, so the residual it
+ * reports is that iterate's true one.  iters counts the products.  A zero
  * diagonal entry is a breakdown (status 2).  res_hist (optional, length
  * max_iter + 1) receives ||b - A x(k)|| for k = 0 .. iters - 1.
  */
@@ -220,6 +221,7 @@ int or_jacobi(int n, const double *A, long lda, const double *b, double *x,
         k++;
         if (!isfinite(nr)) break;
         if (nr <= tol) { status = OR_OK; break; }
+        if (k == max_iter) break;
         for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i];
     }
 done:

@@ -64,3 +64,18 @@ def test_jacobi_divergence_breakdown_limits(oracle):
     assert oracle.jacobi(A3, np.zeros(20))["status"] == oracle.OK
     out = oracle.jacobi(A3, A3 @ inputs.solution(20, seed=1), rtol=1e-14, max_iter=3)
     assert out["status"] == oracle.NOT_CONVERGED and out["iters"] == 3
+
+
+def test_jacobi_limit_returns_measured_iterate(oracle):
+    # after max_iter products the iterate returned is the last one measured:
+    # x(2) = x(1) + D^-1 (b - A x(1)) written out for a 2 x 2 system
+    A = np.array([[4.0, 1.0], [2.0, 5.0]])
+    b = np.array([1.0, 2.0])
+    d = np.diag(A)
+    x1 = b / d
+    x2 = x1 + (b - A @ x1) / d
+    out = oracle.jacobi(A, b, rtol=1e-300, max_iter=3, history=True)
+    assert out["iters"] == 3 and out["status"] == oracle.NOT_CONVERGED
+    assert np.allclose(out["x"], x2, rtol=0, atol=1e-15)
+    assert out["rel_res"] == pytest.approx(np.linalg.norm(b - A @ x2) / np.linalg.norm(b), rel=1e-12)
+    assert out["res_hist"][-1] == pytest.approx(np.linalg.norm(b - A @ x2), rel=1e-12)
