@@ -257,6 +257,15 @@ def run_native(args):
                 "products": i3["iters"], "true_rel_res": i3["true_rel_res"],
                 "rel_err_vs_xstar": float(torch.linalg.norm(x3 - xs2) / torch.linalg.norm(xs2))}
     del x3
+    # Jacobi (the paper's stationary method) on the same nonsymmetric system:
+    # its iteration matrix I - D^-1 A has spectral radius about 1/4
+    x4 = torch.zeros(N, dtype=torch.float64, device=dev)
+    st4, i4 = B.ls_jacobi_solve(ctx, A_ns, b_ns, x4, B.make_opts(rtol=RTOL))
+    jacobi = {"status": B.ls_strerror(st4), "time_to_1e-10_ms": round(i4["time_ms"], 3),
+              "products": i4["iters"], "rel_res": i4["rel_res"],
+              "rel_err_vs_xstar": float(torch.linalg.norm(x4 - xs2) / torch.linalg.norm(xs2)),
+              "ms_per_product": round(i4["time_ms"] / max(i4["iters"], 1), 4)}
+    del x4
 
     # accuracy of the timed results (checked, not assumed)
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
@@ -362,6 +371,7 @@ def run_native(args):
             "true_rel_res": {"cg": i1["true_rel_res"], "gmres": i2["true_rel_res"]},
             "rel_err_vs_xstar": {"cg": err_cg, "gmres": err_gm},
             "bicgstab_nonsym": bicgstab,
+            "jacobi_nonsym": jacobi,
             "gemv_f64_native": gemv_native,
             "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),

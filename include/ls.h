@@ -56,6 +56,7 @@ extern "C" {
 #define LS_METHOD_CG     0
 #define LS_METHOD_GMRES  1
 #define LS_METHOD_BICGSTAB 2   /* ls_bicgstab_solve only (not in the batched engine) */
+#define LS_METHOD_JACOBI   3   /* ls_jacobi_solve only (not in the batched engine)   */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -176,6 +177,25 @@ int ls_gmres_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const doubl
  */
 int ls_bicgstab_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
                       double *x, const ls_opts *opts, ls_info *info);
+
+/*
+ * Jacobi iteration (paper: introduction, the classical stationary methods it
+ * takes from the textbooks; one of the iterative methods the library
+ * implements and times in its speed-up tables): x(k+1) = x(k) + D^-1 (b - A x(k)),
+ * D the diagonal of A.  Each step is one matrix-vector product whose
+ * epilogue forms the next iterate and ||b - A x(k)||; the iteration stops
+ * when ||b - A x(k)|| <= rtol ||b|| (status LS_OK) or after max_iter products
+ * (LS_NOT_CONVERGED; default max_iter 10 n + 10) and returns in x the last
+ * iterate whose residual it measured, so info->rel_res is that iterate's
+ * true relative residual.  info->iters counts products.  It converges when
+ * the spectral radius of I - D^-1 A is below one (e.g. A strictly
+ * diagonally dominant).  A zero diagonal entry returns LS_BREAKDOWN with x
+ * unchanged (x0, or 0) and its residual; a residual that overflows returns
+ * LS_ERR_NAN.  Arguments as for ls_cg_solve; opts->precision must be LS_F64
+ * (else LS_ERR_UNSUPPORTED); opts->f64_matvec selects the product as there.
+ */
+int ls_jacobi_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
+                    double *x, const ls_opts *opts, ls_info *info);
 
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {

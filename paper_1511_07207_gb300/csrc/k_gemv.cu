@@ -21,8 +21,9 @@
 //    epilogue to those rows and reduces the fused dot product in a fixed
 //    order, so results are deterministic for a given n;
 //  * fused epilogues: y = s, y = s with z.y, y = b - s with y.y, y = s with
-//    y.y; the last CTA runs the solver's scalar update (alpha = rho / p.q,
-//    residual norm, ...) so no extra launch is needed.
+//    y.y, and the Jacobi step y = x + D^-1 (b - s) with (b - s).(b - s);
+//    the last CTA runs the solver's scalar update (alpha = rho / p.q,
+//    residual norm and stop test, ...) so no extra launch is needed.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -311,6 +312,11 @@ __device__ __forceinline__ double epilogue(const GemvArgs &a, const MatDesc &M, 
             y[row] = r;
             return (double)r * (double)r;
         }
+        case EPI_JACOBI: {   // y is the next iterate; x and z are read at this row
+            const double r = a.b[row] - (double)s;
+            y[row] = (V)((double)static_cast<const V *>(a.x)[row] + static_cast<const double *>(a.z)[row] * r);
+            return r * r;
+        }
         default:  // EPI_NRM
             y[row] = s;
             return (double)s * (double)s;
@@ -357,6 +363,25 @@ __device__ __forceinline__ void run_finaliser(const GemvArgs &a, double dot) {
                 st->alpha = st->rho / dot;
             }
             break;
+        case FIN_JACOBI: {
+            // the residual of the iterate that was just multiplied; the next
+            // iterate is already in y, taken (or not) by the next kernel
+            const double rn = sqrt(dot);
+            st->rnorm = rn;
+            st->true_rnorm = rn;
+            int stop = 1;
+            if (st->status == LS_BREAKDOWN) {
+                // zero diagonal entry: this product only measured x
+            } else {
+                st->iter++;
+                if (!isfinite(dot)) set_err(st, ERRB_NAN);
+                else if (rn <= st->tol_abs) st->status = LS_OK;
+                else if (st->iter >= st->max_iter) st->status = LS_NOT_CONVERGED;
+                else stop = 0;
+            }
+            st->skip = stop;
+            break;
+        }
         default:
             st->dot = dot;
             break;

@@ -31,6 +31,13 @@
 //                thread applies the old rotations to column k, forms the new
 //                one, updates g and tests |g_{k+1}| <= rtol ||b||;
 //     gm_finish  back-solve R y = g (one warp), x += V_k y.
+//   Jacobi (paper, introduction: the classical stationary methods, taken from
+//   the textbooks): x(k+1) = x(k) + D^-1 (b - A x(k)).  The step itself is the
+//   GEMV's epilogue (next iterate into a second vector, ||b - A x(k)||^2
+//   reduced, stop test in its last CTA); around it:
+//     ja_diag    D^-1 from the FP64 diagonal of A, breakdown on a zero entry;
+//     ja_init    x = 0 (or keep x0), ||b||, the tolerance, the loop condition;
+//     ja_next    take the next iterate unless the GEMV's test stopped the loop.
 //
 // Cooperative kernels (launched with the cooperative attribute, grid =
 // co-resident blocks) meet at a bounded grid barrier; every cross-block sum
@@ -690,6 +697,89 @@ __global__ void __launch_bounds__(KB) bs_check_kernel(Vecs v, cudaGraphCondition
     }
 }
 
+// ============================================================================
+// Jacobi
+// ============================================================================
+// dinv = 1 / a_ii from the FP64 matrix (before the loop, outside the graph,
+// since A may be borrowed per call); a zero a_ii marks the solve a breakdown.
+__global__ void __launch_bounds__(KB) ja_diag_kernel(int n, const double *__restrict__ A, long long lda,
+                                                     double *__restrict__ dinv, State *st) {
+    count_launch(st);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double d = A[i * lda + i];
+        if (d == 0.0) {
+            st->status = LS_BREAKDOWN;   // every writer writes the same value
+            dinv[i] = 0.0;
+        } else {
+            dinv[i] = 1.0 / d;
+        }
+    }
+}
+
+// x = 0 unless x0 was given; ||b|| and the tolerance; b = 0 ends the solve
+// with x = 0 (unless the diagonal broke down first).  v.q holds the next
+// iterate, v.p holds D^-1.
+__global__ void __launch_bounds__(KB) ja_init_kernel(Vecs v, int x0_given,
+                                                     cudaGraphConditionalHandle h_loop) {
+    __shared__ double red[KB / 32];
+    State *st = v.st;
+    count_launch(st);
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    double bb = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double bi = v.b[i];
+        if (!x0_given) v.x[i] = 0.0;
+        bb += bi * bi;
+    }
+    bb = block_sum(bb, red);
+    publish(v.part, 0, bb);
+    if (!grid_sync(v.bar, st)) return;
+    __shared__ double b2_s;
+    if (threadIdx.x < 32) {
+        const double t = reduce_slot(v.part, 0, gridDim.x);
+        if (threadIdx.x == 0) b2_s = t;
+    }
+    __syncthreads();
+    const bool broke = *(volatile int *)&st->status == LS_BREAKDOWN;
+    const double b2 = b2_s;
+    if (b2 == 0.0 && !broke && x0_given)
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) v.x[i] = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double bn = sqrt(b2);
+        st->bnorm = bn;
+        st->tol_abs = v.rtol * bn;
+        st->skip = 0;
+        int go = 1;
+        if (!isfinite(b2)) {
+            set_err(st, ERRB_NAN);
+            go = 0;
+        } else if (broke) {
+            go = 1;                  // one product measures the residual of x
+        } else if (bn == 0.0) {
+            st->status = LS_OK;
+            st->rnorm = st->true_rnorm = 0.0;
+            go = 0;
+        }
+        set_cond(st, h_loop, go);
+    }
+}
+
+// After the Jacobi GEMV: x = x_next unless its last CTA stopped the loop
+// (then x keeps the iterate whose residual was measured).
+__global__ void __launch_bounds__(KB) ja_next_kernel(Vecs v, cudaGraphConditionalHandle h_loop) {
+    State *st = v.st;
+    count_launch(st);
+    const int stop = *(volatile int *)&st->skip || st->err;
+    if (!stop) {
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < v.n;
+             i += (long long)gridDim.x * blockDim.x)
+            v.x[i] = v.q[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(st, h_loop, stop ? 0u : 1u);
+}
+
 KrylovKernels krylov_kernels(int num_sms) {
     KrylovKernels K{};
     K.cg_init = reinterpret_cast<void *>(&cg_init_kernel);
@@ -703,6 +793,9 @@ KrylovKernels krylov_kernels(int num_sms) {
     K.gm_start = reinterpret_cast<void *>(&gm_start_kernel);
     K.gm_arnoldi = reinterpret_cast<void *>(&gm_arnoldi_kernel);
     K.gm_finish = reinterpret_cast<void *>(&gm_finish_kernel);
+    K.ja_diag = reinterpret_cast<void *>(&ja_diag_kernel);
+    K.ja_init = reinterpret_cast<void *>(&ja_init_kernel);
+    K.ja_next = reinterpret_cast<void *>(&ja_next_kernel);
     K.block = KB;
     K.coop_grid = num_sms;   // one block per SM: always co-resident
     return K;

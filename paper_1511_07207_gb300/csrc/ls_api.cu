@@ -50,6 +50,7 @@ int ws_reserve(ls_ctx *c, size_t bytes) {
     c->graph_gm.reset();
     c->graph_mx.reset();
     c->graph_bs.reset();
+    c->graph_ja.reset();
     cudaError_t e = cudaMalloc(&c->ws, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -290,6 +291,7 @@ extern "C" int ls_destroy(ls_ctx *c) {
     c->graph_gm.reset();
     c->graph_mx.reset();
     c->graph_bs.reset();
+    c->graph_ja.reset();
     extra_destroy(c);
     if (c->ws && !c->ws_user) cudaFree(c->ws);
     if (c->fixed) cudaFree(c->fixed);
@@ -311,6 +313,7 @@ extern "C" int ls_set_workspace(ls_ctx *c, void *ptr, size_t bytes) {
     c->graph_gm.reset();
     c->graph_mx.reset();
     c->graph_bs.reset();
+    c->graph_ja.reset();
     c->ws = static_cast<char *>(ptr);
     c->ws_bytes = ptr ? bytes : 0;
     c->ws_user = ptr != nullptr;
@@ -508,6 +511,40 @@ static int build_bicgstab_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, i
     return finish_graph(c, c->graph_bs, R, key);
 }
 
+// Builds: ja_init, while(loop){ Jacobi GEMV (next iterate, ||b - A x||, stop test), ja_next }
+static int build_jacobi_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
+                              const long long *key) {
+    Root R;
+    if (!R.create()) return LS_ERR_CUDA;
+    cudaGraphConditionalHandle hl;
+    if (!R.handle(&hl)) {
+        R.discard();
+        return LS_ERR_CUDA;
+    }
+    Chain top = R.chain();
+    {
+        Vecs vv = v;
+        int x0 = x0_given;
+        void *args[] = {&vv, &x0, &hl};
+        top.kernel(c->K.ja_init, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    Chain loop = top.loop(hl);
+    {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.q; a.b = v.b; a.z = v.p; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_JACOBI; a.fin = FIN_JACOBI;
+        gemv_node(loop, L, c->dA, a);
+        Vecs vv = v;
+        void *args[] = {&vv, &hl};
+        loop.kernel(c->K.ja_next, c->K.coop_grid, c->K.block, 0, args, false);
+    }
+    if (top.err != cudaSuccess || loop.err != cudaSuccess) {
+        R.discard();
+        return LS_ERR_CUDA;
+    }
+    return finish_graph(c, c->graph_ja, R, key);
+}
+
 // Builds: gm_init, while(outer){ resid GEMV, gm_start, while(inner){GEMV, arnoldi}, gm_finish }
 static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
                              const long long *key) {
@@ -606,15 +643,28 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     GemvLaunch GL = gemv_plan(dt, hd->use_tma != 0, EPI_DOT, c->num_sms);
     long long key[8] = {method, n, (long long)(uintptr_t)c->ws, L.ldv, o.x0_given, hd->use_tma,
                         (long long)(uintptr_t)c->stream, dt};
-    GraphCache &gc = method == LS_METHOD_CG ? c->graph_cg : method == LS_METHOD_BICGSTAB ? c->graph_bs
-                                                                                        : c->graph_gm;
+    GraphCache &gc = method == LS_METHOD_CG         ? c->graph_cg
+                     : method == LS_METHOD_BICGSTAB ? c->graph_bs
+                     : method == LS_METHOD_JACOBI   ? c->graph_ja
+                                                    : c->graph_gm;
     if (!gc.matches(key)) {
         rc = method == LS_METHOD_CG         ? build_cg_graph(c, v, GL, o.x0_given, key)
              : method == LS_METHOD_BICGSTAB ? build_bicgstab_graph(c, v, GL, o.x0_given, key)
+             : method == LS_METHOD_JACOBI   ? build_jacobi_graph(c, v, GL, o.x0_given, key)
                                             : build_gmres_graph(c, v, GL, o.x0_given, key);
         if (rc) return rc;
     }
     cudaError_t e = cudaEventRecord(c->ev0, c->stream);
+    if (e == cudaSuccess && method == LS_METHOD_JACOBI) {   // D^-1 into v.p (A may be borrowed per call)
+        int nn = n;
+        long long la = ldad;
+        const double *Ap = Ad;
+        double *dv = v.p;
+        State *stp = c->st;
+        void *args[] = {&nn, &Ap, &la, &dv, &stp};
+        const int g = std::min((n + c->K.block - 1) / c->K.block, 4 * c->num_sms);
+        e = cudaLaunchKernel(c->K.ja_diag, dim3(g), dim3(c->K.block), args, 0, c->stream);
+    }
     // the FP32 pair of A: one pass over A, timed as part of the solve
     if (e == cudaSuccess && split) e = split_f64_launch(n, n, Ad, ldad, L.Ahi, L.Alo, L.ld32, c->num_sms, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
@@ -637,7 +687,9 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     // matrix passes: method products + true-residual checks (+ the x0 residual)
     double passes;
     State sc = s;
-    if (method == LS_METHOD_CG || method == LS_METHOD_BICGSTAB) {
+    if (method == LS_METHOD_JACOBI) {
+        passes = s.iter + (s.status == LS_BREAKDOWN ? 1 : 0);
+    } else if (method == LS_METHOD_CG || method == LS_METHOD_BICGSTAB) {
         passes = s.iter + s.cycles + (o.x0_given ? 1 : 0);
     } else {
         passes = s.total + s.cycles + 1;
@@ -664,6 +716,12 @@ extern "C" int ls_bicgstab_solve(ls_ctx *c, int n, const double *A, int64_t lda,
                                  double *x, const ls_opts *opts, ls_info *info) {
     if (opts && opts->precision != LS_F64) return LS_ERR_UNSUPPORTED;
     return krylov_f64(c, LS_METHOD_BICGSTAB, n, A, lda, b, x, opts, info);
+}
+
+extern "C" int ls_jacobi_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b,
+                               double *x, const ls_opts *opts, ls_info *info) {
+    if (opts && opts->precision != LS_F64) return LS_ERR_UNSUPPORTED;
+    return krylov_f64(c, LS_METHOD_JACOBI, n, A, lda, b, x, opts, info);
 }
 
 extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const ls_opts *opts,

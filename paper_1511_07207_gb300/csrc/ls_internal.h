@@ -111,6 +111,7 @@ enum : int {
     EPI_DOT = 1,        // y_i = s_i; dot += z_i y_i
     EPI_RESID = 2,      // y_i = b_i - s_i; dot += y_i^2
     EPI_NRM = 3,        // y_i = s_i; dot += y_i^2
+    EPI_JACOBI = 4,     // r_i = b_i - s_i; y_i = x_i + z_i r_i (z = D^-1); dot += r_i^2
 };
 // finalisers run by the last CTA on the reduced dot
 enum : int {
@@ -121,6 +122,7 @@ enum : int {
     FIN_INNER_ALPHA = 4,// in_pq = dot; in_alpha = in_rho / in_pq (inner stop on breakdown)
     FIN_FCG_D = 5,      // pq = dot (p.Ap of the outer direction)
     FIN_BS_ALPHA = 6,   // BiCGSTAB: pq = r^.v; alpha = rho / pq; breakdown if pq = 0
+    FIN_JACOBI = 7,     // rnorm = ||b - A x||; iter++; stop test -> skip
 };
 
 struct GemvArgs {
@@ -130,8 +132,8 @@ struct GemvArgs {
     long long kstride;   // (elements) -- lets one graph node walk a stored basis
     int kyoff;           // GMRES: 1 (w = A v_k goes to column k+1); FCG: 0
     int z_is_x;          // EPI_DOT with z = x (after the k offset)
-    const double *b;     // EPI_RESID
-    const void *z;       // EPI_DOT
+    const double *b;     // EPI_RESID, EPI_JACOBI
+    const void *z;       // EPI_DOT; EPI_JACOBI: 1 / a_ii
     double *dot_out;     // optional copy of the final dot
     State *st;
     GemvScratch *scr;
@@ -205,6 +207,7 @@ MixedKernels mixed_kernels();
 struct KrylovKernels {
     void *cg_init, *cg_update, *cg_check;
     void *bs_init, *bs_s, *bs_update, *bs_check;
+    void *ja_diag, *ja_init, *ja_next;
     void *gm_init, *gm_start, *gm_arnoldi, *gm_finish;
     int coop_grid;       // blocks of the cooperative vector kernels
     int block;           // threads per block
