@@ -77,6 +77,7 @@ class Oracle:
         lib.or_gmres.argtypes = [i, P, l, P, P, i, d, i, i, i, P, P, P, P, P, P, P]
         lib.or_bicgstab.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P, P, P, P]
         lib.or_jacobi.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P]
+        lib.or_gauss_seidel.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P]
         lib.or_ge_solve.argtypes = [i, P, l, P, P]
         for name in ("or_bf16_round", "or_e4m3_round"):
             getattr(lib, name).argtypes = [d]
@@ -134,6 +135,13 @@ class Oracle:
 
     def jacobi(self, A, b, rtol=1e-10, max_iter=None, x0=None, nthreads=1, history=False):
         """Jacobi iteration.  Returns dict(x, status, iters, rel_res[, res_hist])."""
+        return self._stationary(self.lib.or_jacobi, A, b, rtol, max_iter, x0, nthreads, history)
+
+    def gauss_seidel(self, A, b, rtol=1e-10, max_iter=None, x0=None, nthreads=1, history=False):
+        """Forward Gauss-Seidel.  Returns dict(x, status, iters, rel_res[, res_hist])."""
+        return self._stationary(self.lib.or_gauss_seidel, A, b, rtol, max_iter, x0, nthreads, history)
+
+    def _stationary(self, fn, A, b, rtol, max_iter, x0, nthreads, history):
         A = _mat(A)
         n = A.shape[0]
         b = _vec(b, n)
@@ -141,8 +149,8 @@ class Oracle:
         x = np.zeros(n) if x0 is None else _vec(x0, n).copy()
         it, rr = ctypes.c_int(0), ctypes.c_double(0)
         rh = np.zeros(max_iter + 1) if history else None
-        st = self.lib.or_jacobi(n, _p(A), n, _p(b), _p(x), rtol, max_iter, int(x0 is not None),
-                                nthreads, ctypes.byref(it), ctypes.byref(rr), _p(rh))
+        st = fn(n, _p(A), n, _p(b), _p(x), rtol, max_iter, int(x0 is not None),
+                nthreads, ctypes.byref(it), ctypes.byref(rr), _p(rh))
         out = dict(x=x, status=st, iters=it.value, rel_res=rr.value)
         if history:
             out.update(res_hist=rh[: it.value])

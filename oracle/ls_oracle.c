@@ -20,6 +20,8 @@
  *     standard one from Saad's book, which the paper cites for GMRES.
  *   - Jacobi: same section, first paragraph (the stationary methods, which
  *     the paper takes from the textbooks): x(k+1) = x(k) + D^-1 (b - A x(k)).
+ *   - Gauss-Seidel: same passage; the forward sweep in place, each x_i
+ *     recomputed from the newest values of the others.
  *   - BiCGSTAB: same section, BiCGSTAB listing, with the steps the listing
  *     leaves out written in (see or_bicgstab).
  *   - Gaussian elimination with partial pivoting: same section,
@@ -223,6 +225,57 @@ int or_jacobi(int n, const double *A, long lda, const double *b, double *x,
         if (nr <= tol) { status = OR_OK; break; }
         if (k == max_iter) break;
         for (int i = 0; i < n; i++) x[i] += r[i] / A[(long)i * lda + i];
+    }
+done:
+    residual(n, A, lda, b, x, r, nthreads);
+    *rel_res_out = nb > 0.0 ? nrm2(n, r) / nb : 0.0;
+    *iters_out = k;
+    free(r);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gauss-Seidel, FP64                                                  */
+/* ------------------------------------------------------------------ */
+/*
+ * The forward Gauss-Seidel sweep: for i = 0 .. n-1 in turn,
+ *   x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii,
+ * with x_j already updated in this sweep for j < i and not yet for j > i.
+ * The stopping rule, the iterate returned, iters, the breakdown on a zero
+ * a_ii and res_hist are those of or_jacobi.
+ */
+int or_gauss_seidel(int n, const double *A, long lda, const double *b, double *x,
+                    double rtol, int max_iter, int x0_given, int nthreads,
+                    int *iters_out, double *rel_res_out, double *res_hist) {
+    if (n < 0 || lda < n || max_iter < 0) return OR_ERR_ARG;
+    const size_t sz = sizeof(double) * (n ? n : 1);
+    double *r = malloc(sz);
+    int status = OR_NOT_CONVERGED, k = 0;
+    const double nb = nrm2(n, b), tol = rtol * nrm2(n, b);
+    if (!x0_given)
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+    for (int i = 0; i < n; i++)
+        if (A[(long)i * lda + i] == 0.0) { status = OR_BREAKDOWN; goto done; }
+    if (nb == 0.0) {
+        for (int i = 0; i < n; i++) x[i] = 0.0;
+        status = OR_OK;
+        goto done;
+    }
+    while (k < max_iter) {
+        residual(n, A, lda, b, x, r, nthreads);          /* r = b - A x(k) */
+        const double nr = nrm2(n, r);
+        if (res_hist) res_hist[k] = nr;
+        k++;
+        if (!isfinite(nr)) break;
+        if (nr <= tol) { status = OR_OK; break; }
+        if (k == max_iter) break;
+        for (int i = 0; i < n; i++) {                    /* the sweep, in place */
+            const double *a = A + (long)i * lda;
+            double s = b[i];
+            for (int j = 0; j < n; j++)
+                if (j != i) s -= a[j] * x[j];
+            x[i] = s / a[i];
+        }
     }
 done:
     residual(n, A, lda, b, x, r, nthreads);

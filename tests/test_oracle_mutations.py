@@ -13,6 +13,7 @@ import oracle as oracle_pkg
 import test_oracle_bicgstab as tbs
 import test_oracle_cg as tcg
 import test_oracle_ge_quant as tgq
+import test_oracle_gauss_seidel as tgs
 import test_oracle_gmres as tgm
 import test_oracle_jacobi as tja
 import test_oracle_mixed as tmx
@@ -70,6 +71,13 @@ MUTATIONS = {
                                   " for (int q = i + 1; q < n; q++) r[q] -= A[(long)q * lda + i] * r[i]"
                                   " / A[(long)i * lda + i]; }",
                                   lambda o: tja.test_jacobi_rate_is_spectral_radius(o)),
+    "gs_backward_sweep": ("for (int i = 0; i < n; i++) {                    /* the sweep, in place */",
+                          "for (int i = n - 1; i >= 0; i--) {                    /* the sweep, in place */",
+                          lambda o: tgs.test_gs_lower_triangular_is_forward_substitution(o)),
+    "gs_drops_upper_part": ("if (j != i) s -= a[j] * x[j];", "if (j < i) s -= a[j] * x[j];",
+                            lambda o: tgs.test_gs_matches_lapack(o, 40)),
+    "gs_rhs_perturbed": ("            double s = b[i];\n", "            double s = b[i] * (1.0 + 1e-9);\n",
+                         lambda o: tgs.test_gs_matches_lapack(o, 200)),
 }
 
 
