@@ -266,6 +266,15 @@ def run_native(args):
               "rel_err_vs_xstar": float(torch.linalg.norm(x4 - xs2) / torch.linalg.norm(xs2)),
               "ms_per_product": round(i4["time_ms"] / max(i4["iters"], 1), 4)}
     del x4
+    # forward Gauss-Seidel on the same system: a residual product and a
+    # blocked triangular solve over the lower half of A per sweep
+    x5 = torch.zeros(N, dtype=torch.float64, device=dev)
+    st5, i5 = B.ls_gauss_seidel_solve(ctx, A_ns, b_ns, x5, B.make_opts(rtol=RTOL))
+    gauss_seidel = {"status": B.ls_strerror(st5), "time_to_1e-10_ms": round(i5["time_ms"], 3),
+                    "residual_tests": i5["iters"], "rel_res": i5["rel_res"],
+                    "rel_err_vs_xstar": float(torch.linalg.norm(x5 - xs2) / torch.linalg.norm(xs2)),
+                    "A_passes": round(i5["bytes_moved"] / (8.0 * N * N), 1)}
+    del x5
 
     # accuracy of the timed results (checked, not assumed)
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
@@ -372,6 +381,7 @@ def run_native(args):
             "rel_err_vs_xstar": {"cg": err_cg, "gmres": err_gm},
             "bicgstab_nonsym": bicgstab,
             "jacobi_nonsym": jacobi,
+            "gauss_seidel_nonsym": gauss_seidel,
             "gemv_f64_native": gemv_native,
             "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),

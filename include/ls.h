@@ -57,6 +57,7 @@ extern "C" {
 #define LS_METHOD_GMRES  1
 #define LS_METHOD_BICGSTAB 2   /* ls_bicgstab_solve only (not in the batched engine) */
 #define LS_METHOD_JACOBI   3   /* ls_jacobi_solve only (not in the batched engine)   */
+#define LS_METHOD_GAUSS_SEIDEL 4   /* ls_gauss_seidel_solve only (not in the batched engine) */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -196,6 +197,24 @@ int ls_bicgstab_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const do
  */
 int ls_jacobi_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
                     double *x, const ls_opts *opts, ls_info *info);
+
+/*
+ * Forward Gauss-Seidel (paper: the same passage as Jacobi): each sweep
+ * recomputes x_0, x_1, ... in turn from the newest values of the others,
+ * i.e. (D + L) x(k+1) = b - U x(k) with D + L the lower triangle of A
+ * including the diagonal and U the strict upper triangle.  The device runs
+ * it as a correction: r = b - A x(k) (one product, whose norm is the stop
+ * test), then the triangular solve (D + L) d = r over row blocks of 64 and
+ * x(k+1) = x(k) + d, so a sweep streams A once and its lower half once more.
+ * Stopping rule, the iterate returned, info->iters (residual evaluations),
+ * the breakdown on a zero diagonal entry and the errors are those of
+ * ls_jacobi_solve.  It converges for every SPD A and for strictly
+ * diagonally dominant A.  Arguments as for ls_cg_solve; opts->precision must
+ * be LS_F64; opts->f64_matvec selects the residual product's kernel (the
+ * sweep always reads the FP32 pair of A, formed once per solve).
+ */
+int ls_gauss_seidel_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
+                          double *x, const ls_opts *opts, ls_info *info);
 
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {

@@ -17,7 +17,7 @@ from . import build as _build
 LS_OK, LS_NOT_CONVERGED, LS_BREAKDOWN = 0, 1, 2
 LS_ERR_ARG, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT = -1, -2, -3, -4
 LS_ERR_BUSY, LS_ERR_NAN, LS_ERR_UNSUPPORTED = -5, -6, -7
-LS_METHOD_CG, LS_METHOD_GMRES, LS_METHOD_BICGSTAB, LS_METHOD_JACOBI = 0, 1, 2, 3
+LS_METHOD_CG, LS_METHOD_GMRES, LS_METHOD_BICGSTAB, LS_METHOD_JACOBI, LS_METHOD_GAUSS_SEIDEL = 0, 1, 2, 3, 4
 LS_F64, LS_BF16_IR, LS_FP8_IR, LS_F32_IR = 0, 1, 2, 3
 LS_F64_PAIR = 4
 LS_REFINE_FCG, LS_REFINE_IR = 0, 1
@@ -27,7 +27,7 @@ LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 8192, 32
 # every symbol declared in include/ls.h
 ABI_FUNCTIONS = (
     "ls_opts_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_set_workspace",
-    "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_batch_solve", "ls_server_start", "ls_server_submit",
+    "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_gauss_seidel_solve", "ls_batch_solve", "ls_server_start", "ls_server_submit",
     "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
     "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror",
 )
@@ -90,7 +90,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.ls_workspace_size.argtypes = [P, I, I, I, ctypes.POINTER(ls_opts), I,
                                           ctypes.POINTER(ctypes.c_size_t)]
         lib.ls_set_workspace.argtypes = [P, P, ctypes.c_size_t]
-        for fn in (lib.ls_cg_solve, lib.ls_gmres_solve, lib.ls_bicgstab_solve, lib.ls_jacobi_solve):
+        for fn in (lib.ls_cg_solve, lib.ls_gmres_solve, lib.ls_bicgstab_solve, lib.ls_jacobi_solve,
+               lib.ls_gauss_seidel_solve):
             fn.argtypes = [P, I, P, I64, P, P, ctypes.POINTER(ls_opts), ctypes.POINTER(ls_info)]
         lib.ls_batch_solve.argtypes = [P, I, ctypes.POINTER(ls_system), ctypes.POINTER(ls_info)]
         lib.ls_server_start.argtypes = [P, ctypes.POINTER(ls_server_cfg), ctypes.POINTER(P)]
@@ -248,6 +249,11 @@ def ls_bicgstab_solve(ctx, A, b, x, opts=None):
 def ls_jacobi_solve(ctx, A, b, x, opts=None):
     """Jacobi iteration on A x = b; see ls_cg_solve."""
     return _solve(load().ls_jacobi_solve, ctx, A, b, x, opts)
+
+
+def ls_gauss_seidel_solve(ctx, A, b, x, opts=None):
+    """Forward Gauss-Seidel on A x = b; see ls_cg_solve."""
+    return _solve(load().ls_gauss_seidel_solve, ctx, A, b, x, opts)
 
 
 def ls_gemv(ctx, dtype, A, x, y, scale=None):

@@ -51,6 +51,7 @@ int ws_reserve(ls_ctx *c, size_t bytes) {
     c->graph_mx.reset();
     c->graph_bs.reset();
     c->graph_ja.reset();
+    c->graph_gs.reset();
     cudaError_t e = cudaMalloc(&c->ws, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -292,6 +293,7 @@ extern "C" int ls_destroy(ls_ctx *c) {
     c->graph_mx.reset();
     c->graph_bs.reset();
     c->graph_ja.reset();
+    c->graph_gs.reset();
     extra_destroy(c);
     if (c->ws && !c->ws_user) cudaFree(c->ws);
     if (c->fixed) cudaFree(c->fixed);
@@ -314,6 +316,7 @@ extern "C" int ls_set_workspace(ls_ctx *c, void *ptr, size_t bytes) {
     c->graph_mx.reset();
     c->graph_bs.reset();
     c->graph_ja.reset();
+    c->graph_gs.reset();
     c->ws = static_cast<char *>(ptr);
     c->ws_bytes = ptr ? bytes : 0;
     c->ws_user = ptr != nullptr;
@@ -331,11 +334,14 @@ struct F64Layout {
     double *x, *b, *r, *p, *q, *V, *Astage;
     double *rh, *vv, *s, *t;   // BiCGSTAB
     float *Ahi, *Alo;    // the FP32 pair of A (double-single products)
+    float *Thi, *Tlo;    // Gauss-Seidel: inverses of the 64 x 64 diagonal blocks (FP32 pairs)
+    unsigned *gflags;    // Gauss-Seidel: 2 x nblk publication flags
     long long npad, ldv, lda_stage, ld32;
+    int nblk;
     size_t bytes;
 };
 
-F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA, bool split) {
+F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA, bool split, bool gs) {
     F64Layout L{};
     L.npad = (long long)align_up((size_t)std::max(n, 1), 64);
     L.ldv = L.npad;
@@ -351,10 +357,16 @@ F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA, bool spl
     L.vv = cv.take<double>(L.npad);
     L.s = cv.take<double>(L.npad);
     L.t = cv.take<double>(L.npad);
-    L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
     L.ld32 = (long long)align_up((size_t)std::max(n, 1), 4);
     L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
     L.Alo = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
+    L.nblk = (std::max(n, 1) + 63) / 64;
+    L.Thi = gs ? cv.take<float>((size_t)L.nblk * 64 * 64) : nullptr;
+    L.Tlo = gs ? cv.take<float>((size_t)L.nblk * 64 * 64) : nullptr;
+    L.gflags = gs ? cv.take<unsigned>((size_t)2 * L.nblk) : nullptr;
+    // last, so that every pointer a cached graph holds is the same whether
+    // A is staged or borrowed
+    L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
     L.bytes = align_up(cv.off, 256);
     return L;
 }
@@ -545,6 +557,54 @@ static int build_jacobi_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int
     return finish_graph(c, c->graph_ja, R, key);
 }
 
+// Builds: ja_init, while(loop){ resid GEMV (||b - A x||, stop test), gs_trsv ((D + L) d = r, x += d) }
+static int build_gs_graph(ls_ctx *c, const Vecs &v, const F64Layout &L, const GemvLaunch &GL, int x0_given,
+                          const long long *key) {
+    Root R;
+    if (!R.create()) return LS_ERR_CUDA;
+    cudaGraphConditionalHandle hl;
+    if (!R.handle(&hl)) {
+        R.discard();
+        return LS_ERR_CUDA;
+    }
+    Chain top = R.chain();
+    {
+        Vecs vv = v;
+        int x0 = x0_given;
+        void *args[] = {&vv, &x0, &hl};
+        top.kernel(c->K.ja_init, c->K.coop_grid, c->K.block, 0, args, true);
+    }
+    Chain loop = top.loop(hl);
+    {
+        GemvArgs a{};
+        a.x = v.x; a.y = v.r; a.b = v.b; a.st = v.st; a.scr = c->scr;
+        a.epi = EPI_RESID; a.fin = FIN_JACOBI;
+        gemv_node(loop, GL, c->dA, a);
+        GsArgs g{};
+        g.n = v.n;
+        g.r = v.r;
+        g.x = v.x;
+        g.delta = v.p;
+        g.u = v.q;
+        g.Ahi = L.Ahi;
+        g.Alo = L.Alo;
+        g.ld = L.ld32;
+        g.Thi = L.Thi;
+        g.Tlo = L.Tlo;
+        g.flagD = L.gflags;
+        g.flagU = L.gflags + L.nblk;
+        g.st = v.st;
+        const GsKernels G = gs_kernels();
+        void *args[] = {&g, &hl};
+        loop.kernel(G.trsv, c->K.coop_grid, G.trsv_block, 0, args, true);
+    }
+    if (top.err != cudaSuccess || loop.err != cudaSuccess) {
+        R.discard();
+        return LS_ERR_CUDA;
+    }
+    return finish_graph(c, c->graph_gs, R, key);
+}
+
 // Builds: gm_init, while(outer){ resid GEMV, gm_start, while(inner){GEMV, arnoldi}, gm_finish }
 static int build_gmres_graph(ls_ctx *c, const Vecs &v, const GemvLaunch &L, int x0_given,
                              const long long *key) {
@@ -614,10 +674,12 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     const int max_iter = o.max_iter > 0 ? o.max_iter : 10 * n + 10;
     const bool a_dev = is_device_ptr(A);
     const bool split = o.f64_matvec == 0;
-    F64Layout L = f64_layout(nullptr, n, m, method == LS_METHOD_GMRES, !a_dev, split);
+    const bool gs = method == LS_METHOD_GAUSS_SEIDEL;
+    const bool pair = split || gs;     // the Gauss-Seidel sweep reads the pair whatever the GEMV
+    F64Layout L = f64_layout(nullptr, n, m, method == LS_METHOD_GMRES, !a_dev, pair, gs);
     rc = ws_reserve(c, L.bytes);
     if (rc) return rc;
-    L = f64_layout(c->ws, n, m, method == LS_METHOD_GMRES, !a_dev, split);
+    L = f64_layout(c->ws, n, m, method == LS_METHOD_GMRES, !a_dev, pair, gs);
 
     // stage inputs
     const double *Ad;
@@ -646,11 +708,13 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     GraphCache &gc = method == LS_METHOD_CG         ? c->graph_cg
                      : method == LS_METHOD_BICGSTAB ? c->graph_bs
                      : method == LS_METHOD_JACOBI   ? c->graph_ja
+                     : gs                           ? c->graph_gs
                                                     : c->graph_gm;
     if (!gc.matches(key)) {
         rc = method == LS_METHOD_CG         ? build_cg_graph(c, v, GL, o.x0_given, key)
              : method == LS_METHOD_BICGSTAB ? build_bicgstab_graph(c, v, GL, o.x0_given, key)
              : method == LS_METHOD_JACOBI   ? build_jacobi_graph(c, v, GL, o.x0_given, key)
+             : gs                           ? build_gs_graph(c, v, L, GL, o.x0_given, key)
                                             : build_gmres_graph(c, v, GL, o.x0_given, key);
         if (rc) return rc;
     }
@@ -665,8 +729,20 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
         const int g = std::min((n + c->K.block - 1) / c->K.block, 4 * c->num_sms);
         e = cudaLaunchKernel(c->K.ja_diag, dim3(g), dim3(c->K.block), args, 0, c->stream);
     }
+    if (e == cudaSuccess && gs) {   // flags zeroed; T_I^-1 of the diagonal blocks (A may be borrowed per call)
+        e = cudaMemsetAsync(L.gflags, 0, sizeof(unsigned) * 2 * L.nblk, c->stream);
+        const GsKernels G = gs_kernels();
+        int nn = n;
+        long long la = ldad;
+        const double *Ap = Ad;
+        float *th = L.Thi, *tl = L.Tlo;
+        State *stp = c->st;
+        void *args[] = {&nn, &Ap, &la, &th, &tl, &stp};
+        const int g = std::min(L.nblk, 8 * c->num_sms);
+        if (e == cudaSuccess) e = cudaLaunchKernel(G.tinv, dim3(g), dim3(G.tinv_block), args, 0, c->stream);
+    }
     // the FP32 pair of A: one pass over A, timed as part of the solve
-    if (e == cudaSuccess && split) e = split_f64_launch(n, n, Ad, ldad, L.Ahi, L.Alo, L.ld32, c->num_sms, c->stream);
+    if (e == cudaSuccess && pair) e = split_f64_launch(n, n, Ad, ldad, L.Ahi, L.Alo, L.ld32, c->num_sms, c->stream);
     if (e != cudaSuccess) return map_cuda(e);
     rc = launch_cached(c, gc);
     if (rc) return rc;
@@ -689,6 +765,8 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     State sc = s;
     if (method == LS_METHOD_JACOBI) {
         passes = s.iter + (s.status == LS_BREAKDOWN ? 1 : 0);
+    } else if (gs) {   // a residual GEMV per test, the lower half of A per sweep
+        passes = s.status == LS_BREAKDOWN ? 1.0 : s.iter + 0.5 * std::max(s.iter - 1, 0);
     } else if (method == LS_METHOD_CG || method == LS_METHOD_BICGSTAB) {
         passes = s.iter + s.cycles + (o.x0_given ? 1 : 0);
     } else {
@@ -724,6 +802,12 @@ extern "C" int ls_jacobi_solve(ls_ctx *c, int n, const double *A, int64_t lda, c
     return krylov_f64(c, LS_METHOD_JACOBI, n, A, lda, b, x, opts, info);
 }
 
+extern "C" int ls_gauss_seidel_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b,
+                                     double *x, const ls_opts *opts, ls_info *info) {
+    if (opts && opts->precision != LS_F64) return LS_ERR_UNSUPPORTED;
+    return krylov_f64(c, LS_METHOD_GAUSS_SEIDEL, n, A, lda, b, x, opts, info);
+}
+
 extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const ls_opts *opts,
                                  int a_on_device, size_t *bytes) {
     if (!c || !bytes || n < 0 || nrhs < 1) return LS_ERR_ARG;
@@ -734,7 +818,9 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
         *bytes = mixed_workspace_bytes(n, &o, a_on_device != 0);
         return LS_OK;
     }
-    *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device, o.f64_matvec == 0).bytes;
+    const bool gs = method == LS_METHOD_GAUSS_SEIDEL;
+    *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device, o.f64_matvec == 0 || gs, gs)
+                 .bytes;
     return LS_OK;
 }
 

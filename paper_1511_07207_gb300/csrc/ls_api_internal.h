@@ -49,7 +49,7 @@ struct ls_ctx {
     size_t ws_bytes = 0;
     bool ws_user = false;
     // cached executable graphs
-    lsi::GraphCache graph_cg, graph_gm, graph_mx, graph_bs, graph_ja;
+    lsi::GraphCache graph_cg, graph_gm, graph_mx, graph_bs, graph_ja, graph_gs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches_total = 0;
     lsi::Engine *batch = nullptr;

@@ -204,6 +204,24 @@ struct MixedKernels {
 MixedKernels mixed_kernels();
 
 // ---- Krylov launchers (k_krylov.cu) -----------------------------------------------
+// ---- Gauss-Seidel triangular solve (k_gs.cu) -----------------------------------------
+struct GsArgs {
+    int n;
+    const double *r;         // b - A x(k), from the residual GEMV
+    double *x;               // x(k) -> x(k+1) = x(k) + d
+    double *delta, *u;       // d, and u_I = T_I^-1 (r_I - sum_{j < I - W} A_Ij d_j)
+    const float *Ahi, *Alo;  // the FP32 pair of A, row pitch ld
+    long long ld;
+    const float *Thi, *Tlo;  // inverses of the 64 x 64 diagonal blocks, FP32 pairs
+    unsigned *flagD, *flagU; // per row block: d_I / u_I published (value = sweep number)
+    State *st;
+};
+struct GsKernels {
+    void *tinv, *trsv;
+    int tinv_block, trsv_block, blk;
+};
+GsKernels gs_kernels();
+
 struct KrylovKernels {
     void *cg_init, *cg_update, *cg_check;
     void *bs_init, *bs_s, *bs_update, *bs_check;

@@ -44,10 +44,11 @@ static MixLayout mix_layout(void *base, int n, int dtype, int m, bool fcg, bool 
     L.qf = cv.take<float>(L.npad);
     L.scale = cv.take<float>(L.npad);
     L.Q = cv.take<unsigned char>((size_t)n * L.ldq * elt_size(dtype));
-    L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
     L.ld32 = (long long)align_up((size_t)std::max(n, 1), 4);
     L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
     L.Alo = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
+    // last: no other pointer moves with whether A is staged or borrowed
+    L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
     L.bytes = align_up(cv.off, 256);
     return L;
 }

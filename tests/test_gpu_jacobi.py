@@ -44,7 +44,7 @@ def test_jacobi_matches_oracle(ctx, gpu, oracle, n):
     assert st == B.LS_OK == ref["status"]
     true_rel = np.linalg.norm(oracle.residual(A, b, x)) / np.linalg.norm(b)
     assert true_rel <= 1e-10
-    assert abs(info["rel_res"] - true_rel) <= 1e-3 * true_rel + 1e-15
+    assert abs(info["rel_res"] - true_rel) <= 1e-3 * true_rel + 1e-14   # A as the pair: 2^-48
     assert abs(info["iters"] - ref["iters"]) <= 1
     assert info["launches"] >= 2 * info["iters"]
 
