@@ -211,7 +211,8 @@ int ls_jacobi_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const doub
  * ls_jacobi_solve.  It converges for every SPD A and for strictly
  * diagonally dominant A.  Arguments as for ls_cg_solve; opts->precision must
  * be LS_F64; opts->f64_matvec selects the residual product's kernel (the
- * sweep always reads the FP32 pair of A, formed once per solve).
+ * sweep always reads the FP32 pair of A, formed once per solve).  n is at
+ * most 64 x 8 x (SMs - 1) (77,312 on GB300), else LS_ERR_UNSUPPORTED.
  */
 int ls_gauss_seidel_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
                           double *x, const ls_opts *opts, ls_info *info);

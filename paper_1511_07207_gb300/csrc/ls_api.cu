@@ -336,6 +336,8 @@ struct F64Layout {
     float *Ahi, *Alo;    // the FP32 pair of A (double-single products)
     float *Thi, *Tlo;    // Gauss-Seidel: inverses of the 64 x 64 diagonal blocks (FP32 pairs)
     unsigned *gflags;    // Gauss-Seidel: 2 x nblk publication flags
+    void *gmaps;         // Gauss-Seidel: 4 tensor maps (pair of A, pair of the T_I^-1)
+    float *gpanel;       // Gauss-Seidel: the chain CTA's M_{I,w} = T_I^-1 A_{I,I-w}, one contiguous panel
     long long npad, ldv, lda_stage, ld32;
     int nblk;
     size_t bytes;
@@ -364,6 +366,13 @@ F64Layout f64_layout(void *base, int n, int m, bool gmres, bool stageA, bool spl
     L.Thi = gs ? cv.take<float>((size_t)L.nblk * 64 * 64) : nullptr;
     L.Tlo = gs ? cv.take<float>((size_t)L.nblk * 64 * 64) : nullptr;
     L.gflags = gs ? cv.take<unsigned>((size_t)2 * L.nblk) : nullptr;
+    L.gmaps = gs ? static_cast<void *>(cv.take<CUtensorMap>(4)) : nullptr;
+    if (gs) {
+        const GsKernels G = gs_kernels();
+        L.gpanel = cv.take<float>((size_t)L.nblk * G.panel_tiles_per_block * G.panel_tile_floats);
+    } else {
+        L.gpanel = nullptr;
+    }
     // last, so that every pointer a cached graph holds is the same whether
     // A is staged or borrowed
     L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;
@@ -584,19 +593,17 @@ static int build_gs_graph(ls_ctx *c, const Vecs &v, const F64Layout &L, const Ge
         g.n = v.n;
         g.r = v.r;
         g.x = v.x;
-        g.delta = v.p;
-        g.u = v.q;
-        g.Ahi = L.Ahi;
-        g.Alo = L.Alo;
-        g.ld = L.ld32;
-        g.Thi = L.Thi;
-        g.Tlo = L.Tlo;
+        g.delta = reinterpret_cast<float2 *>(v.p);   // n FP32 pairs in an n-double vector
+        g.u = reinterpret_cast<float2 *>(v.q);
+        g.tmaps = static_cast<const CUtensorMap *>(L.gmaps);
+        g.panel = L.gpanel;
         g.flagD = L.gflags;
         g.flagU = L.gflags + L.nblk;
+        g.bar = v.bar;
         g.st = v.st;
         const GsKernels G = gs_kernels();
         void *args[] = {&g, &hl};
-        loop.kernel(G.trsv, c->K.coop_grid, G.trsv_block, 0, args, true);
+        loop.kernel(G.trsv, c->K.coop_grid, G.trsv_block, G.trsv_smem, args, true);
     }
     if (top.err != cudaSuccess || loop.err != cudaSuccess) {
         R.discard();
@@ -676,6 +683,7 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     const bool split = o.f64_matvec == 0;
     const bool gs = method == LS_METHOD_GAUSS_SEIDEL;
     const bool pair = split || gs;     // the Gauss-Seidel sweep reads the pair whatever the GEMV
+    if (gs && (n + 63) / 64 > gs_kernels().max_owned * (c->K.coop_grid - 1)) return LS_ERR_UNSUPPORTED;
     F64Layout L = f64_layout(nullptr, n, m, method == LS_METHOD_GMRES, !a_dev, pair, gs);
     rc = ws_reserve(c, L.bytes);
     if (rc) return rc;
@@ -730,7 +738,11 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
         e = cudaLaunchKernel(c->K.ja_diag, dim3(g), dim3(c->K.block), args, 0, c->stream);
     }
     if (e == cudaSuccess && gs) {   // flags zeroed; T_I^-1 of the diagonal blocks (A may be borrowed per call)
-        e = cudaMemsetAsync(L.gflags, 0, sizeof(unsigned) * 2 * L.nblk, c->stream);
+        alignas(64) CUtensorMap maps[4];
+        if (!gs_encode_maps(maps, L.Ahi, L.Alo, n, L.ld32, L.Thi, L.Tlo, L.nblk)) return LS_ERR_UNSUPPORTED;
+        e = cudaMemcpyAsync(L.gmaps, maps, sizeof(maps), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // maps is on this stack frame
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.gflags, 0, sizeof(unsigned) * 2 * L.nblk, c->stream);
         const GsKernels G = gs_kernels();
         int nn = n;
         long long la = ldad;
@@ -743,6 +755,17 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     }
     // the FP32 pair of A: one pass over A, timed as part of the solve
     if (e == cudaSuccess && pair) e = split_f64_launch(n, n, Ad, ldad, L.Ahi, L.Alo, L.ld32, c->num_sms, c->stream);
+    if (e == cudaSuccess && gs) {   // the chain's panel, from the pair and the T_I^-1
+        const GsKernels G = gs_kernels();
+        int nn = n;
+        const float *ah = L.Ahi, *al = L.Alo, *th = L.Thi, *tl = L.Tlo;
+        long long ld = L.ld32;
+        float *pn = L.gpanel;
+        State *stp = c->st;
+        void *args[] = {&nn, &ah, &al, &ld, &th, &tl, &pn, &stp};
+        const int g = std::min(L.nblk * G.panel_tiles_per_block, 8 * c->num_sms);
+        e = cudaLaunchKernel(G.panel, dim3(g), dim3(G.panel_block), args, G.panel_smem, c->stream);
+    }
     if (e != cudaSuccess) return map_cuda(e);
     rc = launch_cached(c, gc);
     if (rc) return rc;

@@ -209,18 +209,23 @@ struct GsArgs {
     int n;
     const double *r;         // b - A x(k), from the residual GEMV
     double *x;               // x(k) -> x(k+1) = x(k) + d
-    double *delta, *u;       // d, and u_I = T_I^-1 (r_I - sum_{j < I - W} A_Ij d_j)
-    const float *Ahi, *Alo;  // the FP32 pair of A, row pitch ld
-    long long ld;
-    const float *Thi, *Tlo;  // inverses of the 64 x 64 diagonal blocks, FP32 pairs
+    float2 *delta, *u;       // d, and u_I = T_I^-1 (r_I - sum_{j < I - W} A_Ij d_j), as FP32 pairs
+    const CUtensorMap *tmaps;// device: A hi, A lo (n x n), T hi, T lo (nblk*64 x 64), 32 x 64 boxes
+    const float *panel;      // the chain's tiles per block, in its read order (gs_panel_kernel)
     unsigned *flagD, *flagU; // per row block: d_I / u_I published (value = sweep number)
+    GridBar *bar;            // the final x += d waits for the whole chain
     State *st;
 };
 struct GsKernels {
-    void *tinv, *trsv;
-    int tinv_block, trsv_block, blk;
+    void *tinv, *trsv, *panel;
+    int tinv_block, trsv_block, blk, panel_block, panel_tiles_per_block, panel_tile_floats;
+    int max_owned;           // row blocks one helper CTA can own
+    size_t trsv_smem, panel_smem;
 };
 GsKernels gs_kernels();
+// The four tensor maps of GsArgs::tmaps (maps: 4 x 128 bytes, 64-byte aligned).
+bool gs_encode_maps(void *maps, const float *Ahi, const float *Alo, int n, long long ld, const float *Thi,
+                    const float *Tlo, int nblk);
 
 struct KrylovKernels {
     void *cg_init, *cg_update, *cg_check;
