@@ -683,6 +683,37 @@ def run_kernel(args):
     B.ls_destroy(ctx)
 
 
+def run_stationary(args):
+    """Jacobi or Gauss-Seidel alone (timing and ncu captures): the
+    nonsymmetric bench matrix 2I + G/(2 sqrt n) at --n, one solve with one
+    residual test and one with 1 + --reps; the difference is --reps sweeps
+    (Jacobi: the product with its fused update; Gauss-Seidel: the residual
+    product and the triangular solve)."""
+    import torch
+    from paper_1511_07207_gb300 import binding as B
+    from paper_1511_07207_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    ctx = B.ls_create(0, torch.cuda.current_stream(dev))
+    n = args.n
+    A = inputs.nonsym_matrix(n, seed=1, device=dev)
+    b = A @ torch.ones(n, dtype=torch.float64, device=dev)
+    solve = B.ls_jacobi_solve if args.method == "jacobi" else B.ls_gauss_seidel_solve
+    times = {}
+    for k in (1, 1, 1 + args.reps):     # the first solve warms the graph up
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        st, info = solve(ctx, A, b, x, B.make_opts(rtol=1e-300, max_iter=k))
+        assert st == B.LS_NOT_CONVERGED and info["iters"] == k, (st, info)
+        times[k] = info["time_ms"]
+    sweep = (times[1 + args.reps] - times[1]) / args.reps
+    byts = 8.0 * n * n + (4.0 * n * n if args.method == "gauss_seidel" else 0.0)
+    peaks, src = load_peaks()
+    print(json.dumps({"kernel": "stationary", "method": args.method, "n": n, "reps": args.reps,
+                      "setup_and_first_test_ms": round(times[1], 4), "ms_per_sweep": round(sweep, 4),
+                      "A_bytes_per_sweep": byts, "GB/s": round(byts / sweep / 1e6, 1),
+                      "hbm_frac": round(byts / sweep / 1e6 / peaks["hbm_gbs"], 4), "peak_source": src}))
+    B.ls_destroy(ctx)
+
+
 def run_batch_only(args):
     """The batched engine alone (ncu captures of its kernels): the first
     --count systems of the 512-system recipe, one ls_batch_solve."""
@@ -714,9 +745,12 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
     ap.add_argument("--cpu-cg-sample", type=int, default=600)
-    ap.add_argument("--kernel", choices=["gemv", "batch"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary"], default=None,
                     help="kernel-only timing (small cases for ncu captures): one GEMV format, "
-                         "or the batched engine alone on --count systems")
+                         "the batched engine alone on --count systems, or --reps sweeps of a "
+                         "stationary method")
+    ap.add_argument("--method", choices=["jacobi", "gauss_seidel"], default="gauss_seidel",
+                    help="--kernel stationary: which method")
     ap.add_argument("--count", type=int, default=128, help="--kernel batch: systems in the batch")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--dtype", choices=["f64", "pair", "bf16", "fp8", "f32"], default="f64")
@@ -730,6 +764,8 @@ def main():
         run_kernel(args)
     elif args.kernel == "batch":
         run_batch_only(args)
+    elif args.kernel == "stationary":
+        run_stationary(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
