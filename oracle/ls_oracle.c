@@ -22,6 +22,8 @@
  *     the paper takes from the textbooks): x(k+1) = x(k) + D^-1 (b - A x(k)).
  *   - Gauss-Seidel: same passage; the forward sweep in place, each x_i
  *     recomputed from the newest values of the others.
+ *   - Block CG: the CG paragraph's method for several right-hand sides at
+ *     once in O'Leary's block form (s x s step matrices instead of scalars).
  *   - BiCGSTAB: same section, BiCGSTAB listing, with the steps the listing
  *     leaves out written in (see or_bicgstab).
  *   - Gaussian elimination with partial pivoting: same section,
@@ -184,6 +186,148 @@ int or_cg(int n, const double *A, long lda, const double *b, double *x,
     *rel_res_out = nrm2(n, q) / nb;
     *iters_out = k;
     free(r); free(p); free(q);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Block CG (O'Leary), FP64                                            */
+/* ------------------------------------------------------------------ */
+/* Cholesky G = L L^T of an s x s SPD matrix (column-major, in place:
+ * L in the lower triangle).  0 on success, 1 if a pivot is not positive. */
+static int chol(int s, double *G) {
+    for (int j = 0; j < s; j++) {
+        double d = G[j + j * s];
+        for (int k = 0; k < j; k++) d -= G[j + k * s] * G[j + k * s];
+        if (!(d > 0.0)) return 1;
+        d = sqrt(d);
+        G[j + j * s] = d;
+        for (int i = j + 1; i < s; i++) {
+            double v = G[i + j * s];
+            for (int k = 0; k < j; k++) v -= G[i + k * s] * G[j + k * s];
+            G[i + j * s] = v / d;
+        }
+    }
+    return 0;
+}
+
+/* Y = G^-1 Y for s x s matrices, G = L L^T factored by chol. */
+static void chol_solve(int s, const double *L, double *Y) {
+    for (int c = 0; c < s; c++) {
+        double *y = Y + c * s;
+        for (int i = 0; i < s; i++) {                 /* L z = y */
+            double v = y[i];
+            for (int k = 0; k < i; k++) v -= L[i + k * s] * y[k];
+            y[i] = v / L[i + i * s];
+        }
+        for (int i = s - 1; i >= 0; i--) {            /* L^T w = z */
+            double v = y[i];
+            for (int k = i + 1; k < s; k++) v -= L[k + i * s] * y[k];
+            y[i] = v / L[i + i * s];
+        }
+    }
+}
+
+/* G = U^T V for n x s column-major blocks (s x s, column-major). */
+static void gram(int n, int s, const double *U, const double *V, double *G) {
+    for (int j = 0; j < s; j++)
+        for (int i = 0; i < s; i++) G[i + j * s] = dot(n, U + (long)i * n, V + (long)j * n);
+}
+
+/*
+ * Block conjugate gradient (O'Leary) for SPD A and s right-hand sides B
+ * (n x s, column-major), X (n x s) in/out:
+ *   R = B - A X, P = R, rho = R^T R
+ *   loop: Q = A P; gamma = P^T Q; alpha = gamma^-1 rho;
+ *         X += P alpha; R -= Q alpha; rho' = R^T R;
+ *         stop when every column has ||R_j|| <= rtol ||B_j|| (confirmed on
+ *         the true residual; a failed confirmation restarts from it);
+ *         beta = rho^-1 rho'; P = R + P beta; rho = rho'.
+ * iters counts block products.  gamma or rho not positive definite (a
+ * rank-deficient residual block: linearly dependent or zero columns of B, or
+ * columns that converged exactly) is a breakdown (status 2).  rel_res_out is
+ * the largest true relative residual over the columns.
+ */
+int or_block_cg(int n, int s, const double *A, long lda, const double *B, double *X,
+                double rtol, int max_iter, int x0_given, int nthreads,
+                int *iters_out, double *rel_res_out) {
+    if (n < 0 || s < 1 || lda < n || max_iter < 0) return OR_ERR_ARG;
+    const size_t nb = sizeof(double) * (size_t)(n ? n : 1) * s, sb = sizeof(double) * s * s;
+    double *R = malloc(nb), *P = malloc(nb), *Q = malloc(nb), *T = malloc(nb);
+    double *rho = malloc(sb), *rhon = malloc(sb), *Lr = malloc(sb), *g = malloc(sb), *al = malloc(sb);
+    double *bn = malloc(sizeof(double) * s);
+    int status = OR_NOT_CONVERGED, k = 0;
+    for (int j = 0; j < s; j++) bn[j] = nrm2(n, B + (long)j * n);
+
+    /* R = B - A X (or B), P = R, rho = R^T R and its factor */
+    #define RESTART()                                                              \
+        do {                                                                       \
+            for (int j = 0; j < s; j++)                                            \
+                residual(n, A, lda, B + (long)j * n, X + (long)j * n, R + (long)j * n, nthreads); \
+            memcpy(P, R, nb);                                                      \
+            gram(n, s, R, R, rho);                                                 \
+        } while (0)
+    if (!x0_given) memset(X, 0, nb);
+    RESTART();
+    int check = 1;
+    for (int j = 0; j < s; j++) check = check && sqrt(rho[j + j * s]) <= rtol * bn[j];
+    for (;;) {
+        if (check) {
+            int ok = 1;
+            for (int j = 0; j < s && ok; j++) {
+                residual(n, A, lda, B + (long)j * n, X + (long)j * n, T, nthreads);
+                ok = nrm2(n, T) <= rtol * bn[j];
+            }
+            if (ok) { status = OR_OK; break; }
+            RESTART();
+            check = 0;
+        }
+        if (k >= max_iter) break;
+        memcpy(Lr, rho, sb);
+        if (chol(s, Lr)) { status = OR_BREAKDOWN; break; }
+        for (int j = 0; j < s; j++) gemv(n, n, A, lda, P + (long)j * n, Q + (long)j * n, nthreads);
+        gram(n, s, P, Q, g);                                  /* gamma = P^T Q */
+        if (chol(s, g)) { status = OR_BREAKDOWN; break; }
+        memcpy(al, rho, sb);
+        chol_solve(s, g, al);                                  /* alpha = gamma^-1 rho */
+        for (int j = 0; j < s; j++)
+            for (int c = 0; c < s; c++) {
+                const double a = al[c + j * s];
+                for (int i = 0; i < n; i++) {
+                    X[i + (long)j * n] += P[i + (long)c * n] * a;
+                    R[i + (long)j * n] -= Q[i + (long)c * n] * a;
+                }
+            }
+        k++;
+        gram(n, s, R, R, rhon);
+        int conv = 1;
+        for (int j = 0; j < s; j++) conv = conv && sqrt(rhon[j + j * s]) <= rtol * bn[j];
+        if (conv) {
+            check = 1;
+            memcpy(rho, rhon, sb);
+            continue;
+        }
+        memcpy(al, rhon, sb);
+        chol_solve(s, Lr, al);                                 /* beta = rho^-1 rho' */
+        for (int j = 0; j < s; j++) {                          /* P = R + P beta */
+            for (int i = 0; i < n; i++) {
+                double v = R[i + (long)j * n];
+                for (int c = 0; c < s; c++) v += P[i + (long)c * n] * al[c + j * s];
+                T[i + (long)j * n] = v;
+            }
+        }
+        memcpy(P, T, nb);
+        memcpy(rho, rhon, sb);
+    }
+    #undef RESTART
+    double worst = 0.0;
+    for (int j = 0; j < s; j++) {
+        residual(n, A, lda, B + (long)j * n, X + (long)j * n, T, nthreads);
+        const double rr = bn[j] > 0.0 ? nrm2(n, T) / bn[j] : nrm2(n, T);
+        if (rr > worst || rr != rr) worst = rr;
+    }
+    *rel_res_out = worst;
+    *iters_out = k;
+    free(R); free(P); free(Q); free(T); free(rho); free(rhon); free(Lr); free(g); free(al); free(bn);
     return status;
 }
 

@@ -11,6 +11,7 @@ import pytest
 
 import oracle as oracle_pkg
 import test_oracle_bicgstab as tbs
+import test_oracle_block_cg as tbc
 import test_oracle_cg as tcg
 import test_oracle_ge_quant as tgq
 import test_oracle_gauss_seidel as tgs
@@ -78,6 +79,13 @@ MUTATIONS = {
                             lambda o: tgs.test_gs_matches_lapack(o, 40)),
     "gs_rhs_perturbed": ("            double s = b[i];\n", "            double s = b[i] * (1.0 + 1e-9);\n",
                          lambda o: tgs.test_gs_matches_lapack(o, 200)),
+    "block_cg_alpha_transposed": ("const double a = al[c + j * s];", "const double a = al[j + c * s];",
+                                  lambda o: tbc.test_block_cg_is_block_krylov_minimiser(o, 3, 5)),
+    "block_cg_beta_transposed": ("for (int c = 0; c < s; c++) v += P[i + (long)c * n] * al[c + j * s];",
+                                 "for (int c = 0; c < s; c++) v += P[i + (long)c * n] * al[j + c * s];",
+                                 lambda o: tbc.test_block_cg_is_block_krylov_minimiser(o, 3, 5)),
+    "block_cg_gamma_without_A": ("gram(n, s, P, Q, g);", "gram(n, s, P, P, g);",
+                                 lambda o: tbc.test_block_cg_is_block_krylov_minimiser(o, 2, 3)),
 }
 
 
