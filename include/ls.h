@@ -58,6 +58,8 @@ extern "C" {
 #define LS_METHOD_BICGSTAB 2   /* ls_bicgstab_solve only (not in the batched engine) */
 #define LS_METHOD_JACOBI   3   /* ls_jacobi_solve only (not in the batched engine)   */
 #define LS_METHOD_GAUSS_SEIDEL 4   /* ls_gauss_seidel_solve only (not in the batched engine) */
+#define LS_METHOD_BLOCK_CG 5       /* ls_block_cg_solve only (not in the batched engine)   */
+#define LS_BLOCK_CG_MAX_S 16       /* right-hand sides of one ls_block_cg_solve, at most   */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -216,6 +218,28 @@ int ls_jacobi_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const doub
  */
 int ls_gauss_seidel_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b,
                           double *x, const ls_opts *opts, ls_info *info);
+
+/*
+ * Block CG (paper: the CG paragraph's method, for s right-hand sides at once
+ * in O'Leary's block form) for SPD A: A X = B with B and X n x s,
+ * column-major (column j at B + j*ldb, X + j*ldx), 1 <= s <= 16.  Each step
+ * forms Q = A P (s products of the FP64 GEMV, A streamed as its FP32 pair
+ * unless opts->f64_matvec), gamma = P^T Q, alpha = gamma^-1 (R^T R) by
+ * Cholesky, X += P alpha, R -= Q alpha, beta = (R^T R)^-1 (R^T R)', and
+ * P = R + P beta.  The iterate minimises the A-norm error over the block
+ * Krylov space, so it needs at most as many steps as single-vector CG on any
+ * column.  Stops when every column has ||R_j|| <= rtol ||B_j||, confirmed on
+ * the true residual (a failed confirmation restarts from it).
+ * info->iters counts block steps (s products each); info->rel_res and
+ * true_rel_res are the largest true relative residual over the columns.  A
+ * rank-deficient residual block (linearly dependent or zero columns of B, or
+ * of R during the iteration) makes a Cholesky factor fail: LS_BREAKDOWN with
+ * the last iterate in X.  X0 is read when opts->x0_given.  opts->precision
+ * must be LS_F64 (else LS_ERR_UNSUPPORTED); s outside 1..16 or ld < n is
+ * LS_ERR_ARG.  Host or device pointers, as for ls_cg_solve.
+ */
+int ls_block_cg_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda, const double *B,
+                      int64_t ldb, double *X, int64_t ldx, const ls_opts *opts, ls_info *info);
 
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {

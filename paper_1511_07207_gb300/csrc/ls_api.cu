@@ -52,6 +52,7 @@ int ws_reserve(ls_ctx *c, size_t bytes) {
     c->graph_bs.reset();
     c->graph_ja.reset();
     c->graph_gs.reset();
+    c->graph_bcg.reset();
     cudaError_t e = cudaMalloc(&c->ws, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -294,6 +295,7 @@ extern "C" int ls_destroy(ls_ctx *c) {
     c->graph_bs.reset();
     c->graph_ja.reset();
     c->graph_gs.reset();
+    c->graph_bcg.reset();
     extra_destroy(c);
     if (c->ws && !c->ws_user) cudaFree(c->ws);
     if (c->fixed) cudaFree(c->fixed);
@@ -317,6 +319,7 @@ extern "C" int ls_set_workspace(ls_ctx *c, void *ptr, size_t bytes) {
     c->graph_bs.reset();
     c->graph_ja.reset();
     c->graph_gs.reset();
+    c->graph_bcg.reset();
     c->ws = static_cast<char *>(ptr);
     c->ws_bytes = ptr ? bytes : 0;
     c->ws_user = ptr != nullptr;
@@ -839,6 +842,11 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
     else ls_opts_default(&o);
     if (o.precision != LS_F64 && method == LS_METHOD_CG) {
         *bytes = mixed_workspace_bytes(n, &o, a_on_device != 0);
+        return LS_OK;
+    }
+    if (method == LS_METHOD_BLOCK_CG) {
+        if (nrhs > BCG_MAX_S) return LS_ERR_ARG;
+        *bytes = bcg_workspace_bytes(n, nrhs, c->K.coop_grid, a_on_device != 0, o.f64_matvec == 0);
         return LS_OK;
     }
     const bool gs = method == LS_METHOD_GAUSS_SEIDEL;

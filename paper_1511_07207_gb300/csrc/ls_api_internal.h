@@ -49,7 +49,7 @@ struct ls_ctx {
     size_t ws_bytes = 0;
     bool ws_user = false;
     // cached executable graphs
-    lsi::GraphCache graph_cg, graph_gm, graph_mx, graph_bs, graph_ja, graph_gs;
+    lsi::GraphCache graph_cg, graph_gm, graph_mx, graph_bs, graph_ja, graph_gs, graph_bcg;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches_total = 0;
     lsi::Engine *batch = nullptr;
@@ -223,6 +223,8 @@ void fill_info(ls_info *info, const State &s, int status, float ms, double bytes
 int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b, double *x,
                    const ls_opts *opts, ls_info *info);
 size_t mixed_workspace_bytes(int n, const ls_opts *o, bool a_on_device);
+// block CG workspace (ls_bcg.cu)
+size_t bcg_workspace_bytes(int n, int s, int grid, bool a_on_device, bool split);
 // extra resources (batch / server) released by ls_destroy
 void extra_destroy(ls_ctx *c);
 }  // namespace lsi

@@ -227,6 +227,34 @@ GsKernels gs_kernels();
 bool gs_encode_maps(void *maps, const float *Ahi, const float *Alo, int n, long long ld, const float *Thi,
                     const float *Tlo, int nblk);
 
+// ---- block CG (k_bcg.cu) ------------------------------------------------------------------
+constexpr int BCG_MAX_S = 16;
+struct BcgSmall {                 // s x s matrices, column-major, leading dimension s
+    double rho[BCG_MAX_S * BCG_MAX_S];     // R^T R
+    double L[BCG_MAX_S * BCG_MAX_S];       // its Cholesky factor (lower triangle)
+    double alpha[BCG_MAX_S * BCG_MAX_S], beta[BCG_MAX_S * BCG_MAX_S];
+    double bn[BCG_MAX_S];                  // ||B_j||
+    double r2[BCG_MAX_S];                  // ||B_j - A X_j||^2 from the residual GEMVs
+    int ok, update_p;
+};
+struct BcgVecs {
+    int n, s;
+    long long ld;                 // column stride of the n x s blocks
+    double *X, *R, *P, *Q;
+    const double *B;
+    double *part;                 // [CTA][BCG_MAX_S^2] partial Gram matrices
+    double *part2;                // [CTA][BCG_MAX_S] partial ||B_j||^2
+    BcgSmall *sm;
+    GridBar *bar;
+    State *st;
+    double rtol;
+};
+struct BcgKernels {
+    void *init, *step, *check;
+    int block;
+};
+BcgKernels bcg_kernels();
+
 struct KrylovKernels {
     void *cg_init, *cg_update, *cg_check;
     void *bs_init, *bs_s, *bs_update, *bs_check;
