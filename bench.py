@@ -275,6 +275,20 @@ def run_native(args):
                     "rel_err_vs_xstar": float(torch.linalg.norm(x5 - xs2) / torch.linalg.norm(xs2)),
                     "A_passes": round(i5["bytes_moved"] / (8.0 * N * N), 1)}
     del x5
+    # block CG (O'Leary) with 8 right-hand sides on the SPD system: one block
+    # product Q = A P per step reads A once for all columns
+    S_BCG = 8
+    from paper_1511_07207_gb300 import inputs as _inputs
+    Xs8 = torch.from_numpy(_inputs.solution(N, seed=2, nrhs=S_BCG).T.copy()).to(dev)   # rows = columns of X*
+    B8 = (A_spd @ Xs8.t()).t().contiguous().t()
+    X8 = torch.zeros((S_BCG, N), dtype=torch.float64, device=dev).t()
+    st6, i6 = B.ls_block_cg_solve(ctx, A_spd, B8, X8, B.make_opts(rtol=RTOL))
+    block_cg = {"status": B.ls_strerror(st6), "rhs": S_BCG, "time_to_1e-10_ms": round(i6["time_ms"], 2),
+                "block_steps": i6["iters"], "ms_per_rhs": round(i6["time_ms"] / S_BCG, 2),
+                "max_true_rel_res": i6["true_rel_res"],
+                "rel_err_vs_xstar": float(torch.linalg.norm(X8 - Xs8.t()) / torch.linalg.norm(Xs8)),
+                "ms_per_step": round(i6["time_ms"] / max(i6["iters"], 1), 3)}
+    del X8, B8, Xs8
 
     # accuracy of the timed results (checked, not assumed)
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
@@ -382,6 +396,7 @@ def run_native(args):
             "bicgstab_nonsym": bicgstab,
             "jacobi_nonsym": jacobi,
             "gauss_seidel_nonsym": gauss_seidel,
+            "block_cg_spd": block_cg,
             "gemv_f64_native": gemv_native,
             "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),

@@ -2,7 +2,7 @@
 // staging of A, B and X, the CUDA graph of the iteration, and the result.
 //
 // Graph: [s residual GEMVs if X0 is given] bcg_init,
-//        while(outer){ while(inner){ s GEMVs Q_j = A P_j, bcg_step },
+//        while(outer){ while(inner){ Q = A P, bcg_step },
 //                      s residual GEMVs R_j = B_j - A X_j (with ||R_j||^2), bcg_check }
 #include <cuda_runtime.h>
 
@@ -20,7 +20,8 @@ struct BcgLayout {
     double *X, *R, *P, *Q, *B, *part, *part2, *Astage;
     BcgSmall *sm;
     float *Ahi, *Alo;
-    long long ld, lda_stage, ld32;
+    float *Ph, *Pl;      // P split for the block product (pair path)
+    long long ld, lda_stage, ld32, ldp;
     size_t bytes;
 };
 
@@ -40,6 +41,9 @@ BcgLayout bcg_layout(void *base, int n, int s, int grid, bool stageA, bool split
     L.sm = cv.take<BcgSmall>(1);
     L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
     L.Alo = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
+    L.ldp = (long long)align_up((size_t)std::max(n, 1), 256);
+    L.Ph = split ? cv.take<float>((size_t)BCG_MAX_S * L.ldp) : nullptr;
+    L.Pl = split ? cv.take<float>((size_t)BCG_MAX_S * L.ldp) : nullptr;
     L.Astage = stageA ? cv.take<double>((size_t)n * L.lda_stage) : nullptr;   // last (see ls_api.cu)
     L.bytes = align_up(cv.off, 256);
     return L;
@@ -80,15 +84,39 @@ int build_bcg_graph(ls_ctx *c, const BcgVecs &v, const BcgLayout &L, const GemvL
     }
     Chain outer = top.loop(ho);
     Chain inner = outer.loop(hi);
-    for (int j = 0; j < v.s; j++) {
-        GemvArgs a{};
-        a.x = v.P + (long long)j * v.ld;
-        a.y = v.Q + (long long)j * v.ld;
-        a.st = v.st;
-        a.scr = c->scr;
-        a.epi = EPI_STORE;
-        a.fin = FIN_STORE;
-        gemv_node(inner, GL, c->dA, a);
+    if (L.Ph) {
+        // Q = A P in one pass over the pair of A (P split first)
+        const BgemvLaunch BL = bgemv_plan(v.s, c->num_sms);
+        int nn = v.n, ss = v.s, SS = BL.S;
+        const double *Pp = v.P;
+        long long ld = v.ld, ldp = L.ldp;
+        float *ph = L.Ph, *pl = L.Pl;
+        State *stp = v.st;
+        void *sargs[] = {&nn, &ss, &SS, &Pp, &ld, &ph, &pl, &ldp, &stp};
+        inner.kernel(BL.split, 4 * c->num_sms, 256, 0, sargs, false);
+        BgemvArgs ba{};
+        ba.n = v.n;
+        ba.s = v.s;
+        ba.Ph = L.Ph;
+        ba.Pl = L.Pl;
+        ba.ldp = L.ldp;
+        ba.Q = v.Q;
+        ba.ldq = v.ld;
+        ba.st = v.st;
+        const MatDesc *pA = c->dA;
+        void *bargs[] = {&pA, &ba};
+        inner.kernel(BL.func, BL.grid, BL.block, BL.smem, bargs, false);
+    } else {
+        for (int j = 0; j < v.s; j++) {   // native FP64 products: one GEMV per column
+            GemvArgs a{};
+            a.x = v.P + (long long)j * v.ld;
+            a.y = v.Q + (long long)j * v.ld;
+            a.st = v.st;
+            a.scr = c->scr;
+            a.epi = EPI_STORE;
+            a.fin = FIN_STORE;
+            gemv_node(inner, GL, c->dA, a);
+        }
     }
     {
         BcgVecs vv = v;

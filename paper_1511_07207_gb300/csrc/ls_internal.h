@@ -255,6 +255,22 @@ struct BcgKernels {
 };
 BcgKernels bcg_kernels();
 
+// ---- block product Q = A P (k_bgemv.cu) ---------------------------------------------------
+struct BgemvArgs {
+    int n, s;
+    const float *Ph, *Pl;         // P split into FP32 pairs: BCG_MAX_S column panels of ldp floats
+    long long ldp;                // a multiple of 256, zero past n
+    double *Q;                    // column-major n x s, column stride ldq
+    long long ldq;
+    State *st;
+};
+struct BgemvLaunch {
+    void *func, *split;           // the product (takes the A descriptor) and the P splitter
+    int grid, block, S;           // S: the kernel's column count (s rounded up to a power of two)
+    size_t smem;
+};
+BgemvLaunch bgemv_plan(int s, int num_sms);
+
 struct KrylovKernels {
     void *cg_init, *cg_update, *cg_check;
     void *bs_init, *bs_s, *bs_update, *bs_check;

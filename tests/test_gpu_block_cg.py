@@ -50,7 +50,7 @@ def test_block_cg_matches_oracle(ctx, gpu, oracle, n, s):
     assert tr <= 1e-10
     assert abs(info["rel_res"] - tr) <= 1e-3 * tr + 1e-14
     assert abs(info["iters"] - ref["iters"]) <= 2 + ref["iters"] // 20
-    assert info["launches"] >= (s + 1) * info["iters"]
+    assert info["launches"] >= 2 * info["iters"]
 
 
 @pytest.mark.parametrize("f64_matvec", [0, 1])
