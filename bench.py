@@ -729,6 +729,35 @@ def run_stationary(args):
     B.ls_destroy(ctx)
 
 
+def run_block_cg_steps(args):
+    """Block CG alone (timing and ncu captures): the SPD matrix G G^T/n + 1e-3 I
+    at --n with --rhs right-hand sides; one solve of one step and one of
+    1 + --reps steps; the difference is --reps steps (block product Q = A P
+    and the step kernel)."""
+    import torch
+    from paper_1511_07207_gb300 import binding as B
+    from paper_1511_07207_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    ctx = B.ls_create(0, torch.cuda.current_stream(dev))
+    n, s = args.n, args.rhs
+    A = inputs.spd_matrix(n, 1e-3, seed=0, device=dev)
+    Xs = torch.from_numpy(inputs.solution(n, seed=2, nrhs=s).T.copy()).to(dev)
+    Bm = (A @ Xs.t()).t().contiguous().t()
+    times = {}
+    for k in (1, 1, 1 + args.reps):
+        X = torch.zeros((s, n), dtype=torch.float64, device=dev).t()
+        st, info = B.ls_block_cg_solve(ctx, A, Bm, X, B.make_opts(rtol=1e-300, max_iter=k))
+        assert st == B.LS_NOT_CONVERGED and info["iters"] == k, (st, info)
+        times[k] = info["time_ms"]
+    step = (times[1 + args.reps] - times[1]) / args.reps
+    mac = float(n) * n * s
+    print(json.dumps({"kernel": "block_cg", "n": n, "rhs": s, "reps": args.reps, "ms_per_step": round(step, 4),
+                      "A_GB/s": round(8.0 * n * n / step / 1e6, 1),
+                      "fp32_ops_per_s": round(12.0 * mac / step / 1e9, 1),
+                      "note": "12 FP32 operations per element of A and column (double-single)"}))
+    B.ls_destroy(ctx)
+
+
 def run_batch_only(args):
     """The batched engine alone (ncu captures of its kernels): the first
     --count systems of the 512-system recipe, one ls_batch_solve."""
@@ -760,12 +789,13 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
     ap.add_argument("--cpu-cg-sample", type=int, default=600)
-    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary", "block_cg"], default=None,
                     help="kernel-only timing (small cases for ncu captures): one GEMV format, "
                          "the batched engine alone on --count systems, or --reps sweeps of a "
                          "stationary method")
     ap.add_argument("--method", choices=["jacobi", "gauss_seidel"], default="gauss_seidel",
                     help="--kernel stationary: which method")
+    ap.add_argument("--rhs", type=int, default=8, help="--kernel block_cg: right-hand sides")
     ap.add_argument("--count", type=int, default=128, help="--kernel batch: systems in the batch")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--dtype", choices=["f64", "pair", "bf16", "fp8", "f32"], default="f64")
@@ -781,6 +811,8 @@ def main():
         run_batch_only(args)
     elif args.kernel == "stationary":
         run_stationary(args)
+    elif args.kernel == "block_cg":
+        run_block_cg_steps(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
