@@ -24,6 +24,8 @@
  *     recomputed from the newest values of the others.
  *   - Block CG: the CG paragraph's method for several right-hand sides at
  *     once in O'Leary's block form (s x s step matrices instead of scalars).
+ *   - Block GMRES: the GMRES pseudocode and restart paragraph with a block
+ *     Arnoldi process over the s right-hand sides at once.
  *   - BiCGSTAB: same section, BiCGSTAB listing, with the steps the listing
  *     leaves out written in (see or_bicgstab).
  *   - Gaussian elimination with partial pivoting: same section,
@@ -673,6 +675,161 @@ done:
     free(w); free(r);
 #undef HR
 #undef HW
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Restarted block GMRES(m), FP64                                      */
+/* ------------------------------------------------------------------ */
+/*
+ * Block GMRES for s right-hand sides B (n x s, column-major), X (n x s)
+ * in/out.  A cycle orthonormalises R = B - A X column by column (modified
+ * Gram-Schmidt, two passes) into V_1 with R = V_1 S; then for j = 1..m:
+ * W = A V_j, and each column of W is orthogonalised (MGS, two passes)
+ * against every basis vector so far and normalised, which gives the
+ * columns of the band Hessenberg matrix H ((m+1)s x ms, s subdiagonals).
+ * Each new column of H is reduced by the earlier Givens rotations and then
+ * by s new ones (its subdiagonal entries from the bottom up), applied also
+ * to G = [S; 0]; after a block step with k columns the residual of
+ * right-hand side c is the norm of rows k..k+s-1 of G's column c.  The
+ * cycle ends when every column passes (<= rtol ||B_c||), after m block steps,
+ * when total block steps reach max_iter, or after a step whose block lost
+ * rank (a column norm at most 1e-14 of its norm before orthogonalisation:
+ * that basis vector is zero); then R Y = G (the leading k x k triangle, back
+ * substitution) and X += V Y.  The iteration stops when the true residual
+ * of every column passes.  iters counts block steps, cycles the restarts.
+ * A rank-deficient starting block or a zero rotation pivot is a breakdown.
+ */
+int or_block_gmres(int n, int s, const double *A, long lda, const double *B, double *X, int m,
+                   double rtol, int max_iter, int x0_given, int nthreads,
+                   int *iters_out, int *cycles_out, double *rel_res_out) {
+    if (n < 0 || s < 1 || lda < n || m < 1 || max_iter < 0) return OR_ERR_ARG;
+    const long ln = n ? n : 1;
+    const int ld = (m + 1) * s, ncol = m * s;
+    double *V = calloc((size_t)ln * ld, sizeof(double));
+    double *H = calloc((size_t)ld * ncol, sizeof(double));
+    double *G = calloc((size_t)ld * s, sizeof(double));
+    double *Y = calloc((size_t)ncol * s, sizeof(double));
+    double *cs = calloc((size_t)ncol * s, sizeof(double)), *sn = calloc((size_t)ncol * s, sizeof(double));
+    int *rr = calloc((size_t)ncol * s, sizeof(int));
+    double *bn = calloc(s, sizeof(double)), *w = malloc(sizeof(double) * ln);
+    int status = OR_NOT_CONVERGED, total = 0, cycles = 0;
+#define HB(i, k) H[(long)(k) * ld + (i)]
+#define GB(i, c) G[(long)(c) * ld + (i)]
+    for (int c = 0; c < s; c++) bn[c] = nrm2(n, B + (long)c * n);
+    if (!x0_given) memset(X, 0, sizeof(double) * ln * s);
+    for (;;) {
+        /* R = B - A X into the first s basis columns; every column passes? */
+        int pass = 1;
+        for (int c = 0; c < s; c++) {
+            residual(n, A, lda, B + (long)c * n, X + (long)c * n, V + (long)c * n, nthreads);
+            pass = pass && nrm2(n, V + (long)c * n) <= rtol * bn[c];
+        }
+        if (pass) { status = OR_OK; break; }
+        if (total >= max_iter) break;
+        cycles++;
+        memset(H, 0, sizeof(double) * ld * ncol);
+        memset(G, 0, sizeof(double) * ld * s);
+        int broke = 0;
+        for (int c = 0; c < s && !broke; c++) {                /* R = V_1 S */
+            double *v = V + (long)c * n;
+            const double before = nrm2(n, v);
+            for (int pass2 = 0; pass2 < 2; pass2++)
+                for (int q = 0; q < c; q++) {
+                    const double h = dot(n, V + (long)q * n, v);
+                    GB(q, c) += h;
+                    for (int i = 0; i < n; i++) v[i] -= h * V[(long)q * n + i];
+                }
+            const double nv = nrm2(n, v);
+            if (!(nv > 1e-14 * before)) { broke = 1; break; }
+            GB(c, c) = nv;
+            for (int i = 0; i < n; i++) v[i] /= nv;
+        }
+        if (broke) { status = OR_BREAKDOWN; break; }
+        int k = 0, nrot = 0, stop = 0;
+        for (int j = 0; j < m && total < max_iter && !stop; j++) {
+            int lucky = 0;
+            for (int c = 0; c < s; c++) {
+                const int col = j * s + c, nb_idx = (j + 1) * s + c;   /* column of H, new basis vector */
+                gemv(n, n, A, lda, V + (long)col * n, w, nthreads);     /* w = A v_col */
+                const double before = nrm2(n, w);
+                for (int pass2 = 0; pass2 < 2; pass2++)
+                    for (int q = 0; q < nb_idx; q++) {
+                        const double h = dot(n, V + (long)q * n, w);
+                        HB(q, col) += h;
+                        for (int i = 0; i < n; i++) w[i] -= h * V[(long)q * n + i];
+                    }
+                const double nw = nrm2(n, w);
+                double *vn = V + (long)nb_idx * n;
+                if (nw > 1e-14 * before) {
+                    HB(nb_idx, col) = nw;
+                    for (int i = 0; i < n; i++) vn[i] = w[i] / nw;
+                } else {
+                    HB(nb_idx, col) = 0.0;
+                    memset(vn, 0, sizeof(double) * n);
+                    lucky = 1;
+                }
+            }
+            /* Givens: the block's s columns in order */
+            for (int c = 0; c < s && !stop; c++) {
+                const int col = j * s + c;
+                for (int t = 0; t < nrot; t++) {
+                    const int r = rr[t];
+                    const double a = HB(r, col), b = HB(r + 1, col);
+                    HB(r, col) = cs[t] * a + sn[t] * b;
+                    HB(r + 1, col) = -sn[t] * a + cs[t] * b;
+                }
+                for (int r = col + s - 1; r >= col; r--) {      /* zero row r + 1 */
+                    const double a = HB(r, col), b = HB(r + 1, col);
+                    const double den = hypot(a, b);
+                    const double cc = den > 0.0 ? a / den : 1.0, ss = den > 0.0 ? b / den : 0.0;
+                    HB(r, col) = den > 0.0 ? den : a;
+                    HB(r + 1, col) = 0.0;
+                    for (int q = 0; q < s; q++) {
+                        const double ga = GB(r, q), gb = GB(r + 1, q);
+                        GB(r, q) = cc * ga + ss * gb;
+                        GB(r + 1, q) = -ss * ga + cc * gb;
+                    }
+                    rr[nrot] = r; cs[nrot] = cc; sn[nrot] = ss; nrot++;
+                }
+                if (HB(col, col) == 0.0) { status = OR_BREAKDOWN; stop = 2; }
+            }
+            if (stop == 2) break;
+            k = (j + 1) * s;
+            total++;
+            int conv = 1;
+            for (int c = 0; c < s; c++) {
+                double e2 = 0.0;
+                for (int r = k; r < k + s; r++) e2 += GB(r, c) * GB(r, c);
+                conv = conv && sqrt(e2) <= rtol * bn[c];
+            }
+            if (conv || lucky) stop = 1;
+        }
+        if (stop == 2) break;
+        /* R Y = G on the leading k x k triangle, X += V Y */
+        for (int c = 0; c < s; c++) {
+            double *y = Y + (long)c * ncol;
+            for (int i = k - 1; i >= 0; i--) {
+                double v = GB(i, c);
+                for (int q = i + 1; q < k; q++) v -= HB(i, q) * y[q];
+                y[i] = v / HB(i, i);
+            }
+            for (int q = 0; q < k; q++)
+                for (int i = 0; i < n; i++) X[(long)c * n + i] += V[(long)q * n + i] * y[q];
+        }
+    }
+    double worst = 0.0;
+    for (int c = 0; c < s; c++) {
+        residual(n, A, lda, B + (long)c * n, X + (long)c * n, w, nthreads);
+        const double r = bn[c] > 0.0 ? nrm2(n, w) / bn[c] : nrm2(n, w);
+        if (!(r <= worst)) worst = r;
+    }
+    *rel_res_out = worst;
+    *iters_out = total;
+    *cycles_out = cycles;
+    free(V); free(H); free(G); free(Y); free(cs); free(sn); free(rr); free(bn); free(w);
+#undef HB
+#undef GB
     return status;
 }
 

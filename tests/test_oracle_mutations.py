@@ -12,6 +12,7 @@ import pytest
 import oracle as oracle_pkg
 import test_oracle_bicgstab as tbs
 import test_oracle_block_cg as tbc
+import test_oracle_block_gmres as tbg
 import test_oracle_cg as tcg
 import test_oracle_ge_quant as tgq
 import test_oracle_gauss_seidel as tgs
@@ -86,6 +87,15 @@ MUTATIONS = {
                                  lambda o: tbc.test_block_cg_is_block_krylov_minimiser(o, 3, 5)),
     "block_cg_gamma_without_A": ("gram(n, s, P, Q, g);", "gram(n, s, P, P, g);",
                                  lambda o: tbc.test_block_cg_is_block_krylov_minimiser(o, 2, 3)),
+    "block_gmres_rotation_sign": ("                    HB(r + 1, col) = 0.0;\n                    for (int q = 0; q < s; q++) {\n                        const double ga = GB(r, q), gb = GB(r + 1, q);\n                        GB(r, q) = cc * ga + ss * gb;\n                        GB(r + 1, q) = -ss * ga + cc * gb;",
+                                  "                    HB(r + 1, col) = 0.0;\n                    for (int q = 0; q < s; q++) {\n                        const double ga = GB(r, q), gb = GB(r + 1, q);\n                        GB(r, q) = cc * ga + ss * gb;\n                        GB(r + 1, q) = ss * ga + cc * gb;",
+                                  lambda o: tbg.test_block_gmres_is_block_krylov_minimiser(o, 3, 4)),
+    "block_gmres_single_pass_basis_short": ("                    for (int q = 0; q < nb_idx; q++) {\n                        const double h = dot(n, V + (long)q * n, w);\n                        HB(q, col) += h;",
+                                            "                    for (int q = 0; q < nb_idx - 1; q++) {\n                        const double h = dot(n, V + (long)q * n, w);\n                        HB(q, col) += h;",
+                                            lambda o: tbg.test_block_gmres_is_block_krylov_minimiser(o, 3, 4)),
+    "block_gmres_backsolve_index": ("for (int q = i + 1; q < k; q++) v -= HB(i, q) * y[q];",
+                                    "for (int q = i + 1; q < k; q++) v -= HB(q, i) * y[q];",
+                                    lambda o: tbg.test_block_gmres_is_block_krylov_minimiser(o, 2, 3)),
 }
 
 
