@@ -60,6 +60,8 @@ extern "C" {
 #define LS_METHOD_GAUSS_SEIDEL 4   /* ls_gauss_seidel_solve only (not in the batched engine) */
 #define LS_METHOD_BLOCK_CG 5       /* ls_block_cg_solve only (not in the batched engine)   */
 #define LS_BLOCK_CG_MAX_S 16       /* right-hand sides of one ls_block_cg_solve, at most   */
+#define LS_METHOD_BLOCK_GMRES 6    /* ls_block_gmres_solve only                              */
+#define LS_BLOCK_GMRES_MAX_MS 256  /* restart x right-hand sides of ls_block_gmres_solve     */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -240,6 +242,29 @@ int ls_gauss_seidel_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, cons
  */
 int ls_block_cg_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda, const double *B,
                       int64_t ldb, double *X, int64_t ldx, const ls_opts *opts, ls_info *info);
+
+/*
+ * Restarted block GMRES(m), m = opts->restart block steps per cycle (paper:
+ * the GMRES pseudocode and restart paragraph, with a block Arnoldi process
+ * over s right-hand sides at once) for general nonsingular A: A X = B with B
+ * and X n x s, column-major (column j at B + j*ldb, X + j*ldx), 1 <= s <= 16,
+ * m * s <= 256.  Each block step forms W = A V_j (one pass over the FP32 pair
+ * of A for all s columns), orthogonalises it against the basis by two
+ * passes of block classical Gram-Schmidt and factors it by CholQR2 into
+ * V_{j+1} H_{j+1,j}; the band Hessenberg matrix is reduced by Givens
+ * rotations, so every right-hand side's residual is known without forming
+ * it; a cycle ends when all of them pass rtol ||B_c||, after m steps, or on a
+ * block that lost rank; then X += V Y.  Each cycle starts from the true
+ * residual and the solve stops when every column's true residual passes.
+ * info->iters counts block steps, info->outer_iters cycles, rel_res the
+ * largest true relative residual over the columns.  A rank-deficient
+ * starting block (dependent or zero columns of B - A X) or a zero rotation
+ * pivot returns LS_BREAKDOWN with the last iterate in X.  opts->precision
+ * must be LS_F64 and opts->f64_matvec 0 (else LS_ERR_UNSUPPORTED); s or m
+ * outside the limits or ld < n is LS_ERR_ARG.  Host or device pointers.
+ */
+int ls_block_gmres_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *X, int64_t ldx, const ls_opts *opts, ls_info *info);
 
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {

@@ -67,10 +67,13 @@ __host__ __device__ constexpr size_t stage_bytes() {
 }  // namespace
 
 // P (column-major n x s, FP64) -> Ph, Pl (column panels of ldp floats, S of
-// them; zero past n and for columns >= s).
+// them; zero past n and for columns >= s).  With kptr set, P starts at
+// P + (*kptr) * kstride (a graph node walking the blocks of a basis).
 __global__ void bgemv_split_kernel(int n, int s, int S, const double *__restrict__ P, long long ld,
-                                   float *__restrict__ Ph, float *__restrict__ Pl, long long ldp, State *st) {
+                                   float *__restrict__ Ph, float *__restrict__ Pl, long long ldp, State *st,
+                                   const int *kptr, long long kstride) {
     count_launch(st);
+    if (kptr) P += (long long)(*kptr) * kstride;
     const long long total = (long long)S * ldp;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {

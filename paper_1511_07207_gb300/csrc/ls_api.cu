@@ -53,6 +53,7 @@ int ws_reserve(ls_ctx *c, size_t bytes) {
     c->graph_ja.reset();
     c->graph_gs.reset();
     c->graph_bcg.reset();
+    c->graph_bgm.reset();
     cudaError_t e = cudaMalloc(&c->ws, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -296,6 +297,7 @@ extern "C" int ls_destroy(ls_ctx *c) {
     c->graph_ja.reset();
     c->graph_gs.reset();
     c->graph_bcg.reset();
+    c->graph_bgm.reset();
     extra_destroy(c);
     if (c->ws && !c->ws_user) cudaFree(c->ws);
     if (c->fixed) cudaFree(c->fixed);
@@ -320,6 +322,7 @@ extern "C" int ls_set_workspace(ls_ctx *c, void *ptr, size_t bytes) {
     c->graph_ja.reset();
     c->graph_gs.reset();
     c->graph_bcg.reset();
+    c->graph_bgm.reset();
     c->ws = static_cast<char *>(ptr);
     c->ws_bytes = ptr ? bytes : 0;
     c->ws_user = ptr != nullptr;
@@ -842,6 +845,11 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
     else ls_opts_default(&o);
     if (o.precision != LS_F64 && method == LS_METHOD_CG) {
         *bytes = mixed_workspace_bytes(n, &o, a_on_device != 0);
+        return LS_OK;
+    }
+    if (method == LS_METHOD_BLOCK_GMRES) {
+        if (nrhs > BGM_MAX_S || o.restart < 1 || o.restart * nrhs > BGM_MAX_MS) return LS_ERR_ARG;
+        *bytes = bgm_workspace_bytes(n, nrhs, o.restart, c->K.coop_grid, a_on_device != 0);
         return LS_OK;
     }
     if (method == LS_METHOD_BLOCK_CG) {

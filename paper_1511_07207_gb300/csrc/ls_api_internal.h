@@ -49,7 +49,7 @@ struct ls_ctx {
     size_t ws_bytes = 0;
     bool ws_user = false;
     // cached executable graphs
-    lsi::GraphCache graph_cg, graph_gm, graph_mx, graph_bs, graph_ja, graph_gs, graph_bcg;
+    lsi::GraphCache graph_cg, graph_gm, graph_mx, graph_bs, graph_ja, graph_gs, graph_bcg, graph_bgm;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches_total = 0;
     lsi::Engine *batch = nullptr;
@@ -225,6 +225,7 @@ int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double 
 size_t mixed_workspace_bytes(int n, const ls_opts *o, bool a_on_device);
 // block CG workspace (ls_bcg.cu)
 size_t bcg_workspace_bytes(int n, int s, int grid, bool a_on_device, bool split);
+size_t bgm_workspace_bytes(int n, int s, int m, int grid, bool a_on_device);
 // extra resources (batch / server) released by ls_destroy
 void extra_destroy(ls_ctx *c);
 }  // namespace lsi

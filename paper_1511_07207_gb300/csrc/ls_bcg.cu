@@ -92,7 +92,9 @@ int build_bcg_graph(ls_ctx *c, const BcgVecs &v, const BcgLayout &L, const GemvL
         long long ld = v.ld, ldp = L.ldp;
         float *ph = L.Ph, *pl = L.Pl;
         State *stp = v.st;
-        void *sargs[] = {&nn, &ss, &SS, &Pp, &ld, &ph, &pl, &ldp, &stp};
+        const int *kp = nullptr;
+        long long kst = 0;
+        void *sargs[] = {&nn, &ss, &SS, &Pp, &ld, &ph, &pl, &ldp, &stp, &kp, &kst};
         inner.kernel(BL.split, 4 * c->num_sms, 256, 0, sargs, false);
         BgemvArgs ba{};
         ba.n = v.n;

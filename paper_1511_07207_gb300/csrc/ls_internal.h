@@ -255,6 +255,40 @@ struct BcgKernels {
 };
 BcgKernels bcg_kernels();
 
+// ---- block GMRES (k_bgmres.cu) -----------------------------------------------------------
+constexpr int BGM_MAX_S = 16;
+constexpr int BGM_MAX_MS = 256;       // m * s at most
+enum : int { BGF_CHOL = 0, BGF_NROT = 1, BGF_LUCKY = 2, BGF_COUNT = 4 };
+struct BgmVecs {
+    int n, s, m;
+    long long ld;                 // column stride of V, W, X, B
+    double *V;                    // basis, n x (m+1)s
+    double *W;                    // A V_j, n x s
+    double *X;
+    const double *B;
+    double *H;                    // rotated band Hessenberg, (m+1)s x ms, leading dimension (m+1)s
+    double *G;                    // rotated right-hand side, (m+1)s x s
+    double *Y;                    // ms x s
+    double *cs, *sn;              // the cycle's rotations (ms * s at most)
+    int *rrow;
+    double *Hc;                   // reduced Gram coefficients, (m+1)s x s at most
+    double *Lm;                   // s x s Cholesky factor of the last CholQR pass
+    double *part;                 // [CTA][part_stride] partial Gram matrices
+    long long part_stride;
+    double *bn, *r2;              // ||B_c||, ||B_c - A X_c||^2
+    int *flags;                   // BGF_*
+    GridBar *bar;
+    State *st;
+    double rtol;
+};
+struct BgmKernels {
+    void *init, *start, *orth, *finish;
+    int block;
+};
+BgmKernels bgm_kernels();
+size_t bgm_orth_smem(int m, int s);
+size_t bgm_finish_smem(int m, int s);
+
 // ---- block product Q = A P (k_bgemv.cu) ---------------------------------------------------
 struct BgemvArgs {
     int n, s;
