@@ -2,8 +2,9 @@
 //
 // Block GMRES (the GMRES pseudocode and restart paragraph of the paper, with
 // a block Arnoldi process over the s right-hand sides at once).  A cycle:
-//   the residual GEMVs write R = B - A X into V's first block with ||R_c||^2;
-//   bgm_start  stop if every column passes; else V_1 S = R by CholQR2 (two
+//   the block product writes A X into V's first block;
+//   bgm_start  R = B - A X there and ||R_c||^2; stop if every column passes;
+//              else V_1 S = R by CholQR2 (two
 //              passes of Gram matrix, Cholesky, triangular solve per row),
 //              G = [S; 0];
 //   per block step j (graph while-node): P split + block product W = A V_j
@@ -55,13 +56,18 @@ __device__ void gram_reduce_spread(const BgmVecs &v, int cnt, double *out) {
     }
 }
 
-// One warp: G = L L^T in place (column-major s x s); false on a non-positive pivot.
+// One warp: G = L L^T in place (column-major s x s).  False when a pivot is
+// at most 1e-12 of its diagonal entry: the squared norm of the column's part
+// orthogonal to the earlier ones carries an absolute rounding error of about
+// u G_jj, so a Gram-matrix QR cannot tell an orthogonal part below about
+// 1e-6 of the column from zero -- the block is treated as rank-deficient.
 __device__ bool warp_chol(int s, double *G) {
     const int lane = threadIdx.x & 31;
     for (int j = 0; j < s; j++) {
-        double d = G[j + j * s];
+        const double gjj = G[j + j * s];
+        double d = gjj;
         for (int k = 0; k < j; k++) d -= G[j + k * s] * G[j + k * s];
-        if (!(d > 0.0) || !isfinite(d)) return false;
+        if (!(d > 1e-12 * gjj) || !isfinite(d)) return false;
         d = sqrt(d);
         __syncwarp();
         if (lane > j && lane < s) {
@@ -177,10 +183,28 @@ __global__ void __launch_bounds__(GT) bgm_start_kernel(BgmVecs v, cudaGraphCondi
     State *st = v.st;
     count_launch(st);
     const int s = v.s;
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    // R = B - A X in V's first block (A X from the block product), ||R_c||^2
+    for (int c = 0; c < s; c++)
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const long long o = (long long)c * v.ld + i;
+            v.V[o] = v.B[o] - v.V[o];
+        }
+    __syncthreads();
+    for (int c = threadIdx.x; c < s; c += blockDim.x) {
+        const double *r = v.V + (long long)c * v.ld;
+        double acc = 0.0;
+        for (long long i = lo; i < hi; i++) acc += r[i] * r[i];
+        v.part[(size_t)blockIdx.x * v.part_stride + c] = acc;
+    }
+    if (!grid_sync(v.bar, st)) return;
     if (threadIdx.x == 0) {
         bool pass = true, nan = false;
         for (int c = 0; c < s; c++) {
-            const double r2 = *(volatile double *)&v.r2[c];
+            double r2 = 0.0;
+            for (int b = 0; b < (int)gridDim.x; b++) r2 += __ldcg(&v.part[(size_t)b * v.part_stride + c]);
+            if (blockIdx.x == 0) v.r2[c] = r2;
             nan = nan || !isfinite(r2);
             pass = pass && sqrt(r2) <= v.rtol * v.bn[c];
         }
@@ -207,8 +231,6 @@ __global__ void __launch_bounds__(GT) bgm_start_kernel(BgmVecs v, cudaGraphCondi
         }
         return;
     }
-    long long lo, hi;
-    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
     // V_1 S = R (CholQR2); a rank-deficient block is a breakdown
     int ok = cholqr_pass(v, v.V, lo, hi);
     if (ok < 0) return;

@@ -1,8 +1,8 @@
 // ls_bgmres.cu -- the host driver of restarted block GMRES (ls_block_gmres_solve):
 // workspace, staging of A, B and X, the CUDA graph of the iteration, the result.
 //
-// Graph: bgm_init, while(outer){ s residual GEMVs R_c = B_c - A X_c into V's
-//        first block (with ||R_c||^2), bgm_start,
+// Graph: bgm_init, while(outer){ split X, A X into V's first block (block
+//        product), bgm_start (R = B - A X, ||R_c||^2, the stop test),
 //        while(inner){ split V_j, W = A V_j (block product), bgm_orth }, bgm_finish }
 #include <cuda_runtime.h>
 
@@ -58,8 +58,7 @@ BgmLayout bgm_layout(void *base, int n, int s, int m, int grid, bool stageA) {
     return L;
 }
 
-int build_bgm_graph(ls_ctx *c, const BgmVecs &v, const BgmLayout &L, const GemvLaunch &GL, int x0_given,
-                    const long long *key) {
+int build_bgm_graph(ls_ctx *c, const BgmVecs &v, const BgmLayout &L, int x0_given, const long long *key) {
     const BgmKernels K = bgm_kernels();
     const BgemvLaunch BL = bgemv_plan(v.s, c->num_sms);
     const size_t orth_smem = bgm_orth_smem(v.m, v.s), fin_smem = bgm_finish_smem(v.m, v.s);
@@ -80,17 +79,28 @@ int build_bgm_graph(ls_ctx *c, const BgmVecs &v, const BgmLayout &L, const GemvL
         top.kernel(K.init, c->K.coop_grid, K.block, 0, args, true);
     }
     Chain outer = top.loop(ho);
-    for (int j = 0; j < v.s; j++) {
-        GemvArgs a{};
-        a.x = v.X + (long long)j * v.ld;
-        a.y = v.V + (long long)j * v.ld;
-        a.b = v.B + (long long)j * v.ld;
-        a.dot_out = v.r2 + j;
-        a.st = v.st;
-        a.scr = c->scr;
-        a.epi = EPI_RESID;
-        a.fin = FIN_STORE;
-        gemv_node(outer, GL, c->dA, a);
+    {   // A X into V's first block, one pass over A for all columns
+        int nn = v.n, ss = v.s, SS = BL.S;
+        const double *Xp = v.X;
+        long long ld = v.ld, ldp = L.ldp;
+        float *ph = L.Ph, *pl = L.Pl;
+        State *stp = v.st;
+        const int *kp = nullptr;
+        long long kst = 0;
+        void *sargs[] = {&nn, &ss, &SS, &Xp, &ld, &ph, &pl, &ldp, &stp, &kp, &kst};
+        outer.kernel(BL.split, 4 * c->num_sms, 256, 0, sargs, false);
+        BgemvArgs ba{};
+        ba.n = v.n;
+        ba.s = v.s;
+        ba.Ph = L.Ph;
+        ba.Pl = L.Pl;
+        ba.ldp = L.ldp;
+        ba.Q = v.V;
+        ba.ldq = v.ld;
+        ba.st = v.st;
+        const MatDesc *pA = c->dA;
+        void *bargs[] = {&pA, &ba};
+        outer.kernel(BL.func, BL.grid, BL.block, BL.smem, bargs, false);
     }
     {
         BgmVecs vv = v;
@@ -213,11 +223,10 @@ extern "C" int ls_block_gmres_solve(ls_ctx *c, int n, int s, const double *A, in
     v.bar = c->bar;
     v.st = c->st;
     v.rtol = o.rtol;
-    GemvLaunch GL = gemv_plan(DT_DS, true, EPI_DOT, c->num_sms);
     long long key[8] = {300 + s, n, (long long)(uintptr_t)c->ws, m, o.x0_given, L.ld,
                         (long long)(uintptr_t)c->stream, DT_DS};
     if (!c->graph_bgm.matches(key)) {
-        rc = build_bgm_graph(c, v, L, GL, o.x0_given, key);
+        rc = build_bgm_graph(c, v, L, o.x0_given, key);
         if (rc) return rc;
     }
     e = cudaEventRecord(c->ev0, c->stream);
@@ -252,7 +261,7 @@ extern "C" int ls_block_gmres_solve(ls_ctx *c, int n, int s, const double *A, in
     sc.bnorm = 1.0;
     sc.rnorm = worst;
     sc.true_rnorm = worst;
-    const double passes = (double)st.iter + (double)s * (st.cycles + 1);
+    const double passes = (double)st.iter + st.cycles + 1;   // one pass of A per block product
     c->launches_total += (long long)st.launches;
     fill_info(info, sc, status, ms, passes * (double)n * n * 8.0, (long long)st.launches);
     return status;
