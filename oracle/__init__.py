@@ -81,6 +81,7 @@ class Oracle:
         lib.or_block_cg.argtypes = [i, i, P, l, P, P, d, i, i, i, P, P]
         lib.or_block_gmres.argtypes = [i, i, P, l, P, P, i, d, i, i, i, P, P, P]
         lib.or_ge_solve.argtypes = [i, P, l, P, P]
+        lib.or_ge_factor.argtypes = [i, P, l, P, P, P, P]
         for name in ("or_bf16_round", "or_e4m3_round"):
             getattr(lib, name).argtypes = [d]
             getattr(lib, name).restype = d
@@ -227,6 +228,18 @@ class Oracle:
         if first_cycle:
             out.update(V=V.T.copy(), H=H.T.copy(), k=k1.value)
         return out
+
+    def ge_factor(self, A, b):
+        """The elimination alone.  Returns (LU, ipiv, y, status): unit L below the
+        diagonal and U on and above it (rows in pivoted order), the row swapped
+        with row k at step k, and y = L^-1 P b."""
+        A = _mat(A)
+        n = A.shape[0]
+        LU = np.zeros((n, n))
+        ipiv = np.zeros(n, dtype=np.int32)
+        y = np.zeros(n)
+        st = self.lib.or_ge_factor(n, _p(A), n, _p(_vec(b, n)), _p(LU), _p(ipiv), _p(y))
+        return LU, ipiv, y, st
 
     def ge_solve(self, A, b):
         """Gaussian elimination with partial pivoting.  Returns (x, status)."""

@@ -843,15 +843,10 @@ int or_block_gmres(int n, int s, const double *A, long lda, const double *B, dou
  * rank-1 update from the trailing block.  Then L y = P b (unit lower,
  * forward) and U x = y (back).  Returns OR_BREAKDOWN on a zero pivot.
  */
-int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
-    if (n < 0 || lda < n) return OR_ERR_ARG;
-    double *W = malloc(sizeof(double) * (size_t)(n ? n : 1) * (n ? n : 1));
-    double *y = malloc(sizeof(double) * (n ? n : 1));
-    for (int i = 0; i < n; i++) {
-        memcpy(W + (long)i * n, A + (long)i * lda, sizeof(double) * n);
-        y[i] = b[i];
-    }
-    int status = OR_OK;
+/* The elimination on W (n x n, row-major) and y, in place; ipiv[k] = the
+ * row swapped with row k (NULL: not recorded).  Returns OR_BREAKDOWN on a
+ * zero pivot (W, y as far as the elimination got). */
+static int ge_eliminate(int n, double *W, double *y, int *ipiv) {
     for (int k = 0; k < n; k++) {
         int v = k;
         double best = fabs(W[(long)k * n + k]);
@@ -859,6 +854,7 @@ int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
             double a = fabs(W[(long)i * n + k]);
             if (a > best) { best = a; v = i; }
         }
+        if (ipiv) ipiv[k] = v;
         if (v != k) {
             for (int j = 0; j < n; j++) {
                 double t = W[(long)k * n + j];
@@ -868,7 +864,7 @@ int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
             double t = y[k]; y[k] = y[v]; y[v] = t;
         }
         double piv = W[(long)k * n + k];
-        if (piv == 0.0) { status = OR_BREAKDOWN; break; }
+        if (piv == 0.0) return OR_BREAKDOWN;
         for (int i = k + 1; i < n; i++) {
             double l = W[(long)i * n + k] / piv;
             W[(long)i * n + k] = l;
@@ -876,6 +872,18 @@ int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
             y[i] -= l * y[k];                     /* forward substitution, fused */
         }
     }
+    return OR_OK;
+}
+
+int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
+    if (n < 0 || lda < n) return OR_ERR_ARG;
+    double *W = malloc(sizeof(double) * (size_t)(n ? n : 1) * (n ? n : 1));
+    double *y = malloc(sizeof(double) * (n ? n : 1));
+    for (int i = 0; i < n; i++) {
+        memcpy(W + (long)i * n, A + (long)i * lda, sizeof(double) * n);
+        y[i] = b[i];
+    }
+    int status = ge_eliminate(n, W, y, NULL);
     if (status == OR_OK) {
         for (int i = n - 1; i >= 0; i--) {        /* back substitution */
             double s = y[i];
@@ -885,6 +893,18 @@ int or_ge_solve(int n, const double *A, long lda, const double *b, double *x) {
     }
     free(W); free(y);
     return status;
+}
+
+/* The factorization alone: LU (n x n, row-major: unit L below the diagonal,
+ * U on and above it, rows in pivoted order), ipiv (the row swapped with row
+ * k at step k) and y = L^-1 P b (the fused forward substitution). */
+int or_ge_factor(int n, const double *A, long lda, const double *b, double *LU, int *ipiv, double *y) {
+    if (n < 0 || lda < n) return OR_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        memcpy(LU + (long)i * n, A + (long)i * lda, sizeof(double) * n);
+        y[i] = b[i];
+    }
+    return ge_eliminate(n, LU, y, ipiv);
 }
 
 /* ------------------------------------------------------------------ */

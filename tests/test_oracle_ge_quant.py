@@ -146,3 +146,27 @@ def test_fp8_quant_row_scales(oracle):
     assert np.all(np.abs(dec - A)[big] <= np.abs(A)[big] * 2.0 ** -4 * 1.0001)
     # row maxima land on the top of the range
     assert np.all(np.abs(oracle.decode_fp8(Q)).max(axis=1) == 448.0)
+
+
+@pytest.mark.parametrize("n", [1, 5, 60])
+def test_ge_factor_is_partial_pivoting_lu(oracle, n):
+    # the exported factors: P A = L U (numpy, FP64) to rounding, |L| <= 1 (the
+    # defining property of partial pivoting), y = L^-1 P b, and the solve path
+    # (or_ge_solve) gives the back substitution of the same factors
+    A = inputs.nonsym_matrix(n, seed=200 + n)
+    b = A @ inputs.solution(n, seed=201 + n)
+    LU, ipiv, y, st = oracle.ge_factor(A, b)
+    assert st == oracle.OK
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    PA, Pb = A.copy(), b.copy()
+    for k in range(n):
+        PA[[k, ipiv[k]]] = PA[[ipiv[k], k]]
+        Pb[[k, ipiv[k]]] = Pb[[ipiv[k], k]]
+        assert ipiv[k] >= k
+    assert np.max(np.abs(PA - L @ U)) <= 4 * n * 2.0 ** -52 * np.max(np.abs(A)) * max(1, n)
+    assert np.max(np.abs(L)) <= 1.0
+    assert np.allclose(L @ y, Pb, rtol=0, atol=1e-12 * np.abs(b).max())
+    x, st2 = oracle.ge_solve(A, b)
+    assert st2 == oracle.OK
+    assert np.allclose(U @ x, y, rtol=0, atol=1e-12 * np.abs(y).max())
