@@ -62,6 +62,7 @@ extern "C" {
 #define LS_BLOCK_CG_MAX_S 16       /* right-hand sides of one ls_block_cg_solve, at most   */
 #define LS_METHOD_BLOCK_GMRES 6    /* ls_block_gmres_solve only                              */
 #define LS_BLOCK_GMRES_MAX_MS 256  /* restart x right-hand sides of ls_block_gmres_solve     */
+#define LS_METHOD_LU 7             /* ls_lu_solve (the direct method)                        */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -265,6 +266,36 @@ int ls_block_cg_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda, c
  */
 int ls_block_gmres_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda, const double *B,
                          int64_t ldb, double *X, int64_t ldx, const ls_opts *opts, ls_info *info);
+
+/*
+ * The direct method (paper: the right-looking LU with partial pivoting of
+ * the direct-methods section): at step k the row v >= k with the largest
+ * |a_vk| (the first one on ties) is swapped with row k, the sub-column is
+ * divided by the pivot and the rank-1 update is subtracted from the trailing
+ * block; b is carried along as an extra column, so L y = P b is done during
+ * the elimination; then U x = y.  FP64, unblocked: every element of L, U
+ * and y is bit for bit what the same elimination gives in plain FP64 (IEEE
+ * division, multiply and subtract not fused).  After the solve the true
+ * residual ||b - A x|| is formed (info->rel_res, true_rel_res; info->iters =
+ * 0).  A zero pivot returns LS_BREAKDOWN with x unchanged; a residual that
+ * is not finite returns LS_ERR_NAN.  A row-major n x n (host or device), b
+ * and x n vectors; opts may be NULL; opts->precision must be LS_F64.  The
+ * elimination streams the trailing block once per step, 16 n^3 / 3 bytes in
+ * all: HBM-bound.
+ */
+int ls_lu_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *x,
+                const ls_opts *opts, ls_info *info);
+
+/*
+ * The factorization of ls_lu_solve alone: LU (n x n, row-major, leading
+ * dimension ldlu >= n) receives the unit lower factor L below the diagonal
+ * and U on and above it, rows in pivoted order; ipiv[k] the row swapped with
+ * row k at step k; y = L^-1 P b.  Outputs may be host or device memory.
+ * Returns LS_BREAKDOWN on a zero pivot (outputs as far as the elimination
+ * got), LS_ERR_ARG on bad sizes or NULL pointers.
+ */
+int ls_lu_factor(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *LU,
+                 int64_t ldlu, int *ipiv, double *y);
 
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {

@@ -20,6 +20,7 @@ LS_ERR_BUSY, LS_ERR_NAN, LS_ERR_UNSUPPORTED = -5, -6, -7
 LS_METHOD_CG, LS_METHOD_GMRES, LS_METHOD_BICGSTAB, LS_METHOD_JACOBI, LS_METHOD_GAUSS_SEIDEL = 0, 1, 2, 3, 4
 LS_METHOD_BLOCK_CG, LS_BLOCK_CG_MAX_S = 5, 16
 LS_METHOD_BLOCK_GMRES, LS_BLOCK_GMRES_MAX_MS = 6, 256
+LS_METHOD_LU = 7
 LS_F64, LS_BF16_IR, LS_FP8_IR, LS_F32_IR = 0, 1, 2, 3
 LS_F64_PAIR = 4
 LS_REFINE_FCG, LS_REFINE_IR = 0, 1
@@ -29,7 +30,7 @@ LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 8192, 32
 # every symbol declared in include/ls.h
 ABI_FUNCTIONS = (
     "ls_opts_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_set_workspace",
-    "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_gauss_seidel_solve", "ls_block_cg_solve", "ls_block_gmres_solve", "ls_batch_solve", "ls_server_start", "ls_server_submit",
+    "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_gauss_seidel_solve", "ls_block_cg_solve", "ls_block_gmres_solve", "ls_lu_solve", "ls_lu_factor", "ls_batch_solve", "ls_server_start", "ls_server_submit",
     "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
     "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror",
 )
@@ -93,10 +94,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_size_t)]
         lib.ls_set_workspace.argtypes = [P, P, ctypes.c_size_t]
         for fn in (lib.ls_cg_solve, lib.ls_gmres_solve, lib.ls_bicgstab_solve, lib.ls_jacobi_solve,
-               lib.ls_gauss_seidel_solve):
+               lib.ls_gauss_seidel_solve, lib.ls_lu_solve):
             fn.argtypes = [P, I, P, I64, P, P, ctypes.POINTER(ls_opts), ctypes.POINTER(ls_info)]
         for fn in (lib.ls_block_cg_solve, lib.ls_block_gmres_solve):
             fn.argtypes = [P, I, I, P, I64, P, I64, P, I64, ctypes.POINTER(ls_opts), ctypes.POINTER(ls_info)]
+        lib.ls_lu_factor.argtypes = [P, I, P, I64, P, P, I64, P, P]
         lib.ls_batch_solve.argtypes = [P, I, ctypes.POINTER(ls_system), ctypes.POINTER(ls_info)]
         lib.ls_server_start.argtypes = [P, ctypes.POINTER(ls_server_cfg), ctypes.POINTER(P)]
         lib.ls_server_submit.argtypes = [P, ctypes.POINTER(ls_system),
@@ -338,6 +340,18 @@ def ls_block_gmres_solve(ctx, A, B, X, opts=None):
     st = load().ls_block_gmres_solve(ctx, n, B.shape[1], ptr(A), lead_dim(A), ptr(B), col_lead_dim(B), ptr(X),
                                      col_lead_dim(X), ctypes.byref(o), ctypes.byref(info))
     return st, info.as_dict()
+
+
+def ls_lu_solve(ctx, A, b, x, opts=None):
+    """The direct method: LU with partial pivoting, then U x = y; see ls_cg_solve."""
+    return _solve(load().ls_lu_solve, ctx, A, b, x, opts)
+
+
+def ls_lu_factor(ctx, A, b, LU, ipiv, y):
+    """The factorization alone into LU (n x n row-major), ipiv (int32), y.  Returns the status."""
+    _check_f64(A, b, LU, y)
+    n = A.shape[0]
+    return load().ls_lu_factor(ctx, n, ptr(A), lead_dim(A), ptr(b), ptr(LU), lead_dim(LU), ptr(ipiv), ptr(y))
 
 
 def ls_batch_solve(ctx, systems):

@@ -226,6 +226,7 @@ size_t mixed_workspace_bytes(int n, const ls_opts *o, bool a_on_device);
 // block CG workspace (ls_bcg.cu)
 size_t bcg_workspace_bytes(int n, int s, int grid, bool a_on_device, bool split);
 size_t bgm_workspace_bytes(int n, int s, int m, int grid, bool a_on_device);
+size_t lu_workspace_bytes(int n, int grid, bool a_on_device);
 // extra resources (batch / server) released by ls_destroy
 void extra_destroy(ls_ctx *c);
 }  // namespace lsi

@@ -255,6 +255,24 @@ struct BcgKernels {
 };
 BcgKernels bcg_kernels();
 
+// ---- LU with partial pivoting (k_lu.cu) --------------------------------------------------
+struct LuArgs {
+    int n;
+    double *W;                    // [A | b], n x (n + 1), row-major, leading dimension ld
+    long long ld;
+    int *ipiv;                    // the row swapped with row k at step k
+    double *x;                    // the solution
+    double *cand_v;               // [CTA] pivot candidates: |value| and row
+    int *cand_i;
+    GridBar *bar;
+    State *st;
+};
+struct LuKernels {
+    void *factor, *backsolve;     // factor takes (LuArgs, k0, k1)
+    int block;
+};
+LuKernels lu_kernels();
+
 // ---- block GMRES (k_bgmres.cu) -----------------------------------------------------------
 constexpr int BGM_MAX_S = 16;
 constexpr int BGM_MAX_MS = 256;       // m * s at most
