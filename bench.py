@@ -112,6 +112,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp32_issue_peak():
+    """FP32 instructions per second of the whole GPU: SMs x 128 lanes x max SM clock."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    mhz = 2070.0
+    try:
+        import subprocess
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout.split()
+        mhz = float(out[0]) if out else mhz
+    except Exception:
+        pass
+    return props.multi_processor_count * 128 * mhz * 1e6
+
+
 # ---------------------------------------------------------------------------
 # profile evidence for the roofline's traffic field
 # ---------------------------------------------------------------------------
@@ -257,6 +272,7 @@ def run_native(args):
                 "products": i3["iters"], "true_rel_res": i3["true_rel_res"],
                 "rel_err_vs_xstar": float(torch.linalg.norm(x3 - xs2) / torch.linalg.norm(xs2))}
     del x3
+    peaks_hbm = load_peaks()[0]["hbm_gbs"]
     # Jacobi (the paper's stationary method) on the same nonsymmetric system:
     # its iteration matrix I - D^-1 A has spectral radius about 1/4
     x4 = torch.zeros(N, dtype=torch.float64, device=dev)
@@ -264,7 +280,8 @@ def run_native(args):
     jacobi = {"status": B.ls_strerror(st4), "time_to_1e-10_ms": round(i4["time_ms"], 3),
               "products": i4["iters"], "rel_res": i4["rel_res"],
               "rel_err_vs_xstar": float(torch.linalg.norm(x4 - xs2) / torch.linalg.norm(xs2)),
-              "ms_per_product": round(i4["time_ms"] / max(i4["iters"], 1), 4)}
+              "ms_per_product": round(i4["time_ms"] / max(i4["iters"], 1), 4),
+              "hbm_frac_whole_solve": round(i4["bytes_moved"] / i4["time_ms"] / 1e6 / peaks_hbm, 4)}
     del x4
     # forward Gauss-Seidel on the same system: a residual product and a
     # blocked triangular solve over the lower half of A per sweep
@@ -273,7 +290,8 @@ def run_native(args):
     gauss_seidel = {"status": B.ls_strerror(st5), "time_to_1e-10_ms": round(i5["time_ms"], 3),
                     "residual_tests": i5["iters"], "rel_res": i5["rel_res"],
                     "rel_err_vs_xstar": float(torch.linalg.norm(x5 - xs2) / torch.linalg.norm(xs2)),
-                    "A_passes": round(i5["bytes_moved"] / (8.0 * N * N), 1)}
+                    "A_passes": round(i5["bytes_moved"] / (8.0 * N * N), 1),
+                    "hbm_frac_whole_solve": round(i5["bytes_moved"] / i5["time_ms"] / 1e6 / peaks_hbm, 4)}
     del x5
     # block CG (O'Leary) with 8 right-hand sides on the SPD system: one block
     # product Q = A P per step reads A once for all columns
@@ -287,7 +305,11 @@ def run_native(args):
                 "block_steps": i6["iters"], "ms_per_rhs": round(i6["time_ms"] / S_BCG, 2),
                 "max_true_rel_res": i6["true_rel_res"],
                 "rel_err_vs_xstar": float(torch.linalg.norm(X8 - Xs8.t()) / torch.linalg.norm(Xs8)),
-                "ms_per_step": round(i6["time_ms"] / max(i6["iters"], 1), 3)}
+                "ms_per_step": round(i6["time_ms"] / max(i6["iters"], 1), 3),
+                "fp32_issue_frac": round(12.0 * N * N * S_BCG / (i6["time_ms"] / max(i6["iters"], 1) * 1e-3)
+                                         / fp32_issue_peak(), 4),
+                "note": "block product: 12 FP32 instructions per element of A and column (double-single); "
+                        "peak = 152 SMs x 128 lanes x SM max clock"}
     del X8, B8, Xs8
     # block GMRES(10) with 8 right-hand sides on the nonsymmetric system
     Xs8 = torch.from_numpy(_inputs.solution(N, seed=3, nrhs=S_BCG).T.copy()).to(dev)
@@ -300,6 +322,8 @@ def run_native(args):
                    "max_true_rel_res": i7["true_rel_res"],
                    "rel_err_vs_xstar": float(torch.linalg.norm(X8 - Xs8.t()) / torch.linalg.norm(Xs8))}
     del X8, B8, Xs8
+    # the paper's direct method (LU with partial pivoting) at n = 8192
+    lu_direct = lu_measure(B, ctx, dev, 8192)
 
     # accuracy of the timed results (checked, not assumed)
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
@@ -409,6 +433,7 @@ def run_native(args):
             "gauss_seidel_nonsym": gauss_seidel,
             "block_cg_spd": block_cg,
             "block_gmres_nonsym": block_gmres,
+            "lu_direct": lu_direct,
             "gemv_f64_native": gemv_native,
             "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
@@ -770,6 +795,37 @@ def run_block_cg_steps(args):
     B.ls_destroy(ctx)
 
 
+def lu_measure(B, ctx, dev, n):
+    """The direct method on the nonsymmetric family 2I + G/(2 sqrt n) at n: time,
+    algorithmic bytes of the unblocked elimination (16 n^3 / 3) per second."""
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    A = inputs.nonsym_matrix(n, seed=5, device=dev)
+    xs = torch.from_numpy(inputs.solution(n, seed=5)).to(dev)
+    b = A @ xs
+    for _ in range(2):   # the first call sizes the workspace
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        st, info = B.ls_lu_solve(ctx, A, b, x)
+    byts = 16.0 * n ** 3 / 3.0
+    peaks, src = load_peaks()
+    return {"status": B.ls_strerror(st), "n": n, "time_ms": round(info["time_ms"], 2),
+            "algorithmic_GB/s": round(byts / info["time_ms"] / 1e6, 1),
+            "hbm_frac": round(byts / info["time_ms"] / 1e6 / peaks["hbm_gbs"], 4),
+            "true_rel_res": info["true_rel_res"],
+            "rel_err_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs)),
+            "note": "unblocked right-looking elimination: each step streams the trailing block (16 n^3/3 bytes)"}
+
+
+def run_lu_only(args):
+    """The direct method alone (timing and ncu captures) at --n."""
+    import torch
+    from paper_1511_07207_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    ctx = B.ls_create(0, torch.cuda.current_stream(dev))
+    print(json.dumps(dict(kernel="lu", **lu_measure(B, ctx, dev, args.n))))
+    B.ls_destroy(ctx)
+
+
 def run_batch_only(args):
     """The batched engine alone (ncu captures of its kernels): the first
     --count systems of the 512-system recipe, one ls_batch_solve."""
@@ -801,7 +857,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
     ap.add_argument("--cpu-cg-sample", type=int, default=600)
-    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary", "block_cg"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary", "block_cg", "lu"], default=None,
                     help="kernel-only timing (small cases for ncu captures): one GEMV format, "
                          "the batched engine alone on --count systems, or --reps sweeps of a "
                          "stationary method")
@@ -825,6 +881,8 @@ def main():
         run_stationary(args)
     elif args.kernel == "block_cg":
         run_block_cg_steps(args)
+    elif args.kernel == "lu":
+        run_lu_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -37,7 +37,8 @@ namespace lsi {
 
 namespace {
 
-constexpr int LT = 256;            // threads per CTA
+constexpr int LT = 512;            // threads per CTA (16 warps: enough loads in flight)
+constexpr int LU_UNROLL = 4;       // elements of a row a lane loads before it computes
 constexpr int LW = LT / 32;        // warps per CTA
 constexpr int LB = 64;             // rows per back-substitution block
 
@@ -67,7 +68,7 @@ __device__ void publish_cand(const LuArgs &a, Cand mine, Cand *red) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(LT) lu_factor_kernel(LuArgs a, int k0, int k1) {
+__global__ void __launch_bounds__(LT, 1) lu_factor_kernel(LuArgs a, int k0, int k1) {
     __shared__ Cand red[LW];
     __shared__ int v_s;
     State *st = a.st;
@@ -119,10 +120,23 @@ __global__ void __launch_bounds__(LT) lu_factor_kernel(LuArgs a, int k0, int k1)
             const double l = __ldcg(&wi[k]) / piv;
             __syncwarp();
             double next = 0.0;   // w_i,k+1 after the update (lane 0 owns column k + 1)
-            for (int j = k + 1 + lane; j <= n; j += 32) {
-                const double w = __dsub_rn(__ldcg(&wi[j]), __dmul_rn(l, __ldcg(&wk[j])));
-                wi[j] = w;
-                if (j == k + 1) next = w;
+            for (int j0 = k + 1 + lane; j0 <= n; j0 += 32 * LU_UNROLL) {
+                double wv[LU_UNROLL], kv[LU_UNROLL];
+#pragma unroll
+                for (int u = 0; u < LU_UNROLL; u++) {
+                    const int j = j0 + 32 * u;
+                    wv[u] = j <= n ? __ldcg(&wi[j]) : 0.0;
+                    kv[u] = j <= n ? __ldcg(&wk[j]) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < LU_UNROLL; u++) {
+                    const int j = j0 + 32 * u;
+                    if (j <= n) {
+                        const double w = __dsub_rn(wv[u], __dmul_rn(l, kv[u]));
+                        wi[j] = w;
+                        if (j == k + 1) next = w;
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0) {
@@ -134,7 +148,7 @@ __global__ void __launch_bounds__(LT) lu_factor_kernel(LuArgs a, int k0, int k1)
     }
 }
 
-__global__ void __launch_bounds__(LT) lu_backsolve_kernel(LuArgs a) {
+__global__ void __launch_bounds__(LT, 1) lu_backsolve_kernel(LuArgs a) {
     __shared__ double s[LB], xs[LB];
     State *st = a.st;
     count_launch(st);
