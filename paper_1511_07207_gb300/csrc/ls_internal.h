@@ -268,8 +268,9 @@ struct LuArgs {
     State *st;
 };
 struct LuKernels {
-    void *factor, *backsolve;     // factor takes (LuArgs, k0, k1)
-    int block;
+    void *factor, *backsolve;     // factor takes (LuArgs, k0, k1): one panel's steps
+    void *laswp, *u12, *trail;    // (LuArgs, k0, nb), (LuArgs, k0, nb), (LuArgs, k0)
+    int block, nb, tile;
 };
 LuKernels lu_kernels();
 

@@ -1,6 +1,8 @@
 // ls_lu.cu -- the host driver of the direct method (ls_lu_solve, ls_lu_factor):
-// the working matrix [A | b] in the workspace, the elimination in chunks of
-// steps (cooperative launches), the back substitution, the residual check.
+// the working matrix [A | b] in the workspace, the elimination by panels
+// (per panel: the cooperative panel factorization, the row swaps elsewhere,
+// the pivot rows right of the panel, the trailing update), the back
+// substitution, the residual check.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,7 +15,6 @@ using namespace lsi;
 
 namespace {
 
-constexpr int LU_CHUNK = 512;   // elimination steps per launch
 
 struct LuLayout {
     double *W, *x, *r, *cand_v, *Astage;
@@ -67,10 +68,23 @@ int lu_run(ls_ctx *c, int n, const double *A, long long lda, const double *b, Lu
     a.st = c->st;
     const LuKernels K = lu_kernels();
     e = cudaEventRecord(c->ev0, c->stream);
-    for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += LU_CHUNK) {
-        int kk0 = k0, kk1 = std::min(n, k0 + LU_CHUNK);
-        void *args[] = {&a, &kk0, &kk1};
-        e = cudaLaunchCooperativeKernel(K.factor, dim3(c->K.coop_grid), dim3(K.block), args, 0, c->stream);
+    for (int k0 = 0; k0 < n && e == cudaSuccess; k0 += K.nb) {
+        int kk0 = k0, kk1 = std::min(n, k0 + K.nb), nb = kk1 - kk0;
+        void *fargs[] = {&a, &kk0, &kk1};
+        e = cudaLaunchCooperativeKernel(K.factor, dim3(c->K.coop_grid), dim3(K.block), fargs, 0, c->stream);
+        const int cols_right = n + 1 - kk1, rows_below = n - kk1;
+        const int g = std::max(1, std::min((n + 1 + 255) / 256, 4 * c->num_sms));
+        void *sargs[] = {&a, &kk0, &nb};
+        if (e == cudaSuccess) e = cudaLaunchKernel(K.laswp, dim3(g), dim3(256), sargs, 0, c->stream);
+        if (e == cudaSuccess && cols_right > 0) {
+            const int gu = std::max(1, std::min((cols_right + 255) / 256, 4 * c->num_sms));
+            e = cudaLaunchKernel(K.u12, dim3(gu), dim3(256), sargs, 0, c->stream);
+        }
+        if (e == cudaSuccess && rows_below > 0 && cols_right > 0) {
+            dim3 tg((cols_right + K.tile - 1) / K.tile, (rows_below + K.tile - 1) / K.tile);
+            void *targs[] = {&a, &kk0};
+            e = cudaLaunchKernel(K.trail, tg, dim3(256), targs, 0, c->stream);
+        }
     }
     if (e == cudaSuccess && solve) {
         void *args[] = {&a};
@@ -163,7 +177,8 @@ extern "C" int ls_lu_solve(ls_ctx *c, int n, const double *A, int64_t lda, const
     }
     c->launches_total += (long long)st.launches;
     const double nn = (double)n;
-    fill_info(info, st, status, ms, 16.0 * nn * nn * nn / 3.0, (long long)st.launches);
+    // one read and one write of the trailing block per panel of LU_NB = 32 columns
+    fill_info(info, st, status, ms, 16.0 * nn * nn * nn / (3.0 * 32.0), (long long)st.launches);
     return status;
 }
 
