@@ -51,7 +51,8 @@ namespace lsi {
 namespace {
 
 constexpr int LT = 512;            // threads per CTA (16 warps: enough loads in flight)
-constexpr int LU_ROWS = 2;         // rows a warp loads before it computes (panel steps)
+constexpr int LU_ROWS = 4;         // rows a warp loads before it computes (panel steps)
+constexpr int U12_T = 128;         // threads per CTA of lu_u12_kernel (32 columns)
 constexpr int LU_NB = 32;          // panel width
 constexpr int LW = LT / 32;        // warps per CTA
 constexpr int LB = 64;             // rows per back-substitution block
@@ -193,9 +194,12 @@ __global__ void __launch_bounds__(256) lu_laswp_kernel(LuArgs a, int k0, int nb)
 }
 
 // The pivot rows k0 .. k0 + nb - 1 right of the panel: u_rj -= l_rt u_tj for
-// t = k0 .. r - 1 in order (a thread a column).
-__global__ void __launch_bounds__(256) lu_u12_kernel(LuArgs a, int k0, int nb) {
-    __shared__ double Lp[LU_NB][LU_NB];   // the panel's multipliers l_rt, zero past nb
+// t = k0 .. r - 1 in order.  Four lanes a column (lane q of the quad holds
+// rows q, q + 4, ...; the owner of row t hands u_tj to the others by a
+// shuffle once it is final), so there are enough warps to keep the FP64
+// pipes of every SM busy.
+__global__ void __launch_bounds__(U12_T) lu_u12_kernel(LuArgs a, int k0, int nb) {
+    __shared__ double Lp[LU_NB][LU_NB + 1];   // the panel's multipliers l_rt, zero past nb
     State *st = a.st;
     count_launch(st);
     if (*(volatile int *)&st->status == LS_BREAKDOWN) return;
@@ -207,19 +211,33 @@ __global__ void __launch_bounds__(256) lu_u12_kernel(LuArgs a, int k0, int nb) {
         Lp[r][t] = (r < nb && t < r) ? W[(long long)(k0 + r) * ld + k0 + t] : 0.0;
     }
     __syncthreads();
-    for (long long j = k0 + nb + (long long)blockIdx.x * blockDim.x + threadIdx.x; j <= n;
-         j += (long long)gridDim.x * blockDim.x) {
+    const int q = threadIdx.x & 3, lane = threadIdx.x & 31;
+    const long long ncols = (long long)n + 1 - (k0 + nb);
+    const int cpb = U12_T / 4;   // columns a CTA takes at a time
+    // the loop bound is the same for the whole CTA, so every lane reaches the shuffles
+    for (long long c0 = (long long)blockIdx.x * cpb; c0 < ncols; c0 += (long long)gridDim.x * cpb) {
+        const long long jj = c0 + threadIdx.x / 4;
+        const bool on = jj < ncols;
+        const long long j = k0 + nb + jj;
         // rows past the panel's nb (a short last panel) stay zero and are not stored
-        double u[LU_NB];
+        double u[LU_NB / 4];
 #pragma unroll
-        for (int r = 0; r < LU_NB; r++) u[r] = r < nb ? W[(long long)(k0 + r) * ld + j] : 0.0;
+        for (int x = 0; x < LU_NB / 4; x++) {
+            const int r = q + 4 * x;
+            u[x] = (on && r < nb) ? W[(long long)(k0 + r) * ld + j] : 0.0;
+        }
 #pragma unroll
-        for (int t = 0; t < LU_NB; t++)
+        for (int t = 0; t < LU_NB - 1; t++) {
+            const double ut = __shfl_sync(0xffffffffu, u[t / 4], (lane & ~3) | (t & 3));
 #pragma unroll
-            for (int r = t + 1; r < LU_NB; r++) u[r] = __dsub_rn(u[r], __dmul_rn(Lp[r][t], u[t]));
+            for (int x = 0; x < LU_NB / 4; x++)
+                if (q + 4 * x > t) u[x] = __dsub_rn(u[x], __dmul_rn(Lp[q + 4 * x][t], ut));
+        }
 #pragma unroll
-        for (int r = 0; r < LU_NB; r++)
-            if (r < nb) W[(long long)(k0 + r) * ld + j] = u[r];
+        for (int x = 0; x < LU_NB / 4; x++) {
+            const int r = q + 4 * x;
+            if (on && r < nb) W[(long long)(k0 + r) * ld + j] = u[x];
+        }
     }
 }
 
@@ -319,6 +337,7 @@ LuKernels lu_kernels() {
     K.u12 = reinterpret_cast<void *>(&lu_u12_kernel);
     K.trail = reinterpret_cast<void *>(&lu_trail_kernel);
     K.nb = LU_NB;
+    K.u12_block = U12_T;
     K.tile = TT;
     K.block = LT;
     return K;

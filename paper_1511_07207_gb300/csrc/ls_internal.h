@@ -270,7 +270,7 @@ struct LuArgs {
 struct LuKernels {
     void *factor, *backsolve;     // factor takes (LuArgs, k0, k1): one panel's steps
     void *laswp, *u12, *trail;    // (LuArgs, k0, nb), (LuArgs, k0, nb), (LuArgs, k0)
-    int block, nb, tile;
+    int block, nb, tile, u12_block;
 };
 LuKernels lu_kernels();
 

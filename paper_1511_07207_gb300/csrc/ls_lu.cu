@@ -76,9 +76,10 @@ int lu_run(ls_ctx *c, int n, const double *A, long long lda, const double *b, Lu
         const int g = std::max(1, std::min((n + 1 + 255) / 256, 4 * c->num_sms));
         void *sargs[] = {&a, &kk0, &nb};
         if (e == cudaSuccess) e = cudaLaunchKernel(K.laswp, dim3(g), dim3(256), sargs, 0, c->stream);
-        if (e == cudaSuccess && cols_right > 0) {
-            const int gu = std::max(1, std::min((cols_right + 255) / 256, 4 * c->num_sms));
-            e = cudaLaunchKernel(K.u12, dim3(gu), dim3(256), sargs, 0, c->stream);
+        if (e == cudaSuccess && cols_right > 0) {   // four threads a column
+            const int cpb = K.u12_block / 4;
+            const int gu = std::max(1, std::min((cols_right + cpb - 1) / cpb, 8 * c->num_sms));
+            e = cudaLaunchKernel(K.u12, dim3(gu), dim3(K.u12_block), sargs, 0, c->stream);
         }
         if (e == cudaSuccess && rows_below > 0 && cols_right > 0) {
             dim3 tg((cols_right + K.tile - 1) / K.tile, (rows_below + K.tile - 1) / K.tile);
