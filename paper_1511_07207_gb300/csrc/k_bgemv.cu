@@ -18,6 +18,7 @@
 
 #include "ls_device.cuh"
 #include "ls_internal.h"
+#include "split_pair.h"
 
 namespace lsi {
 
@@ -80,9 +81,7 @@ __global__ void bgemv_split_kernel(int n, int s, int S, const double *__restrict
         const int j = (int)(e / ldp);
         const long long c = e % ldp;
         const double v = (j < s && c < n) ? P[(long long)j * ld + c] : 0.0;
-        const float h = __double2float_rn(v);
-        Ph[e] = h;
-        Pl[e] = __double2float_rn(v - (double)h);
+        split_pair(v, Ph[e], Pl[e]);
     }
 }
 

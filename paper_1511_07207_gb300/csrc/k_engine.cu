@@ -16,6 +16,7 @@
 #include "ls_device.cuh"
 #include "ls_engine.h"
 #include "ls_internal.h"
+#include "split_pair.h"
 
 namespace lsi {
 
@@ -661,7 +662,8 @@ __device__ bool res_task(const EngineDev &E, const ProdSmem &M, int &seq, int *f
 }
 
 // At admission (START), the FP32 product tasks' tiles of A are split instead:
-// A = A32 + A32lo, rows [r0, r1) x columns [k0, k1), a warp per row.
+// A = A32 + A32lo, rows [r0, r1) x columns [k0, k1), a warp per row
+// (split_pair: integer operations on the bit pattern, off the FP64 pipe).
 __device__ __forceinline__ void convert_task(const SlotDesc &D, const Task &T) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = T.r0 + warp; r < T.r1; r += P32_T / 32) {
@@ -674,11 +676,7 @@ __device__ __forceinline__ void convert_task(const SlotDesc &D, const Task &T) {
             for (int u = 0; u < 4; u++) v[u] = kb + 32 * u < T.k1 ? a[kb + 32 * u] : 0.0;
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                if (kb + 32 * u < T.k1) {
-                    const float hi = __double2float_rn(v[u]);
-                    a32[kb + 32 * u] = hi;
-                    alo[kb + 32 * u] = __double2float_rn(v[u] - (double)hi);
-                }
+                if (kb + 32 * u < T.k1) split_pair(v[u], a32[kb + 32 * u], alo[kb + 32 * u]);
             }
         }
     }

@@ -30,6 +30,7 @@
 
 #include "ls_device.cuh"
 #include "ls_internal.h"
+#include "split_pair.h"
 
 namespace lsi {
 
@@ -766,18 +767,58 @@ bool make_tensor_map_ds(MatDesc *h, const float *hi, const float *lo, int rows, 
     return true;
 }
 
-// hi = fp32(A), lo = fp32(A - hi): one pass over A, done once per solve.
+// hi = fp32(A), lo = fp32(A - hi): one pass over A, done once per solve
+// (split_pair: integer operations on the bit pattern, off the FP64 pipe).
+// Any alignment: a CTA a row, a thread an element.
 __global__ void split_f64_kernel(int rows, int cols, const double *__restrict__ A, long long lda,
                                  float *__restrict__ hi, float *__restrict__ lo, long long ld) {
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const double *a = A + (long long)row * lda;
         float *h = hi + (long long)row * ld, *l = lo + (long long)row * ld;
-        for (int j = threadIdx.x; j < cols; j += blockDim.x) {
-            const double v = a[j];
-            const float vh = __double2float_rn(v);
-            h[j] = vh;
-            l[j] = __double2float_rn(v - (double)vh);
+        for (int j = threadIdx.x; j < cols; j += blockDim.x) split_pair(__ldcs(&a[j]), h[j], l[j]);
+    }
+}
+
+// The same with 16-byte accesses: A rows 16-byte aligned (lda even), hi and lo
+// rows 16-byte aligned (ld a multiple of 4).  A thread takes SPLIT_U groups of
+// four elements at a time (two 16-byte loads each, all issued before the
+// arithmetic); the last cols % 4 elements of a row go one a thread.  A is read
+// once and streamed past the caches.
+constexpr int SPLIT_U = 2;
+__global__ void __launch_bounds__(256) split_f64_vec_kernel(int rows, int cols, const double *__restrict__ A,
+                                                            long long lda, float *__restrict__ hi,
+                                                            float *__restrict__ lo, long long ld) {
+    const int q4 = cols >> 2;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const double2 *a = reinterpret_cast<const double2 *>(A + (long long)row * lda);
+        float4 *h = reinterpret_cast<float4 *>(hi + (long long)row * ld);
+        float4 *l = reinterpret_cast<float4 *>(lo + (long long)row * ld);
+        for (int q0 = threadIdx.x; q0 < q4; q0 += SPLIT_U * blockDim.x) {
+            double2 v[SPLIT_U][2];
+#pragma unroll
+            for (int u = 0; u < SPLIT_U; u++) {
+                const int q = q0 + u * blockDim.x;
+                if (q < q4) {
+                    v[u][0] = __ldcs(&a[2 * q]);
+                    v[u][1] = __ldcs(&a[2 * q + 1]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SPLIT_U; u++) {
+                const int q = q0 + u * blockDim.x;
+                if (q < q4) {
+                    float4 hv, lv;
+                    split_pair(v[u][0].x, hv.x, lv.x);
+                    split_pair(v[u][0].y, hv.y, lv.y);
+                    split_pair(v[u][1].x, hv.z, lv.z);
+                    split_pair(v[u][1].y, hv.w, lv.w);
+                    h[q] = hv;
+                    l[q] = lv;
+                }
+            }
         }
+        for (int j = 4 * q4 + threadIdx.x; j < cols; j += blockDim.x)
+            split_pair(__ldcs(&A[(long long)row * lda + j]), hi[(long long)row * ld + j], lo[(long long)row * ld + j]);
     }
 }
 
@@ -785,7 +826,10 @@ cudaError_t split_f64_launch(int rows, int cols, const double *A, long long lda,
                              long long ld, int num_sms, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     const int grid = rows < 8 * num_sms ? rows : 8 * num_sms;
-    split_f64_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, hi, lo, ld);
+    const bool vec = ((uintptr_t)A & 15) == 0 && (lda & 1) == 0 && ((uintptr_t)hi & 15) == 0 &&
+                     ((uintptr_t)lo & 15) == 0 && (ld & 3) == 0;
+    if (vec) split_f64_vec_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, hi, lo, ld);
+    else split_f64_kernel<<<grid, 256, 0, s>>>(rows, cols, A, lda, hi, lo, ld);
     return cudaGetLastError();
 }
 

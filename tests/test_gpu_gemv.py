@@ -130,3 +130,54 @@ def test_gemv_lowp(ctx, gpu, oracle, dtype, rows, cols):
     ref = Ah @ x.astype(np.float64)
     bound = 2 * gamma(cols + 2, 2.0 ** -24) * (np.abs(Ah) @ np.abs(x.astype(np.float64)))
     assert np.all(np.abs(y.cpu().numpy().astype(np.float64) - ref) <= bound + 1e-30)
+
+
+def _split_edge_values(rng, count):
+    """Random bit patterns, random fractions at every binary exponent from
+    -80 to 130, rounding ties and carries of the 29 dropped bits, and
+    special values (zeros, subnormals, overflow to infinity, infinities, NaN)."""
+    words = [rng.integers(0, 2 ** 63, size=count // 3, dtype=np.uint64) * np.uint64(2)
+             + rng.integers(0, 2, size=count // 3, dtype=np.uint64)]
+    E = rng.integers(-80, 131, size=count // 3).astype(np.uint64)
+    frac = rng.integers(0, 2 ** 52, size=count // 3, dtype=np.uint64)
+    sign = rng.integers(0, 2, size=count // 3, dtype=np.uint64)
+    words.append((sign << np.uint64(63)) | ((E + np.uint64(1023)) << np.uint64(52)) | frac)
+    ties = []
+    for e in range(-80, 131):
+        for keep in (0, 1, 2, 3, 0x7FFFFE, 0x7FFFFF):
+            for R in (0, 1, (1 << 28) - 1, 1 << 28, (1 << 28) + 1, (1 << 29) - 1):
+                for s in (0, 1):
+                    ties.append((s << 63) | ((e + 1023) << 52) | (keep << 29) | R)
+    words.append(np.array(ties, dtype=np.uint64))
+    v = np.concatenate(words).view(np.float64)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, 1e-300, 1e300,
+                        3.4028235677973366e38, -3.4028235677973366e38, np.inf, -np.inf, np.nan, 1.0 / 3.0])
+    return np.concatenate([v, special])
+
+
+@pytest.mark.parametrize("cols,pad", [(1032, 0), (1029, 0), (1031, 1)])
+def test_split_edge_values_bit_exact(ctx, gpu, cols, pad):
+    """The split's hi and lo equal fp32(a) and fp32(a - hi) bit for bit on every
+    input class, through the 16-byte path (even leading dimension) and the
+    element path (odd leading dimension)."""
+    rng = np.random.default_rng(cols)
+    vals = _split_edge_values(rng, 150000)
+    rows = -(-vals.size // cols)
+    full = np.zeros((rows, cols + pad))
+    flat = np.zeros(rows * cols)
+    flat[:vals.size] = vals
+    full[:, :cols] = flat.reshape(rows, cols)
+    A = full[:, :cols]
+    Ad = torch.from_numpy(full).to(gpu)[:, :cols]
+    ldp = (cols + 3) // 4 * 4
+    pair = torch.full((2 * rows, ldp), np.nan, dtype=torch.float32, device=gpu)
+    assert B.ls_split_f64(ctx, Ad, pair[:, :cols]) == B.LS_OK
+    hi = pair[:rows, :cols].cpu().numpy()
+    lo = pair[rows:, :cols].cpu().numpy()
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref_hi = A.astype(np.float32)
+        ref_lo = (A - ref_hi.astype(np.float64)).astype(np.float32)
+    for got, ref in ((hi, ref_hi), (lo, ref_lo)):
+        both_nan = np.isnan(got) & np.isnan(ref)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        assert np.array_equal(got.view(np.uint32)[~both_nan], ref.view(np.uint32)[~both_nan])
