@@ -702,9 +702,18 @@ def run_kernel(args):
     dt = {"f64": B.LS_F64, "pair": B.LS_F64_PAIR, "bf16": B.LS_BF16_IR, "fp8": B.LS_FP8_IR,
           "f32": B.LS_F32_IR}[args.dtype]
     scale = None
+    extra = {}
     if dt == B.LS_F64_PAIR:
         A = torch.empty((2 * n, (n + 3) // 4 * 4), dtype=torch.float32, device=dev)
         assert B.ls_split_f64(ctx, A64, A[:, :n]) == B.LS_OK
+        # the split itself (once per solve): 8 bytes read and 8 written per element
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        assert B.ls_split_f64(ctx, A64, A[:, :n]) == B.LS_OK
+        e1.record()
+        torch.cuda.synchronize()
+        sms = e0.elapsed_time(e1)
+        extra = {"split_ms": round(sms, 4), "split_GB/s": round(16.0 * n * n / sms / 1e6, 1)}
         del A64
         A = A[:n, :n]
         x = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
@@ -731,7 +740,7 @@ def run_kernel(args):
     print(json.dumps({"kernel": "gemv", "dtype": args.dtype, "n": n, "reps": args.reps,
                       "ms": round(ms, 5), "GB/s": round(byts / ms / 1e6, 1),
                       "hbm_frac": round(byts / ms / 1e6 / peaks["hbm_gbs"], 4),
-                      "peak_source": src}))
+                      "peak_source": src, **extra}))
     B.ls_destroy(ctx)
 
 
