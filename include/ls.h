@@ -273,15 +273,18 @@ int ls_block_gmres_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda
  * |a_vk| (the first one on ties) is swapped with row k, the sub-column is
  * divided by the pivot and the rank-1 update is subtracted from the trailing
  * block; b is carried along as an extra column, so L y = P b is done during
- * the elimination; then U x = y.  FP64, unblocked: every element of L, U
- * and y is bit for bit what the same elimination gives in plain FP64 (IEEE
- * division, multiply and subtract not fused).  After the solve the true
+ * the elimination; then U x = y.  FP64, run by panels of 32 columns (the
+ * panel's pivot steps, its row swaps on the other columns, the pivot rows
+ * right of it, the trailing update), which only regroups the elimination's
+ * operations: every element of L, U and y is bit for bit what the plain
+ * elimination gives in FP64 (IEEE division, multiply and subtract not
+ * fused, the updates of each element in step order).  After the solve the true
  * residual ||b - A x|| is formed (info->rel_res, true_rel_res; info->iters =
  * 0).  A zero pivot returns LS_BREAKDOWN with x unchanged; a residual that
  * is not finite returns LS_ERR_NAN.  A row-major n x n (host or device), b
  * and x n vectors; opts may be NULL; opts->precision must be LS_F64.  The
- * elimination streams the trailing block once per step, 16 n^3 / 3 bytes in
- * all: HBM-bound.
+ * elimination is n^3 / 3 updates of two FP64 instructions each, bound by the
+ * FP64 pipe; the trailing block crosses HBM once per panel.
  */
 int ls_lu_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *x,
                 const ls_opts *opts, ls_info *info);
@@ -291,8 +294,10 @@ int ls_lu_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *
  * dimension ldlu >= n) receives the unit lower factor L below the diagonal
  * and U on and above it, rows in pivoted order; ipiv[k] the row swapped with
  * row k at step k; y = L^-1 P b.  Outputs may be host or device memory.
- * Returns LS_BREAKDOWN on a zero pivot (outputs as far as the elimination
- * got), LS_ERR_ARG on bad sizes or NULL pointers.
+ * Returns LS_BREAKDOWN on a zero pivot at step k; then only the columns and
+ * ipiv entries of the panels of 32 steps completed before k are final (the
+ * rest of LU, ipiv and y is partial work).  LS_ERR_ARG on bad sizes or NULL
+ * pointers.
  */
 int ls_lu_factor(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *LU,
                  int64_t ldlu, int *ipiv, double *y);
