@@ -17,6 +17,7 @@ import test_oracle_cg as tcg
 import test_oracle_ge_quant as tgq
 import test_oracle_gauss_seidel as tgs
 import test_oracle_gmres as tgm
+import test_oracle_golden as tgo
 import test_oracle_jacobi as tja
 import test_oracle_mixed as tmx
 
@@ -96,6 +97,17 @@ MUTATIONS = {
     "block_gmres_backsolve_index": ("for (int q = i + 1; q < k; q++) v -= HB(i, q) * y[q];",
                                     "for (int q = i + 1; q < k; q++) v -= HB(q, i) * y[q];",
                                     lambda o: tbg.test_block_gmres_is_block_krylov_minimiser(o, 2, 3)),
+    # caught by the hand-derived worked examples (tests/golden)
+    "ge_last_max_on_ties": ("if (a > best) { best = a; v = i; }", "if (a >= best) { best = a; v = i; }",
+                            lambda o: tgo.test_lu_worked_example(o, "tie_")),
+    "ge_swap_leaves_L": ("            for (int j = 0; j < n; j++) {\n                double t = W[(long)k * n + j];",
+                         "            for (int j = k; j < n; j++) {\n                double t = W[(long)k * n + j];",
+                         lambda o: tgo.test_lu_worked_example(o, "")),
+    "cg_beta_inverted": ("double beta = rho_new / rho;", "double beta = rho / rho_new;",
+                         lambda o: tgo.test_cg_worked_example(o)),
+    "bicgstab_x_drops_omega_s": ("for (int i = 0; i < n; i++) x[i] += alpha * p[i] + omega * s[i];",
+                                 "for (int i = 0; i < n; i++) x[i] += alpha * p[i];",
+                                 lambda o: tgo.test_bicgstab_worked_example(o)),
 }
 
 
