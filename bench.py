@@ -167,6 +167,24 @@ def profiled_traffic(name):
 # ---------------------------------------------------------------------------
 # inputs
 # ---------------------------------------------------------------------------
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (each rank's own time: the job ends with
+    the slowest rank).  An all-reduce (MAX) over the default process group
+    when world > 1, the value itself otherwise."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units all ranks processed per second over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def make_inputs(device):
     import torch
     from paper_1511_07207_gb300 import inputs
@@ -257,12 +275,9 @@ def run_native(args):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     ms_per_step = ms_max / args.steps
-    value = world * 2 * args.steps / (ms_max / 1e3)
+    value = whole_job_rate(2 * args.steps, world, ms_max)
 
     # BiCGSTAB (the paper's fastest iterative method) on the nonsymmetric
     # system, timed outside the step: time to 1e-10 and products
@@ -385,10 +400,8 @@ def run_native(args):
             step_e2e()
         barrier()
         te = time.perf_counter() - t0
-        tt = torch.tensor([te], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": round(world * 2 * k_e2e / float(tt.item()), 4), "unit": "solves/s",
+        te_max = max_over_ranks(te, world, dev)
+        e2e = {"value": round(whole_job_rate(2 * k_e2e, world, te_max * 1e3), 4), "unit": "solves/s",
                "h2d_bytes_per_step": int(2 * (8 * N * N + 8 * N)),
                "d2h_bytes_per_step": int(2 * 8 * N)}
 
