@@ -46,3 +46,53 @@ def test_create_without_gpu_fails_cleanly(lslib):
     st = lslib.ls_create(ctypes.byref(h), 0, None)
     assert st in (binding.LS_ERR_CUDA, binding.LS_ERR_UNSUPPORTED)
     assert not h.value
+
+
+def _null_context_calls(lib):
+    """Every entry that takes a context (or a server), called with NULL and
+    otherwise plausible arguments."""
+    info, o = binding.ls_info(), binding.make_opts()
+    buf = (ctypes.c_double * 16)()
+    ib = (ctypes.c_int * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    pi = ctypes.cast(ib, ctypes.c_void_p)
+    oi = (ctypes.byref(o), ctypes.byref(info))
+    return {
+        "ls_workspace_size": lambda: lib.ls_workspace_size(None, 1, 4, 1, ctypes.byref(o), 0,
+                                                           ctypes.byref(ctypes.c_size_t())),
+        "ls_set_workspace": lambda: lib.ls_set_workspace(None, p, 128),
+        "ls_cg_solve": lambda: lib.ls_cg_solve(None, 4, p, 4, p, p, *oi),
+        "ls_gmres_solve": lambda: lib.ls_gmres_solve(None, 4, p, 4, p, p, *oi),
+        "ls_bicgstab_solve": lambda: lib.ls_bicgstab_solve(None, 4, p, 4, p, p, *oi),
+        "ls_jacobi_solve": lambda: lib.ls_jacobi_solve(None, 4, p, 4, p, p, *oi),
+        "ls_gauss_seidel_solve": lambda: lib.ls_gauss_seidel_solve(None, 4, p, 4, p, p, *oi),
+        "ls_lu_solve": lambda: lib.ls_lu_solve(None, 4, p, 4, p, p, *oi),
+        "ls_block_cg_solve": lambda: lib.ls_block_cg_solve(None, 2, 2, p, 2, p, 2, p, 2, *oi),
+        "ls_block_gmres_solve": lambda: lib.ls_block_gmres_solve(None, 2, 2, p, 2, p, 2, p, 2, *oi),
+        "ls_lu_factor": lambda: lib.ls_lu_factor(None, 2, p, 2, p, p, 2, pi, p),
+        "ls_batch_solve": lambda: lib.ls_batch_solve(None, 1, ctypes.byref(binding.ls_system()),
+                                                     ctypes.byref(info)),
+        "ls_server_start": lambda: lib.ls_server_start(None, ctypes.byref(binding.ls_server_cfg()),
+                                                       ctypes.byref(ctypes.c_void_p())),
+        "ls_server_submit": lambda: lib.ls_server_submit(None, ctypes.byref(binding.ls_system()),
+                                                         ctypes.byref(ctypes.c_uint64())),
+        "ls_server_poll": lambda: lib.ls_server_poll(None, 1, ctypes.byref(ctypes.c_int()), ctypes.byref(info)),
+        "ls_server_stop": lambda: lib.ls_server_stop(None),
+        "ls_gemv": lambda: lib.ls_gemv(None, 0, 2, 2, p, 2, None, p, p),
+        "ls_gemv_timed": lambda: lib.ls_gemv_timed(None, 0, 2, 2, p, 2, None, p, p, 1,
+                                                   ctypes.byref(ctypes.c_double())),
+        "ls_quantize": lambda: lib.ls_quantize(None, 1, 2, 2, p, 2, p, 2, None),
+        "ls_split_f64": lambda: lib.ls_split_f64(None, 2, 2, p, 2, p, 4),
+    }
+
+
+def test_null_context_is_an_argument_error(lslib):
+    """A NULL context or server is refused with LS_ERR_ARG before any CUDA call
+    (no crash, no device touched); the launch counter of no context is 0."""
+    calls = _null_context_calls(lslib)
+    declared = set(_declared()) - {"ls_opts_default", "ls_create", "ls_destroy", "ls_strerror",
+                                   "ls_kernel_launches", "ls_gemv_noalloc"}
+    assert set(calls) == declared
+    for name, call in calls.items():
+        assert call() == binding.LS_ERR_ARG, name
+    assert lslib.ls_kernel_launches(None) == 0
