@@ -82,6 +82,8 @@ class Oracle:
         lib.or_block_gmres.argtypes = [i, i, P, l, P, P, i, d, i, i, i, P, P, P]
         lib.or_ge_solve.argtypes = [i, P, l, P, P]
         lib.or_ge_factor.argtypes = [i, P, l, P, P, P, P]
+        lib.or_chol_factor.argtypes = [i, P, l, P]
+        lib.or_chol_solve.argtypes = [i, P, l, P, P]
         for name in ("or_bf16_round", "or_e4m3_round"):
             getattr(lib, name).argtypes = [d]
             getattr(lib, name).restype = d
@@ -240,6 +242,23 @@ class Oracle:
         y = np.zeros(n)
         st = self.lib.or_ge_factor(n, _p(A), n, _p(_vec(b, n)), _p(LU), _p(ipiv), _p(y))
         return LU, ipiv, y, st
+
+    def chol_factor(self, A):
+        """Cholesky factor L of an SPD A (lower triangular, zero above the
+        diagonal).  Returns (L, status): status 2 when A is not SPD."""
+        A = _mat(A)
+        n = A.shape[0]
+        L = np.zeros((n, n))
+        st = self.lib.or_chol_factor(n, _p(A), n, _p(L))
+        return L, st
+
+    def chol_solve(self, A, b):
+        """A x = b through A = L L^T.  Returns (x, status)."""
+        A = _mat(A)
+        n = A.shape[0]
+        x = np.zeros(n)
+        st = self.lib.or_chol_solve(n, _p(A), n, _p(_vec(b, n)), _p(x))
+        return x, st
 
     def ge_solve(self, A, b):
         """Gaussian elimination with partial pivoting.  Returns (x, status)."""

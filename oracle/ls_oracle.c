@@ -30,6 +30,9 @@
  *     leaves out written in (see or_bicgstab).
  *   - Gaussian elimination with partial pivoting: same section,
  *     "Right-looking LU factorization", then forward/back substitution.
+ *   - Cholesky factorization A = L L^T of an SPD matrix: same section, the
+ *     Cholesky paragraph (Figure 3 and the three computations that follow
+ *     it), taken one column at a time, then L y = b and L^T x = y.
  *   - Mixed precision (BF16 / FP8-e4m3 storage of A, FP32 inner CG, FP64
  *     outer refinement) extends the paper's single/double precision axis
  *     (section "Results").
@@ -905,6 +908,64 @@ int or_ge_factor(int n, const double *A, long lda, const double *b, double *LU, 
         y[i] = b[i];
     }
     return ge_eliminate(n, LU, y, ipiv);
+}
+
+/* ------------------------------------------------------------------ */
+/* Cholesky factorization, FP64                                        */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper's Cholesky relations (A11 = L11 L11^T, L21 L11^T = A21,
+ * A22 - L21 L21^T = L22 L22^T, L overwriting the lower triangle of A)
+ * taken with a 1 x 1 leading block, i.e. right-looking by columns: at step
+ * k, l_kk = sqrt(a_kk); l_ik = a_ik / l_kk for i > k; then
+ * a_ij -= l_ik l_jk for k < j <= i (the lower triangle of the trailing
+ * block).  Every element a_ij receives its updates for k = 0, 1, ... in
+ * order, each as a rounded product and a rounded difference.  A pivot
+ * a_kk <= 0 (or not a number) means A is not SPD: OR_BREAKDOWN, with L as
+ * far as the factorization got.  L is n x n row-major, the strict upper
+ * triangle set to zero.
+ */
+static int chol_columns(int n, double *W) {
+    for (int k = 0; k < n; k++) {
+        double akk = W[(long)k * n + k];
+        if (!(akk > 0.0)) return OR_BREAKDOWN;
+        double lkk = sqrt(akk);
+        W[(long)k * n + k] = lkk;
+        for (int i = k + 1; i < n; i++) W[(long)i * n + k] /= lkk;
+        for (int i = k + 1; i < n; i++) {
+            double lik = W[(long)i * n + k];
+            for (int j = k + 1; j <= i; j++) W[(long)i * n + j] -= lik * W[(long)j * n + k];
+        }
+    }
+    return OR_OK;
+}
+
+int or_chol_factor(int n, const double *A, long lda, double *L) {
+    if (n < 0 || lda < n) return OR_ERR_ARG;
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) L[(long)i * n + j] = j <= i ? A[(long)i * lda + j] : 0.0;
+    return chol_columns(n, L);
+}
+
+/* A x = b by the factorization, then L y = b (forward) and L^T x = y (back). */
+int or_chol_solve(int n, const double *A, long lda, const double *b, double *x) {
+    if (n < 0 || lda < n) return OR_ERR_ARG;
+    double *L = malloc(sizeof(double) * (size_t)(n ? n : 1) * (n ? n : 1));
+    int st = or_chol_factor(n, A, lda, L);
+    if (st == OR_OK) {
+        for (int i = 0; i < n; i++) {            /* L y = b, y in x */
+            double s = b[i];
+            for (int j = 0; j < i; j++) s -= L[(long)i * n + j] * x[j];
+            x[i] = s / L[(long)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {       /* L^T x = y */
+            double s = x[i];
+            for (int j = i + 1; j < n; j++) s -= L[(long)j * n + i] * x[j];
+            x[i] = s / L[(long)i * n + i];
+        }
+    }
+    free(L);
+    return st;
 }
 
 /* ------------------------------------------------------------------ */

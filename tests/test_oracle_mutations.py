@@ -14,6 +14,7 @@ import test_oracle_bicgstab as tbs
 import test_oracle_block_cg as tbc
 import test_oracle_block_gmres as tbg
 import test_oracle_cg as tcg
+import test_oracle_cholesky as tch
 import test_oracle_ge_quant as tgq
 import test_oracle_gauss_seidel as tgs
 import test_oracle_gmres as tgm
@@ -108,6 +109,14 @@ MUTATIONS = {
     "bicgstab_x_drops_omega_s": ("for (int i = 0; i < n; i++) x[i] += alpha * p[i] + omega * s[i];",
                                  "for (int i = 0; i < n; i++) x[i] += alpha * p[i];",
                                  lambda o: tgo.test_bicgstab_worked_example(o)),
+    "chol_no_sqrt": ("double lkk = sqrt(akk);", "double lkk = akk;",
+                     lambda o: tch.test_cholesky_worked_example(o)),
+    "chol_update_reads_upper": ("W[(long)i * n + j] -= lik * W[(long)j * n + k];",
+                                "W[(long)i * n + j] -= lik * W[(long)k * n + j];",
+                                lambda o: tch.test_cholesky_matches_lapack_and_backward_error(o, 17)),
+    "chol_back_solve_not_transposed": ("for (int j = i + 1; j < n; j++) s -= L[(long)j * n + i] * x[j];",
+                                       "for (int j = i + 1; j < n; j++) s -= L[(long)i * n + j] * x[j];",
+                                       lambda o: tch.test_cholesky_solve_matches_lapack(o, 33)),
 }
 
 
