@@ -84,6 +84,8 @@ class Oracle:
         lib.or_ge_factor.argtypes = [i, P, l, P, P, P, P]
         lib.or_chol_factor.argtypes = [i, P, l, P]
         lib.or_chol_solve.argtypes = [i, P, l, P, P]
+        lib.or_chol_forward.argtypes = [i, P, P, P]
+        lib.or_chol_forward.restype = None
         for name in ("or_bf16_round", "or_e4m3_round"):
             getattr(lib, name).argtypes = [d]
             getattr(lib, name).restype = d
@@ -251,6 +253,14 @@ class Oracle:
         L = np.zeros((n, n))
         st = self.lib.or_chol_factor(n, _p(A), n, _p(L))
         return L, st
+
+    def chol_forward(self, L, b):
+        """y = L^-1 b by forward substitution (sums in increasing column order)."""
+        L = _mat(L)
+        n = L.shape[0]
+        y = np.zeros(n)
+        self.lib.or_chol_forward(n, _p(L), _p(_vec(b, n)), _p(y))
+        return y
 
     def chol_solve(self, A, b):
         """A x = b through A = L L^T.  Returns (x, status)."""

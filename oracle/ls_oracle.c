@@ -947,17 +947,23 @@ int or_chol_factor(int n, const double *A, long lda, double *L) {
     return chol_columns(n, L);
 }
 
+/* L y = b by forward substitution (L n x n row-major, lower): y_i =
+ * (b_i - sum_{j < i} l_ij y_j) / l_ii, the sum taken in increasing j. */
+void or_chol_forward(int n, const double *L, const double *b, double *y) {
+    for (int i = 0; i < n; i++) {
+        double s = b[i];
+        for (int j = 0; j < i; j++) s -= L[(long)i * n + j] * y[j];
+        y[i] = s / L[(long)i * n + i];
+    }
+}
+
 /* A x = b by the factorization, then L y = b (forward) and L^T x = y (back). */
 int or_chol_solve(int n, const double *A, long lda, const double *b, double *x) {
     if (n < 0 || lda < n) return OR_ERR_ARG;
     double *L = malloc(sizeof(double) * (size_t)(n ? n : 1) * (n ? n : 1));
     int st = or_chol_factor(n, A, lda, L);
     if (st == OR_OK) {
-        for (int i = 0; i < n; i++) {            /* L y = b, y in x */
-            double s = b[i];
-            for (int j = 0; j < i; j++) s -= L[(long)i * n + j] * x[j];
-            x[i] = s / L[(long)i * n + i];
-        }
+        or_chol_forward(n, L, b, x);             /* y in x */
         for (int i = n - 1; i >= 0; i--) {       /* L^T x = y */
             double s = x[i];
             for (int j = i + 1; j < n; j++) s -= L[(long)j * n + i] * x[j];

@@ -22,6 +22,7 @@ def test_cholesky_worked_example(oracle):
     assert st == 0 and np.array_equal(L, g["L"])
     x, st = oracle.chol_solve(g["A"], g["b"])
     assert st == 0 and np.array_equal(x, g["x"])
+    assert np.array_equal(oracle.chol_forward(g["L"], g["b"]), g["y"])
     L, st = oracle.chol_factor(g["indefinite_A"])
     assert st == 2
 
@@ -69,3 +70,15 @@ def test_cholesky_not_positive_definite(oracle):
     L, st = oracle.chol_factor(A)
     assert st == 2
     assert oracle.chol_solve(A, np.ones(n))[1] == 2
+
+
+@pytest.mark.parametrize("n", [1, 5, 80])
+def test_cholesky_forward_substitution(oracle, n):
+    A = inputs.spd_matrix(n, 0.1, seed=600 + n)
+    L, st = oracle.chol_factor(A)
+    b = inputs.solution(n, seed=601 + n)
+    y = oracle.chol_forward(L, b)
+    import scipy.linalg
+    ref = scipy.linalg.solve_triangular(L, b, lower=True)
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.max(np.abs(L @ y - b)) <= 4 * n * U * np.max(np.abs(L) @ np.abs(y))
