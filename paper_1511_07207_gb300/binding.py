@@ -142,11 +142,14 @@ def _itemsize(a):
 
 
 def lead_dim(a) -> int:
-    """Leading dimension (elements) of a row-major 2-D array; rows must be unit-stride."""
+    """Leading dimension (elements) of a row-major 2-D array; rows must be
+    unit-stride (ValueError otherwise)."""
     if _is_torch(a):
-        assert a.dim() == 2 and a.stride(1) == 1, "row-major with unit column stride required"
+        if a.dim() != 2 or (a.shape[1] > 1 and a.stride(1) != 1):
+            raise ValueError("a row-major 2-D array with unit column stride is required")
         return a.stride(0)
-    assert a.ndim == 2 and a.strides[1] == a.itemsize, "row-major with unit column stride required"
+    if a.ndim != 2 or (a.shape[1] > 1 and a.strides[1] != a.itemsize):
+        raise ValueError("a row-major 2-D array with unit column stride is required")
     return a.strides[0] // a.itemsize
 
 
@@ -157,11 +160,13 @@ def col_lead_dim(a) -> int:
     if _is_torch(a):
         if a.dim() == 1 or a.shape[1] == 1:
             return a.shape[0]
-        assert a.stride(0) == 1, "column-major with unit row stride required"
+        if a.stride(0) != 1:
+            raise ValueError("a column-major block with unit row stride is required")
         return a.stride(1)
     if a.ndim == 1 or a.shape[1] == 1:
         return a.shape[0]
-    assert a.strides[0] == a.itemsize, "column-major with unit row stride required"
+    if a.strides[0] != a.itemsize:
+        raise ValueError("a column-major block with unit row stride is required")
     return a.strides[1] // a.itemsize
 
 
@@ -182,7 +187,27 @@ def _check_f64(*arrs):
         if a is None:
             continue
         dt = str(a.dtype)
-        assert dt in ("float64", "torch.float64"), "FP64 arrays required, got %s" % dt
+        if dt not in ("float64", "torch.float64"):
+            raise TypeError("FP64 arrays required, got %s" % dt)
+
+
+def _numel(a):
+    return a.numel() if _is_torch(a) else a.size
+
+
+def _check_vec(v, n, name):
+    """v must hold n elements contiguously (the library reads v[0 .. n-1])."""
+    if v is None:
+        raise ValueError("%s is required" % name)
+    contig = v.is_contiguous() if _is_torch(v) else v.flags["C_CONTIGUOUS"]
+    if _numel(v) != n or not (contig or n <= 1):
+        raise ValueError("%s: %d contiguous elements required, got shape %s" % (name, n, tuple(v.shape)))
+
+
+def _check_square(A):
+    if len(A.shape) != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be n x n, got shape %s" % (tuple(A.shape),))
+    return A.shape[0]
 
 
 # ---------------------------------------------------------------------------
@@ -228,8 +253,9 @@ def ls_set_workspace(ctx, buf=None, nbytes=0):
 
 def _solve(fn, ctx, A, b, x, opts):
     _check_f64(A, b, x)
-    n = A.shape[0]
-    assert A.shape[1] == n
+    n = _check_square(A)
+    _check_vec(b, n, "b")
+    _check_vec(x, n, "x")
     info = ls_info()
     o = opts if opts is not None else make_opts()
     st = fn(ctx, n, ptr(A), lead_dim(A), ptr(b), ptr(x), ctypes.byref(o), ctypes.byref(info))
@@ -265,12 +291,20 @@ def ls_gauss_seidel_solve(ctx, A, b, x, opts=None):
 def ls_gemv(ctx, dtype, A, x, y, scale=None):
     """y = A x on the device (see ls.h for the per-format types)."""
     rows, cols = A.shape
+    _check_vec(x, cols, "x")
+    _check_vec(y, rows, "y")
+    if scale is not None:
+        _check_vec(scale, rows, "scale")
     return load().ls_gemv(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x), ptr(y))
 
 
 def ls_gemv_timed(ctx, dtype, A, x, y, reps, scale=None):
     """Mean device ms of one y = A x launch over `reps` back-to-back launches."""
     rows, cols = A.shape
+    _check_vec(x, cols, "x")
+    _check_vec(y, rows, "y")
+    if scale is not None:
+        _check_vec(scale, rows, "scale")
     ms = ctypes.c_double(0)
     st = load().ls_gemv_timed(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x),
                               ptr(y), reps, ctypes.byref(ms))
@@ -284,6 +318,10 @@ def ls_gemv_noalloc(dtype, A, x, y, scale=None, stream=None):
     if stream is not None and hasattr(stream, "cuda_stream"):
         stream = stream.cuda_stream
     rows, cols = A.shape
+    _check_vec(x, cols, "x")
+    _check_vec(y, rows, "y")
+    if scale is not None:
+        _check_vec(scale, rows, "scale")
     return load().ls_gemv_noalloc(dtype, rows, cols, ptr(A), lead_dim(A), ptr(scale), ptr(x),
                                   ptr(y), stream)
 
@@ -291,6 +329,10 @@ def ls_gemv_noalloc(dtype, A, x, y, scale=None, stream=None):
 def ls_quantize(ctx, dtype, A, Q, scale=None):
     """Quantise FP64 A (device) into Q (device) [and FP32 row scales]."""
     rows, cols = A.shape
+    if Q.shape[0] != rows or Q.shape[1] < cols:
+        raise ValueError("Q must have %d rows and at least %d columns" % (rows, cols))
+    if scale is not None:
+        _check_vec(scale, rows, "scale")
     return load().ls_quantize(ctx, dtype, rows, cols, ptr(A), lead_dim(A), ptr(Q), lead_dim(Q),
                               ptr(scale))
 
@@ -299,6 +341,8 @@ def ls_split_f64(ctx, A, pair):
     """Split FP64 A (device, rows x cols) into the FP32 pair `pair` (device,
     2 rows x ldp floats: hi rows, then lo rows)."""
     rows, cols = A.shape
+    if pair.shape[0] != 2 * rows or pair.shape[1] < cols:
+        raise ValueError("pair must have %d rows and at least %d columns" % (2 * rows, cols))
     return load().ls_split_f64(ctx, rows, cols, ptr(A), lead_dim(A), ptr(pair), lead_dim(pair))
 
 
@@ -320,8 +364,9 @@ def ls_block_cg_solve(ctx, A, B, X, opts=None):
     contiguous, e.g. the transpose of a contiguous s x n tensor).  X is
     written in place.  Returns (status, info dict)."""
     _check_f64(A, B, X)
-    n = A.shape[0]
-    assert A.shape[1] == n and B.shape[0] == n and X.shape == B.shape
+    n = _check_square(A)
+    if B.shape[0] != n or tuple(X.shape) != tuple(B.shape):
+        raise ValueError("B and X must be n x s blocks of the same shape")
     info = ls_info()
     o = opts if opts is not None else make_opts()
     st = load().ls_block_cg_solve(ctx, n, B.shape[1], ptr(A), lead_dim(A), ptr(B), col_lead_dim(B), ptr(X),
@@ -333,8 +378,9 @@ def ls_block_gmres_solve(ctx, A, B, X, opts=None):
     """Restarted block GMRES(m) on A X = B (m = opts.restart block steps);
     B and X as for ls_block_cg_solve.  Returns (status, info dict)."""
     _check_f64(A, B, X)
-    n = A.shape[0]
-    assert A.shape[1] == n and B.shape[0] == n and X.shape == B.shape
+    n = _check_square(A)
+    if B.shape[0] != n or tuple(X.shape) != tuple(B.shape):
+        raise ValueError("B and X must be n x s blocks of the same shape")
     info = ls_info()
     o = opts if opts is not None else make_opts()
     st = load().ls_block_gmres_solve(ctx, n, B.shape[1], ptr(A), lead_dim(A), ptr(B), col_lead_dim(B), ptr(X),
@@ -350,7 +396,14 @@ def ls_lu_solve(ctx, A, b, x, opts=None):
 def ls_lu_factor(ctx, A, b, LU, ipiv, y):
     """The factorization alone into LU (n x n row-major), ipiv (int32), y.  Returns the status."""
     _check_f64(A, b, LU, y)
-    n = A.shape[0]
+    n = _check_square(A)
+    _check_vec(b, n, "b")
+    _check_vec(y, n, "y")
+    _check_vec(ipiv, n, "ipiv")
+    if str(ipiv.dtype) not in ("int32", "torch.int32"):
+        raise TypeError("ipiv must be int32, got %s" % ipiv.dtype)
+    if LU.shape[0] != n or LU.shape[1] < n:
+        raise ValueError("LU must be n x n")
     return load().ls_lu_factor(ctx, n, ptr(A), lead_dim(A), ptr(b), ptr(LU), lead_dim(LU), ptr(ipiv), ptr(y))
 
 
