@@ -347,9 +347,15 @@ def ls_split_f64(ctx, A, pair):
 
 
 def make_system(method, A, B, X, opts=None) -> ls_system:
+    """One system of a batch or a server request: A (n x n row-major), B and X
+    n-vectors or n x k column-major blocks of the same shape, all FP64."""
+    _check_f64(A, B, X)
+    n = _check_square(A)
+    if B.shape[0] != n or tuple(X.shape) != tuple(B.shape):
+        raise ValueError("B and X must be n-vectors or n x k blocks of the same shape")
     s = ls_system()
     s.method = method
-    s.n = A.shape[0]
+    s.n = n
     s.nrhs = 1 if B.ndim == 1 else B.shape[1]
     s.A, s.lda = ptr(A), lead_dim(A)
     s.B, s.ldb = ptr(B), col_lead_dim(B)

@@ -81,3 +81,18 @@ def test_gemv_family():
     assert B.ls_split_f64(None, A, pair) == B.LS_ERR_ARG
     with pytest.raises(ValueError):
         B.ls_split_f64(None, A, torch.zeros((4, 8), dtype=torch.float32))   # hi rows only
+
+
+def test_make_system():
+    A = np.eye(n)
+    Bm = np.asfortranarray(np.ones((n, 2)))
+    s = B.make_system(B.LS_METHOD_CG, A, Bm, np.asfortranarray(np.zeros((n, 2))))
+    assert s.n == n and s.nrhs == 2 and s.ldb == n and s.lda == n
+    s = B.make_system(B.LS_METHOD_GMRES, A, np.ones(n), np.zeros(n))
+    assert s.nrhs == 1 and s.ldb == n
+    with pytest.raises(ValueError):
+        B.make_system(B.LS_METHOD_CG, A, Bm, np.asfortranarray(np.zeros((n, 3))))
+    with pytest.raises(ValueError):
+        B.make_system(B.LS_METHOD_CG, A, np.ones((n, 2)), np.zeros((n, 2)))      # row-major blocks
+    with pytest.raises(TypeError):
+        B.make_system(B.LS_METHOD_CG, A.astype(np.float32), Bm, Bm.copy(order="F"))
