@@ -302,6 +302,18 @@ int ls_lu_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *
 int ls_lu_factor(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *LU,
                  int64_t ldlu, int *ipiv, double *y);
 
+/*
+ * Self-test of the bounded on-device waits (no paper passage: the library's
+ * own failure detection).  which = 0: a kernel waits on an mbarrier that
+ * nothing completes; which = 1: one CTA of a two-CTA kernel waits at a grid
+ * barrier (a private one) that the other CTA never reaches.  Each wait gives
+ * up after the library's limit (2 s), records the timeout and returns.
+ * Returns LS_ERR_TIMEOUT when that happened, which is the expected result;
+ * the context stays usable.  LS_ERR_ARG for a NULL context or another
+ * `which`.  Synchronous on the context's stream.
+ */
+int ls_selftest_waits(ls_ctx *ctx, int which);
+
 /* ---- batched solver -------------------------------------------------------- */
 typedef struct {
     int method;          /* LS_METHOD_CG (SPD A) or LS_METHOD_GMRES                     */

@@ -32,7 +32,7 @@ ABI_FUNCTIONS = (
     "ls_opts_default", "ls_create", "ls_destroy", "ls_workspace_size", "ls_set_workspace",
     "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_gauss_seidel_solve", "ls_block_cg_solve", "ls_block_gmres_solve", "ls_lu_solve", "ls_lu_factor", "ls_batch_solve", "ls_server_start", "ls_server_submit",
     "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
-    "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror",
+    "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror", "ls_selftest_waits",
 )
 
 
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.ls_quantize.argtypes = [P, I, I, I, P, I64, P, I64, P]
         lib.ls_split_f64.argtypes = [P, I, I, P, I64, P, I64]
         lib.ls_kernel_launches.argtypes = [P]
+        lib.ls_selftest_waits.argtypes = [P, I]
         lib.ls_kernel_launches.restype = ctypes.c_longlong
         lib.ls_strerror.argtypes = [I]
         lib.ls_strerror.restype = ctypes.c_char_p
@@ -446,3 +447,9 @@ def ls_server_poll(srv, ticket):
 
 def ls_server_stop(srv):
     return load().ls_server_stop(srv)
+
+
+def ls_selftest_waits(ctx, which):
+    """Run the self-test of the bounded waits (0: mbarrier, 1: grid barrier);
+    LS_ERR_TIMEOUT is the expected result."""
+    return load().ls_selftest_waits(ctx, which)

@@ -977,3 +977,24 @@ extern "C" int ls_quantize(ls_ctx *c, int dtype, int rows, int cols, const doubl
     if (e == cudaSuccess) c->launches_total += 1;
     return map_cuda(e);
 }
+
+extern "C" int ls_selftest_waits(ls_ctx *c, int which) {
+    if (!c || which < 0 || which > 1) return LS_ERR_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LS_ERR_CUDA;
+    GridBar *bar = nullptr;   // a barrier of its own: the context's stays consistent
+    cudaError_t e = cudaSuccess;
+    if (which == 1) {
+        e = cudaMalloc(&bar, 64);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 64, c->stream);
+    }
+    state_init(c->h_st, 0);
+    int rc = e == cudaSuccess ? upload_state(c) : map_cuda(e);
+    if (!rc) rc = map_cuda(selftest_launch(which, bar, c->st, c->stream));
+    if (!rc) rc = read_state(c);
+    if (bar) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(bar);
+    }
+    if (rc) return rc;
+    return status_from_state(*c->h_st);
+}

@@ -274,6 +274,9 @@ struct LuKernels {
 };
 LuKernels lu_kernels();
 
+// ---- self-test of the bounded waits (k_selftest.cu) -------------------------------------------
+cudaError_t selftest_launch(int which, GridBar *bar, State *st, cudaStream_t s);
+
 // ---- block GMRES (k_bgmres.cu) -----------------------------------------------------------
 constexpr int BGM_MAX_S = 16;
 constexpr int BGM_MAX_MS = 256;       // m * s at most

@@ -83,6 +83,7 @@ def _null_context_calls(lib):
                                                    ctypes.byref(ctypes.c_double())),
         "ls_quantize": lambda: lib.ls_quantize(None, 1, 2, 2, p, 2, p, 2, None),
         "ls_split_f64": lambda: lib.ls_split_f64(None, 2, 2, p, 2, p, 4),
+        "ls_selftest_waits": lambda: lib.ls_selftest_waits(None, 0),
     }
 
 
