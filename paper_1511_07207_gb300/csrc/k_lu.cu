@@ -8,7 +8,8 @@
 // W = [A | b], so the forward substitution L y = P b happens during the
 // elimination (y in column n), and U x = y is solved afterwards.
 //
-// The elimination runs by panels of LU_NB = 32 columns and stays the same
+// The elimination runs as the paper's block LU factorization (Figures 1-2,
+// equations (1)-(4)) with panels of LU_NB = 32 columns, and stays the same
 // elimination element by element: every a_ij receives a_ij - l_it u_tj for
 // t = 0, 1, ... in order, as a rounded product and a rounded difference.
 // Per panel:
@@ -27,8 +28,9 @@
 //   to L2 (ld.global.cg), never to a possibly stale L1 line.
 // lu_laswp_kernel: the panel's row swaps on every other column (a thread a
 //   column, the swaps in step order).
-// lu_u12_kernel: the panel's pivot rows right of the panel: the panel's
-//   updates t = k0 .. in order (a thread a column, the 32 values in registers).
+// lu_u12_kernel: the panel's pivot rows right of the panel (the paper's
+//   triangular solve for U01): the panel's updates t = k0 .. in order, four
+//   lanes a column, each holding 8 of the 32 values in registers.
 // lu_trail_kernel: the block below and right of the panel, 64 x 64 tiles:
 //   each element takes the panel's 32 updates in order from the multipliers
 //   and pivot rows staged in shared memory.  This is where the time goes:
