@@ -14,8 +14,13 @@ cache, so no flush is needed between steps.
                FP32 pipe from the FP32 pair hi + lo of A), timed with CUDA
                events on its stream as back-to-back launches of the same
                kernel and grid the solvers use; HBM-bound
-  cpu_baseline the oracle (plain C, FP64) on this host's cores, on a bounded
-               sample of the same workload, scaled to solves per second
+  cpu_baseline the oracle (plain C, FP64) on this host's cores: one full
+               solve of each of the step's two systems (about 7 s)
+  accuracy     the same solves at rtol 1e-10 and at the accuracy gate
+               rtol 1e-12, with FP32-pair and native FP64 products: error
+               against x* and against the oracle's x (solved to the same rtol)
+  small_n512   the n = 512 systems: time to 1e-10 and microseconds per
+               iteration (latency-bound)
 
 --impl reference times the oracle itself as the reference arm.
 Multi-GPU: the path does not shard; every rank solves its own replica
@@ -131,36 +136,33 @@ def fp32_issue_peak():
 # profile evidence for the roofline's traffic field
 # ---------------------------------------------------------------------------
 def gemv_source_hash():
-    """Hash of the GEMV kernel source: k_gemv.cu, the device helpers and the
-    GEMV_* constants of ls_internal.h."""
+    """Hash of the GEMV kernel's device source: k_gemv.cu up to its host-side
+    section, the device helpers and the GEMV_* constants of ls_internal.h."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1511_07207_gb300", "csrc")
-    for f in ("k_gemv.cu", "ls_device.cuh"):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "k_gemv.cu"), "rb") as fh:
+        h.update(fh.read().split(b"// ---- host side", 1)[0])
+    with open(os.path.join(csrc, "ls_device.cuh"), "rb") as fh:
+        h.update(fh.read())
     with open(os.path.join(csrc, "ls_internal.h")) as fh:
         h.update("".join(l for l in fh if "GEMV_" in l).encode())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", name)
+    """DRAM bytes per launch recorded next to a committed ncu summary (a small
+    JSON file in profiles/), if it was taken on the current kernel source
+    (else None)."""
     try:
-        txt = open(path).read()
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            vals = json.load(f)
+    except (OSError, ValueError):
         return None
-    vals = {}
-    for line in txt.splitlines():
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_sha256_16") != gemv_source_hash():
         return None
     try:
         return float(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
+    except (KeyError, TypeError, ValueError):
         return None
 
 
@@ -201,21 +203,96 @@ def make_inputs(device):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_sample(A_spd, b_spd, A_ns, b_ns, cg_iters, gm_iters, cg_sample=60):
-    """Time the oracle: `cg_sample` CG iterations and a GMRES(50) run of
-    `gm_iters` steps on this host's cores; return (solves/s extrapolated to
-    full solves of cg_iters and gm_iters steps, threads, seconds spent)."""
+def oracle_full_solves(A_spd, b_spd, A_ns, b_ns, rtol=RTOL):
+    """Full oracle solves of the step's two systems on this host's cores: CG on
+    the SPD system and GMRES(50) on the nonsymmetric one, to `rtol`.  Returns
+    (solves/s, threads, seconds, the CG result, the GMRES result); the results
+    carry the oracle's x and iteration counts."""
     import oracle
     nt = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.cg(A_spd, b_spd, rtol=0.0, max_iter=cg_sample, nthreads=nt)
+    cg = oracle.cg(A_spd, b_spd, rtol=rtol, nthreads=nt)
     t1 = time.perf_counter()
-    oracle.gmres(A_ns, b_ns, m=RESTART, rtol=0.0, max_iter=gm_iters, nthreads=nt)
+    gm = oracle.gmres(A_ns, b_ns, m=RESTART, rtol=rtol, nthreads=nt)
     t2 = time.perf_counter()
-    per_cg = (t1 - t0) / cg_sample
-    per_gm = (t2 - t1) / max(gm_iters, 1)
-    t_solves = per_cg * cg_iters + per_gm * gm_iters
-    return 2.0 / t_solves, nt, t2 - t0, per_cg, per_gm
+    return 2.0 / (t2 - t0), nt, t2 - t0, cg, gm
+
+
+def config_dict(world=1):
+    """The workload description shared by both arms."""
+    return {"workload": WORKLOAD, "n": N, "restart": RESTART, "rtol": RTOL,
+            "matvec": ("FP64 A as the FP32 pair hi + lo (A kept to 2^-48), double-single "
+                       "accumulation, FP64 vectors and scalars"),
+            "l2": "inputs larger than L2 (each A is 2 GiB)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def accuracy_runs(B, ctx, dev, A_spd, b_spd, xs1, A_ns, b_ns, xs2):
+    """CG and GMRES(50) on the step's systems at rtol 1e-10 and 1e-12, with
+    FP32-pair and native FP64 products: status, iterations, device time, true
+    residual, error against x* and the bound kappa * true residual (kappa
+    estimated from the recipe: (4 + sigma) / sigma for G G^T/n + sigma I,
+    3 / 1 for 2 I + G/(2 sqrt n)).  Returns (dict, {key: host x})."""
+    import torch
+    out, xs_host = {}, {}
+    for method, A, b, xs, kappa in (("cg", A_spd, b_spd, xs1, (4 + SIGMA) / SIGMA),
+                                    ("gmres", A_ns, b_ns, xs2, 3.0)):
+        fn = B.ls_cg_solve if method == "cg" else B.ls_gmres_solve
+        out[method] = {"kappa_est": kappa}
+        for rt in (1e-10, 1e-12):
+            row = {}
+            for mode, f64 in (("fp32_pair", 0), ("native_f64", 1)):
+                x = torch.zeros(N, dtype=torch.float64, device=dev)
+                st, inf = fn(ctx, A, b, x, B.make_opts(rtol=rt, restart=RESTART, f64_matvec=f64))
+                row[mode] = {"status": B.ls_strerror(st), "iters": inf["iters"],
+                             "time_ms": round(inf["time_ms"], 3), "true_rel_res": inf["true_rel_res"],
+                             "rel_err_vs_xstar": rel_err(x, xs),
+                             "bound_kappa_x_rel_res": kappa * inf["true_rel_res"]}
+                xs_host[(method, rt, mode)] = x.cpu().numpy()
+                del x
+            out[method]["rtol_%g" % rt] = row
+    out["gate"] = "rtol 1e-12: rel. error <= 1e-8 against x* and against the oracle's x"
+    return out, xs_host
+
+
+def run_small(B, ctx, dev, reps=20):
+    """The n = 512 systems (seed 0): CG on G G^T/n + 0.1 I and GMRES(30) on
+    2 I + G/(2 sqrt n), rtol 1e-10, device-resident; latency-bound, so the
+    figures are time to solution and microseconds per iteration (best of
+    `reps` solves after one warm-up)."""
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    n = 512
+    out = {"n": n, "workload": "seed 0: CG on GG^T/n+0.1I, GMRES(30) on 2I+G/(2sqrt n); x*~U[-1,1], "
+                               "b=Ax*, x0=0, rtol 1e-10"}
+    for method, A, restart in (("cg", inputs.spd_matrix(n, 0.1, seed=0), 30),
+                               ("gmres", inputs.nonsym_matrix(n, seed=0), 30)):
+        xs = inputs.solution(n, seed=0)
+        Ad = torch.from_numpy(A).to(dev)
+        bd = torch.from_numpy(A @ xs).to(dev)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        fn = B.ls_cg_solve if method == "cg" else B.ls_gmres_solve
+        o = B.make_opts(rtol=RTOL, restart=restart)
+        fn(ctx, Ad, bd, x, o)
+        best = None
+        for _ in range(reps):
+            x.zero_()
+            st, inf = fn(ctx, Ad, bd, x, o)
+            if best is None or inf["time_ms"] < best["time_ms"]:
+                best = inf
+        out[method] = {"status": B.ls_strerror(st), "iters": best["iters"],
+                       "time_to_1e-10_us": round(best["time_ms"] * 1e3, 1),
+                       "us_per_iter": round(best["time_ms"] * 1e3 / max(best["iters"], 1), 2),
+                       "true_rel_res": best["true_rel_res"], "rel_err_vs_xstar": rel_err(x, xs)}
+    return out
+
+
+def rel_err(x, ref):
+    """||x - ref|| / ||ref|| in FP64 on the host."""
+    import numpy as np
+    x = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    ref = ref.cpu().numpy() if hasattr(ref, "cpu") else np.asarray(ref)
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
 
 
 # ---------------------------------------------------------------------------
@@ -343,6 +420,12 @@ def run_native(args):
     # accuracy of the timed results (checked, not assumed)
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
     err_gm = float(torch.linalg.norm(x2 - xs2) / torch.linalg.norm(xs2))
+    # the same solves at rtol 1e-10 and at the accuracy gate rtol 1e-12, with
+    # the default FP32-pair products and with native FP64 products; the error
+    # against the oracle's x is filled in by the CPU leg below
+    accuracy, acc_x = (None, {}) if args.no_accuracy else accuracy_runs(
+        B, ctx, dev, A_spd, b_spd, xs1, A_ns, b_ns, xs2)
+    small = run_small(B, ctx, dev) if not args.no_small else None
 
     # dominant kernel: the FP64 GEMV through the FP32 pair (the solvers'
     # default), same kernel/grid as inside the solves
@@ -362,7 +445,7 @@ def run_native(args):
     native_tflops = 2.0 * N * N / (native_ms * 1e-3) / 1e12
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = dfma_peak_tflops(sm_max)
-    traffic = profiled_traffic("gemv_pair_n16384.md")
+    traffic = profiled_traffic("gemv_pair_n16384.json")
     roofline = {"bound": "hbm", "achieved": round(gemv_gbs, 1), "peak": round(peaks["hbm_gbs"], 1),
                 "unit": "GB/s", "frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
                 "traffic": traffic,
@@ -412,20 +495,31 @@ def run_native(args):
     batch = run_batch_compare(B, ctx, dev, args) if not args.no_batch else None
     serve = run_serve(B, ctx, dev, args) if not args.no_serve else None
 
-    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    # CPU baseline: the oracle's full solves of the step's two systems (rank 0,
+    # N = 1 only); the accuracy gate's oracle solves (rtol 1e-12) follow,
+    # untimed, and give the error of every GPU result against the oracle's x
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        hA1 = A_spd.cpu().numpy()
-        hA2 = A_ns.cpu().numpy()
-        v, nt, secs, per_cg, per_gm = oracle_sample(
-            hA1, b_spd.cpu().numpy(), hA2, b_ns.cpu().numpy(),
-            infos[-1][0]["iters"], infos[-1][1]["iters"], cg_sample=args.cpu_cg_sample)
+        hA1, hb1 = A_spd.cpu().numpy(), b_spd.cpu().numpy()
+        hA2, hb2 = A_ns.cpu().numpy(), b_ns.cpu().numpy()
+        v, nt, secs, or_cg, or_gm = oracle_full_solves(hA1, hb1, hA2, hb2, rtol=RTOL)
         cpu = {"value": round(v, 6), "unit": "solves/s", "cores": nt, "kind": "oracle",
-               "sample": ("%d oracle CG iterations + a full oracle GMRES(50) solve (%d steps) on "
-                          "the same n=16384 matrices, %.1f s; CG scaled to the GPU's %d "
-                          "iterations" % (args.cpu_cg_sample, infos[-1][1]["iters"], secs,
-                                          infos[-1][0]["iters"])),
-               "ms_per_cg_iter": round(per_cg * 1e3, 3), "ms_per_gmres_step": round(per_gm * 1e3, 3)}
+               "sample": ("one full oracle CG solve (%d iterations) + one full oracle GMRES(50) solve "
+                          "(%d steps) of the same n=16384 systems to rtol 1e-10, %.1f s"
+                          % (or_cg["iters"], or_gm["iters"], secs)),
+               "ms_per_cg_iter": round(secs * 1e3 / (or_cg["iters"] + or_gm["iters"]), 3)}
+        oracle_x = {("cg", 1e-10): or_cg, ("gmres", 1e-10): or_gm}
+        if accuracy is not None:
+            _, _, secs12, or_cg12, or_gm12 = oracle_full_solves(hA1, hb1, hA2, hb2, rtol=1e-12)
+            oracle_x[("cg", 1e-12)] = or_cg12
+            oracle_x[("gmres", 1e-12)] = or_gm12
+            for (method, rt, mode), xh in acc_x.items():
+                ref = oracle_x[(method, rt)]
+                e = accuracy[method]["rtol_%g" % rt][mode]
+                e["rel_err_vs_oracle"] = rel_err(xh, ref["x"])
+                e["oracle_iters"] = ref["iters"]
+            accuracy["oracle_seconds_rtol_1e-12"] = round(secs12, 2)
+        del hA1, hA2
 
     if rank == 0:
         i1, i2 = infos[-1]
@@ -434,13 +528,13 @@ def run_native(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N, "restart": RESTART, "rtol": RTOL,
-                       "l2": "inputs larger than L2 (each A is 2 GiB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": config_dict(world),
             "time_to_1e-10_ms": {"cg": round(i1["time_ms"], 3), "gmres": round(i2["time_ms"], 3)},
             "iters": {"cg": i1["iters"], "gmres": i2["iters"]},
             "true_rel_res": {"cg": i1["true_rel_res"], "gmres": i2["true_rel_res"]},
             "rel_err_vs_xstar": {"cg": err_cg, "gmres": err_gm},
+            "accuracy": accuracy,
+            "small_n512": small,
             "bicgstab_nonsym": bicgstab,
             "jacobi_nonsym": jacobi,
             "gauss_seidel_nonsym": gauss_seidel,
@@ -497,6 +591,23 @@ def run_mixed_compare(B, ctx, dev, stream, args, n=32768):
     if out["fp64"]["status"] == "converged" and out["bf16_fcg"]["status"] == "converged":
         out["speedup_bf16_vs_fp64"] = round(out["fp64"]["time_to_tol_ms"] /
                                             out["bf16_fcg"]["time_to_tol_ms"], 3)
+    # accuracy gate: rtol 1e-12, error against x* and between the two solutions
+    if not args.no_accuracy:
+        gate, xg = {}, {}
+        for name, o in (("fp64", B.make_opts(rtol=1e-12)),
+                        ("bf16_fcg", B.make_opts(rtol=1e-12, precision=B.LS_BF16_IR))):
+            x.zero_()
+            st, info = B.ls_cg_solve(ctx, A, b, x, o)
+            gate[name] = {"status": B.ls_strerror(st), "iters": info["iters"],
+                          "outer_iters": info["outer_iters"], "time_ms": round(info["time_ms"], 3),
+                          "true_rel_res": info["true_rel_res"],
+                          "rel_err_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))}
+            xg[name] = x.clone()
+        gate["rel_diff_bf16_vs_fp64"] = float(torch.linalg.norm(xg["bf16_fcg"] - xg["fp64"]) /
+                                              torch.linalg.norm(xg["fp64"]))
+        gate["gate"] = "rtol 1e-12: rel. error <= 1e-8 against x*"
+        out["accuracy_rtol_1e-12"] = gate
+        del xg
     # GEMV per storage format on this A
     peaks, src = load_peaks()
     gb = {}
@@ -656,7 +767,6 @@ def run_reference(args):
     if rank != 0:
         return
     import torch
-    import oracle
     dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
     if dev is not None:
         A_spd, b_spd, _, A_ns, b_ns, _ = make_inputs(dev)
@@ -670,29 +780,22 @@ def run_reference(args):
         A2 = inputs.nonsym_matrix(N, seed=1)
         b2 = A2 @ inputs.solution(N, seed=1)
     nt = os.cpu_count() or 1
-    # the oracle's own iteration counts, once (GMRES in full; CG from a full solve)
-    full_gm = oracle.gmres(A2, b2, m=RESTART, rtol=RTOL, nthreads=nt)
-    cg_iters = args.ref_cg_iters
-    if cg_iters <= 0:
-        cg_iters = oracle.cg(A1, b1, rtol=RTOL, nthreads=nt)["iters"]
-    gm_iters = full_gm["iters"]
-    vals = []
-    secs = 0.0
+    times, iters = [], None
     for i in range(args.warmup + args.steps):
-        v, _, s, _, _ = oracle_sample(A1, b1, A2, b2, cg_iters, gm_iters, cg_sample=args.cpu_cg_sample)
+        _, nt, secs, cg, gm = oracle_full_solves(A1, b1, A2, b2, rtol=RTOL)
         if i >= args.warmup:
-            vals.append(v)
-            secs += s
-    value = args.steps / sum(1.0 / v for v in vals)    # harmonic mean of solves/s
-    sample = ("per step: %d oracle CG iterations (scaled to the oracle's %d) + a full oracle "
-              "GMRES(50) solve (%d steps), n=16384 FP64, %d threads" %
-              (args.cpu_cg_sample, cg_iters, gm_iters, nt))
+            times.append(secs)
+        iters = (cg["iters"], gm["iters"])
+    total = sum(times)
+    value = 2.0 * args.steps / total
+    sample = ("per step: one full oracle CG solve (%d iterations) + one full oracle GMRES(50) solve "
+              "(%d steps) of the n=16384 FP64 systems to rtol 1e-10, %d threads" % (iters[0], iters[1], nt))
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+           "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": N, "restart": RESTART, "rtol": RTOL},
+           "config": config_dict(int(os.environ.get("WORLD_SIZE", "1"))),
            "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": nt,
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
@@ -878,13 +981,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-system batched solve")
     ap.add_argument("--no-serve", action="store_true", help="skip the served workload")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson arrival window (60 s in the full workload)")
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-step", type=int, default=4)
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
-    ap.add_argument("--cpu-cg-sample", type=int, default=600)
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the rtol 1e-10 / 1e-12 accuracy runs (both product modes)")
+    ap.add_argument("--no-small", action="store_true", help="skip the n = 512 latency line")
     ap.add_argument("--kernel", choices=["gemv", "batch", "stationary", "block_cg", "lu"], default=None,
                     help="kernel-only timing (small cases for ncu captures): one GEMV format, "
                          "the batched engine alone on --count systems, or --reps sweeps of a "
@@ -896,8 +1001,6 @@ def main():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--dtype", choices=["f64", "pair", "bf16", "fp8", "f32"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--ref-cg-iters", type=int, default=0,
-                    help="reference arm: CG iteration count to scale to (0 = run the oracle once)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

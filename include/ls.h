@@ -440,9 +440,12 @@ int ls_gemv_timed(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int
  * cudaMalloc / cudaFree, which can synchronise the whole device.  (ls_gemv
  * needs a context, and ls_create allocates the context's device block.)
  *
- * Arguments are those of ls_gemv, plus the cudaStream_t to run on (NULL = the
- * legacy default stream); the current device is used.  The call returns after
- * y is written.  Every piece of scratch the kernel needs (matrix descriptor,
+ * Arguments are those of ls_gemv (every format, LS_F64_PAIR included), plus
+ * the cudaStream_t to run on (NULL = the legacy default stream); the current
+ * device is used.  The call copies the matrix descriptor from host memory,
+ * launches, reads the kernel's status back and synchronises the stream, so it
+ * returns after y is written and must not be called while the stream is being
+ * captured into a CUDA graph.  Every piece of scratch the kernel needs (matrix descriptor,
  * state block, completion ticket, per-CTA and per-row-tile partial sums)
  * lives in one static device array of LS_NOALLOC_SCRATCH_BYTES that every GPU
  * loading this library holds until the process exits; it has room for the
@@ -453,8 +456,10 @@ int ls_gemv_timed(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int
  * calls whose work overlaps on the GPU -- from several host threads, or on
  * several streams -- race and must be serialised by the caller.  The first
  * call on each device looks up the device address of the array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * LS_ERR_ARG for bad sizes or pointers; LS_ERR_CUDA if a CUDA call fails.
+ * (cudaGetSymbolAddress) and raises the kernel's shared-memory limit on that
+ * device.  LS_ERR_ARG for bad sizes or pointers (LS_F64_PAIR also needs lda a
+ * multiple of 4); LS_ERR_CUDA if a CUDA call fails; LS_ERR_TIMEOUT if a
+ * bounded on-device wait gave up.
  */
 #define LS_NOALLOC_MAX_CTAS 512
 #define LS_NOALLOC_SCRATCH_BYTES (576 * 1024)

@@ -222,12 +222,7 @@ BgemvLaunch bgemv_plan(int s, int num_sms) {
         case 8: L.func = bg_func<8>(); L.smem = stages<8>() * stage_bytes<8>() + 1024; break;
         default: L.func = bg_func<16>(); L.smem = stages<16>() * stage_bytes<16>() + 1024; break;
     }
-    static bool attr_done[5] = {};
-    const int idx = L.S == 1 ? 0 : L.S == 2 ? 1 : L.S == 4 ? 2 : L.S == 8 ? 3 : 4;
-    if (!attr_done[idx]) {
-        cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-        attr_done[idx] = true;
-    }
+    set_smem_limit(L.func, L.smem);
     return L;
 }
 

@@ -673,12 +673,7 @@ GemvLaunch gemv_plan(int dtype, bool use_tma, int epi, int num_sms) {
             break;
     }
     if (!use_tma) L.smem = 2 * GEMV_STAGES * sizeof(uint64_t);   // barriers only (no ring)
-    static bool attr_done[5][2] = {};
-    const int di = dtype >= 0 && dtype < 5 ? dtype : 3;
-    if (!attr_done[di][use_tma]) {
-        cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-        attr_done[di][use_tma] = true;
-    }
+    set_smem_limit(L.func, L.smem);
     if (L.grid > MAX_GRID) L.grid = MAX_GRID;
     return L;
 }
@@ -696,17 +691,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    // initialised once, thread-safe (function-local static)
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
                                              cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
+            return reinterpret_cast<EncodeTiledFn>(p);
+        return nullptr;
+    }();
     return fn;
 }
 

@@ -632,12 +632,8 @@ GsKernels gs_kernels() {
     K.trsv_block = GS_T;
     K.trsv_smem = (size_t)GS_SLOTS * GS_SLOT_B + 1024;
     K.blk = GS_B;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(K.trsv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.trsv_smem);
-        cudaFuncSetAttribute(K.panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.panel_smem);
-        attr_done = true;
-    }
+    set_smem_limit(K.trsv, K.trsv_smem);
+    set_smem_limit(K.panel, K.panel_smem);
     return K;
 }
 

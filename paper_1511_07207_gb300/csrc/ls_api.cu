@@ -13,7 +13,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "ls_api_internal.h"
 
@@ -38,6 +41,21 @@ int is_device_ptr(const void *p) {
 }
 
 int map_cuda(cudaError_t e) { return e == cudaSuccess ? LS_OK : (e == cudaErrorMemoryAllocation ? LS_ERR_NOMEM : LS_ERR_CUDA); }
+
+cudaError_t set_smem_limit(const void *func, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;   // (kernel, device) -> limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find({func, dev});
+    if (it != done.end() && it->second >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) done[{func, dev}] = smem;
+    return e;
+}
+
 
 // ---- workspace ----------------------------------------------------------------
 int ws_reserve(ls_ctx *c, size_t bytes) {

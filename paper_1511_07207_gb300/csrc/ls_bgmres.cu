@@ -62,8 +62,8 @@ int build_bgm_graph(ls_ctx *c, const BgmVecs &v, const BgmLayout &L, int x0_give
     const BgmKernels K = bgm_kernels();
     const BgemvLaunch BL = bgemv_plan(v.s, c->num_sms);
     const size_t orth_smem = bgm_orth_smem(v.m, v.s), fin_smem = bgm_finish_smem(v.m, v.s);
-    cudaFuncSetAttribute(K.orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem);
-    cudaFuncSetAttribute(K.finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fin_smem);
+    set_smem_limit(K.orth, orth_smem);
+    set_smem_limit(K.finish, fin_smem);
     Root R;
     if (!R.create()) return LS_ERR_CUDA;
     cudaGraphConditionalHandle ho, hi;

@@ -179,7 +179,7 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
     K = engine_kernels();
     grid_prod = c->num_sms;                 // one warp-specialised CTA per SM
     grid_vec = 2 * c->num_sms;
-    cudaFuncSetAttribute(K.prod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.prod_smem);
+    set_smem_limit(K.prod, K.prod_smem);
     return build_graph();
 }
 

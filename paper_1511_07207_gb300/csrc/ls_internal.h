@@ -148,6 +148,10 @@ struct GemvLaunch {
 };
 // Choose the kernel for a matrix (TMA or plain-load variant) and epilogue.
 GemvLaunch gemv_plan(int dtype, bool use_tma, int epi, int num_sms);
+// Raise a kernel's dynamic shared-memory limit to at least smem bytes on the
+// current device.  The attribute is per device: it is set again only for a
+// new (kernel, device) pair or a larger size.  Safe from several host threads.
+cudaError_t set_smem_limit(const void *func, size_t smem);
 cudaError_t gemv_launch(const GemvLaunch &L, const MatDesc *dA, const GemvArgs &a,
                         cudaStream_t s);
 // Fill the TMA map of a matrix descriptor (host side); returns false when the

@@ -74,7 +74,8 @@ int scratch_for_current_device(unsigned char **p, int *sms) {
 
 extern "C" int ls_gemv_noalloc(int dtype, int rows, int cols, const void *A, int64_t lda,
                                const float *scale, const void *x, void *y, void *stream) {
-    if (rows < 0 || cols < 0 || lda < cols || dtype < 0 || dtype > 3) return LS_ERR_ARG;
+    if (rows < 0 || cols < 0 || lda < cols || dtype < 0 || dtype > 4) return LS_ERR_ARG;
+    if (dtype == DT_DS && (lda & 3)) return LS_ERR_ARG;
     if (rows == 0) return LS_OK;
     if (!A || !x || !y || (dtype == DT_FP8 && !scale)) return LS_ERR_ARG;
     unsigned char *base = nullptr;
@@ -87,7 +88,12 @@ extern "C" int ls_gemv_noalloc(int dtype, int rows, int cols, const void *A, int
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MatDesc hd;
     memset(&hd, 0, sizeof(hd));
-    make_tensor_map(&hd, dtype, A, rows, cols, lda);
+    if (dtype == DT_DS) {   // the FP32 pair: hi rows, then lo rows, both with leading dimension lda
+        const float *hi = static_cast<const float *>(A);
+        make_tensor_map_ds(&hd, hi, hi + (long long)rows * lda, rows, cols, lda);
+    } else {
+        make_tensor_map(&hd, dtype, A, rows, cols, lda);
+    }
     hd.scale = scale;
     L = gemv_plan(dtype, hd.use_tma != 0, EPI_STORE, sms);
     MatDesc *dA = reinterpret_cast<MatDesc *>(base + OFF_DESC);
