@@ -674,7 +674,26 @@ def run_batch_compare(B, ctx, dev, args, count=512):
            "max_true_rel_res": worst_res, "max_rel_err_vs_xstar": err,
            "inner_iters_max": max(i["iters"] for i in infos),
            "outer_iters_max": max(i["outer_iters"] for i in infos),
-           "gpu_launches": infos[0]["launches"]}
+           "gpu_launches": infos[0]["launches"],
+           "inner_products": "tcgen05 kind::tf32, three products of a TF32 head/tail split, for 9-32 "
+                             "right-hand sides; FP32 pipe for 1-8"}
+    # the same batch with every inner product on the FP32 pipe (for comparison)
+    os.environ["LS_ENGINE_TC"] = "0"
+    try:
+        for (_, _, X, _) in keep:
+            X.zero_()
+        B.ls_batch_solve(ctx, systems)
+        t32 = []
+        for _ in range(max(1, min(args.steps, 3))):
+            for (_, _, X, _) in keep:
+                X.zero_()
+            torch.cuda.synchronize(dev)
+            st2, infos2 = B.ls_batch_solve(ctx, systems)
+            t32.append(infos2[0]["time_ms"])
+        out["batch_ms_device_fp32_pipe_products"] = round(min(t32), 3)
+        out["status_ok_fp32_pipe_products"] = sum(i["status"] == B.LS_OK for i in infos2)
+    finally:
+        del os.environ["LS_ENGINE_TC"]
     del keep, systems
     torch.cuda.empty_cache()
     return out

@@ -16,6 +16,7 @@
 #include "ls_device.cuh"
 #include "ls_engine.h"
 #include "ls_internal.h"
+#include "ls_tc.cuh"
 #include "split_pair.h"
 
 namespace lsi {
@@ -266,10 +267,14 @@ __global__ void __launch_bounds__(RED_T) eng_red_kernel(const EngineDev *Ep, cud
 // ordinary loads.
 // ============================================================================
 constexpr int PC_W = P32_T / 32;                     // consumer warps
-constexpr int PROD_T = P32_T + 32;                   // + the producer warp
-constexpr int PSTAGES = 4;                           // ring stages
+constexpr int PROD_T = P32_T + 64;                   // + the producer warp and the MMA warp
+constexpr int PSTAGES = 3;                           // ring stages
+constexpr int PREFETCH = 4;                          // tiles of a task brought into L2 ahead of their copy
 constexpr int TILE_B = E_RB32 * E_KC32 * 4;          // 32 KB A tile
 constexpr int OPR_B = E_KC32 * 32 * 4;               // one raw operand chunk (widest slot)
+constexpr int BOP_B = E_MAXS * E_KC32 * 4;           // one K-major tensor-core B operand (4 KB)
+constexpr int TMEM_COLS = 256;                       // two 128-row halves of the tile:
+constexpr int TC_HALF_COLS = 128;                    // per half Ah [Bh | Bt] (2 sp columns), then At Bh (sp)
 static_assert(E_KC32 * 4 == 128, "a tile row is one 128-byte swizzle row");
 
 struct StageHdr {
@@ -283,13 +288,22 @@ enum : int { SF_FIRST = 1, SF_LAST = 2, SF_SRC2 = 4 };
 
 constexpr size_t align_c(size_t v, size_t a) { return (v + a - 1) / a * a; }
 constexpr size_t OFF_TILE = 0;                                         // 1024-aligned tiles
-constexpr size_t OFF_OPR = OFF_TILE + (size_t)PSTAGES * TILE_B;        // [stage][2][OPR_B]
+constexpr size_t OFF_CVT = OFF_TILE + (size_t)PSTAGES * TILE_B;        // [2] tensor-core tail tiles
+constexpr size_t OFF_BOP = OFF_CVT + 2 * (size_t)TILE_B;               // [2] B operands [head; tail] /
+                                                                       // the FP32 path's two operand chunks
+constexpr size_t OFF_OPR = OFF_BOP + 4 * (size_t)BOP_B;                // [stage][2][OPR_B]
 constexpr size_t OFF_HDR = OFF_OPR + (size_t)PSTAGES * 2 * OPR_B;
+// barriers: full[PSTAGES], empty[PSTAGES], mma[2], conv[2]
 constexpr size_t OFF_BAR = align_c(OFF_HDR + PSTAGES * sizeof(StageHdr), 16);
-constexpr size_t OFF_PS = align_c(OFF_BAR + 2 * PSTAGES * sizeof(uint64_t), 16);   // [2][OPR_B]
-constexpr size_t OFF_RED = OFF_PS + 2 * OPR_B;                         // 1024 doubles
+constexpr size_t OFF_TCQ = OFF_BAR + (2 * PSTAGES + 4) * sizeof(uint64_t);   // 2 hand-over entries
+constexpr size_t OFF_TSLOT = OFF_TCQ + 2 * 16;
+constexpr size_t OFF_RED = align_c(OFF_TSLOT + 16, 16);                // 1024 doubles
 constexpr size_t PROD_SMEM = OFF_RED + 1024 * sizeof(double) + 1024;  // + alignment slack
+static_assert(OFF_CVT % 1024 == 0 && OFF_BOP % 1024 == 0, "swizzled operands need 1024-byte alignment");
+static_assert(PROD_SMEM <= 232448, "shared memory of one CTA");
+static_assert(BOP_B == OPR_B, "the FP32 path's operand buffer aliases a B operand");
 
+struct TcQ;
 struct ProdSmem {
     unsigned char *base;
     __device__ float *tile(int st) const { return reinterpret_cast<float *>(base + OFF_TILE + (size_t)st * TILE_B); }
@@ -301,7 +315,19 @@ struct ProdSmem {
     __device__ uint64_t *empty(int st) const {
         return reinterpret_cast<uint64_t *>(base + OFF_BAR) + PSTAGES + st;
     }
-    __device__ float *ps(int b) const { return reinterpret_cast<float *>(base + OFF_PS + (size_t)b * OPR_B); }
+    // tensor-core path: products of buffer parity b done / chunk of parity b handed over
+    __device__ uint64_t *mma(int b) const { return reinterpret_cast<uint64_t *>(base + OFF_BAR) + 2 * PSTAGES + b; }
+    __device__ uint64_t *conv(int b) const {
+        return reinterpret_cast<uint64_t *>(base + OFF_BAR) + 2 * PSTAGES + 2 + b;
+    }
+    __device__ struct TcQ *tcq() const { return reinterpret_cast<struct TcQ *>(base + OFF_TCQ); }
+    __device__ uint32_t *tslot() const { return reinterpret_cast<uint32_t *>(base + OFF_TSLOT); }
+    // FP32 path: operand chunk b (32 rows x sp, row-major)
+    __device__ float *ps(int b) const { return reinterpret_cast<float *>(base + OFF_BOP + (size_t)b * BOP_B); }
+    // tensor-core path, buffer parity b: the TF32 tail of the A tile (its head is written over
+    // the stage's tile) and the B operand, 2 sp rows of 128 bytes: the operand's head, then its tail
+    __device__ float *tail(int b) const { return reinterpret_cast<float *>(base + OFF_CVT + (size_t)b * TILE_B); }
+    __device__ float *bop(int b) const { return reinterpret_cast<float *>(base + OFF_BOP + (size_t)b * 2 * BOP_B); }
     __device__ double *red() const { return reinterpret_cast<double *>(base + OFF_RED); }
 };
 
@@ -321,100 +347,20 @@ __device__ __forceinline__ void release_stage(const ProdSmem &M, int st) {
 // rows and the partial dots.  Returns false on a timeout (all consumers
 // together).
 // ----------------------------------------------------------------------------
+// ----------------------------------------------------------------------------
+// The end of an FP32 product task, given the task's accumulators acc (thread
+// (rg, cg) holds rows rg + NRG r, columns 4 cg .. 4 cg + 3): split-K partials,
+// the Y rows of the row block and its partial dots.
+// ----------------------------------------------------------------------------
 template <int SP>
-__device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *flag_s) {
-    constexpr int KC = E_KC32;
-    constexpr int RPT = SP / 4;                 // rows per thread
-    constexpr int NCG = SP / 4;                 // column groups of 4
-    constexpr int NRG = E_RB32 / RPT;           // row groups
-    static_assert(NRG * NCG == P32_T, "thread grid");
-    static_assert(NRG % 8 == 0, "a thread's rows share one swizzle phase");
-    static_assert(ks32(SP) % KC == 0, "K chunks hold whole shared-memory chunks");
+__device__ bool prod_epilogue(const EngineDev &E, const ProdSmem &M, const Task &T, int ph, int it,
+                              const float *dst, float *out, float (&acc)[SP / 4][4], int *flag_s) {
+    constexpr int RPT = SP / 4, NCG = SP / 4, NRG = E_RB32 / RPT;
     const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
-    const StageHdr &H0 = *M.hdr(seq % PSTAGES);
-    const int u = H0.u;
-    const Task T = E.t32[u - E.n64];
     const SlotDesc &D = E.desc[T.slot];
-    const SlotState &S = E.st[T.slot];
-    const int ph = S.phase;
-    const int n = D.n, s = D.s, it = S.it;
+    const int n = D.n;
     const long long nsp = (long long)n * SP;
-    const int r0 = T.r0, r1 = T.r1, nrow = r1 - r0;
-    float *dst, *out;
-    if (ph == PH_CG) {
-        dst = D.P + (it & 1) * nsp;
-        out = D.Q;
-    } else {
-        dst = D.V + (long long)it * nsp;
-        out = D.W + ((it + 1) & 1) * nsp;
-    }
-    float acc[RPT][4];
-#pragma unroll
-    for (int r = 0; r < RPT; r++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) acc[r][c] = 0.0f;
-    const int nch = (T.k1 - T.k0 + KC - 1) / KC;
-    for (int ch = 0; ch < nch; ch++) {
-        const int st = seq % PSTAGES;
-        const bool ok = ch == 0 || mbar_wait(M.full(st), (seq / PSTAGES) & 1);
-        float *Ps = M.ps(ch & 1);
-        if (ok) {   // the operand chunk: P = Rf + beta P' (CG) or V_k = W / h (GMRES)
-            // thread tid always builds column tid % SP (SP divides the block)
-            const StageHdr &H = *M.hdr(st);
-            const float *o1 = M.opr(st, 0), *o2 = M.opr(st, 1);
-            const bool two = (H.flags & SF_SRC2) != 0;
-            const int k0 = H.k0, c = tid % SP;
-            const bool live = c < s && !(ph == PH_CG && H.colstop[c]);
-            const float cs = H.colscale[c];
-            const bool own = k0 < r1 && k0 + KC > r0;           // the chunk holds rows of this block
-#pragma unroll
-            for (int j = 0; j < (KC * SP + P32_T - 1) / P32_T; j++) {
-                const int e = tid + j * P32_T;
-                if (KC * SP % P32_T == 0 || e < KC * SP) {
-                    const int gk = k0 + e / SP;
-                    float val = 0.0f;
-                    if (live && gk < n) {
-                        if (ph == PH_CG) val = two ? fmaf(cs, o2[e], o1[e]) : o1[e];
-                        else val = o1[e] * cs;
-                        if (own && gk >= r0 && gk < r1) dst[(long long)gk * SP + c] = val;   // owned rows
-                    }
-                    Ps[e] = val;
-                }
-            }
-        }
-        if (named_bar_or(1, P32_T, !ok)) return false;
-        // rows rg + NRG r share the swizzle phase rg & 7 (NRG is a multiple
-        // of 8): one chunk offset per k quad, fixed offsets between the rows.
-        // The next quad's operands are loaded before this quad's FMAs.
-        const float *At = M.tile(st) + rg * KC;
-        const int sw = rg & 7;
-        float4 a[2][RPT], p[2][4];
-        auto load_q = [&](int kq, int b) {
-            const float *Aq = At + ((kq ^ sw) << 2);
-#pragma unroll
-            for (int r = 0; r < RPT; r++) a[b][r] = *reinterpret_cast<const float4 *>(Aq + r * NRG * KC);
-#pragma unroll
-            for (int j = 0; j < 4; j++) p[b][j] = *reinterpret_cast<const float4 *>(Ps + (4 * kq + j) * SP + cg * 4);
-        };
-        load_q(0, 0);
-#pragma unroll
-        for (int kq = 0; kq < KC / 4; kq++) {
-            const int b = kq & 1;
-            if (kq + 1 < KC / 4) load_q(kq + 1, b ^ 1);
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const float pc[4] = {p[b][j].x, p[b][j].y, p[b][j].z, p[b][j].w};
-#pragma unroll
-                for (int r = 0; r < RPT; r++) {
-                    const float av = j == 0 ? a[b][r].x : j == 1 ? a[b][r].y : j == 2 ? a[b][r].z : a[b][r].w;
-#pragma unroll
-                    for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av, pc[c], acc[r][c]);
-                }
-            }
-        }
-        release_stage(M, st);
-        seq++;
-    }
+    const int r0 = T.r0, nrow = T.r1 - T.r0;
     const int kc32 = (n + ks32(SP) - 1) / ks32(SP);
     if (kc32 > 1) {
         // publish this chunk's partial product; the last task of the row block
@@ -502,6 +448,337 @@ __device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *
     }
     named_bar(1, P32_T);        // Red free for the next task
     return true;
+}
+
+template <int SP>
+__device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *flag_s) {
+    constexpr int KC = E_KC32;
+    constexpr int RPT = SP / 4;                 // rows per thread
+    constexpr int NCG = SP / 4;                 // column groups of 4
+    constexpr int NRG = E_RB32 / RPT;           // row groups
+    static_assert(NRG * NCG == P32_T, "thread grid");
+    static_assert(NRG % 8 == 0, "a thread's rows share one swizzle phase");
+    static_assert(ks32(SP) % KC == 0, "K chunks hold whole shared-memory chunks");
+    const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
+    const StageHdr &H0 = *M.hdr(seq % PSTAGES);
+    const int u = H0.u;
+    const Task T = E.t32[u - E.n64];
+    const SlotDesc &D = E.desc[T.slot];
+    const SlotState &S = E.st[T.slot];
+    const int ph = S.phase;
+    const int n = D.n, s = D.s, it = S.it;
+    const long long nsp = (long long)n * SP;
+    const int r0 = T.r0, r1 = T.r1;
+    float *dst, *out;
+    if (ph == PH_CG) {
+        dst = D.P + (it & 1) * nsp;
+        out = D.Q;
+    } else {
+        dst = D.V + (long long)it * nsp;
+        out = D.W + ((it + 1) & 1) * nsp;
+    }
+    float acc[RPT][4];
+#pragma unroll
+    for (int r = 0; r < RPT; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = 0.0f;
+    const int nch = (T.k1 - T.k0 + KC - 1) / KC;
+    for (int ch = 0; ch < nch; ch++) {
+        const int st = seq % PSTAGES;
+        const bool ok = ch == 0 || mbar_wait(M.full(st), (seq / PSTAGES) & 1);
+        float *Ps = M.ps(ch & 1);
+        if (ok) {   // the operand chunk: P = Rf + beta P' (CG) or V_k = W / h (GMRES)
+            // thread tid always builds column tid % SP (SP divides the block)
+            const StageHdr &H = *M.hdr(st);
+            const float *o1 = M.opr(st, 0), *o2 = M.opr(st, 1);
+            const bool two = (H.flags & SF_SRC2) != 0;
+            const int k0 = H.k0, c = tid % SP;
+            const bool live = c < s && !(ph == PH_CG && H.colstop[c]);
+            const float cs = H.colscale[c];
+            const bool own = k0 < r1 && k0 + KC > r0;           // the chunk holds rows of this block
+#pragma unroll
+            for (int j = 0; j < (KC * SP + P32_T - 1) / P32_T; j++) {
+                const int e = tid + j * P32_T;
+                if (KC * SP % P32_T == 0 || e < KC * SP) {
+                    const int gk = k0 + e / SP;
+                    float val = 0.0f;
+                    if (live && gk < n) {
+                        if (ph == PH_CG) val = two ? fmaf(cs, o2[e], o1[e]) : o1[e];
+                        else val = o1[e] * cs;
+                        if (own && gk >= r0 && gk < r1) dst[(long long)gk * SP + c] = val;   // owned rows
+                    }
+                    Ps[e] = val;
+                }
+            }
+        }
+        if (named_bar_or(1, P32_T, !ok)) return false;
+        // rows rg + NRG r share the swizzle phase rg & 7 (NRG is a multiple
+        // of 8): one chunk offset per k quad, fixed offsets between the rows.
+        // The next quad's operands are loaded before this quad's FMAs.
+        const float *At = M.tile(st) + rg * KC;
+        const int sw = rg & 7;
+        float4 a[2][RPT], p[2][4];
+        auto load_q = [&](int kq, int b) {
+            const float *Aq = At + ((kq ^ sw) << 2);
+#pragma unroll
+            for (int r = 0; r < RPT; r++) a[b][r] = *reinterpret_cast<const float4 *>(Aq + r * NRG * KC);
+#pragma unroll
+            for (int j = 0; j < 4; j++) p[b][j] = *reinterpret_cast<const float4 *>(Ps + (4 * kq + j) * SP + cg * 4);
+        };
+        load_q(0, 0);
+#pragma unroll
+        for (int kq = 0; kq < KC / 4; kq++) {
+            const int b = kq & 1;
+            if (kq + 1 < KC / 4) load_q(kq + 1, b ^ 1);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float pc[4] = {p[b][j].x, p[b][j].y, p[b][j].z, p[b][j].w};
+#pragma unroll
+                for (int r = 0; r < RPT; r++) {
+                    const float av = j == 0 ? a[b][r].x : j == 1 ? a[b][r].y : j == 2 ? a[b][r].z : a[b][r].w;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) acc[r][c] = fmaf(av, pc[c], acc[r][c]);
+                }
+            }
+        }
+        release_stage(M, st);
+        seq++;
+    }
+    return prod_epilogue<SP>(E, M, T, ph, it, dst, out, acc, flag_s);
+}
+
+// ----------------------------------------------------------------------------
+// Tensor-core form of the FP32 product task (sp = 16 or 32).  The consumers
+// build each chunk's operand as in the FP32 form; then every FP32 value v of
+// the chunk and of the 256 x 32 tile of A is split into a TF32 head h = rn(v)
+// and a TF32 tail t = rn(v - h) (v = h + t to about 2^-24 |v|): the tile's
+// head is written over the tile, its tail into the tail tile of the buffer
+// parity, the operand's head and tail as the two halves of one K-major
+// 128-byte-swizzled B operand [Bh; Bt] of 2 sp rows.  The chunk is then
+// handed to the MMA warp, which issues, per 8-column step of K and per
+// 128-row half of the tile (tcgen05.mma kind::tf32, FP32 accumulators in
+// tensor memory),
+//     D1 += Ah [Bh | Bt]   (N = 2 sp: A's head is read once for both)
+//     D2 += At Bh          (N = sp)
+// so that Y = D1[:, :sp] + D1[:, sp:] + D2 (the dropped At Bt is below
+// 2^-24 |A||P|), and commits twice: to the stage's "empty" barrier (the
+// stage goes back to the producer when the products that read it are done)
+// and to the parity's "done" barrier (the consumers may then overwrite that
+// parity's tail tile and B operand, two chunks later).  The consumers wait
+// for the tensor core only before reusing a buffer parity and for the task's
+// last chunk; the accumulators then come back through tcgen05.ld, summed,
+// through a shared-memory staging copy into the FP32 form's register layout,
+// and the task ends as the FP32 form does.
+// ----------------------------------------------------------------------------
+struct TcQ {                 // a chunk handed to the MMA warp
+    int st;                  // ring stage holding the tile's head
+    int sp;                  // 16 or 32
+    int first;               // first chunk of its task (accumulators start from zero)
+    int stop;                // no more chunks in this launch
+};
+
+struct TcCtx {
+    uint32_t tmem;           // accumulators: half h at column 128 h (D1: 2 sp columns, then D2: sp)
+    unsigned cseq;           // chunks handed to the MMA warp by this CTA
+    int *fail_s;             // a wait gave up: every later wait returns at once
+};
+
+// Bounded wait that also gives up at once after an earlier failure (so a
+// failed task cannot queue one time limit after another).
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, unsigned parity, int *fail_s) {
+    if (*(volatile int *)fail_s) return false;
+    if (mbar_wait(bar, parity)) return true;
+    *(volatile int *)fail_s = 1;
+    return false;
+}
+
+template <int SP>
+__device__ bool prod_task_tc(const EngineDev &E, const ProdSmem &M, int &seq, int *flag_s, TcCtx &tc) {
+    constexpr int KC = E_KC32;
+    constexpr int RPT = SP / 4, NCG = SP / 4, NRG = E_RB32 / RPT;
+    constexpr int KQ = KC / 4;                  // 16-byte quads of K per chunk
+    constexpr int F4 = SP / 4, SWM = F4 - 1;    // staging: float4 per row, swizzle mask
+    static_assert(SP == 16 || SP == 32, "M = 128 needs N a multiple of 16");
+    static_assert(3 * SP <= TC_HALF_COLS && 2 * TC_HALF_COLS <= TMEM_COLS, "D1 and D2 of both halves");
+    static_assert(2 * SP * KC * 4 <= 2 * BOP_B, "B operand [head; tail]");
+    static_assert(E_RB32 * SP * 4 <= TILE_B, "the staging copy fits a tail tile");
+    const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
+    const int warp = tid >> 5, lane = tid & 31;
+    const StageHdr &H0 = *M.hdr(seq % PSTAGES);
+    const int u = H0.u;
+    const Task T = E.t32[u - E.n64];
+    const SlotDesc &D = E.desc[T.slot];
+    const SlotState &S = E.st[T.slot];
+    const int ph = S.phase;
+    const int n = D.n, s = D.s, it = S.it;
+    const long long nsp = (long long)n * SP;
+    const int r0 = T.r0, r1 = T.r1;
+    float *dst, *out;
+    if (ph == PH_CG) {
+        dst = D.P + (it & 1) * nsp;
+        out = D.Q;
+    } else {
+        dst = D.V + (long long)it * nsp;
+        out = D.W + ((it + 1) & 1) * nsp;
+    }
+    const int nch = (T.k1 - T.k0 + KC - 1) / KC;
+    for (int ch = 0; ch < nch; ch++) {
+        const int st = seq % PSTAGES;
+        bool ok = ch == 0 || tc_wait(M.full(st), (seq / PSTAGES) & 1, tc.fail_s);
+        const unsigned q = tc.cseq;
+        const int b = q & 1;
+        // the tail tile and B operand of parity b were last read by chunk q - 2
+        if (q >= 2) ok = tc_wait(M.mma(b), ((q - 2) >> 1) & 1, tc.fail_s) && ok;
+        if (ok) {
+            const StageHdr &H = *M.hdr(st);
+            const float *o1 = M.opr(st, 0), *o2 = M.opr(st, 1);
+            const bool two = (H.flags & SF_SRC2) != 0;
+            const int k0 = H.k0;
+            float *Bo = M.bop(b);
+            // thread (c, kq): rows 4 kq .. 4 kq + 3 of operand column c
+            for (int e = tid; e < SP * KQ; e += P32_T) {
+                const int c = e % SP, kq = e / SP;
+                const bool live = c < s && !(ph == PH_CG && H.colstop[c]);
+                const float cs = H.colscale[c];
+                float hv[4], tv[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int kl = 4 * kq + j, gk = k0 + kl;
+                    float val = 0.0f;
+                    if (live && gk < n) {
+                        const int oe = kl * SP + c;
+                        if (ph == PH_CG) val = two ? fmaf(cs, o2[oe], o1[oe]) : o1[oe];
+                        else val = o1[oe] * cs;
+                        if (gk >= r0 && gk < r1) dst[(long long)gk * SP + c] = val;   // owned rows
+                    }
+                    hv[j] = tf32_rn(val);
+                    tv[j] = tf32_rn(val - hv[j]);
+                }
+                const int pos = c * KC + ((kq ^ (c & 7)) << 2);      // rows c and SP + c: same swizzle phase
+                *reinterpret_cast<float4 *>(Bo + pos) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                *reinterpret_cast<float4 *>(Bo + SP * KC + pos) = make_float4(tv[0], tv[1], tv[2], tv[3]);
+            }
+            float4 *Ah4 = reinterpret_cast<float4 *>(M.tile(st));
+            float4 *At4 = reinterpret_cast<float4 *>(M.tail(b));
+#pragma unroll 4
+            for (int e = tid; e < TILE_B / 16; e += P32_T) {
+                const float4 a = Ah4[e];
+                const float4 h = make_float4(tf32_rn(a.x), tf32_rn(a.y), tf32_rn(a.z), tf32_rn(a.w));
+                Ah4[e] = h;
+                At4[e] = make_float4(tf32_rn(a.x - h.x), tf32_rn(a.y - h.y), tf32_rn(a.z - h.z), tf32_rn(a.w - h.w));
+            }
+        }
+        if (tid == 0) {
+            TcQ &Q = M.tcq()[b];
+            Q.st = st;
+            Q.sp = SP;
+            Q.first = ch == 0;
+            Q.stop = 0;
+        }
+        fence_async_smem();          // this thread's shared-memory writes, before the tensor core reads them
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(M.conv(b));
+            if (warp != PC_W - 1) mbar_arrive(M.empty(st));   // the eighth arrival: the MMA warp's commit
+        }
+        tc.cseq++;
+        seq++;
+    }
+    // the task's last products
+    const unsigned lq = tc.cseq - 1;
+    bool ok = tc_wait(M.mma(lq & 1), (lq >> 1) & 1, tc.fail_s);
+    if (named_bar_or(1, P32_T, !ok)) return false;
+    tc_fence_after();
+    {   // accumulators -> registers (D1 head + D1 tail + D2) -> staging copy
+        // (row-major, float4 f of row r at f ^ (r & SWM))
+        const int h = warp >> 2, qw = warp & 3;
+        const int row = h * 128 + qw * 32 + lane;
+        const uint32_t ta = tc.tmem + ((uint32_t)(qw * 32) << 16) + (uint32_t)(TC_HALF_COLS * h);
+        float4 *Ys = reinterpret_cast<float4 *>(M.tail(0));
+#pragma unroll
+        for (int c0 = 0; c0 < SP; c0 += 16) {
+            float v1[16], v2[16], v3[16];
+            tmem_ld16(ta + c0, v1);
+            tmem_ld16(ta + SP + c0, v2);
+            tmem_ld16(ta + 2 * SP + c0, v3);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int f = c0 / 4 + j;
+                float y[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) y[c] = (v1[4 * j + c] + v2[4 * j + c]) + v3[4 * j + c];
+                Ys[row * F4 + (f ^ (row & SWM))] = make_float4(y[0], y[1], y[2], y[3]);
+            }
+        }
+    }
+    tc_fence_before();
+    named_bar(1, P32_T);
+    float acc[RPT][4];
+    {
+        const float4 *Ys = reinterpret_cast<const float4 *>(M.tail(0));
+#pragma unroll
+        for (int r = 0; r < RPT; r++) {
+            const int row = rg + NRG * r;
+            const float4 v = Ys[row * F4 + (cg ^ (row & SWM))];
+            acc[r][0] = v.x;
+            acc[r][1] = v.y;
+            acc[r][2] = v.z;
+            acc[r][3] = v.w;
+        }
+    }
+    return prod_epilogue<SP>(E, M, T, ph, it, dst, out, acc, flag_s);
+}
+
+// Consumers leaving the launch: a stop entry for the MMA warp (once it has
+// taken the entry two places back, so the barrier phases stay in step).
+__device__ __forceinline__ void tc_send_stop(const ProdSmem &M, TcCtx &tc) {
+    const unsigned q = tc.cseq;
+    const int b = q & 1;
+    if (q >= 2) tc_wait(M.mma(b), ((q - 2) >> 1) & 1, tc.fail_s);
+    if (threadIdx.x == 0) M.tcq()[b].stop = 1;
+    named_bar(1, P32_T);
+    if ((threadIdx.x & 31) == 0) mbar_arrive(M.conv(b));
+}
+
+// The MMA warp: one lane issues every chunk's products in hand-over order.
+// Returns the number of chunks it issued.
+__device__ unsigned tc_mma_warp(const EngineDev &E, const ProdSmem &M, uint32_t tmem) {
+    const int lane = threadIdx.x & 31;
+    unsigned j = 0;
+    for (;;) {
+        const int b = j & 1;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(M.conv(b), (j >> 1) & 1));
+        if (!ok) {
+            if (lane == 0) atomicExch(E.active + A_ERR, 1);
+            break;
+        }
+        const TcQ Q = M.tcq()[b];
+        if (Q.stop) break;
+        if (lane == 0) {
+            tc_fence_after();
+            const uint32_t ah = smem_u32(M.tile(Q.st)), at = smem_u32(M.tail(b)), bo = smem_u32(M.bop(b));
+            const int sp = Q.sp;
+            const uint32_t id1 = tc_idesc_tf32(128, 2 * sp), id2 = tc_idesc_tf32(128, sp);
+#pragma unroll
+            for (int kk = 0; kk < E_KC32 / 8; kk++) {
+                const uint64_t db = tc_desc_sw128(bo + kk * 32);     // [Bh; Bt], and Bh its first sp rows
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t d1 = tmem + TC_HALF_COLS * h, d2 = d1 + 2 * sp;
+                    const uint32_t ao = h * (TILE_B / 2) + kk * 32;
+                    const bool acc = !Q.first || kk > 0;
+                    tc_mma_tf32(d1, tc_desc_sw128(ah + ao), db, id1, acc);
+                    tc_mma_tf32(d2, tc_desc_sw128(at + ao), db, id2, acc);
+                }
+            }
+            tc_commit(M.empty(Q.st));
+            tc_commit(M.mma(b));
+        }
+        __syncwarp();
+        j++;
+    }
+    return j;
 }
 
 // ----------------------------------------------------------------------------
@@ -661,25 +938,60 @@ __device__ bool res_task(const EngineDev &E, const ProdSmem &M, int &seq, int *f
     return true;
 }
 
-// At admission (START), the FP32 product tasks' tiles of A are split instead:
-// A = A32 + A32lo, rows [r0, r1) x columns [k0, k1), a warp per row
-// (split_pair: integer operations on the bit pattern, off the FP64 pipe).
+// At admission (START), the FP32 product tasks' parts of A are split instead:
+// A = A32 + A32lo for the task's rows and columns, written in the tile-major
+// layout of a32_tile (the task that ends at column n also writes the zero
+// columns up to a32_ncols(n)).  A warp takes 128 columns (four tiles' rows)
+// of one row at a time, a lane four consecutive columns, four such pieces in
+// flight per warp; split_pair works on the bit pattern with integer
+// operations, off the FP64 pipe.
 __device__ __forceinline__ void convert_task(const SlotDesc &D, const Task &T) {
+    constexpr int NW = P32_T / 32, U = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = T.r0 + warp; r < T.r1; r += P32_T / 32) {
-        const double *a = D.A64 + (long long)r * D.lda64;
-        float *a32 = D.A32 + (long long)r * D.ld32;
-        float *alo = D.A32lo + (long long)r * D.ld32;
-        for (int kb = T.k0 + lane; kb < T.k1; kb += 4 * 32) {
-            double v[4];
+    const int n = D.n;
+    const int kw = T.k1 == n ? (int)a32_ncols(n) : T.k1;
+    const int nseg = (kw - T.k0 + 127) / 128;
+    const int items = (T.r1 - T.r0) * nseg;
+    const bool vec = (D.lda64 & 1) == 0 && ((uintptr_t)D.A64 & 15) == 0;
+    for (int base = warp; base < items; base += U * NW) {
+        double v[U][4];
+        int rr[U], kk[U];
 #pragma unroll
-            for (int u = 0; u < 4; u++) v[u] = kb + 32 * u < T.k1 ? a[kb + 32 * u] : 0.0;
+        for (int u = 0; u < U; u++) {
+            const int item = base + u * NW;
+            rr[u] = T.r0 + item / nseg;
+            kk[u] = T.k0 + (item % nseg) * 128 + 4 * lane;
+            if (item >= items) kk[u] = kw;             // nothing to do
+            const double *a = D.A64 + (long long)rr[u] * D.lda64 + kk[u];
+            if (kk[u] < kw && vec && kk[u] + 3 < n) {
+                const double2 x = __ldcs(reinterpret_cast<const double2 *>(a));
+                const double2 y = __ldcs(reinterpret_cast<const double2 *>(a) + 1);
+                v[u][0] = x.x;
+                v[u][1] = x.y;
+                v[u][2] = y.x;
+                v[u][3] = y.y;
+            } else {
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                if (kb + 32 * u < T.k1) split_pair(v[u], a32[kb + 32 * u], alo[kb + 32 * u]);
+                for (int c = 0; c < 4; c++) v[u][c] = kk[u] < kw && kk[u] + c < n ? __ldcs(a + c) : 0.0;
             }
         }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (kk[u] >= kw) continue;
+            float h[4], l[4];
+#pragma unroll
+            for (int c = 0; c < 4; c++) split_pair(v[u][c], h[c], l[c]);
+            const long long at = a32_tile(n, T.r0, kk[u] & ~(E_KC32 - 1)) + a32_pos(rr[u] - T.r0, kk[u] & (E_KC32 - 1));
+            *reinterpret_cast<float4 *>(D.A32 + at) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4 *>(D.A32lo + at) = make_float4(l[0], l[1], l[2], l[3]);
+        }
     }
+}
+
+// Bring the next tiles of a task into L2 ahead of their copy to shared memory
+// (no shared memory used, no completion tracking): more bytes in flight.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // ----------------------------------------------------------------------------
@@ -707,11 +1019,27 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
             mbar_init(M.full(st), 32);
             mbar_init(M.empty(st), PC_W);
         }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(M.mma(b), 1);
+            mbar_init(M.conv(b), PC_W);
+        }
         fence_mbar_init();
     }
+    if (warp == 0) {             // tensor memory for the accumulators (one CTA per SM)
+        tmem_alloc(M.tslot(), TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
     const int par = (E.active[A_TICKS] - 1) & 1;               // list set of this tick
-    if (warp == PC_W) {
+    if (warp == PC_W + 1) {
+        // ---------------- MMA warp ----------------
+        const unsigned issued = tc_mma_warp(E, M, *M.tslot());
+        if (issued > 0 && (threadIdx.x & 31) == 0 && !mbar_wait(M.mma((issued - 1) & 1), ((issued - 1) >> 1) & 1))
+            atomicExch(E.active + A_ERR, 1);
+        __syncwarp();
+    } else if (warp == PC_W) {
         // ---------------- producer warp ----------------
         const int nres = E.active[A_LEN_RES + par];
         const int total = nres + E.active[A_LEN_PROD + par];
@@ -747,12 +1075,18 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
                 if (ph != PH_RESID) continue;
                 const SlotDesc &D = E.desc[T.slot];
                 const int n = D.n, sp = D.sp;
-                const void *mh = E.tmaps + (size_t)T.slot * 256, *ml = E.tmaps + (size_t)T.slot * 256 + 128;
-                if (lane == 0) {
-                    tmap_acquire(mh);
-                    tmap_acquire(ml);
-                }
+                const unsigned tb = (unsigned)(min(E_RB32, n - T.r0) * E_KC32 * 4);   // one tile
+                if (lane == 0)
+                    for (int i = 1; i <= PREFETCH; i++)
+                        if (T.k0 + i * E_KC32 < T.k1) {
+                            l2_prefetch(D.A32 + a32_tile(n, T.r0, T.k0 + i * E_KC32), tb);
+                            l2_prefetch(D.A32lo + a32_tile(n, T.r0, T.k0 + i * E_KC32), tb);
+                        }
                 for (int k0 = T.k0; k0 < T.k1 && !fail; k0 += E_KC32) {
+                    if (lane == 0 && k0 + (PREFETCH + 1) * E_KC32 < T.k1) {
+                        l2_prefetch(D.A32 + a32_tile(n, T.r0, k0 + (PREFETCH + 1) * E_KC32), tb);
+                        l2_prefetch(D.A32lo + a32_tile(n, T.r0, k0 + (PREFETCH + 1) * E_KC32), tb);
+                    }
                     const unsigned ob = (unsigned)(min(E_KC32, n - k0) * sp * 4);
                     for (int half = 0; half < 2; half++) {              // A32 + Xh, then A32lo + Xl
                         if (!wait_empty(M, seq)) { fail = true; break; }
@@ -765,8 +1099,9 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
                             H->flags = 0;
                             H->slot = T.slot;
                             H->sp = sp;
-                            mbar_arrive_expect_tx(M.full(st), TILE_B + ob);
-                            tma_load_2d(M.tile(st), half ? ml : mh, k0, T.r0, M.full(st));
+                            mbar_arrive_expect_tx(M.full(st), tb + ob);
+                            bulk_load_1d(M.tile(st), (half ? D.A32lo : D.A32) + a32_tile(n, T.r0, k0), tb,
+                                         M.full(st));
                             bulk_load_1d(M.opr(st, 0), (half ? D.Xl : D.Xh) + (long long)k0 * sp, ob, M.full(st));
                         } else {
                             mbar_arrive(M.full(st));
@@ -792,9 +1127,13 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
             const int stp = lane < D.s ? S.colstop[lane] : 1;
             float sc = 0.0f;
             if (!stp) sc = ph == PH_CG ? (float)S.beta[lane] : (float)(1.0 / S.hnorm[lane]);
-            const void *tmap = E.tmaps + (size_t)T.slot * 256;
-            if (lane == 0) tmap_acquire(tmap);
+            const unsigned tb = (unsigned)(min(E_RB32, n - T.r0) * E_KC32 * 4);   // one tile
+            if (lane == 0)
+                for (int i = 1; i <= PREFETCH; i++)
+                    if (T.k0 + i * E_KC32 < T.k1) l2_prefetch(D.A32 + a32_tile(n, T.r0, T.k0 + i * E_KC32), tb);
             for (int k0 = T.k0; k0 < T.k1; k0 += E_KC32) {
+                if (lane == 0 && k0 + (PREFETCH + 1) * E_KC32 < T.k1)
+                    l2_prefetch(D.A32 + a32_tile(n, T.r0, k0 + (PREFETCH + 1) * E_KC32), tb);
                 if (!wait_empty(M, seq)) { fail = true; break; }
                 const int st = seq % PSTAGES;
                 StageHdr *H = M.hdr(st);
@@ -810,8 +1149,8 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
                                (src2 ? SF_SRC2 : 0);
                     H->slot = T.slot;
                     H->sp = sp;
-                    mbar_arrive_expect_tx(M.full(st), TILE_B + ob + (src2 ? ob : 0));
-                    tma_load_2d(M.tile(st), tmap, k0, T.r0, M.full(st));
+                    mbar_arrive_expect_tx(M.full(st), tb + ob + (src2 ? ob : 0));
+                    bulk_load_1d(M.tile(st), D.A32 + a32_tile(n, T.r0, k0), tb, M.full(st));
                     bulk_load_1d(M.opr(st, 0), src + (long long)k0 * sp, ob, M.full(st));
                     if (src2) bulk_load_1d(M.opr(st, 1), src2 + (long long)k0 * sp, ob, M.full(st));
                 } else {
@@ -831,6 +1170,10 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
     } else {
         // ---------------- consumer warps ----------------
         int seq = 0;
+        __shared__ int fail_s;
+        if (threadIdx.x == 0) fail_s = 0;
+        named_bar(1, P32_T);
+        TcCtx tc{*M.tslot(), 0u, &fail_s};
         for (;;) {
             const int st = seq % PSTAGES;
             const bool ok = mbar_wait(M.full(st), (seq / PSTAGES) & 1);
@@ -868,14 +1211,29 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
             switch (H.sp) {
                 case 4: good = prod_task<4>(E, M, seq, &flag_s); break;
                 case 8: good = prod_task<8>(E, M, seq, &flag_s); break;
-                case 16: good = prod_task<16>(E, M, seq, &flag_s); break;
-                default: good = prod_task<32>(E, M, seq, &flag_s); break;
+                case 16:
+                    good = (E.prod_tc & 1) ? prod_task_tc<16>(E, M, seq, &flag_s, tc)
+                                           : prod_task<16>(E, M, seq, &flag_s);
+                    break;
+                default:
+                    good = (E.prod_tc & 2) ? prod_task_tc<32>(E, M, seq, &flag_s, tc)
+                                           : prod_task<32>(E, M, seq, &flag_s);
+                    break;
             }
             if (!good) {
                 if (threadIdx.x == 0) atomicExch(E.active + A_ERR, 1);
                 break;
             }
         }
+        tc_send_stop(M, tc);
+    }
+    // tensor memory is freed once every product has completed: the MMA warp
+    // waits (bounded) for its last commit before the whole block meets
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(*M.tslot(), TMEM_COLS);
     }
 }
 

@@ -58,7 +58,7 @@ __global__ void eng_collect_kernel(const SlotDesc *desc, const SlotState *st, Sl
 SlotSizes slot_sizes(int n, int s, int method, int m) {
     SlotSizes z{};
     z.sp = s <= 4 ? 4 : s <= 8 ? 8 : s <= 16 ? 16 : 32;   // the product kernel's widths
-    z.ld32 = (n + 3) / 4 * 4;
+    z.ld32 = a32_ncols(n);
     z.lda_stage = (n + 1) / 2 * 2;
     const size_t nsp = (size_t)n * z.sp;
     z.bytes = 0;
@@ -149,7 +149,6 @@ int Engine::reserve(ls_ctx *ctx, int slots, int n32, int nrb, int n64, int nv) {
         hE.part64 = k.take<double>((size_t)capb * 32);
         hE.partv = k.take<double>((size_t)capv * 32);
         hE.order = k.take<int>(cap_slots);
-        hE.tmaps = k.take<unsigned char>((size_t)cap_slots * 256);
         hE.work[0] = k.take<int>((size_t)cap64 + cap32 + capv);
         hE.work[1] = k.take<int>((size_t)cap64 + cap32 + capv);
         hE.wres = cap32;
@@ -288,12 +287,22 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     if (fixed_max_n) nb32 = (int)hd.size() * per.rb32;
 }
 
+// Which FP32 block products run on the tensor cores (EngineDev::prod_tc):
+// both widths by default; LS_ENGINE_TC=0..3 selects them (bit 0: sp = 16,
+// bit 1: sp = 32), e.g. to compare with the FP32-pipe form.
+int engine_tc_mode() {
+    const char *env = getenv("LS_ENGINE_TC");
+    if (env && env[0] >= '0' && env[0] <= '3' && env[1] == 0) return env[0] - '0';
+    return 3;
+}
+
 int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables) {
     hE.nslots = (int)hd.size();
     hE.n32 = (int)h32.size();
     hE.n64 = (int)h64.size();
     hE.nv = (int)hv.size();
     hE.tick_limit = tick_limit;
+    hE.prod_tc = engine_tc_mode();
     cudaError_t e = cudaSuccess;
     if (!tables) {   // same slot set: only the loop counters are reset
         e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
@@ -312,20 +321,6 @@ int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables)
         e = cudaMemcpyAsync(hE.tv, hv.data(), hv.size() * sizeof(Task), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !h_order.empty())
         e = cudaMemcpyAsync(hE.order, h_order.data(), h_order.size() * sizeof(int), cudaMemcpyHostToDevice,
-                            c->stream);
-    // TMA maps of every resident slot's A32 and A32lo (read by eng_prod's
-    // producer warp)
-    h_tmaps.assign(hd.size() * 256 + 64, 0);
-    unsigned char *maps = h_tmaps.data() + ((64 - ((uintptr_t)h_tmaps.data() & 63)) & 63);
-    for (size_t q = 0; q < hd.size() && e == cudaSuccess; q++) {
-        const SlotDesc &D = hd[q];
-        if (D.n <= 0 || !D.A32) continue;
-        if (!encode_f32_tile_map_sw128(maps + q * 256, D.A32, D.n, D.n, D.ld32, E_KC32, E_RB32) ||
-            !encode_f32_tile_map_sw128(maps + q * 256 + 128, D.A32lo, D.n, D.n, D.ld32, E_KC32, E_RB32))
-            return LS_ERR_CUDA;
-    }
-    if (e == cudaSuccess && !hd.empty())
-        e = cudaMemcpyAsync(const_cast<unsigned char *>(hE.tmaps), maps, hd.size() * 256, cudaMemcpyHostToDevice,
                             c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(hE.active, 0, A_SIZE * sizeof(int), c->stream);

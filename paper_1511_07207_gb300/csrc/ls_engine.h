@@ -57,6 +57,24 @@ __host__ __device__ constexpr int ks64(int sp) { return 4096 / (sp > 0 ? sp : 32
 // Rows per vector task: the same number of elements for any width.
 __host__ __device__ constexpr int rbv(int sp) { return E_VEL / (sp > 0 ? sp : 32); }
 
+// Storage of a slot's FP32 matrices (A32, A32lo) on the device: tile-major,
+// in the order eng_prod streams them.  Row block b (rows 256 b .. 256 b +
+// nr - 1, nr = min(256, n - 256 b)) holds ceil(n / 32) column tiles of nr x
+// 32 floats, each contiguous; inside a tile, row r is 128 bytes whose
+// 16-byte pieces are stored XOR-swizzled by r & 7 (piece j at position
+// j ^ (r & 7)), which is the image the tensor core and the FP32 path expect
+// in shared memory, so one tile is one contiguous bulk copy.  Columns past
+// n are stored as zeros; the last row block stores only its nr rows.
+__host__ __device__ inline long long a32_ncols(int n) { return (long long)(n + E_KC32 - 1) / E_KC32 * E_KC32; }
+// Offset (floats) of the tile holding rows r0 .. (r0 a multiple of 256) and
+// columns k0 .. k0 + 31 (k0 a multiple of 32).
+__host__ __device__ inline long long a32_tile(int n, int r0, int k0) {
+    const int nr = n - r0 < E_RB32 ? n - r0 : E_RB32;
+    return (long long)r0 * a32_ncols(n) + (long long)(k0 / E_KC32) * nr * E_KC32;
+}
+// Position of element (r, k) of a tile (r < 256, k < 32).
+__host__ __device__ inline int a32_pos(int r, int k) { return r * E_KC32 + ((((k >> 2) ^ (r & 7))) << 2) + (k & 3); }
+
 // Work decomposition of one slot of size n and padded width sp (it depends on
 // nothing else, so a slot's reduction order never depends on its neighbours).
 struct SlotTasks {
@@ -90,9 +108,9 @@ struct SlotDesc {                // written at admission
     double rtol;                 // outer (FP64) relative tolerance
     const double *A64;           // FP64 A (row-major)
     long long lda64;
-    float *A32;                  // fp32(A) (row-major, ld32): the inner solves' matrix
-    float *A32lo;                // fp32(A - fp32(A)): with A32, A to about 48 bits
-    long long ld32;
+    float *A32;                  // fp32(A), tile-major (a32_tile): the inner solves' matrix
+    float *A32lo;                // fp32(A - fp32(A)), same layout: with A32, A to about 48 bits
+    long long ld32;              // padded column count a32_ncols(n)
     double *X, *B, *R;           // n x sp row-major FP64
     float *Xh, *Xl;              // X = Xh + Xl (fp32 pair), refreshed with X
     float *Yk;                   // split-K partial products: kc32 x n x sp (kc32 > 1)
@@ -152,13 +170,12 @@ struct EngineDev {               // pointers handed to every engine kernel
     double *part64;              // [row block][32]
     double *partv;               // [taskv][32]
     int *order;                  // eng_red block b handles slot order[b] (costliest first)
-    const unsigned char *tmaps;  // per slot: 2 x 128-byte TMA maps, A32 and A32lo (256 x 32 tiles,
-                                 // 128-byte swizzle)
     int *work[2];                // per tick parity: runnable FP32 product tasks, then the
                                  // residual tasks at work[p] + wres, the vector tasks at
                                  // work[p] + wvec
     int wres, wvec;              // offsets of the residual and vector lists in work[p]
     int *active;                 // engine counters, see the A_* indices
+    int prod_tc;                 // FP32 products on the tensor cores: bit 0 for sp = 16, bit 1 for sp = 32
     int tick_limit;              // ticks per graph launch (loop control)
     int host_loop;               // 1: no graph; eng_red writes the loop condition to active[4]
     unsigned long long *launches;

@@ -50,7 +50,6 @@ public:
     SlotResult *results = nullptr;
     std::vector<Task> h32, h64, hv;
     std::vector<int> h_order;            // eng_red block -> slot (costliest first)
-    std::vector<unsigned char> h_tmaps;  // staging of the per-slot TMA maps
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     EngineKernels K{};

@@ -145,3 +145,37 @@ def test_batch_edge_cases(ctx, gpu):
                                        B.make_system(B.LS_METHOD_CG, Ad, Bd, X3)])
     assert infos[0]["status"] == B.LS_ERR_NAN and infos[1]["status"] == B.LS_OK
     assert st == B.LS_ERR_NAN
+
+
+def test_tensor_core_products_match_fp32_pipe(ctx, gpu, oracle, monkeypatch):
+    """The inner block products of systems with 9-32 right-hand sides run on
+    the tensor cores (three TF32 products of a head/tail split, about FP32
+    accuracy); LS_ENGINE_TC=0 runs them on the FP32 pipe instead.  Both reach
+    the FP64 tolerance against the oracle, the solutions agree within the
+    residual bound, and they are not bitwise equal (the tensor-core path ran)."""
+    specs = [inputs.SystemSpec(n, kind, s, seed)
+             for (n, kind, s, seed) in [(300, "spd", 16, 21), (700, "nonsym", 32, 22),
+                                        (1025, "spd", 32, 23), (513, "nonsym", 12, 24),
+                                        (2048, "spd", 20, 25), (97, "spd", 3, 26)]]
+    results = {}
+    for mode in ("3", "0"):
+        monkeypatch.setenv("LS_ENGINE_TC", mode)
+        arrays, systems = _systems(specs, gpu)
+        st, infos = B.ls_batch_solve(ctx, systems)
+        assert st == B.LS_OK
+        _check(oracle, arrays[:3], specs[:3], infos[:3])
+        for (A, Bm, _, _, _, Xd), info in zip(arrays, infos):
+            assert info["status"] == B.LS_OK
+            X = _x(Xd)
+            assert np.all(np.linalg.norm(Bm - A @ X, axis=0) <= 1.0000001e-10 * np.linalg.norm(Bm, axis=0))
+        results[mode] = [_x(a[5]) for a in arrays]
+    monkeypatch.delenv("LS_ENGINE_TC")
+    differs = False
+    for (A, Bm, _, _, _, _), sp, Xt, Xf in zip(arrays, specs, results["3"], results["0"]):
+        inv = 1.0 / np.linalg.svd(A, compute_uv=False)[-1]
+        bound = inv * (np.linalg.norm(Bm - A @ Xt, axis=0) + np.linalg.norm(Bm - A @ Xf, axis=0))
+        assert np.all(np.max(np.abs(Xt - Xf), axis=0) <= bound + 1e-300), sp
+        if sp.nrhs > 8 and not np.array_equal(Xt, Xf):
+            differs = True
+    assert differs
+
