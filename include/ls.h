@@ -466,6 +466,40 @@ int ls_gemv_timed(ls_ctx *ctx, int dtype, int rows, int cols, const void *A, int
 int ls_gemv_noalloc(int dtype, int rows, int cols, const void *A, int64_t lda,
                     const float *scale, const void *x, void *y, void *cuda_stream);
 
+/*
+ * Tile shapes of the batched engine (ls_batch_solve and the server), chosen
+ * by timing.  The paper has no counterpart: its CUBLAS calls have fixed
+ * shapes.  Each system of a batch, with s right-hand sides padded to sp in
+ * {4, 8, 16, 32} columns, streams A in product tasks of 256 rows x ks32
+ * columns and forms its FP32 inner block products on the tensor cores or on
+ * the FP32 pipe (sp >= 16 only).  The choice for a system depends only on its
+ * own n, s and the GPU's SM count, so a system gives the same bits alone or
+ * in any batch.  Defaults without a cache: ks32 = 512, tensor cores for
+ * sp >= 16.
+ *
+ * ls_autotune times every candidate (ks32 in {256, 512, 1024}, tensor cores
+ * or FP32 pipe) on synthetic batches of each size bucket [2^b, 2^(b+1)),
+ * b = 6..13, and each sp, keeps the fastest in this process, and writes them
+ * to `path` (may be NULL) as a JSON cache keyed by (bucket, sp, precision of
+ * the inner products, SM count).  flags: LS_TUNE_QUICK times only buckets 9
+ * and 10 and sp 16 and 32.  It allocates its synthetic systems itself and
+ * runs for seconds (tens of seconds for the full set); synchronous on the
+ * context's stream.  LS_ERR_ARG for a NULL context or an unwritable path.
+ *
+ * ls_tune_load reads a cache written by ls_autotune (entries timed on a GPU
+ * with another SM count are ignored at lookup); LS_ERR_ARG if the file is
+ * missing or malformed (the current choices stay).  Without a call, the
+ * first lookup of the process reads the file named by the environment
+ * variable LS_TUNE_CACHE, if set.  ls_tune_reset returns to the defaults.
+ * ls_tune_lookup reports the choice for an n x n system with nrhs columns on
+ * a GPU of num_sms SMs.  These three touch no GPU and are thread-safe.
+ */
+#define LS_TUNE_QUICK 1
+int ls_autotune(ls_ctx *ctx, const char *path, int flags);
+int ls_tune_load(const char *path);
+int ls_tune_reset(void);
+int ls_tune_lookup(int n, int nrhs, int num_sms, int *ks32, int *tensor_cores);
+
 /* Kernels the context has executed on the device since it was created. */
 long long ls_kernel_launches(ls_ctx *ctx);
 

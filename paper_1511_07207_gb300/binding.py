@@ -26,6 +26,7 @@ LS_F64_PAIR = 4
 LS_REFINE_FCG, LS_REFINE_IR = 0, 1
 LS_MAX_RESTART = 128
 LS_BATCH_MAX_N, LS_BATCH_MAX_RHS = 8192, 32
+LS_TUNE_QUICK = 1
 
 # every symbol declared in include/ls.h
 ABI_FUNCTIONS = (
@@ -33,6 +34,7 @@ ABI_FUNCTIONS = (
     "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_gauss_seidel_solve", "ls_block_cg_solve", "ls_block_gmres_solve", "ls_lu_solve", "ls_lu_factor", "ls_batch_solve", "ls_server_start", "ls_server_submit",
     "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
     "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror", "ls_selftest_waits",
+    "ls_autotune", "ls_tune_load", "ls_tune_reset", "ls_tune_lookup",
 )
 
 
@@ -114,6 +116,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.ls_split_f64.argtypes = [P, I, I, P, I64, P, I64]
         lib.ls_kernel_launches.argtypes = [P]
         lib.ls_selftest_waits.argtypes = [P, I]
+        lib.ls_autotune.argtypes = [P, ctypes.c_char_p, I]
+        lib.ls_tune_load.argtypes = [ctypes.c_char_p]
+        lib.ls_tune_reset.argtypes = []
+        lib.ls_tune_lookup.argtypes = [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.ls_kernel_launches.restype = ctypes.c_longlong
         lib.ls_strerror.argtypes = [I]
         lib.ls_strerror.restype = ctypes.c_char_p
@@ -349,7 +355,11 @@ def ls_split_f64(ctx, A, pair):
 
 def make_system(method, A, B, X, opts=None) -> ls_system:
     """One system of a batch or a server request: A (n x n row-major), B and X
-    n-vectors or n x k column-major blocks of the same shape, all FP64."""
+    n-vectors or n x k column-major blocks of the same shape, all FP64.  The
+    descriptor holds raw pointers; it also keeps references to A, B and X, so
+    the arrays live at least as long as the descriptor does (an expression
+    such as ``torch.from_numpy(a).to(dev)`` passed straight in would
+    otherwise be freed, and its memory reused, before the solve)."""
     _check_f64(A, B, X)
     n = _check_square(A)
     if B.shape[0] != n or tuple(X.shape) != tuple(B.shape):
@@ -362,6 +372,7 @@ def make_system(method, A, B, X, opts=None) -> ls_system:
     s.B, s.ldb = ptr(B), col_lead_dim(B)
     s.X, s.ldx = ptr(X), col_lead_dim(X)
     s.opts = opts if opts is not None else make_opts()
+    s._arrays = (A, B, X)
     return s
 
 
@@ -415,11 +426,33 @@ def ls_lu_factor(ctx, A, b, LU, ipiv, y):
 
 
 def ls_batch_solve(ctx, systems):
-    """systems: list of ls_system.  Returns (status, [info dict])."""
+    """systems: list of ls_system (from make_system, which keeps their arrays
+    alive).  Returns (status, [info dict])."""
     arr = (ls_system * len(systems))(*systems)
     infos = (ls_info * len(systems))()
     st = load().ls_batch_solve(ctx, len(systems), arr, infos)
     return st, [i.as_dict() for i in infos]
+
+
+def ls_autotune(ctx, path=None, flags=0):
+    """Time the batched engine's tile-shape candidates; write the JSON cache to
+    `path` (str or None) and use the choices in this process."""
+    return load().ls_autotune(ctx, path.encode() if path else None, flags)
+
+
+def ls_tune_load(path):
+    return load().ls_tune_load(path.encode())
+
+
+def ls_tune_reset():
+    return load().ls_tune_reset()
+
+
+def ls_tune_lookup(n, nrhs, num_sms):
+    """(status, ks32, tensor_cores) for an n x n system with nrhs columns."""
+    ks, tc = ctypes.c_int(0), ctypes.c_int(0)
+    st = load().ls_tune_lookup(n, nrhs, num_sms, ctypes.byref(ks), ctypes.byref(tc))
+    return st, ks.value, tc.value
 
 
 def ls_server_start(ctx, hbm_budget_bytes, max_slots=64, step_iters=8, queue_capacity=1 << 16,

@@ -337,7 +337,7 @@ __device__ __forceinline__ void release_stage(const ProdSmem &M, int st) {
 }
 
 // ----------------------------------------------------------------------------
-// consumers: one FP32 product task, Y = Ahat P for 256 rows x ks32(SP)
+// consumers: one FP32 product task, Y = Ahat P for 256 rows x D.ks32
 // columns of A, all SP columns.  Each thread owns RPT rows (rg + NRG r) x 4
 // columns (cg); per 4 k it reads each row's 4 A values with one 16-byte load
 // from the swizzled tile and 4 operand quads, then does 16 RPT multiply-adds
@@ -361,7 +361,7 @@ __device__ bool prod_epilogue(const EngineDev &E, const ProdSmem &M, const Task 
     const int n = D.n;
     const long long nsp = (long long)n * SP;
     const int r0 = T.r0, nrow = T.r1 - T.r0;
-    const int kc32 = (n + ks32(SP) - 1) / ks32(SP);
+    const int kc32 = (n + D.ks32 - 1) / D.ks32;
     if (kc32 > 1) {
         // publish this chunk's partial product; the last task of the row block
         // adds all chunks in chunk order
@@ -458,7 +458,6 @@ __device__ bool prod_task(const EngineDev &E, const ProdSmem &M, int &seq, int *
     constexpr int NRG = E_RB32 / RPT;           // row groups
     static_assert(NRG * NCG == P32_T, "thread grid");
     static_assert(NRG % 8 == 0, "a thread's rows share one swizzle phase");
-    static_assert(ks32(SP) % KC == 0, "K chunks hold whole shared-memory chunks");
     const int tid = threadIdx.x, rg = tid / NCG, cg = tid % NCG;
     const StageHdr &H0 = *M.hdr(seq % PSTAGES);
     const int u = H0.u;
@@ -1212,12 +1211,12 @@ __global__ void __launch_bounds__(PROD_T, 1) eng_prod_kernel(const EngineDev *Ep
                 case 4: good = prod_task<4>(E, M, seq, &flag_s); break;
                 case 8: good = prod_task<8>(E, M, seq, &flag_s); break;
                 case 16:
-                    good = (E.prod_tc & 1) ? prod_task_tc<16>(E, M, seq, &flag_s, tc)
-                                           : prod_task<16>(E, M, seq, &flag_s);
+                    good = E.desc[H.slot].tc ? prod_task_tc<16>(E, M, seq, &flag_s, tc)
+                                             : prod_task<16>(E, M, seq, &flag_s);
                     break;
                 default:
-                    good = (E.prod_tc & 2) ? prod_task_tc<32>(E, M, seq, &flag_s, tc)
-                                           : prod_task<32>(E, M, seq, &flag_s);
+                    good = E.desc[H.slot].tc ? prod_task_tc<32>(E, M, seq, &flag_s, tc)
+                                             : prod_task<32>(E, M, seq, &flag_s);
                     break;
             }
             if (!good) {

@@ -53,6 +53,8 @@ struct ls_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     long long launches_total = 0;
     lsi::Engine *batch = nullptr;
+    // set by the tuner while it times a candidate (-1: look the choice up)
+    int tune_ks32 = -1, tune_tc = -1;
 };
 
 namespace lsi {

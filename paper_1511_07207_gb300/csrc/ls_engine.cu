@@ -55,15 +55,18 @@ __global__ void eng_collect_kernel(const SlotDesc *desc, const SlotState *st, Sl
 }
 
 // ---- buffer sizes ---------------------------------------------------------------
-SlotSizes slot_sizes(int n, int s, int method, int m) {
+SlotSizes slot_sizes(const ls_ctx *c, int n, int s, int method, int m) {
     SlotSizes z{};
     z.sp = s <= 4 ? 4 : s <= 8 ? 8 : s <= 16 ? 16 : 32;   // the product kernel's widths
+    const TuneChoice ch = tune_choice(c, n, s);
+    z.ks32 = ch.ks32;
+    z.tc = z.sp >= 16 ? ch.tc : 0;
     z.ld32 = a32_ncols(n);
     z.lda_stage = (n + 1) / 2 * 2;
     const size_t nsp = (size_t)n * z.sp;
     z.bytes = 0;
     auto add = [&](size_t b) { z.bytes += align_up(b, 256); };
-    const SlotTasks tk = slot_tasks(n, z.sp);
+    const SlotTasks tk = slot_tasks(n, z.sp, z.ks32);
     add((size_t)n * z.ld32 * 4);              // A32
     add((size_t)n * z.ld32 * 4);              // A32lo
     add(nsp * 8); add(nsp * 8); add(nsp * 8); // X, B, R
@@ -87,7 +90,9 @@ void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int m
     D.sp = z.sp;
     D.method = method;
     D.m = m;
-    const SlotTasks tk = slot_tasks(n, z.sp);
+    const SlotTasks tk = slot_tasks(n, z.sp, z.ks32);
+    D.ks32 = z.ks32;
+    D.tc = z.tc;
     D.A32 = cv.take<float>((size_t)n * z.ld32);
     D.A32lo = cv.take<float>((size_t)n * z.ld32);
     D.ld32 = z.ld32;
@@ -226,7 +231,7 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     h64.clear();
     hv.clear();
     nb32 = 0;
-    const SlotTasks per = slot_tasks(fixed_max_n, 32);   // the widest slot has the most tasks
+    const SlotTasks per = slot_tasks(fixed_max_n, 32, E_KS32_MIN);   // the most tasks a slot can have
     const Task none{-1, 0, 0, 0, 0, 0, 0, 0};
     auto region = [&](std::vector<Task> &tab, int q, int per_slot, int &t0) {
         if (fixed_max_n) {
@@ -252,8 +257,8 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     for (int q : order) {
         SlotDesc &D = hd[q];
         const int n = D.n > 0 ? D.n : 0;
-        const SlotTasks tk = slot_tasks(n, D.sp);
-        const int ks = ks32(D.sp);
+        const SlotTasks tk = slot_tasks(n, D.sp, D.ks32);
+        const int ks = D.ks32;
         // FP32 product: row block x K chunk; row blocks own the partial dots
         region(h32, q, per.t32, D.t32);
         D.b32 = fixed_max_n ? q * per.rb32 : nb32;
@@ -287,22 +292,12 @@ void Engine::set_tasks(std::vector<SlotDesc> &hd, int fixed_max_n) {
     if (fixed_max_n) nb32 = (int)hd.size() * per.rb32;
 }
 
-// Which FP32 block products run on the tensor cores (EngineDev::prod_tc):
-// both widths by default; LS_ENGINE_TC=0..3 selects them (bit 0: sp = 16,
-// bit 1: sp = 32), e.g. to compare with the FP32-pipe form.
-int engine_tc_mode() {
-    const char *env = getenv("LS_ENGINE_TC");
-    if (env && env[0] >= '0' && env[0] <= '3' && env[1] == 0) return env[0] - '0';
-    return 3;
-}
-
 int Engine::upload(const std::vector<SlotDesc> &hd, int tick_limit, bool tables) {
     hE.nslots = (int)hd.size();
     hE.n32 = (int)h32.size();
     hE.n64 = (int)h64.size();
     hE.nv = (int)hv.size();
     hE.tick_limit = tick_limit;
-    hE.prod_tc = engine_tc_mode();
     cudaError_t e = cudaSuccess;
     if (!tables) {   // same slot set: only the loop counters are reset
         e = cudaMemcpyAsync(dE, &hE, sizeof(EngineDev), cudaMemcpyHostToDevice, c->stream);
@@ -496,13 +491,13 @@ extern "C" int ls_batch_solve(ls_ctx *c, int count, const ls_system *sys, ls_inf
     int n32 = 0, nb32 = 0, n64 = 0, nv = 0;
     for (int q = 0; q < count; q++) {
         const ls_system &S = sys[q];
-        z[q] = slot_sizes(S.n, S.nrhs, S.method, S.opts.restart);
+        z[q] = slot_sizes(c, S.n, S.nrhs, S.method, S.opts.restart);
         a_dev[q] = is_device_ptr(S.A);
         b_dev[q] = is_device_ptr(S.B);
         x_dev[q] = is_device_ptr(S.X);
         total += z[q].bytes + (a_dev[q] ? 0 : z[q].stageA) + (b_dev[q] ? 0 : z[q].stageBX) +
                  (x_dev[q] ? 0 : z[q].stageBX);
-        const SlotTasks tk = slot_tasks(S.n, z[q].sp);
+        const SlotTasks tk = slot_tasks(S.n, z[q].sp, z[q].ks32);
         n32 += tk.t32;
         nb32 += tk.rb32;
         n64 += tk.t64;

@@ -29,7 +29,8 @@ namespace lsi {
 constexpr int E_MAXS = LS_BATCH_MAX_RHS;   // right-hand sides per slot (32)
 constexpr int E_MAXM = 32;                 // GMRES restart length in the engine
 constexpr int E_RB32 = 256;                // rows per FP32 product task (any width)
-constexpr int E_KS32 = 512;                // columns of A per FP32 product task (split K)
+constexpr int E_KS32 = 512;                // default columns of A per FP32 product task (split K)
+constexpr int E_KS32_MIN = 256;            // smallest task width the tuner may choose
 constexpr int E_KC32 = 32;                 // k per shared-memory chunk of the FP32 product
 constexpr int E_VEL = 8192;                // elements of the n x sp block per vector task
 constexpr int E_PS = E_MAXM + 2;           // partial-dot slots per FP32 row block
@@ -47,8 +48,6 @@ enum : int {
     PH_ADMIT = 8,     // just admitted: eng_red turns it into START (nothing to reduce yet)
 };
 
-// Columns of A per FP32 product task for a padded width sp.
-__host__ __device__ constexpr int ks32(int) { return E_KS32; }
 // Columns of A per refinement-residual task (256 rows): the double-single
 // arithmetic costs 12 FP32 operations per term, so about the same time per
 // task for every width.
@@ -85,11 +84,13 @@ struct SlotTasks {
     int t64;         // residual tasks = rb32 * kc64
     int tv;          // vector tasks (rbv(sp) rows each)
 };
-__host__ __device__ inline SlotTasks slot_tasks(int n, int sp) {
+// ks32: columns of A per FP32 product task (a multiple of E_KC32, chosen per
+// slot class by the tuner).
+__host__ __device__ inline SlotTasks slot_tasks(int n, int sp, int ks32) {
     SlotTasks t;
     n = n > 0 ? n : 0;
     t.rb32 = (n + E_RB32 - 1) / E_RB32;
-    t.kc32 = n > 0 ? (n + ks32(sp) - 1) / ks32(sp) : 0;
+    t.kc32 = n > 0 ? (n + ks32 - 1) / ks32 : 0;
     t.t32 = t.rb32 * t.kc32;
     t.kc64 = n > 0 ? (n + ks64(sp) - 1) / ks64(sp) : 0;
     t.t64 = t.rb32 * t.kc64;
@@ -102,6 +103,8 @@ struct SlotDesc {                // written at admission
     int sp;                      // row stride of the n x sp row-major blocks: 4, 8, 16 or 32
     int method;                  // LS_METHOD_CG / LS_METHOD_GMRES
     int m;                       // GMRES restart (<= E_MAXM)
+    int ks32;                    // columns of A per FP32 product task
+    int tc;                      // FP32 products on the tensor cores (sp = 16 or 32 only)
     int inner_iters;             // inner iterations per refinement step
     int max_outer;               // refinement steps
     float inner_tol;             // inner relative tolerance
@@ -175,7 +178,6 @@ struct EngineDev {               // pointers handed to every engine kernel
                                  // work[p] + wvec
     int wres, wvec;              // offsets of the residual and vector lists in work[p]
     int *active;                 // engine counters, see the A_* indices
-    int prod_tc;                 // FP32 products on the tensor cores: bit 0 for sp = 16, bit 1 for sp = 32
     int tick_limit;              // ticks per graph launch (loop control)
     int host_loop;               // 1: no graph; eng_red writes the loop condition to active[4]
     unsigned long long *launches;

@@ -22,15 +22,24 @@ struct FinishItem {
     long long ldx;
 };
 
+// Tile shape of a slot's FP32 products (ls_tune.cu): columns of A per task and
+// whether the products run on the tensor cores.
+struct TuneChoice {
+    int ks32;
+    int tc;
+};
+TuneChoice tune_choice(const ls_ctx *c, int n, int s);
+
 struct SlotSizes {
     int sp;
+    int ks32, tc;        // tuned tile shape
     long long ld32, lda_stage;
     size_t bytes;        // engine buffers of the slot
     size_t stageA;       // FP64 copy of a host A
     size_t stageBX;      // column-major copy of a host B or X
 };
 
-SlotSizes slot_sizes(int n, int s, int method, int m);
+SlotSizes slot_sizes(const ls_ctx *c, int n, int s, int method, int m);
 void slot_carve(SlotDesc &D, const SlotSizes &z, char *base, int n, int s, int method, int m);
 
 class Engine {

@@ -133,9 +133,9 @@ bool same_problem(const Request &a, const Request &b) {
 // Device bytes of a slot of s columns for the problem of `rq` (engine buffers,
 // A's copy when it is on the host, B's staging, X's staging when any member's
 // X is on the host).
-size_t slot_bytes(const Request &rq, int s, bool any_host_x, SlotSizes *zo) {
+size_t slot_bytes(const ls_ctx *c, const Request &rq, int s, bool any_host_x, SlotSizes *zo) {
     const ls_system &S = rq.sys;
-    const SlotSizes z = slot_sizes(S.n, s, S.method, S.opts.restart);
+    const SlotSizes z = slot_sizes(c, S.n, s, S.method, S.opts.restart);
     if (zo) *zo = z;
     return z.bytes + (rq.a_dev ? 0 : z.stageA) + z.stageBX + (any_host_x ? z.stageBX : 0);
 }
@@ -182,7 +182,7 @@ int ls_server::admit_slot(std::vector<Request> &members, int slot) {
         any_host_x = any_host_x || !q.x_dev;
     }
     Resident &R = res[slot];
-    R.bytes = slot_bytes(r0, ncol, any_host_x, &R.z);
+    R.bytes = slot_bytes(&shadow, r0, ncol, any_host_x, &R.z);
     char *mem = pool.alloc(R.bytes);
     if (!mem) return LS_ERR_NOMEM;
     R.mem = mem;
@@ -303,7 +303,7 @@ void ls_server::run() {
                         const Request &o = queue[i];
                         if (ncol + o.sys.nrhs > LS_BATCH_MAX_RHS || !same_problem(rq, o)) continue;
                         const bool hx = any_host_x || !o.x_dev;
-                        if (slot_bytes(rq, ncol + o.sys.nrhs, hx, nullptr) > pool.size) break;
+                        if (slot_bytes(&shadow, rq, ncol + o.sys.nrhs, hx, nullptr) > pool.size) break;
                         pick.push_back(i);
                         ncol += o.sys.nrhs;
                         any_host_x = hx;
@@ -444,7 +444,7 @@ extern "C" int ls_server_start(ls_ctx *c, const ls_server_cfg *cfg, ls_server **
     }
     int rc = s->pool.init(cfg->hbm_budget_bytes);
     const int cap = cfg->max_slots;
-    const SlotTasks per = slot_tasks(SERVER_MAX_N, 32);   // the widest slot has the most tasks
+    const SlotTasks per = slot_tasks(SERVER_MAX_N, 32, E_KS32_MIN);   // the most tasks a slot can have
     if (!rc) rc = s->eng.reserve(&s->shadow, cap, cap * per.t32, cap * per.rb32, cap * per.t64, cap * per.tv);
     if (rc) {
         s->eng.release();
@@ -477,7 +477,7 @@ extern "C" int ls_server_submit(ls_server *s, const ls_system *req, uint64_t *ti
     cudaSetDevice(s->ctx->device);
     rq.a_dev = is_device_ptr(S.A) != 0;
     rq.x_dev = is_device_ptr(S.X) != 0;
-    rq.bytes = slot_bytes(rq, S.nrhs, !rq.x_dev, &rq.z);
+    rq.bytes = slot_bytes(&s->shadow, rq, S.nrhs, !rq.x_dev, &rq.z);
     if (rq.bytes > s->pool.size) return LS_ERR_NOMEM;
     {
         std::lock_guard<std::mutex> lk(s->mu);

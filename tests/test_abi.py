@@ -84,6 +84,7 @@ def _null_context_calls(lib):
         "ls_quantize": lambda: lib.ls_quantize(None, 1, 2, 2, p, 2, p, 2, None),
         "ls_split_f64": lambda: lib.ls_split_f64(None, 2, 2, p, 2, p, 4),
         "ls_selftest_waits": lambda: lib.ls_selftest_waits(None, 0),
+        "ls_autotune": lambda: lib.ls_autotune(None, None, 0),
     }
 
 
@@ -92,7 +93,8 @@ def test_null_context_is_an_argument_error(lslib):
     (no crash, no device touched); the launch counter of no context is 0."""
     calls = _null_context_calls(lslib)
     declared = set(_declared()) - {"ls_opts_default", "ls_create", "ls_destroy", "ls_strerror",
-                                   "ls_kernel_launches", "ls_gemv_noalloc"}
+                                   "ls_kernel_launches", "ls_gemv_noalloc", "ls_tune_load",
+                                   "ls_tune_reset", "ls_tune_lookup"}
     assert set(calls) == declared
     for name, call in calls.items():
         assert call() == binding.LS_ERR_ARG, name

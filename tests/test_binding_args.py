@@ -96,3 +96,22 @@ def test_make_system():
         B.make_system(B.LS_METHOD_CG, A, np.ones((n, 2)), np.zeros((n, 2)))      # row-major blocks
     with pytest.raises(TypeError):
         B.make_system(B.LS_METHOD_CG, A.astype(np.float32), Bm, Bm.copy(order="F"))
+
+
+def test_make_system_keeps_its_arrays_alive():
+    """The descriptor holds raw pointers: it must keep the arrays it points to
+    alive, or a temporary passed straight in would be freed (and its memory
+    reused) before the solve."""
+    import gc
+    import weakref
+    import numpy as np
+    from paper_1511_07207_gb300 import binding as B
+    A = np.eye(4)
+    Bm = np.asfortranarray(np.ones((4, 2)))
+    s = B.make_system(B.LS_METHOD_CG, A, Bm, np.asfortranarray(np.zeros((4, 2))))
+    ref = weakref.ref(s._arrays[2])
+    gc.collect()
+    assert ref() is not None and s.X == s._arrays[2].ctypes.data
+    del s
+    gc.collect()
+    assert ref() is None
