@@ -416,6 +416,7 @@ def run_native(args):
     del X8, B8, Xs8
     # the paper's direct method (LU with partial pivoting) at n = 8192
     lu_direct = lu_measure(B, ctx, dev, 8192)
+    chol_direct = chol_measure(B, ctx, dev, 8192)
 
     # accuracy of the timed results (checked, not assumed)
     err_cg = float(torch.linalg.norm(x1 - xs1) / torch.linalg.norm(xs1))
@@ -541,6 +542,7 @@ def run_native(args):
             "block_cg_spd": block_cg,
             "block_gmres_nonsym": block_gmres,
             "lu_direct": lu_direct,
+            "cholesky_direct": chol_direct,
             "gemv_f64_native": gemv_native,
             "gemv_f64": {"ms": round(gemv_ms, 4), "GB/s": round(gemv_gbs, 1),
                          "hbm_frac": round(gemv_gbs / peaks["hbm_gbs"], 4),
@@ -973,6 +975,31 @@ def lu_measure(B, ctx, dev, n):
             "note": ("blocked right-looking elimination (panels of 32 columns), bit for bit the plain "
                      "elimination: 2 n^3/3 unfused FP64 multiply/subtract instructions, bound by the FP64 "
                      "pipe (peak 152 SMs x 2 per clock x SM max clock, fp64_instr_per_s in T/s)")}
+
+
+def chol_measure(B, ctx, dev, n):
+    """The Cholesky method on the SPD family G G^T/n + 0.1 I at n: time and the
+    share of the FP64 pipe (n^3/6 updates, each a separate FP64 multiply and
+    subtract: n^3/3 instructions)."""
+    import torch
+    from paper_1511_07207_gb300 import inputs
+    A = inputs.spd_matrix(n, 0.1, seed=6, device=dev)
+    xs = torch.from_numpy(inputs.solution(n, seed=6)).to(dev)
+    b = A @ xs
+    for _ in range(2):   # the first call sizes the workspace
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        st, info = B.ls_chol_solve(ctx, A, b, x)
+    peaks, src = load_peaks()
+    instr = n ** 3 / 3.0
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    dp_peak = 152 * 2 * sm_max * 1e6
+    return {"status": B.ls_strerror(st), "n": n, "time_ms": round(info["time_ms"], 2),
+            "fp64_instr_per_s": round(instr / (info["time_ms"] * 1e-3) / 1e12, 4),
+            "fp64_issue_frac": round(instr / (info["time_ms"] * 1e-3) / dp_peak, 4),
+            "true_rel_res": info["true_rel_res"],
+            "rel_err_vs_xstar": float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs)),
+            "note": ("blocked Cholesky (panels of 32 columns, lower triangle), bit for bit the column "
+                     "factorization: n^3/3 unfused FP64 multiply/subtract instructions, bound by the FP64 pipe")}
 
 
 def run_lu_only(args):

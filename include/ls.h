@@ -63,6 +63,7 @@ extern "C" {
 #define LS_METHOD_BLOCK_GMRES 6    /* ls_block_gmres_solve only                              */
 #define LS_BLOCK_GMRES_MAX_MS 256  /* restart x right-hand sides of ls_block_gmres_solve     */
 #define LS_METHOD_LU 7             /* ls_lu_solve (the direct method)                        */
+#define LS_METHOD_CHOLESKY 8       /* ls_chol_solve (the direct method for SPD A)            */
 
 #define LS_F64      0   /* plain FP64 solve                                            */
 #define LS_F64_PAIR 4   /* kernel-level entry points only: FP64 A given as the FP32 pair
@@ -499,6 +500,41 @@ int ls_autotune(ls_ctx *ctx, const char *path, int flags);
 int ls_tune_load(const char *path);
 int ls_tune_reset(void);
 int ls_tune_lookup(int n, int nrhs, int num_sms, int *ks32, int *tensor_cores);
+
+/*
+ * The direct method for symmetric positive definite A (paper: the Cholesky
+ * factorization A = L L^T of the direct-methods section, Fig. 3 and the block
+ * relations after it; then L y = b and L^T x = y).  Column by column: l_kk =
+ * sqrt(a_kk), l_ik = a_ik / l_kk, a_ij -= l_ik l_jk (k < j <= i); only the
+ * lower triangle of A is read.  b is carried along as an extra row, so L y =
+ * b is done during the factorization.  FP64, run by panels of 32 columns (the
+ * panel's steps, then the trailing lower triangle), which only regroups the
+ * operations: every element of L and y is bit for bit what the plain column
+ * factorization and forward substitution give in FP64 (IEEE square root and
+ * division, multiply and subtract not fused, the updates of each element in
+ * step order); x differs from a scalar back substitution by the order of its
+ * sums.  After the solve the true residual ||b - A x|| is formed
+ * (info->rel_res, true_rel_res; info->iters = 0).  A pivot a_kk <= 0 (A not
+ * positive definite) or NaN returns LS_BREAKDOWN with x unchanged; a residual
+ * that is not finite returns LS_ERR_NAN.  A row-major n x n (host or device),
+ * b and x n vectors; opts may be NULL; opts->precision must be LS_F64.  The
+ * factorization is n^3 / 6 updates of two FP64 instructions each, bound by
+ * the FP64 pipe.
+ */
+int ls_chol_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *x,
+                  const ls_opts *opts, ls_info *info);
+
+/*
+ * The factorization of ls_chol_solve alone: L (n x n, row-major, leading
+ * dimension ldl >= n) receives the lower factor with zeros above the
+ * diagonal, y = L^-1 b.  Outputs may be host or device memory.  Returns
+ * LS_BREAKDOWN when a pivot is not positive and then sets *step (if not NULL)
+ * to that step k; only the panels of 32 steps completed before k are final
+ * in L and y.  *step is -1 otherwise.  LS_ERR_ARG on bad sizes or NULL
+ * pointers.
+ */
+int ls_chol_factor(ls_ctx *ctx, int n, const double *A, int64_t lda, const double *b, double *L,
+                   int64_t ldl, double *y, int *step);
 
 /* Kernels the context has executed on the device since it was created. */
 long long ls_kernel_launches(ls_ctx *ctx);

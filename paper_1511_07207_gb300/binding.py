@@ -21,6 +21,7 @@ LS_METHOD_CG, LS_METHOD_GMRES, LS_METHOD_BICGSTAB, LS_METHOD_JACOBI, LS_METHOD_G
 LS_METHOD_BLOCK_CG, LS_BLOCK_CG_MAX_S = 5, 16
 LS_METHOD_BLOCK_GMRES, LS_BLOCK_GMRES_MAX_MS = 6, 256
 LS_METHOD_LU = 7
+LS_METHOD_CHOLESKY = 8
 LS_F64, LS_BF16_IR, LS_FP8_IR, LS_F32_IR = 0, 1, 2, 3
 LS_F64_PAIR = 4
 LS_REFINE_FCG, LS_REFINE_IR = 0, 1
@@ -34,7 +35,7 @@ ABI_FUNCTIONS = (
     "ls_cg_solve", "ls_gmres_solve", "ls_bicgstab_solve", "ls_jacobi_solve", "ls_gauss_seidel_solve", "ls_block_cg_solve", "ls_block_gmres_solve", "ls_lu_solve", "ls_lu_factor", "ls_batch_solve", "ls_server_start", "ls_server_submit",
     "ls_server_poll", "ls_server_stop", "ls_gemv", "ls_gemv_timed", "ls_gemv_noalloc",
     "ls_quantize", "ls_split_f64", "ls_kernel_launches", "ls_strerror", "ls_selftest_waits",
-    "ls_autotune", "ls_tune_load", "ls_tune_reset", "ls_tune_lookup",
+    "ls_autotune", "ls_tune_load", "ls_tune_reset", "ls_tune_lookup", "ls_chol_solve", "ls_chol_factor",
 )
 
 
@@ -96,11 +97,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_size_t)]
         lib.ls_set_workspace.argtypes = [P, P, ctypes.c_size_t]
         for fn in (lib.ls_cg_solve, lib.ls_gmres_solve, lib.ls_bicgstab_solve, lib.ls_jacobi_solve,
-               lib.ls_gauss_seidel_solve, lib.ls_lu_solve):
+               lib.ls_gauss_seidel_solve, lib.ls_lu_solve, lib.ls_chol_solve):
             fn.argtypes = [P, I, P, I64, P, P, ctypes.POINTER(ls_opts), ctypes.POINTER(ls_info)]
         for fn in (lib.ls_block_cg_solve, lib.ls_block_gmres_solve):
             fn.argtypes = [P, I, I, P, I64, P, I64, P, I64, ctypes.POINTER(ls_opts), ctypes.POINTER(ls_info)]
         lib.ls_lu_factor.argtypes = [P, I, P, I64, P, P, I64, P, P]
+        lib.ls_chol_factor.argtypes = [P, I, P, I64, P, P, I64, P, ctypes.POINTER(I)]
         lib.ls_batch_solve.argtypes = [P, I, ctypes.POINTER(ls_system), ctypes.POINTER(ls_info)]
         lib.ls_server_start.argtypes = [P, ctypes.POINTER(ls_server_cfg), ctypes.POINTER(P)]
         lib.ls_server_submit.argtypes = [P, ctypes.POINTER(ls_system),
@@ -423,6 +425,27 @@ def ls_lu_factor(ctx, A, b, LU, ipiv, y):
     if LU.shape[0] != n or LU.shape[1] < n:
         raise ValueError("LU must be n x n")
     return load().ls_lu_factor(ctx, n, ptr(A), lead_dim(A), ptr(b), ptr(LU), lead_dim(LU), ptr(ipiv), ptr(y))
+
+
+def ls_chol_solve(ctx, A, b, x, opts=None):
+    """The direct method for SPD A: A = L L^T, then L y = b, L^T x = y; see ls_cg_solve."""
+    return _solve(load().ls_chol_solve, ctx, A, b, x, opts)
+
+
+def ls_chol_factor(ctx, A, b, L, y):
+    """The Cholesky factorization alone into L (n x n row-major, zeros above the
+    diagonal) and y = L^-1 b.  Returns (status, step): step is the failing
+    step on LS_BREAKDOWN, else -1."""
+    _check_f64(A, b, L, y)
+    n = _check_square(A)
+    _check_vec(b, n, "b")
+    _check_vec(y, n, "y")
+    if L.shape[0] != n or L.shape[1] < n:
+        raise ValueError("L must be n x n")
+    step = ctypes.c_int(-1)
+    st = load().ls_chol_factor(ctx, n, ptr(A), lead_dim(A), ptr(b), ptr(L), lead_dim(L), ptr(y),
+                               ctypes.byref(step))
+    return st, step.value
 
 
 def ls_batch_solve(ctx, systems):

@@ -869,6 +869,10 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
         *bytes = lu_workspace_bytes(n, c->K.coop_grid, a_on_device != 0);
         return LS_OK;
     }
+    if (method == LS_METHOD_CHOLESKY) {
+        *bytes = chol_workspace_bytes(n, a_on_device != 0);
+        return LS_OK;
+    }
     if (method == LS_METHOD_BLOCK_GMRES) {
         if (nrhs > BGM_MAX_S || o.restart < 1 || o.restart * nrhs > BGM_MAX_MS) return LS_ERR_ARG;
         *bytes = bgm_workspace_bytes(n, nrhs, o.restart, c->K.coop_grid, a_on_device != 0);

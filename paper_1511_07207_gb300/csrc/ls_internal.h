@@ -278,6 +278,24 @@ struct LuKernels {
 };
 LuKernels lu_kernels();
 
+// ---- Cholesky (k_chol.cu) --------------------------------------------------------------------
+struct CholArgs {
+    int n;
+    double *W;                    // [A; b^T], (n + 1) x n, row-major, leading dimension ld (lower part used)
+    long long ld;
+    double *Lp;                   // the current panel's l's, (n + 1) x 32, row-major
+    double *y;                    // back substitution: y, overwritten by the updated right sides
+    double *x;                    // the solution
+    GridBar *bar;
+    State *st;                    // status LS_BREAKDOWN (iter = the failing step) on a pivot <= 0
+};
+struct CholKernels {
+    void *panel, *trail, *backsolve, *zero_upper;   // panel and trail take (CholArgs, k0, k1 / nb)
+    int block, nb, tile;
+};
+CholKernels chol_kernels();
+size_t chol_workspace_bytes(int n, bool a_on_device);
+
 // ---- self-test of the bounded waits (k_selftest.cu) -------------------------------------------
 cudaError_t selftest_launch(int which, GridBar *bar, State *st, cudaStream_t s);
 

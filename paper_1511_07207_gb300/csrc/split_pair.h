@@ -51,6 +51,18 @@ LS_SPLIT_FN void split_pair_plain(double v, float &h, float &l) {
     l = (float)(v - (double)h);
 }
 
+#if defined(__CUDACC__)
+// The plain form, out of line on the device: a call is a real branch, so the
+// common path below never issues the plain form's FP64 instructions (an
+// instruction whose predicate is off still takes an issue slot of its pipe,
+// and the FP64 pipe runs at 1/64 of the FP32 rate).
+static __device__ __noinline__ float2 split_pair_plain_call(double v) {
+    float2 r;
+    split_pair_plain(v, r.x, r.y);
+    return r;
+}
+#endif
+
 LS_SPLIT_FN void split_pair(double v, float &h, float &l) {
     uint64_t u;
     memcpy(&u, &v, 8);
@@ -63,7 +75,13 @@ LS_SPLIT_FN void split_pair(double v, float &h, float &l) {
         return;
     }
     if (e < 1023 - 74 || e > 1023 + 126) {
+#if defined(__CUDA_ARCH__)
+        const float2 r = split_pair_plain_call(v);
+        h = r.x;
+        l = r.y;
+#else
         split_pair_plain(v, h, l);
+#endif
         return;
     }
     const uint32_t keep = ((hw & 0xFFFFFu) << 3) | (lw >> 29);   // top 23 bits of f

@@ -67,6 +67,8 @@ def _null_context_calls(lib):
         "ls_jacobi_solve": lambda: lib.ls_jacobi_solve(None, 4, p, 4, p, p, *oi),
         "ls_gauss_seidel_solve": lambda: lib.ls_gauss_seidel_solve(None, 4, p, 4, p, p, *oi),
         "ls_lu_solve": lambda: lib.ls_lu_solve(None, 4, p, 4, p, p, *oi),
+        "ls_chol_solve": lambda: lib.ls_chol_solve(None, 4, p, 4, p, p, *oi),
+        "ls_chol_factor": lambda: lib.ls_chol_factor(None, 2, p, 2, p, p, 2, p, None),
         "ls_block_cg_solve": lambda: lib.ls_block_cg_solve(None, 2, 2, p, 2, p, 2, p, 2, *oi),
         "ls_block_gmres_solve": lambda: lib.ls_block_gmres_solve(None, 2, 2, p, 2, p, 2, p, 2, *oi),
         "ls_lu_factor": lambda: lib.ls_lu_factor(None, 2, p, 2, p, p, 2, pi, p),
