@@ -79,6 +79,7 @@ class Oracle:
         lib.or_jacobi.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P]
         lib.or_gauss_seidel.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P]
         lib.or_block_cg.argtypes = [i, i, P, l, P, P, d, i, i, i, P, P]
+        lib.or_block_cg_deflated.argtypes = [i, i, P, l, P, P, d, i, i, i, P, P, P]
         lib.or_block_gmres.argtypes = [i, i, P, l, P, P, i, d, i, i, i, P, P, P]
         lib.or_ge_solve.argtypes = [i, P, l, P, P]
         lib.or_ge_factor.argtypes = [i, P, l, P, P, P, P]
@@ -161,6 +162,21 @@ class Oracle:
         st = self.lib.or_block_cg(n, s, _p(A), n, _p(Bc), _p(X), rtol, max_iter, int(X0 is not None),
                                   nthreads, ctypes.byref(it), ctypes.byref(rr))
         return dict(X=np.ascontiguousarray(X), status=st, iters=it.value, rel_res=rr.value)
+
+    def block_cg_deflated(self, A, B, rtol=1e-10, max_iter=None, X0=None, nthreads=1):
+        """Block CG with orthonormal, rank-revealed directions (dependent ones
+        dropped).  Returns dict(X, status, iters, rel_res, rank)."""
+        A = _mat(A)
+        n = A.shape[0]
+        B = np.asarray(B, dtype=np.float64).reshape(n, -1)
+        s = B.shape[1]
+        Bc = np.asfortranarray(B)
+        max_iter = 10 * n + 10 if max_iter is None else max_iter
+        X = np.zeros((n, s), order="F") if X0 is None else np.asfortranarray(np.array(X0, dtype=np.float64).reshape(n, s))
+        it, rr, rk = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_int(0)
+        st = self.lib.or_block_cg_deflated(n, s, _p(A), n, _p(Bc), _p(X), rtol, max_iter, int(X0 is not None),
+                                           nthreads, ctypes.byref(it), ctypes.byref(rr), ctypes.byref(rk))
+        return dict(X=np.ascontiguousarray(X), status=st, iters=it.value, rel_res=rr.value, rank=rk.value)
 
     def block_gmres(self, A, B, m=10, rtol=1e-10, max_iter=None, X0=None, nthreads=1):
         """Restarted block GMRES(m) on A X = B.  Returns dict(X, status, iters, cycles, rel_res)."""

@@ -232,6 +232,23 @@ static void chol_solve(int s, const double *L, double *Y) {
     }
 }
 
+/* Y = G^-1 Y for an r x r G = L L^T factored by chol and Y r x c (column-major). */
+static void chol_solve_rect(int r, int c, const double *L, double *Y) {
+    for (int j = 0; j < c; j++) {
+        double *y = Y + (long)j * r;
+        for (int i = 0; i < r; i++) {
+            double v = y[i];
+            for (int k = 0; k < i; k++) v -= L[i + k * r] * y[k];
+            y[i] = v / L[i + i * r];
+        }
+        for (int i = r - 1; i >= 0; i--) {
+            double v = y[i];
+            for (int k = i + 1; k < r; k++) v -= L[k + i * r] * y[k];
+            y[i] = v / L[i + i * r];
+        }
+    }
+}
+
 /* G = U^T V for n x s column-major blocks (s x s, column-major). */
 static void gram(int n, int s, const double *U, const double *V, double *G) {
     for (int j = 0; j < s; j++)
@@ -333,6 +350,151 @@ int or_block_cg(int n, int s, const double *A, long lda, const double *B, double
     *rel_res_out = worst;
     *iters_out = k;
     free(R); free(P); free(Q); free(T); free(rho); free(rhon); free(Lr); free(g); free(al); free(bn);
+    return status;
+}
+
+/*
+ * Orthonormal basis of the range of W (n x s, column-major) with the
+ * dependent columns dropped: modified Gram-Schmidt with column pivoting.
+ * Each step takes, among the columns not yet taken or dropped, the one with
+ * the largest remaining norm, orthogonalizes it once more against the basis
+ * so far, and keeps it as the next basis vector; every remaining column then
+ * loses its component along that vector.  A column whose part outside the
+ * span of the basis is at most tau times its own norm (a zero column
+ * included) is dependent and dropped.  Q receives the rank orthonormal
+ * columns, then zero columns.  Returns the rank.
+ */
+static int orth_rr(int n, int s, const double *W, double *Q, double tau) {
+    double *Wc = malloc(sizeof(double) * (size_t)(n ? n : 1) * s);
+    double *n0 = malloc(sizeof(double) * s), *cur = malloc(sizeof(double) * s);
+    int *state = calloc((size_t)s, sizeof(int));          /* 0 open, 1 taken, 2 dropped */
+    memcpy(Wc, W, sizeof(double) * (size_t)n * s);
+    for (int j = 0; j < s; j++) n0[j] = cur[j] = nrm2(n, Wc + (long)j * n);
+    int r = 0;
+    for (;;) {
+        int p = -1;
+        for (int j = 0; j < s; j++) {
+            if (state[j]) continue;
+            if (!(cur[j] > tau * n0[j])) { state[j] = 2; continue; }
+            if (p < 0 || cur[j] > cur[p]) p = j;
+        }
+        if (p < 0) break;
+        double *w = Wc + (long)p * n;
+        for (int i = 0; i < r; i++) {                      /* the second pass */
+            const double *q = Q + (long)i * n;
+            const double h = dot(n, q, w);
+            for (int t = 0; t < n; t++) w[t] -= h * q[t];
+        }
+        const double nw = nrm2(n, w);
+        if (!(nw > tau * n0[p])) { state[p] = 2; continue; }
+        double *q = Q + (long)r * n;
+        for (int t = 0; t < n; t++) q[t] = w[t] / nw;
+        state[p] = 1;
+        r++;
+        for (int j = 0; j < s; j++) {                      /* the first pass of the others */
+            if (state[j]) continue;
+            double *v = Wc + (long)j * n;
+            const double h = dot(n, q, v);
+            for (int t = 0; t < n; t++) v[t] -= h * q[t];
+            cur[j] = nrm2(n, v);
+        }
+    }
+    for (int j = r; j < s; j++) memset(Q + (long)j * n, 0, sizeof(double) * (size_t)n);
+    free(Wc); free(n0); free(cur); free(state);
+    return r;
+}
+
+/*
+ * Block CG that drops dependent directions instead of breaking down (the
+ * block form of the paper's CG with the search directions kept orthonormal
+ * and of full rank, as in the breakdown-free block CG of Ji and Li):
+ *   R = B - A X;  P = orth(R)                  (rank r <= s)
+ *   loop: Q = A P;  gamma = P^T Q (r x r);  alpha = gamma^-1 (P^T R);
+ *         X += P alpha;  R -= Q alpha;
+ *         stop when every column has ||R_j|| <= rtol ||B_j|| (confirmed on
+ *         the true residual; a failed confirmation restarts from it);
+ *         beta = -gamma^-1 (Q^T R);  P = orth(R + P beta).
+ * The new directions are A-conjugate to P (P^T A (R + P beta) = 0) and span
+ * the same block Krylov space as O'Leary's, so with a full-rank block the
+ * iterates are the same; but dependent, zero or converged residual columns
+ * only lower the rank of P, and gamma stays positive definite for SPD A.
+ * orth drops a column whose part outside the span of the others is at most
+ * 1e-8 of its norm.  iters counts block products; rank_out receives the last
+ * rank.  gamma not positive definite (A not SPD) is a breakdown (status 2).
+ */
+int or_block_cg_deflated(int n, int s, const double *A, long lda, const double *B, double *X,
+                         double rtol, int max_iter, int x0_given, int nthreads,
+                         int *iters_out, double *rel_res_out, int *rank_out) {
+    if (n < 0 || s < 1 || lda < n || max_iter < 0) return OR_ERR_ARG;
+    const double tau = 1e-8;
+    const size_t nb = sizeof(double) * (size_t)(n ? n : 1) * s, sb = sizeof(double) * s * s;
+    double *R = malloc(nb), *P = malloc(nb), *Q = malloc(nb), *T = malloc(nb);
+    double *g = malloc(sb), *al = malloc(sb), *be = malloc(sb), *bn = malloc(sizeof(double) * s);
+    int status = OR_NOT_CONVERGED, k = 0, r = 0;
+    for (int j = 0; j < s; j++) bn[j] = nrm2(n, B + (long)j * n);
+    if (!x0_given) memset(X, 0, nb);
+    #define RESTART_D()                                                            \
+        do {                                                                       \
+            for (int j = 0; j < s; j++)                                            \
+                residual(n, A, lda, B + (long)j * n, X + (long)j * n, R + (long)j * n, nthreads); \
+            r = orth_rr(n, s, R, P, tau);                                          \
+        } while (0)
+    RESTART_D();
+    int check = 1;
+    for (int j = 0; j < s; j++) check = check && nrm2(n, R + (long)j * n) <= rtol * bn[j];
+    for (;;) {
+        if (check) {
+            int ok = 1;
+            for (int j = 0; j < s && ok; j++) {
+                residual(n, A, lda, B + (long)j * n, X + (long)j * n, T, nthreads);
+                ok = nrm2(n, T) <= rtol * bn[j];
+            }
+            if (ok) { status = OR_OK; break; }
+            RESTART_D();
+            check = 0;
+        }
+        if (k >= max_iter) break;
+        if (r == 0) { status = OR_BREAKDOWN; break; }      /* nothing left to search, not converged */
+        for (int j = 0; j < r; j++) gemv(n, n, A, lda, P + (long)j * n, Q + (long)j * n, nthreads);
+        gram(n, r, P, Q, g);                                   /* gamma = P^T Q (r x r) */
+        if (chol(r, g)) { status = OR_BREAKDOWN; break; }
+        for (int j = 0; j < s; j++)                            /* alpha = gamma^-1 P^T R (r x s) */
+            for (int i = 0; i < r; i++) al[i + j * r] = dot(n, P + (long)i * n, R + (long)j * n);
+        chol_solve_rect(r, s, g, al);
+        for (int j = 0; j < s; j++)
+            for (int c = 0; c < r; c++) {
+                const double a = al[c + j * r];
+                for (int i = 0; i < n; i++) {
+                    X[i + (long)j * n] += P[i + (long)c * n] * a;
+                    R[i + (long)j * n] -= Q[i + (long)c * n] * a;
+                }
+            }
+        k++;
+        int conv = 1;
+        for (int j = 0; j < s; j++) conv = conv && nrm2(n, R + (long)j * n) <= rtol * bn[j];
+        if (conv) { check = 1; continue; }
+        for (int j = 0; j < s; j++)                            /* beta = -gamma^-1 Q^T R (r x s) */
+            for (int i = 0; i < r; i++) be[i + j * r] = -dot(n, Q + (long)i * n, R + (long)j * n);
+        chol_solve_rect(r, s, g, be);
+        for (int j = 0; j < s; j++)                            /* T = R + P beta */
+            for (int i = 0; i < n; i++) {
+                double v = R[i + (long)j * n];
+                for (int c = 0; c < r; c++) v += P[i + (long)c * n] * be[c + j * r];
+                T[i + (long)j * n] = v;
+            }
+        r = orth_rr(n, s, T, P, tau);                           /* P = orth(R + P beta) */
+    }
+    #undef RESTART_D
+    double worst = 0.0;
+    for (int j = 0; j < s; j++) {
+        residual(n, A, lda, B + (long)j * n, X + (long)j * n, T, nthreads);
+        const double rr = bn[j] > 0.0 ? nrm2(n, T) / bn[j] : nrm2(n, T);
+        if (rr > worst || rr != rr) worst = rr;
+    }
+    *rel_res_out = worst;
+    *iters_out = k;
+    if (rank_out) *rank_out = r;
+    free(R); free(P); free(Q); free(T); free(g); free(al); free(be); free(bn);
     return status;
 }
 

@@ -12,6 +12,7 @@ import pytest
 import oracle as oracle_pkg
 import test_oracle_bicgstab as tbs
 import test_oracle_block_cg as tbc
+import test_oracle_block_cg_deflated as tbd
 import test_oracle_block_gmres as tbg
 import test_oracle_cg as tcg
 import test_oracle_cholesky as tch
@@ -109,6 +110,16 @@ MUTATIONS = {
     "bicgstab_x_drops_omega_s": ("for (int i = 0; i < n; i++) x[i] += alpha * p[i] + omega * s[i];",
                                  "for (int i = 0; i < n; i++) x[i] += alpha * p[i];",
                                  lambda o: tgo.test_bicgstab_worked_example(o)),
+    # the deflating block CG
+    "bcgd_beta_sign": ("for (int i = 0; i < r; i++) be[i + j * r] = -dot(n, Q + (long)i * n, R + (long)j * n);",
+                       "for (int i = 0; i < r; i++) be[i + j * r] = dot(n, Q + (long)i * n, R + (long)j * n);",
+                       lambda o: tbd.test_full_rank_is_the_block_krylov_minimiser_and_oleary(o, 3, 5)),
+    "bcgd_alpha_from_q": ("for (int i = 0; i < r; i++) al[i + j * r] = dot(n, P + (long)i * n, R + (long)j * n);",
+                          "for (int i = 0; i < r; i++) al[i + j * r] = dot(n, Q + (long)i * n, R + (long)j * n);",
+                          lambda o: tbd.test_s1_is_cg(o)),
+    "bcgd_keeps_dependent": ("    const double tau = 1e-8;\n    const size_t nb",
+                             "    const double tau = 0.0;\n    const size_t nb",
+                             lambda o: tbd.test_rank_deficient_blocks_converge(o)),
     "chol_no_sqrt": ("double lkk = sqrt(akk);", "double lkk = akk;",
                      lambda o: tch.test_cholesky_worked_example(o)),
     "chol_update_reads_upper": ("W[(long)i * n + j] -= lik * W[(long)j * n + k];",
