@@ -95,6 +95,9 @@ typedef struct {
                            (default: GB300 runs FP32 at 64x its FP64 FMA rate, so the
                            product becomes HBM-bound; extra workspace 8 n^2 bytes);
                            1 = native FP64 FMA                                          */
+    int deflate;        /* ls_block_cg_solve: 1 = keep the search directions orthonormal and
+                           of full rank, dropping dependent ones (no breakdown on dependent,
+                           zero or converged columns; default), 0 = O'Leary's form          */
 } ls_opts;
 
 #define LS_MAX_RESTART 128
@@ -225,20 +228,31 @@ int ls_gauss_seidel_solve(ls_ctx *ctx, int n, const double *A, int64_t lda, cons
 
 /*
  * Block CG (paper: the CG paragraph's method, for s right-hand sides at once
- * in O'Leary's block form) for SPD A: A X = B with B and X n x s,
- * column-major (column j at B + j*ldb, X + j*ldx), 1 <= s <= 16.  Each step
- * forms Q = A P (s products of the FP64 GEMV, A streamed as its FP32 pair
- * unless opts->f64_matvec), gamma = P^T Q, alpha = gamma^-1 (R^T R) by
- * Cholesky, X += P alpha, R -= Q alpha, beta = (R^T R)^-1 (R^T R)', and
- * P = R + P beta.  The iterate minimises the A-norm error over the block
- * Krylov space, so it needs at most as many steps as single-vector CG on any
- * column.  Stops when every column has ||R_j|| <= rtol ||B_j||, confirmed on
- * the true residual (a failed confirmation restarts from it).
- * info->iters counts block steps (s products each); info->rel_res and
- * true_rel_res are the largest true relative residual over the columns.  A
- * rank-deficient residual block (linearly dependent or zero columns of B, or
- * of R during the iteration) makes a Cholesky factor fail: LS_BREAKDOWN with
- * the last iterate in X.  X0 is read when opts->x0_given.  opts->precision
+ * in block form) for SPD A: A X = B with B and X n x s, column-major (column
+ * j at B + j*ldb, X + j*ldx), 1 <= s <= 16.  Every step forms the block
+ * product Q = A P (A streamed once for all columns, as its FP32 pair unless
+ * opts->f64_matvec).  Two forms:
+ *   opts->deflate = 1 (default): the search directions are kept orthonormal
+ *   and of full rank r <= s, dependent ones dropped: gamma = P^T Q (r x r),
+ *   alpha = gamma^-1 (P^T R), X += P alpha, R -= Q alpha, beta =
+ *   -gamma^-1 (Q^T R), P = orth(R + P beta), where orth keeps a column only
+ *   if its part outside the span of the columns kept before it exceeds 1e-8
+ *   of its norm (Gram matrix of the normalized columns, Cholesky with
+ *   diagonal pivoting, then a second pass).  Dependent, zero or converged
+ *   residual columns only lower r: no breakdown for SPD A.
+ *   opts->deflate = 0: O'Leary's form, gamma = P^T Q, alpha = gamma^-1
+ *   (R^T R), beta = (R^T R)^-1 (R^T R)', P = R + P beta; a rank-deficient
+ *   residual block (linearly dependent or zero columns of B, or of R during
+ *   the iteration) makes a Cholesky factor fail: LS_BREAKDOWN with the last
+ *   iterate in X.
+ * With a full-rank block both iterates minimise the A-norm error over the
+ * block Krylov space, so they need at most as many steps as single-vector CG
+ * on any column.  Stops when every column has ||R_j|| <= rtol ||B_j||,
+ * confirmed on the true residual (a failed confirmation restarts from it).
+ * info->iters counts block steps (one block product each); info->rel_res and
+ * true_rel_res are the largest true relative residual over the columns.  The
+ * deflating form returns LS_BREAKDOWN only when gamma is not positive
+ * definite (A not SPD).  X0 is read when opts->x0_given.  opts->precision
  * must be LS_F64 (else LS_ERR_UNSUPPORTED); s outside 1..16 or ld < n is
  * LS_ERR_ARG.  Host or device pointers, as for ls_cg_solve.
  */

@@ -1,4 +1,6 @@
-// k_bcg.cu -- O'Leary's block conjugate gradient for s right-hand sides.
+// k_bcg.cu -- block conjugate gradient for s right-hand sides: O'Leary's form
+// and a deflating form with orthonormal, rank-revealed search directions (the
+// second half of this file).
 //
 // Block CG (the paper's CG paragraph, for several right-hand sides at once
 // in O'Leary's block form) replaces CG's scalars by s x s matrices:
@@ -344,11 +346,460 @@ __global__ void __launch_bounds__(BK) bcg_check_kernel(BcgVecs v, cudaGraphCondi
     }
 }
 
+// ============================================================================
+// The deflating form: the search directions P are kept orthonormal and of
+// full rank r <= s by a rank-revealing orthogonalization, dependent ones
+// dropped, so dependent, zero or converged residual columns never make a
+// step matrix singular (block CG with orthonormalized directions, as in the
+// breakdown-free block CG of Ji and Li):
+//   Q = A P;  gamma = P^T Q (r x r);  alpha = gamma^-1 (P^T R);
+//   X += P alpha;  R -= Q alpha;  per-column stop test;
+//   beta = -gamma^-1 (Q^T R);  P = orth(R + P beta).
+// The new directions are A-conjugate to P and span the same block Krylov
+// space as O'Leary's, so with a full-rank block the iterates are the same.
+// orth(W): W^T W, columns normalized to unit norm, Cholesky with diagonal
+// pivoting (largest remaining diagonal first) that stops when the remaining
+// diagonal is at most tau^2 = 1e-16 (the column's part outside the span of
+// the taken ones is at most 1e-8 of its norm: dependent), then P = W T with
+// T = D^-1 Pi L^-T, and a second pass (Gram of P, Cholesky, P = P L2^-T).
+// Small matrices use leading dimension BCG_MAX_S; the s x s algebra (at most
+// 16 x 16) runs on one thread.
+// ============================================================================
+constexpr int SL = BCG_MAX_S;              // leading dimension of the small matrices
+constexpr double BCGD_TAU2 = 1e-16;        // (1e-8)^2 on the normalized diagonal
+
+// This CTA's partial U[:, :nu]^T V[:, :nv] over rows [lo, hi) into buf[cta][SL*SL].
+__device__ __forceinline__ void gram_partial_ld(const BcgVecs &v, double *buf, const double *U, int nu,
+                                                const double *V, int nv, long long lo, long long hi) {
+    for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
+        const int a = e % nu, b = e / nu;
+        const double *u = U + (long long)a * v.ld, *w = V + (long long)b * v.ld;
+        double acc = 0.0;
+        for (long long i = lo; i < hi; i++) acc += u[i] * w[i];
+        buf[(size_t)blockIdx.x * SL * SL + a + b * SL] = acc;
+    }
+}
+// The sum of the CTAs' partials in CTA order (one thread).
+__device__ __forceinline__ void gram_reduce_ld(const double *buf, int nu, int nv, double *G) {
+    for (int b = 0; b < nv; b++)
+        for (int a = 0; a < nu; a++) {
+            double acc = 0.0;
+            for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&buf[(size_t)c * SL * SL + a + b * SL]);
+            G[a + b * SL] = acc;
+        }
+}
+
+// Cholesky of the leading r x r block (lower triangle, leading dimension SL);
+// false on a pivot that is not positive.
+__device__ bool small_chol(int r, double *G) {
+    for (int j = 0; j < r; j++) {
+        double d = G[j + j * SL];
+        for (int k = 0; k < j; k++) d -= G[j + k * SL] * G[j + k * SL];
+        if (!(d > 0.0)) return false;
+        d = sqrt(d);
+        G[j + j * SL] = d;
+        for (int i = j + 1; i < r; i++) {
+            double x = G[i + j * SL];
+            for (int k = 0; k < j; k++) x -= G[i + k * SL] * G[j + k * SL];
+            G[i + j * SL] = x / d;
+        }
+    }
+    return true;
+}
+// Y (r x c) = (L L^T)^-1 Y.
+__device__ void small_chol_solve(int r, int c, const double *L, double *Y) {
+    for (int j = 0; j < c; j++) {
+        double *y = Y + j * SL;
+        for (int i = 0; i < r; i++) {
+            double x = y[i];
+            for (int k = 0; k < i; k++) x -= L[i + k * SL] * y[k];
+            y[i] = x / L[i + i * SL];
+        }
+        for (int i = r - 1; i >= 0; i--) {
+            double x = y[i];
+            for (int k = i + 1; k < r; k++) x -= L[k + i * SL] * y[k];
+            y[i] = x / L[i + i * SL];
+        }
+    }
+}
+// M = L^-T (upper triangular, r x r) for a lower-triangular L.
+__device__ void small_inv_t(int r, const double *L, double *M) {
+    for (int b = 0; b < SL; b++)
+        for (int a = 0; a < SL; a++) M[a + b * SL] = 0.0;
+    for (int b = 0; b < r; b++) {                  // column b of M solves L^T m = e_b
+        for (int a = r - 1; a >= 0; a--) {
+            double x = a == b ? 1.0 : 0.0;
+            for (int k = a + 1; k < r; k++) x -= L[k + a * SL] * M[k + b * SL];
+            M[a + b * SL] = x / L[a + a * SL];
+        }
+    }
+}
+
+// First pass of orth: from G = W^T W (s x s) the rank r and T (s x s) with
+// W T = the r orthonormal-to-first-order columns (then zero columns).
+// work: 3 SL^2 + 2 SL doubles, iwork: 2 SL ints (shared memory of the caller).
+__device__ int rr_factor(int s, const double *G, double *T, double *work, int *iwork) {
+    double *Lp = work, *M = work + SL * SL, *Lcm = work + 2 * SL * SL;
+    double *d = work + 3 * SL * SL, *rem = d + SL;
+    int *perm = iwork, *state = iwork + SL;
+#define Lc(q, t) Lcm[(q) + (t) * SL]
+    for (int j = 0; j < s; j++) {
+        d[j] = sqrt(G[j + j * SL]);
+        state[j] = d[j] > 0.0 ? 0 : 2;             // 0 open, 1 taken, 2 dropped
+        rem[j] = 1.0;
+    }
+    int r = 0;
+    for (;;) {
+        int p = -1;
+        for (int j = 0; j < s; j++) {
+            if (state[j]) continue;
+            if (!(rem[j] > BCGD_TAU2)) { state[j] = 2; continue; }
+            if (p < 0 || rem[j] > rem[p]) p = j;
+        }
+        if (p < 0) break;
+        const double lpp = sqrt(rem[p]);
+        perm[r] = p;
+        state[p] = 1;
+        Lc(p, r) = lpp;
+        for (int q = 0; q < s; q++) {
+            if (state[q]) continue;
+            double x = G[q + p * SL] / (d[q] * d[p]);
+            for (int t = 0; t < r; t++) x -= Lc(q, t) * Lc(p, t);
+            Lc(q, r) = x / lpp;
+            rem[q] -= Lc(q, r) * Lc(q, r);
+        }
+        r++;
+    }
+    for (int b = 0; b < SL; b++)
+        for (int a = 0; a < SL; a++) Lp[a + b * SL] = 0.0;
+    for (int a = 0; a < r; a++)
+        for (int t = 0; t <= a; t++) Lp[a + t * SL] = Lc(perm[a], t);
+    small_inv_t(r, Lp, M);
+    for (int e = 0; e < SL * SL; e++) T[e] = 0.0;
+    for (int a = 0; a < r; a++)
+        for (int b = 0; b < r; b++) T[perm[a] + b * SL] = M[a + b * SL] / d[perm[a]];
+#undef Lc
+    return r;
+}
+
+// P = orth(W) over the whole grid (cooperative launch; W and P must differ).
+// On return sm->rank holds r and sm->w2 the squared column norms of W.
+// false if a grid barrier gave up or the second pass failed.
+__device__ bool coop_orth(const BcgVecs &v, const double *W, long long lo, long long hi) {
+    __shared__ double G[SL * SL], T[SL * SL], work[3 * SL * SL + 2 * SL];
+    __shared__ int r_s, iwork[2 * SL];
+    BcgSmall *sm = v.sm;
+    const int s = v.s;
+    gram_partial_ld(v, v.part, W, s, W, s, lo, hi);
+    if (!grid_sync(v.bar, v.st)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        gram_reduce_ld(v.part, s, s, G);
+        for (int j = 0; j < s; j++) sm->w2[j] = G[j + j * SL];
+        bool nan = false;
+        for (int j = 0; j < s; j++) nan = nan || !isfinite(G[j + j * SL]);
+        const int r = nan ? 0 : rr_factor(s, G, T, work, iwork);
+        for (int e = 0; e < SL * SL; e++) sm->T[e] = T[e];
+        sm->rank = r;
+    }
+    if (!grid_sync(v.bar, v.st)) return false;
+    if (threadIdx.x == 0) r_s = *(volatile int *)&sm->rank;
+    for (int e = threadIdx.x; e < SL * SL; e += blockDim.x) T[e] = __ldcg(&sm->T[e]);
+    __syncthreads();
+    const int r = r_s;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {     // P = W T
+        double w[BCG_MAX_S];
+#pragma unroll
+        for (int c = 0; c < BCG_MAX_S; c++) w[c] = c < s ? W[(long long)c * v.ld + i] : 0.0;
+        for (int b = 0; b < s; b++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < BCG_MAX_S; c++)
+                if (c < s) acc += w[c] * T[c + b * SL];
+            v.P[(long long)b * v.ld + i] = acc;
+        }
+    }
+    __syncthreads();
+    gram_partial_ld(v, v.part, v.P, r, v.P, r, lo, hi);                 // second pass
+    if (!grid_sync(v.bar, v.st)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        gram_reduce_ld(v.part, r, r, G);
+        const bool ok = small_chol(r, G);
+        if (ok) small_inv_t(r, G, T);
+        for (int e = 0; e < SL * SL; e++) sm->T[e] = ok ? T[e] : 0.0;
+        if (!ok) sm->rank = -1;
+    }
+    if (!grid_sync(v.bar, v.st)) return false;
+    for (int e = threadIdx.x; e < SL * SL; e += blockDim.x) T[e] = __ldcg(&sm->T[e]);
+    if (threadIdx.x == 0) r_s = *(volatile int *)&sm->rank;
+    __syncthreads();
+    if (r_s < 0) return false;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {     // P = P L2^-T (upper triangular)
+        double p[BCG_MAX_S];
+#pragma unroll
+        for (int c = 0; c < BCG_MAX_S; c++) p[c] = c < r ? v.P[(long long)c * v.ld + i] : 0.0;
+        for (int b = 0; b < r; b++) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < BCG_MAX_S; c++)
+                if (c <= b) acc += p[c] * T[c + b * SL];
+            v.P[(long long)b * v.ld + i] = acc;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Every column's ||R_j|| <= rtol ||B_j|| (r2 = the squared norms).
+__device__ __forceinline__ bool cols_pass(const BcgVecs &v, const double *r2) {
+    bool ok = true;
+    for (int j = 0; j < v.s; j++) ok = ok && sqrt(r2[j]) <= v.rtol * v.sm->bn[j];
+    return ok;
+}
+
+// X = 0 and R = B (or R from the residual GEMVs), ||B_j||, P = orth(R), the
+// loop conditions.
+__global__ void __launch_bounds__(BK) bcgd_init_kernel(BcgVecs v, int x0_given, cudaGraphConditionalHandle h_outer,
+                                                       cudaGraphConditionalHandle h_inner) {
+    State *st = v.st;
+    BcgSmall *sm = v.sm;
+    count_launch(st);
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    for (int j = 0; j < v.s; j++)
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const long long o = (long long)j * v.ld + i;
+            if (!x0_given) {
+                v.X[o] = 0.0;
+                v.R[o] = v.B[o];
+            }
+        }
+    for (int j = threadIdx.x; j < v.s; j += blockDim.x) {
+        const double *b = v.B + (long long)j * v.ld;
+        double acc = 0.0;
+        for (long long i = lo; i < hi; i++) acc += b[i] * b[i];
+        v.part2[(size_t)blockIdx.x * BCG_MAX_S + j] = acc;
+    }
+    __syncthreads();
+    if (!grid_sync(v.bar, st)) return;
+    if (blockIdx.x == 0 && threadIdx.x < v.s) {
+        double acc = 0.0;
+        for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part2[(size_t)c * BCG_MAX_S + threadIdx.x]);
+        sm->bn[threadIdx.x] = sqrt(acc);
+    }
+    const bool ok = coop_orth(v, v.R, lo, hi);          // its first barrier publishes bn too
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        bool nan = false;
+        for (int j = 0; j < v.s; j++) nan = nan || !isfinite(sm->w2[j]) || !isfinite(sm->bn[j]);
+        const bool pass = !nan && cols_pass(v, sm->w2);
+        int go = 1;
+        if (!ok) {
+            go = 0;
+            if (!*(volatile int *)&st->err) st->status = LS_BREAKDOWN;
+        } else if (nan) {
+            set_err(st, ERRB_NAN);
+            go = 0;
+        } else if (pass || sm->rank == 0) {
+            go = 0;                                     // confirm on the true residual
+        } else if (st->max_iter <= 0) {
+            go = 0;
+        }
+        set_cond(st, h_inner, go);
+        set_cond(st, h_outer, 1u);
+    }
+}
+
+// One step after Q = A P.
+__global__ void __launch_bounds__(BK) bcgd_step_kernel(BcgVecs v, cudaGraphConditionalHandle h_inner) {
+    __shared__ double G[SL * SL], H[SL * SL], coef[SL * SL];
+    __shared__ int flag_s, r_s;
+    State *st = v.st;
+    BcgSmall *sm = v.sm;
+    count_launch(st);
+    const int s = v.s;
+    if (*(volatile int *)&st->err || *(volatile int *)&st->status == LS_BREAKDOWN) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(st, h_inner, 0u);
+        return;
+    }
+    if (threadIdx.x == 0) r_s = *(volatile int *)&sm->rank;
+    __syncthreads();
+    const int r = r_s;
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    // gamma = P^T Q and P^T R
+    gram_partial_ld(v, v.part, v.P, r, v.Q, r, lo, hi);
+    gram_partial_ld(v, v.partb, v.P, r, v.R, s, lo, hi);
+    if (!grid_sync(v.bar, st)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        gram_reduce_ld(v.part, r, r, G);
+        gram_reduce_ld(v.partb, r, s, H);
+        const bool ok = small_chol(r, G);             // positive definite for SPD A
+        if (ok) small_chol_solve(r, s, G, H);          // alpha = gamma^-1 P^T R
+        for (int e = 0; e < SL * SL; e++) {
+            sm->Lg[e] = G[e];
+            sm->alpha[e] = H[e];
+        }
+        sm->ok = ok ? 1 : 0;
+        if (!ok) st->status = LS_BREAKDOWN;
+    }
+    if (!grid_sync(v.bar, st)) return;
+    if (threadIdx.x == 0) flag_s = *(volatile int *)&sm->ok;
+    for (int e = threadIdx.x; e < SL * SL; e += blockDim.x) coef[e] = __ldcg(&sm->alpha[e]);
+    __syncthreads();
+    if (!flag_s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(st, h_inner, 0u);
+        return;
+    }
+    // X += P alpha, R -= Q alpha (row by row), then Q^T R and ||R_j||^2
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        double p[BCG_MAX_S], q[BCG_MAX_S];
+#pragma unroll
+        for (int c = 0; c < BCG_MAX_S; c++) {
+            p[c] = c < r ? v.P[(long long)c * v.ld + i] : 0.0;
+            q[c] = c < r ? v.Q[(long long)c * v.ld + i] : 0.0;
+        }
+        for (int j = 0; j < s; j++) {
+            double dx = 0.0, dr = 0.0;
+#pragma unroll
+            for (int c = 0; c < BCG_MAX_S; c++)
+                if (c < r) {
+                    dx += p[c] * coef[c + j * SL];
+                    dr += q[c] * coef[c + j * SL];
+                }
+            v.X[(long long)j * v.ld + i] += dx;
+            v.R[(long long)j * v.ld + i] -= dr;
+        }
+    }
+    __syncthreads();
+    gram_partial_ld(v, v.part, v.Q, r, v.R, s, lo, hi);
+    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        const double *rr = v.R + (long long)j * v.ld;
+        double acc = 0.0;
+        for (long long i = lo; i < hi; i++) acc += rr[i] * rr[i];
+        v.part2[(size_t)blockIdx.x * BCG_MAX_S + j] = acc;
+    }
+    if (!grid_sync(v.bar, st)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double r2[BCG_MAX_S];
+        bool nan = false;
+        for (int j = 0; j < s; j++) {
+            double acc = 0.0;
+            for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part2[(size_t)c * BCG_MAX_S + j]);
+            r2[j] = acc;
+            nan = nan || !isfinite(acc);
+        }
+        const bool pass = !nan && cols_pass(v, r2);
+        int go = 0;
+        if (!nan && !pass) {
+            gram_reduce_ld(v.part, r, s, H);
+            for (int e = 0; e < SL * SL; e++) G[e] = sm->Lg[e];
+            small_chol_solve(r, s, G, H);              // beta = -gamma^-1 Q^T R
+            for (int e = 0; e < SL * SL; e++) sm->beta[e] = -H[e];
+            go = 1;
+        }
+        st->iter++;
+        if (nan) set_err(st, ERRB_NAN);
+        sm->update_p = go;
+        if (go && st->iter >= st->max_iter) go = 0;
+        sm->ok = go;
+    }
+    if (!grid_sync(v.bar, st)) return;
+    if (threadIdx.x == 0) flag_s = *(volatile int *)&sm->update_p;
+    for (int e = threadIdx.x; e < SL * SL; e += blockDim.x) coef[e] = __ldcg(&sm->beta[e]);
+    __syncthreads();
+    if (!flag_s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(st, h_inner, 0u);
+        return;
+    }
+    // W = R + P beta into Q's storage, then P = orth(W)
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        double p[BCG_MAX_S];
+#pragma unroll
+        for (int c = 0; c < BCG_MAX_S; c++) p[c] = c < r ? v.P[(long long)c * v.ld + i] : 0.0;
+        for (int j = 0; j < s; j++) {
+            double acc = v.R[(long long)j * v.ld + i];
+#pragma unroll
+            for (int c = 0; c < BCG_MAX_S; c++)
+                if (c < r) acc += p[c] * coef[c + j * SL];
+            v.Q[(long long)j * v.ld + i] = acc;
+        }
+    }
+    __syncthreads();
+    const bool ok = coop_orth(v, v.Q, lo, hi);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int go = *(volatile int *)&sm->ok;
+        if (!ok) {
+            go = 0;
+            if (!*(volatile int *)&st->err) st->status = LS_BREAKDOWN;
+        } else if (sm->rank == 0) {
+            go = 0;                                     // nothing left to search: confirm
+        }
+        set_cond(st, h_inner, go ? 1u : 0u);
+    }
+}
+
+// After the loop: the true residual (residual GEMVs, ||R_j||^2 in sm->r2);
+// accept, stop, or restart from it with P = orth(R).
+__global__ void __launch_bounds__(BK) bcgd_check_kernel(BcgVecs v, cudaGraphConditionalHandle h_outer,
+                                                        cudaGraphConditionalHandle h_inner) {
+    __shared__ int restart_s;
+    State *st = v.st;
+    BcgSmall *sm = v.sm;
+    count_launch(st);
+    const int s = v.s;
+    if (threadIdx.x == 0) {
+        bool pass = true, nan = false;
+        for (int j = 0; j < s; j++) {
+            const double r2 = *(volatile double *)&sm->r2[j];
+            nan = nan || !isfinite(r2);
+            pass = pass && sqrt(r2) <= v.rtol * sm->bn[j];
+        }
+        int restart = 0;
+        if (*(volatile int *)&st->err || nan) {
+            if (nan) set_err(st, ERRB_NAN);
+        } else if (*(volatile int *)&st->status == LS_BREAKDOWN) {
+        } else if (pass) {
+            if (blockIdx.x == 0) st->status = LS_OK;
+        } else if (*(volatile int *)&st->iter >= st->max_iter) {
+            if (blockIdx.x == 0) st->status = LS_NOT_CONVERGED;
+        } else {
+            restart = 1;
+        }
+        restart_s = restart;
+    }
+    __syncthreads();
+    if (!restart_s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            set_cond(st, h_outer, 0u);
+            set_cond(st, h_inner, 0u);
+        }
+        return;
+    }
+    long long lo, hi;
+    block_range(v.n, blockIdx.x, gridDim.x, lo, hi);
+    const bool ok = coop_orth(v, v.R, lo, hi);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int go = 1;
+        if (!ok) {
+            go = 0;
+            if (!*(volatile int *)&st->err) st->status = LS_BREAKDOWN;
+        } else if (sm->rank == 0) {
+            go = 0;
+            st->status = LS_BREAKDOWN;                  // not converged and nothing left to search
+        }
+        st->cycles++;
+        set_cond(st, h_inner, go ? 1u : 0u);
+        set_cond(st, h_outer, go ? 1u : 0u);
+    }
+}
+
 BcgKernels bcg_kernels() {
     BcgKernels K{};
     K.init = reinterpret_cast<void *>(&bcg_init_kernel);
     K.step = reinterpret_cast<void *>(&bcg_step_kernel);
     K.check = reinterpret_cast<void *>(&bcg_check_kernel);
+    K.dinit = reinterpret_cast<void *>(&bcgd_init_kernel);
+    K.dstep = reinterpret_cast<void *>(&bcgd_step_kernel);
+    K.dcheck = reinterpret_cast<void *>(&bcgd_check_kernel);
     K.block = BK;
     return K;
 }

@@ -230,6 +230,7 @@ extern "C" int ls_opts_default(ls_opts *o) {
     o->x0_given = 0;
     o->reorth = 0;
     o->f64_matvec = 0;
+    o->deflate = 1;
     return LS_OK;
 }
 

@@ -17,7 +17,7 @@ using namespace lsi;
 namespace {
 
 struct BcgLayout {
-    double *X, *R, *P, *Q, *B, *part, *part2, *Astage;
+    double *X, *R, *P, *Q, *B, *part, *partb, *part2, *Astage;
     BcgSmall *sm;
     float *Ahi, *Alo;
     float *Ph, *Pl;      // P split for the block product (pair path)
@@ -37,6 +37,7 @@ BcgLayout bcg_layout(void *base, int n, int s, int grid, bool stageA, bool split
     L.Q = cv.take<double>((size_t)L.ld * s);
     L.B = cv.take<double>((size_t)L.ld * s);
     L.part = cv.take<double>((size_t)grid * BCG_MAX_S * BCG_MAX_S);
+    L.partb = cv.take<double>((size_t)grid * BCG_MAX_S * BCG_MAX_S);
     L.part2 = cv.take<double>((size_t)grid * BCG_MAX_S);
     L.sm = cv.take<BcgSmall>(1);
     L.Ahi = split ? cv.take<float>((size_t)n * L.ld32) : nullptr;
@@ -65,8 +66,10 @@ void resid_nodes(ls_ctx *c, Chain &ch, const GemvLaunch &GL, const BcgVecs &v, c
 }
 
 int build_bcg_graph(ls_ctx *c, const BcgVecs &v, const BcgLayout &L, const GemvLaunch &GL, int x0_given,
-                    const long long *key) {
+                    int deflate, const long long *key) {
     const BcgKernels K = bcg_kernels();
+    void *const k_init = deflate ? K.dinit : K.init, *const k_step = deflate ? K.dstep : K.step;
+    void *const k_check = deflate ? K.dcheck : K.check;
     Root R;
     if (!R.create()) return LS_ERR_CUDA;
     cudaGraphConditionalHandle ho, hi;
@@ -80,7 +83,7 @@ int build_bcg_graph(ls_ctx *c, const BcgVecs &v, const BcgLayout &L, const GemvL
         BcgVecs vv = v;
         int x0 = x0_given;
         void *args[] = {&vv, &x0, &ho, &hi};
-        top.kernel(K.init, c->K.coop_grid, K.block, 0, args, true);
+        top.kernel(k_init, c->K.coop_grid, K.block, 0, args, true);
     }
     Chain outer = top.loop(ho);
     Chain inner = outer.loop(hi);
@@ -123,13 +126,13 @@ int build_bcg_graph(ls_ctx *c, const BcgVecs &v, const BcgLayout &L, const GemvL
     {
         BcgVecs vv = v;
         void *args[] = {&vv, &hi};
-        inner.kernel(K.step, c->K.coop_grid, K.block, 0, args, true);
+        inner.kernel(k_step, c->K.coop_grid, K.block, 0, args, true);
     }
     resid_nodes(c, outer, GL, v, L);
     {
         BcgVecs vv = v;
         void *args[] = {&vv, &ho, &hi};
-        outer.kernel(K.check, c->K.coop_grid, K.block, 0, args, true);
+        outer.kernel(k_check, c->K.coop_grid, K.block, 0, args, true);
     }
     if (top.err != cudaSuccess || inner.err != cudaSuccess || outer.err != cudaSuccess) {
         R.discard();
@@ -202,6 +205,7 @@ extern "C" int ls_block_cg_solve(ls_ctx *c, int n, int s, const double *A, int64
     v.Q = L.Q;
     v.B = L.B;
     v.part = L.part;
+    v.partb = L.partb;
     v.part2 = L.part2;
     v.sm = L.sm;
     v.bar = c->bar;
@@ -209,10 +213,11 @@ extern "C" int ls_block_cg_solve(ls_ctx *c, int n, int s, const double *A, int64
     v.rtol = o.rtol;
     const int dt = split ? DT_DS : DT_F64;
     GemvLaunch GL = gemv_plan(dt, hd->use_tma != 0, EPI_DOT, c->num_sms);
-    long long key[8] = {200 + s, n, (long long)(uintptr_t)c->ws, L.ld, o.x0_given, hd->use_tma,
+    const int deflate = o.deflate ? 1 : 0;
+    long long key[8] = {200 + s + 100 * deflate, n, (long long)(uintptr_t)c->ws, L.ld, o.x0_given, hd->use_tma,
                         (long long)(uintptr_t)c->stream, dt};
     if (!c->graph_bcg.matches(key)) {
-        rc = build_bcg_graph(c, v, L, GL, o.x0_given, key);
+        rc = build_bcg_graph(c, v, L, GL, o.x0_given, deflate, key);
         if (rc) return rc;
     }
     e = cudaEventRecord(c->ev0, c->stream);

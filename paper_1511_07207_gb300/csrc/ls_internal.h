@@ -240,6 +240,11 @@ struct BcgSmall {                 // s x s matrices, column-major, leading dimen
     double bn[BCG_MAX_S];                  // ||B_j||
     double r2[BCG_MAX_S];                  // ||B_j - A X_j||^2 from the residual GEMVs
     int ok, update_p;
+    // deflating form: leading dimension BCG_MAX_S for every small matrix
+    double T[BCG_MAX_S * BCG_MAX_S];       // P = W T (the current orthogonalization pass)
+    double Lg[BCG_MAX_S * BCG_MAX_S];      // Cholesky factor of gamma = P^T Q (rank x rank)
+    double w2[BCG_MAX_S];                  // ||W_j||^2 of the block being orthogonalized
+    int rank;                              // orthonormal directions in P (its first columns)
 };
 struct BcgVecs {
     int n, s;
@@ -247,6 +252,7 @@ struct BcgVecs {
     double *X, *R, *P, *Q;
     const double *B;
     double *part;                 // [CTA][BCG_MAX_S^2] partial Gram matrices
+    double *partb;                // [CTA][BCG_MAX_S^2] a second set (two Gram matrices at once)
     double *part2;                // [CTA][BCG_MAX_S] partial ||B_j||^2
     BcgSmall *sm;
     GridBar *bar;
@@ -254,7 +260,8 @@ struct BcgVecs {
     double rtol;
 };
 struct BcgKernels {
-    void *init, *step, *check;
+    void *init, *step, *check;             // O'Leary's form
+    void *dinit, *dstep, *dcheck;          // the deflating form (orthonormal directions of full rank)
     int block;
 };
 BcgKernels bcg_kernels();

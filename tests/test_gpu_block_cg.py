@@ -39,12 +39,17 @@ def _true_rel(oracle, A, Bm, X):
                for j in range(Bm.shape[1]))
 
 
+def _oracle_for(oracle, deflate):
+    return oracle.block_cg_deflated if deflate else oracle.block_cg
+
+
+@pytest.mark.parametrize("deflate", [0, 1])
 @pytest.mark.parametrize("n,s", [(1, 1), (33, 1), (257, 3), (1000, 8), (2049, 16)])
-def test_block_cg_matches_oracle(ctx, gpu, oracle, n, s):
+def test_block_cg_matches_oracle(ctx, gpu, oracle, n, s, deflate):
     A = inputs.spd_matrix(n, 0.1, seed=70 + n)
     Bm = A @ inputs.solution(n, seed=71 + n, nrhs=s).reshape(n, s)
-    st, info, X = _solve(ctx, gpu, A, Bm, rtol=1e-10)
-    ref = oracle.block_cg(A, Bm, rtol=1e-10)
+    st, info, X = _solve(ctx, gpu, A, Bm, rtol=1e-10, deflate=deflate)
+    ref = _oracle_for(oracle, deflate)(A, Bm, rtol=1e-10)
     assert st == B.LS_OK == ref["status"]
     tr = _true_rel(oracle, A, Bm, X)
     assert tr <= 1e-10
@@ -53,14 +58,15 @@ def test_block_cg_matches_oracle(ctx, gpu, oracle, n, s):
     assert info["launches"] >= 2 * info["iters"]
 
 
+@pytest.mark.parametrize("deflate", [0, 1])
 @pytest.mark.parametrize("f64_matvec", [0, 1])
 @pytest.mark.parametrize("n,s", [(200, 4), (777, 6)])
-def test_block_cg_fixed_count_elementwise(ctx, gpu, oracle, n, s, f64_matvec):
+def test_block_cg_fixed_count_elementwise(ctx, gpu, oracle, n, s, f64_matvec, deflate):
     A = inputs.spd_matrix(n, 0.1, seed=80 + n)
     Bm = A @ inputs.solution(n, seed=81 + n, nrhs=s).reshape(n, s)
     for k in (1, 2, 5):
-        st, info, X = _solve(ctx, gpu, A, Bm, rtol=1e-300, max_iter=k, f64_matvec=f64_matvec)
-        ref = oracle.block_cg(A, Bm, rtol=1e-300, max_iter=k)
+        st, info, X = _solve(ctx, gpu, A, Bm, rtol=1e-300, max_iter=k, f64_matvec=f64_matvec, deflate=deflate)
+        ref = _oracle_for(oracle, deflate)(A, Bm, rtol=1e-300, max_iter=k)
         assert st == B.LS_NOT_CONVERGED == ref["status"]
         assert info["iters"] == ref["iters"] == k
         assert np.max(np.abs(X - ref["X"])) <= 1e-11 * np.max(np.abs(ref["X"]))
@@ -95,10 +101,14 @@ def test_block_cg_edge_cases(ctx, gpu):
     n = 64
     A = inputs.spd_matrix(n, 0.5, seed=95)
     b = A @ inputs.solution(n, seed=95)
-    st, info, X = _solve(ctx, gpu, A, np.stack([b, b], 1))
+    st, info, X = _solve(ctx, gpu, A, np.stack([b, b], 1), deflate=0)      # O'Leary's form
     assert st == B.LS_BREAKDOWN
+    st, info, X = _solve(ctx, gpu, A, np.stack([b, np.zeros(n)], 1), deflate=0)
+    assert st == B.LS_BREAKDOWN
+    st, info, X = _solve(ctx, gpu, A, np.stack([b, b], 1))                 # the deflating form
+    assert st == B.LS_OK and np.array_equal(X[:, 0], X[:, 1])
     st, info, X = _solve(ctx, gpu, A, np.stack([b, np.zeros(n)], 1))
-    assert st == B.LS_BREAKDOWN
+    assert st == B.LS_OK and not X[:, 1].any()
     st, info, X = _solve(ctx, gpu, A, np.zeros((n, 3)))
     assert st == B.LS_OK and not X.any() and info["iters"] == 0
     Bm = A @ inputs.solution(n, seed=96, nrhs=3).reshape(n, 3)
@@ -115,3 +125,49 @@ def test_block_cg_edge_cases(ctx, gpu):
     big = np.asfortranarray(np.zeros((n, 17)))
     st, _ = B.ls_block_cg_solve(ctx, np.ascontiguousarray(A), big, big.copy(order="F"))
     assert st == B.LS_ERR_ARG
+
+
+@pytest.mark.parametrize("f64_matvec", [0, 1])
+def test_deflation_of_dependent_zero_and_duplicate_columns(ctx, gpu, oracle, f64_matvec):
+    """A block whose residual has dependent columns (b0 + 2 b1), a zero column
+    and a duplicate: O'Leary's form breaks down, the deflating form drops the
+    dependent directions and converges; every column reaches the tolerance,
+    agrees with the oracle's deflating block CG within the residual bound,
+    and the dependent column's solution is the same combination of the
+    others' (to the solve's accuracy)."""
+    n = 500
+    A = inputs.spd_matrix(n, 0.1, seed=97)
+    Bi = A @ inputs.solution(n, seed=98, nrhs=3).reshape(n, 3)
+    Bd = np.column_stack([Bi[:, 0], Bi[:, 1], Bi[:, 0] + 2 * Bi[:, 1], np.zeros(n), Bi[:, 2], Bi[:, 1]])
+    st0, _, _ = _solve(ctx, gpu, A, Bd, rtol=1e-10, deflate=0, f64_matvec=f64_matvec)
+    assert st0 == B.LS_BREAKDOWN
+    st, info, X = _solve(ctx, gpu, A, Bd, rtol=1e-10, f64_matvec=f64_matvec)
+    ref = oracle.block_cg_deflated(A, Bd, rtol=1e-10)
+    assert st == B.LS_OK == ref["status"]
+    nz = [0, 1, 2, 4, 5]
+    assert _true_rel(oracle, A, Bd[:, nz], X[:, nz]) <= 1e-10
+    assert not X[:, 3].any()
+    inv = 1.0 / np.linalg.eigvalsh(A)[0]
+    for j in nz:
+        rg = np.linalg.norm(oracle.residual(A, Bd[:, j], X[:, j]))
+        ro = np.linalg.norm(oracle.residual(A, Bd[:, j], ref["X"][:, j]))
+        assert np.max(np.abs(X[:, j] - ref["X"][:, j])) <= inv * (rg + ro), j
+    sc = np.max(np.abs(X))
+    assert np.max(np.abs(X[:, 2] - (X[:, 0] + 2 * X[:, 1]))) <= 1e-8 * sc
+    assert abs(info["iters"] - ref["iters"]) <= 2 + ref["iters"] // 20
+
+
+def test_deflation_when_columns_converge_at_different_times(ctx, gpu, oracle):
+    """Columns scaled over ten orders of magnitude and one column already solved
+    by the initial guess: the deflating form keeps going on the others and
+    every column reaches its own tolerance."""
+    n, s = 800, 5
+    A = inputs.spd_matrix(n, 0.05, seed=99)
+    Xs = inputs.solution(n, seed=100, nrhs=s).reshape(n, s) * np.array([1.0, 1e-5, 1e5, 1.0, 1.0])
+    Bm = A @ Xs
+    X0 = np.zeros((n, s))
+    X0[:, 3] = np.linalg.solve(A, Bm[:, 3])
+    st, info, X = _solve(ctx, gpu, A, Bm, X0=X0, rtol=1e-10)
+    assert st == B.LS_OK
+    assert _true_rel(oracle, A, Bm, X) <= 1e-10
+
