@@ -1040,7 +1040,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson arrival window (60 s in the full workload)")
     ap.add_argument("--serve-slots", type=int, default=64)
-    ap.add_argument("--serve-step", type=int, default=4)
+    ap.add_argument("--serve-step", type=int, default=8)
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the n=32768 mixed-vs-FP64 comparison (its matrix takes ~1 min to form)")
     ap.add_argument("--no-accuracy", action="store_true",
