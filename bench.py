@@ -137,13 +137,15 @@ def fp32_issue_peak():
 # ---------------------------------------------------------------------------
 def gemv_source_hash():
     """Hash of the GEMV kernel's device source: k_gemv.cu up to its host-side
-    section, the device helpers and the GEMV_* constants of ls_internal.h."""
+    section, the device helpers (ls_device.cuh, the double-single arithmetic of
+    ls_ds.cuh) and the GEMV_* constants of ls_internal.h."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1511_07207_gb300", "csrc")
     with open(os.path.join(csrc, "k_gemv.cu"), "rb") as fh:
         h.update(fh.read().split(b"// ---- host side", 1)[0])
-    with open(os.path.join(csrc, "ls_device.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("ls_device.cuh", "ls_ds.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     with open(os.path.join(csrc, "ls_internal.h")) as fh:
         h.update("".join(l for l in fh if "GEMV_" in l).encode())
     return h.hexdigest()[:16]
@@ -259,7 +261,9 @@ def run_small(B, ctx, dev, reps=20):
     """The n = 512 systems (seed 0): CG on G G^T/n + 0.1 I and GMRES(30) on
     2 I + G/(2 sqrt n), rtol 1e-10, device-resident; latency-bound, so the
     figures are time to solution and microseconds per iteration (best of
-    `reps` solves after one warm-up)."""
+    `reps` solves after one warm-up).  The default path runs each solve as one
+    fused kernel with A's rows in shared memory; `general` is the same solve
+    on the per-step graph path (ls_opts.fused = 0), for comparison."""
     import torch
     from paper_1511_07207_gb300 import inputs
     n = 512
@@ -272,18 +276,24 @@ def run_small(B, ctx, dev, reps=20):
         bd = torch.from_numpy(A @ xs).to(dev)
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         fn = B.ls_cg_solve if method == "cg" else B.ls_gmres_solve
-        o = B.make_opts(rtol=RTOL, restart=restart)
-        fn(ctx, Ad, bd, x, o)
-        best = None
-        for _ in range(reps):
-            x.zero_()
-            st, inf = fn(ctx, Ad, bd, x, o)
-            if best is None or inf["time_ms"] < best["time_ms"]:
-                best = inf
-        out[method] = {"status": B.ls_strerror(st), "iters": best["iters"],
-                       "time_to_1e-10_us": round(best["time_ms"] * 1e3, 1),
-                       "us_per_iter": round(best["time_ms"] * 1e3 / max(best["iters"], 1), 2),
-                       "true_rel_res": best["true_rel_res"], "rel_err_vs_xstar": rel_err(x, xs)}
+        for path, fused in (("fused", 1), ("general", 0)):
+            o = B.make_opts(rtol=RTOL, restart=restart, fused=fused)
+            fn(ctx, Ad, bd, x, o)
+            best = None
+            for _ in range(reps):
+                x.zero_()
+                st, inf = fn(ctx, Ad, bd, x, o)
+                if best is None or inf["time_ms"] < best["time_ms"]:
+                    best = inf
+            r = {"status": B.ls_strerror(st), "iters": best["iters"],
+                 "time_to_1e-10_us": round(best["time_ms"] * 1e3, 1),
+                 "us_per_iter": round(best["time_ms"] * 1e3 / max(best["iters"], 1), 2),
+                 "launches": best["launches"],
+                 "true_rel_res": best["true_rel_res"], "rel_err_vs_xstar": rel_err(x, xs)}
+            if path == "fused":
+                out[method] = r
+            else:
+                out[method + "_general"] = r
     return out
 
 
@@ -833,6 +843,16 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_small_only(args):
+    """The n = 512 latency line alone (one JSON line)."""
+    import torch
+    from paper_1511_07207_gb300 import binding as B
+    dev = torch.device("cuda", 0)
+    ctx = B.ls_create(0, torch.cuda.current_stream(dev))
+    print(json.dumps({"small_n512": run_small(B, ctx, dev, reps=max(args.reps, 1))}))
+    B.ls_destroy(ctx)
+
+
 def run_kernel(args):
     """Kernel-only mode (used for ncu captures on small cases): time the
     y = A x kernel on a random n x n matrix of the given storage format."""
@@ -1047,10 +1067,11 @@ def main():
                     help="skip the rtol 1e-10 / 1e-12 accuracy runs (both product modes)")
     ap.add_argument("--no-small", action="store_true", help="skip the n = 512 latency line")
     ap.add_argument("--no-tune", action="store_true", help="batched engine with its default tile shapes")
-    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary", "block_cg", "lu"], default=None,
+    ap.add_argument("--kernel", choices=["gemv", "batch", "stationary", "block_cg", "lu", "small"],
+                    default=None,
                     help="kernel-only timing (small cases for ncu captures): one GEMV format, "
-                         "the batched engine alone on --count systems, or --reps sweeps of a "
-                         "stationary method")
+                         "the batched engine alone on --count systems, --reps sweeps of a "
+                         "stationary method, or the n = 512 solves alone")
     ap.add_argument("--method", choices=["jacobi", "gauss_seidel"], default="gauss_seidel",
                     help="--kernel stationary: which method")
     ap.add_argument("--rhs", type=int, default=8, help="--kernel block_cg: right-hand sides")
@@ -1071,6 +1092,8 @@ def main():
         run_block_cg_steps(args)
     elif args.kernel == "lu":
         run_lu_only(args)
+    elif args.kernel == "small":
+        run_small_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

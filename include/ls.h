@@ -98,6 +98,13 @@ typedef struct {
     int deflate;        /* ls_block_cg_solve: 1 = keep the search directions orthonormal and
                            of full rank, dropping dependent ones (no breakdown on dependent,
                            zero or converged columns; default), 0 = O'Leary's form          */
+    int fused;          /* ls_cg_solve / ls_gmres_solve with f64_matvec = 0: 1 = when the rows
+                           of A fit in the shared memory of the GPU's co-resident CTAs (n up
+                           to about 1800 on 152 SMs), run the whole solve as one kernel that
+                           reads A from HBM once and keeps it on chip (default); 0 = always
+                           the general path (one graph, a product kernel per step).  The
+                           iteration, its stop tests and results are the same up to
+                           rounding                                                        */
 } ls_opts;
 
 #define LS_MAX_RESTART 128
@@ -109,7 +116,8 @@ typedef struct {
     double rel_res;      /* last recursive (or Givens-estimated) relative residual       */
     double true_rel_res; /* ||b - A x|| / ||b|| recomputed in FP64 at exit               */
     double time_ms;      /* device time of the solve (CUDA events on the context stream) */
-    double bytes_moved;  /* algorithmic bytes of A streamed (sum over all products)      */
+    double bytes_moved;  /* algorithmic bytes of A streamed (sum over all products; a
+                            fused solve streams A once)                                  */
     long long launches;  /* kernels executed on the device for this call                 */
 } ls_info;
 

@@ -44,7 +44,7 @@ class ls_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("refine", ctypes.c_int),
                 ("inner_iters", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("x0_given", ctypes.c_int), ("reorth", ctypes.c_int), ("f64_matvec", ctypes.c_int),
-                ("deflate", ctypes.c_int)]
+                ("deflate", ctypes.c_int), ("fused", ctypes.c_int)]
 
 
 class ls_info(ctypes.Structure):

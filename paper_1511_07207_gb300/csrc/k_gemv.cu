@@ -29,46 +29,11 @@
 #include <cuda_fp8.h>
 
 #include "ls_device.cuh"
+#include "ls_ds.cuh"
 #include "ls_internal.h"
 #include "split_pair.h"
 
 namespace lsi {
-
-// Double-single accumulator (hi, lo): hi + lo carries about 48 bits.
-struct DSV {
-    float h, l;
-};
-// (hi, lo) + (hi, lo): the high parts by two-sum (Knuth), every rounding
-// error into lo.  The intrinsics keep the compiler from contracting or
-// reassociating the error-free steps.
-__device__ __forceinline__ DSV operator+(DSV a, DSV b) {
-    const float s = __fadd_rn(a.h, b.h);
-    const float bv = __fsub_rn(s, a.h);
-    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
-    return DSV{s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
-}
-__device__ __forceinline__ DSV &operator+=(DSV &a, DSV b) { return a = a + b; }
-__device__ __forceinline__ double to_double(DSV v) { return (double)v.h + (double)v.l; }
-__device__ __forceinline__ double to_double(double v) { return v; }
-__device__ __forceinline__ float to_double(float v) { return v; }
-__device__ __forceinline__ float shfl_xor_v(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ double shfl_xor_v(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ DSV shfl_xor_v(DSV v, int o) {
-    return DSV{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
-}
-// acc += a x for a = ah + al, x = xh + xl: ah xh = p + e exactly (FMA gives
-// the product error), the cross terms ah xl + al xh and e go to lo with the
-// two-sum error of hi + p (al xl, below 2^-48 |a x|, is dropped).
-__device__ __forceinline__ void ds_fma(float ah, float al, DSV x, DSV &acc) {
-    const float p = __fmul_rn(ah, x.h);
-    const float pe = fmaf(ah, x.h, -p);
-    const float t = fmaf(al, x.h, fmaf(ah, x.l, pe));
-    const float sh = __fadd_rn(acc.h, p);
-    const float bv = __fsub_rn(sh, acc.h);
-    const float er = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(sh, bv)), __fsub_rn(p, bv));
-    acc.h = sh;
-    acc.l = __fadd_rn(acc.l, __fadd_rn(t, er));
-}
 
 template <int DT>
 struct Cfg;

@@ -231,6 +231,7 @@ extern "C" int ls_opts_default(ls_opts *o) {
     o->reorth = 0;
     o->f64_matvec = 0;
     o->deflate = 1;
+    o->fused = 1;
     return LS_OK;
 }
 
@@ -702,6 +703,10 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
         fill_info(info, s, LS_OK, 0.f, 0.0, 0);
         return LS_OK;
     }
+    if (o.f64_matvec == 0 && o.fused) {   // small n: the whole solve as one kernel
+        FusedPlan P;
+        if (fused_plan(c, method, n, o.restart, &P)) return krylov_fused(c, method, n, A, lda, b, x, o, P, info);
+    }
     const int m = o.restart;
     const int max_iter = o.max_iter > 0 ? o.max_iter : 10 * n + 10;
     const bool a_dev = is_device_ptr(A);
@@ -820,6 +825,7 @@ static int krylov_f64(ls_ctx *c, int method, int n, const double *A, int64_t lda
     } else {
         passes = s.total + s.cycles + 1;
         sc.iter = s.total;
+        sc.rnorm = s.est;   // the Givens estimate of the last step
     }
     c->launches_total += (long long)s.launches;
     fill_info(info, sc, status, ms, passes * (double)n * n * 8.0, (long long)s.launches);
@@ -885,6 +891,12 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
         return LS_OK;
     }
     const bool gs = method == LS_METHOD_GAUSS_SEIDEL;
+    FusedPlan P;
+    if ((method == LS_METHOD_CG || method == LS_METHOD_GMRES) && o.f64_matvec == 0 && o.fused &&
+        fused_plan(c, method, n, o.restart, &P)) {
+        *bytes = fused_workspace_bytes(n, P.G, o.restart, method == LS_METHOD_GMRES, a_on_device != 0);
+        return LS_OK;
+    }
     *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device, o.f64_matvec == 0 || gs, gs)
                  .bytes;
     return LS_OK;

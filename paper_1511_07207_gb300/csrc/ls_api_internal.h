@@ -225,6 +225,17 @@ void fill_info(ls_info *info, const State &s, int status, float ms, double bytes
 int mixed_cg_solve(ls_ctx *c, int n, const double *A, int64_t lda, const double *b, double *x,
                    const ls_opts *opts, ls_info *info);
 size_t mixed_workspace_bytes(int n, const ls_opts *o, bool a_on_device);
+// fused small-system solvers (ls_fused.cu): G CTAs of R rows, row length nc
+struct FusedPlan {
+    int G, R, nc;
+    size_t smem;
+};
+// True when a CG / GMRES(m) solve of size n runs as one fused kernel on this
+// context's device (A's rows fit in the co-resident CTAs' shared memory).
+bool fused_plan(const ls_ctx *c, int method, int n, int m, FusedPlan *p);
+size_t fused_workspace_bytes(int n, int G, int m, bool gmres, bool a_on_device);
+int krylov_fused(ls_ctx *c, int method, int n, const double *A, int64_t lda, const double *b, double *x,
+                 const ls_opts &o, const FusedPlan &P, ls_info *info);
 // block CG workspace (ls_bcg.cu)
 size_t bcg_workspace_bytes(int n, int s, int grid, bool a_on_device, bool split);
 size_t bgm_workspace_bytes(int n, int s, int m, int grid, bool a_on_device);

@@ -366,4 +366,38 @@ struct KrylovKernels {
 };
 KrylovKernels krylov_kernels(int num_sms);
 
+// ---- fused small-system solvers (k_fused.cu) -------------------------------------------
+// One cooperative launch runs a whole CG or GMRES(m) solve; CTA c keeps rows
+// [c R, c R + R) of A as the FP32 pair in shared memory.
+constexpr int FUSED_THREADS = 256;
+struct FusedArgs {
+    int n, R, nc;            // size, rows per CTA, row length in shared memory (n rounded up to 4)
+    const double *A;         // FP64 A on the device, row-major
+    long long lda;
+    const double *b;         // device copy of b
+    double *x;               // x0 in when x0_given; the solution out
+    int x0_given;
+    int max_iter;
+    double rtol;
+    int m, reorth;           // GMRES restart length; 1 = always two Gram-Schmidt passes
+    double *xch, *xch2;      // n doubles each: vectors exchanged between the CTAs
+    double *part;            // partial sums, [slot][CTA], 2 LS_MAX_RESTART + 8 slots
+    double *H;               // GMRES: per-CTA (m + 1) x m Hessenberg copies
+    unsigned *bar;           // three barrier counters, zero at launch
+    State *st;
+};
+constexpr int FUSED_PART_SLOTS = 2 * LS_MAX_RESTART + 8;
+struct FusedKernels {
+    void *cg, *gmres;
+};
+FusedKernels fused_kernels();
+// Dynamic shared memory of a fused launch (R rows per CTA, row length nc,
+// restart length m for GMRES).
+inline size_t fused_smem_bytes(bool gmres, int R, int nc, int m) {
+    const size_t Rp = (size_t)((R + 1) & ~1);
+    const size_t dbl = gmres ? (size_t)(m + 1) * Rp + 3 * Rp + 4 * (size_t)(m + 2) + 3 * (size_t)(m + 1)
+                             : (size_t)nc + 4 * Rp;
+    return dbl * 8 + 16 + (2 * (size_t)R * nc + 2 * (size_t)nc) * 4;
+}
+
 }  // namespace lsi

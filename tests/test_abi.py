@@ -29,6 +29,7 @@ def test_host_only_calls(lslib):
     o = binding.make_opts()
     assert o.rtol == 1e-10 and o.restart == 30 and o.inner_iters == 25
     assert o.precision == binding.LS_F64 and o.refine == binding.LS_REFINE_FCG
+    assert o.deflate == 1 and o.fused == 1 and o.f64_matvec == 0
     assert binding.ls_strerror(binding.LS_OK) == "converged"
     assert "argument" in binding.ls_strerror(binding.LS_ERR_ARG)
     assert lslib.ls_opts_default(None) == binding.LS_ERR_ARG

@@ -61,25 +61,31 @@ def _fixed_tol(k, kappa, n, xref):
 # ---------------------------------------------------------------------------
 # fixed step counts, element by element
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("f64_matvec", [0, 1])
+# the three product paths: FP32 pair in one fused kernel (A in shared memory),
+# FP32 pair in the general path, native FP64
+MODES = {"fused": dict(f64_matvec=0, fused=1), "general": dict(f64_matvec=0, fused=0),
+         "native": dict(f64_matvec=1)}
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("n", [777, 1000])
-def test_cg_fixed_count_elementwise(ctx, gpu, oracle, n, f64_matvec):
+def test_cg_fixed_count_elementwise(ctx, gpu, oracle, n, mode):
     A = inputs.spd_matrix(n, 0.1, seed=5 + n)
     b = A @ inputs.solution(n, seed=6 + n)
     ev = np.linalg.eigvalsh(A)
     kappa = ev[-1] / ev[0]
     Ad = torch.from_numpy(A).to(gpu)
     for k in (1, 2, 5, 20):
-        st, info, x = _cg(ctx, gpu, Ad, b, rtol=1e-300, max_iter=k, f64_matvec=f64_matvec)
+        st, info, x = _cg(ctx, gpu, Ad, b, rtol=1e-300, max_iter=k, **MODES[mode])
         ref = oracle.cg(A, b, rtol=1e-300, max_iter=k)
         assert st == B.LS_NOT_CONVERGED == ref["status"]
         assert info["iters"] == ref["iters"] == k
         assert np.max(np.abs(x - ref["x"])) <= _fixed_tol(k, kappa, n, ref["x"]), k
 
 
-@pytest.mark.parametrize("f64_matvec", [0, 1])
+@pytest.mark.parametrize("mode", sorted(MODES))
 @pytest.mark.parametrize("n,m", [(777, 30), (1000, 50)])
-def test_gmres_fixed_count_elementwise(ctx, gpu, oracle, n, m, f64_matvec):
+def test_gmres_fixed_count_elementwise(ctx, gpu, oracle, n, m, mode):
     """k < m: the k-th iterate of the first cycle; k > m: across a restart.
     The restart family (1.1 I + G / sqrt n) keeps the residual far from
     convergence for 20 steps."""
@@ -89,8 +95,7 @@ def test_gmres_fixed_count_elementwise(ctx, gpu, oracle, n, m, f64_matvec):
     kappa = s[0] / s[-1]
     Ad = torch.from_numpy(A).to(gpu)
     for k in (1, 2, 5, 20, m + 3):
-        st, info, x = _gmres(ctx, gpu, Ad, b, restart=m, rtol=1e-300, max_iter=k,
-                             f64_matvec=f64_matvec)
+        st, info, x = _gmres(ctx, gpu, Ad, b, restart=m, rtol=1e-300, max_iter=k, **MODES[mode])
         ref = oracle.gmres(A, b, m=m, rtol=1e-300, max_iter=k)
         assert st == B.LS_NOT_CONVERGED == ref["status"]
         assert info["iters"] == ref["iters"] == k
@@ -109,13 +114,14 @@ def _converged_bounds(oracle, A, b, xs, x, xref, inv_norm, nthreads=1):
     return rg, ro, inv_norm * (rg + ro), (inv_norm * (rg + db) if db is not None else None)
 
 
-def test_small_config_seed0(ctx, gpu, oracle):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_small_config_seed0(ctx, gpu, oracle, fused):
     n = 512
     # CG on G G^T / n + 0.1 I, seed 0
     A = inputs.spd_matrix(n, 0.1, seed=0)
     xs = inputs.solution(n, seed=0)
     b = A @ xs
-    st, info, x = _cg(ctx, gpu, torch.from_numpy(A).to(gpu), b, rtol=1e-10)
+    st, info, x = _cg(ctx, gpu, torch.from_numpy(A).to(gpu), b, rtol=1e-10, fused=fused)
     ref = oracle.cg(A, b, rtol=1e-10)
     assert st == B.LS_OK == ref["status"]
     inv = 1.0 / np.linalg.eigvalsh(A)[0]
@@ -128,7 +134,7 @@ def test_small_config_seed0(ctx, gpu, oracle):
     A = inputs.nonsym_matrix(n, seed=0)
     xs = inputs.solution(n, seed=0)
     b = A @ xs
-    st, info, x = _gmres(ctx, gpu, torch.from_numpy(A).to(gpu), b, restart=30, rtol=1e-10)
+    st, info, x = _gmres(ctx, gpu, torch.from_numpy(A).to(gpu), b, restart=30, rtol=1e-10, fused=fused)
     ref = oracle.gmres(A, b, m=30, rtol=1e-10)
     assert st == B.LS_OK == ref["status"]
     inv = 1.0 / np.linalg.svd(A, compute_uv=False)[-1]
