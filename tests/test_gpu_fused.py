@@ -56,10 +56,15 @@ def _svd_kappa(A):
 
 
 def _converged_ok(oracle, A, b, x, xref, inv_norm, rtol):
+    """x - xref = A^-1 (r_ref - r), so |x - xref| <= ||A^-1|| (||r|| + ||r_ref||),
+    plus the rounding of the two computed residuals (gamma_{n+1} (|b| + |A||x|)
+    each)."""
     rg = np.linalg.norm(oracle.residual(A, b, x))
     ro = np.linalg.norm(oracle.residual(A, b, xref))
     assert rg <= rtol * np.linalg.norm(b)
-    assert np.max(np.abs(x - xref)) <= inv_norm * (rg + ro)
+    n = len(b)
+    ev = (n + 1) * 2.0 ** -53 * (np.linalg.norm(b) + np.linalg.norm(np.abs(A) @ np.abs(xref)))
+    assert np.max(np.abs(x - xref)) <= inv_norm * (rg + ro + 2 * ev)
 
 
 # ---------------------------------------------------------------------------
