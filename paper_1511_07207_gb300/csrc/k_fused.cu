@@ -8,8 +8,8 @@
 // vector arithmetic.  What changes is where the work lives.  For small n a
 // step is a few microseconds of arithmetic, but the general path spends tens
 // of microseconds per step on kernel launches inside the graph's loop and on
-// grid-wide barriers over every SM.  Here one cooperative launch of G CTAs
-// runs the whole solve:
+// grid-wide barriers over every SM.  Here one launch of G CTAs runs the whole
+// solve:
 //  * CTA c owns rows [c R, c R + R) of A; it splits them into the FP32 pair
 //    once, at the start, and keeps them in shared memory for the whole solve,
 //    so A is read from HBM once per solve, not once per step;
@@ -19,30 +19,38 @@
 //    of the Krylov basis V);
 //  * a product is warp per row, lanes along the row, double-single
 //    accumulation and a butterfly reduction;
-//  * the vector a step produces row by row (r, w) is exchanged through a
-//    global buffer: each CTA writes its rows, meets the others at a grid
-//    barrier, and reads the whole vector back from L2;
+//  * the vector a step produces row by row (r, w, x) is exchanged: each CTA
+//    publishes its rows, meets the others, and reads the whole vector;
 //  * a scalar reduction: each CTA publishes its partial sum into a slot,
-//    meets the others at a barrier, and every CTA adds the G partials of the
-//    slot in the same fixed order, so all CTAs hold the same bits and take
-//    the same decisions without further communication;
-//  * the grid barrier counts arrivals on three counters in turn (see
-//    fbar_sync) with a bounded wait.
-// A CG step takes two barriers (p.Ap; r.r together with the exchange of r);
-// an Arnoldi step two (V^T w with ||w||^2; ||w - V h||^2 with the exchange of
-// w and the speculative second-pass dots), three when the second
-// Gram-Schmidt pass runs.
+//    meets the others, and every CTA adds the G partials of the slot in the
+//    same fixed order, so all CTAs hold the same bits and take the same
+//    decisions without further communication.
+// Two forms of that communication (FComm):
+//  * cluster (n up to about 650): the grid is one thread-block cluster of at
+//    most 16 CTAs; partial sums and published rows stay in each CTA's shared
+//    memory and the others read them through distributed shared memory; the
+//    meeting is the hardware cluster barrier (about 0.4 us);
+//  * global (larger n, up to one CTA per SM): partial sums and rows go
+//    through global memory (L2), and the meeting is a counting grid barrier
+//    with a bounded wait (about 1.7 us on this GPU).
+// A CG step meets twice (p.Ap; r.r with the exchange of r); an Arnoldi step
+// twice (V^T w with ||w||^2; ||w - V h||^2 with the exchange of w and the
+// speculative second-pass dots), three times when the second Gram-Schmidt
+// pass runs.
 //
-// Partial-sum slots and exchange buffers are reused step after step.  Each
-// is written before a barrier and read after it; its next write comes after
-// a later barrier, which no CTA reaches before it has finished reading, so
-// no double buffering is needed (the argument for each buffer is at its use).
+// Partial-sum slots and exchanged rows are reused step after step.  Each is
+// written before a meeting and read after it; its next write comes after a
+// later meeting, which no CTA reaches before it has finished reading, so no
+// double buffering is needed (the argument for each buffer is at its use).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "ls_device.cuh"
 #include "ls_ds.cuh"
 #include "ls_internal.h"
 #include "split_pair.h"
+
+namespace cg = cooperative_groups;
 
 namespace lsi {
 
@@ -59,9 +67,11 @@ __device__ __forceinline__ int gs2(int m, int t) { return m + 2 + t; }
 __device__ __forceinline__ int gs3(int m) { return 2 * m + 4; }   // ||w||^2 after the second pass
 __device__ __forceinline__ int gsr(int m) { return 2 * m + 5; }   // ||b - A x||^2
 __device__ __forceinline__ int gsb(int m) { return 2 * m + 6; }   // ||b||^2
+// the two exchanged vectors
+enum : int { EX_V = 0, EX_X = 1 };
 }  // namespace
 
-// ---- grid barrier ------------------------------------------------------------------
+// ---- grid barrier (global form) -----------------------------------------------------
 __device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
     unsigned old;
     asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -107,17 +117,83 @@ __device__ __forceinline__ bool fbar_sync(unsigned *c, unsigned &e, State *st) {
     return ok_s != 0;
 }
 
-// Sum of slot `slot` over the G CTAs' partials (layout [slot][G]), by the
-// calling warp.  Every CTA adds the same values in the same order, and the
-// butterfly leaves the same bits in every lane.
-__device__ __forceinline__ double fsum(const double *part, int slot, int G) {
+// ---- communication between the CTAs ---------------------------------------------------
+template <bool CL>
+struct FComm;
+
+// Global form: any number of co-resident CTAs (cooperative launch).
+template <>
+struct FComm<false> {
+    double *part;        // [slot][G]
+    double *ex[2];       // the exchanged vectors, n doubles each
+    unsigned *bar;
+    unsigned e;
+    State *st;
+    int G, R;
+    __device__ void put(int slot, double v) { part[(size_t)slot * G + blockIdx.x] = v; }
+    __device__ double get(int slot, int b) const { return __ldcg(&part[(size_t)slot * G + b]); }
+    __device__ void put_row(int w, int i, double v) { ex[w][blockIdx.x * R + i] = v; }
+    __device__ double get_elem(int w, int j) const { return __ldcg(&ex[w][j]); }
+    __device__ bool meet() { return fbar_sync(bar, e, st); }
+    __device__ void leave() {}
+};
+
+// Cluster form: the grid is one thread-block cluster.  Each CTA's partial
+// sums and published rows stay in its own shared memory; the others read
+// them through distributed shared memory after the cluster barrier (whose
+// arrive has release and whose wait has acquire semantics).
+template <>
+struct FComm<true> {
+    double *psm;         // this CTA's partial-sum slots
+    double *exs[2];      // this CTA's published rows of the two exchanged vectors
+    int G, R;
+    __device__ void put(int slot, double v) { psm[slot] = v; }
+    __device__ double get(int slot, int b) const { return *cg::this_cluster().map_shared_rank(psm + slot, b); }
+    __device__ void put_row(int w, int i, double v) { exs[w][i] = v; }
+    __device__ double get_elem(int w, int j) const {
+        const int b = j / R;
+        return *cg::this_cluster().map_shared_rank(exs[w] + (j - b * R), b);
+    }
+    __device__ bool meet() {
+        cg::this_cluster().sync();
+        return true;
+    }
+    // a CTA leaves only when no other still reads its shared memory
+    __device__ void leave() { cg::this_cluster().sync(); }
+};
+
+// Sum of slot `slot` over the G CTAs' partials, by the calling warp.  Every
+// CTA adds the same values in the same order, and the butterfly leaves the
+// same bits in every lane.
+template <bool CL>
+__device__ __forceinline__ double fsum(const FComm<CL> &C, int slot) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int b = lane; b < G; b += 32) s += __ldcg(&part[(size_t)slot * G + b]);
+    for (int b = lane; b < C.G; b += 32) s += C.get(slot, b);
     return warp_sum(s);
 }
-__device__ __forceinline__ void fput(double *part, int slot, double v) {
-    part[(size_t)slot * gridDim.x + blockIdx.x] = v;
+
+// out[t] = sum over the CTAs of slot base + t, t < count: warps take four
+// slots at a time (their loads in flight together); the per-slot order is
+// fsum's.
+template <bool CL>
+__device__ __forceinline__ void fsum_slots(const FComm<CL> &C, int base, int count, double *out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int s0 = 4 * warp; s0 < count; s0 += 4 * FW) {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = lane; b < C.G; b += 32) {
+            double g[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) g[q] = s0 + q < count ? C.get(base + s0 + q, b) : 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) v[q] += g[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const double t = warp_sum(v[q]);
+            if (lane == 0 && s0 + q < count) out[s0 + q] = t;
+        }
+    }
 }
 
 // ---- shared-memory pieces --------------------------------------------------------------
@@ -140,15 +216,15 @@ __device__ void load_rows(const double *__restrict__ A, long long lda, int r0, i
     }
 }
 
-// (vh, vl) = split of the full vector: src[j] / scale (or src[j] when
-// scale_it is false), read from L2 (src was written by other CTAs or by the
-// host); zero padding up to nc.  Optionally keeps the FP64 values in keep[].
-__device__ __forceinline__ void load_vec(const double *src, int n, int nc, bool scale_it, double scale,
-                                         float *vh, float *vl, double *keep) {
+// (vh, vl) = split of v_j = get(j) / scale (scale_it) or get(j), zero
+// padding up to nc; the FP64 values optionally kept in keep[].
+template <class Get>
+__device__ __forceinline__ void load_vec(Get get, int n, int nc, bool scale_it, double scale, float *vh, float *vl,
+                                         double *keep) {
     for (int j = threadIdx.x; j < nc; j += FT) {
         double v = 0.0;
         if (j < n) {
-            v = __ldcg(&src[j]);
+            v = get(j);
             if (scale_it) v = v / scale;
         }
         const DSV d = ds_split(v);
@@ -185,32 +261,76 @@ __device__ __forceinline__ void fused_product(const float *Ah, const float *Al, 
     }
 }
 
+// ---- per-form setup --------------------------------------------------------------------
+template <bool CL>
+__device__ FComm<CL> make_comm(const FusedArgs &a, double *psm, double *ex0, double *ex1);
+template <>
+__device__ FComm<false> make_comm<false>(const FusedArgs &a, double *, double *, double *) {
+    FComm<false> C;
+    C.part = a.part;
+    C.ex[0] = a.xch;
+    C.ex[1] = a.xch2;
+    C.bar = a.bar;
+    C.e = 0;
+    C.st = a.st;
+    C.G = gridDim.x;
+    C.R = a.R;
+    return C;
+}
+template <>
+__device__ FComm<true> make_comm<true>(const FusedArgs &a, double *psm, double *ex0, double *ex1) {
+    FComm<true> C;
+    C.psm = psm;
+    C.exs[0] = ex0;
+    C.exs[1] = ex1;
+    C.G = gridDim.x;
+    C.R = a.R;
+    return C;
+}
+
+// rv[k] = element threadIdx.x + k FT of exchanged vector w (0 past n): the
+// loads are issued together, before the caller waits on anything else.
+template <bool CL>
+__device__ __forceinline__ void prefetch_vec(const FComm<CL> &C, int w, int n, double (&rv)[FUSED_VEC_REGS]) {
+#pragma unroll
+    for (int k = 0; k < FUSED_VEC_REGS; k++) {
+        const int j = threadIdx.x + k * FT;
+        rv[k] = j < n ? C.get_elem(w, j) : 0.0;
+    }
+}
+
 // ============================================================================
 // CG (paper, CG paragraph; Hestenes-Stiefel form)
 // ============================================================================
-// Shared memory (dynamic): p[nc] (FP64 direction), xr, rr, br, qr [Rp each]
-// (this CTA's rows of x, r, b and of the product), then the FP32 pair of the
-// rows Ah, Al [R nc each] and the split vector vh, vl [nc each].
+// Shared memory (dynamic): p[nc] (FP64 direction), xr, rr, br, qr (this CTA's
+// rows of x, r, b and of the product), ex0, ex1 (cluster form: the rows it
+// publishes) [Rp each], psm [FUSED_CG_SLOTS] (cluster form: its partial
+// sums), then the FP32 pair of the rows Ah, Al [R nc each] and the split
+// vector vh, vl [nc each].
+template <bool CL>
 __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
     extern __shared__ __align__(16) unsigned char fsm[];
     __shared__ double sc[4];
     State *st = a.st;
     count_launch(st);
-    const int n = a.n, R = a.R, nc = a.nc, G = gridDim.x, Rp = (a.R + 1) & ~1;
+    const int n = a.n, R = a.R, nc = a.nc, Rp = (a.R + 1) & ~1;
     const int r0 = blockIdx.x * R, rows = min(R, n - r0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *p = reinterpret_cast<double *>(fsm);
-    double *xr = p + nc, *rr = xr + Rp, *br = rr + Rp, *qr = br + Rp;
-    float *Ah = align16(qr + Rp), *Al = Ah + (size_t)R * nc, *vh = Al + (size_t)R * nc,
+    double *xr = p + nc, *rr = xr + Rp, *br = rr + Rp, *qr = br + Rp, *ex0 = qr + Rp, *ex1 = ex0 + Rp;
+    double *psm = ex1 + Rp;
+    float *Ah = align16(psm + FUSED_CG_SLOTS), *Al = Ah + (size_t)R * nc, *vh = Al + (size_t)R * nc,
           *vl = vh + nc;
-    unsigned e = 0;   // barriers passed
+    FComm<CL> C = make_comm<CL>(a, psm, ex0, ex1);
+    auto ex_v = [&](int j) { return C.get_elem(EX_V, j); };
+    auto ex_x = [&](int j) { return C.get_elem(EX_X, j); };
 
     load_rows(a.A, a.lda, r0, rows, n, nc, Ah, Al);
     for (int i = threadIdx.x; i < rows; i += FT) {
         br[i] = a.b[r0 + i];
         xr[i] = a.x0_given ? a.x[r0 + i] : 0.0;
     }
-    if (a.x0_given) load_vec(a.x, n, nc, false, 1.0, vh, vl, nullptr);
+    if (a.x0_given) load_vec([&](int j) { return a.x[j]; }, n, nc, false, 1.0, vh, vl, nullptr);
     __syncthreads();
     // r = b - A x0 (or b); ||b||^2 and ||r||^2
     if (a.x0_given) {
@@ -222,20 +342,20 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
         for (int i = lane; i < rows; i += 32) {
             const double ri = a.x0_given ? br[i] - qr[i] : br[i];
             rr[i] = ri;
-            a.xch[r0 + i] = ri;
+            C.put_row(EX_V, i, ri);
             bb += br[i] * br[i];
             r2 += ri * ri;
         }
         bb = warp_sum(bb);
         r2 = warp_sum(r2);
         if (lane == 0) {
-            fput(a.part, CS_BB, bb);
-            fput(a.part, CS_R0, r2);
+            C.put(CS_BB, bb);
+            C.put(CS_R0, r2);
         }
     }
-    if (!fbar_sync(a.bar, e, st)) return;
+    if (!C.meet()) return;
     if (warp == 0) {
-        const double b2 = fsum(a.part, CS_BB, G), r2 = fsum(a.part, CS_R0, G);
+        const double b2 = fsum(C, CS_BB), r2 = fsum(C, CS_R0);
         if (lane == 0) {
             sc[0] = b2;
             sc[1] = r2;
@@ -260,8 +380,11 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
         status = LS_NOT_CONVERGED;
         go = false;
     }
-    // p = r: the exchange buffer holds r (x0 given) and b equals r otherwise
-    if (go) load_vec(a.x0_given ? a.xch : a.b, n, nc, false, 1.0, vh, vl, p);
+    // p = r: the published rows hold r (x0 given); b equals r otherwise
+    if (go) {
+        if (a.x0_given) load_vec(ex_v, n, nc, false, 1.0, vh, vl, p);
+        else load_vec([&](int j) { return a.b[j]; }, n, nc, false, 1.0, vh, vl, p);
+    }
     __syncthreads();
 
     while (go) {             // residual replacements
@@ -273,12 +396,12 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
                 double s = 0.0;
                 for (int i = lane; i < rows; i += 32) s += p[r0 + i] * qr[i];
                 s = warp_sum(s);
-                if (lane == 0) fput(a.part, CS_PQ, s);
+                if (lane == 0) C.put(CS_PQ, s);
             }
-            // CS_PQ: its readers finish before they arrive at the next r.r barrier
-            if (!fbar_sync(a.bar, e, st)) return;
+            // CS_PQ: its readers finish before they arrive at the r.r meeting
+            if (!C.meet()) return;
             if (warp == 0) {
-                const double t = fsum(a.part, CS_PQ, G);
+                const double t = fsum(C, CS_PQ);
                 if (lane == 0) sc[0] = t;
             }
             __syncthreads();
@@ -289,24 +412,26 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
                 break;
             }
             alpha = rho / pq;
-            // x += alpha p, r -= alpha q on this CTA's rows; r to the exchange
-            // buffer (every reader of its previous contents has passed the
-            // p.q barrier just met)
+            // x += alpha p, r -= alpha q on this CTA's rows; r published
+            // (every reader of its previous rows has passed the p.q meeting)
             if (warp == 0) {
                 double s = 0.0;
                 for (int i = lane; i < rows; i += 32) {
                     xr[i] += alpha * p[r0 + i];
                     const double ri = rr[i] - alpha * qr[i];
                     rr[i] = ri;
-                    a.xch[r0 + i] = ri;
+                    C.put_row(EX_V, i, ri);
                     s += ri * ri;
                 }
                 s = warp_sum(s);
-                if (lane == 0) fput(a.part, CS_RR, s);
+                if (lane == 0) C.put(CS_RR, s);
             }
-            if (!fbar_sync(a.bar, e, st)) return;
+            if (!C.meet()) return;
+            // the whole r in flight while warp 0 adds the partial sums
+            double rv[FUSED_VEC_REGS];
+            prefetch_vec(C, EX_V, n, rv);
             if (warp == 0) {
-                const double t = fsum(a.part, CS_RR, G);
+                const double t = fsum(C, CS_RR);
                 if (lane == 0) sc[1] = t;
             }
             __syncthreads();
@@ -315,12 +440,16 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
             conv = finite && sqrt(rho_new) <= tol;
             beta = rho_new / rho;
             if (finite && !conv) {   // p = r + beta p, the whole vector in every CTA
-                for (int j = threadIdx.x; j < n; j += FT) {
-                    const double pj = __ldcg(&a.xch[j]) + beta * p[j];
-                    p[j] = pj;
-                    const DSV d = ds_split(pj);
-                    vh[j] = d.h;
-                    vl[j] = d.l;
+#pragma unroll
+                for (int k = 0; k < FUSED_VEC_REGS; k++) {
+                    const int j = threadIdx.x + k * FT;
+                    if (j < n) {
+                        const double pj = rv[k] + beta * p[j];
+                        p[j] = pj;
+                        const DSV d = ds_split(pj);
+                        vh[j] = d.h;
+                        vl[j] = d.l;
+                    }
                 }
             }
             rho = rho_new;
@@ -330,29 +459,29 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
             __syncthreads();
             if (!finite || conv || iter >= a.max_iter) break;
         }
-        // the true residual b - A x: x to the second exchange buffer
-        for (int i = threadIdx.x; i < rows; i += FT) a.xch2[r0 + i] = xr[i];
-        if (!fbar_sync(a.bar, e, st)) return;
-        load_vec(a.xch2, n, nc, false, 1.0, vh, vl, nullptr);
+        // the true residual b - A x: x published
+        for (int i = threadIdx.x; i < rows; i += FT) C.put_row(EX_X, i, xr[i]);
+        if (!C.meet()) return;
+        load_vec(ex_x, n, nc, false, 1.0, vh, vl, nullptr);
         __syncthreads();
         fused_product(Ah, Al, vh, vl, rows, nc, qr);
         __syncthreads();
-        // t = b - A x to the exchange buffer: its last readers (the p update)
-        // have passed the barrier above
+        // t = b - A x published: the last readers of r (the p update) have
+        // passed the meeting above
         if (warp == 0) {
             double s = 0.0;
             for (int i = lane; i < rows; i += 32) {
                 const double ti = br[i] - qr[i];
                 qr[i] = ti;
-                a.xch[r0 + i] = ti;
+                C.put_row(EX_V, i, ti);
                 s += ti * ti;
             }
             s = warp_sum(s);
-            if (lane == 0) fput(a.part, CS_TT, s);
+            if (lane == 0) C.put(CS_TT, s);
         }
-        if (!fbar_sync(a.bar, e, st)) return;
+        if (!C.meet()) return;
         if (warp == 0) {
-            const double t = fsum(a.part, CS_TT, G);
+            const double t = fsum(C, CS_TT);
             if (lane == 0) sc[2] = t;
         }
         __syncthreads();
@@ -374,7 +503,7 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
         }
         // restart from the true residual: r = p = b - A x
         for (int i = threadIdx.x; i < rows; i += FT) rr[i] = qr[i];
-        load_vec(a.xch, n, nc, false, 1.0, vh, vl, p);
+        load_vec(ex_v, n, nc, false, 1.0, vh, vl, p);
         rho = t * t;
         rnorm = t;
         conv = 0;
@@ -396,6 +525,7 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
         st->status = status;
         if (nan) set_err(st, ERRB_NAN);
     }
+    C.leave();
 }
 
 // ============================================================================
@@ -403,37 +533,41 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
 // Givens rotations)
 // ============================================================================
 // Shared memory (dynamic): Vr [(m + 1) Rp] (this CTA's rows of the basis,
-// column j at Vr + j Rp), xr, br, wr [Rp each], h1, h2, hs, g [m + 2 each],
-// cs, sn, ys [m + 1 each], then Ah, Al [R nc each] and vh, vl [nc each].
-// Each CTA keeps its own copy of the rotated Hessenberg matrix in global
-// memory (a.H + blockIdx.x (m + 1) m, column-major), written and read by
-// this CTA only; all copies are equal because every CTA applies the same
+// column j at Vr + j Rp), xr, br, wr, ex0, ex1 [Rp each], h1, h2, hs, g, hc
+// [m + 2 each], cs, sn, ys [m + 1 each], psm [FUSED_PART_SLOTS], then (when
+// h_smem) the rotated Hessenberg matrix Hs [(m + 1) m], then Ah, Al [R nc
+// each] and vh, vl [nc each].  Every CTA keeps its own copy of the rotated
+// Hessenberg matrix (in shared memory, or at a.H + blockIdx.x (m + 1) m,
+// column-major); all copies are equal because every CTA applies the same
 // rotations to the same numbers.
+template <bool CL>
 __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     extern __shared__ __align__(16) unsigned char fsm[];
     __shared__ double sc[4];
     __shared__ int flag_s[2];
     State *st = a.st;
     count_launch(st);
-    const int n = a.n, R = a.R, nc = a.nc, G = gridDim.x, m = a.m, Rp = (a.R + 1) & ~1;
+    const int n = a.n, R = a.R, nc = a.nc, m = a.m, Rp = (a.R + 1) & ~1;
     const int r0 = blockIdx.x * R, rows = min(R, n - r0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *Vr = reinterpret_cast<double *>(fsm);
-    double *xr = Vr + (size_t)(m + 1) * Rp, *br = xr + Rp, *wr = br + Rp;
-    double *h1 = wr + Rp, *h2 = h1 + (m + 2), *hs = h2 + (m + 2), *g = hs + (m + 2);
-    double *cs = g + (m + 2), *sn = cs + (m + 1), *ys = sn + (m + 1);
-    float *Ah = align16(ys + (m + 1));
+    double *xr = Vr + (size_t)(m + 1) * Rp, *br = xr + Rp, *wr = br + Rp, *ex0 = wr + Rp, *ex1 = ex0 + Rp;
+    double *h1 = ex1 + Rp, *h2 = h1 + (m + 2), *hs = h2 + (m + 2), *g = hs + (m + 2), *hc = g + (m + 2);
+    double *cs = hc + (m + 2), *sn = cs + (m + 1), *ys = sn + (m + 1), *psm = ys + (m + 1);
+    double *Hs = psm + FUSED_PART_SLOTS;
+    double *H = a.h_smem ? Hs : a.H + (size_t)blockIdx.x * (m + 1) * m;
+    float *Ah = align16(a.h_smem ? Hs + (size_t)(m + 1) * m : Hs);
     float *Al = Ah + (size_t)R * nc, *vh = Al + (size_t)R * nc, *vl = vh + nc;
-    double *H = a.H + (size_t)blockIdx.x * (m + 1) * m;
     const int m1 = m + 1;
-    unsigned e = 0;   // barriers passed
+    FComm<CL> C = make_comm<CL>(a, psm, ex0, ex1);
+    auto ex_x = [&](int j) { return C.get_elem(EX_X, j); };
 
     load_rows(a.A, a.lda, r0, rows, n, nc, Ah, Al);
     for (int i = threadIdx.x; i < rows; i += FT) {
         br[i] = a.b[r0 + i];
         xr[i] = a.x0_given ? a.x[r0 + i] : 0.0;
     }
-    if (a.x0_given) load_vec(a.x, n, nc, false, 1.0, vh, vl, nullptr);
+    if (a.x0_given) load_vec([&](int j) { return a.x[j]; }, n, nc, false, 1.0, vh, vl, nullptr);
     else
         for (int j = threadIdx.x; j < nc; j += FT) vh[j] = vl[j] = 0.f;
     __syncthreads();
@@ -441,9 +575,11 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     double bn = 0.0, tol = 0.0, true_rn = 0.0, est = 0.0;
     int total = 0, cycles = 0, status = 0, nan = 0, k = 0;
     bool first = true;
+    double rv[FUSED_VEC_REGS];
     for (;;) {   // cycles: each starts from the true residual
-        // r = b - A x (x is in vh, vl) to the exchange buffer, whose last
-        // readers (v_{k+1} of the previous cycle) have passed the x barrier
+        // r = b - A x (x is in vh, vl), published: the last readers of the
+        // previous contents (v_{k+1} of the previous cycle) have passed the
+        // meeting that published x
         fused_product(Ah, Al, vh, vl, rows, nc, wr);
         __syncthreads();
         if (warp == 0) {
@@ -451,21 +587,22 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
             for (int i = lane; i < rows; i += 32) {
                 const double ri = br[i] - wr[i];
                 wr[i] = ri;
-                a.xch[r0 + i] = ri;
+                C.put_row(EX_V, i, ri);
                 s += ri * ri;
                 bb += br[i] * br[i];
             }
             s = warp_sum(s);
             bb = warp_sum(bb);
             if (lane == 0) {
-                fput(a.part, gsr(m), s);
-                if (first) fput(a.part, gsb(m), bb);
+                C.put(gsr(m), s);
+                if (first) C.put(gsb(m), bb);
             }
         }
-        if (!fbar_sync(a.bar, e, st)) return;
+        if (!C.meet()) return;
+        prefetch_vec(C, EX_V, n, rv);
         if (warp == 0) {
-            const double t = fsum(a.part, gsr(m), G);
-            const double b2 = first ? fsum(a.part, gsb(m), G) : 0.0;
+            const double t = fsum(C, gsr(m));
+            const double b2 = first ? fsum(C, gsb(m)) : 0.0;
             if (lane == 0) {
                 sc[0] = t;
                 sc[1] = b2;
@@ -503,9 +640,17 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
             status = LS_NOT_CONVERGED;
             break;
         }
-        // v_0 = r / beta
+        // v_0 = r / beta: the whole vector (from the prefetched r) and this CTA's rows
         cycles++;
-        load_vec(a.xch, n, nc, true, beta, vh, vl, nullptr);
+#pragma unroll
+        for (int q = 0; q < FUSED_VEC_REGS; q++) {
+            const int j = threadIdx.x + q * FT;
+            if (j < nc) {
+                const DSV d = ds_split(j < n ? rv[q] / beta : 0.0);
+                vh[j] = d.h;
+                vl[j] = d.l;
+            }
+        }
         for (int i = threadIdx.x; i < rows; i += FT) Vr[i] = wr[i] / beta;
         if (threadIdx.x == 0) g[0] = beta;
         est = beta;
@@ -522,23 +667,20 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
                     for (int i = 0; i < rows; i++) s += Vr[(size_t)t * Rp + i] * wr[i];
                 else
                     for (int i = 0; i < rows; i++) s += wr[i] * wr[i];
-                fput(a.part, gs1(t), s);
+                C.put(gs1(t), s);
             }
-            if (!fbar_sync(a.bar, e, st)) return;
-            for (int t = warp; t <= j + 1; t += FW) {
-                const double v = fsum(a.part, gs1(t), G);
-                if (lane == 0) h1[t] = v;
-            }
+            if (!C.meet()) return;
+            fsum_slots(C, gs1(0), j + 2, h1);
             __syncthreads();
             const double wnorm0 = h1[j + 1];
-            // w -= V_j h; w to the exchange buffer (its readers of the last
-            // step have passed the barrier above); the second-pass dots and
-            // ||w||^2 published with it
+            // w -= V_j h, published (its readers of the last step have passed
+            // the meeting above); the second-pass dots and ||w||^2 published
+            // with it
             for (int i = threadIdx.x; i < rows; i += FT) {
                 double wi = wr[i];
                 for (int t = 0; t <= j; t++) wi -= h1[t] * Vr[(size_t)t * Rp + i];
                 wr[i] = wi;
-                a.xch[r0 + i] = wi;
+                C.put_row(EX_V, i, wi);
             }
             __syncthreads();
             for (int t = threadIdx.x; t <= j + 1; t += FT) {
@@ -547,40 +689,37 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
                     for (int i = 0; i < rows; i++) s += Vr[(size_t)t * Rp + i] * wr[i];
                 else
                     for (int i = 0; i < rows; i++) s += wr[i] * wr[i];
-                fput(a.part, gs2(m, t), s);
+                C.put(gs2(m, t), s);
             }
-            if (!fbar_sync(a.bar, e, st)) return;
-            if (warp == 0) {
-                const double v = fsum(a.part, gs2(m, j + 1), G);
-                if (lane == 0) sc[2] = v;
-            }
+            if (!C.meet()) return;
+            // w in flight while the sums are formed.  When the second pass
+            // runs, a CTA that has taken its decision may overwrite its rows
+            // while another still loads them; those loads are discarded and
+            // the vector is loaded again after the next meeting.
+            prefetch_vec(C, EX_V, n, rv);
+            fsum_slots(C, gs2(m, 0), j + 2, h2);
             for (int t = threadIdx.x; t <= j; t += FT) hs[t] = h1[t];
             __syncthreads();
-            double wn2 = sc[2];
+            double wn2 = h2[j + 1];
             // a second pass only when cancellation lost accuracy (or always if asked)
             if (a.reorth || wn2 < 0.49 * wnorm0) {
-                for (int t = warp; t <= j; t += FW) {
-                    const double v = fsum(a.part, gs2(m, t), G);
-                    if (lane == 0) h2[t] = v;
-                }
-                __syncthreads();
-                // nobody reads the exchange buffer between the last barrier and the next
                 if (warp == 0) {
                     double s = 0.0;
                     for (int i = lane; i < rows; i += 32) {
                         double wi = wr[i];
                         for (int t = 0; t <= j; t++) wi -= h2[t] * Vr[(size_t)t * Rp + i];
                         wr[i] = wi;
-                        a.xch[r0 + i] = wi;
+                        C.put_row(EX_V, i, wi);
                         s += wi * wi;
                     }
                     s = warp_sum(s);
-                    if (lane == 0) fput(a.part, gs3(m), s);
+                    if (lane == 0) C.put(gs3(m), s);
                 }
                 for (int t = threadIdx.x; t <= j; t += FT) hs[t] += h2[t];
-                if (!fbar_sync(a.bar, e, st)) return;
+                if (!C.meet()) return;
+                prefetch_vec(C, EX_V, n, rv);
                 if (warp == 0) {
-                    const double v = fsum(a.part, gs3(m), G);
+                    const double v = fsum(C, gs3(m));
                     if (lane == 0) sc[2] = v;
                 }
                 __syncthreads();
@@ -589,35 +728,45 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
             const double wn = sqrt(wn2);
             const bool lucky = !(wn > 1e-14 * sqrt(wnorm0));
             if (!lucky) {   // v_{j+1} = w / ||w||, the whole vector, and this CTA's rows of it
-                load_vec(a.xch, n, nc, true, wn, vh, vl, nullptr);
+#pragma unroll
+                for (int q = 0; q < FUSED_VEC_REGS; q++) {
+                    const int jj = threadIdx.x + q * FT;
+                    if (jj < nc) {
+                        const DSV d = ds_split(jj < n ? rv[q] / wn : 0.0);
+                        vh[jj] = d.h;
+                        vl[jj] = d.l;
+                    }
+                }
                 for (int i = threadIdx.x; i < rows; i += FT) Vr[(size_t)(j + 1) * Rp + i] = wr[i] / wn;
             }
-            // the new Hessenberg column, the old rotations, the new one (one thread)
+            // the new Hessenberg column, the old rotations, the new one (one
+            // thread, in shared memory), then the column into this CTA's copy
             if (threadIdx.x == 0) {
-                double *Hk = H + (size_t)j * m1;
-                for (int t = 0; t <= j; t++) Hk[t] = hs[t];
-                Hk[j + 1] = wn;
+                for (int t = 0; t <= j; t++) hc[t] = hs[t];
+                hc[j + 1] = wn;
                 for (int t = 0; t < j; t++) {
-                    const double x0 = Hk[t], x1 = Hk[t + 1];
-                    Hk[t] = cs[t] * x0 + sn[t] * x1;
-                    Hk[t + 1] = -sn[t] * x0 + cs[t] * x1;
+                    const double x0 = hc[t], x1 = hc[t + 1];
+                    hc[t] = cs[t] * x0 + sn[t] * x1;
+                    hc[t + 1] = -sn[t] * x0 + cs[t] * x1;
                 }
-                const double den = hypot(Hk[j], Hk[j + 1]);
+                const double den = hypot(hc[j], hc[j + 1]);
                 int stop = 0, brk = 0;
                 if (den == 0.0 || !isfinite(den)) {
                     brk = isfinite(den) ? 1 : 2;
                     stop = 1;
                 } else {
-                    const double c = Hk[j] / den, s = Hk[j + 1] / den;
+                    const double c = hc[j] / den, s = hc[j + 1] / den;
                     cs[j] = c;
                     sn[j] = s;
-                    Hk[j] = den;
-                    Hk[j + 1] = 0.0;
+                    hc[j] = den;
+                    hc[j + 1] = 0.0;
                     g[j + 1] = -s * g[j];
                     g[j] = c * g[j];
                     sc[3] = fabs(g[j + 1]);
                     if (sc[3] <= tol || lucky || j + 1 >= m || total + 1 >= a.max_iter) stop = 1;
                 }
+                double *Hk = H + (size_t)j * m1;
+                for (int t = 0; t <= j + 1; t++) Hk[t] = hc[t];
                 flag_s[0] = stop;
                 flag_s[1] = brk;
             }
@@ -650,10 +799,10 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
                 xr[i] = xi;
             }
         }
-        // x to the second exchange buffer, then the whole x into vh, vl
-        for (int i = threadIdx.x; i < rows; i += FT) a.xch2[r0 + i] = xr[i];
-        if (!fbar_sync(a.bar, e, st)) return;
-        load_vec(a.xch2, n, nc, false, 1.0, vh, vl, nullptr);
+        // x published, then the whole x into vh, vl
+        for (int i = threadIdx.x; i < rows; i += FT) C.put_row(EX_X, i, xr[i]);
+        if (!C.meet()) return;
+        load_vec(ex_x, n, nc, false, 1.0, vh, vl, nullptr);
         __syncthreads();
     }
     for (int i = threadIdx.x; i < rows; i += FT) a.x[r0 + i] = xr[i];
@@ -670,12 +819,15 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
         st->status = status;
         if (nan) set_err(st, ERRB_NAN);
     }
+    C.leave();
 }
 
 FusedKernels fused_kernels() {
     FusedKernels K{};
-    K.cg = reinterpret_cast<void *>(&cg_fused_kernel);
-    K.gmres = reinterpret_cast<void *>(&gm_fused_kernel);
+    K.cg = reinterpret_cast<void *>(&cg_fused_kernel<false>);
+    K.gmres = reinterpret_cast<void *>(&gm_fused_kernel<false>);
+    K.cg_cl = reinterpret_cast<void *>(&cg_fused_kernel<true>);
+    K.gmres_cl = reinterpret_cast<void *>(&gm_fused_kernel<true>);
     return K;
 }
 

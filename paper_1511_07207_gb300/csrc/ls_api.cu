@@ -894,7 +894,7 @@ extern "C" int ls_workspace_size(ls_ctx *c, int method, int n, int nrhs, const l
     FusedPlan P;
     if ((method == LS_METHOD_CG || method == LS_METHOD_GMRES) && o.f64_matvec == 0 && o.fused &&
         fused_plan(c, method, n, o.restart, &P)) {
-        *bytes = fused_workspace_bytes(n, P.G, o.restart, method == LS_METHOD_GMRES, a_on_device != 0);
+        *bytes = fused_workspace_bytes(P, n, o.restart, method == LS_METHOD_GMRES, a_on_device != 0);
         return LS_OK;
     }
     *bytes = f64_layout(nullptr, n, o.restart, method == LS_METHOD_GMRES, !a_on_device, o.f64_matvec == 0 || gs, gs)

@@ -229,11 +229,13 @@ size_t mixed_workspace_bytes(int n, const ls_opts *o, bool a_on_device);
 struct FusedPlan {
     int G, R, nc;
     size_t smem;
+    bool cluster;        // the grid is one thread-block cluster (else a cooperative grid)
+    int h_smem;          // GMRES: the Hessenberg matrix in shared memory
 };
 // True when a CG / GMRES(m) solve of size n runs as one fused kernel on this
 // context's device (A's rows fit in the co-resident CTAs' shared memory).
 bool fused_plan(const ls_ctx *c, int method, int n, int m, FusedPlan *p);
-size_t fused_workspace_bytes(int n, int G, int m, bool gmres, bool a_on_device);
+size_t fused_workspace_bytes(const FusedPlan &P, int n, int m, bool gmres, bool a_on_device);
 int krylov_fused(ls_ctx *c, int method, int n, const double *A, int64_t lda, const double *b, double *x,
                  const ls_opts &o, const FusedPlan &P, ls_info *info);
 // block CG workspace (ls_bcg.cu)

@@ -367,9 +367,16 @@ struct KrylovKernels {
 KrylovKernels krylov_kernels(int num_sms);
 
 // ---- fused small-system solvers (k_fused.cu) -------------------------------------------
-// One cooperative launch runs a whole CG or GMRES(m) solve; CTA c keeps rows
-// [c R, c R + R) of A as the FP32 pair in shared memory.
+// One launch runs a whole CG or GMRES(m) solve; CTA c keeps rows
+// [c R, c R + R) of A as the FP32 pair in shared memory.  Cluster form: the
+// grid is one thread-block cluster (at most FUSED_MAX_CLUSTER CTAs) that
+// communicates through distributed shared memory; global form: a cooperative
+// grid that communicates through global memory.
 constexpr int FUSED_THREADS = 256;
+constexpr int FUSED_VEC_REGS = 8;          // vector elements a thread holds: n <= 8 * 256 - 4
+constexpr int FUSED_MAX_CLUSTER = 16;
+constexpr int FUSED_PART_SLOTS = 2 * LS_MAX_RESTART + 8;
+constexpr int FUSED_CG_SLOTS = 8;
 struct FusedArgs {
     int n, R, nc;            // size, rows per CTA, row length in shared memory (n rounded up to 4)
     const double *A;         // FP64 A on the device, row-major
@@ -380,23 +387,25 @@ struct FusedArgs {
     int max_iter;
     double rtol;
     int m, reorth;           // GMRES restart length; 1 = always two Gram-Schmidt passes
-    double *xch, *xch2;      // n doubles each: vectors exchanged between the CTAs
-    double *part;            // partial sums, [slot][CTA], 2 LS_MAX_RESTART + 8 slots
-    double *H;               // GMRES: per-CTA (m + 1) x m Hessenberg copies
-    unsigned *bar;           // three barrier counters, zero at launch
+    int h_smem;              // GMRES: 1 = the Hessenberg matrix in shared memory, 0 = in H
+    double *xch, *xch2;      // global form: n doubles each, the vectors exchanged between CTAs
+    double *part;            // global form: partial sums, [slot][CTA], FUSED_PART_SLOTS slots
+    double *H;               // GMRES, h_smem = 0: per-CTA (m + 1) x m Hessenberg copies
+    unsigned *bar;           // global form: three barrier counters, zero at launch
     State *st;
 };
-constexpr int FUSED_PART_SLOTS = 2 * LS_MAX_RESTART + 8;
 struct FusedKernels {
-    void *cg, *gmres;
+    void *cg, *gmres;        // global form
+    void *cg_cl, *gmres_cl;  // cluster form
 };
 FusedKernels fused_kernels();
 // Dynamic shared memory of a fused launch (R rows per CTA, row length nc,
-// restart length m for GMRES).
-inline size_t fused_smem_bytes(bool gmres, int R, int nc, int m) {
-    const size_t Rp = (size_t)((R + 1) & ~1);
-    const size_t dbl = gmres ? (size_t)(m + 1) * Rp + 3 * Rp + 4 * (size_t)(m + 2) + 3 * (size_t)(m + 1)
-                             : (size_t)nc + 4 * Rp;
+// restart length m and the Hessenberg matrix's place for GMRES).
+inline size_t fused_smem_bytes(bool gmres, int R, int nc, int m, bool h_smem) {
+    const size_t Rp = (size_t)((R + 1) & ~1), M = (size_t)m;
+    const size_t dbl = gmres ? (M + 1) * Rp + 5 * Rp + 5 * (M + 2) + 3 * (M + 1) + FUSED_PART_SLOTS +
+                                   (h_smem ? (M + 1) * M : 0)
+                             : (size_t)nc + 6 * Rp + FUSED_CG_SLOTS;
     return dbl * 8 + 16 + (2 * (size_t)R * nc + 2 * (size_t)nc) * 4;
 }
 

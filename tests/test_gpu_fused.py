@@ -1,6 +1,9 @@
 """GPU parity of the fused small-system solvers: a CG or GMRES(m) solve as one
 persistent kernel with A's rows kept in shared memory (ls_opts.fused = 1,
-taken when the rows fit; n up to about 1800 on 152 SMs).
+taken when the rows fit; n up to about 1800 on 152 SMs).  Up to n of about
+650 the CTAs form one thread-block cluster (distributed shared memory);
+above, or with LS_FUSED_CTAS set, a cooperative grid communicating through
+global memory.
 
 The iteration is the general path's, so the same bars apply:
 * after k steps the iterate is the oracle's up to rounding, element by element:
@@ -116,9 +119,10 @@ def ctas():
         os.environ["LS_FUSED_CTAS"] = old
 
 
-@pytest.mark.parametrize("n,G", [(997, 0), (150, 5), (997, 64), (997, 152)])
+@pytest.mark.parametrize("n,G", [(512, 0), (512, 64), (997, 0), (150, 5), (997, 64), (997, 152)])
 def test_cg_fused_fixed_count_elementwise(ctx, gpu, oracle, ctas, n, G):
-    """G = 0: the default shape (8 rows per CTA); otherwise G CTAs."""
+    """G = 0: the default shape (n = 512: one cluster of 16 CTAs; n = 997: the
+    global form, 8 rows per CTA); otherwise the global form with G CTAs."""
     if G:
         os.environ["LS_FUSED_CTAS"] = str(G)
     A = inputs.spd_matrix(n, 0.1, seed=60)
@@ -133,7 +137,8 @@ def test_cg_fused_fixed_count_elementwise(ctx, gpu, oracle, ctas, n, G):
         assert np.max(np.abs(x - ref["x"])) <= tol, (G, k)
 
 
-@pytest.mark.parametrize("n,G,reorth", [(901, 0, 0), (150, 5, 1), (901, 152, 0)])
+@pytest.mark.parametrize("n,G,reorth", [(512, 0, 0), (512, 0, 1), (512, 64, 0), (901, 0, 0), (150, 5, 1),
+                                         (901, 152, 0)])
 def test_gmres_fused_fixed_count_elementwise(ctx, gpu, oracle, ctas, n, G, reorth):
     """k < m: the first cycle; k > m: across restarts (m = 8)."""
     m = 8
