@@ -162,6 +162,17 @@ struct FComm<true> {
     __device__ void leave() { cg::this_cluster().sync(); }
 };
 
+// Butterfly sum over the first `width` lanes of the warp (the others hold
+// 0); every lane gets the same bits.  Only as many levels as the data needs:
+// on this GPU each dependent FP64 addition costs on the order of a hundred
+// cycles.
+__device__ __forceinline__ double lane_sum(double s, int width) {
+    int o = 1;
+    while (o < width && o < 32) o <<= 1;
+    for (o >>= 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 // Sum of slot `slot` over the G CTAs' partials, by the calling warp.  Every
 // CTA adds the same values in the same order, and the butterfly leaves the
 // same bits in every lane.
@@ -170,7 +181,7 @@ __device__ __forceinline__ double fsum(const FComm<CL> &C, int slot) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
     for (int b = lane; b < C.G; b += 32) s += C.get(slot, b);
-    return warp_sum(s);
+    return lane_sum(s, C.G);
 }
 
 // out[t] = sum over the CTAs of slot base + t, t < count: warps take four
@@ -188,11 +199,15 @@ __device__ __forceinline__ void fsum_slots(const FComm<CL> &C, int base, int cou
 #pragma unroll
             for (int q = 0; q < 4; q++) v[q] += g[q];
         }
+        int o = 1;
+        while (o < C.G && o < 32) o <<= 1;
+        for (o >>= 1; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const double t = warp_sum(v[q]);
-            if (lane == 0 && s0 + q < count) out[s0 + q] = t;
-        }
+            for (int q = 0; q < 4; q++) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (s0 + q < count) out[s0 + q] = v[q];
     }
 }
 
@@ -200,6 +215,14 @@ __device__ __forceinline__ void fsum_slots(const FComm<CL> &C, int base, int cou
 // The first 16-byte boundary at or after p (the float4 region after the FP64 arrays).
 __device__ __forceinline__ float *align16(void *p) {
     return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+}
+
+// The split (hi, lo) of an FP64 value, from its bit pattern (integer
+// operations, no FP64 instructions on the common path).
+__device__ __forceinline__ DSV split_bits(double v) {
+    DSV d;
+    split_pair(v, d.h, d.l);
+    return d;
 }
 
 // This CTA's rows of A as the FP32 pair, row-major with row length nc (n
@@ -227,37 +250,60 @@ __device__ __forceinline__ void load_vec(Get get, int n, int nc, bool scale_it, 
             v = get(j);
             if (scale_it) v = v / scale;
         }
-        const DSV d = ds_split(v);
+        const DSV d = split_bits(v);
         vh[j] = d.h;
         vl[j] = d.l;
         if (keep) keep[j] = v;
     }
 }
 
-// q_i = sum_j (hi_ij + lo_ij) v_j for the CTA's rows i < rows (FP64 out).
-// Warp per row, lane l on columns 4 l + 128 t (16-byte shared loads, no bank
-// conflicts), two double-single chains per lane joined by a butterfly.
-__device__ __forceinline__ void fused_product(const float *Ah, const float *Al, const float *vh, const float *vl,
-                                              int rows, int nc, double *q) {
+// q_i = sum_j (hi_ij + lo_ij) v_j for the CTA's rows i < rows, left as the
+// double-single pair (qh_i, ql_i); q_i = qh_i + ql_i in FP64 is formed by the
+// caller, one lane per row.  Warp w takes rows w, w + 8, ..., four at a time
+// (independent chains; the vector chunk is loaded once for the four); lane l
+// covers columns 4 l + 128 t (16-byte shared loads, no bank conflicts), two
+// double-single chains per row, joined by a butterfly.
+__device__ __forceinline__ void product_ds(const float *Ah, const float *Al, const float *vh, const float *vl,
+                                           int rows, int nc, float *qh, float *ql) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n4 = nc >> 2;
     const float4 *xh = reinterpret_cast<const float4 *>(vh);
     const float4 *xl = reinterpret_cast<const float4 *>(vl);
-    for (int i = warp; i < rows; i += FW) {
-        const float4 *ah = reinterpret_cast<const float4 *>(Ah + (size_t)i * nc);
-        const float4 *al = reinterpret_cast<const float4 *>(Al + (size_t)i * nc);
-        DSV a0{0.f, 0.f}, a1{0.f, 0.f};
-        for (int c = lane; c < n4; c += 32) {
-            const float4 h = ah[c], l = al[c], ph = xh[c], pl = xl[c];
-            ds_fma(h.x, l.x, DSV{ph.x, pl.x}, a0);
-            ds_fma(h.y, l.y, DSV{ph.y, pl.y}, a1);
-            ds_fma(h.z, l.z, DSV{ph.z, pl.z}, a0);
-            ds_fma(h.w, l.w, DSV{ph.w, pl.w}, a1);
-        }
-        DSV a = a0 + a1;
+    for (int i0 = warp; i0 < rows; i0 += 4 * FW) {
+        DSV acc[4][2];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += shfl_xor_v(a, o);
-        if (lane == 0) q[i] = to_double(a);
+        for (int u = 0; u < 4; u++) acc[u][0] = acc[u][1] = DSV{0.f, 0.f};
+        for (int c = lane; c < n4; c += 32) {
+            const float4 ph = xh[c], pl = xl[c];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * FW;
+                if (i < rows) {
+                    const float4 h = reinterpret_cast<const float4 *>(Ah + (size_t)i * nc)[c];
+                    const float4 l = reinterpret_cast<const float4 *>(Al + (size_t)i * nc)[c];
+                    ds_fma(h.x, l.x, DSV{ph.x, pl.x}, acc[u][0]);
+                    ds_fma(h.y, l.y, DSV{ph.y, pl.y}, acc[u][1]);
+                    ds_fma(h.z, l.z, DSV{ph.z, pl.z}, acc[u][0]);
+                    ds_fma(h.w, l.w, DSV{ph.w, pl.w}, acc[u][1]);
+                }
+            }
+        }
+        DSV t[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) t[u] = acc[u][0] + acc[u][1];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 4; u++) t[u] += shfl_xor_v(t[u], o);
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u * FW;
+                if (i < rows) {
+                    qh[i] = t[u].h;
+                    ql[i] = t[u].l;
+                }
+            }
     }
 }
 
@@ -302,15 +348,25 @@ __device__ __forceinline__ void prefetch_vec(const FComm<CL> &C, int w, int n, d
 // ============================================================================
 // CG (paper, CG paragraph; Hestenes-Stiefel form)
 // ============================================================================
+// The scalar recurrence (alpha, beta, the stop test, the counters) runs in one
+// thread and reaches the others through shared memory (ctl): FP64
+// instructions issue at a small fraction of the FP32 rate here, so a value
+// that every thread computed would cost the FP64 pipe eight warps over.
+struct CgCtl {
+    double rho, tol, rnorm, true_rn, alpha, beta, pq, bn;
+    int iter, cycles, status, nan, conv, go;
+    int upd, stop;     // this step: update p; leave the CG steps
+};
+
 // Shared memory (dynamic): p[nc] (FP64 direction), xr, rr, br, qr (this CTA's
 // rows of x, r, b and of the product), ex0, ex1 (cluster form: the rows it
 // publishes) [Rp each], psm [FUSED_CG_SLOTS] (cluster form: its partial
-// sums), then the FP32 pair of the rows Ah, Al [R nc each] and the split
-// vector vh, vl [nc each].
+// sums), then the FP32 pair of the rows Ah, Al [R nc each], the split vector
+// vh, vl [nc each] and the product's double-single rows qh, ql [Rp each].
 template <bool CL>
 __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    __shared__ double sc[4];
+    __shared__ CgCtl ctl;
     State *st = a.st;
     count_launch(st);
     const int n = a.n, R = a.R, nc = a.nc, Rp = (a.R + 1) & ~1;
@@ -320,10 +376,15 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
     double *xr = p + nc, *rr = xr + Rp, *br = rr + Rp, *qr = br + Rp, *ex0 = qr + Rp, *ex1 = ex0 + Rp;
     double *psm = ex1 + Rp;
     float *Ah = align16(psm + FUSED_CG_SLOTS), *Al = Ah + (size_t)R * nc, *vh = Al + (size_t)R * nc,
-          *vl = vh + nc;
+          *vl = vh + nc, *qh = vl + nc, *ql = qh + Rp;
     FComm<CL> C = make_comm<CL>(a, psm, ex0, ex1);
     auto ex_v = [&](int j) { return C.get_elem(EX_V, j); };
     auto ex_x = [&](int j) { return C.get_elem(EX_X, j); };
+    // q = A v (v in vh, vl) into qr, by warp 0 one lane per row after the product
+    auto product = [&]() {
+        product_ds(Ah, Al, vh, vl, rows, nc, qh, ql);
+        __syncthreads();
+    };
 
     load_rows(a.A, a.lda, r0, rows, n, nc, Ah, Al);
     for (int i = threadIdx.x; i < rows; i += FT) {
@@ -333,21 +394,18 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
     if (a.x0_given) load_vec([&](int j) { return a.x[j]; }, n, nc, false, 1.0, vh, vl, nullptr);
     __syncthreads();
     // r = b - A x0 (or b); ||b||^2 and ||r||^2
-    if (a.x0_given) {
-        fused_product(Ah, Al, vh, vl, rows, nc, qr);
-        __syncthreads();
-    }
+    if (a.x0_given) product();
     if (warp == 0) {
         double bb = 0.0, r2 = 0.0;
         for (int i = lane; i < rows; i += 32) {
-            const double ri = a.x0_given ? br[i] - qr[i] : br[i];
+            const double ri = a.x0_given ? br[i] - ((double)qh[i] + (double)ql[i]) : br[i];
             rr[i] = ri;
             C.put_row(EX_V, i, ri);
             bb += br[i] * br[i];
             r2 += ri * ri;
         }
-        bb = warp_sum(bb);
-        r2 = warp_sum(r2);
+        bb = lane_sum(bb, R);
+        r2 = lane_sum(r2, R);
         if (lane == 0) {
             C.put(CS_BB, bb);
             C.put(CS_R0, r2);
@@ -357,173 +415,185 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
     if (warp == 0) {
         const double b2 = fsum(C, CS_BB), r2 = fsum(C, CS_R0);
         if (lane == 0) {
-            sc[0] = b2;
-            sc[1] = r2;
+            CgCtl &c = ctl;
+            c.bn = sqrt(b2);
+            c.tol = a.rtol * c.bn;
+            c.rho = r2;
+            c.rnorm = c.true_rn = sqrt(r2);
+            c.alpha = c.beta = c.pq = 0.0;
+            c.iter = c.cycles = c.status = c.nan = c.conv = 0;
+            c.go = 1;
+            if (!isfinite(b2) || !isfinite(r2)) {
+                c.nan = 1;
+                c.go = 0;
+            } else if (c.bn == 0.0 || c.rnorm <= c.tol) {
+                c.status = LS_OK;   // b = 0 (x = 0), or the start already solves
+                c.go = 0;
+            } else if (a.max_iter <= 0) {
+                c.status = LS_NOT_CONVERGED;
+                c.go = 0;
+            }
         }
     }
     __syncthreads();
-    const double b2 = sc[0];
-    double rho = sc[1];
-    if (b2 == 0.0 && a.x0_given)   // b = 0: x = 0 solves exactly, whatever x0 was
+    if (ctl.bn == 0.0 && a.x0_given)   // b = 0: x = 0 solves exactly, whatever x0 was
         for (int i = threadIdx.x; i < rows; i += FT) xr[i] = 0.0;
-    const double bn = sqrt(b2), tol = a.rtol * bn;
-    double rnorm = sqrt(rho), true_rn = sqrt(rho), alpha = 0.0, beta = 0.0, pq = 0.0;
-    int iter = 0, cycles = 0, status = 0, nan = 0, conv = 0;
-    bool go = true;
-    if (!isfinite(b2) || !isfinite(rho)) {
-        nan = 1;
-        go = false;
-    } else if (bn == 0.0 || sqrt(rho) <= tol) {
-        status = LS_OK;   // b = 0 (x = 0), or the start already solves
-        go = false;
-    } else if (a.max_iter <= 0) {
-        status = LS_NOT_CONVERGED;
-        go = false;
-    }
     // p = r: the published rows hold r (x0 given); b equals r otherwise
-    if (go) {
+    if (ctl.go) {
         if (a.x0_given) load_vec(ex_v, n, nc, false, 1.0, vh, vl, p);
         else load_vec([&](int j) { return a.b[j]; }, n, nc, false, 1.0, vh, vl, p);
     }
     __syncthreads();
 
-    while (go) {             // residual replacements
+    while (ctl.go) {         // residual replacements
         for (;;) {           // CG steps
-            // q = A p and this CTA's part of p.q
-            fused_product(Ah, Al, vh, vl, rows, nc, qr);
-            __syncthreads();
+            // q = A p, and this CTA's part of p.q (warp 0, a lane per row)
+            product();
             if (warp == 0) {
                 double s = 0.0;
-                for (int i = lane; i < rows; i += 32) s += p[r0 + i] * qr[i];
-                s = warp_sum(s);
+                for (int i = lane; i < rows; i += 32) {
+                    const double q = (double)qh[i] + (double)ql[i];
+                    qr[i] = q;
+                    s += p[r0 + i] * q;
+                }
+                s = lane_sum(s, R);
                 if (lane == 0) C.put(CS_PQ, s);
             }
             // CS_PQ: its readers finish before they arrive at the r.r meeting
             if (!C.meet()) return;
+            // alpha, then x += alpha p, r -= alpha q on this CTA's rows and r
+            // published (every reader of its previous rows has passed the
+            // p.q meeting): all in warp 0
             if (warp == 0) {
-                const double t = fsum(C, CS_PQ);
-                if (lane == 0) sc[0] = t;
+                const double pq = fsum(C, CS_PQ);
+                double alpha = 0.0;
+                if (lane == 0) {
+                    ctl.pq = pq;
+                    if (!(pq > 0.0)) {   // non-positive curvature: A is not SPD (or NaN)
+                        ctl.status = LS_BREAKDOWN;
+                    } else {
+                        alpha = ctl.rho / pq;
+                    }
+                    ctl.alpha = alpha;
+                }
+                alpha = __shfl_sync(0xffffffffu, alpha, 0);
+                if (pq > 0.0) {
+                    double s = 0.0;
+                    for (int i = lane; i < rows; i += 32) {
+                        xr[i] += alpha * p[r0 + i];
+                        const double ri = rr[i] - alpha * qr[i];
+                        rr[i] = ri;
+                        C.put_row(EX_V, i, ri);
+                        s += ri * ri;
+                    }
+                    s = lane_sum(s, R);
+                    if (lane == 0) C.put(CS_RR, s);
+                }
             }
             __syncthreads();
-            pq = sc[0];
-            if (!(pq > 0.0)) {   // non-positive curvature: A is not SPD (or NaN)
-                status = LS_BREAKDOWN;
-                alpha = 0.0;
-                break;
-            }
-            alpha = rho / pq;
-            // x += alpha p, r -= alpha q on this CTA's rows; r published
-            // (every reader of its previous rows has passed the p.q meeting)
-            if (warp == 0) {
-                double s = 0.0;
-                for (int i = lane; i < rows; i += 32) {
-                    xr[i] += alpha * p[r0 + i];
-                    const double ri = rr[i] - alpha * qr[i];
-                    rr[i] = ri;
-                    C.put_row(EX_V, i, ri);
-                    s += ri * ri;
-                }
-                s = warp_sum(s);
-                if (lane == 0) C.put(CS_RR, s);
-            }
+            if (ctl.status == LS_BREAKDOWN) break;
             if (!C.meet()) return;
-            // the whole r in flight while warp 0 adds the partial sums
+            // the whole r in flight while warp 0 adds the partial sums and
+            // one thread takes the scalar step
             double rv[FUSED_VEC_REGS];
             prefetch_vec(C, EX_V, n, rv);
             if (warp == 0) {
-                const double t = fsum(C, CS_RR);
-                if (lane == 0) sc[1] = t;
+                const double rho_new = fsum(C, CS_RR);
+                if (lane == 0) {
+                    CgCtl &c = ctl;
+                    const bool finite = isfinite(rho_new);
+                    const double rn = sqrt(rho_new);
+                    c.beta = rho_new / c.rho;
+                    c.conv = finite && rn <= c.tol;
+                    c.upd = finite && !c.conv;
+                    c.rho = rho_new;
+                    c.rnorm = rn;
+                    c.iter += 1;
+                    if (!finite) c.nan = 1;
+                    c.stop = !finite || c.conv || c.iter >= a.max_iter;
+                }
             }
             __syncthreads();
-            const double rho_new = sc[1];
-            const bool finite = isfinite(rho_new);
-            conv = finite && sqrt(rho_new) <= tol;
-            beta = rho_new / rho;
-            if (finite && !conv) {   // p = r + beta p, the whole vector in every CTA
+            if (ctl.upd) {   // p = r + beta p, the whole vector in every CTA
+                const double beta = ctl.beta;
 #pragma unroll
                 for (int k = 0; k < FUSED_VEC_REGS; k++) {
                     const int j = threadIdx.x + k * FT;
                     if (j < n) {
                         const double pj = rv[k] + beta * p[j];
                         p[j] = pj;
-                        const DSV d = ds_split(pj);
+                        const DSV d = split_bits(pj);
                         vh[j] = d.h;
                         vl[j] = d.l;
                     }
                 }
             }
-            rho = rho_new;
-            rnorm = sqrt(rho_new);
-            iter++;
-            if (!finite) nan = 1;
             __syncthreads();
-            if (!finite || conv || iter >= a.max_iter) break;
+            if (ctl.stop) break;
         }
         // the true residual b - A x: x published
         for (int i = threadIdx.x; i < rows; i += FT) C.put_row(EX_X, i, xr[i]);
         if (!C.meet()) return;
         load_vec(ex_x, n, nc, false, 1.0, vh, vl, nullptr);
         __syncthreads();
-        fused_product(Ah, Al, vh, vl, rows, nc, qr);
-        __syncthreads();
+        product();
         // t = b - A x published: the last readers of r (the p update) have
         // passed the meeting above
         if (warp == 0) {
             double s = 0.0;
             for (int i = lane; i < rows; i += 32) {
-                const double ti = br[i] - qr[i];
+                const double ti = br[i] - ((double)qh[i] + (double)ql[i]);
                 qr[i] = ti;
                 C.put_row(EX_V, i, ti);
                 s += ti * ti;
             }
-            s = warp_sum(s);
+            s = lane_sum(s, R);
             if (lane == 0) C.put(CS_TT, s);
         }
         if (!C.meet()) return;
         if (warp == 0) {
-            const double t = fsum(C, CS_TT);
-            if (lane == 0) sc[2] = t;
+            const double t2 = fsum(C, CS_TT);
+            if (lane == 0) {
+                CgCtl &c = ctl;
+                const double t = sqrt(t2);
+                c.true_rn = t;
+                c.cycles += 1;
+                c.go = 0;
+                if (c.nan || !isfinite(t)) c.nan = 1;
+                else if (c.status == LS_BREAKDOWN) {
+                } else if (t <= c.tol) c.status = LS_OK;
+                else if (c.iter >= a.max_iter) c.status = LS_NOT_CONVERGED;
+                else {   // restart from the true residual
+                    c.go = 1;
+                    c.rho = t * t;
+                    c.rnorm = t;
+                    c.conv = 0;
+                }
+            }
         }
         __syncthreads();
-        const double t = sqrt(sc[2]);
-        true_rn = t;
-        cycles++;
-        if (nan || !isfinite(t)) {
-            nan = 1;
-            break;
-        }
-        if (status == LS_BREAKDOWN) break;
-        if (t <= tol) {
-            status = LS_OK;
-            break;
-        }
-        if (iter >= a.max_iter) {
-            status = LS_NOT_CONVERGED;
-            break;
-        }
-        // restart from the true residual: r = p = b - A x
+        if (!ctl.go) break;
+        // r = p = b - A x
         for (int i = threadIdx.x; i < rows; i += FT) rr[i] = qr[i];
         load_vec(ex_v, n, nc, false, 1.0, vh, vl, p);
-        rho = t * t;
-        rnorm = t;
-        conv = 0;
         __syncthreads();
     }
     for (int i = threadIdx.x; i < rows; i += FT) a.x[r0 + i] = xr[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->bnorm = bn;
-        st->tol_abs = tol;
-        st->rho = rho;
-        st->rnorm = rnorm;
-        st->true_rnorm = true_rn;
-        st->alpha = alpha;
-        st->beta = beta;
-        st->pq = pq;
-        st->iter = iter;
-        st->cycles = cycles;
-        st->conv = conv;
-        st->status = status;
-        if (nan) set_err(st, ERRB_NAN);
+        const CgCtl &c = ctl;
+        st->bnorm = c.bn;
+        st->tol_abs = c.tol;
+        st->rho = c.rho;
+        st->rnorm = c.rnorm;
+        st->true_rnorm = c.true_rn;
+        st->alpha = c.alpha;
+        st->beta = c.beta;
+        st->pq = c.pq;
+        st->iter = c.iter;
+        st->cycles = c.cycles;
+        st->conv = c.conv;
+        st->status = c.status;
+        if (c.nan) set_err(st, ERRB_NAN);
     }
     C.leave();
 }
@@ -532,19 +602,45 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
 // GMRES(m) (paper, GMRES pseudocode and restart paragraph; least squares by
 // Givens rotations)
 // ============================================================================
+// As for CG, the scalar work runs in one thread (ctl).  Sums over this CTA's
+// rows and over the basis run as four interleaved partial sums (FP64
+// latency, not throughput, bounds them here); the normalisations multiply by
+// a reciprocal formed once; the back substitution is column oriented with the
+// reciprocals of R's diagonal formed by the rotations.
+struct GmCtl {
+    double bn, tol, true_rn, est, wn, inv;
+    int total, cycles, status, nan, k, go, pass2, lucky, stop;
+};
+
+// Sum over i < cnt of u[i] w[i] (strides su, sw) as four interleaved partial
+// sums, added in a fixed order.
+__device__ __forceinline__ double dot4(const double *u, int su, const double *w, int sw, int cnt) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 4 <= cnt; i += 4) {
+        s0 += u[(size_t)i * su] * w[(size_t)i * sw];
+        s1 += u[(size_t)(i + 1) * su] * w[(size_t)(i + 1) * sw];
+        s2 += u[(size_t)(i + 2) * su] * w[(size_t)(i + 2) * sw];
+        s3 += u[(size_t)(i + 3) * su] * w[(size_t)(i + 3) * sw];
+    }
+    if (i < cnt) s0 += u[(size_t)i * su] * w[(size_t)i * sw];
+    if (i + 1 < cnt) s1 += u[(size_t)(i + 1) * su] * w[(size_t)(i + 1) * sw];
+    if (i + 2 < cnt) s2 += u[(size_t)(i + 2) * su] * w[(size_t)(i + 2) * sw];
+    return (s0 + s1) + (s2 + s3);
+}
+
 // Shared memory (dynamic): Vr [(m + 1) Rp] (this CTA's rows of the basis,
 // column j at Vr + j Rp), xr, br, wr, ex0, ex1 [Rp each], h1, h2, hs, g, hc
-// [m + 2 each], cs, sn, ys [m + 1 each], psm [FUSED_PART_SLOTS], then (when
-// h_smem) the rotated Hessenberg matrix Hs [(m + 1) m], then Ah, Al [R nc
-// each] and vh, vl [nc each].  Every CTA keeps its own copy of the rotated
-// Hessenberg matrix (in shared memory, or at a.H + blockIdx.x (m + 1) m,
-// column-major); all copies are equal because every CTA applies the same
-// rotations to the same numbers.
+// [m + 2 each], cs, sn, ys, rinv [m + 1 each], psm [FUSED_PART_SLOTS], then
+// (when h_smem) the rotated Hessenberg matrix Hs [(m + 1) m], then Ah, Al
+// [R nc each], vh, vl [nc each] and qh, ql [Rp each].  Every CTA keeps its
+// own copy of the rotated Hessenberg matrix (in shared memory, or at
+// a.H + blockIdx.x (m + 1) m, column-major); all copies are equal because
+// every CTA applies the same rotations to the same numbers.
 template <bool CL>
 __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     extern __shared__ __align__(16) unsigned char fsm[];
-    __shared__ double sc[4];
-    __shared__ int flag_s[2];
+    __shared__ GmCtl ctl;
     State *st = a.st;
     count_launch(st);
     const int n = a.n, R = a.R, nc = a.nc, m = a.m, Rp = (a.R + 1) & ~1;
@@ -553,14 +649,35 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     double *Vr = reinterpret_cast<double *>(fsm);
     double *xr = Vr + (size_t)(m + 1) * Rp, *br = xr + Rp, *wr = br + Rp, *ex0 = wr + Rp, *ex1 = ex0 + Rp;
     double *h1 = ex1 + Rp, *h2 = h1 + (m + 2), *hs = h2 + (m + 2), *g = hs + (m + 2), *hc = g + (m + 2);
-    double *cs = hc + (m + 2), *sn = cs + (m + 1), *ys = sn + (m + 1), *psm = ys + (m + 1);
+    double *cs = hc + (m + 2), *sn = cs + (m + 1), *ys = sn + (m + 1), *rinv = ys + (m + 1);
+    double *psm = rinv + (m + 1);
     double *Hs = psm + FUSED_PART_SLOTS;
     double *H = a.h_smem ? Hs : a.H + (size_t)blockIdx.x * (m + 1) * m;
     float *Ah = align16(a.h_smem ? Hs + (size_t)(m + 1) * m : Hs);
-    float *Al = Ah + (size_t)R * nc, *vh = Al + (size_t)R * nc, *vl = vh + nc;
+    float *Al = Ah + (size_t)R * nc, *vh = Al + (size_t)R * nc, *vl = vh + nc, *qh = vl + nc, *ql = qh + Rp;
     const int m1 = m + 1;
     FComm<CL> C = make_comm<CL>(a, psm, ex0, ex1);
     auto ex_x = [&](int j) { return C.get_elem(EX_X, j); };
+    // w = A v (v in vh, vl) into wr
+    auto product = [&]() {
+        product_ds(Ah, Al, vh, vl, rows, nc, qh, ql);
+        __syncthreads();
+        for (int i = threadIdx.x; i < rows; i += FT) wr[i] = (double)qh[i] + (double)ql[i];
+        __syncthreads();
+    };
+    // (vh, vl) = split of rv * inv (the whole vector); the CTA's rows of it into V column col
+    auto scaled_basis = [&](const double (&rv)[FUSED_VEC_REGS], double inv, int col) {
+#pragma unroll
+        for (int q = 0; q < FUSED_VEC_REGS; q++) {
+            const int jj = threadIdx.x + q * FT;
+            if (jj < nc) {
+                const DSV d = split_bits(jj < n ? rv[q] * inv : 0.0);
+                vh[jj] = d.h;
+                vl[jj] = d.l;
+            }
+        }
+        for (int i = threadIdx.x; i < rows; i += FT) Vr[(size_t)col * Rp + i] = wr[i] * inv;
+    };
 
     load_rows(a.A, a.lda, r0, rows, n, nc, Ah, Al);
     for (int i = threadIdx.x; i < rows; i += FT) {
@@ -570,18 +687,19 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     if (a.x0_given) load_vec([&](int j) { return a.x[j]; }, n, nc, false, 1.0, vh, vl, nullptr);
     else
         for (int j = threadIdx.x; j < nc; j += FT) vh[j] = vl[j] = 0.f;
+    if (threadIdx.x == 0) {
+        ctl.total = ctl.cycles = ctl.status = ctl.nan = ctl.k = 0;
+        ctl.bn = ctl.tol = ctl.true_rn = ctl.est = 0.0;
+    }
     __syncthreads();
 
-    double bn = 0.0, tol = 0.0, true_rn = 0.0, est = 0.0;
-    int total = 0, cycles = 0, status = 0, nan = 0, k = 0;
     bool first = true;
     double rv[FUSED_VEC_REGS];
     for (;;) {   // cycles: each starts from the true residual
         // r = b - A x (x is in vh, vl), published: the last readers of the
         // previous contents (v_{k+1} of the previous cycle) have passed the
         // meeting that published x
-        fused_product(Ah, Al, vh, vl, rows, nc, wr);
-        __syncthreads();
+        product();
         if (warp == 0) {
             double s = 0.0, bb = 0.0;
             for (int i = lane; i < rows; i += 32) {
@@ -589,10 +707,10 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
                 wr[i] = ri;
                 C.put_row(EX_V, i, ri);
                 s += ri * ri;
-                bb += br[i] * br[i];
+                if (first) bb += br[i] * br[i];
             }
-            s = warp_sum(s);
-            bb = warp_sum(bb);
+            s = lane_sum(s, R);
+            if (first) bb = lane_sum(bb, R);
             if (lane == 0) {
                 C.put(gsr(m), s);
                 if (first) C.put(gsb(m), bb);
@@ -603,94 +721,63 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
         if (warp == 0) {
             const double t = fsum(C, gsr(m));
             const double b2 = first ? fsum(C, gsb(m)) : 0.0;
-            if (lane == 0) {
-                sc[0] = t;
-                sc[1] = b2;
+            if (lane == 0) {   // the cycle's start (or the end of the solve)
+                GmCtl &c = ctl;
+                c.go = 0;
+                if (first) {
+                    c.bn = sqrt(b2);
+                    c.tol = a.rtol * c.bn;
+                }
+                const double beta = sqrt(t);
+                if (first && !isfinite(b2)) c.nan = 1;
+                else if (first && c.bn == 0.0) {   // b = 0: x = 0 solves exactly
+                    c.status = LS_OK;
+                    c.true_rn = 0.0;
+                    c.go = -1;
+                } else {
+                    c.true_rn = beta;
+                    if (c.nan || !isfinite(beta)) c.nan = 1;
+                    else if (c.status == LS_BREAKDOWN) {
+                    } else if (beta <= c.tol) c.status = LS_OK;
+                    else if (c.total >= a.max_iter) c.status = LS_NOT_CONVERGED;
+                    else {
+                        c.go = 1;
+                        c.cycles += 1;
+                        c.inv = 1.0 / beta;
+                        c.est = beta;
+                        c.k = 0;
+                        g[0] = beta;
+                    }
+                }
             }
         }
         __syncthreads();
-        if (first) {
-            const double b2 = sc[1];
-            bn = sqrt(b2);
-            tol = a.rtol * bn;
-            if (!isfinite(b2)) {
-                nan = 1;
-                break;
-            }
-            if (bn == 0.0) {   // b = 0: x = 0 solves exactly
-                for (int i = threadIdx.x; i < rows; i += FT) xr[i] = 0.0;
-                status = LS_OK;
-                true_rn = 0.0;
-                break;
-            }
-            first = false;
-        }
-        const double beta = sqrt(sc[0]);
-        true_rn = beta;
-        if (nan || !isfinite(beta)) {
-            nan = 1;
-            break;
-        }
-        if (status == LS_BREAKDOWN) break;
-        if (beta <= tol) {
-            status = LS_OK;
-            break;
-        }
-        if (total >= a.max_iter) {
-            status = LS_NOT_CONVERGED;
-            break;
-        }
-        // v_0 = r / beta: the whole vector (from the prefetched r) and this CTA's rows
-        cycles++;
-#pragma unroll
-        for (int q = 0; q < FUSED_VEC_REGS; q++) {
-            const int j = threadIdx.x + q * FT;
-            if (j < nc) {
-                const DSV d = ds_split(j < n ? rv[q] / beta : 0.0);
-                vh[j] = d.h;
-                vl[j] = d.l;
-            }
-        }
-        for (int i = threadIdx.x; i < rows; i += FT) Vr[i] = wr[i] / beta;
-        if (threadIdx.x == 0) g[0] = beta;
-        est = beta;
-        k = 0;
+        first = false;
+        if (ctl.go < 0)   // b = 0
+            for (int i = threadIdx.x; i < rows; i += FT) xr[i] = 0.0;
+        if (ctl.go <= 0) break;
+        scaled_basis(rv, ctl.inv, 0);   // v_0 = r / beta
         __syncthreads();
 
         for (int j = 0;; j++) {   // Arnoldi steps; v_j is in vh, vl
-            fused_product(Ah, Al, vh, vl, rows, nc, wr);
-            __syncthreads();
+            product();
             // first pass: V_j^T w and ||w||^2 over this CTA's rows (thread t: column t)
-            for (int t = threadIdx.x; t <= j + 1; t += FT) {
-                double s = 0.0;
-                if (t <= j)
-                    for (int i = 0; i < rows; i++) s += Vr[(size_t)t * Rp + i] * wr[i];
-                else
-                    for (int i = 0; i < rows; i++) s += wr[i] * wr[i];
-                C.put(gs1(t), s);
-            }
+            for (int t = threadIdx.x; t <= j + 1; t += FT)
+                C.put(gs1(t), t <= j ? dot4(Vr + (size_t)t * Rp, 1, wr, 1, rows) : dot4(wr, 1, wr, 1, rows));
             if (!C.meet()) return;
             fsum_slots(C, gs1(0), j + 2, h1);
             __syncthreads();
-            const double wnorm0 = h1[j + 1];
             // w -= V_j h, published (its readers of the last step have passed
             // the meeting above); the second-pass dots and ||w||^2 published
             // with it
             for (int i = threadIdx.x; i < rows; i += FT) {
-                double wi = wr[i];
-                for (int t = 0; t <= j; t++) wi -= h1[t] * Vr[(size_t)t * Rp + i];
+                const double wi = wr[i] - dot4(h1, 1, Vr + i, Rp, j + 1);
                 wr[i] = wi;
                 C.put_row(EX_V, i, wi);
             }
             __syncthreads();
-            for (int t = threadIdx.x; t <= j + 1; t += FT) {
-                double s = 0.0;
-                if (t <= j)
-                    for (int i = 0; i < rows; i++) s += Vr[(size_t)t * Rp + i] * wr[i];
-                else
-                    for (int i = 0; i < rows; i++) s += wr[i] * wr[i];
-                C.put(gs2(m, t), s);
-            }
+            for (int t = threadIdx.x; t <= j + 1; t += FT)
+                C.put(gs2(m, t), t <= j ? dot4(Vr + (size_t)t * Rp, 1, wr, 1, rows) : dot4(wr, 1, wr, 1, rows));
             if (!C.meet()) return;
             // w in flight while the sums are formed.  When the second pass
             // runs, a CTA that has taken its decision may overwrite its rows
@@ -700,19 +787,19 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
             fsum_slots(C, gs2(m, 0), j + 2, h2);
             for (int t = threadIdx.x; t <= j; t += FT) hs[t] = h1[t];
             __syncthreads();
-            double wn2 = h2[j + 1];
             // a second pass only when cancellation lost accuracy (or always if asked)
-            if (a.reorth || wn2 < 0.49 * wnorm0) {
+            if (threadIdx.x == 0) ctl.pass2 = a.reorth || h2[j + 1] < 0.49 * h1[j + 1];
+            __syncthreads();
+            if (ctl.pass2) {
                 if (warp == 0) {
                     double s = 0.0;
                     for (int i = lane; i < rows; i += 32) {
-                        double wi = wr[i];
-                        for (int t = 0; t <= j; t++) wi -= h2[t] * Vr[(size_t)t * Rp + i];
+                        const double wi = wr[i] - dot4(h2, 1, Vr + i, Rp, j + 1);
                         wr[i] = wi;
                         C.put_row(EX_V, i, wi);
                         s += wi * wi;
                     }
-                    s = warp_sum(s);
+                    s = lane_sum(s, R);
                     if (lane == 0) C.put(gs3(m), s);
                 }
                 for (int t = threadIdx.x; t <= j; t += FT) hs[t] += h2[t];
@@ -720,84 +807,70 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
                 prefetch_vec(C, EX_V, n, rv);
                 if (warp == 0) {
                     const double v = fsum(C, gs3(m));
-                    if (lane == 0) sc[2] = v;
+                    if (lane == 0) h2[j + 1] = v;   // ||w||^2 after the second pass
                 }
                 __syncthreads();
-                wn2 = sc[2];
             }
-            const double wn = sqrt(wn2);
-            const bool lucky = !(wn > 1e-14 * sqrt(wnorm0));
-            if (!lucky) {   // v_{j+1} = w / ||w||, the whole vector, and this CTA's rows of it
-#pragma unroll
-                for (int q = 0; q < FUSED_VEC_REGS; q++) {
-                    const int jj = threadIdx.x + q * FT;
-                    if (jj < nc) {
-                        const DSV d = ds_split(jj < n ? rv[q] / wn : 0.0);
-                        vh[jj] = d.h;
-                        vl[jj] = d.l;
-                    }
-                }
-                for (int i = threadIdx.x; i < rows; i += FT) Vr[(size_t)(j + 1) * Rp + i] = wr[i] / wn;
-            }
-            // the new Hessenberg column, the old rotations, the new one (one
-            // thread, in shared memory), then the column into this CTA's copy
             if (threadIdx.x == 0) {
+                GmCtl &c = ctl;
+                c.wn = sqrt(h2[j + 1]);
+                c.lucky = !(c.wn > 1e-14 * sqrt(h1[j + 1]));
+                c.inv = 1.0 / c.wn;
+            }
+            __syncthreads();
+            // thread 32 takes the new Hessenberg column through the old
+            // rotations and forms the new one, while the others form
+            // v_{j+1} = w / ||w|| (thread 32 joins them afterwards)
+            if (threadIdx.x == 32) {
+                GmCtl &c = ctl;
                 for (int t = 0; t <= j; t++) hc[t] = hs[t];
-                hc[j + 1] = wn;
+                hc[j + 1] = c.wn;
                 for (int t = 0; t < j; t++) {
                     const double x0 = hc[t], x1 = hc[t + 1];
                     hc[t] = cs[t] * x0 + sn[t] * x1;
                     hc[t + 1] = -sn[t] * x0 + cs[t] * x1;
                 }
                 const double den = hypot(hc[j], hc[j + 1]);
-                int stop = 0, brk = 0;
+                c.stop = 0;
                 if (den == 0.0 || !isfinite(den)) {
-                    brk = isfinite(den) ? 1 : 2;
-                    stop = 1;
+                    c.status = LS_BREAKDOWN;
+                    if (!isfinite(den)) c.nan = 1;
+                    c.stop = 1;
                 } else {
-                    const double c = hc[j] / den, s = hc[j + 1] / den;
-                    cs[j] = c;
-                    sn[j] = s;
+                    const double cj = hc[j] / den, sj = hc[j + 1] / den;
+                    cs[j] = cj;
+                    sn[j] = sj;
                     hc[j] = den;
                     hc[j + 1] = 0.0;
-                    g[j + 1] = -s * g[j];
-                    g[j] = c * g[j];
-                    sc[3] = fabs(g[j + 1]);
-                    if (sc[3] <= tol || lucky || j + 1 >= m || total + 1 >= a.max_iter) stop = 1;
+                    rinv[j] = 1.0 / den;
+                    g[j + 1] = -sj * g[j];
+                    g[j] = cj * g[j];
+                    c.est = fabs(g[j + 1]);
+                    c.k = j + 1;
+                    c.total += 1;
+                    if (c.est <= c.tol || c.lucky || j + 1 >= m || c.total >= a.max_iter) c.stop = 1;
                 }
                 double *Hk = H + (size_t)j * m1;
                 for (int t = 0; t <= j + 1; t++) Hk[t] = hc[t];
-                flag_s[0] = stop;
-                flag_s[1] = brk;
             }
+            if (!ctl.lucky) scaled_basis(rv, ctl.inv, j + 1);
             __syncthreads();
-            if (flag_s[1]) {
-                status = LS_BREAKDOWN;
-                if (flag_s[1] == 2) nan = 1;
-                break;
-            }
-            k = j + 1;
-            total++;
-            est = sc[3];
-            if (flag_s[0]) break;
+            if (ctl.stop) break;
         }
-        // end of the cycle: R y = g (one warp, from this CTA's copy of R), x += V_k y
-        if (status != LS_BREAKDOWN && k > 0) {
+        // end of the cycle: R y = g by columns (warp 0: y_i = g_i / r_ii, then
+        // g_t -= r_ti y_i for t < i, lane t), then x += V_k y on this CTA's rows
+        const int k = ctl.k;
+        if (ctl.status != LS_BREAKDOWN && k > 0) {
             if (warp == 0) {
                 for (int i = k - 1; i >= 0; i--) {
-                    double s = 0.0;
-                    for (int t = i + 1 + lane; t < k; t += 32) s += H[(size_t)t * m1 + i] * ys[t];
-                    s = warp_sum(s);
-                    if (lane == 0) ys[i] = (g[i] - s) / H[(size_t)i * m1 + i];
+                    const double yi = g[i] * rinv[i];
+                    if (lane == 0) ys[i] = yi;
+                    for (int t = lane; t < i; t += 32) g[t] -= H[(size_t)i * m1 + t] * yi;
                     __syncwarp();
                 }
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < rows; i += FT) {
-                double xi = xr[i];
-                for (int t = 0; t < k; t++) xi += Vr[(size_t)t * Rp + i] * ys[t];
-                xr[i] = xi;
-            }
+            for (int i = threadIdx.x; i < rows; i += FT) xr[i] += dot4(ys, 1, Vr + i, Rp, k);
         }
         // x published, then the whole x into vh, vl
         for (int i = threadIdx.x; i < rows; i += FT) C.put_row(EX_X, i, xr[i]);
@@ -807,17 +880,18 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     }
     for (int i = threadIdx.x; i < rows; i += FT) a.x[r0 + i] = xr[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->bnorm = bn;
-        st->tol_abs = tol;
-        st->true_rnorm = true_rn;
-        st->est = est;
-        st->rnorm = est;
-        st->k = k;
-        st->total = total;
-        st->iter = total;
-        st->cycles = cycles;
-        st->status = status;
-        if (nan) set_err(st, ERRB_NAN);
+        const GmCtl &c = ctl;
+        st->bnorm = c.bn;
+        st->tol_abs = c.tol;
+        st->true_rnorm = c.true_rn;
+        st->est = c.est;
+        st->rnorm = c.est;
+        st->k = c.k;
+        st->total = c.total;
+        st->iter = c.total;
+        st->cycles = c.cycles;
+        st->status = c.status;
+        if (c.nan) set_err(st, ERRB_NAN);
     }
     C.leave();
 }
