@@ -163,19 +163,21 @@ struct FComm<true> {
 };
 
 // Butterfly sum over the first `width` lanes of the warp (the others hold
-// 0); every lane gets the same bits.  Only as many levels as the data needs:
-// on this GPU each dependent FP64 addition costs on the order of a hundred
-// cycles.
+// 0), then lane 0's total broadcast, so every lane returns the same bits
+// (the callers branch on it, and a branch that splits the warp around a
+// full-warp shuffle would never finish).  Only as many levels as the data
+// needs: on this GPU each dependent FP64 addition costs on the order of a
+// hundred cycles.  Every lane of the warp must call it.
 __device__ __forceinline__ double lane_sum(double s, int width) {
     int o = 1;
     while (o < width && o < 32) o <<= 1;
     for (o >>= 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return s;
+    return __shfl_sync(0xffffffffu, s, 0);
 }
 
-// Sum of slot `slot` over the G CTAs' partials, by the calling warp.  Every
-// CTA adds the same values in the same order, and the butterfly leaves the
-// same bits in every lane.
+// Sum of slot `slot` over the G CTAs' partials, by the calling warp (every
+// lane returns the total).  Every CTA adds the same values in the same
+// order, so all CTAs get the same bits.
 template <bool CL>
 __device__ __forceinline__ double fsum(const FComm<CL> &C, int slot) {
     const int lane = threadIdx.x & 31;
