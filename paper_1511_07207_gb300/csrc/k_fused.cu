@@ -231,14 +231,28 @@ __device__ __forceinline__ DSV split_bits(double v) {
 // padded with zeros to a multiple of 4).
 __device__ void load_rows(const double *__restrict__ A, long long lda, int r0, int rows, int n, int nc,
                           float *Ah, float *Al) {
+    constexpr int B = 8;   // loads in flight per thread
     const int total = rows * nc;
-    for (int e = threadIdx.x; e < total; e += FT) {
-        const int i = e / nc, j = e - i * nc;
-        float h = 0.f, l = 0.f;
-        if (j < n) split_pair(A[(long long)(r0 + i) * lda + j], h, l);
-        Ah[e] = h;
-        Al[e] = l;
+    for (int e0 = threadIdx.x; e0 < total; e0 += B * FT) {
+        double v[B];
+#pragma unroll
+        for (int u = 0; u < B; u++) {
+            const int e = e0 + u * FT;
+            const int i = e / nc, j = e - i * nc;
+            v[u] = (e < total && j < n) ? A[(long long)(r0 + i) * lda + j] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < B; u++) {
+            const int e = e0 + u * FT;
+            if (e < total) {
+                float h, l;
+                split_pair(v[u], h, l);
+                Ah[e] = h;
+                Al[e] = l;
+            }
+        }
     }
+}
 }
 
 // (vh, vl) = split of v_j = get(j) / scale (scale_it) or get(j), zero
@@ -355,7 +369,7 @@ __device__ __forceinline__ void prefetch_vec(const FComm<CL> &C, int w, int n, d
 // instructions issue at a small fraction of the FP32 rate here, so a value
 // that every thread computed would cost the FP64 pipe eight warps over.
 struct CgCtl {
-    double rho, tol, rnorm, true_rn, alpha, beta, pq, bn;
+    double rho, tol, tol2, inv_rho, rnorm, true_rn, alpha, beta, pq, bn;
     int iter, cycles, status, nan, conv, go;
     int upd, stop;     // this step: update p; leave the CG steps
 };
@@ -420,6 +434,7 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
             CgCtl &c = ctl;
             c.bn = sqrt(b2);
             c.tol = a.rtol * c.bn;
+            c.tol2 = c.tol * c.tol;
             c.rho = r2;
             c.rnorm = c.true_rn = sqrt(r2);
             c.alpha = c.beta = c.pq = 0.0;
@@ -449,6 +464,9 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
 
     while (ctl.go) {         // residual replacements
         for (;;) {           // CG steps
+            // 1 / rho for this step's beta, off the critical path (its
+            // latency hides behind the product)
+            if (threadIdx.x == FT - 32) ctl.inv_rho = 1.0 / ctl.rho;
             // q = A p, and this CTA's part of p.q (warp 0, a lane per row)
             product();
             if (warp == 0) {
@@ -504,12 +522,13 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
                 if (lane == 0) {
                     CgCtl &c = ctl;
                     const bool finite = isfinite(rho_new);
-                    const double rn = sqrt(rho_new);
-                    c.beta = rho_new / c.rho;
-                    c.conv = finite && rn <= c.tol;
+                    // the stop test ||r|| <= tol as ||r||^2 <= tol^2 and beta
+                    // = rho' / rho through the reciprocal formed during the
+                    // product: no square root or division on the critical path
+                    c.beta = rho_new * c.inv_rho;
+                    c.conv = finite && rho_new <= c.tol2;
                     c.upd = finite && !c.conv;
                     c.rho = rho_new;
-                    c.rnorm = rn;
                     c.iter += 1;
                     if (!finite) c.nan = 1;
                     c.stop = !finite || c.conv || c.iter >= a.max_iter;
@@ -568,7 +587,6 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
                 else {   // restart from the true residual
                     c.go = 1;
                     c.rho = t * t;
-                    c.rnorm = t;
                     c.conv = 0;
                 }
             }
@@ -586,7 +604,7 @@ __global__ void __launch_bounds__(FT, 1) cg_fused_kernel(FusedArgs a) {
         st->bnorm = c.bn;
         st->tol_abs = c.tol;
         st->rho = c.rho;
-        st->rnorm = c.rnorm;
+        st->rnorm = sqrt(c.rho);
         st->true_rnorm = c.true_rn;
         st->alpha = c.alpha;
         st->beta = c.beta;
