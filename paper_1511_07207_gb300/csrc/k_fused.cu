@@ -253,7 +253,6 @@ __device__ void load_rows(const double *__restrict__ A, long long lda, int r0, i
         }
     }
 }
-}
 
 // (vh, vl) = split of v_j = get(j) / scale (scale_it) or get(j), zero
 // padding up to nc; the FP64 values optionally kept in keep[].
