@@ -945,7 +945,8 @@ def run_block_cg_steps(args):
     """Block CG alone (timing and ncu captures): the SPD matrix G G^T/n + 1e-3 I
     at --n with --rhs right-hand sides; one solve of one step and one of
     1 + --reps steps; the difference is --reps steps (block product Q = A P
-    and the step kernel)."""
+    and the step kernels), in the deflating form (the default) and in
+    O'Leary's form."""
     import torch
     from paper_1511_07207_gb300 import binding as B
     from paper_1511_07207_gb300 import inputs
@@ -955,18 +956,20 @@ def run_block_cg_steps(args):
     A = inputs.spd_matrix(n, 1e-3, seed=0, device=dev)
     Xs = torch.from_numpy(inputs.solution(n, seed=2, nrhs=s).T.copy()).to(dev)
     Bm = (A @ Xs.t()).t().contiguous().t()
-    times = {}
-    for k in (1, 1, 1 + args.reps):
-        X = torch.zeros((s, n), dtype=torch.float64, device=dev).t()
-        st, info = B.ls_block_cg_solve(ctx, A, Bm, X, B.make_opts(rtol=1e-300, max_iter=k))
-        assert st == B.LS_NOT_CONVERGED and info["iters"] == k, (st, info)
-        times[k] = info["time_ms"]
-    step = (times[1 + args.reps] - times[1]) / args.reps
-    mac = float(n) * n * s
-    print(json.dumps({"kernel": "block_cg", "n": n, "rhs": s, "reps": args.reps, "ms_per_step": round(step, 4),
-                      "A_GB/s": round(8.0 * n * n / step / 1e6, 1),
-                      "fp32_ops_per_s": round(12.0 * mac / step / 1e9, 1),
-                      "note": "12 FP32 operations per element of A and column (double-single)"}))
+    out = {"kernel": "block_cg", "n": n, "rhs": s, "reps": args.reps,
+           "note": "12 FP32 operations per element of A and column (double-single)"}
+    for name, deflate in (("deflating", 1), ("oleary", 0)):
+        times = {}
+        for k in (1, 1, 1 + args.reps):
+            X = torch.zeros((s, n), dtype=torch.float64, device=dev).t()
+            st, info = B.ls_block_cg_solve(ctx, A, Bm, X, B.make_opts(rtol=1e-300, max_iter=k, deflate=deflate))
+            assert st == B.LS_NOT_CONVERGED and info["iters"] == k, (st, info)
+            times[k] = info["time_ms"]
+        step = (times[1 + args.reps] - times[1]) / args.reps
+        mac = float(n) * n * s
+        out[name] = {"ms_per_step": round(step, 4), "A_GB/s": round(8.0 * n * n / step / 1e6, 1),
+                     "fp32_ops_per_s": round(12.0 * mac / step / 1e9, 1)}
+    print(json.dumps(out))
     B.ls_destroy(ctx)
 
 

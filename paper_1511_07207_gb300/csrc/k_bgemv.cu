@@ -6,12 +6,13 @@
 // TMA map) and the matching 256-row chunk of P (pre-split into FP32 pairs,
 // column panels padded with zeros to a multiple of 256, one 1-D bulk copy
 // per column and part) through a ring of shared-memory stages (mbarrier
-// full/empty).  Eight consumer warps: thread t owns row t / 16 of the block
-// and, with g = t % 16, the 4-column chunks g, g + 16, g + 32, g + 48 of each
-// tile; it accumulates all S columns of P in double-single (a tile's partial
-// in a plain pair, added to the running sum with a renormalising two-sum),
-// and the 16 lanes of a row add their sums by shuffles at the end of the
-// row block.  Every row block belongs to one CTA and is summed in column
+// full/empty).  Eight consumer warps: warp w owns rows w and w + 8 of the
+// block and lane g the 4-column chunks g and g + 32 of each tile, so every
+// shared-memory load of P serves two rows; a thread accumulates all S
+// columns of P for its two rows in double-single (a tile's partial in a
+// plain pair, added to the running sum with a renormalising two-sum), and
+// the 32 lanes of a row add their sums by shuffles at the end of the row
+// block.  Every row block belongs to one CTA and is summed in column
 // order, so results are deterministic.  Work per element of A is 12 FP32
 // operations per column of P: compute-bound for S >= 4 (HBM-bound below).
 #include <cuda_runtime.h>
@@ -140,12 +141,15 @@ __global__ void __launch_bounds__(BG_T, 1) bgemv_kernel(const MatDesc *__restric
     }
 
     // ---- consumers ----
-    const int r = threadIdx.x / 16, g = threadIdx.x % 16;
+    // warp w: rows w and w + 8 of the block; lane g: 4-column chunks g and g + 32
+    const int w = threadIdx.x >> 5, g = threadIdx.x & 31;
     int seq = 0;
     for (int rb = blockIdx.x; rb < RB; rb += gridDim.x) {
-        F2 acc[S];
+        F2 acc[2][S];
 #pragma unroll
-        for (int j = 0; j < S; j++) acc[j] = {0.f, 0.f};
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int j = 0; j < S; j++) acc[q][j] = {0.f, 0.f};
         for (int t = 0; t < CT; t++) {
             const int sl = seq % NST;
             const bool ok = mbar_wait(&full[sl], (seq / NST) & 1);
@@ -154,51 +158,67 @@ __global__ void __launch_bounds__(BG_T, 1) bgemv_kernel(const MatDesc *__restric
                 return;
             }
             const unsigned char *base = ring + (size_t)sl * SB;
-            const float *Ah = reinterpret_cast<const float *>(base) + r * BG_TC;
-            const float *Al = reinterpret_cast<const float *>(base + BG_A_B) + r * BG_TC;
+            const float *Ah = reinterpret_cast<const float *>(base);
+            const float *Al = reinterpret_cast<const float *>(base + BG_A_B);
             const float *Xh = reinterpret_cast<const float *>(base + 2 * BG_A_B);
             const float *Xl = Xh + S * BG_TC;
-            F2 part[S];
+            F2 part[2][S];
 #pragma unroll
-            for (int j = 0; j < S; j++) part[j] = {0.f, 0.f};
+            for (int q = 0; q < 2; q++)
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const int c0 = (k * 16 + g) * 4;
-                const float4 ah = *reinterpret_cast<const float4 *>(Ah + c0);
-                const float4 al = *reinterpret_cast<const float4 *>(Al + c0);
+                for (int j = 0; j < S; j++) part[q][j] = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const int c0 = (k * 32 + g) * 4;
+                float4 ah[2], al[2];
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    ah[q] = *reinterpret_cast<const float4 *>(Ah + (w + 8 * q) * BG_TC + c0);
+                    al[q] = *reinterpret_cast<const float4 *>(Al + (w + 8 * q) * BG_TC + c0);
+                }
 #pragma unroll
                 for (int j = 0; j < S; j++) {
                     const float4 xh = *reinterpret_cast<const float4 *>(Xh + j * BG_TC + c0);
                     const float4 xl = *reinterpret_cast<const float4 *>(Xl + j * BG_TC + c0);
-                    f2_mac(part[j], ah.x, al.x, xh.x, xl.x);
-                    f2_mac(part[j], ah.y, al.y, xh.y, xl.y);
-                    f2_mac(part[j], ah.z, al.z, xh.z, xl.z);
-                    f2_mac(part[j], ah.w, al.w, xh.w, xl.w);
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        f2_mac(part[q][j], ah[q].x, al[q].x, xh.x, xl.x);
+                        f2_mac(part[q][j], ah[q].y, al[q].y, xh.y, xl.y);
+                        f2_mac(part[q][j], ah[q].z, al[q].z, xh.z, xl.z);
+                        f2_mac(part[q][j], ah[q].w, al[q].w, xh.w, xl.w);
+                    }
                 }
             }
             __syncwarp();
-            if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[sl]);
+            if (g == 0) mbar_arrive(&empty[sl]);
 #pragma unroll
-            for (int j = 0; j < S; j++) acc[j] = f2_add(acc[j], part[j]);
+            for (int q = 0; q < 2; q++)
+#pragma unroll
+                for (int j = 0; j < S; j++) acc[q][j] = f2_add(acc[q][j], part[q][j]);
             seq++;
         }
-        // the 16 lanes of a row
+        // the 32 lanes of a row
 #pragma unroll
-        for (int j = 0; j < S; j++) {
+        for (int q = 0; q < 2; q++)
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                F2 b;
-                b.h = __shfl_xor_sync(0xffffffffu, acc[j].h, o);
-                b.l = __shfl_xor_sync(0xffffffffu, acc[j].l, o);
-                acc[j] = f2_add(acc[j], b);
+            for (int j = 0; j < S; j++) {
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    F2 b;
+                    b.h = __shfl_xor_sync(0xffffffffu, acc[q][j].h, o);
+                    b.l = __shfl_xor_sync(0xffffffffu, acc[q][j].l, o);
+                    acc[q][j] = f2_add(acc[q][j], b);
+                }
             }
-        }
-        const int row = rb * BG_TR + r;
-        if (g == 0 && row < n) {
+        if (g == 0)
 #pragma unroll
-            for (int j = 0; j < S; j++)
-                if (j < a.s) a.Q[(long long)j * a.ldq + row] = (double)acc[j].h + (double)acc[j].l;
-        }
+            for (int q = 0; q < 2; q++) {
+                const int row = rb * BG_TR + w + 8 * q;
+                if (row < n)
+#pragma unroll
+                    for (int j = 0; j < S; j++)
+                        if (j < a.s) a.Q[(long long)j * a.ldq + row] = (double)acc[q][j].h + (double)acc[q][j].l;
+            }
     }
 }
 
