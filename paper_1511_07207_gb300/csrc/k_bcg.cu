@@ -368,25 +368,51 @@ __global__ void __launch_bounds__(BK) bcg_check_kernel(BcgVecs v, cudaGraphCondi
 constexpr int SL = BCG_MAX_S;              // leading dimension of the small matrices
 constexpr double BCGD_TAU2 = 1e-16;        // (1e-8)^2 on the normalized diagonal
 
-// This CTA's partial U[:, :nu]^T V[:, :nv] over rows [lo, hi) into buf[cta][SL*SL].
+// This CTA's partial U[:, :nu]^T V[:, :nv] over rows [lo, hi) into
+// buf[cta][SL*SL].  Every thread of the CTA takes part: T = BK / (nu nv)
+// threads per entry, thread q of an entry summing rows lo + q, lo + q + T,
+// ...; the T sums added in q order (a fixed order, so the result does not
+// depend on timing).  FP64 latency, not throughput, bounds these sums on
+// this GPU, so the shorter chains are what counts.
 __device__ __forceinline__ void gram_partial_ld(const BcgVecs &v, double *buf, const double *U, int nu,
                                                 const double *V, int nv, long long lo, long long hi) {
-    for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
+    __shared__ double red[BK];
+    const int E = nu * nv;
+    if (E == 0) return;
+    const int T = BK / E;
+    const int e = threadIdx.x / T, q = threadIdx.x - e * T;
+    double acc = 0.0;
+    if (e < E) {
         const int a = e % nu, b = e / nu;
         const double *u = U + (long long)a * v.ld, *w = V + (long long)b * v.ld;
-        double acc = 0.0;
-        for (long long i = lo; i < hi; i++) acc += u[i] * w[i];
-        buf[(size_t)blockIdx.x * SL * SL + a + b * SL] = acc;
+        for (long long i = lo + q; i < hi; i += T) acc += u[i] * w[i];
     }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (e < E && q == 0) {
+        double sum = 0.0;
+        for (int t = 0; t < T; t++) sum += red[threadIdx.x + t];
+        const int a = e % nu, b = e / nu;
+        buf[(size_t)blockIdx.x * SL * SL + a + b * SL] = sum;
+    }
+    __syncthreads();
 }
-// The sum of the CTAs' partials in CTA order (one thread).
+// G = the sum of the CTAs' partials, entry by entry, by all threads of the
+// calling CTA: eight interleaved sums over the CTAs (CTA c into sum c % 8),
+// added pairwise; a fixed order.
 __device__ __forceinline__ void gram_reduce_ld(const double *buf, int nu, int nv, double *G) {
-    for (int b = 0; b < nv; b++)
-        for (int a = 0; a < nu; a++) {
-            double acc = 0.0;
-            for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&buf[(size_t)c * SL * SL + a + b * SL]);
-            G[a + b * SL] = acc;
-        }
+    const int nc = (int)gridDim.x;
+    for (int e = threadIdx.x; e < nu * nv; e += blockDim.x) {
+        const int a = e % nu, b = e / nu;
+        const double *p = buf + a + b * SL;
+        double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int c = 0;
+        for (; c + 8 <= nc; c += 8)
+#pragma unroll
+            for (int u = 0; u < 8; u++) t[u] += __ldcg(p + (size_t)(c + u) * SL * SL);
+        for (int u = 0; c + u < nc; u++) t[u] += __ldcg(p + (size_t)(c + u) * SL * SL);
+        G[a + b * SL] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+    }
 }
 
 // Cholesky of the leading r x r block (lower triangle, leading dimension SL);
@@ -398,39 +424,47 @@ __device__ bool small_chol(int r, double *G) {
         if (!(d > 0.0)) return false;
         d = sqrt(d);
         G[j + j * SL] = d;
+        const double dinv = 1.0 / d;   // one division per column (FP64 division is slow here)
         for (int i = j + 1; i < r; i++) {
             double x = G[i + j * SL];
             for (int k = 0; k < j; k++) x -= G[i + k * SL] * G[j + k * SL];
-            G[i + j * SL] = x / d;
+            G[i + j * SL] = x * dinv;
         }
     }
     return true;
 }
-// Y (r x c) = (L L^T)^-1 Y.
+// Y (r x c) = (L L^T)^-1 Y, column j of Y by thread j of the calling CTA
+// (all threads call it), with the reciprocals of L's diagonal formed once.
 __device__ void small_chol_solve(int r, int c, const double *L, double *Y) {
-    for (int j = 0; j < c; j++) {
+    __shared__ double dinv[SL];
+    if (threadIdx.x < r) dinv[threadIdx.x] = 1.0 / L[threadIdx.x + threadIdx.x * SL];
+    __syncthreads();
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
         double *y = Y + j * SL;
         for (int i = 0; i < r; i++) {
             double x = y[i];
             for (int k = 0; k < i; k++) x -= L[i + k * SL] * y[k];
-            y[i] = x / L[i + i * SL];
+            y[i] = x * dinv[i];
         }
         for (int i = r - 1; i >= 0; i--) {
             double x = y[i];
             for (int k = i + 1; k < r; k++) x -= L[k + i * SL] * y[k];
-            y[i] = x / L[i + i * SL];
+            y[i] = x * dinv[i];
         }
     }
+    __syncthreads();
 }
 // M = L^-T (upper triangular, r x r) for a lower-triangular L.
 __device__ void small_inv_t(int r, const double *L, double *M) {
     for (int b = 0; b < SL; b++)
         for (int a = 0; a < SL; a++) M[a + b * SL] = 0.0;
+    double dinv[SL];
+    for (int a = 0; a < r; a++) dinv[a] = 1.0 / L[a + a * SL];
     for (int b = 0; b < r; b++) {                  // column b of M solves L^T m = e_b
         for (int a = r - 1; a >= 0; a--) {
             double x = a == b ? 1.0 : 0.0;
             for (int k = a + 1; k < r; k++) x -= L[k + a * SL] * M[k + b * SL];
-            M[a + b * SL] = x / L[a + a * SL];
+            M[a + b * SL] = x * dinv[a];
         }
     }
 }
@@ -443,8 +477,10 @@ __device__ int rr_factor(int s, const double *G, double *T, double *work, int *i
     double *d = work + 3 * SL * SL, *rem = d + SL;
     int *perm = iwork, *state = iwork + SL;
 #define Lc(q, t) Lcm[(q) + (t) * SL]
+    double dinv[SL];
     for (int j = 0; j < s; j++) {
         d[j] = sqrt(G[j + j * SL]);
+        dinv[j] = 1.0 / d[j];
         state[j] = d[j] > 0.0 ? 0 : 2;             // 0 open, 1 taken, 2 dropped
         rem[j] = 1.0;
     }
@@ -457,15 +493,15 @@ __device__ int rr_factor(int s, const double *G, double *T, double *work, int *i
             if (p < 0 || rem[j] > rem[p]) p = j;
         }
         if (p < 0) break;
-        const double lpp = sqrt(rem[p]);
+        const double lpp = sqrt(rem[p]), linv = 1.0 / lpp;
         perm[r] = p;
         state[p] = 1;
         Lc(p, r) = lpp;
         for (int q = 0; q < s; q++) {
             if (state[q]) continue;
-            double x = G[q + p * SL] / (d[q] * d[p]);
+            double x = G[q + p * SL] * dinv[q] * dinv[p];
             for (int t = 0; t < r; t++) x -= Lc(q, t) * Lc(p, t);
-            Lc(q, r) = x / lpp;
+            Lc(q, r) = x * linv;
             rem[q] -= Lc(q, r) * Lc(q, r);
         }
         r++;
@@ -477,7 +513,7 @@ __device__ int rr_factor(int s, const double *G, double *T, double *work, int *i
     small_inv_t(r, Lp, M);
     for (int e = 0; e < SL * SL; e++) T[e] = 0.0;
     for (int a = 0; a < r; a++)
-        for (int b = 0; b < r; b++) T[perm[a] + b * SL] = M[a + b * SL] / d[perm[a]];
+        for (int b = 0; b < r; b++) T[perm[a] + b * SL] = M[a + b * SL] * dinv[perm[a]];
 #undef Lc
     return r;
 }
@@ -492,14 +528,17 @@ __device__ bool coop_orth(const BcgVecs &v, const double *W, long long lo, long 
     const int s = v.s;
     gram_partial_ld(v, v.part, W, s, W, s, lo, hi);
     if (!grid_sync(v.bar, v.st)) return false;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0) {
         gram_reduce_ld(v.part, s, s, G);
-        for (int j = 0; j < s; j++) sm->w2[j] = G[j + j * SL];
-        bool nan = false;
-        for (int j = 0; j < s; j++) nan = nan || !isfinite(G[j + j * SL]);
-        const int r = nan ? 0 : rr_factor(s, G, T, work, iwork);
-        for (int e = 0; e < SL * SL; e++) sm->T[e] = T[e];
-        sm->rank = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int j = 0; j < s; j++) sm->w2[j] = G[j + j * SL];
+            bool nan = false;
+            for (int j = 0; j < s; j++) nan = nan || !isfinite(G[j + j * SL]);
+            const int r = nan ? 0 : rr_factor(s, G, T, work, iwork);
+            for (int e = 0; e < SL * SL; e++) sm->T[e] = T[e];
+            sm->rank = r;
+        }
     }
     if (!grid_sync(v.bar, v.st)) return false;
     if (threadIdx.x == 0) r_s = *(volatile int *)&sm->rank;
@@ -521,12 +560,15 @@ __device__ bool coop_orth(const BcgVecs &v, const double *W, long long lo, long 
     __syncthreads();
     gram_partial_ld(v, v.part, v.P, r, v.P, r, lo, hi);                 // second pass
     if (!grid_sync(v.bar, v.st)) return false;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0) {
         gram_reduce_ld(v.part, r, r, G);
-        const bool ok = small_chol(r, G);
-        if (ok) small_inv_t(r, G, T);
-        for (int e = 0; e < SL * SL; e++) sm->T[e] = ok ? T[e] : 0.0;
-        if (!ok) sm->rank = -1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const bool ok = small_chol(r, G);
+            if (ok) small_inv_t(r, G, T);
+            for (int e = 0; e < SL * SL; e++) sm->T[e] = ok ? T[e] : 0.0;
+            if (!ok) sm->rank = -1;
+        }
     }
     if (!grid_sync(v.bar, v.st)) return false;
     for (int e = threadIdx.x; e < SL * SL; e += blockDim.x) T[e] = __ldcg(&sm->T[e]);
@@ -581,10 +623,10 @@ __global__ void __launch_bounds__(BK) bcgd_init_kernel(BcgVecs v, int x0_given, 
     }
     __syncthreads();
     if (!grid_sync(v.bar, st)) return;
-    if (blockIdx.x == 0 && threadIdx.x < v.s) {
-        double acc = 0.0;
-        for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part2[(size_t)c * BCG_MAX_S + threadIdx.x]);
-        sm->bn[threadIdx.x] = sqrt(acc);
+    if (blockIdx.x == 0 && threadIdx.x < v.s) {   // eight interleaved sums over the CTAs
+        double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < (int)gridDim.x; c++) t[c & 7] += __ldcg(&v.part2[(size_t)c * BCG_MAX_S + threadIdx.x]);
+        sm->bn[threadIdx.x] = sqrt(((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7])));
     }
     const bool ok = coop_orth(v, v.R, lo, hi);          // its first barrier publishes bn too
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -629,17 +671,21 @@ __global__ void __launch_bounds__(BK) bcgd_step_kernel(BcgVecs v, cudaGraphCondi
     gram_partial_ld(v, v.part, v.P, r, v.Q, r, lo, hi);
     gram_partial_ld(v, v.partb, v.P, r, v.R, s, lo, hi);
     if (!grid_sync(v.bar, st)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0) {
         gram_reduce_ld(v.part, r, r, G);
         gram_reduce_ld(v.partb, r, s, H);
-        const bool ok = small_chol(r, G);             // positive definite for SPD A
-        if (ok) small_chol_solve(r, s, G, H);          // alpha = gamma^-1 P^T R
-        for (int e = 0; e < SL * SL; e++) {
-            sm->Lg[e] = G[e];
-            sm->alpha[e] = H[e];
+        __syncthreads();
+        if (threadIdx.x == 0) flag_s = small_chol(r, G) ? 1 : 0;   // positive definite for SPD A
+        __syncthreads();
+        if (flag_s) small_chol_solve(r, s, G, H);       // alpha = gamma^-1 P^T R (all threads)
+        if (threadIdx.x == 0) {
+            for (int e = 0; e < SL * SL; e++) {
+                sm->Lg[e] = G[e];
+                sm->alpha[e] = H[e];
+            }
+            sm->ok = flag_s;
+            if (!flag_s) st->status = LS_BREAKDOWN;
         }
-        sm->ok = ok ? 1 : 0;
-        if (!ok) st->status = LS_BREAKDOWN;
     }
     if (!grid_sync(v.bar, st)) return;
     if (threadIdx.x == 0) flag_s = *(volatile int *)&sm->ok;
@@ -678,29 +724,40 @@ __global__ void __launch_bounds__(BK) bcgd_step_kernel(BcgVecs v, cudaGraphCondi
         v.part2[(size_t)blockIdx.x * BCG_MAX_S + j] = acc;
     }
     if (!grid_sync(v.bar, st)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double r2[BCG_MAX_S];
-        bool nan = false;
-        for (int j = 0; j < s; j++) {
-            double acc = 0.0;
-            for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part2[(size_t)c * BCG_MAX_S + j]);
-            r2[j] = acc;
-            nan = nan || !isfinite(acc);
+    if (blockIdx.x == 0) {
+        __shared__ double r2[BCG_MAX_S];
+        __shared__ int nan_s, go_s;
+        // ||R_j||^2: thread j, eight interleaved sums over the CTAs
+        if (threadIdx.x < s) {
+            double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            const int nc = (int)gridDim.x;
+            for (int c = 0; c < nc; c++) t[c & 7] += __ldcg(&v.part2[(size_t)c * BCG_MAX_S + threadIdx.x]);
+            r2[threadIdx.x] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
         }
-        const bool pass = !nan && cols_pass(v, r2);
-        int go = 0;
-        if (!nan && !pass) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            bool nan = false;
+            for (int j = 0; j < s; j++) nan = nan || !isfinite(r2[j]);
+            nan_s = nan;
+            go_s = !nan && !cols_pass(v, r2);
+        }
+        __syncthreads();
+        if (go_s) {
             gram_reduce_ld(v.part, r, s, H);
-            for (int e = 0; e < SL * SL; e++) G[e] = sm->Lg[e];
-            small_chol_solve(r, s, G, H);              // beta = -gamma^-1 Q^T R
-            for (int e = 0; e < SL * SL; e++) sm->beta[e] = -H[e];
-            go = 1;
+            for (int e = threadIdx.x; e < SL * SL; e += blockDim.x) G[e] = sm->Lg[e];
+            __syncthreads();
+            small_chol_solve(r, s, G, H);              // beta = -gamma^-1 Q^T R (all threads)
         }
-        st->iter++;
-        if (nan) set_err(st, ERRB_NAN);
-        sm->update_p = go;
-        if (go && st->iter >= st->max_iter) go = 0;
-        sm->ok = go;
+        if (threadIdx.x == 0) {
+            int go = go_s;
+            if (go)
+                for (int e = 0; e < SL * SL; e++) sm->beta[e] = -H[e];
+            st->iter++;
+            if (nan_s) set_err(st, ERRB_NAN);
+            sm->update_p = go;
+            if (go && st->iter >= st->max_iter) go = 0;
+            sm->ok = go;
+        }
     }
     if (!grid_sync(v.bar, st)) return;
     if (threadIdx.x == 0) flag_s = *(volatile int *)&sm->update_p;
