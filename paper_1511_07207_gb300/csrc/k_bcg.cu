@@ -73,26 +73,38 @@ __device__ void warp_chol_solve(int s, const double *L, double *Y) {
 }
 
 // ---- Gram matrices -------------------------------------------------------------------
-// This CTA's partial U^T V over rows [lo, hi) into part[cta][s*s].
+// This CTA's partial U^T V over rows [lo, hi) into part[cta][s*s]: T =
+// BK / s^2 threads per entry, thread q summing rows lo + q, lo + q + T, ...,
+// the T sums added in q order (all threads of the CTA call it).
 __device__ __forceinline__ void gram_partial(const BcgVecs &v, const double *U, const double *V, long long lo,
                                              long long hi) {
-    const int s = v.s;
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    __shared__ double red[BK];
+    const int s = v.s, E = s * s, T = BK / E;
+    const int e = threadIdx.x / T, q = threadIdx.x - e * T;
+    double acc = 0.0;
+    if (e < E) {
         const int a = e % s, b = e / s;
         const double *u = U + (long long)a * v.ld, *w = V + (long long)b * v.ld;
-        double acc = 0.0;
-        for (long long i = lo; i < hi; i++) acc += u[i] * w[i];
-        v.part[(size_t)blockIdx.x * BCG_MAX_S * BCG_MAX_S + e] = acc;
+        for (long long i = lo + q; i < hi; i += T) acc += u[i] * w[i];
     }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (e < E && q == 0) {
+        double sum = 0.0;
+        for (int t = 0; t < T; t++) sum += red[threadIdx.x + t];
+        v.part[(size_t)blockIdx.x * BCG_MAX_S * BCG_MAX_S + e] = sum;
+    }
+    __syncthreads();
 }
 
-// One warp: G = sum of the partials in CTA order.
+// One warp: G = sum of the partials, entry by entry, as eight interleaved
+// sums over the CTAs added pairwise (a fixed order).
 __device__ __forceinline__ void gram_reduce(const BcgVecs &v, double *G) {
-    const int s = v.s;
+    const int s = v.s, nc = (int)gridDim.x;
     for (int e = threadIdx.x & 31; e < s * s; e += 32) {
-        double acc = 0.0;
-        for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part[(size_t)c * BCG_MAX_S * BCG_MAX_S + e]);
-        G[e] = acc;
+        double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < nc; c++) t[c & 7] += __ldcg(&v.part[(size_t)c * BCG_MAX_S * BCG_MAX_S + e]);
+        G[e] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
     }
     __syncwarp();
 }
