@@ -35,25 +35,58 @@ constexpr int GT = 256;   // threads per CTA
 __device__ __forceinline__ int ldh(const BgmVecs &v) { return (v.m + 1) * v.s; }
 
 // This CTA's partial U^T M (U: ku columns, M: s columns, rows [lo, hi)).
+// When there are fewer entries than threads, T = GT / (ku s) threads share
+// an entry, thread q summing rows lo + q, lo + q + T, ..., their sums added
+// in q order (all threads of the CTA call it; FP64 latency, not throughput,
+// bounds these sums on this GPU).
 __device__ void gram_part(const BgmVecs &v, const double *U, int ku, const double *M, long long lo, long long hi) {
-    const int s = v.s;
-    for (int e = threadIdx.x; e < ku * s; e += blockDim.x) {
+    __shared__ double red[GT];
+    const int s = v.s, E = ku * s;
+    if (E >= GT) {
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            const int a = e % ku, b = e / ku;
+            const double *u = U + (long long)a * v.ld, *w = M + (long long)b * v.ld;
+            double t0 = 0.0, t1 = 0.0;
+            long long i = lo;
+            for (; i + 1 < hi; i += 2) {
+                t0 += u[i] * w[i];
+                t1 += u[i + 1] * w[i + 1];
+            }
+            if (i < hi) t0 += u[i] * w[i];
+            v.part[(size_t)blockIdx.x * v.part_stride + e] = t0 + t1;
+        }
+        return;
+    }
+    const int T = GT / E;
+    const int e = threadIdx.x / T, q = threadIdx.x - e * T;
+    double acc = 0.0;
+    if (e < E) {
         const int a = e % ku, b = e / ku;
         const double *u = U + (long long)a * v.ld, *w = M + (long long)b * v.ld;
-        double acc = 0.0;
-        for (long long i = lo; i < hi; i++) acc += u[i] * w[i];
-        v.part[(size_t)blockIdx.x * v.part_stride + e] = acc;
+        for (long long i = lo + q; i < hi; i += T) acc += u[i] * w[i];
     }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (e < E && q == 0) {
+        double sum = 0.0;
+        for (int t = 0; t < T; t++) sum += red[threadIdx.x + t];
+        v.part[(size_t)blockIdx.x * v.part_stride + e] = sum;
+    }
+    __syncthreads();
 }
 
-// Entries of the reduced Gram matrix spread over the CTAs (CTA order in
-// every sum), into out[0 .. cnt).
+// The sum over the CTAs of entry e of the partial Gram matrices: eight
+// interleaved sums (CTA c into sum c % 8) added pairwise; a fixed order.
+__device__ __forceinline__ double cta_sum(const BgmVecs &v, int e) {
+    double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int nc = (int)gridDim.x;
+    for (int c = 0; c < nc; c++) t[c & 7] += __ldcg(&v.part[(size_t)c * v.part_stride + e]);
+    return ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+}
+
+// Entries of the reduced Gram matrix spread over the CTAs, into out[0 .. cnt).
 __device__ void gram_reduce_spread(const BgmVecs &v, int cnt, double *out) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part[(size_t)c * v.part_stride + e]);
-        out[e] = acc;
-    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) out[e] = cta_sum(v, e);
 }
 
 // One warp: G = L L^T in place (column-major s x s).  False when a pivot is
@@ -91,11 +124,7 @@ __device__ int cholqr_pass(const BgmVecs &v, double *M, long long lo, long long 
     gram_part(v, M, s, M, lo, hi);
     if (!grid_sync(v.bar, v.st)) return -1;
     if (blockIdx.x == 0 && threadIdx.x < 32) {
-        for (int e = threadIdx.x; e < s * s; e += 32) {
-            double acc = 0.0;
-            for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part[(size_t)c * v.part_stride + e]);
-            Gs[e] = acc;
-        }
+        for (int e = threadIdx.x; e < s * s; e += 32) Gs[e] = cta_sum(v, e);
         __syncwarp();
         const bool ok = warp_chol(s, Gs);
         for (int e = threadIdx.x; e < s * s; e += 32) v.Lm[e] = Gs[e];
@@ -164,8 +193,7 @@ __global__ void __launch_bounds__(GT) bgm_init_kernel(BgmVecs v, int x0_given, c
     }
     if (!grid_sync(v.bar, st)) return;
     if (blockIdx.x == 0 && threadIdx.x < s) {
-        double acc = 0.0;
-        for (int c = 0; c < (int)gridDim.x; c++) acc += __ldcg(&v.part[(size_t)c * v.part_stride + threadIdx.x]);
+        const double acc = cta_sum(v, threadIdx.x);
         v.bn[threadIdx.x] = sqrt(acc);
         if (!isfinite(acc)) set_err(st, ERRB_NAN);
     }
