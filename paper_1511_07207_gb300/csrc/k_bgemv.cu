@@ -6,15 +6,17 @@
 // TMA map) and the matching 256-row chunk of P (pre-split into FP32 pairs,
 // column panels padded with zeros to a multiple of 256, one 1-D bulk copy
 // per column and part) through a ring of shared-memory stages (mbarrier
-// full/empty).  Eight consumer warps: warp w owns rows w and w + 8 of the
-// block and lane g the 4-column chunks g and g + 32 of each tile, so every
-// shared-memory load of P serves two rows; a thread accumulates all S
-// columns of P for its two rows in double-single (a tile's partial in a
-// plain pair, added to the running sum with a renormalising two-sum), and
-// the 32 lanes of a row add their sums by shuffles at the end of the row
-// block.  Every row block belongs to one CTA and is summed in column
-// order, so results are deterministic.  Work per element of A is 12 FP32
-// operations per column of P: compute-bound for S >= 4 (HBM-bound below).
+// full/empty).  Consumer warps: for S <= 8 sixteen warps, warp w owning row
+// w of the 16-row block (enough warps to hide the latency of the
+// double-single chains); for S = 16 eight warps of two rows each (w and
+// w + 8: registers); lane g takes the 4-column chunks g and g + 32 of each
+// tile.  A thread accumulates all S columns of P for its rows in
+// double-single (two-sum of the high parts, the low parts and rounding
+// errors summed apart, as the GEMV does), and the 32 lanes of a row add
+// their sums by shuffles at the end of the row block.  Every row block
+// belongs to one CTA and is summed in column order, so results are
+// deterministic.  Work per element of A is 12 FP32 operations per column of
+// P: compute-bound for S >= 4 (HBM-bound below).
 #include <cuda_runtime.h>
 
 #include "ls_device.cuh"
@@ -25,8 +27,6 @@ namespace lsi {
 
 namespace {
 
-constexpr int BG_C = 256;            // consumer threads
-constexpr int BG_T = BG_C + 32;      // plus the producer warp
 constexpr int BG_TR = 16, BG_TC = 256;
 constexpr int BG_A_B = BG_TR * BG_TC * 4;   // one part of an A tile (16 KB)
 
@@ -55,6 +55,22 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
     const float l = __fadd_rn(__fadd_rn(a.l, b.l), err);
     const float h = __fadd_rn(s, l);
     return {h, __fsub_rn(l, __fsub_rn(h, s))};
+}
+
+// Rows of a 16-row block per consumer warp: one for S <= 8 (sixteen warps,
+// to hide the latency of the double-single chains), two for S = 16 (eight
+// warps: registers).  Plus the producer warp.
+template <int S>
+__host__ __device__ constexpr int bg_rows_per_warp() {
+    return S <= 8 ? 1 : 2;
+}
+template <int S>
+__host__ __device__ constexpr int bg_consumers() {
+    return 32 * 16 / bg_rows_per_warp<S>();
+}
+template <int S>
+__host__ __device__ constexpr int bg_threads() {
+    return bg_consumers<S>() + 32;
 }
 
 template <int S>
@@ -87,7 +103,9 @@ __global__ void bgemv_split_kernel(int n, int s, int S, const double *__restrict
 }
 
 template <int S>
-__global__ void __launch_bounds__(BG_T, 1) bgemv_kernel(const MatDesc *__restrict__ dA, BgemvArgs a) {
+__global__ void __launch_bounds__(bg_threads<S>(), 1) bgemv_kernel(const MatDesc *__restrict__ dA, BgemvArgs a) {
+    constexpr int BG_C = bg_consumers<S>();
+    constexpr int RPW = bg_rows_per_warp<S>(), WS = 16 / RPW;   // rows per warp, their stride
     constexpr int NST = stages<S>();
     constexpr size_t SB = stage_bytes<S>();
     extern __shared__ __align__(1024) unsigned char bg_dyn[];
@@ -141,13 +159,14 @@ __global__ void __launch_bounds__(BG_T, 1) bgemv_kernel(const MatDesc *__restric
     }
 
     // ---- consumers ----
-    // warp w: rows w and w + 8 of the block; lane g: 4-column chunks g and g + 32
+    // warp w: rows w, w + WS, ... of the block (RPW of them); lane g: the
+    // 4-column chunks g and g + 32 of each tile
     const int w = threadIdx.x >> 5, g = threadIdx.x & 31;
     int seq = 0;
     for (int rb = blockIdx.x; rb < RB; rb += gridDim.x) {
-        F2 acc[2][S];
+        F2 acc[RPW][S];
 #pragma unroll
-        for (int q = 0; q < 2; q++)
+        for (int q = 0; q < RPW; q++)
 #pragma unroll
             for (int j = 0; j < S; j++) acc[q][j] = {0.f, 0.f};
         for (int t = 0; t < CT; t++) {
@@ -162,44 +181,35 @@ __global__ void __launch_bounds__(BG_T, 1) bgemv_kernel(const MatDesc *__restric
             const float *Al = reinterpret_cast<const float *>(base + BG_A_B);
             const float *Xh = reinterpret_cast<const float *>(base + 2 * BG_A_B);
             const float *Xl = Xh + S * BG_TC;
-            F2 part[2][S];
-#pragma unroll
-            for (int q = 0; q < 2; q++)
-#pragma unroll
-                for (int j = 0; j < S; j++) part[q][j] = {0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 2; k++) {
                 const int c0 = (k * 32 + g) * 4;
-                float4 ah[2], al[2];
+                float4 ah[RPW], al[RPW];
 #pragma unroll
-                for (int q = 0; q < 2; q++) {
-                    ah[q] = *reinterpret_cast<const float4 *>(Ah + (w + 8 * q) * BG_TC + c0);
-                    al[q] = *reinterpret_cast<const float4 *>(Al + (w + 8 * q) * BG_TC + c0);
+                for (int q = 0; q < RPW; q++) {
+                    ah[q] = *reinterpret_cast<const float4 *>(Ah + (w + WS * q) * BG_TC + c0);
+                    al[q] = *reinterpret_cast<const float4 *>(Al + (w + WS * q) * BG_TC + c0);
                 }
 #pragma unroll
                 for (int j = 0; j < S; j++) {
                     const float4 xh = *reinterpret_cast<const float4 *>(Xh + j * BG_TC + c0);
                     const float4 xl = *reinterpret_cast<const float4 *>(Xl + j * BG_TC + c0);
 #pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        f2_mac(part[q][j], ah[q].x, al[q].x, xh.x, xl.x);
-                        f2_mac(part[q][j], ah[q].y, al[q].y, xh.y, xl.y);
-                        f2_mac(part[q][j], ah[q].z, al[q].z, xh.z, xl.z);
-                        f2_mac(part[q][j], ah[q].w, al[q].w, xh.w, xl.w);
+                    for (int q = 0; q < RPW; q++) {
+                        f2_mac(acc[q][j], ah[q].x, al[q].x, xh.x, xl.x);
+                        f2_mac(acc[q][j], ah[q].y, al[q].y, xh.y, xl.y);
+                        f2_mac(acc[q][j], ah[q].z, al[q].z, xh.z, xl.z);
+                        f2_mac(acc[q][j], ah[q].w, al[q].w, xh.w, xl.w);
                     }
                 }
             }
             __syncwarp();
             if (g == 0) mbar_arrive(&empty[sl]);
-#pragma unroll
-            for (int q = 0; q < 2; q++)
-#pragma unroll
-                for (int j = 0; j < S; j++) acc[q][j] = f2_add(acc[q][j], part[q][j]);
             seq++;
         }
         // the 32 lanes of a row
 #pragma unroll
-        for (int q = 0; q < 2; q++)
+        for (int q = 0; q < RPW; q++)
 #pragma unroll
             for (int j = 0; j < S; j++) {
 #pragma unroll
@@ -212,8 +222,8 @@ __global__ void __launch_bounds__(BG_T, 1) bgemv_kernel(const MatDesc *__restric
             }
         if (g == 0)
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
-                const int row = rb * BG_TR + w + 8 * q;
+            for (int q = 0; q < RPW; q++) {
+                const int row = rb * BG_TR + w + WS * q;
                 if (row < n)
 #pragma unroll
                     for (int j = 0; j < S; j++)
@@ -232,9 +242,9 @@ void *bg_func() {
 BgemvLaunch bgemv_plan(int s, int num_sms) {
     BgemvLaunch L{};
     L.split = reinterpret_cast<void *>(&bgemv_split_kernel);
-    L.block = BG_T;
     L.grid = num_sms;
     L.S = s <= 1 ? 1 : s <= 2 ? 2 : s <= 4 ? 4 : s <= 8 ? 8 : 16;
+    L.block = L.S <= 8 ? bg_threads<8>() : bg_threads<16>();
     switch (L.S) {
         case 1: L.func = bg_func<1>(); L.smem = stages<1>() * stage_bytes<1>() + 1024; break;
         case 2: L.func = bg_func<2>(); L.smem = stages<2>() * stage_bytes<2>() + 1024; break;
