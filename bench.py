@@ -481,13 +481,20 @@ def run_native(args):
         hx1 = torch.zeros(N, dtype=torch.float64).pin_memory()
         hx2 = torch.zeros(N, dtype=torch.float64).pin_memory()
 
+        walls = []
+
         def step_e2e():
-            s1, _ = B.ls_cg_solve(ctx, hA1, hb1, hx1, o_cg)
-            s2, _ = B.ls_gmres_solve(ctx, hA2, hb2, hx2, o_gm)
+            t = time.perf_counter()
+            s1, i1 = B.ls_cg_solve(ctx, hA1, hb1, hx1, o_cg)
+            t1 = time.perf_counter()
+            s2, i2 = B.ls_gmres_solve(ctx, hA2, hb2, hx2, o_gm)
+            t2 = time.perf_counter()
             assert s1 == B.LS_OK and s2 == B.LS_OK
+            walls.append((t1 - t, t2 - t1, i1["time_ms"], i2["time_ms"]))
 
         step_e2e()
         barrier()
+        walls.clear()
         t0 = time.perf_counter()
         k_e2e = max(1, min(args.steps, 3))
         for _ in range(k_e2e):
@@ -497,7 +504,12 @@ def run_native(args):
         te_max = max_over_ranks(te, world, dev)
         e2e = {"value": round(whole_job_rate(2 * k_e2e, world, te_max * 1e3), 4), "unit": "solves/s",
                "h2d_bytes_per_step": int(2 * (8 * N * N + 8 * N)),
-               "d2h_bytes_per_step": int(2 * 8 * N)}
+               "d2h_bytes_per_step": int(2 * 8 * N),
+               "per_solve_ms": {"cg_wall": round(statistics.median(w[0] for w in walls) * 1e3, 2),
+                                "gmres_wall": round(statistics.median(w[1] for w in walls) * 1e3, 2),
+                                "cg_device": round(statistics.median(w[2] for w in walls), 2),
+                                "gmres_device": round(statistics.median(w[3] for w in walls), 2)},
+               "note": "each call copies its A (2 GiB) from pinned host memory, solves, and copies x back"}
 
     # mixed vs FP64: n = 32768 SPD system (cond ~ 4e3), time to 1e-10 and GEMV GB/s
     mixed = None
