@@ -395,8 +395,9 @@ def run_native(args):
                     "A_passes": round(i5["bytes_moved"] / (8.0 * N * N), 1),
                     "hbm_frac_whole_solve": round(i5["bytes_moved"] / i5["time_ms"] / 1e6 / peaks_hbm, 4)}
     del x5
-    # block CG (O'Leary) with 8 right-hand sides on the SPD system: one block
-    # product Q = A P per step reads A once for all columns
+    # block CG (the deflating form, the default) with 8 right-hand sides on
+    # the SPD system: one block product Q = A P per step reads A once for all
+    # columns
     S_BCG = 8
     from paper_1511_07207_gb300 import inputs as _inputs
     Xs8 = torch.from_numpy(_inputs.solution(N, seed=2, nrhs=S_BCG).T.copy()).to(dev)   # rows = columns of X*
