@@ -650,7 +650,8 @@ __device__ __forceinline__ double dot4(const double *u, int su, const double *w,
 
 // Shared memory (dynamic): Vr [(m + 1) Rp] (this CTA's rows of the basis,
 // column j at Vr + j Rp), xr, br, wr, ex0, ex1 [Rp each], h1, h2, hs, g, hc
-// [m + 2 each], cs, sn, ys, rinv [m + 1 each], psm [FUSED_PART_SLOTS], then
+// [m + 2 each], cs, sn, ys, rinv [m + 1 each], q4 [4 max(m + 2, Rp)],
+// psm [FUSED_PART_SLOTS], then
 // (when h_smem) the rotated Hessenberg matrix Hs [(m + 1) m], then Ah, Al
 // [R nc each], vh, vl [nc each] and qh, ql [Rp each].  Every CTA keeps its
 // own copy of the rotated Hessenberg matrix (in shared memory, or at
@@ -669,7 +670,9 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
     double *xr = Vr + (size_t)(m + 1) * Rp, *br = xr + Rp, *wr = br + Rp, *ex0 = wr + Rp, *ex1 = ex0 + Rp;
     double *h1 = ex1 + Rp, *h2 = h1 + (m + 2), *hs = h2 + (m + 2), *g = hs + (m + 2), *hc = g + (m + 2);
     double *cs = hc + (m + 2), *sn = cs + (m + 1), *ys = sn + (m + 1), *rinv = ys + (m + 1);
-    double *psm = rinv + (m + 1);
+    const int QS = max(m + 2, Rp);
+    double *q4 = rinv + (m + 1);   // [4][QS] quarter sums
+    double *psm = q4 + 4 * QS;
     double *Hs = psm + FUSED_PART_SLOTS;
     double *H = a.h_smem ? Hs : a.H + (size_t)blockIdx.x * (m + 1) * m;
     float *Ah = align16(a.h_smem ? Hs + (size_t)(m + 1) * m : Hs);
@@ -683,6 +686,48 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
         __syncthreads();
         for (int i = threadIdx.x; i < rows; i += FT) wr[i] = (double)qh[i] + (double)ql[i];
         __syncthreads();
+    };
+    // An FP64 instruction occupies its scheduler's FP64 unit for 64 cycles
+    // here whatever its lanes, so the sums over the rows and over the basis
+    // run on four warps (warp w on scheduler w % 4), a quarter each, the
+    // quarters added in order.
+    // Slot base + t = (column t of V, or w itself for t = ne - 1) . w over this CTA's rows.
+    auto dots_put = [&](int ne, int base) {
+        for (int e = threadIdx.x; e < 128 * ((ne + 31) / 32); e += FT) {
+            const int q = (e >> 5) & 3, t = ((e >> 7) << 5) + (e & 31);
+            if (t < ne) {
+                const double *u = t < ne - 1 ? Vr + (size_t)t * Rp : wr;
+                double s0 = 0.0, s1 = 0.0;
+                int i = q;
+                for (; i + 4 < rows; i += 8) {
+                    s0 += u[i] * wr[i];
+                    s1 += u[i + 4] * wr[i + 4];
+                }
+                if (i < rows) s0 += u[i] * wr[i];
+                q4[q * QS + t] = s0 + s1;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne; t += FT)
+            C.put(base + t, (q4[t] + q4[QS + t]) + (q4[2 * QS + t] + q4[3 * QS + t]));
+    };
+    // w_i -= sum_{t < nt} h_t V_ti over this CTA's rows, published: the terms
+    // t = q mod 4 on warp q, the four sums added in order.
+    auto w_update = [&](const double *h, int nt) {
+        for (int e = threadIdx.x; e < 128 * ((rows + 31) / 32); e += FT) {
+            const int q = (e >> 5) & 3, i = ((e >> 7) << 5) + (e & 31);
+            if (i < rows) {
+                double sum = 0.0;
+                for (int t = q; t < nt; t += 4) sum += h[t] * Vr[(size_t)t * Rp + i];
+                q4[q * QS + i] = sum;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < rows; i += FT) {
+            const double wi = wr[i] - ((q4[i] + q4[QS + i]) + (q4[2 * QS + i] + q4[3 * QS + i]));
+            wr[i] = wi;
+            C.put_row(EX_V, i, wi);
+        }
     };
     // (vh, vl) = split of rv * inv (the whole vector); the CTA's rows of it into V column col
     auto scaled_basis = [&](const double (&rv)[FUSED_VEC_REGS], double inv, int col) {
@@ -780,23 +825,17 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
 
         for (int j = 0;; j++) {   // Arnoldi steps; v_j is in vh, vl
             product();
-            // first pass: V_j^T w and ||w||^2 over this CTA's rows (thread t: column t)
-            for (int t = threadIdx.x; t <= j + 1; t += FT)
-                C.put(gs1(t), t <= j ? dot4(Vr + (size_t)t * Rp, 1, wr, 1, rows) : dot4(wr, 1, wr, 1, rows));
+            // first pass: V_j^T w and ||w||^2 over this CTA's rows
+            dots_put(j + 2, gs1(0));
             if (!C.meet()) return;
             fsum_slots(C, gs1(0), j + 2, h1);
             __syncthreads();
             // w -= V_j h, published (its readers of the last step have passed
             // the meeting above); the second-pass dots and ||w||^2 published
             // with it
-            for (int i = threadIdx.x; i < rows; i += FT) {
-                const double wi = wr[i] - dot4(h1, 1, Vr + i, Rp, j + 1);
-                wr[i] = wi;
-                C.put_row(EX_V, i, wi);
-            }
+            w_update(h1, j + 1);
             __syncthreads();
-            for (int t = threadIdx.x; t <= j + 1; t += FT)
-                C.put(gs2(m, t), t <= j ? dot4(Vr + (size_t)t * Rp, 1, wr, 1, rows) : dot4(wr, 1, wr, 1, rows));
+            dots_put(j + 2, gs2(m, 0));
             if (!C.meet()) return;
             // w in flight while the sums are formed.  When the second pass
             // runs, a CTA that has taken its decision may overwrite its rows
@@ -810,14 +849,11 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
             if (threadIdx.x == 0) ctl.pass2 = a.reorth || h2[j + 1] < 0.49 * h1[j + 1];
             __syncthreads();
             if (ctl.pass2) {
+                w_update(h2, j + 1);
+                __syncthreads();
                 if (warp == 0) {
                     double s = 0.0;
-                    for (int i = lane; i < rows; i += 32) {
-                        const double wi = wr[i] - dot4(h2, 1, Vr + i, Rp, j + 1);
-                        wr[i] = wi;
-                        C.put_row(EX_V, i, wi);
-                        s += wi * wi;
-                    }
+                    for (int i = lane; i < rows; i += 32) s += wr[i] * wr[i];
                     s = lane_sum(s, R);
                     if (lane == 0) C.put(gs3(m), s);
                 }

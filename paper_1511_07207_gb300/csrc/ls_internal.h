@@ -403,7 +403,8 @@ FusedKernels fused_kernels();
 // restart length m and the Hessenberg matrix's place for GMRES).
 inline size_t fused_smem_bytes(bool gmres, int R, int nc, int m, bool h_smem) {
     const size_t Rp = (size_t)((R + 1) & ~1), M = (size_t)m;
-    const size_t dbl = gmres ? (M + 1) * Rp + 5 * Rp + 5 * (M + 2) + 4 * (M + 1) + FUSED_PART_SLOTS +
+    const size_t dbl = gmres ? (M + 1) * Rp + 5 * Rp + 5 * (M + 2) + 4 * (M + 1) +
+                                   4 * (M + 2 > Rp ? M + 2 : Rp) + FUSED_PART_SLOTS +
                                    (h_smem ? (M + 1) * M : 0)
                              : (size_t)nc + 6 * Rp + FUSED_CG_SLOTS;
     return dbl * 8 + 16 + (2 * (size_t)R * nc + 2 * (size_t)nc + 2 * Rp) * 4;
