@@ -384,8 +384,9 @@ constexpr double BCGD_TAU2 = 1e-16;        // (1e-8)^2 on the normalized diagona
 // buf[cta][SL*SL].  Every thread of the CTA takes part: T = BK / (nu nv)
 // threads per entry, thread q of an entry summing rows lo + q, lo + q + T,
 // ...; the T sums added in q order (a fixed order, so the result does not
-// depend on timing).  FP64 latency, not throughput, bounds these sums on
-// this GPU, so the shorter chains are what counts.
+// depend on timing).  A warp's FP64 instruction takes about 64 cycles of
+// its scheduler's FP64 unit on this GPU, so shorter chains spread over all
+// warps (and all four schedulers) are what counts.
 __device__ __forceinline__ void gram_partial_ld(const BcgVecs &v, double *buf, const double *U, int nu,
                                                 const double *V, int nv, long long lo, long long hi) {
     __shared__ double red[BK];

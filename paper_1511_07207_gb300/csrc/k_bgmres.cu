@@ -37,8 +37,9 @@ __device__ __forceinline__ int ldh(const BgmVecs &v) { return (v.m + 1) * v.s; }
 // This CTA's partial U^T M (U: ku columns, M: s columns, rows [lo, hi)).
 // When there are fewer entries than threads, T = GT / (ku s) threads share
 // an entry, thread q summing rows lo + q, lo + q + T, ..., their sums added
-// in q order (all threads of the CTA call it; FP64 latency, not throughput,
-// bounds these sums on this GPU).
+// in q order (all threads of the CTA call it; a warp's FP64 instruction
+// takes about 64 cycles of its scheduler's FP64 unit on this GPU, so the
+// work is spread over all warps).
 __device__ void gram_part(const BgmVecs &v, const double *U, int ku, const double *M, long long lo, long long hi) {
     __shared__ double red[GT];
     const int s = v.s, E = ku * s;

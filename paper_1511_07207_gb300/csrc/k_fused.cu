@@ -166,8 +166,8 @@ struct FComm<true> {
 // 0), then lane 0's total broadcast, so every lane returns the same bits
 // (the callers branch on it, and a branch that splits the warp around a
 // full-warp shuffle would never finish).  Only as many levels as the data
-// needs: on this GPU each dependent FP64 addition costs on the order of a
-// hundred cycles.  Every lane of the warp must call it.
+// needs: on this GPU a warp's FP64 addition takes about 64 cycles.  Every
+// lane of the warp must call it.
 __device__ __forceinline__ double lane_sum(double s, int width) {
     int o = 1;
     while (o < width && o < 32) o <<= 1;
@@ -687,10 +687,10 @@ __global__ void __launch_bounds__(FT, 1) gm_fused_kernel(FusedArgs a) {
         for (int i = threadIdx.x; i < rows; i += FT) wr[i] = (double)qh[i] + (double)ql[i];
         __syncthreads();
     };
-    // An FP64 instruction occupies its scheduler's FP64 unit for 64 cycles
-    // here whatever its lanes, so the sums over the rows and over the basis
-    // run on four warps (warp w on scheduler w % 4), a quarter each, the
-    // quarters added in order.
+    // A warp's FP64 instruction occupies its scheduler's FP64 unit for about
+    // 64 cycles here, dependent or not, so the sums over the rows and over
+    // the basis run on four warps (warp w on scheduler w % 4), a quarter
+    // each, the quarters added in order.
     // Slot base + t = (column t of V, or w itself for t = ne - 1) . w over this CTA's rows.
     auto dots_put = [&](int ne, int base) {
         for (int e = threadIdx.x; e < 128 * ((ne + 31) / 32); e += FT) {
