@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "ls_device.cuh"
+#include "ls_ds.cuh"
 #include "ls_engine.h"
 #include "ls_internal.h"
 #include "ls_tc.cuh"
@@ -412,38 +413,45 @@ __device__ bool prod_epilogue(const EngineDev &E, const ProdSmem &M, const Task 
     // partial dots over this row block: CG p.q; GMRES v_i.w for i <= it
     // (the new direction's rows may come from another task: read through L2).
     // Per dot: a shuffle tree over the warp's row groups, then the 8 warps'
-    // sums in warp order; the two halves of Red alternate between dots.
-    double *Red = M.red();
+    // sums in warp order; the two halves of Red alternate between dots.  The
+    // sums run in double-single arithmetic (each product of two FP32 values
+    // exact, about 48 bits kept) on the FP32 pipe: a warp's FP64 instruction
+    // takes about 64 cycles of its scheduler's FP64 unit on this GPU, and a
+    // GMRES epilogue forms up to m dots of RPT x 4 products per thread.
+    float2 *Red = reinterpret_cast<float2 *>(M.red());
     const int nd = ph == PH_CG ? 1 : it + 1;
     const int lane = tid & 31, warp = tid >> 5;
     for (int i = 0; i < nd; i++) {
         const float *vi = ph == PH_CG ? dst : D.V + (long long)i * nsp;
-        double pc[4] = {0.0, 0.0, 0.0, 0.0};
+        DSV pc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
         for (int r = 0; r < RPT; r++) {
             const int row = rg + NRG * r;
             if (row < nrow) {
                 const float4 v = __ldcg(reinterpret_cast<const float4 *>(vi + (long long)(r0 + row) * SP + cg * 4));
-                pc[0] += (double)v.x * acc[r][0];
-                pc[1] += (double)v.y * acc[r][1];
-                pc[2] += (double)v.z * acc[r][2];
-                pc[3] += (double)v.w * acc[r][3];
+                ds_fma(v.x, 0.0f, DSV{acc[r][0], 0.0f}, pc[0]);
+                ds_fma(v.y, 0.0f, DSV{acc[r][1], 0.0f}, pc[1]);
+                ds_fma(v.z, 0.0f, DSV{acc[r][2], 0.0f}, pc[2]);
+                ds_fma(v.w, 0.0f, DSV{acc[r][3], 0.0f}, pc[3]);
             }
         }
 #pragma unroll
         for (int o = NCG; o < 32; o <<= 1)
 #pragma unroll
-            for (int c = 0; c < 4; c++) pc[c] += __shfl_xor_sync(0xffffffffu, pc[c], o);
-        double *Rb = Red + (i & 1) * (PC_W * 32);
+            for (int c = 0; c < 4; c++) pc[c] += shfl_xor_v(pc[c], o);
+        float2 *Rb = Red + (i & 1) * (PC_W * 32);
         if (lane < NCG)
 #pragma unroll
-            for (int c = 0; c < 4; c++) Rb[warp * 32 + lane * 4 + c] = pc[c];
+            for (int c = 0; c < 4; c++) Rb[warp * 32 + lane * 4 + c] = make_float2(pc[c].h, pc[c].l);
         named_bar(1, P32_T);
         if (tid < 32) {
-            double sacc = 0.0;
+            DSV sacc{0.f, 0.f};
             if (tid < SP)
-                for (int w = 0; w < PC_W; w++) sacc += Rb[w * 32 + tid];
-            E.part32[((size_t)T.rb * E_PS + i) * 32 + tid] = sacc;
+                for (int w = 0; w < PC_W; w++) {
+                    const float2 t = Rb[w * 32 + tid];
+                    sacc += DSV{t.x, t.y};
+                }
+            E.part32[((size_t)T.rb * E_PS + i) * 32 + tid] = to_double(sacc);
         }
     }
     named_bar(1, P32_T);        // Red free for the next task
@@ -1301,7 +1309,8 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
         const long long e0 = (long long)T.r0 * sp, e1 = (long long)T.r1 * sp;
         const int c = tid % sp;                                        // fixed for this thread
         const bool live = c < s;
-        double part = 0.0;
+        double part = 0.0;    // PH_START (FP64 b)
+        DSV pds{0.0f, 0.0f};  // the other phases: squares of FP32 values, double-single
         if (ph == PH_START) {
             for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
                 double b[VU];
@@ -1324,7 +1333,7 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
             }
         } else if (ph == PH_INIT) {
             const bool on = live && !S.conv[c];
-            const double rn = colv_s[c];
+            const double rinv = on ? 1.0 / colv_s[c] : 0.0;   // one division per thread
             const bool gm = D.method != LS_METHOD_CG;
             for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
                 double r[VU];
@@ -1337,11 +1346,11 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                 for (int u = 0; u < VU; u++) {
                     const long long e = eb + (long long)u * VEC_T;
                     if (e < e1) {
-                        const float f = on ? (float)(r[u] / rn) : 0.0f;
+                        const float f = on ? (float)(r[u] * rinv) : 0.0f;
                         D.Rf[e] = f;
                         D.Z[e] = 0.0f;
                         if (gm) D.W[e] = f;                             // W buffer 0
-                        part += (double)f * (double)f;
+                        ds_fma(f, 0.0f, DSV{f, 0.0f}, pds);
                     }
                 }
             }
@@ -1366,35 +1375,36 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                         D.Z[e] = fmaf(al, pv[u], z[u]);
                         const float rv = fmaf(-al, q[u], r[u]);
                         D.Rf[e] = rv;
-                        part += (double)rv * (double)rv;
+                        ds_fma(rv, 0.0f, DSV{rv, 0.0f}, pds);
                     }
                 }
             }
         } else if (ph == PH_GM) {
             float *w = D.W + ((it + 1) & 1) * nsp;
             for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
-                double wv[VU];
+                DSV wv[VU];   // w - sum_q h_q v_q in double-single (about 48 bits)
 #pragma unroll
                 for (int u = 0; u < VU; u++) {
                     const long long e = eb + (long long)u * VEC_T;
-                    wv[u] = e < e1 ? (double)__ldcg(w + e) : 0.0;
+                    wv[u] = DSV{e < e1 ? __ldcg(w + e) : 0.0f, 0.0f};
                 }
                 for (int q = 0; q <= it; q++) {
                     const float *vq = D.V + (long long)q * nsp;
-                    const double hq = hsm[q][c];
+                    float hh, hl;
+                    split_pair(-hsm[q][c], hh, hl);
 #pragma unroll
                     for (int u = 0; u < VU; u++) {
                         const long long e = eb + (long long)u * VEC_T;
-                        if (e < e1) wv[u] -= hq * (double)__ldcg(vq + e);
+                        if (e < e1) ds_fma(hh, hl, DSV{__ldcg(vq + e), 0.0f}, wv[u]);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < VU; u++) {
                     const long long e = eb + (long long)u * VEC_T;
                     if (e < e1) {
-                        const float wf = (float)wv[u];
+                        const float wf = __fadd_rn(wv[u].h, wv[u].l);
                         w[e] = wf;
-                        part += (double)wf * (double)wf;
+                        ds_fma(wf, 0.0f, DSV{wf, 0.0f}, pds);
                     }
                 }
             }
@@ -1404,32 +1414,35 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
                 const bool cgm = D.method == LS_METHOD_CG;
                 const int kj = cgm ? 0 : (int)S.alpha[c];
                 for (long long eb = e0 + tid; eb < e1; eb += VU * VEC_T) {
-                    double d[VU], x[VU];
+                    double x[VU];
+                    DSV d[VU];   // the correction direction in double-single
 #pragma unroll
                     for (int u = 0; u < VU; u++) {
                         const long long e = eb + (long long)u * VEC_T;
                         const bool in = e < e1;
                         x[u] = in ? D.X[e] : 0.0;
-                        d[u] = (in && cgm) ? (double)D.Z[e] : 0.0;
+                        d[u] = DSV{(in && cgm) ? D.Z[e] : 0.0f, 0.0f};
                     }
                     for (int q = 0; q < kj; q++) {
                         const float *vq = D.V + (long long)q * nsp;
-                        const double yq = S.yv[c][q];
+                        float yh, yl;
+                        split_pair(S.yv[c][q], yh, yl);
 #pragma unroll
                         for (int u = 0; u < VU; u++) {
                             const long long e = eb + (long long)u * VEC_T;
-                            if (e < e1) d[u] += yq * (double)vq[e];
+                            if (e < e1) ds_fma(yh, yl, DSV{vq[e], 0.0f}, d[u]);
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < VU; u++) {
                         const long long e = eb + (long long)u * VEC_T;
                         if (e < e1) {
-                            const double xn = x[u] + rn * d[u];
-                            const float xh = __double2float_rn(xn);
+                            const double xn = x[u] + rn * to_double(d[u]);
+                            float xh, xl;
+                            split_pair(xn, xh, xl);
                             D.X[e] = xn;
                             D.Xh[e] = xh;
-                            D.Xl[e] = __double2float_rn(xn - (double)xh);
+                            D.Xl[e] = xl;
                         }
                     }
                 }
@@ -1437,7 +1450,7 @@ __global__ void __launch_bounds__(VEC_T) eng_vec_kernel(const EngineDev *Ep) {
         }
         // partial column sums over this task's rows (fixed order)
         if (ph != PH_UPDATE) {
-            psum[tid] = part;
+            psum[tid] = part + to_double(pds);
             __syncthreads();
             if (tid < 32) {
                 double sacc = 0.0;
