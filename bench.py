@@ -482,6 +482,15 @@ def run_native(args):
         hx1 = torch.zeros(N, dtype=torch.float64).pin_memory()
         hx2 = torch.zeros(N, dtype=torch.float64).pin_memory()
 
+        # the host link's rate in this run: one plain copy of the same pinned buffer
+        probe_dst = torch.empty((N, N), dtype=torch.float64, device=dev)
+        probe_dst.copy_(hA1, non_blocking=True)
+        barrier()
+        tp = time.perf_counter()
+        probe_dst.copy_(hA1, non_blocking=True)
+        barrier()
+        h2d_gbs = 8.0 * N * N / (time.perf_counter() - tp) / 1e9
+        del probe_dst
         walls = []
 
         def step_e2e():
@@ -510,7 +519,9 @@ def run_native(args):
                                 "gmres_wall": round(statistics.median(w[1] for w in walls) * 1e3, 2),
                                 "cg_device": round(statistics.median(w[2] for w in walls), 2),
                                 "gmres_device": round(statistics.median(w[3] for w in walls), 2)},
-               "note": "each call copies its A (2 GiB) from pinned host memory, solves, and copies x back"}
+               "h2d_GBs_plain_copy": round(h2d_gbs, 1),
+               "note": ("each call copies its A (2 GiB) from pinned host memory, solves, and copies x "
+                        "back; h2d_GBs_plain_copy is one plain copy of the same buffer in this run")}
 
     # mixed vs FP64: n = 32768 SPD system (cond ~ 4e3), time to 1e-10 and GEMV GB/s
     mixed = None
