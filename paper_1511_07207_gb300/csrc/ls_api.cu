@@ -206,8 +206,11 @@ int stage_matrix(ls_ctx *c, int n, const double *A, long long lda, double *stage
         *outlda = lda;
         return LS_OK;
     }
-    cudaError_t e = cudaMemcpy2DAsync(stage, lda_stage * sizeof(double), A, lda * sizeof(double),
-                                      n * sizeof(double), n, cudaMemcpyHostToDevice, c->stream);
+    // a contiguous A (lda equal to the staging pitch) as one plain copy
+    cudaError_t e = lda == lda_stage
+                        ? cudaMemcpyAsync(stage, A, (size_t)n * lda * sizeof(double), cudaMemcpyHostToDevice, c->stream)
+                        : cudaMemcpy2DAsync(stage, lda_stage * sizeof(double), A, lda * sizeof(double),
+                                            n * sizeof(double), n, cudaMemcpyHostToDevice, c->stream);
     *outA = stage;
     *outlda = lda_stage;
     return map_cuda(e);
