@@ -163,10 +163,13 @@ __global__ void __launch_bounds__(bg_threads<S>(), 1) bgemv_kernel(const MatDesc
     // 4-column chunks g and g + 32 of each tile
     const int w = threadIdx.x >> 5, g = threadIdx.x & 31;
     int seq = 0;
+    // one row per warp (S <= 8): the two column chunks accumulate apart (two
+    // independent chains per column of P), added at the end of the row block
+    constexpr int NA = RPW == 1 ? 2 : 1;
     for (int rb = blockIdx.x; rb < RB; rb += gridDim.x) {
-        F2 acc[RPW][S];
+        F2 acc[RPW * NA][S];
 #pragma unroll
-        for (int q = 0; q < RPW; q++)
+        for (int q = 0; q < RPW * NA; q++)
 #pragma unroll
             for (int j = 0; j < S; j++) acc[q][j] = {0.f, 0.f};
         for (int t = 0; t < CT; t++) {
@@ -196,10 +199,11 @@ __global__ void __launch_bounds__(bg_threads<S>(), 1) bgemv_kernel(const MatDesc
                     const float4 xl = *reinterpret_cast<const float4 *>(Xl + j * BG_TC + c0);
 #pragma unroll
                     for (int q = 0; q < RPW; q++) {
-                        f2_mac(acc[q][j], ah[q].x, al[q].x, xh.x, xl.x);
-                        f2_mac(acc[q][j], ah[q].y, al[q].y, xh.y, xl.y);
-                        f2_mac(acc[q][j], ah[q].z, al[q].z, xh.z, xl.z);
-                        f2_mac(acc[q][j], ah[q].w, al[q].w, xh.w, xl.w);
+                        F2 &a2 = acc[NA == 2 ? k : q][j];
+                        f2_mac(a2, ah[q].x, al[q].x, xh.x, xl.x);
+                        f2_mac(a2, ah[q].y, al[q].y, xh.y, xl.y);
+                        f2_mac(a2, ah[q].z, al[q].z, xh.z, xl.z);
+                        f2_mac(a2, ah[q].w, al[q].w, xh.w, xl.w);
                     }
                 }
             }
@@ -207,6 +211,9 @@ __global__ void __launch_bounds__(bg_threads<S>(), 1) bgemv_kernel(const MatDesc
             if (g == 0) mbar_arrive(&empty[sl]);
             seq++;
         }
+        if constexpr (NA == 2)
+#pragma unroll
+            for (int j = 0; j < S; j++) acc[0][j] = f2_add(acc[0][j], acc[1][j]);
         // the 32 lanes of a row
 #pragma unroll
         for (int q = 0; q < RPW; q++)
