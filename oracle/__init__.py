@@ -80,7 +80,9 @@ class Oracle:
         lib.or_gauss_seidel.argtypes = [i, P, l, P, P, d, i, i, i, P, P, P]
         lib.or_block_cg.argtypes = [i, i, P, l, P, P, d, i, i, i, P, P]
         lib.or_block_cg_deflated.argtypes = [i, i, P, l, P, P, d, i, i, i, P, P, P]
-        lib.or_block_gmres.argtypes = [i, i, P, l, P, P, i, d, i, i, i, P, P, P]
+        lib.or_block_gmres.argtypes = [i, i, P, l, P, P, i, d, i, i, i, i, P, P, P]
+        lib.or_block_gmres_replacement.argtypes = [i, i, P]
+        lib.or_block_gmres_replacement.restype = None
         lib.or_ge_solve.argtypes = [i, P, l, P, P]
         lib.or_ge_factor.argtypes = [i, P, l, P, P, P, P]
         lib.or_chol_factor.argtypes = [i, P, l, P]
@@ -178,8 +180,10 @@ class Oracle:
                                            nthreads, ctypes.byref(it), ctypes.byref(rr), ctypes.byref(rk))
         return dict(X=np.ascontiguousarray(X), status=st, iters=it.value, rel_res=rr.value, rank=rk.value)
 
-    def block_gmres(self, A, B, m=10, rtol=1e-10, max_iter=None, X0=None, nthreads=1):
-        """Restarted block GMRES(m) on A X = B.  Returns dict(X, status, iters, cycles, rel_res)."""
+    def block_gmres(self, A, B, m=10, rtol=1e-10, max_iter=None, X0=None, deflate=1, nthreads=1):
+        """Restarted block GMRES(m) on A X = B; deflate = 1 replaces the dependent
+        columns of a cycle's starting block (0: they are a breakdown).
+        Returns dict(X, status, iters, cycles, rel_res)."""
         A = _mat(A)
         n = A.shape[0]
         B = np.asarray(B, dtype=np.float64).reshape(n, -1)
@@ -189,8 +193,15 @@ class Oracle:
         X = np.zeros((n, s), order="F") if X0 is None else np.asfortranarray(np.array(X0, dtype=np.float64).reshape(n, s))
         it, cy, rr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
         st = self.lib.or_block_gmres(n, s, _p(A), n, _p(Bc), _p(X), m, rtol, max_iter, int(X0 is not None),
-                                     nthreads, ctypes.byref(it), ctypes.byref(cy), ctypes.byref(rr))
+                                     int(deflate), nthreads, ctypes.byref(it), ctypes.byref(cy), ctypes.byref(rr))
         return dict(X=np.ascontiguousarray(X), status=st, iters=it.value, cycles=cy.value, rel_res=rr.value)
+
+    def block_gmres_replacement(self, n, c):
+        """The vector that replaces dependent column c of a block GMRES
+        starting block (n entries)."""
+        z = np.zeros(max(n, 1))
+        self.lib.or_block_gmres_replacement(n, c, _p(z))
+        return z[:n]
 
     def _stationary(self, fn, A, b, rtol, max_iter, x0, nthreads, history):
         A = _mat(A)

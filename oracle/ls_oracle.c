@@ -863,10 +863,78 @@ done:
  * that basis vector is zero); then R Y = G (the leading k x k triangle, back
  * substitution) and X += V Y.  The iteration stops when the true residual
  * of every column passes.  iters counts block steps, cycles the restarts.
- * A rank-deficient starting block or a zero rotation pivot is a breakdown.
+ *
+ * The starting block of a cycle may be rank-deficient (a zero column, two
+ * equal columns, a column that combines others).  Column c is dependent
+ * when its part orthogonal to the columns kept before it has a norm of at
+ * most 1e-6 of its own (the first Gram-Schmidt pass over R is then a
+ * rank-revealing QR that keeps the columns in order).  With deflate = 0
+ * that is a breakdown.  With deflate = 1 each dependent column c is
+ * replaced by the vector z_c (z_c[i] = 2 u - 1, u = the top 53 bits of
+ * output k = c 2^32 + i of SplitMix64 seeded with 0, over 2^53; see
+ * splitmix64_out), the block with the replacements is orthonormalised
+ * into V_1 as above, and S = V_1^T R, so that R = V_1 S holds for every
+ * column up to the dependent columns' remainders (at most 1e-6 of them).
+ * The block Krylov space then grows from the kept directions and the
+ * replacements, and the block width stays s.  A zero rotation pivot is a
+ * breakdown.
  */
+
+/* Output k (counted from 0) of SplitMix64 seeded with 0 (Steele, Lea and
+ * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+ * the state after k + 1 steps of the Weyl sequence, then the mixing
+ * function. */
+static uint64_t splitmix64_out(uint64_t k) {
+    uint64_t x = (k + 1u) * 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+/* The replacement vector z_c of a dependent column c (see or_block_gmres). */
+static void replacement_vector(int n, int c, double *z) {
+    for (int i = 0; i < n; i++) {
+        const uint64_t k = ((uint64_t)c << 32) | (uint64_t)i;
+        z[i] = 2.0 * ((double)(splitmix64_out(k) >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
+/* The replacement vector z_c, exported for its pin. */
+void or_block_gmres_replacement(int n, int c, double *z) {
+    if (n > 0 && c >= 0 && z) replacement_vector(n, c, z);
+}
+
+/* Two-pass modified Gram-Schmidt of the n x s block M (column-major, in
+ * place) in column order, accumulating the coefficients into Gc (ld rows).
+ * Column c counts as dependent when its norm after orthogonalisation is at
+ * most tol times its norm before; it is then set to zero (a zero column
+ * adds nothing to the later projections) and dead[c] = 1.  Returns the
+ * number of dependent columns. */
+static int mgs2_block(int n, int s, double *M, double *Gc, int ld, double tol, int *dead) {
+    int ndead = 0;
+    for (int c = 0; c < s; c++) {
+        double *v = M + (long)c * n;
+        const double before = nrm2(n, v);
+        for (int pass2 = 0; pass2 < 2; pass2++)
+            for (int q = 0; q < c; q++) {
+                const double h = dot(n, M + (long)q * n, v);
+                Gc[(long)c * ld + q] += h;
+                for (int i = 0; i < n; i++) v[i] -= h * M[(long)q * n + i];
+            }
+        const double nv = nrm2(n, v);
+        dead[c] = !(nv > tol * before);
+        if (dead[c]) {
+            ndead++;
+            memset(v, 0, sizeof(double) * n);
+            continue;
+        }
+        Gc[(long)c * ld + c] = nv;
+        for (int i = 0; i < n; i++) v[i] /= nv;
+    }
+    return ndead;
+}
 int or_block_gmres(int n, int s, const double *A, long lda, const double *B, double *X, int m,
-                   double rtol, int max_iter, int x0_given, int nthreads,
+                   double rtol, int max_iter, int x0_given, int deflate, int nthreads,
                    int *iters_out, int *cycles_out, double *rel_res_out) {
     if (n < 0 || s < 1 || lda < n || m < 1 || max_iter < 0) return OR_ERR_ARG;
     const long ln = n ? n : 1;
@@ -878,6 +946,8 @@ int or_block_gmres(int n, int s, const double *A, long lda, const double *B, dou
     double *cs = calloc((size_t)ncol * s, sizeof(double)), *sn = calloc((size_t)ncol * s, sizeof(double));
     int *rr = calloc((size_t)ncol * s, sizeof(int));
     double *bn = calloc(s, sizeof(double)), *w = malloc(sizeof(double) * ln);
+    double *R0 = malloc(sizeof(double) * ln * s);
+    int *dead = calloc(s, sizeof(int));
     int status = OR_NOT_CONVERGED, total = 0, cycles = 0;
 #define HB(i, k) H[(long)(k) * ld + (i)]
 #define GB(i, c) G[(long)(c) * ld + (i)]
@@ -895,22 +965,19 @@ int or_block_gmres(int n, int s, const double *A, long lda, const double *B, dou
         cycles++;
         memset(H, 0, sizeof(double) * ld * ncol);
         memset(G, 0, sizeof(double) * ld * s);
-        int broke = 0;
-        for (int c = 0; c < s && !broke; c++) {                /* R = V_1 S */
-            double *v = V + (long)c * n;
-            const double before = nrm2(n, v);
-            for (int pass2 = 0; pass2 < 2; pass2++)
-                for (int q = 0; q < c; q++) {
-                    const double h = dot(n, V + (long)q * n, v);
-                    GB(q, c) += h;
-                    for (int i = 0; i < n; i++) v[i] -= h * V[(long)q * n + i];
-                }
-            const double nv = nrm2(n, v);
-            if (!(nv > 1e-14 * before)) { broke = 1; break; }
-            GB(c, c) = nv;
-            for (int i = 0; i < n; i++) v[i] /= nv;
+        /* R = V_1 S; the first pass is the rank-revealing QR of R */
+        memcpy(R0, V, sizeof(double) * n * s);
+        if (mgs2_block(n, s, V, G, ld, deflate ? 1e-6 : 1e-14, dead)) {
+            if (!deflate) { status = OR_BREAKDOWN; break; }
+            memcpy(V, R0, sizeof(double) * n * s);
+            for (int c = 0; c < s; c++)
+                if (dead[c]) replacement_vector(n, c, V + (long)c * n);
+            memset(G, 0, sizeof(double) * ld * s);
+            if (mgs2_block(n, s, V, G, ld, 1e-14, dead)) { status = OR_BREAKDOWN; break; }
+            memset(G, 0, sizeof(double) * ld * s);           /* S = V_1^T R */
+            for (int c = 0; c < s; c++)
+                for (int q = 0; q < s; q++) GB(q, c) = dot(n, V + (long)q * n, R0 + (long)c * n);
         }
-        if (broke) { status = OR_BREAKDOWN; break; }
         int k = 0, nrot = 0, stop = 0;
         for (int j = 0; j < m && total < max_iter && !stop; j++) {
             int lucky = 0;
@@ -993,6 +1060,7 @@ int or_block_gmres(int n, int s, const double *A, long lda, const double *B, dou
     *iters_out = total;
     *cycles_out = cycles;
     free(V); free(H); free(G); free(Y); free(cs); free(sn); free(rr); free(bn); free(w);
+    free(R0); free(dead);
 #undef HB
 #undef GB
     return status;

@@ -99,6 +99,14 @@ MUTATIONS = {
     "block_gmres_backsolve_index": ("for (int q = i + 1; q < k; q++) v -= HB(i, q) * y[q];",
                                     "for (int q = i + 1; q < k; q++) v -= HB(q, i) * y[q];",
                                     lambda o: tbg.test_block_gmres_is_block_krylov_minimiser(o, 2, 3)),
+    "block_gmres_deflated_s_from_basis": ("GB(q, c) = dot(n, V + (long)q * n, R0 + (long)c * n);",
+                                          "GB(q, c) = dot(n, V + (long)q * n, V + (long)c * n);",
+                                          lambda o: tbg.test_deflated_block_gmres_rank_deficient_blocks_converge(o, 8)),
+    "block_gmres_replacement_range": ("z[i] = 2.0 * ((double)(splitmix64_out(k) >> 11) * 0x1.0p-53) - 1.0;",
+                                      "z[i] = 2.0 * ((double)(splitmix64_out(k) >> 11) * 0x1.0p-53) - 0.5;",
+                                      lambda o: tbg.test_replacement_vectors_are_splitmix64(o)),
+    "block_gmres_dependent_column_kept": ("dead[c] = !(nv > tol * before);", "dead[c] = !(nv > 0.0 * tol * before);",
+                                          lambda o: tbg.test_deflated_block_gmres_minimises_over_kept_and_replacement_directions(o, 2)),
     # caught by the hand-derived worked examples (tests/golden)
     "ge_last_max_on_ties": ("if (a > best) { best = a; v = i; }", "if (a >= best) { best = a; v = i; }",
                             lambda o: tgo.test_lu_worked_example(o, "tie_")),
