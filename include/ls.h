@@ -97,7 +97,9 @@ typedef struct {
                            1 = native FP64 FMA                                          */
     int deflate;        /* ls_block_cg_solve: 1 = keep the search directions orthonormal and
                            of full rank, dropping dependent ones (no breakdown on dependent,
-                           zero or converged columns; default), 0 = O'Leary's form          */
+                           zero or converged columns; default), 0 = O'Leary's form;
+                           ls_block_gmres_solve: 1 = replace the dependent columns of a
+                           cycle's starting block (default), 0 = they are a breakdown       */
     int fused;          /* ls_cg_solve / ls_gmres_solve with f64_matvec = 0: 1 = when the rows
                            of A fit in the shared memory of the GPU's co-resident CTAs (n up
                            to about 1800 on 152 SMs), run the whole solve as one kernel that
@@ -281,8 +283,15 @@ int ls_block_cg_solve(ls_ctx *ctx, int n, int s, const double *A, int64_t lda, c
  * block that lost rank; then X += V Y.  Each cycle starts from the true
  * residual and the solve stops when every column's true residual passes.
  * info->iters counts block steps, info->outer_iters cycles, rel_res the
- * largest true relative residual over the columns.  A rank-deficient
- * starting block (dependent or zero columns of B - A X) or a zero rotation
+ * largest true relative residual over the columns.  A cycle's starting
+ * block R = B - A X may be rank-deficient (zero, repeated or dependent
+ * columns: a column whose part orthogonal to the columns before it is at
+ * most 1e-6 of its norm).  With opts->deflate (the default) each such
+ * column is replaced by a fixed pseudo-random vector (entry i of column c:
+ * 2u - 1, u the top 53 bits of output c 2^32 + i of SplitMix64 seeded with
+ * 0, over 2^53), the block is orthonormalised into V_1 and S = V_1^T R, so
+ * every right-hand side, the dependent ones included, is solved; with
+ * opts->deflate = 0 such a block returns LS_BREAKDOWN.  A zero rotation
  * pivot returns LS_BREAKDOWN with the last iterate in X.  opts->precision
  * must be LS_F64 and opts->f64_matvec 0 (else LS_ERR_UNSUPPORTED); s or m
  * outside the limits or ld < n is LS_ERR_ARG.  Host or device pointers.

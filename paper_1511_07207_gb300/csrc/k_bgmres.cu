@@ -6,7 +6,11 @@
 //   bgm_start  R = B - A X there and ||R_c||^2; stop if every column passes;
 //              else V_1 S = R by CholQR2 (two
 //              passes of Gram matrix, Cholesky, triangular solve per row),
-//              G = [S; 0];
+//              G = [S; 0]; when R is rank-deficient (a Cholesky pivot at
+//              most 1e-12 of its diagonal entry) and deflation is on, its
+//              dependent columns (found in column order) are replaced by
+//              fixed pseudo-random vectors, V_1 is the CholQR2 of that block
+//              and S = V_1^T R (deflate_start);
 //   per block step j (graph while-node): P split + block product W = A V_j
 //              (k_bgemv.cu, A read once for all s columns), then bgm_orth:
 //              two passes of block classical Gram-Schmidt against V_1..V_j
@@ -152,6 +156,54 @@ __device__ int cholqr_pass(const BgmVecs &v, double *M, long long lo, long long 
     return 1;
 }
 
+// One warp: the dependent columns of the s x s Gram matrix G of a block, in
+// column order.  The Cholesky factorisation of warp_chol, except that a
+// column whose pivot is at most 1e-12 of its diagonal entry (its part
+// orthogonal to the columns kept before it has at most 1e-6 of its norm) is
+// marked dead[j] = 1 and its column of the factor set to zero, so that it
+// takes no part in the later columns.
+__device__ void warp_chol_skip(int s, double *G, int *dead) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < s; j++) {
+        const double gjj = G[j + j * s];
+        double d = gjj;
+        for (int k = 0; k < j; k++) d -= G[j + k * s] * G[j + k * s];
+        const bool dj = !(d > 1e-12 * gjj) || !isfinite(d);
+        __syncwarp();
+        if (dj) {
+            if (lane < s) G[lane + j * s] = 0.0;
+        } else {
+            d = sqrt(d);
+            if (lane > j && lane < s) {
+                double x = G[lane + j * s];
+                for (int k = 0; k < j; k++) x -= G[lane + k * s] * G[j + k * s];
+                G[lane + j * s] = x / d;
+            }
+            if (lane == 0) G[j + j * s] = d;
+        }
+        if (lane == 0) dead[j] = dj ? 1 : 0;
+        __syncwarp();
+    }
+}
+
+// Output k (counted from 0) of SplitMix64 seeded with 0 (Steele, Lea and
+// Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):
+// the state after k + 1 steps of its Weyl sequence, then its mixing function.
+__device__ __forceinline__ unsigned long long splitmix64_out(unsigned long long k) {
+    unsigned long long x = (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Entry i of the vector that replaces dependent column c of a starting
+// block: 2 u - 1, u = the top 53 bits of output c 2^32 + i over 2^53.
+__device__ __forceinline__ double replacement_entry(int c, long long i) {
+    const unsigned long long k = ((unsigned long long)c << 32) | (unsigned long long)i;
+    const double u = (double)(splitmix64_out(k) >> 11) * 0x1.0p-53;
+    return __dsub_rn(__dmul_rn(2.0, u), 1.0);
+}
+
 // T = R2 R1 for upper-triangular R = L^T factors (block 0, one warp):
 // R1 (from the first pass) is kept in R; R2 is v.Lm^T.  Column-major s x s.
 __device__ void combine_r(const BgmVecs &v, double *R) {
@@ -171,6 +223,56 @@ __device__ void combine_r(const BgmVecs &v, double *R) {
 __device__ __forceinline__ void stop_both(State *st, cudaGraphConditionalHandle ho, cudaGraphConditionalHandle hi) {
     set_cond(st, ho, 0u);
     set_cond(st, hi, 0u);
+}
+
+// V_1 S = R for a rank-deficient R (V's first block), called by every CTA
+// right after a CholQR pass over R found a pivot at most 1e-12 of its
+// diagonal entry (R's partial Gram matrices are still in v.part):
+//   the dependent columns, in column order (warp_chol_skip);
+//   R kept in W, each dependent column of V's first block replaced by its
+//   replacement vector (replacement_entry);
+//   V_1 by CholQR2 of that block;
+//   S = V_1^T R into G's first s rows, G's other rows zero.
+// R = V_1 S then holds for every column up to the dependent columns'
+// remainders (at most 1e-6 of their norms); the block Krylov space grows
+// from the kept directions and the replacements.  Returns 1 on success, 0
+// when the block with the replacements is still rank-deficient (every CTA
+// agrees), -1 on a barrier timeout.
+__device__ int deflate_start(const BgmVecs &v, long long lo, long long hi) {
+    __shared__ double Gs[BGM_MAX_S * BGM_MAX_S];
+    __shared__ int dd[BGM_MAX_S];
+    const int s = v.s;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        for (int e = threadIdx.x; e < s * s; e += 32) Gs[e] = cta_sum(v, e);
+        __syncwarp();
+        warp_chol_skip(s, Gs, dd);
+        __syncwarp();
+        if (threadIdx.x < s) v.dead[threadIdx.x] = dd[threadIdx.x];
+    }
+    if (!grid_sync(v.bar, v.st)) return -1;
+    if (threadIdx.x < s) dd[threadIdx.x] = __ldcg(&v.dead[threadIdx.x]);
+    __syncthreads();
+    for (int c = 0; c < s; c++)
+        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const long long o = (long long)c * v.ld + i;
+            v.W[o] = v.V[o];
+            if (dd[c]) v.V[o] = replacement_entry(c, i);
+        }
+    __syncthreads();
+    int ok = cholqr_pass(v, v.V, lo, hi);
+    if (ok <= 0) return ok;
+    ok = cholqr_pass(v, v.V, lo, hi);
+    if (ok <= 0) return ok;
+    gram_part(v, v.V, s, v.W, lo, hi);              // entry q + c s: V_q . R_c
+    if (!grid_sync(v.bar, v.st)) return -1;
+    if (blockIdx.x == 0) {
+        const int L = ldh(v);
+        for (int e = threadIdx.x; e < L * s; e += blockDim.x) {
+            const int q = e % L, c = e / L;
+            v.G[e] = q < s ? cta_sum(v, q + c * s) : 0.0;
+        }
+    }
+    return 1;
 }
 
 }  // namespace
@@ -260,20 +362,27 @@ __global__ void __launch_bounds__(GT) bgm_start_kernel(BgmVecs v, cudaGraphCondi
         }
         return;
     }
-    // V_1 S = R (CholQR2); a rank-deficient block is a breakdown
+    // V_1 S = R (CholQR2); a rank-deficient block is deflated (deflate_start)
+    // or, without deflation, a breakdown
     int ok = cholqr_pass(v, v.V, lo, hi);
     if (ok < 0) return;
-    if (ok && blockIdx.x == 0 && threadIdx.x < 32) {
-        for (int e = threadIdx.x; e < s * s; e += 32) {
-            const int i = e % s, j = e / s;
-            R[e] = i <= j ? v.Lm[j + i * s] : 0.0;   // R1 = L^T
+    const bool deflated = !ok && v.deflate;
+    if (deflated) {
+        ok = deflate_start(v, lo, hi);
+        if (ok < 0) return;
+    } else {
+        if (ok && blockIdx.x == 0 && threadIdx.x < 32) {
+            for (int e = threadIdx.x; e < s * s; e += 32) {
+                const int i = e % s, j = e / s;
+                R[e] = i <= j ? v.Lm[j + i * s] : 0.0;   // R1 = L^T
+            }
+            __syncwarp();
         }
-        __syncwarp();
+        if (ok) ok = cholqr_pass(v, v.V, lo, hi);
+        if (ok < 0) return;
     }
-    if (ok) ok = cholqr_pass(v, v.V, lo, hi);
-    if (ok < 0) return;
     if (blockIdx.x == 0 && threadIdx.x < 32) {
-        if (ok) {
+        if (ok && !deflated) {
             combine_r(v, R);
             const int L = ldh(v);
             for (int e = threadIdx.x; e < L * s; e += 32) v.G[e] = 0.0;

@@ -2,7 +2,8 @@
 // workspace, staging of A, B and X, the CUDA graph of the iteration, the result.
 //
 // Graph: bgm_init, while(outer){ split X, A X into V's first block (block
-//        product), bgm_start (R = B - A X, ||R_c||^2, the stop test),
+//        product), bgm_start (R = B - A X, ||R_c||^2, the stop test, V_1 S = R
+//        with the dependent columns of R replaced when opts.deflate is set),
 //        while(inner){ split V_j, W = A V_j (block product), bgm_orth }, bgm_finish }
 #include <cuda_runtime.h>
 
@@ -18,7 +19,7 @@ namespace {
 
 struct BgmLayout {
     double *X, *B, *W, *V, *H, *G, *Y, *cs, *sn, *Hc, *Lm, *part, *bn, *r2, *Astage;
-    int *rrow, *flags;
+    int *rrow, *flags, *dead;
     float *Ahi, *Alo, *Ph, *Pl;
     long long ld, lda_stage, ld32, ldp, part_stride;
     size_t bytes;
@@ -49,6 +50,7 @@ BgmLayout bgm_layout(void *base, int n, int s, int m, int grid, bool stageA) {
     L.bn = cv.take<double>(BGM_MAX_S);
     L.r2 = cv.take<double>(BGM_MAX_S);
     L.flags = cv.take<int>(BGF_COUNT);
+    L.dead = cv.take<int>(BGM_MAX_S);
     L.Ahi = cv.take<float>((size_t)n * L.ld32);
     L.Alo = cv.take<float>((size_t)n * L.ld32);
     L.Ph = cv.take<float>((size_t)BCG_MAX_S * L.ldp);
@@ -220,10 +222,12 @@ extern "C" int ls_block_gmres_solve(ls_ctx *c, int n, int s, const double *A, in
     v.bn = L.bn;
     v.r2 = L.r2;
     v.flags = L.flags;
+    v.dead = L.dead;
     v.bar = c->bar;
     v.st = c->st;
     v.rtol = o.rtol;
-    long long key[8] = {300 + s, n, (long long)(uintptr_t)c->ws, m, o.x0_given, L.ld,
+    v.deflate = o.deflate ? 1 : 0;
+    long long key[8] = {300 + s + 50 * v.deflate, n, (long long)(uintptr_t)c->ws, m, o.x0_given, L.ld,
                         (long long)(uintptr_t)c->stream, DT_DS};
     if (!c->graph_bgm.matches(key)) {
         rc = build_bgm_graph(c, v, L, o.x0_given, key);

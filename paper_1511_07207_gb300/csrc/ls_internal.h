@@ -328,9 +328,11 @@ struct BgmVecs {
     long long part_stride;
     double *bn, *r2;              // ||B_c||, ||B_c - A X_c||^2
     int *flags;                   // BGF_*
+    int *dead;                    // the dependent columns of the last starting block (s)
     GridBar *bar;
     State *st;
     double rtol;
+    int deflate;                  // replace dependent starting columns (else a breakdown)
 };
 struct BgmKernels {
     void *init, *start, *orth, *finish;

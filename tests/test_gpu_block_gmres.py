@@ -7,8 +7,16 @@ step count the comparison is element by element, across restarts too.  To a
 tolerance: every column's true residual (computed by the oracle) reaches
 rtol and the step counts agree within a few.  Edge cases: s = 1 (GMRES),
 s = 16, n = 1, ragged n, slow convergence with restarts, an initial guess,
-an exact initial guess, dependent columns (breakdown), B = 0, the iteration
-limit, NaN input, unsupported options and sizes, host buffers.
+an exact initial guess, dependent columns (deflated by default, a breakdown
+with deflate = 0), B = 0, the iteration limit, NaN input, unsupported options
+and sizes, host buffers.
+
+Deflation: a starting block with a dependent, a zero and a repeated column
+has its dependent columns replaced by the same pseudo-random vectors on both
+sides, so at a fixed step count the iterates agree element by element with
+the oracle's; solved to rtol, every column reaches the LAPACK solution, the
+dependent column's solution is the same combination of the others', the
+zero column's is zero and the repeated column's equals the original's.
 """
 import numpy as np
 import pytest
@@ -88,8 +96,10 @@ def test_block_gmres_edge_cases(ctx, gpu):
     n = 64
     A = inputs.nonsym_matrix(n, seed=140)
     b = A @ inputs.solution(n, seed=140)
-    st, info, X = _solve(ctx, gpu, A, np.stack([b, 2 * b], 1), restart=4)
+    st, info, X = _solve(ctx, gpu, A, np.stack([b, 2 * b], 1), restart=4, deflate=0)
     assert st == B.LS_BREAKDOWN
+    st, info, X = _solve(ctx, gpu, A, np.stack([b, 2 * b], 1), restart=4)
+    assert st == B.LS_OK and np.max(np.abs(X[:, 1] - 2 * X[:, 0])) <= 1e-8 * np.max(np.abs(X))
     st, info, X = _solve(ctx, gpu, A, np.zeros((n, 3)), restart=4)
     assert st == B.LS_OK and not X.any() and info["iters"] == 0
     Bm = A @ inputs.solution(n, seed=141, nrhs=3).reshape(n, 3)
@@ -104,3 +114,44 @@ def test_block_gmres_edge_cases(ctx, gpu):
         assert st == B.LS_ERR_UNSUPPORTED
     st, info, X = _solve(ctx, gpu, A, Bm, restart=100)        # 100 x 3 > 256
     assert st == B.LS_ERR_ARG
+
+
+def _deficient_block(A, n, seed):
+    """Columns b0, b1, b0 + 2 b1 (dependent), 0, b2, b1 (a repeat)."""
+    Bf = A @ inputs.solution(n, seed=seed, nrhs=3).reshape(n, 3)
+    return np.column_stack([Bf[:, 0], Bf[:, 1], Bf[:, 0] + 2 * Bf[:, 1], np.zeros(n), Bf[:, 2], Bf[:, 1]])
+
+
+@pytest.mark.parametrize("n,m", [(200, 4), (777, 6)])
+def test_block_gmres_deflated_fixed_count_elementwise(ctx, gpu, oracle, n, m):
+    A = inputs.restart_matrix(n, seed=150 + n)
+    Bm = _deficient_block(A, n, 151 + n)
+    for k in (1, 2, m + 1):             # the last one crosses a restart
+        st, info, X = _solve(ctx, gpu, A, Bm, rtol=1e-300, max_iter=k, restart=m)
+        ref = oracle.block_gmres(A, Bm, m=m, rtol=1e-300, max_iter=k)
+        assert st == B.LS_NOT_CONVERGED == ref["status"]
+        assert info["iters"] == ref["iters"] == k
+        assert info["outer_iters"] == ref["cycles"]
+        assert np.max(np.abs(X - ref["X"])) <= 1e-10 * np.max(np.abs(ref["X"]))
+        assert not X[:, 3].any()
+        assert np.max(np.abs(X[:, 5] - X[:, 1])) <= 1e-13 * np.max(np.abs(X))
+
+
+@pytest.mark.parametrize("n,m", [(300, 5), (1000, 10)])
+def test_block_gmres_deflated_converges(ctx, gpu, oracle, n, m):
+    A = inputs.nonsym_matrix(n, seed=160 + n)
+    Bm = _deficient_block(A, n, 161 + n)
+    st0, _, _ = _solve(ctx, gpu, A, Bm, rtol=1e-10, restart=m, deflate=0)
+    assert st0 == B.LS_BREAKDOWN
+    st, info, X = _solve(ctx, gpu, A, Bm, rtol=1e-10, restart=m)
+    ref = oracle.block_gmres(A, Bm, m=m, rtol=1e-10)
+    assert st == B.LS_OK == ref["status"]
+    cols = [0, 1, 2, 4, 5]
+    tr = _true_rel(oracle, A, Bm[:, cols], X[:, cols])
+    assert tr <= 1e-10 and abs(info["rel_res"] - tr) <= 1e-3 * tr + 1e-14
+    assert abs(info["iters"] - ref["iters"]) <= 2 + ref["iters"] // 10
+    sc = np.max(np.abs(X))
+    assert not X[:, 3].any() and np.max(np.abs(X[:, 5] - X[:, 1])) <= 1e-12 * sc
+    assert np.max(np.abs(X[:, 2] - (X[:, 0] + 2 * X[:, 1]))) <= 1e-8 * sc
+    assert np.max(np.abs(X - np.linalg.solve(A, Bm))) <= 1e-7 * sc
+    assert np.max(np.abs(X - ref["X"])) <= 1e-7 * sc
