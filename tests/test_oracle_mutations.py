@@ -18,6 +18,7 @@ import test_oracle_cg as tcg
 import test_oracle_cholesky as tch
 import test_oracle_ge_quant as tgq
 import test_oracle_gauss_seidel as tgs
+import test_oracle_gemv as tgv
 import test_oracle_gmres as tgm
 import test_oracle_golden as tgo
 import test_oracle_jacobi as tja
@@ -31,6 +32,12 @@ MUTATIONS = {
     "gemv_transposed": ("for (int j = 0; j < ncols; j++) s += a[j] * x[j];",
                         "for (int j = 0; j < ncols; j++) s += A[(long)j * lda + i] * x[j];",
                         lambda o: tgm.test_gmres_matches_lapack(o, 64)),
+    "gemv_right_to_left": ("for (int j = 0; j < ncols; j++) s += a[j] * x[j];",
+                           "for (int j = ncols - 1; j >= 0; j--) s += a[j] * x[j];",
+                           lambda o: tgv.test_rows_summed_left_to_right(o)),
+    "residual_sign": ("for (int i = 0; i < n; i++) r[i] = b[i] - r[i];",
+                      "for (int i = 0; i < n; i++) r[i] = r[i] - b[i];",
+                      lambda o: tgv.test_residual_exact_on_integers(o)),
     "givens_g_sign": ("g[k + 1] = -sn[k] * g[k];", "g[k + 1] = sn[k] * g[k];",
                       lambda o: tgm.test_gmres_minimal_residual(o)),
     "givens_rot_sign": ("HR(j + 1, k) = -sn[j] * a + cs[j] * c;",
