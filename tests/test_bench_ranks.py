@@ -36,7 +36,7 @@ def _rank_main(rank, world, port, times, out):
 def test_max_over_ranks_gloo_world2():
     world, port = 2, _free_port()
     times = [120.0, 250.0]                      # rank 1 is the slowest
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of a process with threads
         out = m.dict()
         mp.spawn(_rank_main, args=(world, port, times, out), nprocs=world, join=True)
         res = dict(out)
